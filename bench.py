@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the W2-FWI likelihood-guidance gradient on GB300.
+
+One step = one pass of the whole hot path over a batch of B synthetic 70x70
+models (5 surface shots, 70 receivers, 1000 steps, 40-cell absorbing layer):
+observation preparation, forward solve with wavefield record, W2 misfit and
+adjoint source, adjoint solve with imaging and fold, and the preconditioned
+guided update.  Metric: W2-FWI gradients/s (plus Gcell-updates/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank owns its own B models (weak scaling, no
+data-path collective); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NZ_PHYS, NX_PHYS, NB, NT, NS, NR, DX, DT = 70, 70, 40, 1000, 5, 70, 10.0, 1e-3
+METRIC = "W2-FWI gradients/s (70x70, 5 shots, 1000 steps)"
+UNIT = "gradients/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload_inputs(B, seed0):
+    from paper_2603_16393_gb300 import inputs as I
+    vt = I.model_batch("layered", range(seed0, seed0 + B), NZ_PHYS, NX_PHYS)
+    v0 = np.stack([I.linear_initial_model(NZ_PHYS, NX_PHYS)] * B)
+    geo = I.surface_geometry(NX_PHYS, NS, NR)
+    return vt, v0, geo
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
+        loaded = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(n_models, threads, seed0=0):
+    """Time the FP64 oracle on a bounded sample of the same workload: n_models
+    full gradients (forward + W2 misfit + adjoint for each of the 5 shots)."""
+    from oracle import oracle as O
+    vt, v0, geo = workload_inputs(n_models, seed0)
+    op = O.Problem(nz=NZ_PHYS, nx=NX_PHYS, nb=NB, nt=NT, dz=DX, dx=DX, dt=DT, src_iz=geo.src_iz,
+                   src_ix=geo.src_ix, rec_iz=geo.rec_iz, rec_ix=geo.rec_ix)
+    w2p = O.W2Params()
+    ctx = O.w2_prepare(O.forward(op, vt, threads=threads), op.dt, w2p)
+    t = time.perf_counter()
+    O.gradient(op, v0, ctx, w2p, threads=threads)
+    return time.perf_counter() - t
+
+
+def cpu_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle as it stands, on the host cores, rank 0 only."""
+    if rank != 0:
+        return
+    threads = cpu_cores()
+    n_models = max(1, threads // NS + (1 if threads % NS else 0))
+    for _ in range(args.warmup):
+        oracle_sample(n_models, threads)
+    times = [oracle_sample(n_models, threads) for _ in range(args.steps)]
+    tstep = statistics.mean(times)
+    value = n_models / tstep
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tstep * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded layered models)",
+        "config": {"workload": f"{n_models} x 70x70 layered models, 5 shots, 70 receivers, "
+                               "1000 steps, 40-cell absorbing layer (bounded CPU sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{n_models} full gradients per step on {threads} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our path
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_16393_gb300 import api
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B = args.batch
+    vt, v0, geo = workload_inputs(B, seed0=rank * B)
+    prob = api.Problem(nz=NZ_PHYS, nx=NX_PHYS, nb=NB, nt=NT, dz=DX, dx=DX, dt=DT,
+                       src_iz=geo.src_iz, src_ix=geo.src_ix, rec_iz=geo.rec_iz,
+                       rec_ix=geo.rec_ix, v_max=4500.0, batch=B)
+    plan = api.Plan(prob, api.W2Params(), device=dev)
+    gparams = api.GuideParams(rho0=1.15, gamma=0.55)   # Table 1 (CurveVel-A), Sec. 6.3 c, tau, eps
+    stream = torch.cuda.current_stream(dev)
+
+    # observed data of the true models (untimed setup), inputs resident in HBM
+    vt_d = torch.tensor(vt, dtype=torch.float32, device=dev)
+    d_obs, _ = plan.forward(vt_d, store=False)
+    d_obs = d_obs.clone()
+    v_d = torch.tensor(v0, dtype=torch.float32, device=dev)
+    ctx = plan.new_ctx()
+    shape = plan.model_shape
+    d_syn = torch.empty(plan.data_shape, dtype=torch.float32, device=dev)
+    adj = torch.empty(plan.data_shape, dtype=torch.float32, device=dev)
+    J = torch.empty(B, dtype=torch.float32, device=dev)
+    grad = torch.empty(shape, dtype=torch.float32, device=dev)
+    vn = torch.empty(shape, dtype=torch.float32, device=dev)
+    gn = torch.empty(shape, dtype=torch.float32, device=dev)
+    v_out = torch.empty(shape, dtype=torch.float32, device=dev)
+    rho = torch.empty(B, dtype=torch.float32, device=dev)
+    ev = {k: [] for k in ("fwd0", "fwd1", "adj0", "adj1")}
+
+    def step(v_in, dobs_in, timed):
+        api.fwi_w2_prepare(plan.handle, dobs_in, ctx)
+        if timed:
+            e0 = torch.cuda.Event(enable_timing=True); e0.record(stream)
+        api.fwi_forward(plan.handle, v_in, d_syn, plan.snapshots, plan.workspace)
+        if timed:
+            e1 = torch.cuda.Event(enable_timing=True); e1.record(stream)
+        api.fwi_w2_misfit(plan.handle, ctx, d_syn, J, None, adj, plan.workspace)
+        if timed:
+            e2 = torch.cuda.Event(enable_timing=True); e2.record(stream)
+        api.fwi_adjoint_grad(plan.handle, v_in, adj, plan.snapshots, grad, plan.workspace)
+        if timed:
+            e3 = torch.cuda.Event(enable_timing=True); e3.record(stream)
+            ev["fwd0"].append(e0); ev["fwd1"].append(e1); ev["adj0"].append(e2); ev["adj1"].append(e3)
+        # guidance in the normalised space v_n = (v - 3000)/1500: dJ/dv_n = 1500 dJ/dv
+        torch.sub(v_in, 3000.0, out=vn).div_(1500.0)
+        torch.mul(grad, 1500.0, out=gn)
+        api.fwi_guided_step(B, NZ_PHYS, NX_PHYS, gparams, vn, vn, gn, gn, v_out, rho)
+
+    kernels_per_step = 3 + 1 + 2 + 2 + 1   # prepare, forward, misfit, adjoint+shot sum, guided
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step(v_d, d_obs, False)
+    barrier()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(v_d, d_obs, True)
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop() if clocks else None
+    plan.check()
+    ms = t0.elapsed_time(t1) / args.steps
+    fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(ev["fwd0"], ev["fwd1"]))
+    adj_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(ev["adj0"], ev["adj1"]))
+
+    # end to end through the public API with pinned host buffers
+    v_h = torch.tensor(v0, dtype=torch.float32).pin_memory()
+    dobs_h = d_obs.cpu().pin_memory()
+    out_grad_h = torch.empty(shape, dtype=torch.float32).pin_memory()
+    out_J_h = torch.empty(B, dtype=torch.float32).pin_memory()
+    out_v_h = torch.empty(shape, dtype=torch.float32).pin_memory()
+    v_e = torch.empty_like(v_d)
+    dobs_e = torch.empty_like(d_obs)
+    barrier()
+    e_s = torch.cuda.Event(enable_timing=True)
+    e_e = torch.cuda.Event(enable_timing=True)
+    e_s.record(stream)
+    for _ in range(args.steps):
+        v_e.copy_(v_h, non_blocking=True)
+        dobs_e.copy_(dobs_h, non_blocking=True)
+        step(v_e, dobs_e, False)
+        out_grad_h.copy_(grad, non_blocking=True)
+        out_J_h.copy_(J, non_blocking=True)
+        out_v_h.copy_(v_out, non_blocking=True)
+    e_e.record(stream)
+    barrier()
+    e2e_ms = e_s.elapsed_time(e_e) / args.steps
+    h2d = (v_h.numel() + dobs_h.numel()) * 4
+    d2h = (out_grad_h.numel() + out_J_h.numel() + out_v_h.numel()) * 4
+
+    # max over ranks
+    vals = torch.tensor([ms, e2e_ms, fwd_ms, adj_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms, e2e_ms, fwd_ms, adj_ms = vals.tolist()
+    if rank != 0:
+        return
+
+    plane = (NZ_PHYS + NB) * (NX_PHYS + 2 * NB)
+    cell_updates = 2 * B * NS * NT * plane          # forward + adjoint, per step per rank
+    # dominant kernel: the adjoint propagator; its algorithmic HBM traffic per
+    # launch = the wavefield record it streams in (4 B per cell-update) + the
+    # adjoint source + the model + the per-shot gradient
+    adj_bytes = B * NS * NT * plane * 4 + B * NS * NR * NT * 4 + B * NZ_PHYS * NX_PHYS * 4 * (1 + NS + 1)
+    fwd_bytes = B * NS * NT * plane * 4 + B * NS * NR * NT * 4 + B * NZ_PHYS * NX_PHYS * 4
+    hbm_peak, peak_kind = peaks()
+    dom = max((adj_ms, adj_bytes, "adjoint propagator"), (fwd_ms, fwd_bytes, "forward propagator"))
+    achieved = dom[1] / (dom[0] * 1e-3) / 1e9
+    value = world * B / (ms * 1e-3)
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        threads = cpu_cores()
+        n_models = max(1, (2 * threads + NS - 1) // NS)
+        t = oracle_sample(n_models, threads)
+        cpu = {"value": n_models / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{n_models} full 70x70 gradients (5 shots x 1000 steps, FP64) on "
+                         f"{threads} threads, {t:.1f} s wall"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded layered models)",
+        "config": {"workload": f"{B} x 70x70 layered models per GPU, 5 shots, 70 receivers, "
+                               "1000 steps, 40-cell absorbing layer, store-all wavefield record",
+                   "batch_per_gpu": B, "global_batch": B * world,
+                   "l2": "inputs larger than L2 (wavefield record %.1f GB per step)"
+                         % (B * NS * NT * plane * 4 / 1e9),
+                   "gcell_updates_per_s": world * cell_updates / (ms * 1e-3) / 1e9},
+        "roofline": {"bound": "hbm", "kernel": dom[2], "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                     "peak_source": peak_kind, "ms_per_launch": dom[0]},
+        "kernel_ms": {"forward": fwd_ms, "adjoint": adj_ms},
+        "e2e": {"value": world * B / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=152)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1 and args.impl == "ours":
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

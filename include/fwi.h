@@ -1,0 +1,216 @@
+/*
+ * fwi.h -- C ABI of the GB300 (sm_103a) likelihood-guidance gradient library
+ * for "Robust Physics-Guided Diffusion for Full-Waveform Inversion"
+ * (arXiv 2603.16393).
+ *
+ * The library computes, for a batch of B velocity models and Ns shots each:
+ *   fwi_forward       d_syn = F(v): 2D constant-density acoustic FD solve
+ *                     (Eq. 1; 2nd order in time, 4th order in space, absorbing
+ *                     layer, Ricker source, receiver restriction R; Sec. 2.1, 6.1)
+ *   fwi_w2_prepare    the observation-only quantities of the misfit (Sec. 5.1:
+ *                     weight omega, shift c', observed quantiles, S_obs)
+ *   fwi_w2_misfit     J(v) = sum_{s,r} W2 / S_obs (Eq. final_objective) and the
+ *                     adjoint source dJ/dd_syn
+ *   fwi_adjoint_grad  dJ/dv by the time-reversed discrete adjoint solve
+ *                     (the F'* of Eq. dps_baseline_step, Sec. 4.2)
+ *   fwi_guided_step   v_{i-1} = v'_{i-1} - rho_i D_i h (Eq. precond_step,
+ *                     Eq. tv, Eq. rho, Eq. kappa; Algorithm 2)
+ *
+ * Conventions shared by every call
+ *   - Array arguments are DEVICE pointers to contiguous float32 (int32 where
+ *     stated) buffers owned and allocated by the caller.  The library never
+ *     allocates device memory and never frees caller memory.
+ *   - Layouts are row-major with the last index fastest:
+ *       v, grad           [B][nz][nx]          m/s and 1/(m/s); row = depth z
+ *       d_obs, d_syn, adj [B][ns][nr][nt]      traces, sample n at t_n = n dt
+ *       w2                [B][ns][nr]
+ *       J, rho            [B]
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls only enqueue work; they return before it runs.
+ *   - Argument checks happen on the host before anything is enqueued; a
+ *     failing check returns an error code and enqueues nothing.  Launch
+ *     failures return FWI_ERR_CUDA.  Conditions only the device can see
+ *     (a velocity above the declared v_max or not positive) are written to a
+ *     status word in the workspace; fwi_check() reads it.
+ *   - fwi_last_error() returns a message for the last failing call of the
+ *     calling thread.
+ *   - Results are deterministic: the same inputs give bitwise-identical
+ *     outputs (no floating-point atomics; fixed reduction orders).
+ */
+#ifndef FWI_H
+#define FWI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FWI_VERSION 10000  /* major*10000 + minor*100 + patch */
+
+#if defined(__GNUC__)
+#define FWI_API __attribute__((visibility("default")))
+#else
+#define FWI_API
+#endif
+
+/* Limits of this build. */
+#define FWI_MAX_SHOTS 256
+#define FWI_MAX_RECEIVERS 1024
+
+typedef enum fwi_status {
+    FWI_OK = 0,
+    FWI_ERR_INVALID_ARG = 1,    /* a pointer, size or parameter is invalid      */
+    FWI_ERR_UNSTABLE_CFL = 2,   /* v_max dt sqrt(1/dx^2+1/dz^2) > sqrt(3)/2, or a
+                                   velocity above v_max / not positive was found
+                                   on the device                                   */
+    FWI_ERR_UNSUPPORTED = 3,    /* valid but outside what this build implements */
+    FWI_ERR_CUDA = 4,           /* a CUDA runtime call or launch failed         */
+    FWI_ERR_DEVICE_TIMEOUT = 5, /* a device-side wait ran out of its budget     */
+    FWI_ERR_OOM = 6             /* a caller buffer is too small                 */
+} fwi_status;
+
+/* Discretisation and acquisition (Sec. 2.1, 6.1; see the readings listed with
+ * each field).  Host struct; fwi_plan_create copies everything it needs,
+ * including the index arrays. */
+typedef struct fwi_problem {
+    int nz, nx;          /* physical grid (rows = depth), >= 1                      */
+    float dz, dx;        /* grid spacing in m, > 0                                  */
+    int nb;              /* absorbing-layer width in cells on left, right, bottom   */
+    int top_bc;          /* 0: zero ghosts above row 0; 1: mirror (du/dn = 0, Eq. 1) */
+    int nt;              /* time steps, >= 2                                        */
+    float dt;            /* time step in s, > 0                                     */
+    int ns, nr;          /* shots (<= FWI_MAX_SHOTS), receivers (<= FWI_MAX_RECEIVERS) */
+    const int *src_iz, *src_ix;   /* HOST arrays [ns]: source cell per shot          */
+    const int *rec_iz, *rec_ix;   /* HOST arrays [nr]: receivers shared by all shots */
+    float f_peak;        /* Ricker peak frequency in Hz (Sec. 6.1: 15)              */
+    float t0;            /* Ricker delay in s; <= 0 selects 1.1 / f_peak (Sec. 6.1) */
+    float v_ref;         /* speed the damping is designed for, m/s (not differentiated) */
+    float refl_R;        /* nominal two-way amplitude reflection of the layer, (0,1] */
+    float v_max;         /* declared upper bound of every velocity passed in, m/s  */
+    int batch;           /* B models per call, >= 1                                 */
+} fwi_problem;
+
+/* Misfit hyperparameters (Sec. 5.1, 6.2, 6.3): k = 100, c' factor 1.1,
+ * eps' = 1e-9, N_xi = 1000. */
+typedef struct fwi_w2_params {
+    float k;             /* Eq. omega_def, >= 0                                     */
+    float cshift_factor; /* c' = cshift_factor |min_t omega d_obs|, >= 0            */
+    float eps_density;   /* eps' in the density denominator, >= 0                   */
+    int n_xi;            /* quantile nodes xi_j = j/(n_xi-1), >= 2                  */
+} fwi_w2_params;
+
+/* Guided-step hyperparameters (Eq. rho, Eq. kappa; Sec. 6.3: c = 0.1, tau = 0,
+ * eps = 1e-4, gamma and rho0 per dataset in Table 1).  kappa is clipped to
+ * [kappa_min, kappa_max] only when kappa_min < kappa_max. */
+typedef struct fwi_guide_params {
+    float rho0, c, tau, gamma, eps, kappa_min, kappa_max;
+} fwi_guide_params;
+
+typedef struct fwi_plan fwi_plan;   /* opaque, host memory only */
+
+/* Validate a problem and build a plan (host only; no CUDA call).
+ * Checks every field above, the CFL bound for v_max (sqrt(3)/2 is the
+ * leapfrog limit of the 4th-order Laplacian, whose symbol is at most 16/3),
+ * that sources and receivers lie on the physical grid, and that this build
+ * can run the grid (FWI_ERR_UNSUPPORTED otherwise).  *out receives the plan
+ * or NULL.  Errors: FWI_ERR_INVALID_ARG, FWI_ERR_UNSTABLE_CFL,
+ * FWI_ERR_UNSUPPORTED. */
+FWI_API fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2,
+                           fwi_plan **out);
+
+/* Release a plan (NULL is ignored). */
+FWI_API void fwi_plan_destroy(fwi_plan *plan);
+
+/* Bytes the caller must provide:
+ *   workspace: device scratch passed to fwi_forward / fwi_w2_misfit /
+ *              fwi_adjoint_grad / fwi_check; its first 256 bytes hold the
+ *              device status word;
+ *   obs_ctx:   filled by fwi_w2_prepare, read by fwi_w2_misfit;
+ *   snapshots: the forward wavefield record (nt time levels of the padded
+ *              grid per model and shot) that fwi_adjoint_grad reads.
+ * Any output pointer may be NULL. */
+FWI_API fwi_status fwi_plan_sizes(const fwi_plan *plan, size_t *workspace_bytes,
+                          size_t *obs_ctx_bytes, size_t *snapshot_bytes);
+
+/* Padded grid of the plan: NZ = nz + nb, NX = nx + 2 nb. */
+FWI_API fwi_status fwi_plan_padded(const fwi_plan *plan, int *NZ, int *NX);
+
+/* Forward solve of Eq. (1) for every model and shot (Sec. 2.1, 6.1).
+ *   v         [B][nz][nx] device, m/s; every value must be in (0, v_max]
+ *   d_syn     [B][ns][nr][nt] device, written: sample n = field at step n+1
+ *             at each receiver
+ *   snapshots device buffer of fwi_plan_sizes' snapshot_bytes, written with
+ *             the record fwi_adjoint_grad needs; NULL to skip it (e.g. when
+ *             only data are wanted)
+ *   workspace device buffer of workspace_bytes; its status word is reset
+ * A velocity outside (0, v_max] sets FWI_ERR_UNSTABLE_CFL in the status word
+ * and leaves that model's outputs undefined. */
+FWI_API fwi_status fwi_forward(const fwi_plan *plan, const float *v, float *d_syn,
+                       float *snapshots, void *workspace, void *stream);
+
+/* Observation-only part of the misfit for B observed data cubes
+ * (Sec. 5.1 (I)-(III), Sec. 6.2):
+ *   M = max_{s,r,t} |d_obs|, omega = 1/(1 + k |d_obs| / M)      (Eq. omega_def)
+ *   c'(s,r) = cshift_factor |min_t omega d_obs|                  (Sec. 6.2)
+ *   Q_obs = quantiles of P(omega d_obs + c')                     (Eq. pdf_map, Wp_1d)
+ *   S_obs = sum_{s,r} (int_0^1 |Q_obs|^2)^(1/2)                  (Sec. 5.1 (III))
+ *   d_obs   [B][ns][nr][nt] device
+ *   obs_ctx device buffer of obs_ctx_bytes, written (opaque layout). */
+FWI_API fwi_status fwi_w2_prepare(const fwi_plan *plan, const float *d_obs, void *obs_ctx,
+                          void *stream);
+
+/* Weighted, normalised W2 misfit (Eq. final_objective; Sec. 6.2 numerics:
+ * trapezoid CDF, interpolated generalised-inverse quantiles, trapezoid in xi)
+ * and its exact derivative.
+ *   obs_ctx  from fwi_w2_prepare (same plan)
+ *   d_syn    [B][ns][nr][nt] device
+ *   J        [B] device, written
+ *   w2       [B][ns][nr] device, written per-trace W2; NULL to skip
+ *   adj_src  [B][ns][nr][nt] device, written dJ/dd_syn; NULL to skip
+ *   workspace device buffer of workspace_bytes (per-trace scratch) */
+FWI_API fwi_status fwi_w2_misfit(const fwi_plan *plan, const void *obs_ctx, const float *d_syn,
+                         float *J, float *w2, float *adj_src, void *workspace,
+                         void *stream);
+
+/* dJ/dv by the discrete adjoint of fwi_forward (time-reversed solve with the
+ * adjoint source injected at the receivers, imaging condition, fold of the
+ * absorbing layer onto the edge cells, sum over shots in a fixed order).
+ *   v         [B][nz][nx] device, the same models fwi_forward was given
+ *   adj_src   [B][ns][nr][nt] device (from fwi_w2_misfit)
+ *   snapshots the record fwi_forward wrote for these models
+ *   grad      [B][nz][nx] device, written, 1/(m/s)
+ *   workspace device buffer of workspace_bytes */
+FWI_API fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const float *adj_src,
+                            const float *snapshots, float *grad, void *workspace,
+                            void *stream);
+
+/* Preconditioned guided update of Algorithm 2 for B instances of nz x nx:
+ *   TV  = (1/N_g) sum |forward differences| of v0hat        (Eq. tv; a
+ *         difference leaving the grid counts as 0)
+ *   rho = rho0 exp(-(TV - tau)_+ / c)                        (Eq. rho)
+ *   kappa_j = ((||g||_inf + eps)/(|g_j| + eps))^gamma         (Eq. kappa)
+ *   v_out = v_prime - rho kappa . h                          (Eq. precond_step)
+ *   v_prime, v0hat, g (= grad wrt v0hat), h (= grad wrt v_i): [B][nz][nx] device
+ *   v_out  [B][nz][nx] device, written (may alias v_prime)
+ *   rho_out [B] device, written; NULL to skip
+ * TV is taken on v0hat as passed (callers pass the normalised field). */
+FWI_API fwi_status fwi_guided_step(int batch, int nz, int nx, const fwi_guide_params *params,
+                           const float *v_prime, const float *v0hat, const float *g,
+                           const float *h, float *v_out, float *rho_out, void *stream);
+
+/* Wait for `stream` and return the device status word of `workspace`
+ * (FWI_OK, FWI_ERR_UNSTABLE_CFL, FWI_ERR_DEVICE_TIMEOUT), then clear it. */
+FWI_API fwi_status fwi_check(const fwi_plan *plan, void *workspace, void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+FWI_API const char *fwi_last_error(void);
+
+/* FWI_VERSION of the loaded library. */
+FWI_API int fwi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FWI_H */

@@ -1,0 +1,363 @@
+"""Thin Python binding of libfwi.so (C ABI in include/fwi.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch provides device memory and the current CUDA stream.  The
+module refuses to import when libfwi.so is missing: there is no fallback.
+
+Functions named ``fwi_*`` take the same arguments as the C entry points, with
+torch tensors in place of device pointers.  :class:`Plan` bundles a plan with
+the buffers it needs and offers the whole gradient in one call.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfwi.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+# status codes (fwi_status)
+FWI_OK = 0
+FWI_ERR_INVALID_ARG = 1
+FWI_ERR_UNSTABLE_CFL = 2
+FWI_ERR_UNSUPPORTED = 3
+FWI_ERR_CUDA = 4
+FWI_ERR_DEVICE_TIMEOUT = 5
+FWI_ERR_OOM = 6
+FWI_MAX_SHOTS = 256
+FWI_MAX_RECEIVERS = 1024
+
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("nz", ctypes.c_int), ("nx", ctypes.c_int), ("dz", ctypes.c_float),
+                ("dx", ctypes.c_float), ("nb", ctypes.c_int), ("top_bc", ctypes.c_int),
+                ("nt", ctypes.c_int), ("dt", ctypes.c_float), ("ns", ctypes.c_int),
+                ("nr", ctypes.c_int), ("src_iz", _ip), ("src_ix", _ip), ("rec_iz", _ip),
+                ("rec_ix", _ip), ("f_peak", ctypes.c_float), ("t0", ctypes.c_float),
+                ("v_ref", ctypes.c_float), ("refl_R", ctypes.c_float), ("v_max", ctypes.c_float),
+                ("batch", ctypes.c_int)]
+
+
+class _W2(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_float), ("cshift_factor", ctypes.c_float),
+                ("eps_density", ctypes.c_float), ("n_xi", ctypes.c_int)]
+
+
+class _Guide(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in
+                ("rho0", "c", "tau", "gamma", "eps", "kappa_min", "kappa_max")]
+
+
+_S = ctypes.c_int
+_lib.fwi_plan_create.restype = _S
+_lib.fwi_plan_create.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_W2), ctypes.POINTER(_vp)]
+_lib.fwi_plan_destroy.restype = None
+_lib.fwi_plan_destroy.argtypes = [_vp]
+_lib.fwi_plan_sizes.restype = _S
+_lib.fwi_plan_sizes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t),
+                                ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+_lib.fwi_plan_padded.restype = _S
+_lib.fwi_plan_padded.argtypes = [_vp, _ip, _ip]
+_lib.fwi_forward.restype = _S
+_lib.fwi_forward.argtypes = [_vp] * 6
+_lib.fwi_w2_prepare.restype = _S
+_lib.fwi_w2_prepare.argtypes = [_vp] * 4
+_lib.fwi_w2_misfit.restype = _S
+_lib.fwi_w2_misfit.argtypes = [_vp] * 8
+_lib.fwi_adjoint_grad.restype = _S
+_lib.fwi_adjoint_grad.argtypes = [_vp] * 7
+_lib.fwi_guided_step.restype = _S
+_lib.fwi_guided_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(_Guide)] + [_vp] * 7
+_lib.fwi_check.restype = _S
+_lib.fwi_check.argtypes = [_vp, _vp, _vp]
+_lib.fwi_last_error.restype = ctypes.c_char_p
+_lib.fwi_last_error.argtypes = []
+_lib.fwi_version.restype = ctypes.c_int
+_lib.fwi_version.argtypes = []
+
+
+class FwiError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fwi status {code}: {msg}")
+        self.code = code
+
+
+def _check(code: int):
+    if code != FWI_OK:
+        raise FwiError(code, _lib.fwi_last_error().decode())
+
+
+def fwi_version() -> int:
+    return _lib.fwi_version()
+
+
+def fwi_last_error() -> str:
+    return _lib.fwi_last_error().decode()
+
+
+# ----------------------------------------------------------------- parameter mirrors
+
+@dataclasses.dataclass
+class Problem:
+    """Mirror of ``fwi_problem`` (see include/fwi.h for every field)."""
+    nz: int
+    nx: int
+    nb: int
+    nt: int
+    dz: float
+    dx: float
+    dt: float
+    src_iz: Sequence[int]
+    src_ix: Sequence[int]
+    rec_iz: Sequence[int]
+    rec_ix: Sequence[int]
+    f_peak: float = 15.0
+    t0: float = 0.0
+    v_ref: float = 4500.0
+    refl_R: float = 1e-3
+    v_max: float = 4500.0
+    batch: int = 1
+    top_bc: int = 0
+
+    @property
+    def ns(self):
+        return len(self.src_ix)
+
+    @property
+    def nr(self):
+        return len(self.rec_ix)
+
+    @property
+    def NZ(self):
+        return self.nz + self.nb
+
+    @property
+    def NX(self):
+        return self.nx + 2 * self.nb
+
+
+@dataclasses.dataclass
+class W2Params:
+    """Mirror of ``fwi_w2_params``; defaults are the paper's (Sec. 6.2, 6.3)."""
+    k: float = 100.0
+    cshift_factor: float = 1.1
+    eps_density: float = 1e-9
+    n_xi: int = 1000
+
+
+@dataclasses.dataclass
+class GuideParams:
+    """Mirror of ``fwi_guide_params``; c, tau, eps default to Sec. 6.3."""
+    rho0: float = 1.0
+    c: float = 0.1
+    tau: float = 0.0
+    gamma: float = 0.5
+    eps: float = 1e-4
+    kappa_min: float = 0.0
+    kappa_max: float = 0.0
+
+    def _c(self):
+        return _Guide(*(float(getattr(self, f)) for f, _ in _Guide._fields_))
+
+
+# ----------------------------------------------------------------- marshalling helpers
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t, shape, name):
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return _ptr(t)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class _Handle:
+    def __init__(self, raw):
+        self.raw = raw
+
+    def __del__(self):
+        if self.raw:
+            _lib.fwi_plan_destroy(self.raw)
+            self.raw = None
+
+
+def fwi_plan_create(prob: Problem, w2: W2Params) -> _Handle:
+    arrays = [(ctypes.c_int * len(a))(*[int(x) for x in a])
+              for a in (prob.src_iz, prob.src_ix, prob.rec_iz, prob.rec_ix)]
+    cp = _Problem(prob.nz, prob.nx, prob.dz, prob.dx, prob.nb, prob.top_bc, prob.nt, prob.dt,
+                  len(prob.src_ix), len(prob.rec_ix),
+                  *[ctypes.cast(a, _ip) for a in arrays],
+                  prob.f_peak, prob.t0, prob.v_ref, prob.refl_R, prob.v_max, prob.batch)
+    if len(prob.src_iz) != len(prob.src_ix) or len(prob.rec_iz) != len(prob.rec_ix):
+        raise ValueError("source/receiver index lists differ in length")
+    cw = _W2(w2.k, w2.cshift_factor, w2.eps_density, w2.n_xi)
+    out = _vp()
+    _check(_lib.fwi_plan_create(ctypes.byref(cp), ctypes.byref(cw), ctypes.byref(out)))
+    return _Handle(out)
+
+
+def fwi_plan_sizes(plan: _Handle):
+    ws, ctx, snap = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(_lib.fwi_plan_sizes(plan.raw, ctypes.byref(ws), ctypes.byref(ctx), ctypes.byref(snap)))
+    return ws.value, ctx.value, snap.value
+
+
+def fwi_forward(plan, v, d_syn, snapshots, workspace, stream=None):
+    _check(_lib.fwi_forward(plan.raw, _ptr(v), _ptr(d_syn), _ptr(snapshots), _ptr(workspace),
+                            _stream(stream)))
+
+
+def fwi_w2_prepare(plan, d_obs, obs_ctx, stream=None):
+    _check(_lib.fwi_w2_prepare(plan.raw, _ptr(d_obs), _ptr(obs_ctx), _stream(stream)))
+
+
+def fwi_w2_misfit(plan, obs_ctx, d_syn, J, w2, adj_src, workspace, stream=None):
+    _check(_lib.fwi_w2_misfit(plan.raw, _ptr(obs_ctx), _ptr(d_syn), _ptr(J), _ptr(w2),
+                              _ptr(adj_src), _ptr(workspace), _stream(stream)))
+
+
+def fwi_adjoint_grad(plan, v, adj_src, snapshots, grad, workspace, stream=None):
+    _check(_lib.fwi_adjoint_grad(plan.raw, _ptr(v), _ptr(adj_src), _ptr(snapshots), _ptr(grad),
+                                 _ptr(workspace), _stream(stream)))
+
+
+def fwi_guided_step(batch, nz, nx, params: GuideParams, v_prime, v0hat, g, h, v_out, rho_out,
+                    stream=None):
+    gp = params._c()
+    _check(_lib.fwi_guided_step(batch, nz, nx, ctypes.byref(gp), _ptr(v_prime), _ptr(v0hat),
+                                _ptr(g), _ptr(h), _ptr(v_out), _ptr(rho_out), _stream(stream)))
+
+
+def fwi_check(plan, workspace, stream=None):
+    _check(_lib.fwi_check(plan.raw, _ptr(workspace), _stream(stream)))
+
+
+# ----------------------------------------------------------------- convenience plan
+
+class Plan:
+    """A plan plus the device buffers it needs, allocated with torch on
+    ``device`` (default: the current CUDA device)."""
+
+    def __init__(self, prob: Problem, w2: W2Params | None = None, device=None,
+                 snapshots: bool = True):
+        self.prob = prob
+        self.w2p = w2 or W2Params()
+        self.handle = fwi_plan_create(prob, self.w2p)
+        self.ws_bytes, self.ctx_bytes, self.snap_bytes = fwi_plan_sizes(self.handle)
+        self.device = torch.device(device) if device is not None else \
+            torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.snapshots = torch.empty(self.snap_bytes // 4, dtype=torch.float32,
+                                     device=self.device) if snapshots else None
+
+    # shapes
+    @property
+    def model_shape(self):
+        p = self.prob
+        return (p.batch, p.nz, p.nx)
+
+    @property
+    def data_shape(self):
+        p = self.prob
+        return (p.batch, p.ns, p.nr, p.nt)
+
+    def new_ctx(self):
+        return torch.empty(self.ctx_bytes, dtype=torch.uint8, device=self.device)
+
+    def forward(self, v, d_syn=None, store=True, stream=None):
+        """d_syn = F(v); with ``store`` the snapshots for the adjoint are kept."""
+        _f32(v, self.model_shape, "v")
+        if d_syn is None:
+            d_syn = torch.empty(self.data_shape, dtype=torch.float32, device=self.device)
+        _f32(d_syn, self.data_shape, "d_syn")
+        snap = self.snapshots if store else None
+        if store and snap is None:
+            raise ValueError("plan was created without a snapshot buffer")
+        fwi_forward(self.handle, v, d_syn, snap, self.workspace, stream)
+        return d_syn, snap
+
+    def w2_prepare(self, d_obs, ctx=None, stream=None):
+        _f32(d_obs, self.data_shape, "d_obs")
+        if ctx is None:
+            ctx = self.new_ctx()
+        fwi_w2_prepare(self.handle, d_obs, ctx, stream)
+        return ctx
+
+    def w2_misfit(self, ctx, d_syn, want_w2=True, want_adj=True, stream=None):
+        _f32(d_syn, self.data_shape, "d_syn")
+        p = self.prob
+        J = torch.empty(p.batch, dtype=torch.float32, device=self.device)
+        w2 = torch.empty((p.batch, p.ns, p.nr), dtype=torch.float32,
+                         device=self.device) if want_w2 else None
+        adj = torch.empty(self.data_shape, dtype=torch.float32,
+                          device=self.device) if want_adj else None
+        fwi_w2_misfit(self.handle, ctx, d_syn, J, w2, adj, self.workspace, stream)
+        return J, w2, adj
+
+    def adjoint_grad(self, v, adj, grad=None, stream=None):
+        _f32(v, self.model_shape, "v")
+        _f32(adj, self.data_shape, "adj")
+        if grad is None:
+            grad = torch.empty(self.model_shape, dtype=torch.float32, device=self.device)
+        fwi_adjoint_grad(self.handle, v, adj, self.snapshots, grad, self.workspace, stream)
+        return grad
+
+    def gradient(self, v, ctx, stream=None):
+        """J(v), dJ/dv and per-trace W2 (forward -> misfit -> adjoint)."""
+        d_syn, _ = self.forward(v, stream=stream)
+        J, w2, adj = self.w2_misfit(ctx, d_syn, stream=stream)
+        grad = self.adjoint_grad(v, adj, stream=stream)
+        return J, grad, w2
+
+    def check(self, stream=None):
+        fwi_check(self.handle, self.workspace, stream)
+
+    def close(self):
+        self.workspace = None
+        self.snapshots = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def guided_step(v_prime, v0hat, g, h, params: GuideParams, v_out=None, stream=None):
+    """Algorithm 2 update on [B][nz][nx] tensors; returns (v_out, rho [B])."""
+    B, nz, nx = v_prime.shape
+    for t, n in ((v_prime, "v_prime"), (v0hat, "v0hat"), (g, "g"), (h, "h")):
+        _f32(t, (B, nz, nx), n)
+    if v_out is None:
+        v_out = torch.empty_like(v_prime)
+    rho = torch.empty(B, dtype=torch.float32, device=v_prime.device)
+    fwi_guided_step(B, nz, nx, params, v_prime, v0hat, g, h, v_out, rho, stream)
+    return v_out, rho

@@ -1,0 +1,273 @@
+// api.cu -- host side of the C ABI declared in include/fwi.h: argument
+// validation, plans (host memory only), buffer sizing and the entry points.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "fwi_internal.cuh"
+
+namespace fwi {
+size_t w2_trace_smem(int nt, int nxi);
+}
+
+using fwi::Plan;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+fwi_status fail(fwi_status code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+fwi_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(FWI_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
+
+const Plan *as_plan(const fwi_plan *p) { return reinterpret_cast<const Plan *>(p); }
+
+int *status_ptr(void *ws) { return reinterpret_cast<int *>(ws); }
+
+}  // namespace
+
+extern "C" {
+
+const char *fwi_last_error(void) { return g_err; }
+
+int fwi_version(void) { return FWI_VERSION; }
+
+fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi_plan **out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(FWI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!prob || !w2) return fail(FWI_ERR_INVALID_ARG, "problem or w2 params is NULL");
+    const fwi_problem &p = *prob;
+    if (p.nz < 1 || p.nx < 1) return fail(FWI_ERR_INVALID_ARG, "nz, nx must be >= 1");
+    if (p.nb < 0) return fail(FWI_ERR_INVALID_ARG, "nb must be >= 0");
+    if (p.top_bc != 0 && p.top_bc != 1) return fail(FWI_ERR_INVALID_ARG, "top_bc must be 0 or 1");
+    if (p.nt < 2) return fail(FWI_ERR_INVALID_ARG, "nt must be >= 2");
+    if (!finite_pos(p.dt) || !finite_pos(p.dx) || !finite_pos(p.dz))
+        return fail(FWI_ERR_INVALID_ARG, "dt, dx, dz must be finite and > 0");
+    if (p.ns < 1 || p.ns > FWI_MAX_SHOTS)
+        return fail(FWI_ERR_INVALID_ARG, "ns must be in [1, %d]", FWI_MAX_SHOTS);
+    if (p.nr < 1 || p.nr > FWI_MAX_RECEIVERS)
+        return fail(FWI_ERR_INVALID_ARG, "nr must be in [1, %d]", FWI_MAX_RECEIVERS);
+    if (!p.src_iz || !p.src_ix || !p.rec_iz || !p.rec_ix)
+        return fail(FWI_ERR_INVALID_ARG, "source/receiver index arrays must not be NULL");
+    if (p.batch < 1) return fail(FWI_ERR_INVALID_ARG, "batch must be >= 1");
+    if (!finite_pos(p.f_peak)) return fail(FWI_ERR_INVALID_ARG, "f_peak must be > 0");
+    if (!std::isfinite(p.t0)) return fail(FWI_ERR_INVALID_ARG, "t0 must be finite");
+    if (!finite_pos(p.v_ref)) return fail(FWI_ERR_INVALID_ARG, "v_ref must be > 0");
+    if (!(p.refl_R > 0.f && p.refl_R <= 1.f))
+        return fail(FWI_ERR_INVALID_ARG, "refl_R must be in (0, 1]");
+    if (!finite_pos(p.v_max)) return fail(FWI_ERR_INVALID_ARG, "v_max must be > 0");
+    if (w2->n_xi < 2) return fail(FWI_ERR_INVALID_ARG, "n_xi must be >= 2");
+    if (!(w2->k >= 0.f) || !std::isfinite(w2->k)) return fail(FWI_ERR_INVALID_ARG, "k must be >= 0");
+    if (!(w2->cshift_factor >= 0.f) || !std::isfinite(w2->cshift_factor))
+        return fail(FWI_ERR_INVALID_ARG, "cshift_factor must be >= 0");
+    if (!(w2->eps_density >= 0.f) || !std::isfinite(w2->eps_density))
+        return fail(FWI_ERR_INVALID_ARG, "eps_density must be >= 0");
+    // leapfrog + 4th-order Laplacian: |symbol| <= 16/3 per axis => C <= sqrt(3)/2
+    const double cfl = (double)p.v_max * p.dt *
+                       std::sqrt(1.0 / ((double)p.dx * p.dx) + 1.0 / ((double)p.dz * p.dz));
+    if (cfl > std::sqrt(3.0) / 2.0)
+        return fail(FWI_ERR_UNSTABLE_CFL,
+                    "v_max dt sqrt(1/dx^2 + 1/dz^2) = %.4f exceeds sqrt(3)/2 = 0.8660", cfl);
+
+    Plan *pl = new (std::nothrow) Plan();
+    if (!pl) return fail(FWI_ERR_INVALID_ARG, "out of host memory");
+    pl->p = p;
+    pl->w2 = *w2;
+    pl->NZ = p.nz + p.nb;
+    pl->NX = p.nx + 2 * p.nb;
+    pl->t0 = p.t0 > 0.f ? p.t0 : 1.1f / p.f_peak;
+    for (int i = 0; i < p.ns; ++i) {
+        if (p.src_iz[i] < 0 || p.src_iz[i] >= p.nz || p.src_ix[i] < 0 || p.src_ix[i] >= p.nx) {
+            delete pl;
+            return fail(FWI_ERR_INVALID_ARG, "source %d at (%d, %d) is outside the %dx%d grid", i,
+                        p.src_iz[i], p.src_ix[i], p.nz, p.nx);
+        }
+        pl->src_pz[i] = p.src_iz[i];
+        pl->src_px[i] = p.src_ix[i] + p.nb;
+    }
+    for (int i = 0; i < p.nr; ++i) {
+        if (p.rec_iz[i] < 0 || p.rec_iz[i] >= p.nz || p.rec_ix[i] < 0 || p.rec_ix[i] >= p.nx) {
+            delete pl;
+            return fail(FWI_ERR_INVALID_ARG, "receiver %d at (%d, %d) is outside the %dx%d grid", i,
+                        p.rec_iz[i], p.rec_ix[i], p.nz, p.nx);
+        }
+        pl->rec_pz[i] = p.rec_iz[i];
+        pl->rec_px[i] = p.rec_ix[i] + p.nb;
+    }
+    pl->p.src_iz = pl->p.src_ix = pl->p.rec_iz = pl->p.rec_ix = nullptr;
+    if (pl->NZ > 32767 || pl->NX > 32767) {
+        delete pl;
+        return fail(FWI_ERR_UNSUPPORTED, "padded grid %dx%d too large", pl->NZ, pl->NX);
+    }
+    if (!fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, false, &pl->shape) ||
+        !fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, true, &pl->shape_adj)) {
+        delete pl;
+        return fail(FWI_ERR_UNSUPPORTED,
+                    "padded grid %dx%d does not fit the shared-memory resident propagator",
+                    pl->NZ, pl->NX);
+    }
+    // the adjoint injects each receiver from the thread that owns its cell:
+    // receivers must sit in distinct column strips
+    for (int i = 0; i < p.nr; ++i)
+        for (int k = 0; k < i; ++k)
+            if (pl->rec_px[i] == pl->rec_px[k] &&
+                pl->rec_pz[i] / pl->shape_adj.rows == pl->rec_pz[k] / pl->shape_adj.rows) {
+                delete pl;
+                return fail(FWI_ERR_UNSUPPORTED,
+                            "receivers %d and %d share a column strip of %d rows", k, i,
+                            pl->shape_adj.rows);
+            }
+    // W2 trace kernel shared memory
+    if (fwi::w2_trace_smem(p.nt, w2->n_xi) > 227 * 1024) {
+        delete pl;
+        return fail(FWI_ERR_UNSUPPORTED, "nt + n_xi too large for the W2 trace kernel");
+    }
+    const size_t B = p.batch, ntr = (size_t)p.ns * p.nr;
+    using fwi::align_up;
+    size_t o = fwi::kStatusBytes;
+    pl->ws_w2 = o;
+    o += align_up(B * ntr * 4);
+    pl->ws_gshot = o;
+    o += align_up(B * p.ns * (size_t)p.nz * p.nx * 4);
+    pl->ws_bytes = o;
+    o = 0;
+    pl->ctx_M = o;      o += align_up(B * 4);
+    pl->ctx_S = o;      o += align_up(B * 4);
+    pl->ctx_cshift = o; o += align_up(B * ntr * 4);
+    pl->ctx_str = o;    o += align_up(B * ntr * 4);
+    pl->ctx_omega = o;  o += align_up(B * ntr * p.nt * 4);
+    pl->ctx_Q = o;      o += align_up(B * ntr * w2->n_xi * 4);
+    pl->ctx_bytes = o;
+    pl->snap_bytes = B * p.ns * (size_t)p.nt * pl->NZ * pl->NX * 4;
+    *out = reinterpret_cast<fwi_plan *>(pl);
+    return FWI_OK;
+}
+
+void fwi_plan_destroy(fwi_plan *plan) { delete reinterpret_cast<Plan *>(plan); }
+
+fwi_status fwi_plan_sizes(const fwi_plan *plan, size_t *workspace_bytes, size_t *obs_ctx_bytes,
+                          size_t *snapshot_bytes)
+{
+    if (!plan) return fail(FWI_ERR_INVALID_ARG, "plan is NULL");
+    const Plan *pl = as_plan(plan);
+    if (workspace_bytes) *workspace_bytes = pl->ws_bytes;
+    if (obs_ctx_bytes) *obs_ctx_bytes = pl->ctx_bytes;
+    if (snapshot_bytes) *snapshot_bytes = pl->snap_bytes;
+    return FWI_OK;
+}
+
+fwi_status fwi_plan_padded(const fwi_plan *plan, int *NZ, int *NX)
+{
+    if (!plan) return fail(FWI_ERR_INVALID_ARG, "plan is NULL");
+    if (NZ) *NZ = as_plan(plan)->NZ;
+    if (NX) *NX = as_plan(plan)->NX;
+    return FWI_OK;
+}
+
+fwi_status fwi_forward(const fwi_plan *plan, const float *v, float *d_syn, float *snapshots,
+                       void *workspace, void *stream)
+{
+    if (!plan || !v || !d_syn || !workspace)
+        return fail(FWI_ERR_INVALID_ARG, "plan, v, d_syn and workspace must not be NULL");
+    const Plan &pl = *as_plan(plan);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_forward status reset");
+    e = fwi::launch_forward(pl, v, d_syn, snapshots, status_ptr(workspace), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_forward launch");
+    return FWI_OK;
+}
+
+fwi_status fwi_w2_prepare(const fwi_plan *plan, const float *d_obs, void *obs_ctx, void *stream)
+{
+    if (!plan || !d_obs || !obs_ctx)
+        return fail(FWI_ERR_INVALID_ARG, "plan, d_obs and obs_ctx must not be NULL");
+    cudaError_t e = fwi::launch_w2_prepare(*as_plan(plan), d_obs, (unsigned char *)obs_ctx,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_w2_prepare launch");
+    return FWI_OK;
+}
+
+fwi_status fwi_w2_misfit(const fwi_plan *plan, const void *obs_ctx, const float *d_syn, float *J,
+                         float *w2, float *adj_src, void *workspace, void *stream)
+{
+    if (!plan || !obs_ctx || !d_syn || !J || !workspace)
+        return fail(FWI_ERR_INVALID_ARG,
+                    "plan, obs_ctx, d_syn, J and workspace must not be NULL");
+    const Plan &pl = *as_plan(plan);
+    float *scratch = (float *)((unsigned char *)workspace + pl.ws_w2);
+    cudaError_t e = fwi::launch_w2_misfit(pl, (const unsigned char *)obs_ctx, d_syn, J, w2,
+                                          adj_src, scratch, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_w2_misfit launch");
+    return FWI_OK;
+}
+
+fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const float *adj_src,
+                            const float *snapshots, float *grad, void *workspace, void *stream)
+{
+    if (!plan || !v || !adj_src || !snapshots || !grad || !workspace)
+        return fail(FWI_ERR_INVALID_ARG,
+                    "plan, v, adj_src, snapshots, grad and workspace must not be NULL");
+    const Plan &pl = *as_plan(plan);
+    float *gshot = (float *)((unsigned char *)workspace + pl.ws_gshot);
+    cudaError_t e = fwi::launch_adjoint(pl, v, adj_src, snapshots, grad, gshot,
+                                        status_ptr(workspace), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_adjoint_grad launch");
+    return FWI_OK;
+}
+
+fwi_status fwi_guided_step(int batch, int nz, int nx, const fwi_guide_params *params,
+                           const float *v_prime, const float *v0hat, const float *g,
+                           const float *h, float *v_out, float *rho_out, void *stream)
+{
+    if (batch < 1 || nz < 1 || nx < 1) return fail(FWI_ERR_INVALID_ARG, "batch, nz, nx must be >= 1");
+    if (!params || !v_prime || !v0hat || !g || !h || !v_out)
+        return fail(FWI_ERR_INVALID_ARG, "params and array pointers must not be NULL");
+    const fwi_guide_params &gp = *params;
+    if (!(gp.c > 0.f) || !(gp.eps > 0.f) || !(gp.gamma >= 0.f) || !(gp.rho0 >= 0.f) ||
+        !std::isfinite(gp.tau))
+        return fail(FWI_ERR_INVALID_ARG, "need c > 0, eps > 0, gamma >= 0, rho0 >= 0, finite tau");
+    if ((size_t)nz * nx > (size_t)1 << 30) return fail(FWI_ERR_UNSUPPORTED, "grid too large");
+    cudaError_t e = fwi::launch_guided(batch, nz, nx, gp, v_prime, v0hat, g, h, v_out, rho_out,
+                                       (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_guided_step launch");
+    return FWI_OK;
+}
+
+fwi_status fwi_check(const fwi_plan *plan, void *workspace, void *stream)
+{
+    if (!plan || !workspace) return fail(FWI_ERR_INVALID_ARG, "plan and workspace must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int code = 0;
+    cudaError_t e = cudaMemcpyAsync(&code, workspace, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_check");
+    e = cudaMemsetAsync(workspace, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_check reset");
+    if (code == FWI_ERR_UNSTABLE_CFL)
+        return fail(FWI_ERR_UNSTABLE_CFL, "a velocity outside (0, v_max] reached the device");
+    if (code == FWI_ERR_DEVICE_TIMEOUT)
+        return fail(FWI_ERR_DEVICE_TIMEOUT, "a device-side wait ran out of its budget");
+    if (code != 0) return fail((fwi_status)code, "device status %d", code);
+    return FWI_OK;
+}
+
+}  // extern "C"

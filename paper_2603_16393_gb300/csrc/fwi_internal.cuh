@@ -1,0 +1,99 @@
+// fwi_internal.cuh -- plan layout and kernel argument blocks shared by the
+// translation units of libfwi (host + device).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "fwi.h"
+
+namespace fwi {
+
+constexpr int kStatusBytes = 256;   // status word region at the start of the workspace
+// Threads per propagator CTA: the adjoint keeps two register arrays per
+// thread (imaging accumulator and snapshot prefetch), so it runs with fewer,
+// longer strips and up to 85 registers per thread.
+constexpr int kMaxThreadsFwd = 1024;
+constexpr int kMaxThreadsAdj = 768;
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// ---------------------------------------------------------------------------
+// Propagator (forward / adjoint) launch shape for the SMEM-resident kernel:
+// one CTA per (model, shot), each thread owns a column strip of `rows`
+// consecutive padded rows at one padded column.
+struct ResidentShape {
+    int threads;     // blockDim.x (multiple of 32)
+    int nstrip;      // strips per column
+    int rows;        // rows per strip
+    int maxrows;     // template bucket >= rows
+    int chunk;       // time steps per staging chunk
+    size_t smem;     // dynamic shared memory bytes
+};
+
+struct Plan {
+    fwi_problem p;           // copy; index pointers below replace the caller's
+    fwi_w2_params w2;
+    int NZ, NX;
+    float t0;
+    int src_pz[FWI_MAX_SHOTS], src_px[FWI_MAX_SHOTS];   // padded coordinates
+    int rec_pz[FWI_MAX_RECEIVERS], rec_px[FWI_MAX_RECEIVERS];
+    ResidentShape shape;       // forward propagator
+    ResidentShape shape_adj;   // adjoint propagator
+    // byte offsets inside the caller buffers
+    size_t ws_w2, ws_gshot, ws_bytes;
+    size_t ctx_M, ctx_S, ctx_cshift, ctx_str, ctx_omega, ctx_Q, ctx_bytes;
+    size_t snap_bytes;
+};
+
+// ---------------------------------------------------------------------------
+// Argument block of the propagator kernels (passed as a __grid_constant__
+// parameter; geometry tables travel inside it, so no device allocation is
+// needed for them).
+struct PropArgs {
+    int nz, nx, nb, NZ, NX, nt, ns, nr;
+    int rows, nstrip, chunk;
+    float dt;
+    float c0, cx1, cx2, cz1, cz2;        // Laplacian weights divided by h^2
+    float ex0, ez0;                      // eta0 * dt / 2 per axis
+    float inv_nb;
+    float fp, t0, src_scale;             // Ricker and 1/(dx dz)
+    float vmax;
+    const float *v;                      // [B][nz][nx]
+    float *d_syn;                        // forward: [B][ns][nr][nt]
+    float *snap;                         // forward: written (may be null); adjoint: read
+    const float *adj;                    // adjoint: [B][ns][nr][nt]
+    float *gshot;                        // adjoint: [B][ns][nz][nx]
+    int *status;
+    int16_t src_pz[FWI_MAX_SHOTS], src_px[FWI_MAX_SHOTS];
+    int16_t rec_pz[FWI_MAX_RECEIVERS], rec_px[FWI_MAX_RECEIVERS];
+};
+
+// Status codes the device writes (first error wins).
+__device__ __forceinline__ void set_status(int *status, int code)
+{
+    atomicCAS(status, 0, code);
+}
+
+// Launchers (return cudaGetLastError() of the launches they made).
+cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *snap,
+                           int *status, cudaStream_t st);
+cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj,
+                           const float *snap, float *grad, float *gshot, int *status,
+                           cudaStream_t st);
+cudaError_t launch_w2_prepare(const Plan &pl, const float *d_obs, unsigned char *ctx,
+                              cudaStream_t st);
+cudaError_t launch_w2_misfit(const Plan &pl, const unsigned char *ctx, const float *d_syn,
+                             float *J, float *w2_out, float *adj, float *w2_scratch,
+                             cudaStream_t st);
+cudaError_t launch_guided(int B, int nz, int nx, const fwi_guide_params &gp,
+                          const float *vprime, const float *v0hat, const float *g,
+                          const float *h, float *vout, float *rho, cudaStream_t st);
+
+// Host-side choice of the resident launch shape; returns false if the grid
+// does not fit the shared-memory resident kernel.
+bool choose_resident_shape(int NZ, int NX, int nr, bool adj, ResidentShape *out);
+
+}  // namespace fwi

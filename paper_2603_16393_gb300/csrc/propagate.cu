@@ -1,0 +1,381 @@
+// propagate.cu -- shared-memory-resident acoustic propagator for sm_103a.
+//
+// Forward (Eq. 1, Sec. 2.1 / 6.1):
+//   u^{j+1} = A (2 u^j - B u^{j-1} + kappa (L u^j + s^j)),  j = 0..nt-1
+//   kappa = v_pad^2 dt^2,  A = 1/(1+e), B = 1-e, e = eta dt/2,
+//   s^j = f(j dt)/(dx dz) at the source cell (Ricker, Sec. 6.1),
+//   d[r][j] = u^{j+1} at receiver r; the snapshot of step j is t^j = L u^j + s^j.
+//
+// Adjoint.  With mu the discrete adjoint of u and phi = kappa A mu, the
+// transposed recurrence becomes the same propagator run on reversed time:
+//   psi^{j+1} = A (2 psi^j - B psi^{j-1} + kappa (L^T psi^j + R^T r^{nt-1-j}))
+// with psi^j = phi^{nt+1-j}; the imaging condition is
+//   dJ/dv_pad = (2 / v_pad) sum_j psi^{j+1} t^{nt-1-j}.
+// L is symmetric with zero ghosts; with the mirrored top (top_bc = 1) the
+// transpose adds the reflected weights back onto rows 1 and 2.
+//
+// Layout: one CTA per (model, shot) holds both time levels of the padded
+// field (with a two-cell ghost ring) and kappa in shared memory for the whole
+// time loop; thread t owns a column strip of `rows` cells at one padded
+// column, keeps a 5-value z window in registers and reads its x neighbours
+// from shared memory.  One barrier per time step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fwi_internal.cuh"
+
+namespace fwi {
+
+namespace {
+
+constexpr float kPi = 3.14159265358979323846f;
+
+template <int MAXROWS, bool ADJ, int TOPBC>
+__global__ void __launch_bounds__(ADJ ? kMaxThreadsAdj : kMaxThreadsFwd, 1)
+k_propagate(const __grid_constant__ PropArgs a)
+{
+    extern __shared__ float sm[];
+    const int NX = a.NX, NZ = a.NZ;
+    const int P = NX + 4;
+    const int fsz = (NZ + 4) * P;
+    float *F0 = sm;
+    float *F1 = sm + fsz;
+    float *K = sm + 2 * fsz;
+    float *ST = K + NZ * NX;
+    const int bs = blockIdx.x;
+    const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int tid = threadIdx.x, nth = blockDim.x;
+
+    for (int i = tid; i < 2 * fsz; i += nth) sm[i] = 0.f;
+    const float *vb = a.v + (size_t)b * a.nz * a.nx;
+    int bad = 0;
+    for (int i = tid; i < NZ * NX; i += nth) {
+        const int pz = i / NX, px = i - (i / NX) * NX;
+        const int iz = min(pz, a.nz - 1);
+        const int ix = min(max(px - a.nb, 0), a.nx - 1);
+        const float vv = vb[iz * a.nx + ix];
+        if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
+        const float vdt = vv * a.dt;
+        K[i] = vdt * vdt;
+    }
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
+        return;
+    }
+
+    const int x = tid % NX, strip = tid / NX;
+    const bool active = strip < a.nstrip;
+    const int z0 = strip * a.rows;
+    const int myrows = active ? max(0, min(a.rows, NZ - z0)) : 0;
+
+    // damping: e = ex(x) + ez(z); rows above the bottom layer use constants
+    float cxd = 0.f;
+    if (x < a.nb) cxd = (float)(a.nb - x);
+    else if (x > a.nb + a.nx - 1) cxd = (float)(x - (a.nb + a.nx - 1));
+    const float ex = a.ex0 * (cxd * a.inv_nb) * (cxd * a.inv_nb);
+    const float A0 = 1.f / (1.f + ex), B0 = 1.f - ex;
+
+    // point injection owned by this thread (host guarantees at most one)
+    int inj_row = -1, inj_slot = -1;
+    if (!ADJ) {
+        const int sz = a.src_pz[s], sx = a.src_px[s];
+        if (myrows > 0 && x == sx && sz >= z0 && sz < z0 + myrows) inj_row = sz - z0;
+    } else {
+        for (int i = 0; i < a.nr; ++i) {
+            const int rz = a.rec_pz[i], rx = a.rec_px[i];
+            if (myrows > 0 && x == rx && rz >= z0 && rz < z0 + myrows) {
+                inj_row = rz - z0;
+                inj_slot = i;
+            }
+        }
+    }
+
+    const size_t plane = (size_t)NZ * NX;
+    float *snap_bs = a.snap ? a.snap + (size_t)bs * a.nt * plane : nullptr;
+    const int cell0 = z0 * NX + x;
+    const float *kp = K + cell0;
+
+    float acc[ADJ ? MAXROWS : 1];
+    float sv[ADJ ? MAXROWS : 1];
+    if (ADJ) {
+        const float *s0 = snap_bs + (size_t)(a.nt - 1) * plane + cell0;
+#pragma unroll
+        for (int r = 0; r < MAXROWS; ++r) {
+            acc[r] = 0.f;
+            sv[r] = (r < myrows) ? s0[r * NX] : 0.f;
+        }
+    }
+
+    for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
+        const int nch = min(a.chunk, a.nt - j0);
+        if (ADJ) {
+            const float *ab = a.adj + (size_t)bs * a.nr * a.nt;
+            for (int e = tid; e < nch * a.nr; e += nth) {
+                const int i = e / nch, jj = e - (e / nch) * nch;
+                ST[jj * a.nr + i] = ab[(size_t)i * a.nt + (a.nt - 1 - (j0 + jj))];
+            }
+            __syncthreads();
+        }
+        for (int jj = 0; jj < nch; ++jj) {
+            const int j = j0 + jj;
+            const float *cur = (j & 1) ? F1 : F0;
+            float *old = (j & 1) ? F0 : F1;
+
+            float inj = 0.f;
+            if (inj_row >= 0) {
+                if (!ADJ) {
+                    const float t = (float)j * a.dt - a.t0;
+                    const float q = (kPi * a.fp * t) * (kPi * a.fp * t);
+                    inj = a.src_scale * (1.f - 2.f * q) * expf(-q);
+                } else {
+                    inj = ST[jj * a.nr + inj_slot];
+                }
+            }
+
+            if (myrows > 0) {
+                const float *cp = cur + (z0 + 2) * P + x + 2;
+                float *op = old + (z0 + 2) * P + x + 2;
+                float *row0 = old + 2 * P + x + 2;
+                float *snap_w = (!ADJ && snap_bs) ? snap_bs + (size_t)j * plane + cell0 : nullptr;
+                const bool pf = ADJ && (j + 1 < a.nt);
+                const float *snap_r = pf ? snap_bs + (size_t)(a.nt - 2 - j) * plane + cell0 : nullptr;
+                float wm2 = cp[-2 * P], wm1 = cp[-P], w0 = cp[0], wp1 = cp[P];
+#pragma unroll
+                for (int r = 0; r < MAXROWS; ++r) {
+                    if (r < myrows) {
+                        const float *c = cp + r * P;
+                        const float wp2 = c[2 * P];
+                        float lap = a.c0 * w0 + a.cx1 * (c[-1] + c[1]) + a.cx2 * (c[-2] + c[2]) +
+                                    a.cz1 * (wm1 + wp1) + a.cz2 * (wm2 + wp2);
+                        const int z = z0 + r;
+                        if (ADJ && TOPBC == 1) {
+                            if (z == 1) lap += a.cz1 * wm1 + a.cz2 * w0;
+                            if (z == 2) lap += a.cz2 * wm2;
+                        }
+                        if (r == inj_row) lap += inj;
+                        float A = A0, B = B0;
+                        if (z >= a.nz) {
+                            const float cz = (float)(z - (a.nz - 1)) * a.inv_nb;
+                            const float e = ex + a.ez0 * cz * cz;
+                            A = 1.f / (1.f + e);
+                            B = 1.f - e;
+                        }
+                        const float fo = op[r * P];
+                        const float fn = A * (fmaf(kp[r * NX], lap, 2.f * w0) - B * fo);
+                        op[r * P] = fn;
+                        if (!ADJ && TOPBC == 1) {
+                            if (z == 1) row0[-P] = fn;
+                            if (z == 2) row0[-2 * P] = fn;
+                        }
+                        if (!ADJ && snap_w) snap_w[r * NX] = lap;
+                        if (ADJ) {
+                            acc[r] = fmaf(fn, sv[r], acc[r]);
+                            if (pf) sv[r] = snap_r[r * NX];
+                        }
+                        wm2 = wm1;
+                        wm1 = w0;
+                        w0 = wp1;
+                        wp1 = wp2;
+                    }
+                }
+            }
+            __syncthreads();
+            if (!ADJ && tid < a.nr)
+                ST[jj * a.nr + tid] = old[(a.rec_pz[tid] + 2) * P + a.rec_px[tid] + 2];
+        }
+        if (!ADJ) {
+            __syncthreads();
+            float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
+            for (int e = tid; e < nch * a.nr; e += nth) {
+                const int i = e / nch, jj = e - (e / nch) * nch;
+                db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+            }
+            __syncthreads();
+        }
+    }
+
+    if (ADJ) {
+        // dJ/dv_pad = 2 acc / v_pad, then fold the absorbing layer onto the
+        // physical edge cells (transpose of the edge replication), columns
+        // first, then rows, each in a fixed order.
+        __syncthreads();
+        float *G = F0;            // [NZ][NX]
+        float *T = F1;            // [NZ][nx]
+#pragma unroll
+        for (int r = 0; r < MAXROWS; ++r) {
+            if (r < myrows) {
+                const int z = z0 + r;
+                const int iz = min(z, a.nz - 1);
+                const int ix = min(max(x - a.nb, 0), a.nx - 1);
+                const float vp = vb[iz * a.nx + ix];
+                G[z * NX + x] = 2.f * acc[r] / vp;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < NZ * a.nx; i += nth) {
+            const int pz = i / a.nx, ix = i - (i / a.nx) * a.nx;
+            const int c0 = (ix == 0) ? 0 : ix + a.nb;
+            const int c1 = (ix == a.nx - 1) ? NX - 1 : ix + a.nb;
+            float sum = 0.f;
+            for (int px = c0; px <= c1; ++px) sum += G[pz * NX + px];
+            T[i] = sum;
+        }
+        __syncthreads();
+        float *gs = a.gshot + (size_t)bs * a.nz * a.nx;
+        for (int i = tid; i < a.nz * a.nx; i += nth) {
+            const int iz = i / a.nx, ix = i - (i / a.nx) * a.nx;
+            const int r1 = (iz == a.nz - 1) ? NZ - 1 : iz;
+            float sum = 0.f;
+            for (int pz = iz; pz <= r1; ++pz) sum += T[pz * a.nx + ix];
+            gs[i] = sum;
+        }
+    }
+}
+
+// grad[b][i] = sum_s gshot[b][s][i], s in increasing order.
+__global__ void k_shot_sum(int B, int ns, int n, const float *__restrict__ gshot,
+                           float *__restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (i >= n || b >= B) return;
+    const float *g = gshot + (size_t)b * ns * n + i;
+    float sum = 0.f;
+    for (int s = 0; s < ns; ++s) sum += g[(size_t)s * n];
+    grad[(size_t)b * n + i] = sum;
+}
+
+PropArgs make_args(const Plan &pl)
+{
+    const fwi_problem &p = pl.p;
+    PropArgs a{};
+    a.nz = p.nz; a.nx = p.nx; a.nb = p.nb; a.NZ = pl.NZ; a.NX = pl.NX;
+    a.nt = p.nt; a.ns = p.ns; a.nr = p.nr;
+    a.dt = p.dt;
+    const double ix2 = 1.0 / ((double)p.dx * p.dx), iz2 = 1.0 / ((double)p.dz * p.dz);
+    a.c0 = (float)(-2.5 * (ix2 + iz2));
+    a.cx1 = (float)(4.0 / 3.0 * ix2);
+    a.cx2 = (float)(-1.0 / 12.0 * ix2);
+    a.cz1 = (float)(4.0 / 3.0 * iz2);
+    a.cz2 = (float)(-1.0 / 12.0 * iz2);
+    const double lnR = std::log(1.0 / (double)p.refl_R);
+    const double eta0x = p.nb > 0 ? 3.0 * p.v_ref * lnR / (p.nb * (double)p.dx) : 0.0;
+    const double eta0z = p.nb > 0 ? 3.0 * p.v_ref * lnR / (p.nb * (double)p.dz) : 0.0;
+    a.ex0 = (float)(eta0x * p.dt / 2.0);
+    a.ez0 = (float)(eta0z * p.dt / 2.0);
+    a.inv_nb = p.nb > 0 ? (float)(1.0 / p.nb) : 0.f;
+    a.fp = p.f_peak;
+    a.t0 = pl.t0;
+    a.src_scale = (float)(1.0 / ((double)p.dx * p.dz));
+    a.vmax = p.v_max;
+    for (int i = 0; i < p.ns; ++i) {
+        a.src_pz[i] = (int16_t)pl.src_pz[i];
+        a.src_px[i] = (int16_t)pl.src_px[i];
+    }
+    for (int i = 0; i < p.nr; ++i) {
+        a.rec_pz[i] = (int16_t)pl.rec_pz[i];
+        a.rec_px[i] = (int16_t)pl.rec_px[i];
+    }
+    return a;
+}
+
+template <int MR, bool ADJ, int TBC>
+cudaError_t launch_one(const PropArgs &a, const ResidentShape &sh, int nblocks, cudaStream_t st)
+{
+    auto kern = k_propagate<MR, ADJ, TBC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sh.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nblocks, sh.threads, sh.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <bool ADJ>
+cudaError_t dispatch(PropArgs &a, const Plan &pl, cudaStream_t st)
+{
+    const int nb = pl.p.batch * pl.p.ns;
+    const int tb = pl.p.top_bc;
+    const ResidentShape &sh = ADJ ? pl.shape_adj : pl.shape;
+    a.rows = sh.rows;
+    a.nstrip = sh.nstrip;
+    a.chunk = sh.chunk;
+    switch (sh.maxrows) {
+#define FWI_CASE(MR)                                                              \
+    case MR:                                                                      \
+        return tb ? launch_one<MR, ADJ, 1>(a, sh, nb, st)                        \
+                  : launch_one<MR, ADJ, 0>(a, sh, nb, st);
+        FWI_CASE(4)
+        FWI_CASE(8)
+        FWI_CASE(12)
+        FWI_CASE(16)
+        FWI_CASE(20)
+        FWI_CASE(22)
+        FWI_CASE(24)
+#undef FWI_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool choose_resident_shape(int NZ, int NX, int nr, bool adj, ResidentShape *out)
+{
+    const int maxthreads = adj ? kMaxThreadsAdj : kMaxThreadsFwd;
+    if (NX > maxthreads || NZ < 1 || NX < 1) return false;
+    int nstrip = maxthreads / NX;
+    if (nstrip > NZ) nstrip = NZ;
+    int rows = (NZ + nstrip - 1) / nstrip;
+    nstrip = (NZ + rows - 1) / rows;
+    static const int buckets[] = {4, 8, 12, 16, 20, 22, 24};
+    int maxrows = 0;
+    for (int bkt : buckets)
+        if (rows <= bkt) { maxrows = bkt; break; }
+    if (maxrows == 0) return false;
+    const int threads = ((NX * nstrip + 31) / 32) * 32;
+    if (threads > maxthreads) return false;
+    const size_t limit = 227 * 1024;
+    const size_t fixed = (2 * (size_t)(NZ + 4) * (NX + 4) + (size_t)NZ * NX) * sizeof(float);
+    if (fixed + (size_t)nr * sizeof(float) > limit) return false;
+    int chunk = (int)((limit - fixed) / ((size_t)nr * sizeof(float)));
+    if (chunk > 32) chunk = 32;
+    if (chunk < 1) return false;
+    out->threads = threads;
+    out->nstrip = nstrip;
+    out->rows = rows;
+    out->maxrows = maxrows;
+    out->chunk = chunk;
+    out->smem = fixed + (size_t)chunk * nr * sizeof(float);
+    return true;
+}
+
+cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *snap,
+                           int *status, cudaStream_t st)
+{
+    PropArgs a = make_args(pl);
+    a.v = v;
+    a.d_syn = d_syn;
+    a.snap = snap;
+    a.status = status;
+    return dispatch<false>(a, pl, st);
+}
+
+cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj, const float *snap,
+                           float *grad, float *gshot, int *status, cudaStream_t st)
+{
+    PropArgs a = make_args(pl);
+    a.v = v;
+    a.adj = adj;
+    a.snap = const_cast<float *>(snap);
+    a.gshot = gshot;
+    a.status = status;
+    cudaError_t e = dispatch<true>(a, pl, st);
+    if (e != cudaSuccess) return e;
+    const int n = pl.p.nz * pl.p.nx;
+    dim3 grid((n + 255) / 256, pl.p.batch);
+    k_shot_sum<<<grid, 256, 0, st>>>(pl.p.batch, pl.p.ns, n, gshot, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace fwi

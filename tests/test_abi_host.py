@@ -1,0 +1,107 @@
+"""The C ABI on the host (no GPU needed): libfwi.so loads, exports every entry
+point include/fwi.h declares, and fwi_plan_create validates its arguments
+(host-only call) with the documented error codes."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fwi.h")
+LIB = os.path.join(ROOT, "paper_2603_16393_gb300", "libfwi.so")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not os.path.exists(LIB):
+        from paper_2603_16393_gb300 import _build
+        _build.build_library()
+    from paper_2603_16393_gb300 import api as A
+    return A
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"FWI_API\s+[^;(]*?\b(fwi_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for n in ("fwi_forward", "fwi_w2_misfit", "fwi_adjoint_grad", "fwi_guided_step",
+              "fwi_w2_prepare", "fwi_plan_create", "fwi_plan_sizes", "fwi_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(api):
+    lib = ctypes.CDLL(LIB)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    assert api.fwi_version() == 10000
+
+
+def _prob(api, **kw):
+    base = dict(nz=70, nx=70, nb=40, nt=1000, dz=10.0, dx=10.0, dt=1e-3,
+                src_iz=(0,) * 5, src_ix=(0, 17, 34, 52, 69), rec_iz=(0,) * 70,
+                rec_ix=tuple(range(70)), v_max=4500.0, batch=3)
+    base.update(kw)
+    return api.Problem(**base)
+
+
+def test_plan_sizes_of_the_benchmark_problem(api):
+    h = api.fwi_plan_create(_prob(api), api.W2Params())
+    ws, ctx, snap = api.fwi_plan_sizes(h)
+    B, ns, nr, nt, NZ, NX = 3, 5, 70, 1000, 110, 150
+    assert snap == B * ns * nt * NZ * NX * 4
+    assert ws >= 256 + B * ns * nr * 4 + B * ns * 70 * 70 * 4
+    assert ctx >= B * ns * nr * (nt + 1000) * 4
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(v_max=9000.0), 2),                 # CFL: 9000*1e-3*sqrt(2)/10 = 1.27 > 0.866
+    (dict(dt=2e-3, v_max=4500.0), 2),        # 0.636*2 = 1.27
+    (dict(nz=0), 1),
+    (dict(nt=1), 1),
+    (dict(dx=-1.0), 1),
+    (dict(src_iz=(0, 0), src_ix=(0, 70)), 1),  # outside the grid
+    (dict(rec_iz=(0, 70), rec_ix=(1, 2)), 1),
+    (dict(batch=0), 1),
+    (dict(top_bc=2), 1),
+    (dict(refl_R=0.0), 1),
+    (dict(nx=1200), 3),                      # does not fit the resident kernel
+    (dict(rec_iz=(0, 1), rec_ix=(5, 5)), 3),  # two receivers in one column strip
+])
+def test_plan_rejects_invalid_problems(api, kw, code):
+    with pytest.raises(api.FwiError) as e:
+        api.fwi_plan_create(_prob(api, **kw), api.W2Params())
+    assert e.value.code == code
+    assert api.fwi_last_error() != ""
+
+
+def test_plan_rejects_bad_w2_params(api):
+    for w2 in (api.W2Params(n_xi=1), api.W2Params(k=-1.0), api.W2Params(eps_density=-1e-9)):
+        with pytest.raises(api.FwiError) as e:
+            api.fwi_plan_create(_prob(api), w2)
+        assert e.value.code == 1
+
+
+def test_cfl_limit_is_sqrt3_over_2(api):
+    # exactly at the bound passes, just above fails
+    vmax_ok = 0.866 / (1e-3 * (2 ** 0.5) / 10.0)
+    api.fwi_plan_create(_prob(api, v_max=vmax_ok * 0.9999), api.W2Params())
+    with pytest.raises(api.FwiError):
+        api.fwi_plan_create(_prob(api, v_max=vmax_ok * 1.001), api.W2Params())
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    # the binding must not fall back to anything when libfwi.so is absent
+    import subprocess
+    import sys
+    code = ("import sys, os; sys.path.insert(0, %r); import paper_2603_16393_gb300.api as A"
+            % str(tmp_path))
+    pkg = tmp_path / "paper_2603_16393_gb300"
+    pkg.mkdir()
+    for f in ("__init__.py", "api.py"):
+        (pkg / f).write_text(open(os.path.join(ROOT, "paper_2603_16393_gb300", f)).read())
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert r.returncode != 0 and "libfwi.so is missing" in r.stderr

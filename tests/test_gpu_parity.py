@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs, stage by stage and end to end.
+
+Small cases span several column strips with a ragged last strip; the full
+70x70 / 5 shots / 1000 steps case is checked on sampled models of a batch
+launched exactly as the benchmark launches it.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_cases import TOL_ADJ, TOL_DATA, TOL_GRAD, TOL_J, initial, models, problems, rel_l2  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_16393_gb300 import api as A
+    return A
+
+
+DEV = "cuda:0"
+
+
+def T(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device=DEV)
+
+
+def H(t):
+    return t.double().cpu().numpy()
+
+
+# ---------------------------------------------------------------- forward
+
+@pytest.mark.parametrize("nz,nx,nb,nt,ns,top_bc", [
+    (20, 23, 7, 300, 3, 0),      # NZ=27 -> ragged strips
+    (31, 17, 9, 250, 2, 1),      # mirrored top
+    (12, 40, 4, 200, 4, 0),
+    (1, 9, 3, 120, 1, 0),        # single physical row
+])
+def test_forward_matches_oracle(api, nz, nx, nb, nt, ns, top_bc):
+    gp, op = problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc)
+    v = models("layered", [3, 4], nz, nx)
+    with api.Plan(gp) as plan:
+        d, _ = plan.forward(T(v))
+        torch.cuda.synchronize()
+        plan.check()
+    d_o = O.forward(op, v)
+    err = rel_l2(H(d), d_o)
+    assert err <= TOL_DATA, err
+
+
+def test_forward_full_size(api):
+    gp, op = problems(70, 70, 40, 1000, 5, batch=2)
+    v = models("layered", [0, 1], 70, 70)
+    with api.Plan(gp) as plan:
+        d, _ = plan.forward(T(v), store=False)
+        torch.cuda.synchronize()
+    d_o = O.forward(op, v)
+    for b in range(2):
+        err = rel_l2(H(d)[b], d_o[b])
+        assert err <= TOL_DATA, (b, err)
+
+
+def test_forward_rejects_velocity_above_vmax_on_device(api):
+    gp, _ = problems(16, 16, 4, 50, 1, batch=2, v_max=3000.0)
+    v = models("layered", [0, 1], 16, 16)       # reaches 4500 > v_max
+    with api.Plan(gp) as plan:
+        plan.forward(T(v))
+        with pytest.raises(api.FwiError) as e:
+            plan.check()
+        assert e.value.code == api.FWI_ERR_UNSTABLE_CFL
+        # the status word is cleared by the check and reset by the next forward
+        plan.forward(T(np.full((2, 16, 16), 2000.0)))
+        plan.check()
+
+
+# ---------------------------------------------------------------- misfit
+
+def _w2_case(api, nz=24, nx=30, nb=8, nt=400, ns=3, nxi=500, k=100.0):
+    gp, op = problems(nz, nx, nb, nt, ns, batch=2, f_peak=20.0)
+    vt = models("layered", [5, 6], nz, nx)
+    v0 = initial(2, nz, nx)
+    w2p = api.W2Params(k=k, n_xi=nxi)
+    ow2 = O.W2Params(k=k, n_xi=nxi)
+    return gp, op, vt, v0, w2p, ow2
+
+
+@pytest.mark.parametrize("k,nxi", [(100.0, 500), (0.0, 257), (100.0, 1000)])
+def test_w2_misfit_on_shared_data(api, k, nxi):
+    # the same data (GPU forward output, rounded to float32) through both
+    # misfit implementations isolates the W2 stage
+    gp, op, vt, v0, w2p, ow2 = _w2_case(api, k=k, nxi=nxi)
+    with api.Plan(gp, w2p) as plan:
+        d_obs, _ = plan.forward(T(vt), store=False)
+        d_obs = d_obs.clone()
+        ctx = plan.w2_prepare(d_obs)
+        d_syn, _ = plan.forward(T(v0), store=False)
+        J, w2, adj = plan.w2_misfit(ctx, d_syn)
+        torch.cuda.synchronize()
+    octx = O.w2_prepare(H(d_obs), op.dt, ow2)
+    J_o, w2_o, adj_o = O.w2_misfit(octx, H(d_syn), op.dt, ow2)
+    assert rel_l2(H(J), J_o) <= TOL_J, (H(J), J_o)
+    assert rel_l2(H(w2), w2_o) <= TOL_J
+    assert rel_l2(H(adj), adj_o) <= TOL_ADJ, rel_l2(H(adj), adj_o)
+
+
+def test_w2_zero_at_observation(api):
+    gp, op, vt, v0, w2p, ow2 = _w2_case(api)
+    with api.Plan(gp, w2p) as plan:
+        d_obs, _ = plan.forward(T(vt), store=False)
+        ctx = plan.w2_prepare(d_obs)
+        J, w2, adj = plan.w2_misfit(ctx, d_obs)
+        torch.cuda.synchronize()
+    assert float(J.abs().max()) == 0.0 and float(w2.abs().max()) == 0.0
+    assert float(adj.abs().max()) == 0.0
+
+
+# ---------------------------------------------------------------- gradient
+
+@pytest.mark.parametrize("nz,nx,nb,nt,ns,top_bc", [
+    (20, 23, 7, 300, 3, 0),
+    (18, 26, 6, 260, 2, 1),
+])
+def test_gradient_matches_oracle_small(api, nz, nx, nb, nt, ns, top_bc):
+    gp, op = problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc)
+    w2p, ow2 = api.W2Params(n_xi=400), O.W2Params(n_xi=400)
+    vt = models("layered", [7, 8], nz, nx)
+    v0 = initial(2, nz, nx)
+    with api.Plan(gp, w2p) as plan:
+        d_obs, _ = plan.forward(T(vt), store=False)
+        ctx = plan.w2_prepare(d_obs.clone())
+        J, g, _ = plan.gradient(T(v0), ctx)
+        torch.cuda.synchronize()
+        plan.check()
+    octx = O.w2_prepare(O.forward(op, vt), op.dt, ow2)
+    J_o, g_o, _ = O.gradient(op, v0, octx, ow2)
+    assert rel_l2(H(J), J_o) <= TOL_J * 10, (H(J), J_o)
+    for b in range(2):
+        assert rel_l2(H(g)[b], g_o[b]) <= TOL_GRAD, (b, rel_l2(H(g)[b], g_o[b]))
+
+
+def test_adjoint_stage_on_shared_adjoint_source(api):
+    # feed the GPU adjoint source to the oracle's wave adjoint: isolates a7/a8
+    nz, nx, nb, nt, ns = 22, 25, 6, 280, 3
+    gp, op = problems(nz, nx, nb, nt, ns, batch=1, f_peak=25.0)
+    v = models("curved_faulted", [11], nz, nx)
+    rng = np.random.default_rng(0)
+    adj = rng.standard_normal((1, ns, gp.nr, nt))
+    with api.Plan(gp) as plan:
+        plan.forward(T(v))
+        g = plan.adjoint_grad(T(v), T(adj))
+        torch.cuda.synchronize()
+    g_o = np.zeros((nz, nx))
+    adj32 = adj.astype(np.float32).astype(np.float64)
+    for s in range(ns):
+        _, u_all = O.forward_shot(op, v[0], s, keep_wavefield=True)
+        g_o += O.fold(op, O.adjoint_shot(op, v[0], s, adj32[0, s], u_all))
+    assert rel_l2(H(g)[0], g_o) <= TOL_GRAD
+
+
+def test_gradient_full_size_sampled_from_benchmark_batch(api):
+    # the launch configuration of the benchmark (70x70, 5 shots, 1000 steps,
+    # a batch of models in one call); three sampled models against the oracle
+    B = 24
+    gp, op = problems(70, 70, 40, 1000, 5, batch=B)
+    vt = models("layered", list(range(B)), 70, 70)
+    v0 = initial(B, 70, 70)
+    with api.Plan(gp) as plan:
+        d_obs, _ = plan.forward(T(vt), store=False)
+        ctx = plan.w2_prepare(d_obs.clone())
+        J, g, _ = plan.gradient(T(v0), ctx)
+        torch.cuda.synchronize()
+        plan.check()
+    ow2 = O.W2Params()
+    for b in (0, B // 2, B - 1):
+        octx = O.w2_prepare(O.forward(op, vt[b:b + 1]), op.dt, ow2)
+        J_o, g_o, _ = O.gradient(op, v0[b:b + 1], octx, ow2)
+        assert abs(float(J[b]) - J_o[0]) <= TOL_J * 10 * abs(J_o[0]), (b, float(J[b]), J_o[0])
+        err = rel_l2(H(g)[b], g_o[0])
+        assert err <= TOL_GRAD, (b, err)
+
+
+def test_gradient_is_deterministic(api):
+    gp, _ = problems(70, 70, 40, 400, 5, batch=3)
+    vt = models("layered", [1, 2, 3], 70, 70)
+    v0 = initial(3, 70, 70)
+    with api.Plan(gp) as plan:
+        d_obs, _ = plan.forward(T(vt), store=False)
+        ctx = plan.w2_prepare(d_obs.clone())
+        J1, g1, w1 = [t.clone() for t in plan.gradient(T(v0), ctx)]
+        J2, g2, w2 = plan.gradient(T(v0), ctx)
+        torch.cuda.synchronize()
+    assert torch.equal(J1, J2) and torch.equal(g1, g2) and torch.equal(w1, w2)
+
+
+# ---------------------------------------------------------------- guided step
+
+@pytest.mark.parametrize("B,nz,nx,gamma,kmin,kmax", [
+    (3, 70, 70, 0.55, 0.0, 0.0),
+    (2, 33, 47, 0.35, 1.0, 5.0),
+    (1, 1, 5, 0.0, 0.0, 0.0),
+])
+def test_guided_step_matches_oracle(api, B, nz, nx, gamma, kmin, kmax):
+    rng = np.random.default_rng(B * 100 + nz)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)  # noqa: E731
+    vp = f32(rng.standard_normal((B, nz, nx)))
+    v0 = f32(rng.uniform(-1, 1, (B, nz, nx)) * 0.05 + np.linspace(-1, 1, nz)[None, :, None])
+    g = f32(rng.standard_normal((B, nz, nx)) * 1e-6)
+    h = f32(rng.standard_normal((B, nz, nx)) * 1e-3)
+    prm = dict(rho0=1.3, c=0.1, tau=0.0, gamma=gamma, eps=1e-4 * 1e-6, kappa_min=kmin,
+               kappa_max=kmax)
+    vout, rho = api.guided_step(T(vp), T(v0), T(g), T(h), api.GuideParams(**prm))
+    vo, rho_o = O.guided_step(vp, v0, g, h, O.GuideParams(**prm))
+    assert rel_l2(H(rho), rho_o) <= 1e-5
+    assert rel_l2(vp - H(vout), vp - vo) <= 1e-5

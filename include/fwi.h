@@ -72,31 +72,33 @@ typedef enum fwi_status {
 
 /* Discretisation and acquisition (Sec. 2.1, 6.1; see the readings listed with
  * each field).  Host struct; fwi_plan_create copies everything it needs,
- * including the index arrays. */
+ * including the index arrays.  Physical scalars are double: the kernels form
+ * their per-cell coefficients from them in double and round once, so that a
+ * float32 time step (0.001 is not a float) does not bias every velocity. */
 typedef struct fwi_problem {
     int nz, nx;          /* physical grid (rows = depth), >= 1                      */
-    float dz, dx;        /* grid spacing in m, > 0                                  */
+    double dz, dx;       /* grid spacing in m, > 0                                  */
     int nb;              /* absorbing-layer width in cells on left, right, bottom   */
     int top_bc;          /* 0: zero ghosts above row 0; 1: mirror (du/dn = 0, Eq. 1) */
     int nt;              /* time steps, >= 2                                        */
-    float dt;            /* time step in s, > 0                                     */
+    double dt;           /* time step in s, > 0                                     */
     int ns, nr;          /* shots (<= FWI_MAX_SHOTS), receivers (<= FWI_MAX_RECEIVERS) */
     const int *src_iz, *src_ix;   /* HOST arrays [ns]: source cell per shot          */
     const int *rec_iz, *rec_ix;   /* HOST arrays [nr]: receivers shared by all shots */
-    float f_peak;        /* Ricker peak frequency in Hz (Sec. 6.1: 15)              */
-    float t0;            /* Ricker delay in s; <= 0 selects 1.1 / f_peak (Sec. 6.1) */
-    float v_ref;         /* speed the damping is designed for, m/s (not differentiated) */
-    float refl_R;        /* nominal two-way amplitude reflection of the layer, (0,1] */
-    float v_max;         /* declared upper bound of every velocity passed in, m/s  */
+    double f_peak;       /* Ricker peak frequency in Hz (Sec. 6.1: 15)              */
+    double t0;           /* Ricker delay in s; <= 0 selects 1.1 / f_peak (Sec. 6.1) */
+    double v_ref;        /* speed the damping is designed for, m/s (not differentiated) */
+    double refl_R;       /* nominal two-way amplitude reflection of the layer, (0,1] */
+    double v_max;        /* declared upper bound of every velocity passed in, m/s  */
     int batch;           /* B models per call, >= 1                                 */
 } fwi_problem;
 
 /* Misfit hyperparameters (Sec. 5.1, 6.2, 6.3): k = 100, c' factor 1.1,
  * eps' = 1e-9, N_xi = 1000. */
 typedef struct fwi_w2_params {
-    float k;             /* Eq. omega_def, >= 0                                     */
-    float cshift_factor; /* c' = cshift_factor |min_t omega d_obs|, >= 0            */
-    float eps_density;   /* eps' in the density denominator, >= 0                   */
+    double k;            /* Eq. omega_def, >= 0                                     */
+    double cshift_factor; /* c' = cshift_factor |min_t omega d_obs|, >= 0           */
+    double eps_density;  /* eps' in the density denominator, >= 0                   */
     int n_xi;            /* quantile nodes xi_j = j/(n_xi-1), >= 2                  */
 } fwi_w2_params;
 
@@ -104,7 +106,7 @@ typedef struct fwi_w2_params {
  * eps = 1e-4, gamma and rho0 per dataset in Table 1).  kappa is clipped to
  * [kappa_min, kappa_max] only when kappa_min < kappa_max. */
 typedef struct fwi_guide_params {
-    float rho0, c, tau, gamma, eps, kappa_min, kappa_max;
+    double rho0, c, tau, gamma, eps, kappa_min, kappa_max;
 } fwi_guide_params;
 
 typedef struct fwi_plan fwi_plan;   /* opaque, host memory only */

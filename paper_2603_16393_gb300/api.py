@@ -41,22 +41,22 @@ _vp = ctypes.c_void_p
 
 
 class _Problem(ctypes.Structure):
-    _fields_ = [("nz", ctypes.c_int), ("nx", ctypes.c_int), ("dz", ctypes.c_float),
-                ("dx", ctypes.c_float), ("nb", ctypes.c_int), ("top_bc", ctypes.c_int),
-                ("nt", ctypes.c_int), ("dt", ctypes.c_float), ("ns", ctypes.c_int),
+    _fields_ = [("nz", ctypes.c_int), ("nx", ctypes.c_int), ("dz", ctypes.c_double),
+                ("dx", ctypes.c_double), ("nb", ctypes.c_int), ("top_bc", ctypes.c_int),
+                ("nt", ctypes.c_int), ("dt", ctypes.c_double), ("ns", ctypes.c_int),
                 ("nr", ctypes.c_int), ("src_iz", _ip), ("src_ix", _ip), ("rec_iz", _ip),
-                ("rec_ix", _ip), ("f_peak", ctypes.c_float), ("t0", ctypes.c_float),
-                ("v_ref", ctypes.c_float), ("refl_R", ctypes.c_float), ("v_max", ctypes.c_float),
-                ("batch", ctypes.c_int)]
+                ("rec_ix", _ip), ("f_peak", ctypes.c_double), ("t0", ctypes.c_double),
+                ("v_ref", ctypes.c_double), ("refl_R", ctypes.c_double),
+                ("v_max", ctypes.c_double), ("batch", ctypes.c_int)]
 
 
 class _W2(ctypes.Structure):
-    _fields_ = [("k", ctypes.c_float), ("cshift_factor", ctypes.c_float),
-                ("eps_density", ctypes.c_float), ("n_xi", ctypes.c_int)]
+    _fields_ = [("k", ctypes.c_double), ("cshift_factor", ctypes.c_double),
+                ("eps_density", ctypes.c_double), ("n_xi", ctypes.c_int)]
 
 
 class _Guide(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_float) for n in
+    _fields_ = [(n, ctypes.c_double) for n in
                 ("rho0", "c", "tau", "gamma", "eps", "kappa_min", "kappa_max")]
 
 

@@ -34,7 +34,7 @@ fwi_status cuda_fail(cudaError_t e, const char *where)
     return fail(FWI_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 const Plan *as_plan(const fwi_plan *p) { return reinterpret_cast<const Plan *>(p); }
 
@@ -71,14 +71,14 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (!finite_pos(p.f_peak)) return fail(FWI_ERR_INVALID_ARG, "f_peak must be > 0");
     if (!std::isfinite(p.t0)) return fail(FWI_ERR_INVALID_ARG, "t0 must be finite");
     if (!finite_pos(p.v_ref)) return fail(FWI_ERR_INVALID_ARG, "v_ref must be > 0");
-    if (!(p.refl_R > 0.f && p.refl_R <= 1.f))
+    if (!(p.refl_R > 0.0 && p.refl_R <= 1.0))
         return fail(FWI_ERR_INVALID_ARG, "refl_R must be in (0, 1]");
     if (!finite_pos(p.v_max)) return fail(FWI_ERR_INVALID_ARG, "v_max must be > 0");
     if (w2->n_xi < 2) return fail(FWI_ERR_INVALID_ARG, "n_xi must be >= 2");
-    if (!(w2->k >= 0.f) || !std::isfinite(w2->k)) return fail(FWI_ERR_INVALID_ARG, "k must be >= 0");
-    if (!(w2->cshift_factor >= 0.f) || !std::isfinite(w2->cshift_factor))
+    if (!(w2->k >= 0.0) || !std::isfinite(w2->k)) return fail(FWI_ERR_INVALID_ARG, "k must be >= 0");
+    if (!(w2->cshift_factor >= 0.0) || !std::isfinite(w2->cshift_factor))
         return fail(FWI_ERR_INVALID_ARG, "cshift_factor must be >= 0");
-    if (!(w2->eps_density >= 0.f) || !std::isfinite(w2->eps_density))
+    if (!(w2->eps_density >= 0.0) || !std::isfinite(w2->eps_density))
         return fail(FWI_ERR_INVALID_ARG, "eps_density must be >= 0");
     // leapfrog + 4th-order Laplacian: |symbol| <= 16/3 per axis => C <= sqrt(3)/2
     const double cfl = (double)p.v_max * p.dt *
@@ -93,7 +93,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     pl->w2 = *w2;
     pl->NZ = p.nz + p.nb;
     pl->NX = p.nx + 2 * p.nb;
-    pl->t0 = p.t0 > 0.f ? p.t0 : 1.1f / p.f_peak;
+    pl->t0 = p.t0 > 0.0 ? p.t0 : 1.1 / p.f_peak;
     for (int i = 0; i < p.ns; ++i) {
         if (p.src_iz[i] < 0 || p.src_iz[i] >= p.nz || p.src_ix[i] < 0 || p.src_ix[i] >= p.nx) {
             delete pl;
@@ -117,12 +117,55 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         delete pl;
         return fail(FWI_ERR_UNSUPPORTED, "padded grid %dx%d too large", pl->NZ, pl->NX);
     }
-    if (!fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, false, &pl->shape) ||
-        !fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, true, &pl->shape_adj)) {
-        delete pl;
-        return fail(FWI_ERR_UNSUPPORTED,
-                    "padded grid %dx%d does not fit the shared-memory resident propagator",
-                    pl->NZ, pl->NX);
+    pl->fast = fwi::fast_bucket(pl->NZ, pl->NX, &pl->fast_P, &pl->fast_NZM);
+    if (pl->fast) {
+        const int nstrip = (pl->NZ + fwi::kFastRows - 1) / fwi::kFastRows;
+        const size_t limit = 227 * 1024;
+        for (int adj = 0; adj < 2; ++adj) {
+            fwi::ResidentShape &sh = adj ? pl->shape_adj : pl->shape;
+            sh.rows = fwi::kFastRows;
+            sh.maxrows = fwi::kFastRows;
+            sh.nstrip = nstrip;
+            sh.threads = ((pl->NX * nstrip + 31) / 32) * 32;
+            const size_t fixed = fwi::fast_smem(pl->fast_P, pl->fast_NZM, adj != 0, 0, p.nr);
+            int chunk = fixed + (size_t)p.nr * 4 > limit
+                            ? 0 : (int)((limit - fixed) / ((size_t)p.nr * 4));
+            if (chunk > 32) chunk = 32;
+            sh.chunk = chunk;
+            sh.smem = fwi::fast_smem(pl->fast_P, pl->fast_NZM, adj != 0, chunk, p.nr);
+            if (chunk < 1) pl->fast = false;
+        }
+        pl->nzs = nstrip * fwi::kFastRows;
+    }
+    if (!pl->fast) {
+        if (!fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, false, &pl->shape) ||
+            !fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, true, &pl->shape_adj)) {
+            delete pl;
+            return fail(FWI_ERR_UNSUPPORTED,
+                        "padded grid %dx%d does not fit the shared-memory resident propagator",
+                        pl->NZ, pl->NX);
+        }
+        pl->nzs = pl->NZ;
+    }
+    // the adjoint source of a receiver enters through the level psi^{j-1}
+    // scaled by 1/B, B = 1 - eta dt/2 of the receiver cell
+    {
+        const double lnR = std::log(1.0 / (double)p.refl_R);
+        for (int i = 0; i < p.nr; ++i) {
+            const int px = pl->rec_px[i], pz = pl->rec_pz[i];
+            double cx = 0.0, cz = pz > p.nz - 1 ? pz - (p.nz - 1) : 0;
+            if (px < p.nb) cx = p.nb - px;
+            if (px > p.nb + p.nx - 1) cx = px - (p.nb + p.nx - 1);
+            const double e = p.nb > 0 ? 3.0 * p.v_ref * lnR / p.nb *
+                                            ((cx / p.nb) * (cx / p.nb) / p.dx +
+                                             (cz / p.nb) * (cz / p.nb) / p.dz) * p.dt / 2.0
+                                      : 0.0;
+            if (std::fabs(1.0 - e) < 1e-3) {
+                delete pl;
+                return fail(FWI_ERR_UNSUPPORTED,
+                            "receiver %d sits where the damping makes 1 - eta dt/2 vanish", i);
+            }
+        }
     }
     // the adjoint injects each receiver from the thread that owns its cell:
     // receivers must sit in distinct column strips
@@ -154,9 +197,11 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     pl->ctx_cshift = o; o += align_up(B * ntr * 4);
     pl->ctx_str = o;    o += align_up(B * ntr * 4);
     pl->ctx_omega = o;  o += align_up(B * ntr * p.nt * 4);
-    pl->ctx_Q = o;      o += align_up(B * ntr * w2->n_xi * 4);
+    pl->ctx_Qb = o;     o += align_up(B * ntr * w2->n_xi * 4);   // int bracket base
+    pl->ctx_Qf = o;     o += align_up(B * ntr * w2->n_xi * 4);   // fraction in bracket
     pl->ctx_bytes = o;
-    pl->snap_bytes = B * p.ns * (size_t)p.nt * pl->NZ * pl->NX * 4;
+    // record planes: nzs rows of pitch fast_P (fast kernels) or NX (generic)
+    pl->snap_bytes = B * p.ns * (size_t)p.nt * pl->nzs * (pl->fast ? pl->fast_P : pl->NX) * 4;
     *out = reinterpret_cast<fwi_plan *>(pl);
     return FWI_OK;
 }
@@ -242,7 +287,7 @@ fwi_status fwi_guided_step(int batch, int nz, int nx, const fwi_guide_params *pa
     if (!params || !v_prime || !v0hat || !g || !h || !v_out)
         return fail(FWI_ERR_INVALID_ARG, "params and array pointers must not be NULL");
     const fwi_guide_params &gp = *params;
-    if (!(gp.c > 0.f) || !(gp.eps > 0.f) || !(gp.gamma >= 0.f) || !(gp.rho0 >= 0.f) ||
+    if (!(gp.c > 0.0) || !(gp.eps > 0.0) || !(gp.gamma >= 0.0) || !(gp.rho0 >= 0.0) ||
         !std::isfinite(gp.tau))
         return fail(FWI_ERR_INVALID_ARG, "need c > 0, eps > 0, gamma >= 0, rho0 >= 0, finite tau");
     if ((size_t)nz * nx > (size_t)1 << 30) return fail(FWI_ERR_UNSUPPORTED, "grid too large");

@@ -16,6 +16,8 @@ constexpr int kStatusBytes = 256;   // status word region at the start of the wo
 // longer strips and up to 85 registers per thread.
 constexpr int kMaxThreadsFwd = 1024;
 constexpr int kMaxThreadsAdj = 768;
+// Rows per thread strip of the fast (compile-time pitch) propagators.
+constexpr int kFastRows = 22;
 constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -37,14 +39,17 @@ struct Plan {
     fwi_problem p;           // copy; index pointers below replace the caller's
     fwi_w2_params w2;
     int NZ, NX;
-    float t0;
+    double t0;
     int src_pz[FWI_MAX_SHOTS], src_px[FWI_MAX_SHOTS];   // padded coordinates
     int rec_pz[FWI_MAX_RECEIVERS], rec_px[FWI_MAX_RECEIVERS];
     ResidentShape shape;       // forward propagator
     ResidentShape shape_adj;   // adjoint propagator
+    bool fast;                 // compile-time pitch kernels (else the generic ones)
+    int fast_P, fast_NZM;      // their shared-memory pitch and row capacity
+    int nzs;                   // rows of one wavefield-record plane (>= NZ)
     // byte offsets inside the caller buffers
     size_t ws_w2, ws_gshot, ws_bytes;
-    size_t ctx_M, ctx_S, ctx_cshift, ctx_str, ctx_omega, ctx_Q, ctx_bytes;
+    size_t ctx_M, ctx_S, ctx_cshift, ctx_str, ctx_omega, ctx_Qb, ctx_Qf, ctx_bytes;
     size_t snap_bytes;
 };
 
@@ -54,8 +59,13 @@ struct Plan {
 // needed for them).
 struct PropArgs {
     int nz, nx, nb, NZ, NX, nt, ns, nr;
+    int nzs;                             // rows of one wavefield-record plane
     int rows, nstrip, chunk;
     float dt;
+    double dtd, t0d;                     // dt and the Ricker delay in double: the
+                                         // per-cell coefficients and the source
+                                         // times are formed in double, rounded once
+    double ex0d, ez0d;                   // eta0 * dt / 2 per axis, double
     float c0, cx1, cx2, cz1, cz2;        // Laplacian weights divided by h^2
     float ex0, ez0;                      // eta0 * dt / 2 per axis
     float inv_nb;
@@ -95,5 +105,11 @@ cudaError_t launch_guided(int B, int nz, int nx, const fwi_guide_params &gp,
 // Host-side choice of the resident launch shape; returns false if the grid
 // does not fit the shared-memory resident kernel.
 bool choose_resident_shape(int NZ, int NX, int nr, bool adj, ResidentShape *out);
+
+// Fast propagators: bucket (pitch, row capacity) for a padded grid, their
+// shared memory, and their launch.
+bool fast_bucket(int NZ, int NX, int *P, int *NZM);
+size_t fast_smem(int P, int NZM, bool adj, int chunk, int nr);
+cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st);
 
 }  // namespace fwi

@@ -40,7 +40,11 @@ __device__ float block_reduce_g(float v, float *red)
     return red[32];
 }
 
-__global__ void __launch_bounds__(NT_G) k_guided(int nz, int nx, fwi_guide_params gp,
+struct GuideF {
+    float rho0, c, tau, gamma, eps, kappa_min, kappa_max;
+};
+
+__global__ void __launch_bounds__(NT_G) k_guided(int nz, int nx, GuideF gp,
                                                  const float *vprime,
                                                  const float *__restrict__ v0hat,
                                                  const float *__restrict__ g,
@@ -77,7 +81,9 @@ cudaError_t launch_guided(int B, int nz, int nx, const fwi_guide_params &gp, con
                           const float *v0hat, const float *g, const float *h, float *vout,
                           float *rho, cudaStream_t st)
 {
-    k_guided<<<B, NT_G, 0, st>>>(nz, nx, gp, vprime, v0hat, g, h, vout, rho);
+    const GuideF gf = {(float)gp.rho0, (float)gp.c, (float)gp.tau, (float)gp.gamma,
+                       (float)gp.eps, (float)gp.kappa_min, (float)gp.kappa_max};
+    k_guided<<<B, NT_G, 0, st>>>(nz, nx, gf, vprime, v0hat, g, h, vout, rho);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,16 @@ namespace {
 
 constexpr float kPi = 3.14159265358979323846f;
 
+// Returns x through an opaque move: values derived from it inside the time
+// loop are recomputed every step instead of being hoisted out of the loop
+// (per-row damping coefficients would pin two registers per row).
+__device__ __forceinline__ float opaque_g(float x)
+{
+    float y;
+    asm volatile("mov.b32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 template <int MAXROWS, bool ADJ, int TOPBC>
 __global__ void __launch_bounds__(ADJ ? kMaxThreadsAdj : kMaxThreadsFwd, 1)
 k_propagate(const __grid_constant__ PropArgs a)
@@ -56,8 +66,8 @@ k_propagate(const __grid_constant__ PropArgs a)
         const int ix = min(max(px - a.nb, 0), a.nx - 1);
         const float vv = vb[iz * a.nx + ix];
         if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
-        const float vdt = vv * a.dt;
-        K[i] = vdt * vdt;
+        const double vdt = (double)vv * a.dtd;
+        K[i] = (float)(vdt * vdt);
     }
     if (__syncthreads_or(bad)) {
         if (tid == 0) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
@@ -74,7 +84,8 @@ k_propagate(const __grid_constant__ PropArgs a)
     if (x < a.nb) cxd = (float)(a.nb - x);
     else if (x > a.nb + a.nx - 1) cxd = (float)(x - (a.nb + a.nx - 1));
     const float ex = a.ex0 * (cxd * a.inv_nb) * (cxd * a.inv_nb);
-    const float A0 = 1.f / (1.f + ex), B0 = 1.f - ex;
+    const double exd = a.ex0d * ((double)cxd / a.nb) * ((double)cxd / a.nb);
+    const float A0 = (float)(1.0 / (1.0 + exd)), B0 = (float)(1.0 - exd);
 
     // point injection owned by this thread (host guarantees at most one)
     int inj_row = -1, inj_slot = -1;
@@ -125,7 +136,7 @@ k_propagate(const __grid_constant__ PropArgs a)
             float inj = 0.f;
             if (inj_row >= 0) {
                 if (!ADJ) {
-                    const float t = (float)j * a.dt - a.t0;
+                    const float t = (float)((double)j * a.dtd - a.t0d);
                     const float q = (kPi * a.fp * t) * (kPi * a.fp * t);
                     inj = a.src_scale * (1.f - 2.f * q) * expf(-q);
                 } else {
@@ -133,6 +144,7 @@ k_propagate(const __grid_constant__ PropArgs a)
                 }
             }
 
+            const float exs = opaque_g(ex);
             if (myrows > 0) {
                 const float *cp = cur + (z0 + 2) * P + x + 2;
                 float *op = old + (z0 + 2) * P + x + 2;
@@ -157,7 +169,7 @@ k_propagate(const __grid_constant__ PropArgs a)
                         float A = A0, B = B0;
                         if (z >= a.nz) {
                             const float cz = (float)(z - (a.nz - 1)) * a.inv_nb;
-                            const float e = ex + a.ez0 * cz * cz;
+                            const float e = exs + a.ez0 * cz * cz;
                             A = 1.f / (1.f + e);
                             B = 1.f - e;
                         }
@@ -252,7 +264,8 @@ PropArgs make_args(const Plan &pl)
     PropArgs a{};
     a.nz = p.nz; a.nx = p.nx; a.nb = p.nb; a.NZ = pl.NZ; a.NX = pl.NX;
     a.nt = p.nt; a.ns = p.ns; a.nr = p.nr;
-    a.dt = p.dt;
+    a.nzs = pl.nzs;
+    a.dt = (float)p.dt;
     const double ix2 = 1.0 / ((double)p.dx * p.dx), iz2 = 1.0 / ((double)p.dz * p.dz);
     a.c0 = (float)(-2.5 * (ix2 + iz2));
     a.cx1 = (float)(4.0 / 3.0 * ix2);
@@ -264,11 +277,15 @@ PropArgs make_args(const Plan &pl)
     const double eta0z = p.nb > 0 ? 3.0 * p.v_ref * lnR / (p.nb * (double)p.dz) : 0.0;
     a.ex0 = (float)(eta0x * p.dt / 2.0);
     a.ez0 = (float)(eta0z * p.dt / 2.0);
+    a.ex0d = eta0x * (double)p.dt / 2.0;
+    a.ez0d = eta0z * (double)p.dt / 2.0;
+    a.dtd = (double)p.dt;
+    a.t0d = (double)pl.t0;
     a.inv_nb = p.nb > 0 ? (float)(1.0 / p.nb) : 0.f;
-    a.fp = p.f_peak;
-    a.t0 = pl.t0;
+    a.fp = (float)p.f_peak;
+    a.t0 = (float)pl.t0;
     a.src_scale = (float)(1.0 / ((double)p.dx * p.dz));
-    a.vmax = p.v_max;
+    a.vmax = (float)p.v_max;
     for (int i = 0; i < p.ns; ++i) {
         a.src_pz[i] = (int16_t)pl.src_pz[i];
         a.src_px[i] = (int16_t)pl.src_px[i];
@@ -358,6 +375,12 @@ cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *
     a.d_syn = d_syn;
     a.snap = snap;
     a.status = status;
+    if (pl.fast) {
+        a.rows = pl.shape.rows;
+        a.nstrip = pl.shape.nstrip;
+        a.chunk = pl.shape.chunk;
+        return launch_fast(pl, false, a, st);
+    }
     return dispatch<false>(a, pl, st);
 }
 
@@ -370,7 +393,15 @@ cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj, con
     a.snap = const_cast<float *>(snap);
     a.gshot = gshot;
     a.status = status;
-    cudaError_t e = dispatch<true>(a, pl, st);
+    cudaError_t e;
+    if (pl.fast) {
+        a.rows = pl.shape_adj.rows;
+        a.nstrip = pl.shape_adj.nstrip;
+        a.chunk = pl.shape_adj.chunk;
+        e = launch_fast(pl, true, a, st);
+    } else {
+        e = dispatch<true>(a, pl, st);
+    }
     if (e != cudaSuccess) return e;
     const int n = pl.p.nz * pl.p.nx;
     dim3 grid((n + 255) / 256, pl.p.batch);

@@ -1,0 +1,458 @@
+// propagate_fast.cu -- shared-memory-resident propagators with a compile-time
+// shared-memory pitch (every stencil offset is an immediate) and fixed
+// 22-row column strips, for padded grids that fit one CTA.
+//
+// Forward (Eq. 1, Sec. 2.1 / 6.1), written in increment form: with
+// v^{j+1/2} = u^{j+1} - u^j the damped leapfrog
+//   u^{j+1} = A (2 u^j - B u^{j-1} + kappa (L u^j + s^j))
+// is exactly
+//   v^{j+1/2} = A B v^{j-1/2} + kappa A (L u^j + s^j),   u^{j+1} = u^j + v^{j+1/2}.
+// Carrying the small increment instead of u^{j-1} keeps float32 round-off
+// from growing with the nearly double root of the recurrence at low
+// frequency; the Laplacian is evaluated on neighbour differences
+// ((u_{k-1} - u_k) + (u_{k+1} - u_k)) for the same reason.  The record of step
+// j is L u^j (the point source is added back by the adjoint).
+//
+// Adjoint: psi^{j+1} = A (2 psi^j - B psi^{j-1} + kappa (L^T psi^j + R^T r^{nt-1-j}))
+// (the discrete adjoint in the self-adjoint phi = kappa A mu form, reversed
+// time), dJ/dv_pad = (2/v_pad) sum_j psi^{j+1} t^{nt-1-j}.  A receiver's
+// adjoint source is folded into the owner-only old level,
+// psi^{j-1} -= (kappa/B) q, which the update turns into + A kappa q.
+//
+// Shared memory: two time levels of the field with a two-cell ghost ring,
+// pitch P (and, for the adjoint, kappa A per cell), plus a staging buffer for
+// receiver samples.  Thread (x, strip) owns rows [22 strip, 22 strip + 22) at
+// padded column x.  Rows past the padded grid are dead rows: kappa = 0 keeps
+// them at zero, and they act as the zero ghosts below the grid.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fwi_internal.cuh"
+
+namespace fwi {
+
+namespace {
+
+constexpr int ROWS = kFastRows;
+constexpr float kPi = 3.14159265358979323846f;
+
+__device__ __forceinline__ float ricker_scaled(int j, const PropArgs &a)
+{
+    const float t = (float)((double)j * a.dtd - a.t0d);
+    const float q = (kPi * a.fp * t) * (kPi * a.fp * t);
+    return a.src_scale * (1.f - 2.f * q) * expf(-q);
+}
+
+// damping e = eta dt / 2 of column x (side layers)
+__device__ __forceinline__ float ex_of(int x, const PropArgs &a)
+{
+    float cxd = 0.f;
+    if (x < a.nb) cxd = (float)(a.nb - x);
+    else if (x > a.nb + a.nx - 1) cxd = (float)(x - (a.nb + a.nx - 1));
+    return a.ex0 * (cxd * a.inv_nb) * (cxd * a.inv_nb);
+}
+
+// damping e of row z (bottom layer), as a function of zb + r with
+// zb = z0 - (nz - 1): exact small integers in float
+__device__ __forceinline__ float ez_of(float zbr, const PropArgs &a)
+{
+    const float cz = fmaxf(zbr, 0.f) * a.inv_nb;
+    return a.ez0 * cz * cz;
+}
+
+// Per-cell coefficients formed in double and rounded once (set-up only):
+// kappa A = (v dt)^2 / (1 + e), A B = (1 - e) / (1 + e), kappa / B.  Forming
+// (v dt)^2 from a float dt would bias every cell's velocity by the same
+// ~5e-8 and shift all arrivals coherently over a thousand steps.
+__device__ __forceinline__ double e_cell(int px, int pz, const PropArgs &a)
+{
+    double cx = 0.0, cz = 0.0;
+    if (px < a.nb) cx = a.nb - px;
+    else if (px > a.nb + a.nx - 1) cx = px - (a.nb + a.nx - 1);
+    if (pz > a.nz - 1) cz = pz - (a.nz - 1);
+    if (a.nb == 0) return 0.0;
+    return a.ex0d * (cx / a.nb) * (cx / a.nb) + a.ez0d * (cz / a.nb) * (cz / a.nb);
+}
+__device__ __forceinline__ float kappaA_cell(float v, int px, int pz, const PropArgs &a)
+{
+    const double vdt = (double)v * a.dtd;
+    return (float)(vdt * vdt / (1.0 + e_cell(px, pz, a)));
+}
+
+// ------------------------------------------------------------------ forward
+template <int P, int TOPBC, bool STORE>
+__device__ __forceinline__ void fwd_rows(const float *cp, float *np, const float *abp, float *sw,
+                                         int NX, bool top_strip, float (&ka)[ROWS],
+                                         float (&vi)[ROWS], const PropArgs &a)
+{
+    float wm2 = cp[-2 * P], wm1 = cp[-P], w0 = cp[0], wp1 = cp[P];
+    float Dp = w0 - wm1;      // u_z - u_{z-1}
+    float Em2 = w0 - wm2;     // u_z - u_{z-2}      (E of row z-2)
+    float Em1 = wp1 - wm1;    // u_{z+1} - u_{z-1}  (E of row z-1)
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const float *c = cp + r * P;
+        const float wp2 = c[2 * P];
+        const float Dn = wp1 - w0;
+        const float E0 = wp2 - w0;
+        const float dzA = Dn - Dp;                        // (u_{z-1}-u_z) + (u_{z+1}-u_z)
+        const float dzB = E0 - Em2;                       // (u_{z-2}-u_z) + (u_{z+2}-u_z)
+        const float dxA = (c[-1] - w0) + (c[1] - w0);
+        const float dxB = (c[-2] - w0) + (c[2] - w0);
+        float lap = a.cx1 * dxA;
+        lap = fmaf(a.cx2, dxB, lap);
+        lap = fmaf(a.cz1, dzA, lap);
+        lap = fmaf(a.cz2, dzB, lap);
+        vi[r] = fmaf(ka[r], lap, abp[r * P] * vi[r]);
+        const float un = w0 + vi[r];
+        np[r * P] = un;
+        if (TOPBC == 1 && (r == 1 || r == 2)) {
+            if (top_strip) np[-r * P] = un;               // mirrored ghost rows -1, -2
+        }
+        if (STORE) sw[r * P] = lap;
+        Dp = Dn;
+        Em2 = Em1;
+        Em1 = E0;
+        wm2 = wm1;
+        wm1 = w0;
+        w0 = wp1;
+        wp1 = wp2;
+    }
+}
+
+template <int P, int NZM, int TOPBC, bool STORE>
+__global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_constant__ PropArgs a)
+{
+    extern __shared__ float sm[];
+    constexpr int FSZ = (NZM + 4) * P;
+    float *U0 = sm, *U1 = sm + FSZ, *ABt = sm + 2 * FSZ, *ST = ABt + NZM * P;
+    const int NX = a.NX, NZ = a.NZ;
+    const int bs = blockIdx.x, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < 2 * FSZ; i += nth) sm[i] = 0.f;
+    // A B = (1 - e)/(1 + e) per cell (e = eta dt / 2)
+    for (int i = tid; i < NZM * P; i += nth) {
+        const int pz = i / P, px = i - (i / P) * P;
+        const double e = e_cell(px, pz, a);
+        ABt[i] = (float)((1.0 - e) / (1.0 + e));
+    }
+
+    const int x = tid % NX, strip = tid / NX;
+    const bool active = strip < a.nstrip;
+    const int z0 = strip * ROWS;
+    const float *vb = a.v + (size_t)b * a.nz * a.nx;
+    const int ixc = min(max(x - a.nb, 0), a.nx - 1);
+    const float ex = ex_of(x, a);
+    const float zbf = (float)(z0 - (a.nz - 1));
+    float ka[ROWS], vi[ROWS];
+    int bad = 0;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const int z = z0 + r;
+        float k = 0.f;
+        if (active && z < NZ) {
+            const float vv = vb[min(z, a.nz - 1) * a.nx + ixc];
+            if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
+            k = kappaA_cell(vv, x, z, a);
+        }
+        ka[r] = k;
+        vi[r] = 0.f;
+    }
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
+        return;
+    }
+    const bool top_strip = active && z0 == 0;
+
+    // source owner
+    const int sz = a.src_pz[s], sx = a.src_px[s];
+    const int src_row = (active && x == sx && sz >= z0 && sz < z0 + ROWS) ? sz - z0 : -1;
+    float ka_src = 0.f;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r)
+        if (r == src_row) ka_src = ka[r];
+
+    const size_t plane = (size_t)a.nzs * P;   // record planes use the pitch P
+    float *snap_bs = STORE ? a.snap + (size_t)bs * a.nt * plane : nullptr;
+
+    for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
+        const int nch = min(a.chunk, a.nt - j0);
+        for (int jj = 0; jj < nch; ++jj) {
+            const int j = j0 + jj;
+            const float *cur = (j & 1) ? U1 : U0;
+            float *nxt = (j & 1) ? U0 : U1;
+            if (active) {
+                const float *cp = cur + (z0 + 2) * P + x + 2;
+                float *np = nxt + (z0 + 2) * P + x + 2;
+                float *sw = STORE ? snap_bs + (size_t)j * plane + z0 * P + x : nullptr;
+                fwd_rows<P, TOPBC, STORE>(cp, np, ABt + z0 * P + x, sw, NX, top_strip, ka, vi, a);
+                if (src_row >= 0) {
+                    // point source: + kappa A s at the source cell (increment and field)
+                    const float d = ka_src * ricker_scaled(j, a);
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r)
+                        if (r == src_row) vi[r] += d;
+                    np[src_row * P] += d;
+                    if (TOPBC == 1 && top_strip && (src_row == 1 || src_row == 2))
+                        np[-src_row * P] += d;
+                }
+            }
+            __syncthreads();
+            if (tid < a.nr) ST[jj * a.nr + tid] = nxt[(a.rec_pz[tid] + 2) * P + a.rec_px[tid] + 2];
+        }
+        __syncthreads();
+        float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
+        for (int e = tid; e < nch * a.nr; e += nth) {
+            const int i = e / nch, jj = e - (e / nch) * nch;
+            db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ adjoint
+// Returns x through an opaque move: values derived from it inside the time
+// loop are recomputed every step instead of being hoisted out of the loop
+// (22 rows x 2 damping coefficients would pin 44 registers).
+__device__ __forceinline__ float opaque(float x)
+{
+    float y;
+    asm volatile("mov.b32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int P, int TOPBC>
+__device__ __forceinline__ void adj_rows(const float *cp, float *np, const float *kp,
+                                         const float *sr, float zbf, float ex, bool top_strip,
+                                         bool active, float (&acc)[ROWS], float (&sv)[ROWS],
+                                         const PropArgs &a)
+{
+    float wm2 = cp[-2 * P], wm1 = cp[-P], w0 = cp[0], wp1 = cp[P];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        const float *c = cp + r * P;
+        const float wp2 = c[2 * P];
+        float lap = a.c0 * w0;
+        lap = fmaf(a.cx1, c[-1] + c[1], lap);
+        lap = fmaf(a.cx2, c[-2] + c[2], lap);
+        lap = fmaf(a.cz1, wm1 + wp1, lap);
+        lap = fmaf(a.cz2, wm2 + wp2, lap);
+        if (TOPBC == 1 && (r == 1 || r == 2)) {
+            // transpose of the mirrored top: reflected weights back onto rows 1, 2
+            if (top_strip) lap += (r == 1) ? a.cz1 * wm1 + a.cz2 * w0 : a.cz2 * wm2;
+        }
+        const float e = ex + ez_of(zbf + (float)r, a);
+        const float A2 = __fdividef(2.f, 1.f + e);        // 2A
+        const float AB = A2 - 1.f;                        // A B = (1-e)/(1+e)
+        const float fo = np[r * P];
+        const float fn = fmaf(kp[r * P], lap, fmaf(A2, w0, -AB * fo));
+        if (active) np[r * P] = fn;
+        acc[r] = fmaf(fn, sv[r], acc[r]);
+        sv[r] = sr[r * P];
+        wm2 = wm1;
+        wm1 = w0;
+        w0 = wp1;
+        wp1 = wp2;
+    }
+}
+
+template <int P, int NZM, int TOPBC>
+__global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_constant__ PropArgs a)
+{
+    extern __shared__ float sm[];
+    constexpr int FSZ = (NZM + 4) * P;
+    float *U0 = sm, *U1 = sm + FSZ, *K = sm + 2 * FSZ, *IC = K + NZM * P, *ST = IC + a.nr;
+    const int NX = a.NX, NZ = a.NZ;
+    const int bs = blockIdx.x, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < 2 * FSZ; i += nth) sm[i] = 0.f;
+    const float *vb = a.v + (size_t)b * a.nz * a.nx;
+    // kappa / B at each receiver cell (its adjoint source enters through the
+    // old level, see below)
+    for (int i = tid; i < a.nr; i += nth) {
+        const int rz = a.rec_pz[i], rx = a.rec_px[i];
+        const float vv = vb[min(rz, a.nz - 1) * a.nx + min(max(rx - a.nb, 0), a.nx - 1)];
+        const double vdt = (double)vv * a.dtd;
+        IC[i] = (float)(vdt * vdt / (1.0 - e_cell(rx, rz, a)));
+    }
+    int bad = 0;
+    for (int i = tid; i < NZM * P; i += nth) {
+        const int pz = i / P, px = i - (i / P) * P;
+        float k = 0.f;
+        if (pz < NZ && px < NX) {
+            const float vv = vb[min(pz, a.nz - 1) * a.nx + min(max(px - a.nb, 0), a.nx - 1)];
+            if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
+            k = kappaA_cell(vv, px, pz, a);
+        }
+        K[i] = k;   // kappa A per cell (0 outside the grid: dead rows stay zero)
+    }
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
+        return;
+    }
+
+    // inactive threads (past the last strip) run the same instructions on the
+    // addresses of strip 0, column 0, with every write gated
+    const int strip = tid / NX;
+    const bool active = strip < a.nstrip;
+    const int x = active ? tid % NX : 0;
+    const int z0 = active ? strip * ROWS : 0;
+    const float ex = ex_of(x, a);
+    const float zbf = (float)(z0 - (a.nz - 1));
+    const bool top_strip = active && z0 == 0;
+
+    // receiver owned by this thread: its adjoint source enters through the
+    // old level, psi^{j-1} -= (kappa / B) q (recomputed where used, to keep
+    // the loop-carried state small)
+    int inj_slot = -1;
+    for (int i = 0; i < a.nr; ++i) {
+        const int rz = a.rec_pz[i], rx = a.rec_px[i];
+        if (active && x == rx && rz >= z0 && rz < z0 + ROWS) inj_slot = i;
+    }
+    // source cell: its imaging term sum_j psi^{j+1} s^{nt-1-j} is kept apart
+    // (in shared memory, thread 0) because the forward record holds L u only
+    __shared__ float acc_src;
+    if (tid == 0) acc_src = 0.f;
+
+    const size_t plane = (size_t)a.nzs * P;   // record planes use the pitch P
+    float acc[ROWS], sv[ROWS];
+    // record plane read next: starts at plane nt-1, moves back one plane per step
+    const float *sr = a.snap + ((size_t)bs * a.nt + (a.nt - 1)) * plane + z0 * P + x;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+        acc[r] = 0.f;
+        sv[r] = sr[r * P];
+    }
+
+    for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
+        const int nch = min(a.chunk, a.nt - j0);
+        const float *ab = a.adj + (size_t)bs * a.nr * a.nt;
+        for (int e = tid; e < nch * a.nr; e += nth) {
+            const int i = e / nch, jj = e - (e / nch) * nch;
+            ST[jj * a.nr + i] = ab[(size_t)i * a.nt + (a.nt - 1 - (j0 + jj))];
+        }
+        __syncthreads();
+        for (int jj = 0; jj < nch; ++jj) {
+            const int j = j0 + jj;
+            const float *cur = (j & 1) ? U1 : U0;
+            float *nxt = (j & 1) ? U0 : U1;
+            if (inj_slot >= 0) {
+                const int rz = a.rec_pz[inj_slot], rx = a.rec_px[inj_slot];
+                nxt[(rz + 2) * P + rx + 2] -= IC[inj_slot] * ST[jj * a.nr + inj_slot];
+            }
+            if (j + 1 < a.nt) sr -= plane;
+            const float *cp = cur + (z0 + 2) * P + x + 2;
+            float *np = nxt + (z0 + 2) * P + x + 2;
+            const float *kp = K + z0 * P + x;
+            adj_rows<P, TOPBC>(cp, np, kp, sr, opaque(zbf), opaque(ex), top_strip, active, acc, sv,
+                               a);
+            __syncthreads();
+            if (tid == 0) {
+                const int sz = a.src_pz[s], sx = a.src_px[s];
+                acc_src = fmaf(nxt[(sz + 2) * P + sx + 2], ricker_scaled(a.nt - 1 - j, a), acc_src);
+            }
+        }
+    }
+
+    // dJ/dv_pad = 2 acc / v_pad, fold of the absorbing layer onto the edge
+    // cells (transpose of the edge replication), then per-shot gradient
+    __syncthreads();
+    float *G = U0;   // [NZ][NX]
+    float *T = U1;   // [NZ][nx]
+    if (active) {
+        const int ixc = min(max(x - a.nb, 0), a.nx - 1);
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int z = z0 + r;
+            if (z < NZ) G[z * NX + x] = 2.f * acc[r] / vb[min(z, a.nz - 1) * a.nx + ixc];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int sz = a.src_pz[s], sx = a.src_px[s];
+        const float vsrc = vb[min(sz, a.nz - 1) * a.nx + min(max(sx - a.nb, 0), a.nx - 1)];
+        G[sz * NX + sx] += 2.f * acc_src / vsrc;
+    }
+    __syncthreads();
+    for (int i = tid; i < NZ * a.nx; i += nth) {
+        const int pz = i / a.nx, ix = i - (i / a.nx) * a.nx;
+        const int c0 = (ix == 0) ? 0 : ix + a.nb;
+        const int c1 = (ix == a.nx - 1) ? NX - 1 : ix + a.nb;
+        float sum = 0.f;
+        for (int px = c0; px <= c1; ++px) sum += G[pz * NX + px];
+        T[i] = sum;
+    }
+    __syncthreads();
+    float *gs = a.gshot + (size_t)bs * a.nz * a.nx;
+    for (int i = tid; i < a.nz * a.nx; i += nth) {
+        const int iz = i / a.nx, ix = i - (i / a.nx) * a.nx;
+        const int r1 = (iz == a.nz - 1) ? NZ - 1 : iz;
+        float sum = 0.f;
+        for (int pz = iz; pz <= r1; ++pz) sum += T[pz * a.nx + ix];
+        gs[i] = sum;
+    }
+}
+
+template <typename K>
+cudaError_t launch_k(K kern, const PropArgs &a, const ResidentShape &sh, int nblocks,
+                     cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sh.smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nblocks, sh.threads, sh.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Buckets of the fast kernels: (pitch P, maximum padded rows NZM).
+bool fast_bucket(int NZ, int NX, int *P, int *NZM)
+{
+    static const int buckets[][2] = {{64, 264}, {160, 110}};
+    for (const auto &bk : buckets) {
+        const int p = bk[0], nzm = bk[1];
+        if (NX + 4 > p || NZ > nzm) continue;
+        const int nstrip = (NZ + kFastRows - 1) / kFastRows;
+        if (NX * nstrip > kMaxThreadsAdj) continue;
+        *P = p;
+        *NZM = nzm;
+        return true;
+    }
+    return false;
+}
+
+size_t fast_smem(int P, int NZM, bool adj, int chunk, int nr)
+{
+    // two field levels + one per-cell table (A B for the forward, kappa A for
+    // the adjoint) + the adjoint's per-receiver coefficients + the receiver
+    // staging chunk
+    return ((size_t)2 * (NZM + 4) * P + (size_t)NZM * P + (adj ? (size_t)nr : 0) +
+            (size_t)chunk * nr) * sizeof(float);
+}
+
+cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st)
+{
+    const int nb = pl.p.batch * pl.p.ns;
+    const ResidentShape &sh = adj ? pl.shape_adj : pl.shape;
+    const bool store = a.snap != nullptr;
+    const int tb = pl.p.top_bc;
+#define FWI_FAST(PP, NN)                                                                       \
+    if (pl.fast_P == PP && pl.fast_NZM == NN) {                                                \
+        if (adj)                                                                               \
+            return tb ? launch_k(k_adj_fast<PP, NN, 1>, a, sh, nb, st)                         \
+                      : launch_k(k_adj_fast<PP, NN, 0>, a, sh, nb, st);                        \
+        if (store)                                                                             \
+            return tb ? launch_k(k_fwd_fast<PP, NN, 1, true>, a, sh, nb, st)                   \
+                      : launch_k(k_fwd_fast<PP, NN, 0, true>, a, sh, nb, st);                  \
+        return tb ? launch_k(k_fwd_fast<PP, NN, 1, false>, a, sh, nb, st)                      \
+                  : launch_k(k_fwd_fast<PP, NN, 0, false>, a, sh, nb, st);                     \
+    }
+    FWI_FAST(64, 264)
+    FWI_FAST(160, 110)
+#undef FWI_FAST
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace fwi

@@ -1,19 +1,28 @@
 // w2.cu -- weighted, normalised Wasserstein-2 misfit (Sec. 5.1, 6.2) and its
 // exact derivative, one CTA per trace.
 //
-// Per trace (Sec. 6.2 numerics):
-//   y = omega d + c',  Z = dt (sum y - (y_0 + y_{nt-1})/2),  p = y / (Z + eps')
-//   F_0 = 0, F_k = F_{k-1} + dt (p_{k-1} + p_k)/2          (block prefix scan)
-//   k*_j = min{k : F_k >= xi_j} = lower_bound of the running max of F
-//   Q_j = t_{k*-1} + dt (xi_j - F_{k*-1}) / (F_{k*} - F_{k*-1}), clamped at the ends
-//   W2 = (dxi sum_j w_j (Q_j - Qobs_j)^2)^(1/2),  J = sum W2 / S_obs
-// Reverse pass without scatter: with a_j, b_j the contributions of node j to
-// dJ/dF_{k*-1} and dJ/dF_{k*}, and k*_j non-decreasing in j,
-//   H_k = sum_{k' >= k} dJ/dF_{k'} = SA[J(k+1)] + SB[J(k)],
-// where SA, SB are suffix sums over j and J(k) = min{j : k*_j >= k}; then
-//   dJ/dp_m = dt/2 (H_m [m >= 1] + H_{m+1}),
-//   dJ/dy_m = dJ/dp_m / (Z+eps') - (sum_n dJ/dp_n y_n) dt w'_m / (Z+eps')^2,
-//   dJ/dd_m = omega_m dJ/dy_m.
+// Per trace (Sec. 6.2 numerics), written in the un-normalised running sum
+//   G_0 = 0,  G_k = sum_{i=1..k} (y_{i-1} + y_i),   y = omega d + c'
+// The trapezoid CDF is F_k = G_k / Gtot with Gtot = G_{nt-1} + 2 eps'/dt
+// (because Z = dt G_{nt-1} / 2), so
+//   k*_j  = min{k : F_k >= xi_j} = min{k : G_k >= t_j},  t_j = xi_j Gtot
+//   Q_j   = t_{k*-1} + dt (t_j - G_{k*-1}) / (G_{k*} - G_{k*-1})   (clamped at the ends)
+//   W2    = (dxi sum_j w_j (Q_j - Qobs_j)^2)^(1/2),  J = sum W2 / S_obs
+// Quantiles are kept as (bracket base index, fraction in [0,1]); the
+// difference of two quantiles is then an exact integer number of samples
+// plus a difference of fractions, without cancellation.
+//
+// Reverse pass (no scatter).  With a_j, b_j the contributions of node j to
+// dJ/dG_{k*-1} and dJ/dG_{k*}, c_j = dJ/dQ_j dt xi_j / D_j its contribution
+// to dJ/dG_{nt-1} through t_j, and k*_j non-decreasing in j:
+//   H_k = sum_{k' >= k} dJ/dG_{k'} = SA[J(k+1)] + SB[J(k)] + C [k <= nt-1],
+// with SA, SB suffix sums over j, J(k) = min{j : k*_j >= k}, C = sum_j c_j;
+//   dJ/dy_m = H_m [m >= 1] + H_{m+1},   dJ/dd_m = omega_m dJ/dy_m.
+//
+// Precision: everything is float32; the running sums, the thresholds, the
+// suffix sums and C are double-float (hi + lo float pairs, ~48-bit
+// mantissa), because quantiles of two close distributions are compared and
+// dJ/dy has the mean of dJ/dG removed (J is invariant to a rescaling of y).
 // Every reduction has a fixed order, so results are bitwise reproducible.
 #include <cuda_runtime.h>
 
@@ -27,100 +36,182 @@ constexpr int NT_W2 = 256;          // threads per trace CTA
 constexpr int NW_W2 = NT_W2 / 32;
 constexpr unsigned FULL = 0xffffffffu;
 
-// ---------------------------------------------------------------- block helpers
-__device__ __forceinline__ float warp_sum(float v)
+// ---------------------------------------------------------------- double-float
+// A value hi + lo with |lo| <= ulp(hi)/2 (Knuth two-sum / Dekker two-product,
+// error-free transformations in float32).
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-    return v;
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
 }
-__device__ __forceinline__ float warp_max(float v)
+__device__ __forceinline__ df fast_two_sum(float a, float b)   // |a| >= |b|
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
-    return v;
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
-__device__ __forceinline__ float warp_min(float v)
+__device__ __forceinline__ df df_add(df a, df b)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
-    return v;
+    df s = two_sum(a.hi, b.hi);
+    const df t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_from(float a) { return {a, 0.f}; }
+__device__ __forceinline__ float df_f(df a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ df df_mul_f(df a, float b)
+{
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_div_f(df a, float b)
+{
+    const float q1 = __fdiv_rn(a.hi, b);
+    const df p = {__fmul_rn(q1, b), __fmaf_rn(q1, b, -__fmul_rn(q1, b))};
+    const df r = df_sub(a, p);
+    const float q2 = __fdiv_rn(r.hi, b);
+    return fast_two_sum(q1, q2);
+}
+__device__ __forceinline__ bool df_lt(df a, df b)
+{
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ df df_max(df a, df b) { return df_lt(a, b) ? b : a; }
+__device__ __forceinline__ df df_shfl_up(df v, int o)
+{
+    return {__shfl_up_sync(FULL, v.hi, o), __shfl_up_sync(FULL, v.lo, o)};
+}
+__device__ __forceinline__ df df_shfl_xor(df v, int o)
+{
+    return {__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
 }
 
-// op: 0 sum, 1 max, 2 min.  Result broadcast to every thread.
+// ---------------------------------------------------------------- block helpers
+// OP: 0 sum, 1 max, 2 min.
+template <int OP>
+__device__ __forceinline__ float fcomb(float a, float b)
+{
+    return OP == 0 ? a + b : OP == 1 ? fmaxf(a, b) : fminf(a, b);
+}
+template <int OP>
+__device__ __forceinline__ float fident()
+{
+    return OP == 0 ? 0.f : OP == 1 ? -INFINITY : INFINITY;
+}
+template <int OP>
+__device__ __forceinline__ df dcomb(df a, df b)
+{
+    return OP == 0 ? df_add(a, b) : df_max(a, b);
+}
+template <int OP>
+__device__ __forceinline__ df dident()
+{
+    return OP == 0 ? df{0.f, 0.f} : df{-INFINITY, 0.f};
+}
+
+// float reduction over the block; red holds NTH/32 + 1 floats
 template <int OP, int NTH>
 __device__ float block_reduce(float v, float *red)
 {
     constexpr int NW = NTH / 32;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    v = OP == 0 ? warp_sum(v) : OP == 1 ? warp_max(v) : warp_min(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fcomb<OP>(v, __shfl_xor_sync(FULL, v, o));
     __syncthreads();
     if (lane == 0) red[w] = v;
     __syncthreads();
     if (w == 0) {
-        float u = lane < NW ? red[lane] : (OP == 0 ? 0.f : OP == 1 ? -INFINITY : INFINITY);
-        u = OP == 0 ? warp_sum(u) : OP == 1 ? warp_max(u) : warp_min(u);
+        float u = lane < NW ? red[lane] : fident<OP>();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u = fcomb<OP>(u, __shfl_xor_sync(FULL, u, o));
         if (lane == 0) red[NW] = u;
     }
     __syncthreads();
     return red[NW];
 }
 
-// In-place inclusive scan (OP 0: sum, 1: max) of arr[0..n) in shared memory,
-// blocked arrangement (thread t owns a contiguous run).  If REV, the scan runs
-// from the end (suffix scan).
+// double-float sum over the block; red holds NW_W2 + 1 df
+__device__ df block_sum_df(df v, df *red)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        df u = lane < NW_W2 ? red[lane] : df{0.f, 0.f};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u = df_add(u, df_shfl_xor(u, o));
+        if (lane == 0) red[NW_W2] = u;
+    }
+    __syncthreads();
+    return red[NW_W2];
+}
+
+// In-place inclusive double-float scan (OP 0: sum, 1: max) of arr[0..n) in
+// shared memory, blocked arrangement; REV scans from the end (suffix scan).
 template <int OP, bool REV>
-__device__ void block_scan(float *arr, int n, float *red)
+__device__ void block_scan_df(df *arr, int n, df *red)
 {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int per = (n + NT_W2 - 1) / NT_W2;
     const int lo = tid * per, hi = min(lo + per, n);
-    const float ident = OP == 0 ? 0.f : -INFINITY;
-    float run = ident;
+    df run = dident<OP>();
     for (int i = lo; i < hi; ++i) {
         const int k = REV ? n - 1 - i : i;
-        run = OP == 0 ? run + arr[k] : fmaxf(run, arr[k]);
+        run = dcomb<OP>(run, arr[k]);
         arr[k] = run;
     }
-    float incl = run;
+    df incl = run;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const float y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl = OP == 0 ? incl + y : fmaxf(incl, y);
+        const df y = df_shfl_up(incl, o);
+        if (lane >= o) incl = dcomb<OP>(y, incl);
     }
     __syncthreads();
     if (lane == 31) red[w] = incl;
     __syncthreads();
     if (w == 0) {
-        float u = lane < NW_W2 ? red[lane] : ident;
+        df u = lane < NW_W2 ? red[lane] : dident<OP>();
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const float y = __shfl_up_sync(FULL, u, o);
-            if (lane >= o) u = OP == 0 ? u + y : fmaxf(u, y);
+            const df y = df_shfl_up(u, o);
+            if (lane >= o) u = dcomb<OP>(y, u);
         }
         if (lane < NW_W2) red[lane] = u;
     }
     __syncthreads();
-    // exclusive prefix of this thread = warp-exclusive part + previous warps
-    const float prev_in_warp = __shfl_up_sync(FULL, incl, 1);
-    float off = (lane > 0) ? prev_in_warp : ident;
-    if (w > 0) off = (lane > 0) ? (OP == 0 ? off + red[w - 1] : fmaxf(off, red[w - 1])) : red[w - 1];
+    const df prev = df_shfl_up(incl, 1);
+    df off = lane > 0 ? prev : dident<OP>();
+    if (w > 0) off = lane > 0 ? dcomb<OP>(red[w - 1], off) : red[w - 1];
     if (tid > 0) {
         for (int i = lo; i < hi; ++i) {
             const int k = REV ? n - 1 - i : i;
-            arr[k] = OP == 0 ? arr[k] + off : fmaxf(arr[k], off);
+            arr[k] = dcomb<OP>(off, arr[k]);
         }
     }
     __syncthreads();
 }
 
-// first k in [0, n) with a[k] >= x for non-decreasing a; n if none
-__device__ __forceinline__ int lower_bound_f(const float *a, int n, float x)
+// first k in [0, n) with a[k] >= x (a non-decreasing); n if none
+__device__ __forceinline__ int lower_bound_df(const df *a, int n, df x)
 {
     int lo = 0, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1;
+        if (df_lt(a[mid], x)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -137,7 +228,13 @@ __device__ __forceinline__ int lower_bound_i(const int *a, int n, int x)
 }
 
 struct CtxPtrs {
-    float *M, *S, *cshift, *s_tr, *omega, *Q;
+    float *M;        // [B]
+    float *S;        // [B]
+    float *cshift;   // [B][ntr]
+    float *s_tr;     // [B][ntr]
+    float *omega;    // [B][ntr][nt]
+    int *Qb;         // [B][ntr][nxi] bracket base index of the observed quantile
+    float *Qf;       // [B][ntr][nxi] fraction inside the bracket
 };
 
 inline CtxPtrs ctx_ptrs(const Plan &pl, unsigned char *ctx)
@@ -148,46 +245,51 @@ inline CtxPtrs ctx_ptrs(const Plan &pl, unsigned char *ctx)
     c.cshift = (float *)(ctx + pl.ctx_cshift);
     c.s_tr = (float *)(ctx + pl.ctx_str);
     c.omega = (float *)(ctx + pl.ctx_omega);
-    c.Q = (float *)(ctx + pl.ctx_Q);
+    c.Qb = (int *)(ctx + pl.ctx_Qb);
+    c.Qf = (float *)(ctx + pl.ctx_Qf);
     return c;
 }
 
 struct W2Args {
     int nt, nxi, ntr;           // ntr = ns * nr traces per instance
-    float dt, k, cfac, eps;
+    float dt, k, cfac, eps2dt;  // eps2dt = 2 eps' / dt
     CtxPtrs c;
 };
 
-// y (in smem) holds omega*d + c'; builds p -> F (in place into F), the running
-// max Fm, and returns Z.
-__device__ float density_cdf(const float *y, float *F, float *Fm, int nt, float dt, float eps,
-                             float *red)
+// y = omega d + c' with both roundings explicit, so that the observation
+// preparation and the misfit map identical data to identical densities.
+__device__ __forceinline__ float shifted(float w, float d, float cs)
 {
-    float part = 0.f;
-    for (int i = threadIdx.x; i < nt; i += NT_W2) part += y[i];
-    const float sum = block_reduce<0, NT_W2>(part, red);
-    const float Z = dt * (sum - 0.5f * (y[0] + y[nt - 1]));
-    const float inv = 1.f / (Z + eps);
-    // increments of the trapezoid CDF
-    for (int i = threadIdx.x; i < nt; i += NT_W2)
-        F[i] = (i == 0) ? 0.f : 0.5f * dt * (y[i - 1] + y[i]) * inv;
-    __syncthreads();
-    block_scan<0, false>(F, nt, red);
-    for (int i = threadIdx.x; i < nt; i += NT_W2) Fm[i] = F[i];
-    __syncthreads();
-    block_scan<1, false>(Fm, nt, red);
-    return Z;
+    return __fadd_rn(__fmul_rn(w, d), cs);
 }
 
-// quantile of node j; writes k*
-__device__ __forceinline__ float quantile(const float *F, const float *Fm, int nt, float dt,
-                                          float xi, int *kst)
+// Running sums G and their running max Gm from y (all in shared memory);
+// returns the quantile step unit = Gtot / (nxi - 1).
+__device__ df build_cdf(const float *y, df *G, df *Gm, int nt, int nxi, float eps2dt, df *red)
 {
-    const int k = lower_bound_f(Fm, nt, xi);
+    for (int i = threadIdx.x; i < nt; i += NT_W2)
+        G[i] = i == 0 ? df{0.f, 0.f} : two_sum(y[i - 1], y[i]);
+    __syncthreads();
+    block_scan_df<0, false>(G, nt, red);
+    for (int i = threadIdx.x; i < nt; i += NT_W2) Gm[i] = G[i];
+    __syncthreads();
+    block_scan_df<1, false>(Gm, nt, red);
+    const df gtot = df_add(G[nt - 1], df_from(eps2dt));
+    return df_div_f(gtot, (float)(nxi - 1));
+}
+
+// Quantile of node j as (base, frac): Q = (base + frac) dt.  Writes k*.
+__device__ __forceinline__ void quantile(const df *G, const df *Gm, int nt, df unit, int j,
+                                         int *kst, int *base, float *frac, df *tj)
+{
+    const df t = df_mul_f(unit, (float)j);
+    const int k = lower_bound_df(Gm, nt, t);
     *kst = k;
-    if (k == 0) return 0.f;
-    if (k == nt) return (float)(nt - 1) * dt;
-    return (float)(k - 1) * dt + dt * (xi - F[k - 1]) / (F[k] - F[k - 1]);
+    *tj = t;
+    if (k == 0) { *base = 0; *frac = 0.f; return; }
+    if (k == nt) { *base = nt - 1; *frac = 0.f; return; }
+    *base = k - 1;
+    *frac = __fdiv_rn(df_f(df_sub(t, G[k - 1])), df_f(df_sub(G[k], G[k - 1])));
 }
 
 // ------------------------------------------------------------------ kernels
@@ -205,11 +307,13 @@ __global__ void __launch_bounds__(1024) k_obs_max(const float *__restrict__ d, s
 
 __global__ void __launch_bounds__(NT_W2) k_obs_trace(const float *__restrict__ d_obs, W2Args a)
 {
-    extern __shared__ float smw[];
-    __shared__ float red[NW_W2 + 2];
+    extern __shared__ df smd[];
+    __shared__ df red[NW_W2 + 2];
+    __shared__ float redf[NW_W2 + 2];
     const int tr_g = blockIdx.x;                 // b * ntr + tr
     const int b = tr_g / a.ntr;
-    float *y = smw, *F = y + a.nt, *Fm = F + a.nt;
+    df *G = smd, *Gm = G + a.nt;
+    float *y = (float *)(Gm + a.nt);
     const float *d = d_obs + (size_t)tr_g * a.nt;
     float *om = a.c.omega + (size_t)tr_g * a.nt;
     const float M = a.c.M[b];
@@ -218,32 +322,33 @@ __global__ void __launch_bounds__(NT_W2) k_obs_trace(const float *__restrict__ d
         const float di = d[i];
         const float w = 1.f / (1.f + a.k * (M > 0.f ? fabsf(di) / M : 0.f));
         om[i] = w;
-        const float yi = w * di;
-        y[i] = yi;
-        mn = fminf(mn, yi);
+        mn = fminf(mn, __fmul_rn(w, di));
     }
-    mn = block_reduce<2, NT_W2>(mn, red);
+    mn = block_reduce<2, NT_W2>(mn, redf);
     const float cs = a.cfac * fabsf(mn);
     if (threadIdx.x == 0) a.c.cshift[tr_g] = cs;
-    for (int i = threadIdx.x; i < a.nt; i += NT_W2) y[i] += cs;
+    for (int i = threadIdx.x; i < a.nt; i += NT_W2) y[i] = shifted(om[i], d[i], cs);
     __syncthreads();
-    density_cdf(y, F, Fm, a.nt, a.dt, a.eps, red);
-    float *Q = a.c.Q + (size_t)tr_g * a.nxi;
-    const float inv = 1.f / (float)(a.nxi - 1);
+    const df unit = build_cdf(y, G, Gm, a.nt, a.nxi, a.eps2dt, red);
+    int *Qb = a.c.Qb + (size_t)tr_g * a.nxi;
+    float *Qf = a.c.Qf + (size_t)tr_g * a.nxi;
     float part = 0.f;
     for (int j = threadIdx.x; j < a.nxi; j += NT_W2) {
-        const float xi = (float)j / (float)(a.nxi - 1);
-        int ks;
-        const float q = quantile(F, Fm, a.nt, a.dt, xi, &ks);
-        Q[j] = q;
+        int k, base;
+        float frac;
+        df t;
+        quantile(G, Gm, a.nt, unit, j, &k, &base, &frac, &t);
+        Qb[j] = base;
+        Qf[j] = frac;
+        const float q = ((float)base + frac) * a.dt;
         const float wj = (j == 0 || j == a.nxi - 1) ? 0.5f : 1.f;
         part += wj * q * q;
     }
-    const float s2 = block_reduce<0, NT_W2>(part, red);
-    if (threadIdx.x == 0) a.c.s_tr[tr_g] = sqrtf(inv * s2);
+    const float s2 = block_reduce<0, NT_W2>(part, redf);
+    if (threadIdx.x == 0) a.c.s_tr[tr_g] = sqrtf(s2 / (float)(a.nxi - 1));
 }
 
-// S[b] = sum of the per-trace scales (fixed order)
+// out[b] = sum_i v[b][i] (fixed order), divided by div[b] if given
 __global__ void __launch_bounds__(NT_W2) k_sum_traces(const float *__restrict__ v, int ntr,
                                                       const float *__restrict__ div,
                                                       float *__restrict__ out)
@@ -260,34 +365,39 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
                                                         float *__restrict__ w2_dst,
                                                         float *__restrict__ adj)
 {
-    extern __shared__ float smw[];
-    __shared__ float red[NW_W2 + 2];
+    extern __shared__ df smd[];
+    __shared__ df red[NW_W2 + 2];
+    __shared__ float redf[NW_W2 + 2];
     const int tr_g = blockIdx.x;
     const int b = tr_g / a.ntr;
     const int nt = a.nt, nxi = a.nxi;
-    float *y = smw, *F = y + nt, *Fm = F + nt;
-    float *dq = Fm + nt, *A = dq + nxi, *Bq = A + nxi;
-    int *ks = (int *)(Bq + nxi);
+    df *G = smd, *Gm = G + nt, *SA = Gm + nt, *SB = SA + nxi;
+    float *y = (float *)(SB + nxi);
+    float *dq = y + nt;
+    int *ks = (int *)(dq + nxi);
     const float *d = d_syn + (size_t)tr_g * nt;
     const float *om = a.c.omega + (size_t)tr_g * nt;
     const float cs = a.c.cshift[tr_g];
-    for (int i = threadIdx.x; i < nt; i += NT_W2) y[i] = om[i] * d[i] + cs;
+    for (int i = threadIdx.x; i < nt; i += NT_W2) y[i] = shifted(om[i], d[i], cs);
     __syncthreads();
-    const float Z = density_cdf(y, F, Fm, nt, a.dt, a.eps, red);
-    const float *Qo = a.c.Q + (size_t)tr_g * nxi;
-    const float dxi = 1.f / (float)(nxi - 1);
+    const df unit = build_cdf(y, G, Gm, nt, nxi, a.eps2dt, red);
+    const int *Qb = a.c.Qb + (size_t)tr_g * nxi;
+    const float *Qf = a.c.Qf + (size_t)tr_g * nxi;
     float part = 0.f;
     for (int j = threadIdx.x; j < nxi; j += NT_W2) {
-        const float xi = (float)j / (float)(nxi - 1);
-        int k;
-        const float q = quantile(F, Fm, nt, a.dt, xi, &k);
-        const float diff = q - Qo[j];
+        int k, base;
+        float frac;
+        df t;
+        quantile(G, Gm, nt, unit, j, &k, &base, &frac, &t);
+        // (base - base_obs) is exact; the fractions are in [0, 1]
+        const float diff = ((float)(base - Qb[j]) + (frac - Qf[j])) * a.dt;
         dq[j] = diff;
         ks[j] = k;
         const float wj = (j == 0 || j == nxi - 1) ? 0.5f : 1.f;
         part += wj * diff * diff;
     }
-    const float W2 = sqrtf(dxi * block_reduce<0, NT_W2>(part, red));
+    const float dxi = 1.f / (float)(nxi - 1);
+    const float W2 = sqrtf(dxi * block_reduce<0, NT_W2>(part, redf));
     if (threadIdx.x == 0) w2_dst[tr_g] = W2;
     if (!adj) return;
     float *ad = adj + (size_t)tr_g * nt;
@@ -296,46 +406,41 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
         return;
     }
     const float scale = dxi / (W2 * a.c.S[b]);
+    df cpart = {0.f, 0.f};
     for (int j = threadIdx.x; j < nxi; j += NT_W2) {
         const int k = ks[j];
-        float aj = 0.f, bj = 0.f;
+        df aj = {0.f, 0.f}, bj = {0.f, 0.f};
         if (k > 0 && k < nt) {
-            const float xi = (float)j / (float)(nxi - 1);
+            const df t = df_mul_f(unit, (float)j);
             const float wj = (j == 0 || j == nxi - 1) ? 0.5f : 1.f;
-            const float qbar = scale * wj * dq[j];
-            const float D = F[k] - F[k - 1];
+            const float qbar = scale * wj * dq[j];            // dJ/dQ_j
+            const float D = df_f(df_sub(G[k], G[k - 1]));
             const float r = qbar * a.dt / (D * D);
-            aj = r * (xi - F[k]);
-            bj = -r * (xi - F[k - 1]);
+            aj = df_from(r * df_f(df_sub(t, G[k])));          // -> dJ/dG_{k-1}
+            bj = df_from(-r * df_f(df_sub(t, G[k - 1])));     // -> dJ/dG_k
+            // through t_j = xi_j Gtot -> dJ/dG_{nt-1}
+            cpart = df_add(cpart, df_from(qbar * a.dt * ((float)j * dxi) / D));
         }
-        A[j] = aj;
-        Bq[j] = bj;
+        SA[j] = aj;
+        SB[j] = bj;
     }
-    __syncthreads();
-    block_scan<0, true>(A, nxi, red);
-    block_scan<0, true>(Bq, nxi, red);
-    // H_k into F (no longer needed), k = 0..nt-1
+    const df C = block_sum_df(cpart, red);
+    block_scan_df<0, true>(SA, nxi, red);
+    block_scan_df<0, true>(SB, nxi, red);
+    // H_k into Gm (no longer needed), k = 0..nt-1 (H_nt = 0)
     for (int k = threadIdx.x; k < nt; k += NT_W2) {
         const int jk = lower_bound_i(ks, nxi, k);
         const int jk1 = lower_bound_i(ks, nxi, k + 1);
-        F[k] = (jk1 < nxi ? A[jk1] : 0.f) + (jk < nxi ? Bq[jk] : 0.f);
+        df h = C;
+        if (jk1 < nxi) h = df_add(h, SA[jk1]);
+        if (jk < nxi) h = df_add(h, SB[jk]);
+        Gm[k] = h;
     }
     __syncthreads();
-    float zp = 0.f;
     for (int m = threadIdx.x; m < nt; m += NT_W2) {
-        const float hm = m >= 1 ? F[m] : 0.f;
-        const float hm1 = (m + 1 < nt) ? F[m + 1] : 0.f;
-        const float pb = 0.5f * a.dt * (hm + hm1);
-        Fm[m] = pb;
-        zp += pb * y[m];
-    }
-    const float zsum = block_reduce<0, NT_W2>(zp, red);
-    const float inv = 1.f / (Z + a.eps);
-    const float zbar = -zsum * inv * inv;
-    for (int m = threadIdx.x; m < nt; m += NT_W2) {
-        const float wm = (m == 0 || m == nt - 1) ? 0.5f : 1.f;
-        const float yb = Fm[m] * inv + zbar * a.dt * wm;
-        ad[m] = om[m] * yb;
+        df yb = m + 1 < nt ? Gm[m + 1] : df{0.f, 0.f};
+        if (m >= 1) yb = df_add(yb, Gm[m]);
+        ad[m] = om[m] * df_f(yb);
     }
 }
 
@@ -345,17 +450,23 @@ W2Args make_w2(const Plan &pl, unsigned char *ctx)
     a.nt = pl.p.nt;
     a.nxi = pl.w2.n_xi;
     a.ntr = pl.p.ns * pl.p.nr;
-    a.dt = pl.p.dt;
-    a.k = pl.w2.k;
-    a.cfac = pl.w2.cshift_factor;
-    a.eps = pl.w2.eps_density;
+    a.dt = (float)pl.p.dt;
+    a.k = (float)pl.w2.k;
+    a.cfac = (float)pl.w2.cshift_factor;
+    a.eps2dt = (float)(2.0 * (double)pl.w2.eps_density / (double)pl.p.dt);
     a.c = ctx_ptrs(pl, ctx);
     return a;
 }
 
+size_t obs_trace_smem(int nt) { return 2 * (size_t)nt * sizeof(df) + (size_t)nt * 4; }
+
 }  // namespace
 
-size_t w2_trace_smem(int nt, int nxi) { return (3 * (size_t)nt + 4 * (size_t)nxi) * 4; }
+size_t w2_trace_smem(int nt, int nxi)
+{
+    return 2 * (size_t)nt * sizeof(df) + 2 * (size_t)nxi * sizeof(df) + (size_t)nt * 4 +
+           (size_t)nxi * 8;
+}
 
 cudaError_t launch_w2_prepare(const Plan &pl, const float *d_obs, unsigned char *ctx,
                               cudaStream_t st)
@@ -363,7 +474,7 @@ cudaError_t launch_w2_prepare(const Plan &pl, const float *d_obs, unsigned char 
     W2Args a = make_w2(pl, ctx);
     const int B = pl.p.batch;
     k_obs_max<<<B, 1024, 0, st>>>(d_obs, (size_t)a.ntr * a.nt, a.c.M);
-    const size_t sm = 3 * (size_t)a.nt * 4;
+    const size_t sm = obs_trace_smem(a.nt);
     cudaError_t e = cudaFuncSetAttribute(k_obs_trace, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;

@@ -201,6 +201,30 @@ FWI_API fwi_status fwi_guided_step(int batch, int nz, int nx, const fwi_guide_pa
                            const float *v_prime, const float *v0hat, const float *g,
                            const float *h, float *v_out, float *rho_out, void *stream);
 
+/* Largest batch x ns x nr that fwi_w2_misfit_static accepts. */
+#define FWI_STATIC_MAX_TRACES 65536
+
+/* fwi_w2_misfit without a workspace argument (the paper has no counterpart:
+ * this is a deployment variant).  For callers that cannot provide device
+ * memory of their own -- code that runs inside a host framework owning every
+ * device allocation through its own pool, or a steady-state loop in which no
+ * allocation may happen -- the per-trace scratch of the misfit comes from an
+ * array compiled into the library (FWI_STATIC_MAX_TRACES floats of device
+ * global memory on every GPU that loads the library, held until the process
+ * exits).  The call itself allocates nothing.
+ *   Arguments and results are those of fwi_w2_misfit.
+ *   The first call on a device looks up the array's device address with
+ *   that device current; make that first call before any stream capture.
+ *   All calls on a device share the one array and it keeps the last call's
+ *   contents; every value a call reads is written by that same call first,
+ *   so nothing needs clearing.  Calls whose GPU work overlaps (different
+ *   streams or threads on the same device) race on the array: serialise them.
+ * Errors: FWI_ERR_INVALID_ARG for NULL arguments, FWI_ERR_UNSUPPORTED when
+ * batch x ns x nr exceeds FWI_STATIC_MAX_TRACES, FWI_ERR_CUDA otherwise. */
+FWI_API fwi_status fwi_w2_misfit_static(const fwi_plan *plan, const void *obs_ctx,
+                                        const float *d_syn, float *J, float *w2,
+                                        float *adj_src, void *stream);
+
 /* Wait for `stream` and return the device status word of `workspace`
  * (FWI_OK, FWI_ERR_UNSTABLE_CFL, FWI_ERR_DEVICE_TIMEOUT), then clear it. */
 FWI_API fwi_status fwi_check(const fwi_plan *plan, void *workspace, void *stream);

@@ -81,6 +81,8 @@ _lib.fwi_adjoint_grad.argtypes = [_vp] * 7
 _lib.fwi_guided_step.restype = _S
 _lib.fwi_guided_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(_Guide)] + [_vp] * 7
+_lib.fwi_w2_misfit_static.restype = _S
+_lib.fwi_w2_misfit_static.argtypes = [_vp] * 7
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -242,6 +244,14 @@ def fwi_w2_prepare(plan, d_obs, obs_ctx, stream=None):
 def fwi_w2_misfit(plan, obs_ctx, d_syn, J, w2, adj_src, workspace, stream=None):
     _check(_lib.fwi_w2_misfit(plan.raw, _ptr(obs_ctx), _ptr(d_syn), _ptr(J), _ptr(w2),
                               _ptr(adj_src), _ptr(workspace), _stream(stream)))
+
+
+def fwi_w2_misfit_static(plan, obs_ctx, d_syn, J, w2, adj_src, stream=None):
+    _check(_lib.fwi_w2_misfit_static(plan.raw, _ptr(obs_ctx), _ptr(d_syn), _ptr(J), _ptr(w2),
+                                     _ptr(adj_src), _stream(stream)))
+
+
+FWI_STATIC_MAX_TRACES = 65536
 
 
 def fwi_adjoint_grad(plan, v, adj_src, snapshots, grad, workspace, stream=None):

@@ -42,6 +42,15 @@ int *status_ptr(void *ws) { return reinterpret_cast<int *>(ws); }
 
 }  // namespace
 
+fwi_status fwi::record_error(fwi_status code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
 extern "C" {
 
 const char *fwi_last_error(void) { return g_err; }

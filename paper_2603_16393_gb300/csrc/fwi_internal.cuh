@@ -81,6 +81,10 @@ struct PropArgs {
     int16_t rec_pz[FWI_MAX_RECEIVERS], rec_px[FWI_MAX_RECEIVERS];
 };
 
+// Records the message returned by fwi_last_error() for the calling thread
+// and returns code.
+fwi_status record_error(fwi_status code, const char *fmt, ...);
+
 // Status codes the device writes (first error wins).
 __device__ __forceinline__ void set_status(int *status, int code)
 {

@@ -104,9 +104,15 @@ typedef struct fwi_w2_params {
 
 /* Guided-step hyperparameters (Eq. rho, Eq. kappa; Sec. 6.3: c = 0.1, tau = 0,
  * eps = 1e-4, gamma and rho0 per dataset in Table 1).  kappa is clipped to
- * [kappa_min, kappa_max] only when kappa_min < kappa_max. */
+ * [kappa_min, kappa_max] only when kappa_min < kappa_max.
+ * unit (> 0): the size of one unit of the diffusion's normalised space in the
+ * units of the arrays passed (1 when they are already normalised; 1500 for
+ * velocities in m/s with the normalisation (v - 3000)/1500).  The update is
+ * then exactly the normalised-space update mapped back: TV is taken on
+ * v0hat/unit, kappa on unit*g, and the step is rho kappa unit^2 h. */
 typedef struct fwi_guide_params {
     double rho0, c, tau, gamma, eps, kappa_min, kappa_max;
+    double unit;
 } fwi_guide_params;
 
 typedef struct fwi_plan fwi_plan;   /* opaque, host memory only */
@@ -193,6 +199,7 @@ FWI_API fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const 
  *   rho = rho0 exp(-(TV - tau)_+ / c)                        (Eq. rho)
  *   kappa_j = ((||g||_inf + eps)/(|g_j| + eps))^gamma         (Eq. kappa)
  *   v_out = v_prime - rho kappa . h                          (Eq. precond_step)
+ *   (with params->unit != 1, see fwi_guide_params)
  *   v_prime, v0hat, g (= grad wrt v0hat), h (= grad wrt v_i): [B][nz][nx] device
  *   v_out  [B][nz][nx] device, written (may alias v_prime)
  *   rho_out [B] device, written; NULL to skip

@@ -57,7 +57,7 @@ class _W2(ctypes.Structure):
 
 class _Guide(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
-                ("rho0", "c", "tau", "gamma", "eps", "kappa_min", "kappa_max")]
+                ("rho0", "c", "tau", "gamma", "eps", "kappa_min", "kappa_max", "unit")]
 
 
 _S = ctypes.c_int
@@ -170,6 +170,7 @@ class GuideParams:
     eps: float = 1e-4
     kappa_min: float = 0.0
     kappa_max: float = 0.0
+    unit: float = 1.0        # one normalised-space unit in the units of the arrays
 
     def _c(self):
         return _Guide(*(float(getattr(self, f)) for f, _ in _Guide._fields_))

@@ -126,7 +126,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         delete pl;
         return fail(FWI_ERR_UNSUPPORTED, "padded grid %dx%d too large", pl->NZ, pl->NX);
     }
-    pl->fast = fwi::fast_bucket(pl->NZ, pl->NX, &pl->fast_P, &pl->fast_NZM);
+    pl->fast = fwi::fast_bucket(pl->NZ, pl->NX, &pl->fast_P, &pl->fast_PR, &pl->fast_NZM);
     if (pl->fast) {
         const int nstrip = (pl->NZ + fwi::kFastRows - 1) / fwi::kFastRows;
         const size_t limit = 227 * 1024;
@@ -209,8 +209,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     pl->ctx_Qb = o;     o += align_up(B * ntr * w2->n_xi * 4);   // int bracket base
     pl->ctx_Qf = o;     o += align_up(B * ntr * w2->n_xi * 4);   // fraction in bracket
     pl->ctx_bytes = o;
-    // record planes: nzs rows of pitch fast_P (fast kernels) or NX (generic)
-    pl->snap_bytes = B * p.ns * (size_t)p.nt * pl->nzs * (pl->fast ? pl->fast_P : pl->NX) * 4;
+    // record planes: nzs rows of pitch fast_PR (fast kernels) or NX (generic)
+    pl->snap_bytes = B * p.ns * (size_t)p.nt * pl->nzs * (pl->fast ? pl->fast_PR : pl->NX) * 4;
     *out = reinterpret_cast<fwi_plan *>(pl);
     return FWI_OK;
 }
@@ -297,8 +297,9 @@ fwi_status fwi_guided_step(int batch, int nz, int nx, const fwi_guide_params *pa
         return fail(FWI_ERR_INVALID_ARG, "params and array pointers must not be NULL");
     const fwi_guide_params &gp = *params;
     if (!(gp.c > 0.0) || !(gp.eps > 0.0) || !(gp.gamma >= 0.0) || !(gp.rho0 >= 0.0) ||
-        !std::isfinite(gp.tau))
-        return fail(FWI_ERR_INVALID_ARG, "need c > 0, eps > 0, gamma >= 0, rho0 >= 0, finite tau");
+        !std::isfinite(gp.tau) || !finite_pos(gp.unit))
+        return fail(FWI_ERR_INVALID_ARG,
+                    "need c > 0, eps > 0, gamma >= 0, rho0 >= 0, finite tau, unit > 0");
     if ((size_t)nz * nx > (size_t)1 << 30) return fail(FWI_ERR_UNSUPPORTED, "grid too large");
     cudaError_t e = fwi::launch_guided(batch, nz, nx, gp, v_prime, v0hat, g, h, v_out, rho_out,
                                        (cudaStream_t)stream);

@@ -45,7 +45,7 @@ struct Plan {
     ResidentShape shape;       // forward propagator
     ResidentShape shape_adj;   // adjoint propagator
     bool fast;                 // compile-time pitch kernels (else the generic ones)
-    int fast_P, fast_NZM;      // their shared-memory pitch and row capacity
+    int fast_P, fast_PR, fast_NZM;  // their shared-memory pitch, record pitch, row capacity
     int nzs;                   // rows of one wavefield-record plane (>= NZ)
     // byte offsets inside the caller buffers
     size_t ws_w2, ws_gshot, ws_bytes;
@@ -112,7 +112,7 @@ bool choose_resident_shape(int NZ, int NX, int nr, bool adj, ResidentShape *out)
 
 // Fast propagators: bucket (pitch, row capacity) for a padded grid, their
 // shared memory, and their launch.
-bool fast_bucket(int NZ, int NX, int *P, int *NZM);
+bool fast_bucket(int NZ, int NX, int *P, int *PR, int *NZM);
 size_t fast_smem(int P, int NZM, bool adj, int chunk, int nr);
 cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st);
 

@@ -42,6 +42,7 @@ __device__ float block_reduce_g(float v, float *red)
 
 struct GuideF {
     float rho0, c, tau, gamma, eps, kappa_min, kappa_max;
+    float inv_unit, unit, unit2;   // normalised-space unit and its powers
 };
 
 __global__ void __launch_bounds__(NT_G) k_guided(int nz, int nx, GuideF gp,
@@ -63,14 +64,14 @@ __global__ void __launch_bounds__(NT_G) k_guided(int nz, int nx, GuideF gp,
         if (iz + 1 < nz) tv += fabsf(v0[i + nx] - c);
         gmax = fmaxf(gmax, fabsf(gb[i]));
     }
-    tv = block_reduce_g<false>(tv, red) / ((float)nz * (float)nx);
-    gmax = block_reduce_g<true>(gmax, red);
+    tv = block_reduce_g<false>(tv, red) / ((float)nz * (float)nx) * gp.inv_unit;
+    gmax = block_reduce_g<true>(gmax, red) * gp.unit;
     const float rho = gp.rho0 * expf(-fmaxf(tv - gp.tau, 0.f) / gp.c);
     const bool clip = gp.kappa_min < gp.kappa_max;
     for (int i = threadIdx.x; i < n; i += NT_G) {
-        float kap = powf((gmax + gp.eps) / (fabsf(gb[i]) + gp.eps), gp.gamma);
+        float kap = powf((gmax + gp.eps) / (fabsf(gb[i]) * gp.unit + gp.eps), gp.gamma);
         if (clip) kap = fminf(fmaxf(kap, gp.kappa_min), gp.kappa_max);
-        vout[off + i] = vprime[off + i] - rho * kap * h[off + i];
+        vout[off + i] = vprime[off + i] - rho * kap * (gp.unit2 * h[off + i]);
     }
     if (threadIdx.x == 0 && rho_out) rho_out[blockIdx.x] = rho;
 }
@@ -82,7 +83,8 @@ cudaError_t launch_guided(int B, int nz, int nx, const fwi_guide_params &gp, con
                           float *rho, cudaStream_t st)
 {
     const GuideF gf = {(float)gp.rho0, (float)gp.c, (float)gp.tau, (float)gp.gamma,
-                       (float)gp.eps, (float)gp.kappa_min, (float)gp.kappa_max};
+                       (float)gp.eps, (float)gp.kappa_min, (float)gp.kappa_max,
+                       (float)(1.0 / gp.unit), (float)gp.unit, (float)(gp.unit * gp.unit)};
     k_guided<<<B, NT_G, 0, st>>>(nz, nx, gf, vprime, v0hat, g, h, vout, rho);
     return cudaGetLastError();
 }

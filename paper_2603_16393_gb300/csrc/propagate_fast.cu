@@ -81,8 +81,9 @@ __device__ __forceinline__ float kappaA_cell(float v, int px, int pz, const Prop
 }
 
 // ------------------------------------------------------------------ forward
-template <int P, int TOPBC, bool STORE>
-__device__ __forceinline__ void fwd_rows(const float *cp, float *np, const float *abp, float *sw,
+template <int P, int PR, int TOPBC, bool STORE>
+__device__ __forceinline__ void fwd_rows(const float *__restrict__ cp, float *__restrict__ np,
+                                         const float *__restrict__ abp, float *__restrict__ sw,
                                          int NX, bool top_strip, float (&ka)[ROWS],
                                          float (&vi)[ROWS], const PropArgs &a)
 {
@@ -110,7 +111,7 @@ __device__ __forceinline__ void fwd_rows(const float *cp, float *np, const float
         if (TOPBC == 1 && (r == 1 || r == 2)) {
             if (top_strip) np[-r * P] = un;               // mirrored ghost rows -1, -2
         }
-        if (STORE) sw[r * P] = lap;
+        if (STORE) sw[r * PR] = lap;
         Dp = Dn;
         Em2 = Em1;
         Em1 = E0;
@@ -121,7 +122,7 @@ __device__ __forceinline__ void fwd_rows(const float *cp, float *np, const float
     }
 }
 
-template <int P, int NZM, int TOPBC, bool STORE>
+template <int P, int PR, int NZM, int TOPBC, bool STORE>
 __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_constant__ PropArgs a)
 {
     extern __shared__ float sm[];
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
     for (int r = 0; r < ROWS; ++r)
         if (r == src_row) ka_src = ka[r];
 
-    const size_t plane = (size_t)a.nzs * P;   // record planes use the pitch P
+    const size_t plane = (size_t)a.nzs * PR;   // record planes use the pitch PR
     float *snap_bs = STORE ? a.snap + (size_t)bs * a.nt * plane : nullptr;
 
     for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
@@ -185,8 +186,8 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
             if (active) {
                 const float *cp = cur + (z0 + 2) * P + x + 2;
                 float *np = nxt + (z0 + 2) * P + x + 2;
-                float *sw = STORE ? snap_bs + (size_t)j * plane + z0 * P + x : nullptr;
-                fwd_rows<P, TOPBC, STORE>(cp, np, ABt + z0 * P + x, sw, NX, top_strip, ka, vi, a);
+                float *sw = STORE ? snap_bs + (size_t)j * plane + z0 * PR + x : nullptr;
+                fwd_rows<P, PR, TOPBC, STORE>(cp, np, ABt + z0 * P + x, sw, NX, top_strip, ka, vi, a);
                 if (src_row >= 0) {
                     // point source: + kappa A s at the source cell (increment and field)
                     const float d = ka_src * ricker_scaled(j, a);
@@ -222,9 +223,11 @@ __device__ __forceinline__ float opaque(float x)
     return y;
 }
 
-template <int P, int TOPBC>
-__device__ __forceinline__ void adj_rows(const float *cp, float *np, const float *kp,
-                                         const float *sr, float zbf, float ex, bool top_strip,
+template <int P, int PR, int TOPBC>
+__device__ __forceinline__ void adj_rows(const float *__restrict__ cp, float *__restrict__ np,
+                                         const float *__restrict__ kp,
+                                         const float *__restrict__ sr, float zbf, float ex,
+                                         bool top_strip,
                                          bool active, float (&acc)[ROWS], float (&sv)[ROWS],
                                          const PropArgs &a)
 {
@@ -249,7 +252,7 @@ __device__ __forceinline__ void adj_rows(const float *cp, float *np, const float
         const float fn = fmaf(kp[r * P], lap, fmaf(A2, w0, -AB * fo));
         if (active) np[r * P] = fn;
         acc[r] = fmaf(fn, sv[r], acc[r]);
-        sv[r] = sr[r * P];
+        sv[r] = sr[r * PR];
         wm2 = wm1;
         wm1 = w0;
         w0 = wp1;
@@ -257,7 +260,7 @@ __device__ __forceinline__ void adj_rows(const float *cp, float *np, const float
     }
 }
 
-template <int P, int NZM, int TOPBC>
+template <int P, int PR, int NZM, int TOPBC>
 __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_constant__ PropArgs a)
 {
     extern __shared__ float sm[];
@@ -315,14 +318,14 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
     __shared__ float acc_src;
     if (tid == 0) acc_src = 0.f;
 
-    const size_t plane = (size_t)a.nzs * P;   // record planes use the pitch P
+    const size_t plane = (size_t)a.nzs * PR;   // record planes use the pitch PR
     float acc[ROWS], sv[ROWS];
     // record plane read next: starts at plane nt-1, moves back one plane per step
-    const float *sr = a.snap + ((size_t)bs * a.nt + (a.nt - 1)) * plane + z0 * P + x;
+    const float *sr = a.snap + ((size_t)bs * a.nt + (a.nt - 1)) * plane + z0 * PR + x;
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         acc[r] = 0.f;
-        sv[r] = sr[r * P];
+        sv[r] = sr[r * PR];
     }
 
     for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
             const float *cp = cur + (z0 + 2) * P + x + 2;
             float *np = nxt + (z0 + 2) * P + x + 2;
             const float *kp = K + z0 * P + x;
-            adj_rows<P, TOPBC>(cp, np, kp, sr, opaque(zbf), opaque(ex), top_strip, active, acc, sv,
+            adj_rows<P, PR, TOPBC>(cp, np, kp, sr, opaque(zbf), opaque(ex), top_strip, active, acc, sv,
                                a);
             __syncthreads();
             if (tid == 0) {
@@ -407,16 +410,21 @@ cudaError_t launch_k(K kern, const PropArgs &a, const ResidentShape &sh, int nbl
 
 }  // namespace
 
-// Buckets of the fast kernels: (pitch P, maximum padded rows NZM).
-bool fast_bucket(int NZ, int NX, int *P, int *NZM)
+// Buckets of the fast kernels: shared-memory pitch P, record pitch PR and
+// row capacity NZM.  P = 1 (mod 16) shifts the banks of the next 22-row strip
+// by 22 words, which keeps the warps that straddle two strips free of bank
+// conflicts at 150 padded columns (5 strips of 150 threads); the record
+// planes keep a multiple-of-32 pitch so that their rows stay 128-byte aligned.
+bool fast_bucket(int NZ, int NX, int *P, int *PR, int *NZM)
 {
-    static const int buckets[][2] = {{64, 264}, {160, 110}};
+    static const int buckets[][3] = {{65, 64, 264}, {161, 160, 110}};
     for (const auto &bk : buckets) {
-        const int p = bk[0], nzm = bk[1];
-        if (NX + 4 > p || NZ > nzm) continue;
+        const int p = bk[0], pr = bk[1], nzm = bk[2];
+        if (NX + 4 > pr || NZ > nzm) continue;
         const int nstrip = (NZ + kFastRows - 1) / kFastRows;
         if (NX * nstrip > kMaxThreadsAdj) continue;
         *P = p;
+        *PR = pr;
         *NZM = nzm;
         return true;
     }
@@ -438,19 +446,19 @@ cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_
     const ResidentShape &sh = adj ? pl.shape_adj : pl.shape;
     const bool store = a.snap != nullptr;
     const int tb = pl.p.top_bc;
-#define FWI_FAST(PP, NN)                                                                       \
+#define FWI_FAST(PP, PPR, NN)                                                                  \
     if (pl.fast_P == PP && pl.fast_NZM == NN) {                                                \
         if (adj)                                                                               \
-            return tb ? launch_k(k_adj_fast<PP, NN, 1>, a, sh, nb, st)                         \
-                      : launch_k(k_adj_fast<PP, NN, 0>, a, sh, nb, st);                        \
+            return tb ? launch_k(k_adj_fast<PP, PPR, NN, 1>, a, sh, nb, st)                    \
+                      : launch_k(k_adj_fast<PP, PPR, NN, 0>, a, sh, nb, st);                   \
         if (store)                                                                             \
-            return tb ? launch_k(k_fwd_fast<PP, NN, 1, true>, a, sh, nb, st)                   \
-                      : launch_k(k_fwd_fast<PP, NN, 0, true>, a, sh, nb, st);                  \
-        return tb ? launch_k(k_fwd_fast<PP, NN, 1, false>, a, sh, nb, st)                      \
-                  : launch_k(k_fwd_fast<PP, NN, 0, false>, a, sh, nb, st);                     \
+            return tb ? launch_k(k_fwd_fast<PP, PPR, NN, 1, true>, a, sh, nb, st)              \
+                      : launch_k(k_fwd_fast<PP, PPR, NN, 0, true>, a, sh, nb, st);             \
+        return tb ? launch_k(k_fwd_fast<PP, PPR, NN, 1, false>, a, sh, nb, st)                 \
+                  : launch_k(k_fwd_fast<PP, PPR, NN, 0, false>, a, sh, nb, st);                \
     }
-    FWI_FAST(64, 264)
-    FWI_FAST(160, 110)
+    FWI_FAST(65, 64, 264)
+    FWI_FAST(161, 160, 110)
 #undef FWI_FAST
     return cudaErrorInvalidValue;
 }

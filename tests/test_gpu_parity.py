@@ -246,3 +246,21 @@ def test_guided_step_matches_oracle(api, B, nz, nx, gamma, kmin, kmax):
     upd, _ = api.guided_step(T(z), T(v0), T(g), T(h), api.GuideParams(**prm))
     upd_o, _ = O.guided_step(z, v0, g, h, O.GuideParams(**prm))
     assert rel_l2(H(upd), upd_o) <= 1e-5
+
+
+def test_guided_step_in_physical_units(api):
+    # unit = a: the kernel must equal the paper's update applied in the
+    # normalised space v_n = (v - b)/a and mapped back, i.e. the oracle on
+    # (v', v0hat / a, a g, a^2 h)
+    rng = np.random.default_rng(42)
+    f32 = lambda x: x.astype(np.float32).astype(np.float64)  # noqa: E731
+    B, nz, nx, a = 2, 70, 70, 1500.0
+    v = f32(1500.0 + 3000.0 * rng.random((B, nz, nx)))
+    g = f32(rng.standard_normal((B, nz, nx)) * 1e-7)
+    h = f32(rng.standard_normal((B, nz, nx)) * 1e-7)
+    prm = dict(rho0=1.15, c=0.1, tau=0.0, gamma=0.55, eps=1e-4, kappa_min=0.0, kappa_max=0.0)
+    z = np.zeros_like(v)          # v' = 0: the output is the update itself
+    upd, rho = api.guided_step(T(z), T(v), T(g), T(h), api.GuideParams(unit=a, **prm))
+    upd_o, rho_o = O.guided_step(z, v / a, g * a, h * a * a, O.GuideParams(**prm))
+    assert rel_l2(H(rho), rho_o) <= 1e-5
+    assert rel_l2(H(upd), upd_o) <= 1e-5

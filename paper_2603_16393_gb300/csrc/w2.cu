@@ -4,8 +4,11 @@
 // Per trace (Sec. 6.2 numerics), written in the un-normalised running sum
 //   G_0 = 0,  G_k = sum_{i=1..k} (y_{i-1} + y_i),   y = omega d + c'
 // The trapezoid CDF is F_k = G_k / Gtot with Gtot = G_{nt-1} + 2 eps'/dt
-// (because Z = dt G_{nt-1} / 2), so
-//   k*_j  = min{k : F_k >= xi_j} = min{k : G_k >= t_j},  t_j = xi_j Gtot
+// (because Z = dt G_{nt-1} / 2).  A synthetic trace can lie mostly below the
+// shift taken from the observed data, so Gtot may be negative; with
+// s = sign(Gtot) both sides of F_k >= xi_j are multiplied by s |Gtot| and the
+// CDF is worked in the sign-corrected sums G~ = s G:
+//   k*_j  = min{k : F_k >= xi_j} = min{k : G~_k >= t_j},  t_j = xi_j |Gtot|
 //   Q_j   = t_{k*-1} + dt (t_j - G_{k*-1}) / (G_{k*} - G_{k*-1})   (clamped at the ends)
 //   W2    = (dxi sum_j w_j (Q_j - Qobs_j)^2)^(1/2),  J = sum W2 / S_obs
 // Quantiles are kept as (bracket base index, fraction in [0,1]); the
@@ -17,7 +20,9 @@
 // to dJ/dG_{nt-1} through t_j, and k*_j non-decreasing in j:
 //   H_k = sum_{k' >= k} dJ/dG_{k'} = SA[J(k+1)] + SB[J(k)] + C [k <= nt-1],
 // with SA, SB suffix sums over j, J(k) = min{j : k*_j >= k}, C = sum_j c_j;
-//   dJ/dy_m = H_m [m >= 1] + H_{m+1},   dJ/dd_m = omega_m dJ/dy_m.
+//   dJ/dy_m = s (H_m [m >= 1] + H_{m+1}),   dJ/dd_m = omega_m dJ/dy_m,
+// where H is taken with respect to G~ (the interpolation fraction is the
+// same in G and G~, and t_j depends on G~_{nt-1} through xi_j).
 //
 // Precision: everything is float32; the running sums, the thresholds, the
 // suffix sums and C are double-float (hi + lo float pairs, ~48-bit
@@ -263,18 +268,28 @@ __device__ __forceinline__ float shifted(float w, float d, float cs)
     return __fadd_rn(__fmul_rn(w, d), cs);
 }
 
-// Running sums G and their running max Gm from y (all in shared memory);
-// returns the quantile step unit = Gtot / (nxi - 1).
-__device__ df build_cdf(const float *y, df *G, df *Gm, int nt, int nxi, float eps2dt, df *red)
+// Sign-corrected running sums G~ = s G and their running max Gm from y (all
+// in shared memory); returns the quantile step unit = |Gtot| / (nxi - 1) and
+// writes s = sign(Gtot) (+1 when Gtot is zero).
+__device__ df build_cdf(const float *y, df *G, df *Gm, int nt, int nxi, float eps2dt, df *red,
+                        float *sgn)
 {
     for (int i = threadIdx.x; i < nt; i += NT_W2)
         G[i] = i == 0 ? df{0.f, 0.f} : two_sum(y[i - 1], y[i]);
     __syncthreads();
     block_scan_df<0, false>(G, nt, red);
-    for (int i = threadIdx.x; i < nt; i += NT_W2) Gm[i] = G[i];
+    df gtot = df_add(G[nt - 1], df_from(eps2dt));
+    const bool neg = gtot.hi < 0.f;
+    __syncthreads();                  // every thread has read G[nt - 1]
+    for (int i = threadIdx.x; i < nt; i += NT_W2) {
+        const df g = neg ? df_neg(G[i]) : G[i];
+        G[i] = g;
+        Gm[i] = g;
+    }
     __syncthreads();
     block_scan_df<1, false>(Gm, nt, red);
-    const df gtot = df_add(G[nt - 1], df_from(eps2dt));
+    if (neg) gtot = df_neg(gtot);
+    *sgn = neg ? -1.f : 1.f;
     return df_div_f(gtot, (float)(nxi - 1));
 }
 
@@ -329,7 +344,8 @@ __global__ void __launch_bounds__(NT_W2) k_obs_trace(const float *__restrict__ d
     if (threadIdx.x == 0) a.c.cshift[tr_g] = cs;
     for (int i = threadIdx.x; i < a.nt; i += NT_W2) y[i] = shifted(om[i], d[i], cs);
     __syncthreads();
-    const df unit = build_cdf(y, G, Gm, a.nt, a.nxi, a.eps2dt, red);
+    float sgn;
+    const df unit = build_cdf(y, G, Gm, a.nt, a.nxi, a.eps2dt, red, &sgn);
     int *Qb = a.c.Qb + (size_t)tr_g * a.nxi;
     float *Qf = a.c.Qf + (size_t)tr_g * a.nxi;
     float part = 0.f;
@@ -380,7 +396,8 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
     const float cs = a.c.cshift[tr_g];
     for (int i = threadIdx.x; i < nt; i += NT_W2) y[i] = shifted(om[i], d[i], cs);
     __syncthreads();
-    const df unit = build_cdf(y, G, Gm, nt, nxi, a.eps2dt, red);
+    float sgn;
+    const df unit = build_cdf(y, G, Gm, nt, nxi, a.eps2dt, red, &sgn);
     const int *Qb = a.c.Qb + (size_t)tr_g * nxi;
     const float *Qf = a.c.Qf + (size_t)tr_g * nxi;
     float part = 0.f;
@@ -440,7 +457,7 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
     for (int m = threadIdx.x; m < nt; m += NT_W2) {
         df yb = m + 1 < nt ? Gm[m + 1] : df{0.f, 0.f};
         if (m >= 1) yb = df_add(yb, Gm[m]);
-        ad[m] = om[m] * df_f(yb);
+        ad[m] = om[m] * (sgn * df_f(yb));
     }
 }
 

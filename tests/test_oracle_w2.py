@@ -196,3 +196,36 @@ def test_adjoint_source_matches_central_differences():
         fd = (O.w2_misfit(ctx, syn + h * e, DT, w2p, False)[0][0] -
               O.w2_misfit(ctx, syn - h * e, DT, w2p, False)[0][0]) / (2 * h)
         assert abs(fd - adj[0, 1, 2, k]) < 1e-6 * np.abs(adj[0, 1, 2]).max()
+
+
+def test_negative_total_mass_density_and_derivative():
+    # A synthetic trace can lie mostly below the shift c' taken from the
+    # observed data, so that its weighted, shifted values integrate to a
+    # negative total Z.  The density map y / (Z + eps') (Eq. pdf_map) still
+    # normalises it; with eps' = 0 negating a signal leaves its density, its
+    # quantiles and every W2 unchanged.
+    ya, yb = gauss(0.40, 0.05), gauss(0.52, 0.03)
+    w = O.w2_signals(ya, yb, DT, eps=0.0, nxi=500)
+    assert O.w2_signals(-ya, yb, DT, eps=0.0, nxi=500) == w
+    assert O.w2_signals(-ya, -yb, DT, eps=0.0, nxi=500) == w
+    # translation closed form still holds for the negated pair
+    yc = gauss(0.40 + 0.07, 0.05)
+    np.testing.assert_allclose(O.w2_signals(-ya, -yc, DT, eps=0.0, nxi=1000), 0.07, rtol=2e-3)
+    # the misfit of a cube whose traces have a negative total, and its
+    # derivative against central differences
+    d = _cube(11)
+    syn = -4.0 * np.abs(_cube(12))
+    w2p = O.W2Params(n_xi=400)
+    ctx = O.w2_prepare(d, DT, w2p)
+    y = ctx.omega * syn + ctx.cshift[..., None]
+    assert np.all(np.trapezoid(y, dx=DT, axis=-1) < 0)
+    J, w2, adj = O.w2_misfit(ctx, syn, DT, w2p)
+    assert np.all(np.isfinite(w2)) and J[0] > 0
+    rng = np.random.default_rng(13)
+    for _ in range(2):
+        dd = rng.standard_normal(syn.shape)
+        h = 1e-7
+        Jp = O.w2_misfit(ctx, syn + h * dd, DT, w2p, with_adjoint=False)[0][0]
+        Jm = O.w2_misfit(ctx, syn - h * dd, DT, w2p, with_adjoint=False)[0][0]
+        an = np.vdot(adj, dd)
+        assert abs((Jp - Jm) / (2 * h) - an) < 1e-6 * abs(an)

@@ -97,6 +97,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
                     "v_max dt sqrt(1/dx^2 + 1/dz^2) = %.4f exceeds sqrt(3)/2 = 0.8660", cfl);
 
     Plan *pl = new (std::nothrow) Plan();
+    if (pl) pl->fwd_pair = false;
     if (!pl) return fail(FWI_ERR_INVALID_ARG, "out of host memory");
     pl->p = p;
     pl->w2 = *w2;
@@ -145,6 +146,37 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
             if (chunk < 1) pl->fast = false;
         }
         pl->nzs = nstrip * fwi::kFastRows;
+        pl->fwd_pair = pl->fast && fwi::fwd_pair_ok(pl->NX, pl->NZ, pl->fast_NZM);
+        if (pl->fwd_pair) {
+            fwi::ResidentShape &sh = pl->shape;
+            const int nstrip2 = (pl->NZ + fwi::kFastRows / 2 - 1) / (fwi::kFastRows / 2);
+            sh.rows = fwi::kFastRows / 2;
+            sh.maxrows = sh.rows;
+            sh.nstrip = nstrip2;
+            sh.threads = (((pl->NX / 2) * nstrip2 + 31) / 32) * 32;
+            const size_t limit = 227 * 1024;
+            const size_t fixed = fwi::fast_smem(fwi::kPairPitch, pl->fast_NZM, false, 0, p.nr);
+            int chunk = fixed + (size_t)p.nr * 4 > limit
+                            ? 0 : (int)((limit - fixed) / ((size_t)p.nr * 4));
+            if (chunk > 32) chunk = 32;
+            sh.chunk = chunk;
+            sh.smem = fwi::fast_smem(fwi::kPairPitch, pl->fast_NZM, false, chunk, p.nr);
+            if (chunk < 1) pl->fwd_pair = false;
+            if (nstrip2 * sh.rows > pl->nzs) pl->nzs = nstrip2 * sh.rows;
+        }
+        if (!pl->fwd_pair && pl->fast) {   // restore the single-column forward shape
+            fwi::ResidentShape &sh = pl->shape;
+            sh.rows = fwi::kFastRows;
+            sh.maxrows = fwi::kFastRows;
+            sh.nstrip = nstrip;
+            sh.threads = ((pl->NX * nstrip + 31) / 32) * 32;
+            const size_t limit = 227 * 1024;
+            const size_t fixed = fwi::fast_smem(pl->fast_P, pl->fast_NZM, false, 0, p.nr);
+            int chunk = (int)((limit - fixed) / ((size_t)p.nr * 4));
+            if (chunk > 32) chunk = 32;
+            sh.chunk = chunk;
+            sh.smem = fwi::fast_smem(pl->fast_P, pl->fast_NZM, false, chunk, p.nr);
+        }
     }
     if (!pl->fast) {
         if (!fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, false, &pl->shape) ||

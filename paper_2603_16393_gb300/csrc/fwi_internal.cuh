@@ -18,6 +18,9 @@ constexpr int kMaxThreadsFwd = 1024;
 constexpr int kMaxThreadsAdj = 768;
 // Rows per thread strip of the fast (compile-time pitch) propagators.
 constexpr int kFastRows = 22;
+// Shared-memory pitch of the column-pair forward (even for 8-byte accesses;
+// 11 x 162 = 22 (mod 32) keeps strip-straddling half-warps conflict-free).
+constexpr int kPairPitch = 162;
 constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -45,6 +48,7 @@ struct Plan {
     ResidentShape shape;       // forward propagator
     ResidentShape shape_adj;   // adjoint propagator
     bool fast;                 // compile-time pitch kernels (else the generic ones)
+    bool fwd_pair;             // forward on column pairs (even padded width)
     int fast_P, fast_PR, fast_NZM;  // their shared-memory pitch, record pitch, row capacity
     int nzs;                   // rows of one wavefield-record plane (>= NZ)
     // byte offsets inside the caller buffers
@@ -114,6 +118,7 @@ bool choose_resident_shape(int NZ, int NX, int nr, bool adj, ResidentShape *out)
 // shared memory, and their launch.
 bool fast_bucket(int NZ, int NX, int *P, int *PR, int *NZM);
 size_t fast_smem(int P, int NZM, bool adj, int chunk, int nr);
+bool fwd_pair_ok(int NX, int NZ, int NZM);
 cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st);
 
 }  // namespace fwi

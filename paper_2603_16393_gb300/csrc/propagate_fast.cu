@@ -212,6 +212,153 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
     }
 }
 
+// ------------------------------------------------------------------ forward, column pairs
+// Same arithmetic as k_fwd_fast, but each thread owns two adjacent columns
+// (x, x+1) and 11 rows, and moves them as float2: per row three 8-byte
+// loads ((x-2, x-1), the window row z+2, (x+2, x+3)) and one 8-byte store
+// serve two cell-updates.  Needs an even padded width.
+constexpr int ROWS2 = kFastRows / 2;
+
+template <int P, int PR, int TOPBC, bool STORE>
+__device__ __forceinline__ void fwd_rows_pair(const float *__restrict__ cp, float *__restrict__ np,
+                                              const float *__restrict__ abp,
+                                              float *__restrict__ sw, bool top_strip,
+                                              float (&ka)[2 * ROWS2], float (&vi)[2 * ROWS2],
+                                              const PropArgs &a)
+{
+    float2 wm2 = *(const float2 *)(cp - 2 * P), wm1 = *(const float2 *)(cp - P);
+    float2 w0 = *(const float2 *)cp, wp1 = *(const float2 *)(cp + P);
+#pragma unroll
+    for (int r = 0; r < ROWS2; ++r) {
+        const float *c = cp + r * P;
+        const float2 wp2 = *(const float2 *)(c + 2 * P);
+        const float2 L = *(const float2 *)(c - 2);     // u[x-2], u[x-1]
+        const float2 R = *(const float2 *)(c + 2);     // u[x+2], u[x+3]
+        const float d01 = w0.y - w0.x;
+        const float dxA0 = (L.y - w0.x) + d01;
+        const float dxB0 = (L.x - w0.x) + (R.x - w0.x);
+        const float dxA1 = (R.x - w0.y) - d01;
+        const float dxB1 = (L.y - w0.y) + (R.y - w0.y);
+        const float dzA0 = (wm1.x - w0.x) + (wp1.x - w0.x);
+        const float dzA1 = (wm1.y - w0.y) + (wp1.y - w0.y);
+        const float dzB0 = (wm2.x - w0.x) + (wp2.x - w0.x);
+        const float dzB1 = (wm2.y - w0.y) + (wp2.y - w0.y);
+        float lap0 = a.cx1 * dxA0, lap1 = a.cx1 * dxA1;
+        lap0 = fmaf(a.cx2, dxB0, lap0);
+        lap1 = fmaf(a.cx2, dxB1, lap1);
+        lap0 = fmaf(a.cz1, dzA0, lap0);
+        lap1 = fmaf(a.cz1, dzA1, lap1);
+        lap0 = fmaf(a.cz2, dzB0, lap0);
+        lap1 = fmaf(a.cz2, dzB1, lap1);
+        const float2 ab = *(const float2 *)(abp + r * P);
+        vi[2 * r] = fmaf(ka[2 * r], lap0, ab.x * vi[2 * r]);
+        vi[2 * r + 1] = fmaf(ka[2 * r + 1], lap1, ab.y * vi[2 * r + 1]);
+        const float2 un = make_float2(w0.x + vi[2 * r], w0.y + vi[2 * r + 1]);
+        *(float2 *)(np + r * P) = un;
+        if (TOPBC == 1 && (r == 1 || r == 2)) {
+            if (top_strip) *(float2 *)(np - r * P) = un;  // mirrored ghost rows -1, -2
+        }
+        if (STORE) *(float2 *)(sw + r * PR) = make_float2(lap0, lap1);
+        wm2 = wm1;
+        wm1 = w0;
+        w0 = wp1;
+        wp1 = wp2;
+    }
+}
+
+template <int P, int PR, int NZM, int TOPBC, bool STORE>
+__global__ void __launch_bounds__(kMaxThreadsAdj, 1)
+k_fwd_pair(const __grid_constant__ PropArgs a)
+{
+    extern __shared__ __align__(16) float sm[];
+    constexpr int FSZ = (NZM + 4) * P;
+    float *U0 = sm, *U1 = sm + FSZ, *ABt = sm + 2 * FSZ, *ST = ABt + NZM * P;
+    const int NX = a.NX, NZ = a.NZ;
+    const int bs = blockIdx.x, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < 2 * FSZ; i += nth) sm[i] = 0.f;
+    for (int i = tid; i < NZM * P; i += nth) {
+        const int pz = i / P, px = i - (i / P) * P;
+        const double e = e_cell(px, pz, a);
+        ABt[i] = (float)((1.0 - e) / (1.0 + e));
+    }
+
+    const int NXP = NX / 2;
+    const int xp = tid % NXP, strip = tid / NXP;
+    const bool active = strip < a.nstrip;
+    const int x = 2 * xp, z0 = strip * ROWS2;
+    const float *vb = a.v + (size_t)b * a.nz * a.nx;
+    float ka[2 * ROWS2], vi[2 * ROWS2];
+    int bad = 0;
+#pragma unroll
+    for (int r = 0; r < ROWS2; ++r) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int z = z0 + r;
+            float k = 0.f;
+            if (active && z < NZ) {
+                const int ixc = min(max(x + c - a.nb, 0), a.nx - 1);
+                const float vv = vb[min(z, a.nz - 1) * a.nx + ixc];
+                if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
+                k = kappaA_cell(vv, x + c, z, a);
+            }
+            ka[2 * r + c] = k;
+            vi[2 * r + c] = 0.f;
+        }
+    }
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
+        return;
+    }
+    const bool top_strip = active && z0 == 0;
+
+    // source owner: row and column inside this thread's 11 x 2 block
+    const int sz = a.src_pz[s], sx = a.src_px[s];
+    const int src_k = (active && (sx >> 1) == xp && sz >= z0 && sz < z0 + ROWS2)
+                          ? 2 * (sz - z0) + (sx & 1) : -1;
+    // record plane of the current step (advanced by one plane per step)
+    float *sw = STORE ? a.snap + (size_t)bs * a.nt * a.nzs * PR + z0 * PR + x : nullptr;
+
+    for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
+        const int nch = min(a.chunk, a.nt - j0);
+        for (int jj = 0; jj < nch; ++jj) {
+            const int j = j0 + jj;
+            const float *cur = (j & 1) ? U1 : U0;
+            float *nxt = (j & 1) ? U0 : U1;
+            if (active) {
+                const float *cp = cur + (z0 + 2) * P + x + 2;
+                float *np = nxt + (z0 + 2) * P + x + 2;
+                fwd_rows_pair<P, PR, TOPBC, STORE>(cp, np, ABt + z0 * P + x, sw, top_strip, ka,
+                                                   vi, a);
+                if (src_k >= 0) {
+                    // point source: + kappa A s at the source cell (increment and field)
+                    float kas = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 2 * ROWS2; ++k)
+                        if (k == src_k) kas = ka[k];
+                    const float d = kas * ricker_scaled(j, a);
+#pragma unroll
+                    for (int k = 0; k < 2 * ROWS2; ++k)
+                        if (k == src_k) vi[k] += d;
+                    const int sz = a.src_pz[s], sx = a.src_px[s];
+                    nxt[(sz + 2) * P + sx + 2] += d;
+                    if (TOPBC == 1 && (sz == 1 || sz == 2)) nxt[(2 - sz) * P + sx + 2] += d;
+                }
+            }
+            if (STORE) sw += (size_t)a.nzs * PR;
+            __syncthreads();
+            if (tid < a.nr) ST[jj * a.nr + tid] = nxt[(a.rec_pz[tid] + 2) * P + a.rec_px[tid] + 2];
+        }
+        __syncthreads();
+        float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
+        for (int e = tid; e < nch * a.nr; e += nth) {
+            const int i = e / nch, jj = e - (e / nch) * nch;
+            db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ adjoint
 // Returns x through an opaque move: values derived from it inside the time
 // loop are recomputed every step instead of being hoisted out of the loop
@@ -431,6 +578,12 @@ bool fast_bucket(int NZ, int NX, int *P, int *PR, int *NZM)
     return false;
 }
 
+bool fwd_pair_ok(int NX, int NZ, int NZM)
+{
+    const int nstrip = (NZ + kFastRows / 2 - 1) / (kFastRows / 2);
+    return NZM == 110 && NX % 2 == 0 && NX + 4 <= 160 && (NX / 2) * nstrip <= kMaxThreadsAdj;
+}
+
 size_t fast_smem(int P, int NZM, bool adj, int chunk, int nr)
 {
     // two field levels + one per-cell table (A B for the forward, kappa A for
@@ -456,6 +609,14 @@ cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_
                       : launch_k(k_fwd_fast<PP, PPR, NN, 0, true>, a, sh, nb, st);             \
         return tb ? launch_k(k_fwd_fast<PP, PPR, NN, 1, false>, a, sh, nb, st)                 \
                   : launch_k(k_fwd_fast<PP, PPR, NN, 0, false>, a, sh, nb, st);                \
+    }
+    if (!adj && pl.fwd_pair) {
+        if (pl.fast_NZM == 110)
+            return store ? (tb ? launch_k(k_fwd_pair<kPairPitch, 160, 110, 1, true>, a, sh, nb, st)
+                               : launch_k(k_fwd_pair<kPairPitch, 160, 110, 0, true>, a, sh, nb, st))
+                         : (tb ? launch_k(k_fwd_pair<kPairPitch, 160, 110, 1, false>, a, sh, nb, st)
+                               : launch_k(k_fwd_pair<kPairPitch, 160, 110, 0, false>, a, sh, nb, st));
+        return cudaErrorInvalidValue;
     }
     FWI_FAST(65, 64, 264)
     FWI_FAST(161, 160, 110)

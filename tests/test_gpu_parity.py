@@ -41,6 +41,8 @@ def H(t):
     (31, 17, 9, 250, 2, 1),      # mirrored top
     (12, 40, 4, 200, 4, 0),
     (1, 9, 3, 120, 1, 0),        # single physical row
+    (30, 70, 20, 300, 3, 0),     # NX = 110 even: column-pair forward, ragged last strip
+    (41, 64, 25, 260, 2, 1),     # column-pair forward with the mirrored top
 ])
 def test_forward_matches_oracle(api, nz, nx, nb, nt, ns, top_bc):
     gp, op = problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc)
@@ -108,6 +110,38 @@ def test_w2_misfit_on_shared_data(api, k, nxi):
     assert rel_l2(H(adj), adj_o) <= TOL_ADJ, rel_l2(H(adj), adj_o)
 
 
+def test_w2_misfit_negative_total_mass(api):
+    # synthetic traces far below the observed data's shift c': their shifted
+    # values have a negative total, so the density y / (Z + eps') flips sign
+    # (Eq. pdf_map); one instance all negative, one mixed
+    gp, op, vt, v0, w2p, ow2 = _w2_case(api, nt=300, nxi=400)
+    B, ns, nr, nt = 2, gp.ns, gp.nr, gp.nt
+    rng = np.random.default_rng(21)
+    t = np.arange(nt) * op.dt
+    d_obs = np.zeros((B, ns, nr, nt))
+    for idx in np.ndindex(B, ns, nr):
+        t0, f = rng.uniform(0.03, 0.15), rng.uniform(15, 30)
+        a = (np.pi * f * (t - t0)) ** 2
+        d_obs[idx] = rng.uniform(0.2, 1.0) * (1 - 2 * a) * np.exp(-a)
+    d_obs += 0.01 * rng.standard_normal(d_obs.shape)
+    d_syn = np.roll(d_obs, 7, axis=-1) - 0.02 * rng.uniform(0.5, 1.5, (B, ns, nr, 1))
+    d_syn[0] = -np.abs(d_syn[0]) - 0.05
+    d_obs = d_obs.astype(np.float32).astype(np.float64)
+    d_syn = d_syn.astype(np.float32).astype(np.float64)
+    octx = O.w2_prepare(d_obs, op.dt, ow2)
+    ysum = np.sum(octx.omega * d_syn + octx.cshift[..., None], axis=-1)
+    assert np.all(ysum[0] < 0) and np.any(ysum[1] < 0) and np.any(ysum[1] > 0)
+    with api.Plan(gp, w2p) as plan:
+        ctx = plan.w2_prepare(T(d_obs))
+        J, w2, adj = plan.w2_misfit(ctx, T(d_syn))
+        torch.cuda.synchronize()
+    J_o, w2_o, adj_o = O.w2_misfit(octx, d_syn, op.dt, ow2)
+    assert rel_l2(H(J), J_o) <= TOL_J, (H(J), J_o)
+    assert rel_l2(H(w2), w2_o) <= TOL_J
+    for b in range(B):
+        assert rel_l2(H(adj)[b], adj_o[b]) <= TOL_ADJ, (b, rel_l2(H(adj)[b], adj_o[b]))
+
+
 def test_w2_zero_at_observation(api):
     gp, op, vt, v0, w2p, ow2 = _w2_case(api)
     with api.Plan(gp, w2p) as plan:
@@ -124,6 +158,7 @@ def test_w2_zero_at_observation(api):
 @pytest.mark.parametrize("nz,nx,nb,nt,ns,top_bc", [
     (20, 23, 7, 300, 3, 0),
     (18, 26, 6, 260, 2, 1),
+    (30, 70, 20, 300, 3, 0),     # column-pair forward
 ])
 def test_gradient_matches_oracle_small(api, nz, nx, nb, nt, ns, top_bc):
     gp, op = problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc)

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 10000  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 10100  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -91,6 +91,11 @@ typedef struct fwi_problem {
     double refl_R;       /* nominal two-way amplitude reflection of the layer, (0,1] */
     double v_max;        /* declared upper bound of every velocity passed in, m/s  */
     int batch;           /* B models per call, >= 1                                 */
+    int checkpoint_every; /* 0: fwi_forward keeps the whole wavefield record for the
+                            adjoint; K >= 1: it keeps the propagator state every K
+                            steps and fwi_adjoint_grad recomputes each K-step segment
+                            from it (same arithmetic, bitwise-identical gradient,
+                            about nt/K times less memory, one extra forward pass) */
 } fwi_problem;
 
 /* Misfit hyperparameters (Sec. 5.1, 6.2, 6.3): k = 100, c' factor 1.1,
@@ -133,10 +138,13 @@ FWI_API void fwi_plan_destroy(fwi_plan *plan);
 /* Bytes the caller must provide:
  *   workspace: device scratch passed to fwi_forward / fwi_w2_misfit /
  *              fwi_adjoint_grad / fwi_check; its first 256 bytes hold the
- *              device status word;
+ *              device status word (with checkpoint_every = K it also holds
+ *              the K-step record of one segment and the adjoint state);
  *   obs_ctx:   filled by fwi_w2_prepare, read by fwi_w2_misfit;
- *   snapshots: the forward wavefield record (nt time levels of the padded
- *              grid per model and shot) that fwi_adjoint_grad reads.
+ *   snapshots: what fwi_forward keeps for fwi_adjoint_grad: the wavefield
+ *              record (nt time levels of the padded grid per model and shot)
+ *              when checkpoint_every = 0, else ceil(nt/K) checkpoints of the
+ *              propagator state (two padded grids per model and shot each).
  * Any output pointer may be NULL. */
 FWI_API fwi_status fwi_plan_sizes(const fwi_plan *plan, size_t *workspace_bytes,
                           size_t *obs_ctx_bytes, size_t *snapshot_bytes);
@@ -184,9 +192,12 @@ FWI_API fwi_status fwi_w2_misfit(const fwi_plan *plan, const void *obs_ctx, cons
 /* dJ/dv by the discrete adjoint of fwi_forward (time-reversed solve with the
  * adjoint source injected at the receivers, imaging condition, fold of the
  * absorbing layer onto the edge cells, sum over shots in a fixed order).
+ * With checkpoint_every = K the time loop runs as ceil(nt/K) segments, last
+ * first: each recomputes its K forward steps from its checkpoint into the
+ * workspace, then runs them backwards (2 ceil(nt/K) + 1 launches).
  *   v         [B][nz][nx] device, the same models fwi_forward was given
  *   adj_src   [B][ns][nr][nt] device (from fwi_w2_misfit)
- *   snapshots the record fwi_forward wrote for these models
+ *   snapshots what fwi_forward wrote for these models (record or checkpoints)
  *   grad      [B][nz][nx] device, written, 1/(m/s)
  *   workspace device buffer of workspace_bytes */
 FWI_API fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const float *adj_src,

@@ -47,7 +47,8 @@ class _Problem(ctypes.Structure):
                 ("nr", ctypes.c_int), ("src_iz", _ip), ("src_ix", _ip), ("rec_iz", _ip),
                 ("rec_ix", _ip), ("f_peak", ctypes.c_double), ("t0", ctypes.c_double),
                 ("v_ref", ctypes.c_double), ("refl_R", ctypes.c_double),
-                ("v_max", ctypes.c_double), ("batch", ctypes.c_int)]
+                ("v_max", ctypes.c_double), ("batch", ctypes.c_int),
+                ("checkpoint_every", ctypes.c_int)]
 
 
 class _W2(ctypes.Structure):
@@ -133,6 +134,7 @@ class Problem:
     v_max: float = 4500.0
     batch: int = 1
     top_bc: int = 0
+    checkpoint_every: int = 0     # 0: keep the whole record; K: checkpoint every K steps
 
     @property
     def ns(self):
@@ -218,7 +220,8 @@ def fwi_plan_create(prob: Problem, w2: W2Params) -> _Handle:
     cp = _Problem(prob.nz, prob.nx, prob.dz, prob.dx, prob.nb, prob.top_bc, prob.nt, prob.dt,
                   len(prob.src_ix), len(prob.rec_ix),
                   *[ctypes.cast(a, _ip) for a in arrays],
-                  prob.f_peak, prob.t0, prob.v_ref, prob.refl_R, prob.v_max, prob.batch)
+                  prob.f_peak, prob.t0, prob.v_ref, prob.refl_R, prob.v_max, prob.batch,
+                  prob.checkpoint_every)
     if len(prob.src_iz) != len(prob.src_ix) or len(prob.rec_iz) != len(prob.rec_ix):
         raise ValueError("source/receiver index lists differ in length")
     cw = _W2(w2.k, w2.cshift_factor, w2.eps_density, w2.n_xi)

@@ -83,6 +83,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (!(p.refl_R > 0.0 && p.refl_R <= 1.0))
         return fail(FWI_ERR_INVALID_ARG, "refl_R must be in (0, 1]");
     if (!finite_pos(p.v_max)) return fail(FWI_ERR_INVALID_ARG, "v_max must be > 0");
+    if (p.checkpoint_every < 0) return fail(FWI_ERR_INVALID_ARG, "checkpoint_every must be >= 0");
     if (w2->n_xi < 2) return fail(FWI_ERR_INVALID_ARG, "n_xi must be >= 2");
     if (!(w2->k >= 0.0) || !std::isfinite(w2->k)) return fail(FWI_ERR_INVALID_ARG, "k must be >= 0");
     if (!(w2->cshift_factor >= 0.0) || !std::isfinite(w2->cshift_factor))
@@ -231,6 +232,20 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     o += align_up(B * ntr * 4);
     pl->ws_gshot = o;
     o += align_up(B * p.ns * (size_t)p.nz * p.nx * 4);
+    // record planes: nzs rows of pitch fast_PR (fast kernels) or NX (generic)
+    const size_t rec_plane = (size_t)pl->nzs * (pl->fast ? pl->fast_PR : pl->NX) * 4;
+    const size_t cells = (size_t)pl->NZ * pl->NX;
+    pl->ckpt_every = p.checkpoint_every > p.nt ? p.nt : p.checkpoint_every;
+    pl->nslot = pl->ckpt_every ? (p.nt + pl->ckpt_every - 1) / pl->ckpt_every : 0;
+    pl->ws_seg = pl->ws_astate = pl->ws_asrc = 0;
+    if (pl->ckpt_every) {
+        pl->ws_seg = o;       // one segment of the record
+        o += align_up(B * p.ns * (size_t)pl->ckpt_every * rec_plane);
+        pl->ws_astate = o;    // adjoint levels j, j-1 and imaging sums
+        o += align_up(B * p.ns * 3 * cells * 4);
+        pl->ws_asrc = o;      // source-cell imaging sums
+        o += align_up(B * p.ns * 4);
+    }
     pl->ws_bytes = o;
     o = 0;
     pl->ctx_M = o;      o += align_up(B * 4);
@@ -241,8 +256,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     pl->ctx_Qb = o;     o += align_up(B * ntr * w2->n_xi * 4);   // int bracket base
     pl->ctx_Qf = o;     o += align_up(B * ntr * w2->n_xi * 4);   // fraction in bracket
     pl->ctx_bytes = o;
-    // record planes: nzs rows of pitch fast_PR (fast kernels) or NX (generic)
-    pl->snap_bytes = B * p.ns * (size_t)p.nt * pl->nzs * (pl->fast ? pl->fast_PR : pl->NX) * 4;
+    pl->snap_bytes = pl->ckpt_every ? (size_t)pl->nslot * B * p.ns * 2 * cells * 4
+                                    : B * p.ns * (size_t)p.nt * rec_plane;
     *out = reinterpret_cast<fwi_plan *>(pl);
     return FWI_OK;
 }
@@ -277,7 +292,14 @@ fwi_status fwi_forward(const fwi_plan *plan, const float *v, float *d_syn, float
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, "fwi_forward status reset");
-    e = fwi::launch_forward(pl, v, d_syn, snapshots, status_ptr(workspace), st);
+    if (pl.ckpt_every) {
+        fwi::Window w;
+        w.ckpt = snapshots;
+        w.ckpt_every = pl.ckpt_every;
+        e = fwi::launch_forward(pl, v, d_syn, nullptr, status_ptr(workspace), st, w);
+    } else {
+        e = fwi::launch_forward(pl, v, d_syn, snapshots, status_ptr(workspace), st);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "fwi_forward launch");
     return FWI_OK;
 }
@@ -313,10 +335,41 @@ fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const float *a
         return fail(FWI_ERR_INVALID_ARG,
                     "plan, v, adj_src, snapshots, grad and workspace must not be NULL");
     const Plan &pl = *as_plan(plan);
-    float *gshot = (float *)((unsigned char *)workspace + pl.ws_gshot);
-    cudaError_t e = fwi::launch_adjoint(pl, v, adj_src, snapshots, grad, gshot,
-                                        status_ptr(workspace), (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "fwi_adjoint_grad launch");
+    unsigned char *ws = (unsigned char *)workspace;
+    float *gshot = (float *)(ws + pl.ws_gshot);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!pl.ckpt_every) {
+        cudaError_t e = fwi::launch_adjoint(pl, v, adj_src, snapshots, grad, gshot,
+                                            status_ptr(workspace), st);
+        if (e != cudaSuccess) return cuda_fail(e, "fwi_adjoint_grad launch");
+        return FWI_OK;
+    }
+    // checkpointed: segments of K forward steps, last first; each is
+    // recomputed from its checkpoint into the segment record, then run
+    // backwards with the adjoint state carried from the previous segment
+    const int K = pl.ckpt_every, nt = pl.p.nt;
+    const size_t slot = (size_t)pl.p.batch * pl.p.ns * 2 * pl.NZ * pl.NX;
+    float *seg = (float *)(ws + pl.ws_seg);
+    for (int sgi = pl.nslot - 1; sgi >= 0; --sgi) {
+        const int fb = sgi * K, fe = fb + K < nt ? fb + K : nt;
+        fwi::Window wf;
+        wf.j_begin = fb;
+        wf.j_end = fe;
+        wf.rec_base = fb;
+        wf.rec_planes = K;
+        wf.resume = sgi > 0 ? snapshots + sgi * slot : nullptr;
+        cudaError_t e = fwi::launch_forward(pl, v, nullptr, seg, status_ptr(workspace), st, wf);
+        if (e != cudaSuccess) return cuda_fail(e, "fwi_adjoint_grad recompute launch");
+        fwi::Window wa;
+        wa.j_begin = nt - fe;
+        wa.j_end = nt - fb;
+        wa.rec_base = fb;
+        wa.rec_planes = K;
+        wa.astate = (float *)(ws + pl.ws_astate);
+        wa.asrc = (float *)(ws + pl.ws_asrc);
+        e = fwi::launch_adjoint(pl, v, adj_src, seg, grad, gshot, status_ptr(workspace), st, wa);
+        if (e != cudaSuccess) return cuda_fail(e, "fwi_adjoint_grad launch");
+    }
     return FWI_OK;
 }
 

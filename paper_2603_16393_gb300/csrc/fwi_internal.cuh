@@ -55,6 +55,9 @@ struct Plan {
     size_t ws_w2, ws_gshot, ws_bytes;
     size_t ctx_M, ctx_S, ctx_cshift, ctx_str, ctx_omega, ctx_Qb, ctx_Qf, ctx_bytes;
     size_t snap_bytes;
+    // checkpoint + recompute: every ckpt_every steps (0: store-all record)
+    int ckpt_every, nslot;
+    size_t ws_seg, ws_astate, ws_asrc;    // workspace: segment record, adjoint state
 };
 
 // ---------------------------------------------------------------------------
@@ -81,6 +84,21 @@ struct PropArgs {
     const float *adj;                    // adjoint: [B][ns][nr][nt]
     float *gshot;                        // adjoint: [B][ns][nz][nx]
     int *status;
+    // Time window of this launch (checkpointed runs split the time loop):
+    // forward steps [j_begin, j_end), or adjoint steps [j_begin, j_end).
+    int j_begin, j_end;
+    // Record plane of forward step f is f - rec_base inside a block of
+    // rec_planes planes per (model, shot).
+    int rec_base, rec_planes;
+    // Forward: state to resume from at j_begin ([B*ns][2][NZ][NX]; null =
+    // start from rest), and checkpoint slots written at every multiple of
+    // ckpt_every ([nslot][B*ns][2][NZ][NX]; null = none).
+    const float *resume;
+    float *ckpt;
+    int ckpt_every;
+    // Adjoint: state carried between windows ([B*ns][3][NZ][NX]: level j,
+    // level j-1, imaging sums) and the source-cell imaging sum ([B*ns]).
+    float *astate, *asrc;
     int16_t src_pz[FWI_MAX_SHOTS], src_px[FWI_MAX_SHOTS];
     int16_t rec_pz[FWI_MAX_RECEIVERS], rec_px[FWI_MAX_RECEIVERS];
 };
@@ -95,12 +113,25 @@ __device__ __forceinline__ void set_status(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
+// One launch's share of a checkpointed run (defaults: the whole time loop,
+// records indexed by absolute step, no state carried).
+struct Window {
+    int j_begin = 0, j_end = -1;          // -1: nt
+    int rec_base = 0, rec_planes = -1;    // -1: nt
+    const float *resume = nullptr;
+    float *ckpt = nullptr;
+    int ckpt_every = 0;
+    float *astate = nullptr, *asrc = nullptr;
+};
+
 // Launchers (return cudaGetLastError() of the launches they made).
 cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *snap,
-                           int *status, cudaStream_t st);
+                           int *status, cudaStream_t st, const Window &w = Window());
+// Adjoint over one window; the gradient is folded and written to gshot when
+// the window ends at nt (and then summed over shots into grad if grad is set).
 cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj,
                            const float *snap, float *grad, float *gshot, int *status,
-                           cudaStream_t st);
+                           cudaStream_t st, const Window &w = Window());
 cudaError_t launch_w2_prepare(const Plan &pl, const float *d_obs, unsigned char *ctx,
                               cudaStream_t st);
 cudaError_t launch_w2_misfit(const Plan &pl, const unsigned char *ctx, const float *d_syn,

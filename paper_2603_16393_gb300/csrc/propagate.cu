@@ -103,23 +103,59 @@ k_propagate(const __grid_constant__ PropArgs a)
     }
 
     const size_t plane = (size_t)NZ * NX;
-    float *snap_bs = a.snap ? a.snap + (size_t)bs * a.nt * plane : nullptr;
+    float *snap_bs = a.snap ? a.snap + (size_t)bs * a.rec_planes * plane : nullptr;
     const int cell0 = z0 * NX + x;
     const float *kp = K + cell0;
+    const int jb = a.j_begin, je = a.j_end;
 
     float acc[ADJ ? MAXROWS : 1];
     float sv[ADJ ? MAXROWS : 1];
     if (ADJ) {
-        const float *s0 = snap_bs + (size_t)(a.nt - 1) * plane + cell0;
+        const float *s0 = snap_bs + (size_t)(a.nt - 1 - jb - a.rec_base) * plane + cell0;
 #pragma unroll
         for (int r = 0; r < MAXROWS; ++r) {
             acc[r] = 0.f;
             sv[r] = (r < myrows) ? s0[r * NX] : 0.f;
         }
     }
+    // resume at step jb: levels j and j-1 (the adjoint also its imaging sums)
+    const float *rs = ADJ ? (jb > 0 ? a.astate + (size_t)bs * 3 * plane : nullptr)
+                          : (a.resume ? a.resume + (size_t)bs * 2 * plane : nullptr);
+    if (rs) {
+        // flat copy of both levels (per-owner copies cost registers in the
+        // time loop), then the owner's imaging sums
+        float *cur = (jb & 1) ? F1 : F0, *old = (jb & 1) ? F0 : F1;
+        for (int i = tid; i < NZ * NX; i += nth) {
+            const int z = i / NX, xx = i - (i / NX) * NX;
+            cur[(z + 2) * P + xx + 2] = rs[i];
+            old[(z + 2) * P + xx + 2] = rs[plane + i];
+            if (!ADJ && TOPBC == 1 && (z == 1 || z == 2))
+                cur[(2 - z) * P + xx + 2] = rs[i];   // mirrored ghost row -z
+        }
+        if (ADJ) {
+#pragma unroll
+            for (int r = 0; r < MAXROWS; ++r)
+                if (r < myrows) acc[r] = rs[2 * plane + (z0 + r) * NX + x];
+        }
+    }
+    __syncthreads();
 
-    for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
-        const int nch = min(a.chunk, a.nt - j0);
+    for (int j0 = jb, nch = 0; j0 < je; j0 += nch) {
+        nch = min(a.chunk, je - j0);
+        if (!ADJ && a.ckpt) {
+            // chunks end at checkpoint steps; the state at the first step of
+            // a chunk that is one is saved here (both levels, flat copy)
+            nch = min(nch, (j0 / a.ckpt_every + 1) * a.ckpt_every - j0);
+            if (j0 % a.ckpt_every == 0) {
+                const float *cur = (j0 & 1) ? F1 : F0, *old = (j0 & 1) ? F0 : F1;
+                float *cs = a.ckpt + ((size_t)(j0 / a.ckpt_every) * gridDim.x + bs) * 2 * plane;
+                for (int i = tid; i < NZ * NX; i += nth) {
+                    const int z = i / NX, xx = i - (i / NX) * NX;
+                    cs[i] = cur[(z + 2) * P + xx + 2];
+                    cs[plane + i] = old[(z + 2) * P + xx + 2];
+                }
+            }
+        }
         if (ADJ) {
             const float *ab = a.adj + (size_t)bs * a.nr * a.nt;
             for (int e = tid; e < nch * a.nr; e += nth) {
@@ -149,9 +185,11 @@ k_propagate(const __grid_constant__ PropArgs a)
                 const float *cp = cur + (z0 + 2) * P + x + 2;
                 float *op = old + (z0 + 2) * P + x + 2;
                 float *row0 = old + 2 * P + x + 2;
-                float *snap_w = (!ADJ && snap_bs) ? snap_bs + (size_t)j * plane + cell0 : nullptr;
-                const bool pf = ADJ && (j + 1 < a.nt);
-                const float *snap_r = pf ? snap_bs + (size_t)(a.nt - 2 - j) * plane + cell0 : nullptr;
+                float *snap_w = (!ADJ && snap_bs)
+                                    ? snap_bs + (size_t)(j - a.rec_base) * plane + cell0 : nullptr;
+                const bool pf = ADJ && (j + 1 < je);
+                const float *snap_r =
+                    pf ? snap_bs + (size_t)(a.nt - 2 - j - a.rec_base) * plane + cell0 : nullptr;
                 float wm2 = cp[-2 * P], wm1 = cp[-P], w0 = cp[0], wp1 = cp[P];
 #pragma unroll
                 for (int r = 0; r < MAXROWS; ++r) {
@@ -198,13 +236,31 @@ k_propagate(const __grid_constant__ PropArgs a)
         }
         if (!ADJ) {
             __syncthreads();
-            float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
-            for (int e = tid; e < nch * a.nr; e += nth) {
-                const int i = e / nch, jj = e - (e / nch) * nch;
-                db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+            if (a.d_syn) {
+                float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
+                for (int e = tid; e < nch * a.nr; e += nth) {
+                    const int i = e / nch, jj = e - (e / nch) * nch;
+                    db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+                }
             }
             __syncthreads();
         }
+    }
+
+    if (ADJ && je < a.nt) {
+        // suspend: levels psi^je, psi^(je-1) and the imaging sums
+        __syncthreads();
+        float *st = a.astate + (size_t)bs * 3 * plane;
+        const float *cur = (je & 1) ? F1 : F0, *old = (je & 1) ? F0 : F1;
+        for (int i = tid; i < NZ * NX; i += nth) {
+            const int z = i / NX, xx = i - (i / NX) * NX;
+            st[i] = cur[(z + 2) * P + xx + 2];
+            st[plane + i] = old[(z + 2) * P + xx + 2];
+        }
+#pragma unroll
+        for (int r = 0; r < MAXROWS; ++r)
+            if (r < myrows) st[2 * plane + (z0 + r) * NX + x] = acc[r];
+        return;
     }
 
     if (ADJ) {
@@ -367,14 +423,32 @@ bool choose_resident_shape(int NZ, int NX, int nr, bool adj, ResidentShape *out)
     return true;
 }
 
+namespace {
+
+void apply_window(PropArgs &a, const Window &w)
+{
+    a.j_begin = w.j_begin;
+    a.j_end = w.j_end < 0 ? a.nt : w.j_end;
+    a.rec_base = w.rec_base;
+    a.rec_planes = w.rec_planes < 0 ? a.nt : w.rec_planes;
+    a.resume = w.resume;
+    a.ckpt = w.ckpt;
+    a.ckpt_every = w.ckpt_every;
+    a.astate = w.astate;
+    a.asrc = w.asrc;
+}
+
+}  // namespace
+
 cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *snap,
-                           int *status, cudaStream_t st)
+                           int *status, cudaStream_t st, const Window &w)
 {
     PropArgs a = make_args(pl);
     a.v = v;
     a.d_syn = d_syn;
     a.snap = snap;
     a.status = status;
+    apply_window(a, w);
     if (pl.fast) {
         a.rows = pl.shape.rows;
         a.nstrip = pl.shape.nstrip;
@@ -385,7 +459,8 @@ cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *
 }
 
 cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj, const float *snap,
-                           float *grad, float *gshot, int *status, cudaStream_t st)
+                           float *grad, float *gshot, int *status, cudaStream_t st,
+                           const Window &w)
 {
     PropArgs a = make_args(pl);
     a.v = v;
@@ -393,6 +468,7 @@ cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj, con
     a.snap = const_cast<float *>(snap);
     a.gshot = gshot;
     a.status = status;
+    apply_window(a, w);
     cudaError_t e;
     if (pl.fast) {
         a.rows = pl.shape_adj.rows;
@@ -403,6 +479,7 @@ cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj, con
         e = dispatch<true>(a, pl, st);
     }
     if (e != cudaSuccess) return e;
+    if (a.j_end < a.nt || !grad) return cudaSuccess;
     const int n = pl.p.nz * pl.p.nx;
     dim3 grid((n + 255) / 256, pl.p.batch);
     k_shot_sum<<<grid, 256, 0, st>>>(pl.p.batch, pl.p.ns, n, gshot, grad);

@@ -175,10 +175,53 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
         if (r == src_row) ka_src = ka[r];
 
     const size_t plane = (size_t)a.nzs * PR;   // record planes use the pitch PR
-    float *snap_bs = STORE ? a.snap + (size_t)bs * a.nt * plane : nullptr;
+    float *snap_bs = STORE ? a.snap + (size_t)bs * a.rec_planes * plane : nullptr;
+    const int jb = a.j_begin;
+    if (a.resume) {
+        // state at step jb: field u^jb (a flat copy, with the mirrored ghost
+        // rows -1, -2) and the owner's increments v^(jb-1/2)
+        const size_t cells = (size_t)NZ * NX;
+        const float *st = a.resume + (size_t)bs * 2 * cells;
+        float *cur = (jb & 1) ? U1 : U0;
+        for (int i = tid; i < NZ * NX; i += nth) {
+            const int z = i / NX, xx = i - (i / NX) * NX;
+            const float u = st[i];
+            cur[(z + 2) * P + xx + 2] = u;
+            if (TOPBC == 1 && (z == 1 || z == 2)) cur[(2 - z) * P + xx + 2] = u;
+        }
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const int z = z0 + r;
+                if (z < NZ) vi[r] = st[cells + z * NX + x];
+            }
+        }
+        __syncthreads();
+    }
 
-    for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
-        const int nch = min(a.chunk, a.nt - j0);
+    for (int j0 = jb, nch = 0; j0 < a.j_end; j0 += nch) {
+        nch = min(a.chunk, a.j_end - j0);
+        if (a.ckpt) {
+            // chunks end at checkpoint steps; the state at the first step of
+            // a chunk that is one is saved here
+            nch = min(nch, (j0 / a.ckpt_every + 1) * a.ckpt_every - j0);
+            if (j0 % a.ckpt_every == 0) {
+                const float *cur = (j0 & 1) ? U1 : U0;
+                const size_t cl = (size_t)NZ * NX;
+                float *st = a.ckpt + ((size_t)(j0 / a.ckpt_every) * gridDim.x + bs) * 2 * cl;
+                for (int i = tid; i < NZ * NX; i += nth) {
+                    const int z = i / NX, xx = i - (i / NX) * NX;
+                    st[i] = cur[(z + 2) * P + xx + 2];
+                }
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) {
+                        const int z = z0 + r;
+                        if (z < NZ) st[cl + z * NX + x] = vi[r];
+                    }
+                }
+            }
+        }
         for (int jj = 0; jj < nch; ++jj) {
             const int j = j0 + jj;
             const float *cur = (j & 1) ? U1 : U0;
@@ -186,7 +229,8 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
             if (active) {
                 const float *cp = cur + (z0 + 2) * P + x + 2;
                 float *np = nxt + (z0 + 2) * P + x + 2;
-                float *sw = STORE ? snap_bs + (size_t)j * plane + z0 * PR + x : nullptr;
+                float *sw = STORE ? snap_bs + (size_t)(j - a.rec_base) * plane + z0 * PR + x
+                                  : nullptr;
                 fwd_rows<P, PR, TOPBC, STORE>(cp, np, ABt + z0 * P + x, sw, NX, top_strip, ka, vi, a);
                 if (src_row >= 0) {
                     // point source: + kappa A s at the source cell (increment and field)
@@ -203,10 +247,12 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
             if (tid < a.nr) ST[jj * a.nr + tid] = nxt[(a.rec_pz[tid] + 2) * P + a.rec_px[tid] + 2];
         }
         __syncthreads();
-        float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
-        for (int e = tid; e < nch * a.nr; e += nth) {
-            const int i = e / nch, jj = e - (e / nch) * nch;
-            db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+        if (a.d_syn) {
+            float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
+            for (int e = tid; e < nch * a.nr; e += nth) {
+                const int i = e / nch, jj = e - (e / nch) * nch;
+                db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+            }
         }
         __syncthreads();
     }
@@ -316,11 +362,61 @@ k_fwd_pair(const __grid_constant__ PropArgs a)
     const int sz = a.src_pz[s], sx = a.src_px[s];
     const int src_k = (active && (sx >> 1) == xp && sz >= z0 && sz < z0 + ROWS2)
                           ? 2 * (sz - z0) + (sx & 1) : -1;
+    const int jb = a.j_begin;
     // record plane of the current step (advanced by one plane per step)
-    float *sw = STORE ? a.snap + (size_t)bs * a.nt * a.nzs * PR + z0 * PR + x : nullptr;
+    float *sw = STORE ? a.snap + ((size_t)bs * a.rec_planes + (jb - a.rec_base)) * a.nzs * PR +
+                            z0 * PR + x
+                      : nullptr;
+    if (a.resume) {
+        // state at step jb: field u^jb and increment v^(jb-1/2)
+        const size_t cells = (size_t)NZ * NX;
+        const float *st = a.resume + (size_t)bs * 2 * cells;
+        float *cur = (jb & 1) ? U1 : U0;
+        for (int i = tid; i < NZ * NX; i += nth) {   // flat copy of u^jb
+            const int z = i / NX, xx = i - (i / NX) * NX;
+            const float u = st[i];
+            cur[(z + 2) * P + xx + 2] = u;
+            if (TOPBC == 1 && (z == 1 || z == 2)) cur[(2 - z) * P + xx + 2] = u;
+        }
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < ROWS2; ++r) {
+                const int z = z0 + r;
+                if (z < NZ) {
+                    const float2 w = *(const float2 *)(st + cells + z * NX + x);
+                    vi[2 * r] = w.x;
+                    vi[2 * r + 1] = w.y;
+                }
+            }
+        }
+        __syncthreads();
+    }
 
-    for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
-        const int nch = min(a.chunk, a.nt - j0);
+    for (int j0 = jb, nch = 0; j0 < a.j_end; j0 += nch) {
+        nch = min(a.chunk, a.j_end - j0);
+        if (a.ckpt) {
+            // chunks end at checkpoint steps; the state at the first step of
+            // a chunk that is one is saved here
+            nch = min(nch, (j0 / a.ckpt_every + 1) * a.ckpt_every - j0);
+            if (j0 % a.ckpt_every == 0) {
+                const float *cur = (j0 & 1) ? U1 : U0;
+                const size_t cl = (size_t)NZ * NX;
+                float *st = a.ckpt + ((size_t)(j0 / a.ckpt_every) * gridDim.x + bs) * 2 * cl;
+                for (int i = tid; i < NZ * NX; i += nth) {
+                    const int z = i / NX, xx = i - (i / NX) * NX;
+                    st[i] = cur[(z + 2) * P + xx + 2];
+                }
+                if (active) {
+#pragma unroll
+                    for (int r = 0; r < ROWS2; ++r) {
+                        const int z = z0 + r;
+                        if (z < NZ)
+                            *(float2 *)(st + cl + z * NX + x) =
+                                make_float2(vi[2 * r], vi[2 * r + 1]);
+                    }
+                }
+            }
+        }
         for (int jj = 0; jj < nch; ++jj) {
             const int j = j0 + jj;
             const float *cur = (j & 1) ? U1 : U0;
@@ -350,10 +446,12 @@ k_fwd_pair(const __grid_constant__ PropArgs a)
             if (tid < a.nr) ST[jj * a.nr + tid] = nxt[(a.rec_pz[tid] + 2) * P + a.rec_px[tid] + 2];
         }
         __syncthreads();
-        float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
-        for (int e = tid; e < nch * a.nr; e += nth) {
-            const int i = e / nch, jj = e - (e / nch) * nch;
-            db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+        if (a.d_syn) {
+            float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
+            for (int e = tid; e < nch * a.nr; e += nth) {
+                const int i = e / nch, jj = e - (e / nch) * nch;
+                db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+            }
         }
         __syncthreads();
     }
@@ -466,17 +564,42 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
     if (tid == 0) acc_src = 0.f;
 
     const size_t plane = (size_t)a.nzs * PR;   // record planes use the pitch PR
+    const int jb = a.j_begin;
     float acc[ROWS], sv[ROWS];
-    // record plane read next: starts at plane nt-1, moves back one plane per step
-    const float *sr = a.snap + ((size_t)bs * a.nt + (a.nt - 1)) * plane + z0 * PR + x;
+    // record plane read next: starts at forward step nt-1-jb, moves back one
+    // plane per step
+    const float *sr = a.snap +
+                      ((size_t)bs * a.rec_planes + (a.nt - 1 - jb - a.rec_base)) * plane +
+                      z0 * PR + x;
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
         acc[r] = 0.f;
         sv[r] = sr[r * PR];
     }
+    if (jb > 0) {
+        // resume: levels psi^jb, psi^(jb-1) (a flat copy: per-owner copies
+        // of the levels cost registers in the time loop) and the imaging sums
+        const size_t cells = (size_t)NZ * NX;
+        const float *st = a.astate + (size_t)bs * 3 * cells;
+        float *cur = (jb & 1) ? U1 : U0, *old = (jb & 1) ? U0 : U1;
+        for (int i = tid; i < NZ * NX; i += nth) {
+            const int z = i / NX, xx = i - (i / NX) * NX;
+            cur[(z + 2) * P + xx + 2] = st[i];
+            old[(z + 2) * P + xx + 2] = st[cells + i];
+        }
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const int z = z0 + r;
+                if (z < NZ) acc[r] = st[2 * cells + z * NX + x];
+            }
+        }
+        if (tid == 0) acc_src = a.asrc[bs];
+    }
+    __syncthreads();
 
-    for (int j0 = 0; j0 < a.nt; j0 += a.chunk) {
-        const int nch = min(a.chunk, a.nt - j0);
+    for (int j0 = jb; j0 < a.j_end; j0 += a.chunk) {
+        const int nch = min(a.chunk, a.j_end - j0);
         const float *ab = a.adj + (size_t)bs * a.nr * a.nt;
         for (int e = tid; e < nch * a.nr; e += nth) {
             const int i = e / nch, jj = e - (e / nch) * nch;
@@ -491,7 +614,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
                 const int rz = a.rec_pz[inj_slot], rx = a.rec_px[inj_slot];
                 nxt[(rz + 2) * P + rx + 2] -= IC[inj_slot] * ST[jj * a.nr + inj_slot];
             }
-            if (j + 1 < a.nt) sr -= plane;
+            if (j + 1 < a.j_end) sr -= plane;
             const float *cp = cur + (z0 + 2) * P + x + 2;
             float *np = nxt + (z0 + 2) * P + x + 2;
             const float *kp = K + z0 * P + x;
@@ -505,9 +628,31 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
         }
     }
 
+    __syncthreads();
+    if (a.j_end < a.nt) {
+        // suspend: levels psi^je, psi^(je-1) and the imaging sums
+        const int je = a.j_end;
+        const size_t cells = (size_t)NZ * NX;
+        float *st = a.astate + (size_t)blockIdx.x * 3 * cells;
+        const float *cur = (je & 1) ? U1 : U0, *old = (je & 1) ? U0 : U1;
+        for (int i = tid; i < NZ * NX; i += nth) {
+            const int z = i / NX, xx = i - (i / NX) * NX;
+            st[i] = cur[(z + 2) * P + xx + 2];
+            st[cells + i] = old[(z + 2) * P + xx + 2];
+        }
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                const int z = z0 + r;
+                if (z < NZ) st[2 * cells + z * NX + x] = acc[r];
+            }
+        }
+        if (tid == 0) a.asrc[bs] = acc_src;
+        return;
+    }
+
     // dJ/dv_pad = 2 acc / v_pad, fold of the absorbing layer onto the edge
     // cells (transpose of the edge replication), then per-shot gradient
-    __syncthreads();
     float *G = U0;   // [NZ][NX]
     float *T = U1;   // [NZ][nx]
     if (active) {

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(api):
     lib = ctypes.CDLL(LIB)
     for n in declared_functions():
         assert hasattr(lib, n), n
-    assert api.fwi_version() == 10000
+    assert api.fwi_version() == 10100
 
 
 def _prob(api, **kw):
@@ -59,6 +59,26 @@ def test_plan_sizes_of_the_benchmark_problem(api):
     assert ctx >= B * ns * nr * (nt * 4 + 1000 * 8)
 
 
+@pytest.mark.parametrize("K", [32, 7, 1, 1000, 5000])
+def test_plan_sizes_with_checkpoints(api, K):
+    # checkpoint_every = K: ceil(nt/K) slots of two padded grids per (model,
+    # shot) instead of nt record planes; the workspace gains one K-plane
+    # segment of the record, the adjoint state (three grids) and one float
+    B, ns, nt, NZ, NX = 3, 5, 1000, 110, 150
+    h0 = api.fwi_plan_create(_prob(api), api.W2Params())
+    ws0, ctx0, snap0 = api.fwi_plan_sizes(h0)
+    h = api.fwi_plan_create(_prob(api, checkpoint_every=K), api.W2Params())
+    ws, ctx, snap = api.fwi_plan_sizes(h)
+    Ke = min(K, nt)
+    assert snap == -(-nt // Ke) * B * ns * 2 * NZ * NX * 4
+    assert ctx == ctx0
+    seg = B * ns * Ke * NZ * 160 * 4
+    state = B * ns * 3 * NZ * NX * 4 + B * ns * 4
+    assert seg + state <= ws - ws0 <= seg + state + 3 * 256
+    if K == 32:
+        assert snap0 / snap > 16     # K/2 x (record pitch 160 / 150)
+
+
 @pytest.mark.parametrize("kw,code", [
     (dict(v_max=9000.0), 2),                 # CFL: 9000*1e-3*sqrt(2)/10 = 1.27 > 0.866
     (dict(dt=2e-3, v_max=4500.0), 2),        # 0.636*2 = 1.27
@@ -69,6 +89,7 @@ def test_plan_sizes_of_the_benchmark_problem(api):
     (dict(rec_iz=(0, 70), rec_ix=(1, 2)), 1),
     (dict(batch=0), 1),
     (dict(top_bc=2), 1),
+    (dict(checkpoint_every=-1), 1),
     (dict(refl_R=0.0), 1),
     (dict(nx=1200), 3),                      # does not fit the resident kernel
     (dict(rec_iz=(0, 1), rec_ix=(5, 5)), 3),  # two receivers in one column strip

@@ -38,7 +38,6 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 const Plan *as_plan(const fwi_plan *p) { return reinterpret_cast<const Plan *>(p); }
 
-int *status_ptr(void *ws) { return reinterpret_cast<int *>(ws); }
 
 }  // namespace
 
@@ -98,8 +97,9 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
                     "v_max dt sqrt(1/dx^2 + 1/dz^2) = %.4f exceeds sqrt(3)/2 = 0.8660", cfl);
 
     Plan *pl = new (std::nothrow) Plan();
-    if (pl) pl->fwd_pair = false;
     if (!pl) return fail(FWI_ERR_INVALID_ARG, "out of host memory");
+    pl->fwd_pair = false;
+    pl->tiled = false;
     pl->p = p;
     pl->w2 = *w2;
     pl->NZ = p.nz + p.nb;
@@ -180,15 +180,22 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         }
     }
     if (!pl->fast) {
+        pl->nzs = pl->NZ;
         if (!fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, false, &pl->shape) ||
             !fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, true, &pl->shape_adj)) {
-            delete pl;
-            return fail(FWI_ERR_UNSUPPORTED,
-                        "padded grid %dx%d does not fit the shared-memory resident propagator",
-                        pl->NZ, pl->NX);
+            // beyond one CTA's shared memory: global-memory tiled kernels
+            // (one launch per step; grid z = models x shots)
+            if ((long long)p.batch * p.ns > 65535) {
+                delete pl;
+                return fail(FWI_ERR_UNSUPPORTED,
+                            "batch x ns = %lld exceeds 65535 for the tiled propagator",
+                            (long long)p.batch * p.ns);
+            }
+            pl->tiled = true;
         }
-        pl->nzs = pl->NZ;
     }
+    pl->NXp = (pl->NX + 3) / 4 * 4;
+    pl->rec_pitch = pl->fast ? pl->fast_PR : (pl->tiled ? pl->NXp : pl->NX);
     // the adjoint source of a receiver enters through the level psi^{j-1}
     // scaled by 1/B, B = 1 - eta dt/2 of the receiver cell
     {
@@ -209,9 +216,9 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
             }
         }
     }
-    // the adjoint injects each receiver from the thread that owns its cell:
-    // receivers must sit in distinct column strips
-    for (int i = 0; i < p.nr; ++i)
+    // the resident adjoint injects each receiver from the thread that owns
+    // its cell: receivers must sit in distinct column strips
+    for (int i = 0; i < (pl->tiled ? 0 : p.nr); ++i)
         for (int k = 0; k < i; ++k)
             if (pl->rec_px[i] == pl->rec_px[k] &&
                 pl->rec_pz[i] / pl->shape_adj.rows == pl->rec_pz[k] / pl->shape_adj.rows) {
@@ -232,8 +239,9 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     o += align_up(B * ntr * 4);
     pl->ws_gshot = o;
     o += align_up(B * p.ns * (size_t)p.nz * p.nx * 4);
-    // record planes: nzs rows of pitch fast_PR (fast kernels) or NX (generic)
-    const size_t rec_plane = (size_t)pl->nzs * (pl->fast ? pl->fast_PR : pl->NX) * 4;
+    // record planes: nzs rows of pitch fast_PR (fast kernels), NX (generic)
+    // or NXp (tiled)
+    const size_t rec_plane = (size_t)pl->nzs * pl->rec_pitch * 4;
     const size_t cells = (size_t)pl->NZ * pl->NX;
     pl->ckpt_every = p.checkpoint_every > p.nt ? p.nt : p.checkpoint_every;
     pl->nslot = pl->ckpt_every ? (p.nt + pl->ckpt_every - 1) / pl->ckpt_every : 0;
@@ -241,10 +249,30 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (pl->ckpt_every) {
         pl->ws_seg = o;       // one segment of the record
         o += align_up(B * p.ns * (size_t)pl->ckpt_every * rec_plane);
-        pl->ws_astate = o;    // adjoint levels j, j-1 and imaging sums
-        o += align_up(B * p.ns * 3 * cells * 4);
-        pl->ws_asrc = o;      // source-cell imaging sums
-        o += align_up(B * p.ns * 4);
+        if (!pl->tiled) {     // (the tiled adjoint keeps its state in its own fields)
+            pl->ws_astate = o;    // adjoint levels j, j-1 and imaging sums
+            o += align_up(B * p.ns * 3 * cells * 4);
+            pl->ws_asrc = o;      // source-cell imaging sums
+            o += align_up(B * p.ns * 4);
+        }
+    }
+    pl->ws_t_u0 = pl->ws_t_u1 = pl->ws_t_v = pl->ws_t_p0 = pl->ws_t_p1 = pl->ws_t_acc = 0;
+    pl->ws_t_ka = pl->ws_t_ab = pl->ws_t_ic = pl->ws_t_accsrc = pl->ws_t_rec = pl->ws_t_src = 0;
+    if (pl->tiled) {
+        const size_t field = align_up(B * p.ns * (size_t)pl->NZ * pl->NXp * 4);
+        const size_t table = align_up(B * (size_t)pl->NZ * pl->NXp * 4);
+        pl->ws_t_u0 = o;  o += field;
+        pl->ws_t_u1 = o;  o += field;
+        pl->ws_t_v = o;   o += field;
+        pl->ws_t_p0 = o;  o += field;
+        pl->ws_t_p1 = o;  o += field;
+        pl->ws_t_acc = o; o += field;
+        pl->ws_t_ka = o;  o += table;
+        pl->ws_t_ab = o;  o += table;
+        pl->ws_t_ic = o;  o += align_up(B * p.nr * 4);
+        pl->ws_t_accsrc = o; o += align_up(B * p.ns * 4);
+        pl->ws_t_rec = o; o += align_up((size_t)p.nr * 4);
+        pl->ws_t_src = o; o += align_up((size_t)p.ns * 4);
     }
     pl->ws_bytes = o;
     o = 0;
@@ -296,9 +324,9 @@ fwi_status fwi_forward(const fwi_plan *plan, const float *v, float *d_syn, float
         fwi::Window w;
         w.ckpt = snapshots;
         w.ckpt_every = pl.ckpt_every;
-        e = fwi::launch_forward(pl, v, d_syn, nullptr, status_ptr(workspace), st, w);
+        e = fwi::launch_forward(pl, v, d_syn, nullptr, workspace, st, w);
     } else {
-        e = fwi::launch_forward(pl, v, d_syn, snapshots, status_ptr(workspace), st);
+        e = fwi::launch_forward(pl, v, d_syn, snapshots, workspace, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "fwi_forward launch");
     return FWI_OK;
@@ -339,8 +367,7 @@ fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const float *a
     float *gshot = (float *)(ws + pl.ws_gshot);
     cudaStream_t st = (cudaStream_t)stream;
     if (!pl.ckpt_every) {
-        cudaError_t e = fwi::launch_adjoint(pl, v, adj_src, snapshots, grad, gshot,
-                                            status_ptr(workspace), st);
+        cudaError_t e = fwi::launch_adjoint(pl, v, adj_src, snapshots, grad, gshot, workspace, st);
         if (e != cudaSuccess) return cuda_fail(e, "fwi_adjoint_grad launch");
         return FWI_OK;
     }
@@ -358,7 +385,7 @@ fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const float *a
         wf.rec_base = fb;
         wf.rec_planes = K;
         wf.resume = sgi > 0 ? snapshots + sgi * slot : nullptr;
-        cudaError_t e = fwi::launch_forward(pl, v, nullptr, seg, status_ptr(workspace), st, wf);
+        cudaError_t e = fwi::launch_forward(pl, v, nullptr, seg, workspace, st, wf);
         if (e != cudaSuccess) return cuda_fail(e, "fwi_adjoint_grad recompute launch");
         fwi::Window wa;
         wa.j_begin = nt - fe;
@@ -367,7 +394,7 @@ fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const float *a
         wa.rec_planes = K;
         wa.astate = (float *)(ws + pl.ws_astate);
         wa.asrc = (float *)(ws + pl.ws_asrc);
-        e = fwi::launch_adjoint(pl, v, adj_src, seg, grad, gshot, status_ptr(workspace), st, wa);
+        e = fwi::launch_adjoint(pl, v, adj_src, seg, grad, gshot, workspace, st, wa);
         if (e != cudaSuccess) return cuda_fail(e, "fwi_adjoint_grad launch");
     }
     return FWI_OK;

@@ -48,6 +48,9 @@ struct Plan {
     ResidentShape shape;       // forward propagator
     ResidentShape shape_adj;   // adjoint propagator
     bool fast;                 // compile-time pitch kernels (else the generic ones)
+    bool tiled;                // global-memory tiled kernels (grids beyond shared memory)
+    int NXp;                   // tiled: row pitch of the fields (NX rounded up to 4)
+    int rec_pitch;             // row pitch of a record plane
     bool fwd_pair;             // forward on column pairs (even padded width)
     int fast_P, fast_PR, fast_NZM;  // their shared-memory pitch, record pitch, row capacity
     int nzs;                   // rows of one wavefield-record plane (>= NZ)
@@ -58,6 +61,9 @@ struct Plan {
     // checkpoint + recompute: every ckpt_every steps (0: store-all record)
     int ckpt_every, nslot;
     size_t ws_seg, ws_astate, ws_asrc;    // workspace: segment record, adjoint state
+    // tiled path: fields, adjoint levels and sums, per-model tables
+    size_t ws_t_u0, ws_t_u1, ws_t_v, ws_t_p0, ws_t_p1, ws_t_acc, ws_t_ka, ws_t_ab, ws_t_ic,
+        ws_t_accsrc, ws_t_rec, ws_t_src;
 };
 
 // ---------------------------------------------------------------------------
@@ -125,12 +131,13 @@ struct Window {
 };
 
 // Launchers (return cudaGetLastError() of the launches they made).
+// `workspace` is the caller's workspace (status word at its start).
 cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *snap,
-                           int *status, cudaStream_t st, const Window &w = Window());
+                           void *workspace, cudaStream_t st, const Window &w = Window());
 // Adjoint over one window; the gradient is folded and written to gshot when
 // the window ends at nt (and then summed over shots into grad if grad is set).
 cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj,
-                           const float *snap, float *grad, float *gshot, int *status,
+                           const float *snap, float *grad, float *gshot, void *workspace,
                            cudaStream_t st, const Window &w = Window());
 cudaError_t launch_w2_prepare(const Plan &pl, const float *d_obs, unsigned char *ctx,
                               cudaStream_t st);
@@ -151,5 +158,8 @@ bool fast_bucket(int NZ, int NX, int *P, int *PR, int *NZM);
 size_t fast_smem(int P, int NZM, bool adj, int chunk, int nr);
 bool fwd_pair_ok(int NX, int NZ, int NZM);
 cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st);
+// Tiled propagators: one launch per step over [a.j_begin, a.j_end)
+cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
+                         cudaStream_t st);
 
 }  // namespace fwi

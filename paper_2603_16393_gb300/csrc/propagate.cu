@@ -441,14 +441,15 @@ void apply_window(PropArgs &a, const Window &w)
 }  // namespace
 
 cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *snap,
-                           int *status, cudaStream_t st, const Window &w)
+                           void *workspace, cudaStream_t st, const Window &w)
 {
     PropArgs a = make_args(pl);
     a.v = v;
     a.d_syn = d_syn;
     a.snap = snap;
-    a.status = status;
+    a.status = static_cast<int *>(workspace);
     apply_window(a, w);
+    if (pl.tiled) return launch_tiled(pl, false, a, static_cast<unsigned char *>(workspace), st);
     if (pl.fast) {
         a.rows = pl.shape.rows;
         a.nstrip = pl.shape.nstrip;
@@ -459,7 +460,7 @@ cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *
 }
 
 cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj, const float *snap,
-                           float *grad, float *gshot, int *status, cudaStream_t st,
+                           float *grad, float *gshot, void *workspace, cudaStream_t st,
                            const Window &w)
 {
     PropArgs a = make_args(pl);
@@ -467,10 +468,12 @@ cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj, con
     a.adj = adj;
     a.snap = const_cast<float *>(snap);
     a.gshot = gshot;
-    a.status = status;
+    a.status = static_cast<int *>(workspace);
     apply_window(a, w);
     cudaError_t e;
-    if (pl.fast) {
+    if (pl.tiled) {
+        e = launch_tiled(pl, true, a, static_cast<unsigned char *>(workspace), st);
+    } else if (pl.fast) {
         a.rows = pl.shape_adj.rows;
         a.nstrip = pl.shape_adj.nstrip;
         a.chunk = pl.shape_adj.chunk;

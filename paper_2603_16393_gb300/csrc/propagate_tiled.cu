@@ -1,0 +1,593 @@
+// propagate_tiled.cu -- propagators for padded grids larger than one CTA's
+// shared memory (for example 256 x 256 or 512 x 1024 models with a 40-cell
+// absorbing layer), same recurrences as the shared-memory resident kernels:
+//
+//   forward  v^{j+1/2} = A B v^{j-1/2} + kappa A (L u^j + s^j),  u^{j+1} = u^j + v^{j+1/2}
+//            (Eq. 1 in increment form, Laplacian on neighbour differences)
+//   adjoint  psi^{j+1} = 2A psi^j - A B psi^{j-1} + kappa A L^T psi^j, receivers'
+//            adjoint source through the old level, imaging
+//            dJ/dv_pad = (2 / v_pad) sum_j psi^{j+1} t^{nt-1-j}
+//
+// The fields of every (model, shot) live in global memory, [bs][NZ][NXp]
+// with NXp = NX rounded up to a multiple of 4 (16-byte rows; the pad columns
+// stay zero).  One launch advances all (model, shot) pairs by one time step.
+// A CTA owns a 32 x 64 tile: thread (tx, g) owns column x0 + tx and rows
+// z0 + 8g .. z0 + 8g + 7 and keeps a z window in registers.  The current
+// level's halo tile (36 x 72 cells; it starts at x0 - 4 so that the copy
+// starts on a 16-byte boundary) is moved into shared memory by one
+// cp.async.bulk.tensor load completing on an mbarrier; the tensor's
+// out-of-bounds fill supplies the zero ghosts around the padded grid (the
+// mirrored top rows are copied in after the load).  The per-cell operands
+// that have no halo (increment or old level, coefficients, record, imaging
+// sums) are read with coalesced loads while the copy is in flight.
+//
+// Data samples: the launch of step j records d[:, j-1] = u^j from its tile;
+// a final gather records d[:, nt-1].
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "fwi_device.cuh"
+#include "fwi_internal.cuh"
+
+namespace fwi {
+
+namespace {
+
+constexpr int TX = 64, TZ = 32, TROWS = 8, TTHREADS = 256;
+constexpr int HX = TX + 8, HZ = TZ + 4;              // halo tile (x from x0 - 4, z from z0 - 2)
+constexpr unsigned kTileBytes = HX * HZ * sizeof(float);
+constexpr long kWaitLimit = 1L << 22;                 // mbarrier polls before giving up
+
+// Compact per-launch arguments (one launch per time step).
+struct TileArgs {
+    int nz, nx, nb, NZ, NX, NXp, nt, ns, nr;
+    int j;                      // time step of this launch
+    int rec_base;               // record plane of forward step f is f - rec_base
+    long long rec_planes;       // record planes per (model, shot)
+    int ckpt_every;
+    int rzmin, rzmax;           // rows that hold receivers
+    double dtd, t0d, ex0d, ez0d;
+    float c0, cx1, cx2, cz1, cz2, ex0, ez0, inv_nb, fp, src_scale;
+    const float *ka, *ab;       // [B][NZ][NXp]: kappa A, A B
+    const float *ic;            // [B][nr]: kappa / B at the receivers
+    const int *rec;             // [nr]: pz << 16 | px
+    const int *src;             // [ns]: pz << 16 | px
+    // forward
+    float *unext, *vinc;        // u^{j+1} (written), increment (in place)
+    float *rec_out;             // record [bs][rec_planes][NZ][NXp], null: off
+    float *d_syn;               // [bs][nr][nt], null: off
+    float *ckpt;                // checkpoint slots [slot][bs][2][NZ][NX], null: off
+    // adjoint
+    float *pold;                // psi^{j-1}, overwritten with psi^{j+1}
+    float *acc, *acc_src;       // imaging sums [bs][NZ][NXp], source-cell sums [bs]
+    const float *adj;           // adjoint source [bs][nr][nt]
+    const float *rec_in;        // record read by the adjoint
+    int *status;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// Starts the halo-tile copy (one thread) after arming the mbarrier.
+__device__ __forceinline__ void tile_load(float *tile, uint64_t *mbar, const CUtensorMap *tm,
+                                         int x, int z, int bs)
+{
+    const unsigned mb = smem_u32(mbar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
+                 "r"(kTileBytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(tile)),
+        "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(z), "r"(bs), "r"(mb)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *mbar)
+{
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(mbar))
+        : "memory");
+    return done != 0;
+}
+
+// Every thread waits for the tile (bounded).  Returns false for the whole
+// CTA if the copy did not land in time: the status word then holds
+// FWI_ERR_DEVICE_TIMEOUT, and the CTA waits once more (bounded) so that no
+// copy is left writing into its shared memory when it exits.
+__device__ __forceinline__ bool tile_wait(uint64_t *mbar, int *status)
+{
+    bool done = false;
+    for (long it = 0; it < kWaitLimit && !done; ++it) done = mbar_try(mbar);
+    if (__syncthreads_and(done)) return true;
+    if (threadIdx.x == 0) set_status(status, FWI_ERR_DEVICE_TIMEOUT);
+    for (long it = 0; it < kWaitLimit && !done; ++it) done = mbar_try(mbar);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *mbar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ set-up
+// Per-model tables (kappa A, A B, kappa / B at the receivers) formed in
+// double exactly as the resident kernels form them, the receiver and source
+// tables, and the velocity check.
+__global__ void __launch_bounds__(256) k_tile_setup(const __grid_constant__ PropArgs a, int NXp,
+                                                    float *__restrict__ ka,
+                                                    float *__restrict__ ab,
+                                                    float *__restrict__ ic, int *__restrict__ rec,
+                                                    int *__restrict__ src)
+{
+    const int b = blockIdx.y;
+    const float *vb = a.v + (size_t)b * a.nz * a.nx;
+    const size_t plane = (size_t)a.NZ * NXp;
+    int bad = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int pz = (int)(i / NXp), px = (int)(i - (i / NXp) * NXp);
+        float k = 0.f, m = 0.f;
+        if (px < a.NX) {
+            const float vv = vb[min(pz, a.nz - 1) * a.nx + min(max(px - a.nb, 0), a.nx - 1)];
+            if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
+            const double e = dev::e_cell(px, pz, a);
+            k = dev::kappaA_cell(vv, px, pz, a);
+            m = (float)((1.0 - e) / (1.0 + e));
+        }
+        ka[(size_t)b * plane + i] = k;
+        ab[(size_t)b * plane + i] = m;
+    }
+    if (bad) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < a.nr; i += blockDim.x) {
+            const int rz = a.rec_pz[i], rx = a.rec_px[i];
+            const float vv = vb[min(rz, a.nz - 1) * a.nx + min(max(rx - a.nb, 0), a.nx - 1)];
+            const double vdt = (double)vv * a.dtd;
+            ic[(size_t)b * a.nr + i] = (float)(vdt * vdt / (1.0 - dev::e_cell(rx, rz, a)));
+            if (b == 0) rec[i] = (rz << 16) | rx;
+        }
+        if (b == 0)
+            for (int i = threadIdx.x; i < a.ns; i += blockDim.x)
+                src[i] = ((int)a.src_pz[i] << 16) | a.src_px[i];
+    }
+}
+
+// ------------------------------------------------------------------ forward step
+template <int TOPBC, bool STORE>
+__global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ CUtensorMap tm,
+                                                       const __grid_constant__ TileArgs a)
+{
+    __shared__ __align__(128) float tile[HZ * HX];
+    __shared__ __align__(8) uint64_t mbar;
+    const int tid = threadIdx.x, tx = tid % TX, g = tid / TX;
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, bs = blockIdx.z;
+    const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    if (tid == 0) mbar_init(&mbar);
+    __syncthreads();
+    if (tid == 0) tile_load(tile, &mbar, &tm, x0 - 4, z0 - 2, bs);
+
+    const int x = x0 + tx, zr = z0 + g * TROWS;
+    const bool colok = x < a.NX;
+    const size_t plane = (size_t)a.NZ * a.NXp;
+    const float *kab = a.ka + (size_t)b * plane, *abb = a.ab + (size_t)b * plane;
+    float *vb = a.vinc + (size_t)bs * plane;
+    float ka[TROWS], ab[TROWS], vi[TROWS];
+#pragma unroll
+    for (int r = 0; r < TROWS; ++r) {
+        const int z = zr + r;
+        const bool ok = colok && z < a.NZ;
+        const size_t i = (size_t)z * a.NXp + x;
+        ka[r] = ok ? kab[i] : 0.f;
+        ab[r] = ok ? abb[i] : 0.f;
+        vi[r] = ok ? vb[i] : 0.f;
+    }
+    if (!tile_wait(&mbar, a.status)) return;
+    if (TOPBC == 1 && z0 == 0) {
+        // mirrored ghost rows: row -1 = row 1, row -2 = row 2
+        for (int c = tid; c < HX; c += TTHREADS) {
+            tile[1 * HX + c] = tile[3 * HX + c];
+            tile[0 * HX + c] = tile[4 * HX + c];
+        }
+        __syncthreads();
+    }
+    // data sample of the previous step at the receivers inside this tile
+    if (a.d_syn && a.j > 0 && z0 <= a.rzmax && z0 + TZ > a.rzmin) {
+        for (int r = tid; r < a.nr; r += TTHREADS) {
+            const int pz = a.rec[r] >> 16, px = a.rec[r] & 0xffff;
+            if (pz >= z0 && pz < z0 + TZ && px >= x0 && px < x0 + TX)
+                a.d_syn[((size_t)bs * a.nr + r) * a.nt + a.j - 1] =
+                    tile[(pz - z0 + 2) * HX + px - x0 + 4];
+        }
+    }
+    // checkpoint of the state at step j (field u^j, increment v^(j-1/2))
+    if (a.ckpt && a.j % a.ckpt_every == 0) {
+        const size_t cells = (size_t)a.NZ * a.NX;
+        float *st = a.ckpt + ((size_t)(a.j / a.ckpt_every) * gridDim.z + bs) * 2 * cells;
+#pragma unroll
+        for (int r = 0; r < TROWS; ++r) {
+            const int z = zr + r;
+            if (colok && z < a.NZ) {
+                st[(size_t)z * a.NX + x] = tile[(z - z0 + 2) * HX + tx + 4];
+                st[cells + (size_t)z * a.NX + x] = vi[r];
+            }
+        }
+    }
+
+    const int sp = a.src[s], sz = sp >> 16, sx = sp & 0xffff;
+    float *ub = a.unext + (size_t)bs * plane;
+    float *rb = STORE ? a.rec_out + ((size_t)bs * a.rec_planes + (a.j - a.rec_base)) * plane
+                      : nullptr;
+    const float *cp = tile + (g * TROWS + 2) * HX + tx + 4;
+    float wm2 = cp[-2 * HX], wm1 = cp[-HX], w0 = cp[0], wp1 = cp[HX];
+    float Dp = w0 - wm1, Em2 = w0 - wm2, Em1 = wp1 - wm1;
+#pragma unroll
+    for (int r = 0; r < TROWS; ++r) {
+        const float *c = cp + r * HX;
+        const float wp2 = c[2 * HX];
+        const float Dn = wp1 - w0;
+        const float E0 = wp2 - w0;
+        const float dzA = Dn - Dp;
+        const float dzB = E0 - Em2;
+        const float dxA = (c[-1] - w0) + (c[1] - w0);
+        const float dxB = (c[-2] - w0) + (c[2] - w0);
+        float lap = a.cx1 * dxA;
+        lap = fmaf(a.cx2, dxB, lap);
+        lap = fmaf(a.cz1, dzA, lap);
+        lap = fmaf(a.cz2, dzB, lap);
+        float vn = fmaf(ka[r], lap, ab[r] * vi[r]);
+        float un = w0 + vn;
+        const int z = zr + r;
+        if (colok && z < a.NZ) {
+            if (z == sz && x == sx) {
+                // point source: + kappa A s at the source cell (increment and field)
+                const float d = ka[r] * dev::ricker_scaled(a.j, a);
+                vn += d;
+                un += d;
+            }
+            const size_t i = (size_t)z * a.NXp + x;
+            ub[i] = un;
+            vb[i] = vn;
+            if (STORE) rb[i] = lap;
+        }
+        Dp = Dn;
+        Em2 = Em1;
+        Em1 = E0;
+        wm2 = wm1;
+        wm1 = w0;
+        w0 = wp1;
+        wp1 = wp2;
+    }
+}
+
+// d[:, nt-1] = u^nt at the receivers
+__global__ void k_tile_gather(const float *__restrict__ u, const int *__restrict__ rec, int nbs,
+                              int nr, int nt, size_t plane, int NXp, float *__restrict__ d_syn)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nbs * nr) return;
+    const int bs = i / nr, r = i - (i / nr) * nr;
+    const int pz = rec[r] >> 16, px = rec[r] & 0xffff;
+    d_syn[((size_t)bs * nr + r) * nt + nt - 1] = u[(size_t)bs * plane + (size_t)pz * NXp + px];
+}
+
+// state at a checkpoint slot ([bs][2][NZ][NX]) into the field and increment
+__global__ void k_tile_resume(const float *__restrict__ st, int nbs, int NZ, int NX, int NXp,
+                              float *__restrict__ u, float *__restrict__ v)
+{
+    const size_t cells = (size_t)NZ * NX, n = (size_t)nbs * cells;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t bs = i / cells, c = i - bs * cells;
+        const int z = (int)(c / NX), x = (int)(c - (c / NX) * NX);
+        const size_t o = bs * (size_t)NZ * NXp + (size_t)z * NXp + x;
+        u[o] = st[bs * 2 * cells + c];
+        v[o] = st[bs * 2 * cells + cells + c];
+    }
+}
+
+// ------------------------------------------------------------------ adjoint step
+template <int TOPBC>
+__global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ CUtensorMap tm,
+                                                       const __grid_constant__ TileArgs a)
+{
+    __shared__ __align__(128) float tile[HZ * HX];
+    __shared__ float inj[TZ * TX];
+    __shared__ __align__(8) uint64_t mbar;
+    const int tid = threadIdx.x, tx = tid % TX, g = tid / TX;
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, bs = blockIdx.z;
+    const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    if (tid == 0) mbar_init(&mbar);
+    __syncthreads();
+    if (tid == 0) tile_load(tile, &mbar, &tm, x0 - 4, z0 - 2, bs);
+
+    const int x = x0 + tx, zr = z0 + g * TROWS;
+    const bool colok = x < a.NX;
+    const size_t plane = (size_t)a.NZ * a.NXp;
+    const float *kab = a.ka + (size_t)b * plane;
+    float *pb = a.pold + (size_t)bs * plane, *accb = a.acc + (size_t)bs * plane;
+    const float *rb =
+        a.rec_in + ((size_t)bs * a.rec_planes + (a.nt - 1 - a.j - a.rec_base)) * plane;
+    float ka[TROWS], fo[TROWS], ac[TROWS], sv[TROWS];
+#pragma unroll
+    for (int r = 0; r < TROWS; ++r) {
+        const int z = zr + r;
+        const bool ok = colok && z < a.NZ;
+        const size_t i = (size_t)z * a.NXp + x;
+        ka[r] = ok ? kab[i] : 0.f;
+        fo[r] = ok ? pb[i] : 0.f;
+        ac[r] = ok ? accb[i] : 0.f;
+        sv[r] = ok ? rb[i] : 0.f;
+    }
+    // receivers inside this tile: their adjoint source enters through the
+    // old level, psi^{j-1} -= (kappa / B) q
+    const bool has_rec = z0 <= a.rzmax && z0 + TZ > a.rzmin;
+    if (has_rec) {
+#pragma unroll
+        for (int r = 0; r < TROWS; ++r) inj[(g * TROWS + r) * TX + tx] = 0.f;
+    }
+    if (!tile_wait(&mbar, a.status)) return;
+    if (has_rec) {
+        for (int r = tid; r < a.nr; r += TTHREADS) {
+            const int pz = a.rec[r] >> 16, px = a.rec[r] & 0xffff;
+            if (pz >= z0 && pz < z0 + TZ && px >= x0 && px < x0 + TX)
+                inj[(pz - z0) * TX + px - x0] =
+                    a.ic[(size_t)b * a.nr + r] *
+                    a.adj[((size_t)bs * a.nr + r) * a.nt + (a.nt - 1 - a.j)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < TROWS; ++r) fo[r] -= inj[(g * TROWS + r) * TX + tx];
+    }
+
+    const int sp = a.src[s], sz = sp >> 16, sx = sp & 0xffff;
+    const float ex = dev::ex_of(x, a);
+    const float *cp = tile + (g * TROWS + 2) * HX + tx + 4;
+    float wm2 = cp[-2 * HX], wm1 = cp[-HX], w0 = cp[0], wp1 = cp[HX];
+#pragma unroll
+    for (int r = 0; r < TROWS; ++r) {
+        const float *c = cp + r * HX;
+        const float wp2 = c[2 * HX];
+        const int z = zr + r;
+        float lap = a.c0 * w0;
+        lap = fmaf(a.cx1, c[-1] + c[1], lap);
+        lap = fmaf(a.cx2, c[-2] + c[2], lap);
+        lap = fmaf(a.cz1, wm1 + wp1, lap);
+        lap = fmaf(a.cz2, wm2 + wp2, lap);
+        if (TOPBC == 1 && (z == 1 || z == 2)) {
+            // transpose of the mirrored top: reflected weights back onto rows 1, 2
+            lap += (z == 1) ? a.cz1 * wm1 + a.cz2 * w0 : a.cz2 * wm2;
+        }
+        const float e = ex + dev::ez_of((float)(z - (a.nz - 1)), a);
+        const float A2 = __fdividef(2.f, 1.f + e);        // 2A
+        const float AB = A2 - 1.f;                        // A B = (1-e)/(1+e)
+        const float fn = fmaf(ka[r], lap, fmaf(A2, w0, -AB * fo[r]));
+        if (colok && z < a.NZ) {
+            const size_t i = (size_t)z * a.NXp + x;
+            pb[i] = fn;
+            accb[i] = fmaf(fn, sv[r], ac[r]);
+            if (z == sz && x == sx)
+                a.acc_src[bs] = fmaf(fn, dev::ricker_scaled(a.nt - 1 - a.j, a), a.acc_src[bs]);
+        }
+        wm2 = wm1;
+        wm1 = w0;
+        w0 = wp1;
+        wp1 = wp2;
+    }
+}
+
+// dJ/dv_pad = 2 acc / v_pad, folded onto the physical cells (transpose of the
+// edge replication: each physical cell sums the padded cells that copy it,
+// columns then rows in increasing order), per (model, shot)
+__global__ void k_tile_fold(const __grid_constant__ PropArgs a, int NXp,
+                            const float *__restrict__ acc, const float *__restrict__ acc_src,
+                            float *__restrict__ gshot)
+{
+    const int bs = blockIdx.y, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nz * a.nx) return;
+    const int iz = i / a.nx, ix = i - (i / a.nx) * a.nx;
+    const float v = a.v[(size_t)b * a.nz * a.nx + i];
+    const int r0 = iz, r1 = (iz == a.nz - 1) ? a.NZ - 1 : iz;
+    const int c0 = (ix == 0) ? 0 : ix + a.nb, c1 = (ix == a.nx - 1) ? a.NX - 1 : ix + a.nb;
+    const int sz = a.src_pz[s], sx = a.src_px[s];
+    const float *ab = acc + (size_t)bs * a.NZ * NXp;
+    float sum = 0.f;
+    for (int pz = r0; pz <= r1; ++pz) {
+        float row = 0.f;
+        for (int px = c0; px <= c1; ++px) {
+            float gpad = 2.f * ab[(size_t)pz * NXp + px] / v;
+            if (pz == sz && px == sx) gpad += 2.f * acc_src[bs] / v;
+            row += gpad;
+        }
+        sum += row;
+    }
+    gshot[(size_t)bs * a.nz * a.nx + i] = sum;
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 3D map [nbs][NZ][NXp] of float32 with the halo-tile box
+bool make_map(CUtensorMap *m, float *base, int nbs, int NZ, int NXp)
+{
+    auto enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)NXp, (cuuint64_t)NZ, (cuuint64_t)nbs};
+    const cuuint64_t strides[2] = {(cuuint64_t)NXp * 4, (cuuint64_t)NZ * NXp * 4};
+    const cuuint32_t box[3] = {HX, HZ, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TileBufs {
+    float *u[2], *v, *p[2], *acc, *ka, *ab, *ic, *acc_src;
+    int *rec, *src;
+};
+
+TileBufs tile_bufs(const Plan &pl, unsigned char *ws)
+{
+    TileBufs t;
+    t.u[0] = (float *)(ws + pl.ws_t_u0);
+    t.u[1] = (float *)(ws + pl.ws_t_u1);
+    t.v = (float *)(ws + pl.ws_t_v);
+    t.p[0] = (float *)(ws + pl.ws_t_p0);
+    t.p[1] = (float *)(ws + pl.ws_t_p1);
+    t.acc = (float *)(ws + pl.ws_t_acc);
+    t.ka = (float *)(ws + pl.ws_t_ka);
+    t.ab = (float *)(ws + pl.ws_t_ab);
+    t.ic = (float *)(ws + pl.ws_t_ic);
+    t.acc_src = (float *)(ws + pl.ws_t_accsrc);
+    t.rec = (int *)(ws + pl.ws_t_rec);
+    t.src = (int *)(ws + pl.ws_t_src);
+    return t;
+}
+
+TileArgs tile_args(const Plan &pl, const PropArgs &a, const TileBufs &t)
+{
+    TileArgs s{};
+    s.nz = a.nz; s.nx = a.nx; s.nb = a.nb; s.NZ = a.NZ; s.NX = a.NX; s.NXp = pl.NXp;
+    s.nt = a.nt; s.ns = a.ns; s.nr = a.nr;
+    s.dtd = a.dtd; s.t0d = a.t0d; s.ex0d = a.ex0d; s.ez0d = a.ez0d;
+    s.c0 = a.c0; s.cx1 = a.cx1; s.cx2 = a.cx2; s.cz1 = a.cz1; s.cz2 = a.cz2;
+    s.ex0 = a.ex0; s.ez0 = a.ez0; s.inv_nb = a.inv_nb; s.fp = a.fp; s.src_scale = a.src_scale;
+    int zmin = 1 << 30, zmax = -1;
+    for (int i = 0; i < a.nr; ++i) {
+        zmin = a.rec_pz[i] < zmin ? a.rec_pz[i] : zmin;
+        zmax = a.rec_pz[i] > zmax ? a.rec_pz[i] : zmax;
+    }
+    s.rzmin = zmin;
+    s.rzmax = zmax;
+    s.ka = t.ka; s.ab = t.ab; s.ic = t.ic; s.rec = t.rec; s.src = t.src;
+    s.status = a.status;
+    return s;
+}
+
+cudaError_t setup(const Plan &pl, const PropArgs &a, const TileBufs &t, cudaStream_t st)
+{
+    const size_t plane = (size_t)pl.NZ * pl.NXp;
+    dim3 grid((unsigned)((plane + 255) / 256 < 1024 ? (plane + 255) / 256 : 1024), pl.p.batch);
+    k_tile_setup<<<grid, 256, 0, st>>>(a, pl.NXp, t.ka, t.ab, t.ic, t.rec, t.src);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
+                         cudaStream_t st)
+{
+    const int nbs = pl.p.batch * pl.p.ns;
+    const size_t plane = (size_t)pl.NZ * pl.NXp, field = (size_t)nbs * plane * sizeof(float);
+    const TileBufs t = tile_bufs(pl, ws);
+    cudaError_t e = setup(pl, a, t, st);
+    if (e != cudaSuccess) return e;
+    TileArgs s = tile_args(pl, a, t);
+    s.rec_base = a.rec_base;
+    s.rec_planes = a.rec_planes;
+    const dim3 grid((pl.NX + TX - 1) / TX, (pl.NZ + TZ - 1) / TZ, nbs);
+    const int tb = pl.p.top_bc;
+    CUtensorMap maps[2];
+    if (!adj) {
+        const int jb = a.j_begin;
+        if (a.resume) {
+            e = cudaMemsetAsync(t.u[jb & 1], 0, field, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(t.v, 0, field, st);
+            if (e != cudaSuccess) return e;
+            k_tile_resume<<<1024, 256, 0, st>>>(a.resume + 0, nbs, pl.NZ, pl.NX, pl.NXp,
+                                                t.u[jb & 1], t.v);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        } else {
+            e = cudaMemsetAsync(t.u[jb & 1], 0, field, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(t.v, 0, field, st);
+            if (e != cudaSuccess) return e;
+        }
+        // the other level's pad columns and dead cells must read as zero too
+        e = cudaMemsetAsync(t.u[(jb + 1) & 1], 0, field, st);
+        if (e != cudaSuccess) return e;
+        if (!make_map(&maps[0], t.u[0], nbs, pl.NZ, pl.NXp) ||
+            !make_map(&maps[1], t.u[1], nbs, pl.NZ, pl.NXp))
+            return cudaErrorNotSupported;
+        s.vinc = t.v;
+        s.rec_out = a.snap;
+        s.d_syn = a.d_syn;
+        s.ckpt = a.ckpt;
+        s.ckpt_every = a.ckpt_every;
+        const bool store = a.snap != nullptr;
+        for (int j = jb; j < a.j_end; ++j) {
+            s.j = j;
+            s.unext = t.u[(j + 1) & 1];
+            if (store)
+                tb ? k_tile_fwd<1, true><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
+                   : k_tile_fwd<0, true><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
+            else
+                tb ? k_tile_fwd<1, false><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
+                   : k_tile_fwd<0, false><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if (a.d_syn && a.j_end == a.nt) {
+            const int n = nbs * pl.p.nr;
+            k_tile_gather<<<(n + 255) / 256, 256, 0, st>>>(t.u[a.nt & 1], t.rec, nbs, pl.p.nr,
+                                                          a.nt, plane, pl.NXp, a.d_syn);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    // adjoint window [j_begin, j_end); the levels and sums persist in the
+    // workspace between windows
+    const int jb = a.j_begin;
+    if (jb == 0) {
+        e = cudaMemsetAsync(t.p[0], 0, field, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t.p[1], 0, field, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t.acc, 0, field, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t.acc_src, 0, (size_t)nbs * sizeof(float), st);
+        if (e != cudaSuccess) return e;
+    }
+    if (!make_map(&maps[0], t.p[0], nbs, pl.NZ, pl.NXp) ||
+        !make_map(&maps[1], t.p[1], nbs, pl.NZ, pl.NXp))
+        return cudaErrorNotSupported;
+    s.acc = t.acc;
+    s.acc_src = t.acc_src;
+    s.adj = a.adj;
+    s.rec_in = a.snap;
+    for (int j = jb; j < a.j_end; ++j) {
+        s.j = j;
+        s.pold = t.p[(j + 1) & 1];
+        tb ? k_tile_adj<1><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
+           : k_tile_adj<0><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (a.j_end == a.nt) {
+        const dim3 fg((pl.p.nz * pl.p.nx + 255) / 256, nbs);
+        k_tile_fold<<<fg, 256, 0, st>>>(a, pl.NXp, t.acc, t.acc_src, a.gshot);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fwi

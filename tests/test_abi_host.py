@@ -59,6 +59,29 @@ def test_plan_sizes_of_the_benchmark_problem(api):
     assert ctx >= B * ns * nr * (nt * 4 + 1000 * 8)
 
 
+def test_plan_of_a_grid_beyond_shared_memory_uses_the_tiled_fields(api):
+    # 256 x 256 with a 40-cell layer: 296 x 336 padded cells, fields of pitch 336
+    B, ns, nt = 2, 16, 200
+    prob = _prob(api, nz=256, nx=256, nt=nt, batch=B, src_iz=(0,) * ns,
+                 src_ix=tuple(range(0, 256, 16)), rec_iz=(0,) * 256, rec_ix=tuple(range(256)))
+    h = api.fwi_plan_create(prob, api.W2Params())
+    ws, ctx, snap = api.fwi_plan_sizes(h)
+    NZ, NX, NXp = 296, 336, 336
+    assert snap == B * ns * nt * NZ * NXp * 4
+    assert ws >= 6 * B * ns * NZ * NXp * 4 + 2 * B * NZ * NXp * 4
+    # odd padded width: rows padded to a multiple of 4 floats
+    prob = _prob(api, nz=200, nx=301, nt=nt, batch=1, src_ix=(0, 75, 150, 225, 300),
+                 rec_iz=(0,) * 301, rec_ix=tuple(range(301)))
+    h = api.fwi_plan_create(prob, api.W2Params())
+    assert api.fwi_plan_sizes(h)[2] == 5 * nt * 240 * 384 * 4
+    # with checkpoints: two compact NZ x NX grids per slot
+    h = api.fwi_plan_create(_prob(api, nz=256, nx=256, nt=nt, batch=B, src_iz=(0,) * ns,
+                                  src_ix=tuple(range(0, 256, 16)), rec_iz=(0,) * 256,
+                                  rec_ix=tuple(range(256)), checkpoint_every=32),
+                            api.W2Params())
+    assert api.fwi_plan_sizes(h)[2] == 7 * B * ns * 2 * NZ * NX * 4
+
+
 @pytest.mark.parametrize("K", [32, 7, 1, 1000, 5000])
 def test_plan_sizes_with_checkpoints(api, K):
     # checkpoint_every = K: ceil(nt/K) slots of two padded grids per (model,
@@ -91,7 +114,7 @@ def test_plan_sizes_with_checkpoints(api, K):
     (dict(top_bc=2), 1),
     (dict(checkpoint_every=-1), 1),
     (dict(refl_R=0.0), 1),
-    (dict(nx=1200), 3),                      # does not fit the resident kernel
+    (dict(nx=1200, batch=13108), 3),         # tiled grid, batch x ns > 65535 (its grid z)
     (dict(rec_iz=(0, 1), rec_ix=(5, 5)), 3),  # two receivers in one column strip
 ])
 def test_plan_rejects_invalid_problems(api, kw, code):

@@ -256,8 +256,9 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
             o += align_up(B * p.ns * 4);
         }
     }
-    pl->ws_t_u0 = pl->ws_t_u1 = pl->ws_t_v = pl->ws_t_p0 = pl->ws_t_p1 = pl->ws_t_acc = 0;
-    pl->ws_t_ka = pl->ws_t_ab = pl->ws_t_ic = pl->ws_t_accsrc = pl->ws_t_rec = pl->ws_t_src = 0;
+    pl->ws_t_u0 = pl->ws_t_u1 = pl->ws_t_v = pl->ws_t_p0 = pl->ws_t_p1 = pl->ws_t_w = 0;
+    pl->ws_t_acc = 0;
+    pl->ws_t_ka = pl->ws_t_ab = pl->ws_t_accsrc = pl->ws_t_rec = pl->ws_t_src = 0;
     if (pl->tiled) {
         const size_t field = align_up(B * p.ns * (size_t)pl->NZ * pl->NXp * 4);
         const size_t table = align_up(B * (size_t)pl->NZ * pl->NXp * 4);
@@ -266,10 +267,10 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         pl->ws_t_v = o;   o += field;
         pl->ws_t_p0 = o;  o += field;
         pl->ws_t_p1 = o;  o += field;
+        pl->ws_t_w = o;   o += field;
         pl->ws_t_acc = o; o += field;
         pl->ws_t_ka = o;  o += table;
         pl->ws_t_ab = o;  o += table;
-        pl->ws_t_ic = o;  o += align_up(B * p.nr * 4);
         pl->ws_t_accsrc = o; o += align_up(B * p.ns * 4);
         pl->ws_t_rec = o; o += align_up((size_t)p.nr * 4);
         pl->ws_t_src = o; o += align_up((size_t)p.ns * 4);

@@ -62,7 +62,7 @@ struct Plan {
     int ckpt_every, nslot;
     size_t ws_seg, ws_astate, ws_asrc;    // workspace: segment record, adjoint state
     // tiled path: fields, adjoint levels and sums, per-model tables
-    size_t ws_t_u0, ws_t_u1, ws_t_v, ws_t_p0, ws_t_p1, ws_t_acc, ws_t_ka, ws_t_ab, ws_t_ic,
+    size_t ws_t_u0, ws_t_u1, ws_t_v, ws_t_p0, ws_t_p1, ws_t_w, ws_t_acc, ws_t_ka, ws_t_ab,
         ws_t_accsrc, ws_t_rec, ws_t_src;
 };
 

@@ -4,8 +4,8 @@
 //
 //   forward  v^{j+1/2} = A B v^{j-1/2} + kappa A (L u^j + s^j),  u^{j+1} = u^j + v^{j+1/2}
 //            (Eq. 1 in increment form, Laplacian on neighbour differences)
-//   adjoint  psi^{j+1} = 2A psi^j - A B psi^{j-1} + kappa A L^T psi^j, receivers'
-//            adjoint source through the old level, imaging
+//   adjoint  w^{j+1/2} = A B w^{j-1/2} + kappa A (L^T psi^j + q^j),  psi^{j+1} = psi^j + w^{j+1/2}
+//            (the same form with L^T; q the receivers' adjoint source), imaging
 //            dJ/dv_pad = (2 / v_pad) sum_j psi^{j+1} t^{nt-1-j}
 //
 // The fields of every (model, shot) live in global memory, [bs][NZ][NXp]
@@ -52,7 +52,6 @@ struct TileArgs {
     double dtd, t0d, ex0d, ez0d;
     float c0, cx1, cx2, cz1, cz2, ex0, ez0, inv_nb, fp, src_scale;
     const float *ka, *ab;       // [B][NZ][NXp]: kappa A, A B
-    const float *ic;            // [B][nr]: kappa / B at the receivers
     const int *rec;             // [nr]: pz << 16 | px
     const int *src;             // [ns]: pz << 16 | px
     // forward
@@ -60,8 +59,7 @@ struct TileArgs {
     float *rec_out;             // record [bs][rec_planes][NZ][NXp], null: off
     float *d_syn;               // [bs][nr][nt], null: off
     float *ckpt;                // checkpoint slots [slot][bs][2][NZ][NX], null: off
-    // adjoint
-    float *pold;                // psi^{j-1}, overwritten with psi^{j+1}
+    // adjoint (reuses unext = psi^{j+1}, vinc = its increment)
     float *acc, *acc_src;       // imaging sums [bs][NZ][NXp], source-cell sums [bs]
     const float *adj;           // adjoint source [bs][nr][nt]
     const float *rec_in;        // record read by the adjoint
@@ -121,13 +119,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar)
 }
 
 // ------------------------------------------------------------------ set-up
-// Per-model tables (kappa A, A B, kappa / B at the receivers) formed in
-// double exactly as the resident kernels form them, the receiver and source
-// tables, and the velocity check.
+// Per-model tables (kappa A, A B) formed in double exactly as the resident
+// kernels form them, the receiver and source tables, and the velocity check.
 __global__ void __launch_bounds__(256) k_tile_setup(const __grid_constant__ PropArgs a, int NXp,
                                                     float *__restrict__ ka,
-                                                    float *__restrict__ ab,
-                                                    float *__restrict__ ic, int *__restrict__ rec,
+                                                    float *__restrict__ ab, int *__restrict__ rec,
                                                     int *__restrict__ src)
 {
     const int b = blockIdx.y;
@@ -149,17 +145,11 @@ __global__ void __launch_bounds__(256) k_tile_setup(const __grid_constant__ Prop
         ab[(size_t)b * plane + i] = m;
     }
     if (bad) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
-    if (blockIdx.x == 0) {
-        for (int i = threadIdx.x; i < a.nr; i += blockDim.x) {
-            const int rz = a.rec_pz[i], rx = a.rec_px[i];
-            const float vv = vb[min(rz, a.nz - 1) * a.nx + min(max(rx - a.nb, 0), a.nx - 1)];
-            const double vdt = (double)vv * a.dtd;
-            ic[(size_t)b * a.nr + i] = (float)(vdt * vdt / (1.0 - dev::e_cell(rx, rz, a)));
-            if (b == 0) rec[i] = (rz << 16) | rx;
-        }
-        if (b == 0)
-            for (int i = threadIdx.x; i < a.ns; i += blockDim.x)
-                src[i] = ((int)a.src_pz[i] << 16) | a.src_px[i];
+    if (blockIdx.x == 0 && b == 0) {
+        for (int i = threadIdx.x; i < a.nr; i += blockDim.x)
+            rec[i] = ((int)a.rec_pz[i] << 16) | a.rec_px[i];
+        for (int i = threadIdx.x; i < a.ns; i += blockDim.x)
+            src[i] = ((int)a.src_pz[i] << 16) | a.src_px[i];
     }
 }
 
@@ -297,6 +287,11 @@ __global__ void k_tile_resume(const float *__restrict__ st, int nbs, int NZ, int
 }
 
 // ------------------------------------------------------------------ adjoint step
+// Increment form of the adjoint recurrence (the forward's form with L^T):
+//   w^{j+1/2} = A B w^{j-1/2} + kappa A (L^T psi^j + q^j),  psi^{j+1} = psi^j + w^{j+1/2},
+// q^j the adjoint source r^{nt-1-j} at the receivers.  Over thousands of
+// steps the standard form 2A psi^j - A B psi^{j-1} loses the slowly varying
+// part of psi to float32 round-off, as the forward's standard form does.
 template <int TOPBC>
 __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ CUtensorMap tm,
                                                        const __grid_constant__ TileArgs a)
@@ -314,23 +309,24 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
     const int x = x0 + tx, zr = z0 + g * TROWS;
     const bool colok = x < a.NX;
     const size_t plane = (size_t)a.NZ * a.NXp;
-    const float *kab = a.ka + (size_t)b * plane;
-    float *pb = a.pold + (size_t)bs * plane, *accb = a.acc + (size_t)bs * plane;
+    const float *kab = a.ka + (size_t)b * plane, *abb = a.ab + (size_t)b * plane;
+    float *wb = a.vinc + (size_t)bs * plane, *accb = a.acc + (size_t)bs * plane;
+    float *pn = a.unext + (size_t)bs * plane;
     const float *rb =
         a.rec_in + ((size_t)bs * a.rec_planes + (a.nt - 1 - a.j - a.rec_base)) * plane;
-    float ka[TROWS], fo[TROWS], ac[TROWS], sv[TROWS];
+    float ka[TROWS], ab[TROWS], wi[TROWS], ac[TROWS], sv[TROWS];
 #pragma unroll
     for (int r = 0; r < TROWS; ++r) {
         const int z = zr + r;
         const bool ok = colok && z < a.NZ;
         const size_t i = (size_t)z * a.NXp + x;
         ka[r] = ok ? kab[i] : 0.f;
-        fo[r] = ok ? pb[i] : 0.f;
+        ab[r] = ok ? abb[i] : 0.f;
+        wi[r] = ok ? wb[i] : 0.f;
         ac[r] = ok ? accb[i] : 0.f;
         sv[r] = ok ? rb[i] : 0.f;
     }
-    // receivers inside this tile: their adjoint source enters through the
-    // old level, psi^{j-1} -= (kappa / B) q
+    // adjoint source of the receivers inside this tile
     const bool has_rec = z0 <= a.rzmax && z0 + TZ > a.rzmin;
     if (has_rec) {
 #pragma unroll
@@ -342,43 +338,48 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
             const int pz = a.rec[r] >> 16, px = a.rec[r] & 0xffff;
             if (pz >= z0 && pz < z0 + TZ && px >= x0 && px < x0 + TX)
                 inj[(pz - z0) * TX + px - x0] =
-                    a.ic[(size_t)b * a.nr + r] *
                     a.adj[((size_t)bs * a.nr + r) * a.nt + (a.nt - 1 - a.j)];
         }
         __syncthreads();
-#pragma unroll
-        for (int r = 0; r < TROWS; ++r) fo[r] -= inj[(g * TROWS + r) * TX + tx];
     }
 
     const int sp = a.src[s], sz = sp >> 16, sx = sp & 0xffff;
-    const float ex = dev::ex_of(x, a);
     const float *cp = tile + (g * TROWS + 2) * HX + tx + 4;
     float wm2 = cp[-2 * HX], wm1 = cp[-HX], w0 = cp[0], wp1 = cp[HX];
+    float Dp = w0 - wm1, Em2 = w0 - wm2, Em1 = wp1 - wm1;
 #pragma unroll
     for (int r = 0; r < TROWS; ++r) {
         const float *c = cp + r * HX;
         const float wp2 = c[2 * HX];
         const int z = zr + r;
-        float lap = a.c0 * w0;
-        lap = fmaf(a.cx1, c[-1] + c[1], lap);
-        lap = fmaf(a.cx2, c[-2] + c[2], lap);
-        lap = fmaf(a.cz1, wm1 + wp1, lap);
-        lap = fmaf(a.cz2, wm2 + wp2, lap);
+        const float Dn = wp1 - w0;
+        const float E0 = wp2 - w0;
+        const float dzA = Dn - Dp;
+        const float dzB = E0 - Em2;
+        const float dxA = (c[-1] - w0) + (c[1] - w0);
+        const float dxB = (c[-2] - w0) + (c[2] - w0);
+        float lap = a.cx1 * dxA;
+        lap = fmaf(a.cx2, dxB, lap);
+        lap = fmaf(a.cz1, dzA, lap);
+        lap = fmaf(a.cz2, dzB, lap);
         if (TOPBC == 1 && (z == 1 || z == 2)) {
             // transpose of the mirrored top: reflected weights back onto rows 1, 2
             lap += (z == 1) ? a.cz1 * wm1 + a.cz2 * w0 : a.cz2 * wm2;
         }
-        const float e = ex + dev::ez_of((float)(z - (a.nz - 1)), a);
-        const float A2 = __fdividef(2.f, 1.f + e);        // 2A
-        const float AB = A2 - 1.f;                        // A B = (1-e)/(1+e)
-        const float fn = fmaf(ka[r], lap, fmaf(A2, w0, -AB * fo[r]));
+        float wn = fmaf(ka[r], lap, ab[r] * wi[r]);
+        if (has_rec) wn = fmaf(ka[r], inj[(g * TROWS + r) * TX + tx], wn);
+        const float pnv = w0 + wn;
         if (colok && z < a.NZ) {
             const size_t i = (size_t)z * a.NXp + x;
-            pb[i] = fn;
-            accb[i] = fmaf(fn, sv[r], ac[r]);
+            pn[i] = pnv;
+            wb[i] = wn;
+            accb[i] = fmaf(pnv, sv[r], ac[r]);
             if (z == sz && x == sx)
-                a.acc_src[bs] = fmaf(fn, dev::ricker_scaled(a.nt - 1 - a.j, a), a.acc_src[bs]);
+                a.acc_src[bs] = fmaf(pnv, dev::ricker_scaled(a.nt - 1 - a.j, a), a.acc_src[bs]);
         }
+        Dp = Dn;
+        Em2 = Em1;
+        Em1 = E0;
         wm2 = wm1;
         wm1 = w0;
         w0 = wp1;
@@ -447,7 +448,7 @@ bool make_map(CUtensorMap *m, float *base, int nbs, int NZ, int NXp)
 }
 
 struct TileBufs {
-    float *u[2], *v, *p[2], *acc, *ka, *ab, *ic, *acc_src;
+    float *u[2], *v, *p[2], *w, *acc, *ka, *ab, *acc_src;
     int *rec, *src;
 };
 
@@ -459,10 +460,10 @@ TileBufs tile_bufs(const Plan &pl, unsigned char *ws)
     t.v = (float *)(ws + pl.ws_t_v);
     t.p[0] = (float *)(ws + pl.ws_t_p0);
     t.p[1] = (float *)(ws + pl.ws_t_p1);
+    t.w = (float *)(ws + pl.ws_t_w);
     t.acc = (float *)(ws + pl.ws_t_acc);
     t.ka = (float *)(ws + pl.ws_t_ka);
     t.ab = (float *)(ws + pl.ws_t_ab);
-    t.ic = (float *)(ws + pl.ws_t_ic);
     t.acc_src = (float *)(ws + pl.ws_t_accsrc);
     t.rec = (int *)(ws + pl.ws_t_rec);
     t.src = (int *)(ws + pl.ws_t_src);
@@ -484,7 +485,7 @@ TileArgs tile_args(const Plan &pl, const PropArgs &a, const TileBufs &t)
     }
     s.rzmin = zmin;
     s.rzmax = zmax;
-    s.ka = t.ka; s.ab = t.ab; s.ic = t.ic; s.rec = t.rec; s.src = t.src;
+    s.ka = t.ka; s.ab = t.ab; s.rec = t.rec; s.src = t.src;
     s.status = a.status;
     return s;
 }
@@ -493,7 +494,7 @@ cudaError_t setup(const Plan &pl, const PropArgs &a, const TileBufs &t, cudaStre
 {
     const size_t plane = (size_t)pl.NZ * pl.NXp;
     dim3 grid((unsigned)((plane + 255) / 256 < 1024 ? (plane + 255) / 256 : 1024), pl.p.batch);
-    k_tile_setup<<<grid, 256, 0, st>>>(a, pl.NXp, t.ka, t.ab, t.ic, t.rec, t.src);
+    k_tile_setup<<<grid, 256, 0, st>>>(a, pl.NXp, t.ka, t.ab, t.rec, t.src);
     return cudaGetLastError();
 }
 
@@ -564,6 +565,7 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
     if (jb == 0) {
         e = cudaMemsetAsync(t.p[0], 0, field, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(t.p[1], 0, field, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t.w, 0, field, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(t.acc, 0, field, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(t.acc_src, 0, (size_t)nbs * sizeof(float), st);
         if (e != cudaSuccess) return e;
@@ -575,9 +577,10 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
     s.acc_src = t.acc_src;
     s.adj = a.adj;
     s.rec_in = a.snap;
+    s.vinc = t.w;
     for (int j = jb; j < a.j_end; ++j) {
         s.j = j;
-        s.pold = t.p[(j + 1) & 1];
+        s.unext = t.p[(j + 1) & 1];
         tb ? k_tile_adj<1><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
            : k_tile_adj<0><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

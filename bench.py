@@ -8,6 +8,11 @@ adjoint source, adjoint solve with imaging and fold, and the preconditioned
 guided update.  Metric: W2-FWI gradients/s (plus Gcell-updates/s).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
+                    [--workload 70x70|256x256|512x1024]
+
+--workload selects the larger grids that run on the tiled propagators
+(256x256: 16 shots, 2000 steps, record kept; 512x1024: 32 shots, 4000 steps,
+checkpoints every 32 steps); the default is the 70x70 workload above.
 
 Under torchrun (N > 1) every rank owns its own B models (weak scaling, no
 data-path collective); the step time is the max over ranks.
@@ -30,9 +35,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-NZ_PHYS, NX_PHYS, NB, NT, NS, NR, DX, DT = 70, 70, 40, 1000, 5, 70, 10.0, 1e-3
-METRIC = "W2-FWI gradients/s (70x70, 5 shots, 1000 steps)"
+DX, DT, NB = 10.0, 1e-3, 40
 UNIT = "gradients/s"
+# name: physical grid, steps, shots, receivers, model family, default batch,
+# checkpoint interval (0: whole record kept), propagator family
+WORKLOADS = {
+    "70x70": dict(nz=70, nx=70, nt=1000, ns=5, nr=70, kind="layered", batch=152, ckpt=0,
+                  path="resident"),
+    "256x256": dict(nz=256, nx=256, nt=2000, ns=16, nr=256, kind="curved_faulted", batch=8,
+                    ckpt=0, path="tiled"),
+    "512x1024": dict(nz=512, nx=1024, nt=4000, ns=32, nr=1024, kind="curved_faulted", batch=2,
+                     ckpt=32, path="tiled"),
+}
+
+
+def metric_of(name):
+    w = WORKLOADS[name]
+    return f"W2-FWI gradients/s ({w['nz']}x{w['nx']}, {w['ns']} shots, {w['nt']} steps)"
 
 
 def peaks():
@@ -77,11 +96,11 @@ def max_over_ranks(values, world: int, device=None):
     return t.tolist()
 
 
-def workload_inputs(B, seed0):
+def workload_inputs(wl, B, seed0):
     from paper_2603_16393_gb300 import inputs as I
-    vt = I.model_batch("layered", range(seed0, seed0 + B), NZ_PHYS, NX_PHYS)
-    v0 = np.stack([I.linear_initial_model(NZ_PHYS, NX_PHYS)] * B)
-    geo = I.surface_geometry(NX_PHYS, NS, NR)
+    vt = I.model_batch(wl["kind"], range(seed0, seed0 + B), wl["nz"], wl["nx"])
+    v0 = np.stack([I.linear_initial_model(wl["nz"], wl["nx"])] * B)
+    geo = I.surface_geometry(wl["nx"], wl["ns"], wl["nr"])
     return vt, v0, geo
 
 
@@ -135,13 +154,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle timing
-def oracle_sample(n_models, threads, seed0=0):
+def oracle_sample(n_models, threads, seed0=0, wl=None):
     """Time the FP64 oracle on a bounded sample of the same workload: n_models
-    full gradients (forward + W2 misfit + adjoint for each of the 5 shots)."""
+    full gradients (forward + W2 misfit + adjoint for each shot)."""
     from oracle import oracle as O
-    vt, v0, geo = workload_inputs(n_models, seed0)
-    op = O.Problem(nz=NZ_PHYS, nx=NX_PHYS, nb=NB, nt=NT, dz=DX, dx=DX, dt=DT, src_iz=geo.src_iz,
-                   src_ix=geo.src_ix, rec_iz=geo.rec_iz, rec_ix=geo.rec_ix)
+    wl = wl or WORKLOADS["70x70"]
+    vt, v0, geo = workload_inputs(wl, n_models, seed0)
+    op = O.Problem(nz=wl["nz"], nx=wl["nx"], nb=NB, nt=wl["nt"], dz=DX, dx=DX, dt=DT,
+                   src_iz=geo.src_iz, src_ix=geo.src_ix, rec_iz=geo.rec_iz, rec_ix=geo.rec_ix)
     w2p = O.W2Params()
     ctx = O.w2_prepare(O.forward(op, vt, threads=threads), op.dt, w2p)
     t = time.perf_counter()
@@ -157,6 +177,8 @@ def run_reference(args, rank, world):
     """--impl reference: the oracle as it stands, on the host cores, rank 0 only."""
     if rank != 0:
         return
+    wl = WORKLOADS["70x70"]
+    NS = wl["ns"]
     threads = cpu_cores()
     n_models = max(1, threads // NS + (1 if threads % NS else 0))
     for _ in range(args.warmup):
@@ -165,7 +187,8 @@ def run_reference(args, rank, world):
     tstep = statistics.mean(times)
     value = n_models / tstep
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "impl": "reference", "metric": metric_of("70x70"), "value": value, "unit": UNIT,
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tstep * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded layered models)",
@@ -187,11 +210,15 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    B = args.batch
-    vt, v0, geo = workload_inputs(B, seed0=rank_seed0(rank, B))
+    wl = dict(WORKLOADS[args.workload])
+    if args.nt:
+        wl["nt"] = args.nt
+    NZ_PHYS, NX_PHYS, NT, NS, NR = wl["nz"], wl["nx"], wl["nt"], wl["ns"], wl["nr"]
+    B = args.batch or wl["batch"]
+    vt, v0, geo = workload_inputs(wl, B, seed0=rank_seed0(rank, B))
     prob = api.Problem(nz=NZ_PHYS, nx=NX_PHYS, nb=NB, nt=NT, dz=DX, dx=DX, dt=DT,
                        src_iz=geo.src_iz, src_ix=geo.src_ix, rec_iz=geo.rec_iz,
-                       rec_ix=geo.rec_ix, v_max=4500.0, batch=B)
+                       rec_ix=geo.rec_ix, v_max=4500.0, batch=B, checkpoint_every=wl["ckpt"])
     plan = api.Plan(prob, api.W2Params(), device=dev)
     # Table 1 (CurveVel-A) rho0, gamma; Sec. 6.3 c, tau, eps; the diffusion's
     # normalised space (v - 3000)/1500 has a unit of 1500 m/s
@@ -230,7 +257,18 @@ def run_ours(args, rank, world, local_rank):
         # preconditioned update (no network: v' = v0hat = v, g = h = dJ/dv)
         api.fwi_guided_step(B, NZ_PHYS, NX_PHYS, gparams, v_in, v_in, grad, grad, v_out, rho)
 
-    kernels_per_step = 3 + 1 + 2 + 2 + 1   # prepare, forward, misfit, adjoint+shot sum, guided
+    # library kernels per step: prepare (3), forward, misfit (2), adjoint +
+    # shot sum, guided (1); the tiled propagators launch once per time step,
+    # plus a set-up (and a resume per recomputed segment) and a final gather
+    # or fold
+    if wl["path"] == "resident":
+        kernels_per_step = 3 + 1 + 2 + 2 + 1
+    else:
+        K = wl["ckpt"]
+        S = -(-NT // K) if K else 0
+        fwd_k = 1 + NT + 1
+        adj_k = (2 * S + (S - 1) + 2 * NT + 2) if K else (1 + NT + 2)
+        kernels_per_step = 3 + fwd_k + 2 + adj_k + 1
 
     def barrier():
         if world > 1:
@@ -287,39 +325,62 @@ def run_ours(args, rank, world, local_rank):
         return
 
     plane = (NZ_PHYS + NB) * (NX_PHYS + 2 * NB)
-    cell_updates = 2 * B * NS * NT * plane          # forward + adjoint, per step per rank
-    # dominant kernel: the adjoint propagator; its algorithmic HBM traffic per
-    # launch = the wavefield record it streams in (4 B per cell-update) + the
-    # adjoint source + the model + the per-shot gradient
-    adj_bytes = B * NS * NT * plane * 4 + B * NS * NR * NT * 4 + B * NZ_PHYS * NX_PHYS * 4 * (1 + NS + 1)
-    fwd_bytes = B * NS * NT * plane * 4 + B * NS * NR * NT * 4 + B * NZ_PHYS * NX_PHYS * 4
+    cu = B * NS * NT * plane                         # cell-updates of one propagator pass
+    cell_updates = 2 * cu                            # forward + adjoint, per step per rank
+    small = B * NS * NR * NT * 4 + B * NZ_PHYS * NX_PHYS * 4 * (1 + NS + 1)
+    K = wl["ckpt"]
+    if wl["path"] == "resident":
+        # the propagators stream the wavefield record (4 B per cell-update:
+        # the forward writes it, the adjoint reads it) + traces, models and
+        # per-shot gradients
+        adj_bytes, fwd_bytes = cu * 4 + small, cu * 4 + B * NS * NR * NT * 4 + B * NZ_PHYS * NX_PHYS * 4
+        adj_name, fwd_name = "adjoint propagator", "forward propagator"
+    else:
+        # tiled, per cell-update: forward reads u, v and writes u, v (16 B;
+        # + 4 B record); adjoint reads psi, w, imaging sum, record and writes
+        # psi, w, imaging sum (28 B); the per-model tables kappa A, A B (8 B
+        # per cell) are read once per model and step (shots of a model share
+        # them); with checkpoints the adjoint call also recomputes the
+        # forward with its record
+        tables = B * NT * plane * 8
+        ck = (2 * B * NS * plane * 4 * -(-NT // K)) if K else 0
+        fwd_bytes = cu * (16 if K else 20) + tables + ck + small
+        adj_bytes = cu * 28 + tables + ((cu * 20 + tables) if K else 0) + small
+        fwd_name = "tiled forward"
+        adj_name = "tiled adjoint call (recompute + adjoint)" if K else "tiled adjoint"
     hbm_peak, peak_kind = peaks()
-    dom = max((adj_ms, adj_bytes, "adjoint"), (fwd_ms, fwd_bytes, "forward"))
+    dom = max((adj_ms, adj_bytes, adj_name, "adjoint"), (fwd_ms, fwd_bytes, fwd_name, "forward"))
     achieved = dom[1] / (dom[0] * 1e-3) / 1e9
-    traffic = record_traffic(B * NS)
-    traffic = traffic[dom[2]] if traffic else None
+    traffic = record_traffic(B * NS) if wl["path"] == "resident" else None
+    traffic = traffic[dom[3]] if traffic else None
     value = world * B / (ms * 1e-3)
 
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload != "512x1024":
         threads = cpu_cores()
-        n_models = max(1, (2 * threads + NS - 1) // NS)
-        t = oracle_sample(n_models, threads)
+        n_models = max(1, (2 * threads + NS - 1) // NS) if args.workload == "70x70" else 1
+        t = oracle_sample(n_models, threads, wl=wl)
         cpu = {"value": n_models / t, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{n_models} full 70x70 gradients (5 shots x 1000 steps, FP64) on "
-                         f"{threads} threads, {t:.1f} s wall"}
+               "sample": f"{n_models} full {NZ_PHYS}x{NX_PHYS} gradients ({NS} shots x {NT} "
+                         f"steps, FP64) on {threads} threads, {t:.1f} s wall"}
 
+    record = (f"checkpoints every {K} steps" if K else "store-all wavefield record")
+    resident_gb = (B * NS * NT * plane * 4 if not K else B * NS * 6 * plane * 4) / 1e9
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded layered models)",
-        "config": {"workload": f"{B} x 70x70 layered models per GPU, 5 shots, 70 receivers, "
-                               "1000 steps, 40-cell absorbing layer, store-all wavefield record",
+        "metric": metric_of(args.workload) if not args.nt else metric_of(args.workload).replace(
+            f"{WORKLOADS[args.workload]['nt']} steps", f"{NT} steps"), "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": f"synthetic (seeded {wl['kind'].replace('_', '/')} models)",
+        "config": {"workload": f"{B} x {NZ_PHYS}x{NX_PHYS} {wl['kind'].replace('_', '/')} models "
+                               f"per GPU, {NS} shots, {NR} receivers, {NT} steps, 40-cell "
+                               f"absorbing layer, {record}",
                    "batch_per_gpu": B, "global_batch": B * world,
-                   "l2": "inputs larger than L2 (wavefield record %.1f GB per step)"
-                         % (B * NS * NT * plane * 4 / 1e9),
+                   "l2": ("inputs larger than L2 (wavefield record %.1f GB per step)" if not K
+                          else "inputs larger than L2 (propagator fields %.1f GB)")
+                         % resident_gb,
                    "gcell_updates_per_s": world * cell_updates / (ms * 1e-3) / 1e9},
-        "roofline": {"bound": "hbm", "kernel": dom[2] + " propagator", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": dom[2], "achieved": achieved,
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": traffic, "algorithmic_bytes": dom[1],
                      "peak_source": peak_kind, "ms_per_launch": dom[0]},
@@ -330,6 +391,9 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "cpu_baseline": cpu,
     }
+    if cpu is None and args.workload == "512x1024":
+        line["config"]["cpu_baseline_note"] = ("not sampled: one FP64 oracle unit keeps 4000 "
+                                               "wavefield levels of 552x1104 cells (19.5 GB)")
     print(json.dumps(line), flush=True)
 
 
@@ -338,7 +402,10 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=152)
+    ap.add_argument("--batch", type=int, default=0, help="models per GPU (0: workload default)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="70x70")
+    ap.add_argument("--nt", type=int, default=0,
+                    help="time steps (0: the workload's); shorter runs size profiler captures")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -23,7 +23,7 @@ def _worker(rank, world, port, out):
     from paper_2603_16393_gb300 import inputs
     B = 3
     seed0 = bench.rank_seed0(rank, B)
-    vt, _, _ = bench.workload_inputs(B, seed0)
+    vt, _, _ = bench.workload_inputs(bench.WORKLOADS["70x70"], B, seed0)
     local = [10.0 + rank, 20.0 - rank, 1.0 * rank]
     mx = bench.max_over_ranks(local, world)
     # every rank sees the same maximum

@@ -131,17 +131,13 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     pl->fast = fwi::fast_bucket(pl->NZ, pl->NX, &pl->fast_P, &pl->fast_PR, &pl->fast_NZM);
     if (pl->fast) {
         const int nstrip = (pl->NZ + fwi::kFastRows - 1) / fwi::kFastRows;
-        const size_t limit = 227 * 1024;
         for (int adj = 0; adj < 2; ++adj) {
             fwi::ResidentShape &sh = adj ? pl->shape_adj : pl->shape;
             sh.rows = fwi::kFastRows;
             sh.maxrows = fwi::kFastRows;
             sh.nstrip = nstrip;
             sh.threads = ((pl->NX * nstrip + 31) / 32) * 32;
-            const size_t fixed = fwi::fast_smem(pl->fast_P, pl->fast_NZM, adj != 0, 0, p.nr);
-            int chunk = fixed + (size_t)p.nr * 4 > limit
-                            ? 0 : (int)((limit - fixed) / ((size_t)p.nr * 4));
-            if (chunk > 32) chunk = 32;
+            const int chunk = fwi::fast_chunk(pl->fast_P, pl->fast_NZM, adj != 0, p.nr);
             sh.chunk = chunk;
             sh.smem = fwi::fast_smem(pl->fast_P, pl->fast_NZM, adj != 0, chunk, p.nr);
             if (chunk < 1) pl->fast = false;
@@ -155,11 +151,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
             sh.maxrows = sh.rows;
             sh.nstrip = nstrip2;
             sh.threads = (((pl->NX / 2) * nstrip2 + 31) / 32) * 32;
-            const size_t limit = 227 * 1024;
-            const size_t fixed = fwi::fast_smem(fwi::kPairPitch, pl->fast_NZM, false, 0, p.nr);
-            int chunk = fixed + (size_t)p.nr * 4 > limit
-                            ? 0 : (int)((limit - fixed) / ((size_t)p.nr * 4));
-            if (chunk > 32) chunk = 32;
+            const int chunk = fwi::fast_chunk(fwi::kPairPitch, pl->fast_NZM, false, p.nr);
             sh.chunk = chunk;
             sh.smem = fwi::fast_smem(fwi::kPairPitch, pl->fast_NZM, false, chunk, p.nr);
             if (chunk < 1) pl->fwd_pair = false;
@@ -171,10 +163,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
             sh.maxrows = fwi::kFastRows;
             sh.nstrip = nstrip;
             sh.threads = ((pl->NX * nstrip + 31) / 32) * 32;
-            const size_t limit = 227 * 1024;
-            const size_t fixed = fwi::fast_smem(pl->fast_P, pl->fast_NZM, false, 0, p.nr);
-            int chunk = (int)((limit - fixed) / ((size_t)p.nr * 4));
-            if (chunk > 32) chunk = 32;
+            const int chunk = fwi::fast_chunk(pl->fast_P, pl->fast_NZM, false, p.nr);
             sh.chunk = chunk;
             sh.smem = fwi::fast_smem(pl->fast_P, pl->fast_NZM, false, chunk, p.nr);
         }

@@ -156,6 +156,7 @@ bool choose_resident_shape(int NZ, int NX, int nr, bool adj, ResidentShape *out)
 // shared memory, and their launch.
 bool fast_bucket(int NZ, int NX, int *P, int *PR, int *NZM);
 size_t fast_smem(int P, int NZM, bool adj, int chunk, int nr);
+int fast_chunk(int P, int NZM, bool adj, int nr);   // staging steps that fit (<= 32; 0: none)
 bool fwd_pair_ok(int NX, int NZ, int NZM);
 cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st);
 // Tiled propagators: one launch per step over [a.j_begin, a.j_end)

@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
     extern __shared__ float sm[];
     constexpr int FSZ = (NZM + 4) * P;
     float *U0 = sm, *U1 = sm + FSZ, *K = sm + 2 * FSZ, *IC = K + NZM * P, *ST = IC + a.nr;
+    float *RS = ST + a.chunk * a.nr;
     const int NX = a.NX, NZ = a.NZ;
     const int bs = blockIdx.x, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -566,8 +567,10 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
         const float *ab = a.adj + (size_t)bs * a.nr * a.nt;
         for (int e = tid; e < nch * a.nr; e += nth) {
             const int i = e / nch, jj = e - (e / nch) * nch;
-            ST[jj * a.nr + i] = ab[(size_t)i * a.nt + (a.nt - 1 - (j0 + jj))];
+            ST[jj * a.nr + i] = IC[i] * ab[(size_t)i * a.nt + (a.nt - 1 - (j0 + jj))];
         }
+        // source wavelet of the chunk (source-cell imaging term, thread 0)
+        for (int e = tid; e < nch; e += nth) RS[e] = ricker_scaled(a.nt - 1 - (j0 + e), a);
         __syncthreads();
         for (int jj = 0; jj < nch; ++jj) {
             const int j = j0 + jj;
@@ -575,7 +578,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
             float *nxt = (j & 1) ? U0 : U1;
             if (inj_slot >= 0) {
                 const int rz = a.rec_pz[inj_slot], rx = a.rec_px[inj_slot];
-                nxt[(rz + 2) * P + rx + 2] -= IC[inj_slot] * ST[jj * a.nr + inj_slot];
+                nxt[(rz + 2) * P + rx + 2] -= ST[jj * a.nr + inj_slot];   // (kappa/B) q
             }
             if (j + 1 < a.j_end) sr -= plane;
             const float *cp = cur + (z0 + 2) * P + x + 2;
@@ -584,9 +587,9 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
             adj_rows<P, PR, TOPBC>(cp, np, kp, sr, opaque(zbf), opaque(ex), top_strip, active, acc, sv,
                                a);
             __syncthreads();
-            if (tid == 0) {
+            if (tid == nth - 1) {   // (its warp holds no receivers of the top rows)
                 const int sz = a.src_pz[s], sx = a.src_px[s];
-                acc_src = fmaf(nxt[(sz + 2) * P + sx + 2], ricker_scaled(a.nt - 1 - j, a), acc_src);
+                acc_src = fmaf(nxt[(sz + 2) * P + sx + 2], RS[jj], acc_src);
             }
         }
     }
@@ -695,10 +698,19 @@ bool fwd_pair_ok(int NX, int NZ, int NZM)
 size_t fast_smem(int P, int NZM, bool adj, int chunk, int nr)
 {
     // two field levels + one per-cell table (A B for the forward, kappa A for
-    // the adjoint) + the adjoint's per-receiver coefficients + the receiver
-    // staging chunk
+    // the adjoint) + the adjoint's per-receiver coefficients + the staging
+    // chunk (receiver samples; the adjoint also stages the source wavelet)
     return ((size_t)2 * (NZM + 4) * P + (size_t)NZM * P + (adj ? (size_t)nr : 0) +
-            (size_t)chunk * nr) * sizeof(float);
+            (size_t)chunk * (nr + (adj ? 1 : 0))) * sizeof(float);
+}
+
+int fast_chunk(int P, int NZM, bool adj, int nr)
+{
+    const size_t limit = 227 * 1024, fixed = fast_smem(P, NZM, adj, 0, nr);
+    const size_t per = ((size_t)nr + (adj ? 1 : 0)) * sizeof(float);
+    if (fixed + per > limit) return 0;
+    const size_t c = (limit - fixed) / per;
+    return c > 32 ? 32 : (int)c;
 }
 
 cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st)

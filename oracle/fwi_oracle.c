@@ -390,7 +390,7 @@ double orc_w2_prepare(int ntr, int nt, double dt, double k, double cfac,
 double orc_w2_misfit(int ntr, int nt, double dt, double eps, int nxi,
                      const double *dsyn, const double *omega,
                      const double *cshift, const double *Qobs, double S_obs,
-                     double *w2_out, double *adj)
+                     int squared, double *w2_out, double *adj)
 {
     double *y = malloc(sizeof(double) * nt), *p = malloc(sizeof(double) * nt);
     double *F = malloc(sizeof(double) * nt), *Q = malloc(sizeof(double) * nxi);
@@ -407,11 +407,14 @@ double orc_w2_misfit(int ntr, int nt, double dt, double eps, int nxi,
         orc_cdf(nt, dt, eps, y, p, F, &Z);
         orc_quantiles(nt, dt, nxi, F, Q, ks);
         double W2 = orc_w2_from_quantiles(nxi, Q, Qo);
-        if (w2_out) w2_out[tr] = W2;
-        J += W2 / S_obs;
+        /* squared: the raw baseline objective sum W2^2 / sum int |Qobs|^2
+         * (Sec. 6.3, Baseline 1), S_obs then holding the denominator */
+        double term = squared ? W2 * W2 : W2;
+        if (w2_out) w2_out[tr] = term;
+        J += term / S_obs;
         if (!adj) continue;
         double *a = adj + (size_t)tr * nt;
-        if (W2 == 0.0) {   /* reading C-10: non-differentiable point, take 0 */
+        if (!squared && W2 == 0.0) {   /* reading C-10: non-differentiable point, take 0 */
             for (int t = 0; t < nt; ++t) a[t] = 0.0;
             continue;
         }
@@ -420,7 +423,8 @@ double orc_w2_misfit(int ntr, int nt, double dt, double eps, int nxi,
             int kk = ks[j];
             if (kk == 0 || kk == nt) continue;   /* clamped quantile */
             double xi = (double)j * dxi;
-            double qbar = dxi * xi_weight(j, nxi) * (Q[j] - Qo[j]) / (W2 * S_obs);
+            double qbar = squared ? 2.0 * dxi * xi_weight(j, nxi) * (Q[j] - Qo[j]) / S_obs
+                                  : dxi * xi_weight(j, nxi) * (Q[j] - Qo[j]) / (W2 * S_obs);
             double D = F[kk] - F[kk - 1];
             Fbar[kk - 1] += qbar * dt * (xi - F[kk]) / (D * D);
             Fbar[kk] += qbar * (-dt * (xi - F[kk - 1]) / (D * D));
@@ -482,4 +486,109 @@ double orc_guided_step(int nz, int nx, double rho0, double c, double tau,
         vout[i] = vprime[i] - rho * kap * h[i];
     }
     return rho;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Least-squares potential of the DPS baseline (Sec. 4.2, Baseline 3):
+ *   J = (1/2) sum (d_syn - d_obs)^2 / sigma^2,  adj = dJ/dd_syn = (d_syn - d_obs) / sigma^2
+ * over n samples of one instance.  Returns J. */
+double orc_l2_misfit(long n, double sigma2, const double *dobs, const double *dsyn,
+                     double *adj)
+{
+    double J = 0.0;
+    for (long i = 0; i < n; ++i) {
+        double r = dsyn[i] - dobs[i];
+        J += 0.5 * r * r / sigma2;
+        if (adj) adj[i] = r / sigma2;
+    }
+    return J;
+}
+
+/* Total variation of the normalised field u = v / unit (Eq. tv, forward
+ * differences, a difference leaving the grid counts as 0, divided by
+ * N_g = nz nx) and h = g + alpha dTV(v / unit)/dv, the subgradient taking
+ * sign(0) = 0 (the (sub)gradient steps of Baselines 1 and 2).  Returns TV. */
+double orc_tv_grad(int nz, int nx, double alpha, double unit, const double *v,
+                   const double *g, double *h)
+{
+    size_t n = (size_t)nz * nx;
+    double ng = (double)n, tv = 0.0;
+    for (size_t i = 0; i < n; ++i) h[i] = g ? g[i] : 0.0;
+    for (int iz = 0; iz < nz; ++iz)
+        for (int ix = 0; ix < nx; ++ix) {
+            size_t i = IDX(iz, ix, nx);
+            if (ix + 1 < nx) {
+                double d = (v[i + 1] - v[i]) / unit;
+                double sg = d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0);
+                tv += fabs(d);
+                h[i + 1] += alpha * sg / (ng * unit);
+                h[i] -= alpha * sg / (ng * unit);
+            }
+            if (iz + 1 < nz) {
+                size_t k = IDX(iz + 1, ix, nx);
+                double d = (v[k] - v[i]) / unit;
+                double sg = d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0);
+                tv += fabs(d);
+                h[k] += alpha * sg / (ng * unit);
+                h[i] -= alpha * sg / (ng * unit);
+            }
+        }
+    return tv / ng;
+}
+
+/* Reconstruction measures of Sec. 6.3 between a true and a reconstructed
+ * field (nz x nx):
+ *   out[0] = ||v_true - v_rec||_2 / ||v_true||_2
+ *   out[1] = PSNR = 10 log10(R^2 / mean (v_true - v_rec)^2)   (R = data range)
+ *   out[2] = SSIM: mean over every 11 x 11 window lying inside the grid of
+ *            (2 mu_t mu_r + C1)(2 s_tr + C2) / ((mu_t^2 + mu_r^2 + C1)(s_t^2 + s_r^2 + C2)),
+ *            window weights exp(-(a^2 + b^2) / (2 1.5^2)) normalised to sum 1,
+ *            weighted means, variances and covariance, C1 = (0.01 R)^2,
+ *            C2 = (0.03 R)^2 (Wang et al. 2004); NAN when the grid is
+ *            smaller than a window */
+void orc_image_metrics(int nz, int nx, double R, const double *vt, const double *vr,
+                       double *out)
+{
+    size_t n = (size_t)nz * nx;
+    double se = 0.0, st = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        double e = vt[i] - vr[i];
+        se += e * e;
+        st += vt[i] * vt[i];
+    }
+    out[0] = sqrt(se) / sqrt(st);
+    out[1] = 10.0 * log10(R * R / (se / (double)n));
+    const int W = 11, H = 5;
+    double w[11][11], ws = 0.0;
+    for (int a = 0; a < W; ++a)
+        for (int b = 0; b < W; ++b) {
+            w[a][b] = exp(-((double)(a - H) * (a - H) + (double)(b - H) * (b - H)) / (2.0 * 1.5 * 1.5));
+            ws += w[a][b];
+        }
+    for (int a = 0; a < W; ++a)
+        for (int b = 0; b < W; ++b) w[a][b] /= ws;
+    double C1 = (0.01 * R) * (0.01 * R), C2 = (0.03 * R) * (0.03 * R);
+    double sum = 0.0;
+    long cnt = 0;
+    for (int i = 0; i + W <= nz; ++i)
+        for (int j = 0; j + W <= nx; ++j) {
+            double mt = 0.0, mr = 0.0;
+            for (int a = 0; a < W; ++a)
+                for (int b = 0; b < W; ++b) {
+                    mt += w[a][b] * vt[IDX(i + a, j + b, nx)];
+                    mr += w[a][b] * vr[IDX(i + a, j + b, nx)];
+                }
+            double vtt = 0.0, vrr = 0.0, vtr = 0.0;
+            for (int a = 0; a < W; ++a)
+                for (int b = 0; b < W; ++b) {
+                    double dt_ = vt[IDX(i + a, j + b, nx)] - mt, dr = vr[IDX(i + a, j + b, nx)] - mr;
+                    vtt += w[a][b] * dt_ * dt_;
+                    vrr += w[a][b] * dr * dr;
+                    vtr += w[a][b] * dt_ * dr;
+                }
+            sum += (2.0 * mt * mr + C1) * (2.0 * vtr + C2) /
+                   ((mt * mt + mr * mr + C1) * (vtt + vrr + C2));
+            ++cnt;
+        }
+    out[2] = cnt ? sum / (double)cnt : NAN;
 }

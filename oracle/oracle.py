@@ -71,7 +71,12 @@ def lib():
         L.orc_w2_prepare.restype = d
         L.orc_w2_prepare.argtypes = [i, i, d, d, d, d, i, _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_w2_misfit.restype = d
-        L.orc_w2_misfit.argtypes = [i, i, d, d, i, _dp, _dp, _dp, _dp, d, _dp, _dp]
+        L.orc_w2_misfit.argtypes = [i, i, d, d, i, _dp, _dp, _dp, _dp, d, i, _dp, _dp]
+        L.orc_l2_misfit.restype = d
+        L.orc_l2_misfit.argtypes = [ctypes.c_long, d, _dp, _dp, _dp]
+        L.orc_tv_grad.restype = d
+        L.orc_tv_grad.argtypes = [i, i, d, d, _dp, _dp, _dp]
+        L.orc_image_metrics.argtypes = [i, i, d, _dp, _dp, _dp]
         L.orc_guided_step.restype = d
         L.orc_guided_step.argtypes = [i, i, d, d, d, d, d, d, d, _dp, _dp, _dp, _dp, _dp]
         _lib = L
@@ -144,6 +149,9 @@ class W2Params:
     cshift_factor: float = 1.1
     eps_density: float = 1e-9
     n_xi: int = 1000
+    # False: J = sum W2 / S_obs (Eq. final_objective); True: the raw baseline
+    # J = sum W2^2 / sum int |Q_obs|^2 (Sec. 6.3, Baseline 1; use with k = 0)
+    squared: bool = False
 
 
 @dataclasses.dataclass
@@ -271,6 +279,7 @@ class ObsContext:
     s_tr: np.ndarray      # [B][ns][nr]
     S_obs: np.ndarray     # [B]
     M: np.ndarray         # [B]
+    S2: np.ndarray = None  # [B] sum of s_tr^2 (denominator of the squared objective)
 
 
 def w2_prepare(d_obs, dt, w2p: W2Params) -> ObsContext:
@@ -289,7 +298,11 @@ def w2_prepare(d_obs, dt, w2p: W2Params) -> ObsContext:
                                     w2p.n_xi, _p(d_obs[b]), _p(om[b]), _p(cs[b]), _p(Q[b]),
                                     _p(s_tr[b]), ctypes.byref(m))
         M[b] = m.value
-    return ObsContext(om, cs, Q, s_tr, S, M)
+    return ObsContext(om, cs, Q, s_tr, S, M, (s_tr ** 2).sum(axis=(1, 2)))
+
+
+def _denominator(ctx: ObsContext, w2p: W2Params, b: int) -> float:
+    return float(ctx.S2[b] if w2p.squared else ctx.S_obs[b])
 
 
 def w2_misfit(ctx: ObsContext, d_syn, dt, w2p: W2Params, with_adjoint=True):
@@ -302,7 +315,7 @@ def w2_misfit(ctx: ObsContext, d_syn, dt, w2p: W2Params, with_adjoint=True):
     for b in range(B):
         J[b] = lib().orc_w2_misfit(ns * nr, nt, dt, w2p.eps_density, w2p.n_xi, _p(d_syn[b]),
                                    _p(ctx.omega[b]), _p(ctx.cshift[b]), _p(ctx.Qobs[b]),
-                                   float(ctx.S_obs[b]), _p(w2[b]),
+                                   _denominator(ctx, w2p, b), int(w2p.squared), _p(w2[b]),
                                    _p(adj[b]) if with_adjoint else None)
     return J, w2, adj
 
@@ -347,8 +360,8 @@ def gradient(prob: Problem, v, ctx: ObsContext, w2p: W2Params, threads: int | No
         adj = np.empty_like(d)
         Jp[b, s] = lib().orc_w2_misfit(prob.nr, prob.nt, prob.dt, w2p.eps_density, w2p.n_xi,
                                        _p(d), _p(_f64(ctx.omega[b, s])), _p(_f64(ctx.cshift[b, s])),
-                                       _p(_f64(ctx.Qobs[b, s])), float(ctx.S_obs[b]),
-                                       _p(w2[b, s]), _p(adj))
+                                       _p(_f64(ctx.Qobs[b, s])), _denominator(ctx, w2p, b),
+                                       int(w2p.squared), _p(w2[b, s]), _p(adj))
         gpad = adjoint_shot(prob, v[b], s, adj, u_all)
         gp[b, s] = fold(prob, gpad)
 
@@ -370,3 +383,39 @@ def guided_step(vprime, v0hat, g, h, gp: GuideParams):
                                        gp.kappa_min, gp.kappa_max, _p(vprime[b]), _p(v0hat[b]),
                                        _p(g[b]), _p(h[b]), _p(vout[b]))
     return vout, rho
+
+
+# --------------------------------------------------------------------------- baselines, measures
+
+def l2_misfit(d_obs, d_syn, sigma=1.0):
+    """Least-squares potential per instance: (J [B], adj [B][...])."""
+    d_obs, d_syn = _f64(d_obs), _f64(d_syn)
+    B = d_syn.shape[0]
+    n = d_syn[0].size
+    J = np.empty(B)
+    adj = np.empty_like(d_syn)
+    for b in range(B):
+        J[b] = lib().orc_l2_misfit(n, float(sigma) ** 2, _p(d_obs[b]), _p(d_syn[b]), _p(adj[b]))
+    return J, adj
+
+
+def tv_grad(v, g, alpha, unit=1.0):
+    """(TV of v / unit [B], h = g + alpha dTV(v / unit)/dv [B][nz][nx])."""
+    v = _f64(v)
+    g = _f64(g) if g is not None else np.zeros_like(v)
+    B, nz, nx = v.shape
+    h = np.empty_like(v)
+    tv = np.empty(B)
+    for b in range(B):
+        tv[b] = lib().orc_tv_grad(nz, nx, float(alpha), float(unit), _p(v[b]), _p(g[b]), _p(h[b]))
+    return tv, h
+
+
+def image_metrics(v_true, v_rec, data_range):
+    """[B][3]: relative l2 error, PSNR (dB), SSIM."""
+    vt, vr = _f64(v_true), _f64(v_rec)
+    B, nz, nx = vt.shape
+    out = np.empty((B, 3))
+    for b in range(B):
+        lib().orc_image_metrics(nz, nx, float(data_range), _p(vt[b]), _p(vr[b]), _p(out[b]))
+    return out

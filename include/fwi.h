@@ -105,6 +105,10 @@ typedef struct fwi_w2_params {
     double cshift_factor; /* c' = cshift_factor |min_t omega d_obs|, >= 0           */
     double eps_density;  /* eps' in the density denominator, >= 0                   */
     int n_xi;            /* quantile nodes xi_j = j/(n_xi-1), >= 2                  */
+    int squared;         /* 0: J = sum W2 / S_obs (Eq. final_objective); 1: the raw
+                            objective of the W2+TV baseline (Sec. 6.3, Baseline 1),
+                            J = sum W2^2 / sum int_0^1 |Q_obs|^2, per-trace output W2^2
+                            (pass k = 0 for its unenhanced traces)                  */
 } fwi_w2_params;
 
 /* Guided-step hyperparameters (Eq. rho, Eq. kappa; Sec. 6.3: c = 0.1, tau = 0,
@@ -218,6 +222,44 @@ FWI_API fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const 
 FWI_API fwi_status fwi_guided_step(int batch, int nz, int nx, const fwi_guide_params *params,
                            const float *v_prime, const float *v0hat, const float *g,
                            const float *h, float *v_out, float *rho_out, void *stream);
+
+/* Least-squares data potential of the DPS baseline (Phi_l2 of Eq.
+ * dps_baseline_step, Sec. 4.2; Baseline 3 of Sec. 6.3), per instance b:
+ *   J[b]    = (1/2) sum_{s,r,t} (d_syn - d_obs)^2 / sigma^2
+ *   adj_src = dJ/dd_syn = (d_syn - d_obs) / sigma^2   (the adjoint source of
+ *             fwi_adjoint_grad for this potential)
+ *   plan    gives the sizes B, ns, nr, nt
+ *   d_obs, d_syn [B][ns][nr][nt] device; J [B] device, written;
+ *   adj_src [B][ns][nr][nt] device, written, or NULL; sigma finite, > 0.
+ * Errors: FWI_ERR_INVALID_ARG before any launch, FWI_ERR_CUDA. */
+FWI_API fwi_status fwi_l2_misfit(const fwi_plan *plan, const float *d_obs, const float *d_syn,
+                                 double sigma, float *J, float *adj_src, void *stream);
+
+/* Total variation of Eq. tv on the field v / unit (forward differences, a
+ * difference leaving the grid counts as 0, divided by N_g = nz nx) and the
+ * (sub)gradient step direction of the TV-regularised baselines (Sec. 6.3,
+ * Baselines 1 and 2):
+ *   h  = g + alpha dTV(v / unit)/dv,  taking sign(0) = 0 for a tie
+ *   tv[b] = TV(v_b / unit)
+ *   v, g, h [batch][nz][nx] device (g may be NULL: taken as 0; h may alias g);
+ *   tv [batch] device or NULL; alpha finite, unit > 0.
+ * Errors: FWI_ERR_INVALID_ARG, FWI_ERR_UNSUPPORTED (grid above 2^30 cells),
+ * FWI_ERR_CUDA. */
+FWI_API fwi_status fwi_tv_grad(int batch, int nz, int nx, double alpha, double unit,
+                               const float *v, const float *g, float *h, float *tv,
+                               void *stream);
+
+/* Reconstruction measures of Sec. 6.3 per instance, out[b][3]:
+ *   [0] ||v_true - v_rec||_2 / ||v_true||_2
+ *   [1] PSNR = 10 log10(R^2 / mean (v_true - v_rec)^2), R = data_range
+ *   [2] SSIM averaged over every 11 x 11 window inside the grid, Gaussian
+ *       weights (sigma 1.5) normalised to 1, C1 = (0.01 R)^2, C2 = (0.03 R)^2;
+ *       NaN if the grid is smaller than a window
+ *   v_true, v_rec [batch][nz][nx] device; out [batch][3] device, written.
+ * Errors: FWI_ERR_INVALID_ARG, FWI_ERR_UNSUPPORTED, FWI_ERR_CUDA. */
+FWI_API fwi_status fwi_image_metrics(int batch, int nz, int nx, double data_range,
+                                     const float *v_true, const float *v_rec, float *out,
+                                     void *stream);
 
 /* Largest batch x ns x nr that fwi_w2_misfit_static accepts. */
 #define FWI_STATIC_MAX_TRACES 65536

@@ -7,7 +7,7 @@ without loading the CUDA library.
 """
 import importlib
 
-__all__ = ["api", "inputs", "autograd"]
+__all__ = ["api", "inputs", "autograd", "baselines"]
 
 
 def __getattr__(name):

@@ -53,7 +53,8 @@ class _Problem(ctypes.Structure):
 
 class _W2(ctypes.Structure):
     _fields_ = [("k", ctypes.c_double), ("cshift_factor", ctypes.c_double),
-                ("eps_density", ctypes.c_double), ("n_xi", ctypes.c_int)]
+                ("eps_density", ctypes.c_double), ("n_xi", ctypes.c_int),
+                ("squared", ctypes.c_int)]
 
 
 class _Guide(ctypes.Structure):
@@ -84,6 +85,14 @@ _lib.fwi_guided_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(_Guide)] + [_vp] * 7
 _lib.fwi_w2_misfit_static.restype = _S
 _lib.fwi_w2_misfit_static.argtypes = [_vp] * 7
+_lib.fwi_l2_misfit.restype = _S
+_lib.fwi_l2_misfit.argtypes = [_vp, _vp, _vp, ctypes.c_double, _vp, _vp, _vp]
+_lib.fwi_tv_grad.restype = _S
+_lib.fwi_tv_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                             ctypes.c_double, _vp, _vp, _vp, _vp, _vp]
+_lib.fwi_image_metrics.restype = _S
+_lib.fwi_image_metrics.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                   _vp, _vp, _vp, _vp]
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -160,6 +169,7 @@ class W2Params:
     cshift_factor: float = 1.1
     eps_density: float = 1e-9
     n_xi: int = 1000
+    squared: bool = False   # True: sum W2^2 / sum |Q_obs|^2 (W2+TV baseline; use k = 0)
 
 
 @dataclasses.dataclass
@@ -224,7 +234,7 @@ def fwi_plan_create(prob: Problem, w2: W2Params) -> _Handle:
                   prob.checkpoint_every)
     if len(prob.src_iz) != len(prob.src_ix) or len(prob.rec_iz) != len(prob.rec_ix):
         raise ValueError("source/receiver index lists differ in length")
-    cw = _W2(w2.k, w2.cshift_factor, w2.eps_density, w2.n_xi)
+    cw = _W2(w2.k, w2.cshift_factor, w2.eps_density, w2.n_xi, int(w2.squared))
     out = _vp()
     _check(_lib.fwi_plan_create(ctypes.byref(cp), ctypes.byref(cw), ctypes.byref(out)))
     return _Handle(out)
@@ -268,6 +278,21 @@ def fwi_guided_step(batch, nz, nx, params: GuideParams, v_prime, v0hat, g, h, v_
     gp = params._c()
     _check(_lib.fwi_guided_step(batch, nz, nx, ctypes.byref(gp), _ptr(v_prime), _ptr(v0hat),
                                 _ptr(g), _ptr(h), _ptr(v_out), _ptr(rho_out), _stream(stream)))
+
+
+def fwi_l2_misfit(plan, d_obs, d_syn, sigma, J, adj_src, stream=None):
+    _check(_lib.fwi_l2_misfit(plan.raw, _ptr(d_obs), _ptr(d_syn), ctypes.c_double(sigma),
+                              _ptr(J), _ptr(adj_src), _stream(stream)))
+
+
+def fwi_tv_grad(batch, nz, nx, alpha, unit, v, g, h, tv, stream=None):
+    _check(_lib.fwi_tv_grad(batch, nz, nx, ctypes.c_double(alpha), ctypes.c_double(unit),
+                            _ptr(v), _ptr(g), _ptr(h), _ptr(tv), _stream(stream)))
+
+
+def fwi_image_metrics(batch, nz, nx, data_range, v_true, v_rec, out, stream=None):
+    _check(_lib.fwi_image_metrics(batch, nz, nx, ctypes.c_double(data_range), _ptr(v_true),
+                                  _ptr(v_rec), _ptr(out), _stream(stream)))
 
 
 def fwi_check(plan, workspace, stream=None):
@@ -336,6 +361,16 @@ class Plan:
         fwi_w2_misfit(self.handle, ctx, d_syn, J, w2, adj, self.workspace, stream)
         return J, w2, adj
 
+    def l2_misfit(self, d_obs, d_syn, sigma=1.0, want_adj=True, stream=None):
+        """Least-squares potential (J [B], adj or None) of the DPS baseline."""
+        _f32(d_obs, self.data_shape, "d_obs")
+        _f32(d_syn, self.data_shape, "d_syn")
+        J = torch.empty(self.prob.batch, dtype=torch.float32, device=self.device)
+        adj = torch.empty(self.data_shape, dtype=torch.float32,
+                          device=self.device) if want_adj else None
+        fwi_l2_misfit(self.handle, d_obs, d_syn, sigma, J, adj, stream)
+        return J, adj
+
     def adjoint_grad(self, v, adj, grad=None, stream=None):
         _f32(v, self.model_shape, "v")
         _f32(adj, self.data_shape, "adj")
@@ -375,3 +410,25 @@ def guided_step(v_prime, v0hat, g, h, params: GuideParams, v_out=None, stream=No
     rho = torch.empty(B, dtype=torch.float32, device=v_prime.device)
     fwi_guided_step(B, nz, nx, params, v_prime, v0hat, g, h, v_out, rho, stream)
     return v_out, rho
+
+
+def tv_grad(v, g=None, alpha=1.0, unit=1.0, stream=None):
+    """(h = g + alpha dTV(v / unit)/dv, TV(v / unit) [B]) on [B][nz][nx] tensors."""
+    B, nz, nx = v.shape
+    _f32(v, (B, nz, nx), "v")
+    if g is not None:
+        _f32(g, (B, nz, nx), "g")
+    h = torch.empty_like(v)
+    tv = torch.empty(B, dtype=torch.float32, device=v.device)
+    fwi_tv_grad(B, nz, nx, alpha, unit, v, g, h, tv, stream)
+    return h, tv
+
+
+def image_metrics(v_true, v_rec, data_range, stream=None):
+    """[B][3]: relative l2 error, PSNR (dB), SSIM (Sec. 6.3)."""
+    B, nz, nx = v_true.shape
+    _f32(v_true, (B, nz, nx), "v_true")
+    _f32(v_rec, (B, nz, nx), "v_rec")
+    out = torch.empty((B, 3), dtype=torch.float32, device=v_true.device)
+    fwi_image_metrics(B, nz, nx, data_range, v_true, v_rec, out, stream)
+    return out

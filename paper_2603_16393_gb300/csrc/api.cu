@@ -89,6 +89,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         return fail(FWI_ERR_INVALID_ARG, "cshift_factor must be >= 0");
     if (!(w2->eps_density >= 0.0) || !std::isfinite(w2->eps_density))
         return fail(FWI_ERR_INVALID_ARG, "eps_density must be >= 0");
+    if (w2->squared != 0 && w2->squared != 1) return fail(FWI_ERR_INVALID_ARG, "squared must be 0 or 1");
     // leapfrog + 4th-order Laplacian: |symbol| <= 16/3 per axis => C <= sqrt(3)/2
     const double cfl = (double)p.v_max * p.dt *
                        std::sqrt(1.0 / ((double)p.dx * p.dx) + 1.0 / ((double)p.dz * p.dz));
@@ -268,6 +269,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     o = 0;
     pl->ctx_M = o;      o += align_up(B * 4);
     pl->ctx_S = o;      o += align_up(B * 4);
+    pl->ctx_S2 = o;     o += align_up(B * 4);
     pl->ctx_cshift = o; o += align_up(B * ntr * 4);
     pl->ctx_str = o;    o += align_up(B * ntr * 4);
     pl->ctx_omega = o;  o += align_up(B * ntr * p.nt * 4);

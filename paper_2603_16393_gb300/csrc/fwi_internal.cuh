@@ -56,7 +56,7 @@ struct Plan {
     int nzs;                   // rows of one wavefield-record plane (>= NZ)
     // byte offsets inside the caller buffers
     size_t ws_w2, ws_gshot, ws_bytes;
-    size_t ctx_M, ctx_S, ctx_cshift, ctx_str, ctx_omega, ctx_Qb, ctx_Qf, ctx_bytes;
+    size_t ctx_M, ctx_S, ctx_S2, ctx_cshift, ctx_str, ctx_omega, ctx_Qb, ctx_Qf, ctx_bytes;
     size_t snap_bytes;
     // checkpoint + recompute: every ckpt_every steps (0: store-all record)
     int ckpt_every, nslot;

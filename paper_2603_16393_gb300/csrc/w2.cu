@@ -234,7 +234,8 @@ __device__ __forceinline__ int lower_bound_i(const int *a, int n, int x)
 
 struct CtxPtrs {
     float *M;        // [B]
-    float *S;        // [B]
+    float *S;        // [B] sum of s_tr (Eq. final_objective denominator)
+    float *S2;       // [B] sum of s_tr^2 (the squared raw objective's denominator)
     float *cshift;   // [B][ntr]
     float *s_tr;     // [B][ntr]
     float *omega;    // [B][ntr][nt]
@@ -247,6 +248,7 @@ inline CtxPtrs ctx_ptrs(const Plan &pl, unsigned char *ctx)
     CtxPtrs c;
     c.M = (float *)(ctx + pl.ctx_M);
     c.S = (float *)(ctx + pl.ctx_S);
+    c.S2 = (float *)(ctx + pl.ctx_S2);
     c.cshift = (float *)(ctx + pl.ctx_cshift);
     c.s_tr = (float *)(ctx + pl.ctx_str);
     c.omega = (float *)(ctx + pl.ctx_omega);
@@ -258,6 +260,7 @@ inline CtxPtrs ctx_ptrs(const Plan &pl, unsigned char *ctx)
 struct W2Args {
     int nt, nxi, ntr;           // ntr = ns * nr traces per instance
     float dt, k, cfac, eps2dt;  // eps2dt = 2 eps' / dt
+    int squared;                // J = sum W2^2 / S2 instead of sum W2 / S
     CtxPtrs c;
 };
 
@@ -364,7 +367,8 @@ __global__ void __launch_bounds__(NT_W2) k_obs_trace(const float *__restrict__ d
     if (threadIdx.x == 0) a.c.s_tr[tr_g] = sqrtf(s2 / (float)(a.nxi - 1));
 }
 
-// out[b] = sum_i v[b][i] (fixed order), divided by div[b] if given
+// out[b] = sum_i v[b][i] (SQ: v^2; fixed order), divided by div[b] if given
+template <bool SQ>
 __global__ void __launch_bounds__(NT_W2) k_sum_traces(const float *__restrict__ v, int ntr,
                                                       const float *__restrict__ div,
                                                       float *__restrict__ out)
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(NT_W2) k_sum_traces(const float *__restrict__ 
     __shared__ float red[NW_W2 + 2];
     const float *vb = v + (size_t)blockIdx.x * ntr;
     float part = 0.f;
-    for (int i = threadIdx.x; i < ntr; i += NT_W2) part += vb[i];
+    for (int i = threadIdx.x; i < ntr; i += NT_W2) part += SQ ? vb[i] * vb[i] : vb[i];
     const float s = block_reduce<0, NT_W2>(part, red);
     if (threadIdx.x == 0) out[blockIdx.x] = div ? s / div[blockIdx.x] : s;
 }
@@ -414,15 +418,17 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
         part += wj * diff * diff;
     }
     const float dxi = 1.f / (float)(nxi - 1);
-    const float W2 = sqrtf(dxi * block_reduce<0, NT_W2>(part, redf));
-    if (threadIdx.x == 0) w2_dst[tr_g] = W2;
+    const float W2sq = dxi * block_reduce<0, NT_W2>(part, redf);
+    const float W2 = sqrtf(W2sq);
+    if (threadIdx.x == 0) w2_dst[tr_g] = a.squared ? W2sq : W2;
     if (!adj) return;
     float *ad = adj + (size_t)tr_g * nt;
-    if (W2 == 0.f) {   // non-differentiable point: zero adjoint source
+    if (W2 == 0.f) {   // W2 (non-differentiable there) or W2^2 (derivative 0): zero
         for (int i = threadIdx.x; i < nt; i += NT_W2) ad[i] = 0.f;
         return;
     }
-    const float scale = dxi / (W2 * a.c.S[b]);
+    // dJ/dQ_j = scale w_j (Q_j - Qobs_j)
+    const float scale = a.squared ? 2.f * dxi / a.c.S2[b] : dxi / (W2 * a.c.S[b]);
     df cpart = {0.f, 0.f};
     for (int j = threadIdx.x; j < nxi; j += NT_W2) {
         const int k = ks[j];
@@ -471,6 +477,7 @@ W2Args make_w2(const Plan &pl, unsigned char *ctx)
     a.k = (float)pl.w2.k;
     a.cfac = (float)pl.w2.cshift_factor;
     a.eps2dt = (float)(2.0 * (double)pl.w2.eps_density / (double)pl.p.dt);
+    a.squared = pl.w2.squared;
     a.c = ctx_ptrs(pl, ctx);
     return a;
 }
@@ -496,7 +503,8 @@ cudaError_t launch_w2_prepare(const Plan &pl, const float *d_obs, unsigned char 
                                          (int)sm);
     if (e != cudaSuccess) return e;
     k_obs_trace<<<B * a.ntr, NT_W2, sm, st>>>(d_obs, a);
-    k_sum_traces<<<B, NT_W2, 0, st>>>(a.c.s_tr, a.ntr, nullptr, a.c.S);
+    k_sum_traces<false><<<B, NT_W2, 0, st>>>(a.c.s_tr, a.ntr, nullptr, a.c.S);
+    k_sum_traces<true><<<B, NT_W2, 0, st>>>(a.c.s_tr, a.ntr, nullptr, a.c.S2);
     return cudaGetLastError();
 }
 
@@ -512,7 +520,7 @@ cudaError_t launch_w2_misfit(const Plan &pl, const unsigned char *ctx, const flo
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_misfit_trace<<<B * a.ntr, NT_W2, sm, st>>>(d_syn, a, w2d, adj);
-    k_sum_traces<<<B, NT_W2, 0, st>>>(w2d, a.ntr, a.c.S, J);
+    k_sum_traces<false><<<B, NT_W2, 0, st>>>(w2d, a.ntr, a.squared ? a.c.S2 : a.c.S, J);
     return cudaGetLastError();
 }
 

@@ -111,8 +111,19 @@ void orc_damping(int nz, int nx, int nb, double dz, double dx, double v_ref,
 }
 
 /* ------------------------------------------------------------------------ */
-/* 4th-order central second-derivative weights (-1/12, 4/3, -5/2, 4/3, -1/12). */
+/* Central second-derivative weights: 4th order (-1/12, 4/3, -5/2, 4/3, -1/12),
+ * the hot path's; 8th order (-1/560, 8/315, -1/5, 8/5, -205/72, ...), the
+ * space order of the paper's solver (Sec. 6.1). */
 static const double W4[5] = {-1.0 / 12.0, 4.0 / 3.0, -5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0};
+static const double W8[9] = {-1.0 / 560.0, 8.0 / 315.0, -1.0 / 5.0, 8.0 / 5.0, -205.0 / 72.0,
+                             8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+
+/* weights and radius of a space order (4 or 8) */
+static const double *stencil(int order, int *radius)
+{
+    *radius = order == 8 ? 4 : 2;
+    return order == 8 ? W8 : W4;
+}
 
 /* Value of u at (pz, px) with the boundary treatment of the padded grid:
  * outside left/right/bottom -> 0; above row 0 -> 0 (top_bc = 0) or the
@@ -130,17 +141,19 @@ static long ghost_map(int NZ, int NX, int top_bc, int pz, int px)
 }
 
 /* out = L u, gather form: out[p] = sum_q w(p,q) u[q]. */
-void orc_laplacian(int NZ, int NX, double dz, double dx, int top_bc,
+void orc_laplacian(int NZ, int NX, double dz, double dx, int top_bc, int order,
                    const double *u, double *out)
 {
+    int R;
+    const double *W = stencil(order, &R);
     for (int pz = 0; pz < NZ; ++pz)
         for (int px = 0; px < NX; ++px) {
             double s = 0.0;
-            for (int m = -2; m <= 2; ++m) {
+            for (int m = -R; m <= R; ++m) {
                 long qx = ghost_map(NZ, NX, top_bc, pz, px + m);
-                if (qx >= 0) s += W4[m + 2] * u[qx] / (dx * dx);
+                if (qx >= 0) s += W[m + R] * u[qx] / (dx * dx);
                 long qz = ghost_map(NZ, NX, top_bc, pz + m, px);
-                if (qz >= 0) s += W4[m + 2] * u[qz] / (dz * dz);
+                if (qz >= 0) s += W[m + R] * u[qz] / (dz * dz);
             }
             out[IDX(pz, px, NX)] = s;
         }
@@ -149,19 +162,21 @@ void orc_laplacian(int NZ, int NX, double dz, double dx, int top_bc,
 /* out = L^T w, scatter form of the very same stencil: every weight w(p,q)
  * used by orc_laplacian moves w[p] into out[q].  Equal to orc_laplacian for
  * top_bc = 0 (symmetric operator), different for top_bc = 1. */
-void orc_laplacian_T(int NZ, int NX, double dz, double dx, int top_bc,
+void orc_laplacian_T(int NZ, int NX, double dz, double dx, int top_bc, int order,
                      const double *w, double *out)
 {
+    int R;
+    const double *W = stencil(order, &R);
     size_t n = (size_t)NZ * NX;
     for (size_t i = 0; i < n; ++i) out[i] = 0.0;
     for (int pz = 0; pz < NZ; ++pz)
         for (int px = 0; px < NX; ++px) {
             double wp = w[IDX(pz, px, NX)];
-            for (int m = -2; m <= 2; ++m) {
+            for (int m = -R; m <= R; ++m) {
                 long qx = ghost_map(NZ, NX, top_bc, pz, px + m);
-                if (qx >= 0) out[qx] += W4[m + 2] * wp / (dx * dx);
+                if (qx >= 0) out[qx] += W[m + R] * wp / (dx * dx);
                 long qz = ghost_map(NZ, NX, top_bc, pz + m, px);
-                if (qz >= 0) out[qz] += W4[m + 2] * wp / (dz * dz);
+                if (qz >= 0) out[qz] += W[m + R] * wp / (dz * dz);
             }
         }
 }
@@ -173,7 +188,7 @@ void orc_laplacian_T(int NZ, int NX, double dz, double dx, int top_bc,
  *   kappa = vpad^2 dt^2, s^n = f[n]/(dx dz) at the source cell
  *   d[r][n] = u^{n+1} at receiver r   (restriction R, Sec. 2.1)
  * u_all (optional, (nt+1) x NZ x NX) receives u^0 .. u^nt. */
-void orc_forward_shot(int NZ, int NX, int top_bc, int nt, double dz, double dx,
+void orc_forward_shot(int NZ, int NX, int top_bc, int order, int nt, double dz, double dx,
                       double dt, const double *vpad, const double *eta,
                       const double *wavelet, int src_pz, int src_px,
                       int nrec, const int *rec_pz, const int *rec_px,
@@ -186,7 +201,7 @@ void orc_forward_shot(int NZ, int NX, int top_bc, int nt, double dz, double dx,
     double *lap = calloc(n, sizeof(double));
     if (u_all) memset(u_all, 0, n * sizeof(double));   /* u^0 */
     for (int it = 0; it < nt; ++it) {
-        orc_laplacian(NZ, NX, dz, dx, top_bc, u0, lap);
+        orc_laplacian(NZ, NX, dz, dx, top_bc, order, u0, lap);
         lap[IDX(src_pz, src_px, NX)] += wavelet[it] / (dx * dz);
         for (size_t i = 0; i < n; ++i) {
             double A = 1.0 / (1.0 + eta[i] * dt / 2.0);
@@ -210,7 +225,7 @@ void orc_forward_shot(int NZ, int NX, int top_bc, int nt, double dz, double dx,
  *   dJ/dkappa = sum_{n=0}^{nt-1} mu^{n+1} A (L u^n + s^n)
  *   dJ/dvpad  = dJ/dkappa * 2 vpad dt^2
  * adj is r = dJ/dd, nrec x nt; u_all holds u^0..u^{nt-1} from the forward. */
-void orc_adjoint_shot(int NZ, int NX, int top_bc, int nt, double dz, double dx,
+void orc_adjoint_shot(int NZ, int NX, int top_bc, int order, int nt, double dz, double dx,
                       double dt, const double *vpad, const double *eta,
                       const double *wavelet, int src_pz, int src_px,
                       int nrec, const int *rec_pz, const int *rec_px,
@@ -230,7 +245,7 @@ void orc_adjoint_shot(int NZ, int NX, int top_bc, int nt, double dz, double dx,
             double kappa = vpad[i] * vpad[i] * dt * dt;
             tmp[i] = kappa * A * mu1[i];
         }
-        orc_laplacian_T(NZ, NX, dz, dx, top_bc, tmp, ltmp);
+        orc_laplacian_T(NZ, NX, dz, dx, top_bc, order, tmp, ltmp);
         for (size_t i = 0; i < n; ++i) {
             double A = 1.0 / (1.0 + eta[i] * dt / 2.0);
             double B = 1.0 - eta[i] * dt / 2.0;
@@ -239,7 +254,7 @@ void orc_adjoint_shot(int NZ, int NX, int top_bc, int nt, double dz, double dx,
         for (int r = 0; r < nrec; ++r)
             mu[IDX(rec_pz[r], rec_px[r], NX)] += adj[(size_t)r * nt + (m - 1)];
         /* imaging term for forward step n = m-1 */
-        orc_laplacian(NZ, NX, dz, dx, top_bc, u_all + (size_t)(m - 1) * n, lu);
+        orc_laplacian(NZ, NX, dz, dx, top_bc, order, u_all + (size_t)(m - 1) * n, lu);
         lu[IDX(src_pz, src_px, NX)] += wavelet[m - 1] / (dx * dz);
         for (size_t i = 0; i < n; ++i) {
             double A = 1.0 / (1.0 + eta[i] * dt / 2.0);

@@ -56,11 +56,11 @@ def lib():
         L.orc_pad_model.argtypes = [i, i, i, _dp, _dp]
         L.orc_fold_add.argtypes = [i, i, i, _dp, _dp]
         L.orc_damping.argtypes = [i, i, i, d, d, d, d, _dp]
-        L.orc_laplacian.argtypes = [i, i, d, d, i, _dp, _dp]
-        L.orc_laplacian_T.argtypes = [i, i, d, d, i, _dp, _dp]
-        L.orc_forward_shot.argtypes = [i, i, i, i, d, d, d, _dp, _dp, _dp, i, i,
+        L.orc_laplacian.argtypes = [i, i, d, d, i, i, _dp, _dp]
+        L.orc_laplacian_T.argtypes = [i, i, d, d, i, i, _dp, _dp]
+        L.orc_forward_shot.argtypes = [i, i, i, i, i, d, d, d, _dp, _dp, _dp, i, i,
                                        i, _ip, _ip, _dp, _dp]
-        L.orc_adjoint_shot.argtypes = [i, i, i, i, d, d, d, _dp, _dp, _dp, i, i,
+        L.orc_adjoint_shot.argtypes = [i, i, i, i, i, d, d, d, _dp, _dp, _dp, i, i,
                                        i, _ip, _ip, _dp, _dp, _dp]
         L.orc_cdf.argtypes = [i, d, d, _dp, _dp, _dp, _dp]
         L.orc_quantiles.argtypes = [i, d, i, _dp, _dp, _ip]
@@ -119,6 +119,7 @@ class Problem:
     v_ref: float = 4500.0
     refl_R: float = 1e-3
     top_bc: int = 0
+    space_order: int = 4      # 4 (the hot path) or 8 (the paper's solver, Sec. 6.1)
 
     @property
     def NZ(self):
@@ -199,11 +200,11 @@ def damping(prob: Problem) -> np.ndarray:
     return eta
 
 
-def laplacian(u, dz, dx, top_bc=0, transpose=False) -> np.ndarray:
+def laplacian(u, dz, dx, top_bc=0, transpose=False, order=4) -> np.ndarray:
     u = _f64(u)
     out = np.empty_like(u)
     fn = lib().orc_laplacian_T if transpose else lib().orc_laplacian
-    fn(u.shape[0], u.shape[1], dz, dx, top_bc, _p(u), _p(out))
+    fn(u.shape[0], u.shape[1], dz, dx, top_bc, order, _p(u), _p(out))
     return out
 
 
@@ -226,7 +227,8 @@ def forward_shot(prob: Problem, v, s: int, keep_wavefield: bool = False,
                                                     np.ascontiguousarray(rec[1], dtype=np.int32))
     d = np.empty((len(rz), prob.nt))
     u_all = np.empty((prob.nt + 1, prob.NZ, prob.NX)) if keep_wavefield else None
-    lib().orc_forward_shot(prob.NZ, prob.NX, prob.top_bc, prob.nt, prob.dz, prob.dx, prob.dt,
+    lib().orc_forward_shot(prob.NZ, prob.NX, prob.top_bc, prob.space_order, prob.nt, prob.dz,
+                           prob.dx, prob.dt,
                            _p(vpad), _p(eta), _p(f), int(prob.src_iz[s]),
                            int(prob.src_ix[s]) + prob.nb, len(rz), _p(rz), _p(rx),
                            _p(d), _p(u_all))
@@ -242,7 +244,8 @@ def adjoint_shot(prob: Problem, v, s: int, adj, u_all, wavelet=None, rec=None) -
                                                     np.ascontiguousarray(rec[1], dtype=np.int32))
     adj = _f64(adj)
     g = np.empty((prob.NZ, prob.NX))
-    lib().orc_adjoint_shot(prob.NZ, prob.NX, prob.top_bc, prob.nt, prob.dz, prob.dx, prob.dt,
+    lib().orc_adjoint_shot(prob.NZ, prob.NX, prob.top_bc, prob.space_order, prob.nt, prob.dz,
+                           prob.dx, prob.dt,
                            _p(vpad), _p(eta), _p(f), int(prob.src_iz[s]),
                            int(prob.src_ix[s]) + prob.nb, len(rz), _p(rz), _p(rx),
                            _p(adj), _p(_f64(u_all)), _p(g))

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 10100  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 10200  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -96,6 +96,9 @@ typedef struct fwi_problem {
                             steps and fwi_adjoint_grad recomputes each K-step segment
                             from it (same arithmetic, bitwise-identical gradient,
                             about nt/K times less memory, one extra forward pass) */
+    int space_order;     /* 0 or 4: 4th-order Laplacian (the default); 8: the 8th-order
+                            stencil of the paper's solver (Sec. 6.1), run on the
+                            global-memory tiled kernels for every grid size         */
 } fwi_problem;
 
 /* Misfit hyperparameters (Sec. 5.1, 6.2, 6.3): k = 100, c' factor 1.1,
@@ -127,8 +130,9 @@ typedef struct fwi_guide_params {
 typedef struct fwi_plan fwi_plan;   /* opaque, host memory only */
 
 /* Validate a problem and build a plan (host only; no CUDA call).
- * Checks every field above, the CFL bound for v_max (sqrt(3)/2 is the
- * leapfrog limit of the 4th-order Laplacian, whose symbol is at most 16/3),
+ * Checks every field above, the CFL bound for v_max (v_max dt sqrt(1/dx^2 +
+ * 1/dz^2) <= 2 / sqrt(lambda), lambda the largest symbol of the 1D stencil:
+ * 16/3 at 4th order (bound sqrt(3)/2), 6.5016 at 8th order (bound 0.7844)),
  * that sources and receivers lie on the physical grid, and that this build
  * can run the grid (FWI_ERR_UNSUPPORTED otherwise).  *out receives the plan
  * or NULL.  Errors: FWI_ERR_INVALID_ARG, FWI_ERR_UNSTABLE_CFL,

@@ -48,7 +48,7 @@ class _Problem(ctypes.Structure):
                 ("rec_ix", _ip), ("f_peak", ctypes.c_double), ("t0", ctypes.c_double),
                 ("v_ref", ctypes.c_double), ("refl_R", ctypes.c_double),
                 ("v_max", ctypes.c_double), ("batch", ctypes.c_int),
-                ("checkpoint_every", ctypes.c_int)]
+                ("checkpoint_every", ctypes.c_int), ("space_order", ctypes.c_int)]
 
 
 class _W2(ctypes.Structure):
@@ -144,6 +144,7 @@ class Problem:
     batch: int = 1
     top_bc: int = 0
     checkpoint_every: int = 0     # 0: keep the whole record; K: checkpoint every K steps
+    space_order: int = 4          # 4 or 8 (8: the paper solver's stencil, tiled kernels)
 
     @property
     def ns(self):
@@ -231,7 +232,7 @@ def fwi_plan_create(prob: Problem, w2: W2Params) -> _Handle:
                   len(prob.src_ix), len(prob.rec_ix),
                   *[ctypes.cast(a, _ip) for a in arrays],
                   prob.f_peak, prob.t0, prob.v_ref, prob.refl_R, prob.v_max, prob.batch,
-                  prob.checkpoint_every)
+                  prob.checkpoint_every, prob.space_order)
     if len(prob.src_iz) != len(prob.src_ix) or len(prob.rec_iz) != len(prob.rec_ix):
         raise ValueError("source/receiver index lists differ in length")
     cw = _W2(w2.k, w2.cshift_factor, w2.eps_density, w2.n_xi, int(w2.squared))

@@ -90,18 +90,28 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (!(w2->eps_density >= 0.0) || !std::isfinite(w2->eps_density))
         return fail(FWI_ERR_INVALID_ARG, "eps_density must be >= 0");
     if (w2->squared != 0 && w2->squared != 1) return fail(FWI_ERR_INVALID_ARG, "squared must be 0 or 1");
-    // leapfrog + 4th-order Laplacian: |symbol| <= 16/3 per axis => C <= sqrt(3)/2
+    if (p.space_order != 0 && p.space_order != 4 && p.space_order != 8)
+        return fail(FWI_ERR_INVALID_ARG, "space_order must be 0, 4 or 8");
+    const int order = p.space_order == 8 ? 8 : 4;
+    // leapfrog: stable while v dt sqrt(1/dx^2 + 1/dz^2) <= 2 / sqrt(lambda), lambda
+    // the largest |symbol| of the 1D second difference at theta = pi:
+    // 16/3 at 4th order, 205/72 + 2 (8/5 + 1/5 + 8/315 + 1/560) at 8th order
+    const double lambda = order == 8 ? 205.0 / 72 + 2 * (8.0 / 5 + 1.0 / 5 + 8.0 / 315 + 1.0 / 560)
+                                     : 16.0 / 3.0;
+    const double cfl_max = 2.0 / std::sqrt(lambda);
     const double cfl = (double)p.v_max * p.dt *
                        std::sqrt(1.0 / ((double)p.dx * p.dx) + 1.0 / ((double)p.dz * p.dz));
-    if (cfl > std::sqrt(3.0) / 2.0)
+    if (cfl > cfl_max)
         return fail(FWI_ERR_UNSTABLE_CFL,
-                    "v_max dt sqrt(1/dx^2 + 1/dz^2) = %.4f exceeds sqrt(3)/2 = 0.8660", cfl);
+                    "v_max dt sqrt(1/dx^2 + 1/dz^2) = %.4f exceeds %.4f (order %d leapfrog)", cfl,
+                    cfl_max, order);
 
     Plan *pl = new (std::nothrow) Plan();
     if (!pl) return fail(FWI_ERR_INVALID_ARG, "out of host memory");
     pl->fwd_pair = false;
     pl->tiled = false;
     pl->p = p;
+    pl->p.space_order = order;
     pl->w2 = *w2;
     pl->NZ = p.nz + p.nb;
     pl->NX = p.nx + 2 * p.nb;
@@ -129,7 +139,9 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         delete pl;
         return fail(FWI_ERR_UNSUPPORTED, "padded grid %dx%d too large", pl->NZ, pl->NX);
     }
-    pl->fast = fwi::fast_bucket(pl->NZ, pl->NX, &pl->fast_P, &pl->fast_PR, &pl->fast_NZM);
+    // the resident kernels implement the 4th-order stencil only
+    pl->fast = order == 4 &&
+               fwi::fast_bucket(pl->NZ, pl->NX, &pl->fast_P, &pl->fast_PR, &pl->fast_NZM);
     if (pl->fast) {
         const int nstrip = (pl->NZ + fwi::kFastRows - 1) / fwi::kFastRows;
         for (int adj = 0; adj < 2; ++adj) {
@@ -171,7 +183,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     }
     if (!pl->fast) {
         pl->nzs = pl->NZ;
-        if (!fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, false, &pl->shape) ||
+        if (order == 8 ||
+            !fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, false, &pl->shape) ||
             !fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, true, &pl->shape_adj)) {
             // beyond one CTA's shared memory: global-memory tiled kernels
             // (one launch per step; grid z = models x shots)

@@ -37,8 +37,10 @@ namespace fwi {
 namespace {
 
 constexpr int TX = 64, TZ = 32, TROWS = 8, TTHREADS = 256;
-constexpr int HX = TX + 8, HZ = TZ + 4;              // halo tile (x from x0 - 4, z from z0 - 2)
-constexpr unsigned kTileBytes = HX * HZ * sizeof(float);
+// halo tile: x from x0 - 4 (16-byte aligned start, covers a radius up to 4),
+// z from z0 - R for a stencil of radius R (2: 4th order, 4: 8th order)
+constexpr int HX = TX + 8;
+template <int R> __host__ __device__ constexpr int halo_rows() { return TZ + 2 * R; }
 constexpr long kWaitLimit = 1L << 22;                 // mbarrier polls before giving up
 
 // Compact per-launch arguments (one launch per time step).
@@ -51,6 +53,7 @@ struct TileArgs {
     int rzmin, rzmax;           // rows that hold receivers
     double dtd, t0d, ex0d, ez0d;
     float c0, cx1, cx2, cz1, cz2, ex0, ez0, inv_nb, fp, src_scale;
+    float cxm[4], czm[4];       // second-difference weights / h^2 for offsets 1..R
     const float *ka, *ab;       // [B][NZ][NXp]: kappa A, A B
     const int *rec;             // [nr]: pz << 16 | px
     const int *src;             // [ns]: pz << 16 | px
@@ -73,11 +76,11 @@ __device__ __forceinline__ unsigned smem_u32(const void *p)
 
 // Starts the halo-tile copy (one thread) after arming the mbarrier.
 __device__ __forceinline__ void tile_load(float *tile, uint64_t *mbar, const CUtensorMap *tm,
-                                         int x, int z, int bs)
+                                         int x, int z, int bs, unsigned bytes)
 {
     const unsigned mb = smem_u32(mbar);
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
-                 "r"(kTileBytes)
+                 "r"(bytes)
                  : "memory");
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
@@ -154,10 +157,11 @@ __global__ void __launch_bounds__(256) k_tile_setup(const __grid_constant__ Prop
 }
 
 // ------------------------------------------------------------------ forward step
-template <int TOPBC, bool STORE>
+template <int R, int TOPBC, bool STORE>
 __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ CUtensorMap tm,
                                                        const __grid_constant__ TileArgs a)
 {
+    constexpr int HZ = halo_rows<R>();
     __shared__ __align__(128) float tile[HZ * HX];
     __shared__ __align__(8) uint64_t mbar;
     const int tid = threadIdx.x, tx = tid % TX, g = tid / TX;
@@ -165,7 +169,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
     const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
     if (tid == 0) mbar_init(&mbar);
     __syncthreads();
-    if (tid == 0) tile_load(tile, &mbar, &tm, x0 - 4, z0 - 2, bs);
+    if (tid == 0) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
 
     const int x = x0 + tx, zr = z0 + g * TROWS;
     const bool colok = x < a.NX;
@@ -184,10 +188,10 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
     }
     if (!tile_wait(&mbar, a.status)) return;
     if (TOPBC == 1 && z0 == 0) {
-        // mirrored ghost rows: row -1 = row 1, row -2 = row 2
+        // mirrored ghost rows: row -k = row k, k = 1..R
         for (int c = tid; c < HX; c += TTHREADS) {
-            tile[1 * HX + c] = tile[3 * HX + c];
-            tile[0 * HX + c] = tile[4 * HX + c];
+#pragma unroll
+            for (int k = 1; k <= R; ++k) tile[(R - k) * HX + c] = tile[(R + k) * HX + c];
         }
         __syncthreads();
     }
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
             const int pz = a.rec[r] >> 16, px = a.rec[r] & 0xffff;
             if (pz >= z0 && pz < z0 + TZ && px >= x0 && px < x0 + TX)
                 a.d_syn[((size_t)bs * a.nr + r) * a.nt + a.j - 1] =
-                    tile[(pz - z0 + 2) * HX + px - x0 + 4];
+                    tile[(pz - z0 + R) * HX + px - x0 + 4];
         }
     }
     // checkpoint of the state at step j (field u^j, increment v^(j-1/2))
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
         for (int r = 0; r < TROWS; ++r) {
             const int z = zr + r;
             if (colok && z < a.NZ) {
-                st[(size_t)z * a.NX + x] = tile[(z - z0 + 2) * HX + tx + 4];
+                st[(size_t)z * a.NX + x] = tile[(z - z0 + R) * HX + tx + 4];
                 st[cells + (size_t)z * a.NX + x] = vi[r];
             }
         }
@@ -218,23 +222,22 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
     float *ub = a.unext + (size_t)bs * plane;
     float *rb = STORE ? a.rec_out + ((size_t)bs * a.rec_planes + (a.j - a.rec_base)) * plane
                       : nullptr;
-    const float *cp = tile + (g * TROWS + 2) * HX + tx + 4;
-    float wm2 = cp[-2 * HX], wm1 = cp[-HX], w0 = cp[0], wp1 = cp[HX];
-    float Dp = w0 - wm1, Em2 = w0 - wm2, Em1 = wp1 - wm1;
+    const float *cp = tile + (g * TROWS + R) * HX + tx + 4;
+    float w[2 * R + 1];     // z window: w[R + k] = row z + k
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) w[k] = cp[(k - R) * HX];
 #pragma unroll
     for (int r = 0; r < TROWS; ++r) {
         const float *c = cp + r * HX;
-        const float wp2 = c[2 * HX];
-        const float Dn = wp1 - w0;
-        const float E0 = wp2 - w0;
-        const float dzA = Dn - Dp;
-        const float dzB = E0 - Em2;
-        const float dxA = (c[-1] - w0) + (c[1] - w0);
-        const float dxB = (c[-2] - w0) + (c[2] - w0);
-        float lap = a.cx1 * dxA;
-        lap = fmaf(a.cx2, dxB, lap);
-        lap = fmaf(a.cz1, dzA, lap);
-        lap = fmaf(a.cz2, dzB, lap);
+        w[2 * R] = c[R * HX];
+        const float w0 = w[R];
+        // Laplacian on neighbour differences: sum_m c_m ((u_{-m} - u_0) + (u_{+m} - u_0))
+        float lap = a.cxm[0] * ((c[-1] - w0) + (c[1] - w0));
+#pragma unroll
+        for (int m = 2; m <= R; ++m) lap = fmaf(a.cxm[m - 1], (c[-m] - w0) + (c[m] - w0), lap);
+#pragma unroll
+        for (int m = 1; m <= R; ++m)
+            lap = fmaf(a.czm[m - 1], (w[R - m] - w0) + (w[R + m] - w0), lap);
         float vn = fmaf(ka[r], lap, ab[r] * vi[r]);
         float un = w0 + vn;
         const int z = zr + r;
@@ -250,13 +253,8 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
             vb[i] = vn;
             if (STORE) rb[i] = lap;
         }
-        Dp = Dn;
-        Em2 = Em1;
-        Em1 = E0;
-        wm2 = wm1;
-        wm1 = w0;
-        w0 = wp1;
-        wp1 = wp2;
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) w[k] = w[k + 1];
     }
 }
 
@@ -292,10 +290,13 @@ __global__ void k_tile_resume(const float *__restrict__ st, int nbs, int NZ, int
 // q^j the adjoint source r^{nt-1-j} at the receivers.  Over thousands of
 // steps the standard form 2A psi^j - A B psi^{j-1} loses the slowly varying
 // part of psi to float32 round-off, as the forward's standard form does.
-template <int TOPBC>
+// With the mirrored top, L^T adds the reflected weights back onto rows
+// 1..R: (L^T psi)_k += sum_{r=0}^{R-k} c_{r+k} psi_r.
+template <int R, int TOPBC>
 __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ CUtensorMap tm,
                                                        const __grid_constant__ TileArgs a)
 {
+    constexpr int HZ = halo_rows<R>();
     __shared__ __align__(128) float tile[HZ * HX];
     __shared__ float inj[TZ * TX];
     __shared__ __align__(8) uint64_t mbar;
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
     const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
     if (tid == 0) mbar_init(&mbar);
     __syncthreads();
-    if (tid == 0) tile_load(tile, &mbar, &tm, x0 - 4, z0 - 2, bs);
+    if (tid == 0) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
 
     const int x = x0 + tx, zr = z0 + g * TROWS;
     const bool colok = x < a.NX;
@@ -344,27 +345,29 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
     }
 
     const int sp = a.src[s], sz = sp >> 16, sx = sp & 0xffff;
-    const float *cp = tile + (g * TROWS + 2) * HX + tx + 4;
-    float wm2 = cp[-2 * HX], wm1 = cp[-HX], w0 = cp[0], wp1 = cp[HX];
-    float Dp = w0 - wm1, Em2 = w0 - wm2, Em1 = wp1 - wm1;
+    const float *cp = tile + (g * TROWS + R) * HX + tx + 4;
+    float w[2 * R + 1];     // z window: w[R + k] = row z + k
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) w[k] = cp[(k - R) * HX];
 #pragma unroll
     for (int r = 0; r < TROWS; ++r) {
         const float *c = cp + r * HX;
-        const float wp2 = c[2 * HX];
+        w[2 * R] = c[R * HX];
+        const float w0 = w[R];
         const int z = zr + r;
-        const float Dn = wp1 - w0;
-        const float E0 = wp2 - w0;
-        const float dzA = Dn - Dp;
-        const float dzB = E0 - Em2;
-        const float dxA = (c[-1] - w0) + (c[1] - w0);
-        const float dxB = (c[-2] - w0) + (c[2] - w0);
-        float lap = a.cx1 * dxA;
-        lap = fmaf(a.cx2, dxB, lap);
-        lap = fmaf(a.cz1, dzA, lap);
-        lap = fmaf(a.cz2, dzB, lap);
-        if (TOPBC == 1 && (z == 1 || z == 2)) {
-            // transpose of the mirrored top: reflected weights back onto rows 1, 2
-            lap += (z == 1) ? a.cz1 * wm1 + a.cz2 * w0 : a.cz2 * wm2;
+        float lap = a.cxm[0] * ((c[-1] - w0) + (c[1] - w0));
+#pragma unroll
+        for (int m = 2; m <= R; ++m) lap = fmaf(a.cxm[m - 1], (c[-m] - w0) + (c[m] - w0), lap);
+#pragma unroll
+        for (int m = 1; m <= R; ++m)
+            lap = fmaf(a.czm[m - 1], (w[R - m] - w0) + (w[R + m] - w0), lap);
+        if (TOPBC == 1 && r >= 1 && r <= R && zr == 0) {
+            // transpose of the mirrored top: rows 0..R-r reflect onto row r
+            // (rows 1..R of the grid are rows 1..R of the first row group)
+            float extra = 0.f;
+#pragma unroll
+            for (int r0 = 0; r0 <= R - r; ++r0) extra = fmaf(a.czm[r0 + r - 1], w[R + r0 - r], extra);
+            lap += extra;
         }
         float wn = fmaf(ka[r], lap, ab[r] * wi[r]);
         if (has_rec) wn = fmaf(ka[r], inj[(g * TROWS + r) * TX + tx], wn);
@@ -377,13 +380,8 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
             if (z == sz && x == sx)
                 a.acc_src[bs] = fmaf(pnv, dev::ricker_scaled(a.nt - 1 - a.j, a), a.acc_src[bs]);
         }
-        Dp = Dn;
-        Em2 = Em1;
-        Em1 = E0;
-        wm2 = wm1;
-        wm1 = w0;
-        w0 = wp1;
-        wp1 = wp2;
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) w[k] = w[k + 1];
     }
 }
 
@@ -432,14 +430,14 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder()
     return fn;
 }
 
-// 3D map [nbs][NZ][NXp] of float32 with the halo-tile box
-bool make_map(CUtensorMap *m, float *base, int nbs, int NZ, int NXp)
+// 3D map [nbs][NZ][NXp] of float32 with the halo-tile box of radius R
+bool make_map(CUtensorMap *m, float *base, int nbs, int NZ, int NXp, int R)
 {
     auto enc = encoder();
     if (!enc) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)NXp, (cuuint64_t)NZ, (cuuint64_t)nbs};
     const cuuint64_t strides[2] = {(cuuint64_t)NXp * 4, (cuuint64_t)NZ * NXp * 4};
-    const cuuint32_t box[3] = {HX, HZ, 1};
+    const cuuint32_t box[3] = {HX, (cuuint32_t)(TZ + 2 * R), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -478,6 +476,16 @@ TileArgs tile_args(const Plan &pl, const PropArgs &a, const TileBufs &t)
     s.dtd = a.dtd; s.t0d = a.t0d; s.ex0d = a.ex0d; s.ez0d = a.ez0d;
     s.c0 = a.c0; s.cx1 = a.cx1; s.cx2 = a.cx2; s.cz1 = a.cz1; s.cz2 = a.cz2;
     s.ex0 = a.ex0; s.ez0 = a.ez0; s.inv_nb = a.inv_nb; s.fp = a.fp; s.src_scale = a.src_scale;
+    // second-difference weights of offsets 1..R (4th order: 4/3, -1/12; 8th
+    // order: 8/5, -1/5, 8/315, -1/560), divided by h^2
+    static const double w4[4] = {4.0 / 3.0, -1.0 / 12.0, 0.0, 0.0};
+    static const double w8[4] = {8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+    const double *wm = pl.p.space_order == 8 ? w8 : w4;
+    const double ix2 = 1.0 / ((double)pl.p.dx * pl.p.dx), iz2 = 1.0 / ((double)pl.p.dz * pl.p.dz);
+    for (int m = 0; m < 4; ++m) {
+        s.cxm[m] = (float)(wm[m] * ix2);
+        s.czm[m] = (float)(wm[m] * iz2);
+    }
     int zmin = 1 << 30, zmax = -1;
     for (int i = 0; i < a.nr; ++i) {
         zmin = a.rec_pz[i] < zmin ? a.rec_pz[i] : zmin;
@@ -513,6 +521,7 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
     s.rec_planes = a.rec_planes;
     const dim3 grid((pl.NX + TX - 1) / TX, (pl.NZ + TZ - 1) / TZ, nbs);
     const int tb = pl.p.top_bc;
+    const int R = pl.p.space_order == 8 ? 4 : 2;
     CUtensorMap maps[2];
     if (!adj) {
         const int jb = a.j_begin;
@@ -531,8 +540,8 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
         // the other level's pad columns and dead cells must read as zero too
         e = cudaMemsetAsync(t.u[(jb + 1) & 1], 0, field, st);
         if (e != cudaSuccess) return e;
-        if (!make_map(&maps[0], t.u[0], nbs, pl.NZ, pl.NXp) ||
-            !make_map(&maps[1], t.u[1], nbs, pl.NZ, pl.NXp))
+        if (!make_map(&maps[0], t.u[0], nbs, pl.NZ, pl.NXp, R) ||
+            !make_map(&maps[1], t.u[1], nbs, pl.NZ, pl.NXp, R))
             return cudaErrorNotSupported;
         s.vinc = t.v;
         s.rec_out = a.snap;
@@ -543,12 +552,15 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
         for (int j = jb; j < a.j_end; ++j) {
             s.j = j;
             s.unext = t.u[(j + 1) & 1];
-            if (store)
-                tb ? k_tile_fwd<1, true><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
-                   : k_tile_fwd<0, true><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
-            else
-                tb ? k_tile_fwd<1, false><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
-                   : k_tile_fwd<0, false><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
+#define FWI_TFWD(RR, TB, ST) k_tile_fwd<RR, TB, ST><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
+            if (R == 4) {
+                if (store) tb ? FWI_TFWD(4, 1, true) : FWI_TFWD(4, 0, true);
+                else tb ? FWI_TFWD(4, 1, false) : FWI_TFWD(4, 0, false);
+            } else {
+                if (store) tb ? FWI_TFWD(2, 1, true) : FWI_TFWD(2, 0, true);
+                else tb ? FWI_TFWD(2, 1, false) : FWI_TFWD(2, 0, false);
+            }
+#undef FWI_TFWD
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if (a.d_syn && a.j_end == a.nt) {
@@ -570,8 +582,8 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
         if (e == cudaSuccess) e = cudaMemsetAsync(t.acc_src, 0, (size_t)nbs * sizeof(float), st);
         if (e != cudaSuccess) return e;
     }
-    if (!make_map(&maps[0], t.p[0], nbs, pl.NZ, pl.NXp) ||
-        !make_map(&maps[1], t.p[1], nbs, pl.NZ, pl.NXp))
+    if (!make_map(&maps[0], t.p[0], nbs, pl.NZ, pl.NXp, R) ||
+        !make_map(&maps[1], t.p[1], nbs, pl.NZ, pl.NXp, R))
         return cudaErrorNotSupported;
     s.acc = t.acc;
     s.acc_src = t.acc_src;
@@ -581,8 +593,12 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
     for (int j = jb; j < a.j_end; ++j) {
         s.j = j;
         s.unext = t.p[(j + 1) & 1];
-        tb ? k_tile_adj<1><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
-           : k_tile_adj<0><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
+        if (R == 4)
+            tb ? k_tile_adj<4, 1><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
+               : k_tile_adj<4, 0><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
+        else
+            tb ? k_tile_adj<2, 1><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
+               : k_tile_adj<2, 0><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (a.j_end == a.nt) {

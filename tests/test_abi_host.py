@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(api):
     lib = ctypes.CDLL(LIB)
     for n in declared_functions():
         assert hasattr(lib, n), n
-    assert api.fwi_version() == 10100
+    assert api.fwi_version() == 10200
 
 
 def _prob(api, **kw):
@@ -151,3 +151,22 @@ def test_binding_fails_loudly_without_library(tmp_path):
         (pkg / f).write_text(open(os.path.join(ROOT, "paper_2603_16393_gb300", f)).read())
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     assert r.returncode != 0 and "libfwi.so is missing" in r.stderr
+
+
+def test_space_order_and_its_cfl_bound(api):
+    # 8th order: lambda = 205/72 + 2 (8/5 + 1/5 + 8/315 + 1/560) = 6.50159, bound 2/sqrt(lambda)
+    lam = 205 / 72 + 2 * (8 / 5 + 1 / 5 + 8 / 315 + 1 / 560)
+    bound = 2 / lam ** 0.5
+    vmax = bound / (1e-3 * 2 ** 0.5 / 10.0)
+    api.fwi_plan_create(_prob(api, v_max=vmax * 0.9999, space_order=8), api.W2Params())
+    with pytest.raises(api.FwiError) as e:
+        api.fwi_plan_create(_prob(api, v_max=vmax * 1.001, space_order=8), api.W2Params())
+    assert e.value.code == 2
+    # the same v_max is fine at 4th order (bound sqrt(3)/2)
+    api.fwi_plan_create(_prob(api, v_max=vmax * 1.001), api.W2Params())
+    with pytest.raises(api.FwiError) as e:
+        api.fwi_plan_create(_prob(api, space_order=6), api.W2Params())
+    assert e.value.code == 1
+    # an 8th-order plan of a 70x70 grid runs on the tiled fields (row pitch 152)
+    h = api.fwi_plan_create(_prob(api, space_order=8), api.W2Params())
+    assert api.fwi_plan_sizes(h)[2] == 3 * 5 * 1000 * 110 * 152 * 4

@@ -113,3 +113,50 @@ def test_tiled_autograd_is_the_library_gradient(api):
         J2, g2, _ = plan2.gradient(v.detach(), ctx)
         torch.cuda.synchronize()
     assert torch.equal(J.detach(), J2) and torch.equal(v.grad, g2)
+
+
+# ---------------------------------------------------------------- 8th-order stencil
+
+def _order8(gp, op):
+    return dataclasses.replace(gp, space_order=8), dataclasses.replace(op, space_order=8)
+
+
+@pytest.mark.parametrize("nz,nx,nb,nt,ns,top_bc", [
+    (30, 70, 20, 300, 3, 0),      # a grid the 4th-order path keeps in shared memory
+    (41, 64, 25, 260, 2, 1),      # mirrored top over four rows
+    (100, 140, 20, 400, 2, 0),
+])
+def test_order8_forward_matches_oracle(api, nz, nx, nb, nt, ns, top_bc):
+    gp, op = _order8(*problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc))
+    v = models("curved_faulted", [3, 4], nz, nx)
+    with api.Plan(gp) as plan:
+        d, _ = plan.forward(T(v))
+        torch.cuda.synchronize()
+        plan.check()
+    d_o = O.forward(op, v)
+    assert rel_l2(H(d), d_o) <= TOL_DATA, rel_l2(H(d), d_o)
+    # and it is not the 4th-order result
+    assert rel_l2(d_o, O.forward(dataclasses.replace(op, space_order=4), v)) > 1e-3
+
+
+@pytest.mark.parametrize("top_bc", [0, 1])
+def test_order8_gradient_matches_oracle(api, top_bc):
+    nz, nx, nb, nt, ns = 30, 70, 20, 300, 3
+    gp, op = _order8(*problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc))
+    w2p, ow2 = api.W2Params(n_xi=400), O.W2Params(n_xi=400)
+    vt = models("layered", [7, 8], nz, nx)
+    v0 = initial(2, nz, nx)
+    d_obs = O.forward(op, vt).astype(np.float32).astype(np.float64)
+    out = []
+    for K in (0, 41):
+        with api.Plan(dataclasses.replace(gp, checkpoint_every=K), w2p) as plan:
+            J, g, _ = plan.gradient(T(v0), plan.w2_prepare(T(d_obs)))
+            torch.cuda.synchronize()
+            plan.check()
+            out.append((J, g))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    J, g = H(out[0][0]), H(out[0][1])
+    J_o, g_o, _ = O.gradient(op, v0, O.w2_prepare(d_obs, op.dt, ow2), ow2)
+    assert rel_l2(J, J_o) <= TOL_J * 10, (J, J_o)
+    for b in range(2):
+        assert rel_l2(g[b], g_o[b]) <= TOL_GRAD, (b, rel_l2(g[b], g_o[b]))

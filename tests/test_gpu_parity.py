@@ -182,6 +182,7 @@ def test_gradient_matches_oracle_small(api, nz, nx, nb, nt, ns, top_bc):
     (22, 25, 6, 280, 3, 0),
     (22, 25, 6, 280, 3, 1),
     (70, 70, 40, 1000, 5, 0),
+    (70, 70, 40, 1000, 5, 1),     # full size with the mirrored top
 ])
 def test_adjoint_stage_on_shared_adjoint_source(api, nz, nx, nb, nt, ns, top_bc):
     # a seeded adjoint source goes to both wave adjoints: isolates a7/a8

@@ -10,9 +10,10 @@ guided update.  Metric: W2-FWI gradients/s (plus Gcell-updates/s).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl ours|reference]
                     [--workload 70x70|256x256|512x1024]
 
---workload selects the larger grids that run on the tiled propagators
-(256x256: 16 shots, 2000 steps, record kept; 512x1024: 32 shots, 4000 steps,
-checkpoints every 32 steps); the default is the 70x70 workload above.
+--workload selects the larger grids (256x256: 16 shots, 2000 steps, record
+kept, on the cluster propagators; 512x1024: 32 shots, 4000 steps, checkpoints
+every 32 steps, on the tiled propagators); the default is the 70x70 workload
+above (resident propagators).
 
 Under torchrun (N > 1) every rank owns its own B models (weak scaling, no
 data-path collective); the step time is the max over ranks.
@@ -38,14 +39,14 @@ if ROOT not in sys.path:
 DX, DT, NB = 10.0, 1e-3, 40
 UNIT = "gradients/s"
 # name: physical grid, steps, shots, receivers, model family, default batch,
-# checkpoint interval (0: whole record kept), propagator family
+# checkpoint interval (0: whole record kept); the plan picks the propagator
+# family (resident, cluster or tiled) from the grid
 WORKLOADS = {
-    "70x70": dict(nz=70, nx=70, nt=1000, ns=5, nr=70, kind="layered", batch=152, ckpt=0,
-                  path="resident"),
+    "70x70": dict(nz=70, nx=70, nt=1000, ns=5, nr=70, kind="layered", batch=152, ckpt=0),
     "256x256": dict(nz=256, nx=256, nt=2000, ns=16, nr=256, kind="curved_faulted", batch=8,
-                    ckpt=0, path="tiled"),
+                    ckpt=0),
     "512x1024": dict(nz=512, nx=1024, nt=4000, ns=32, nr=1024, kind="curved_faulted", batch=2,
-                     ckpt=32, path="tiled"),
+                     ckpt=32),
 }
 
 
@@ -220,6 +221,8 @@ def run_ours(args, rank, world, local_rank):
                        src_iz=geo.src_iz, src_ix=geo.src_ix, rec_iz=geo.rec_iz,
                        rec_ix=geo.rec_ix, v_max=4500.0, batch=B, checkpoint_every=wl["ckpt"])
     plan = api.Plan(prob, api.W2Params(), device=dev)
+    path = {api.KERNELS_RESIDENT: "resident", api.KERNELS_TILED: "tiled",
+            api.KERNELS_CLUSTER: "cluster"}[plan.kernels]
     # Table 1 (CurveVel-A) rho0, gamma; Sec. 6.3 c, tau, eps; the diffusion's
     # normalised space (v - 3000)/1500 has a unit of 1500 m/s
     gparams = api.GuideParams(rho0=1.15, gamma=0.55, unit=1500.0)
@@ -258,11 +261,13 @@ def run_ours(args, rank, world, local_rank):
         api.fwi_guided_step(B, NZ_PHYS, NX_PHYS, gparams, v_in, v_in, grad, grad, v_out, rho)
 
     # library kernels per step: prepare (3), forward, misfit (2), adjoint +
-    # shot sum, guided (1); the tiled propagators launch once per time step,
-    # plus a set-up (and a resume per recomputed segment) and a final gather
-    # or fold
-    if wl["path"] == "resident":
+    # shot sum, guided (1); the cluster adjoint adds a fold; the tiled
+    # propagators launch once per time step, plus a set-up (and a resume per
+    # recomputed segment) and a final gather or fold
+    if path == "resident":
         kernels_per_step = 3 + 1 + 2 + 2 + 1
+    elif path == "cluster":
+        kernels_per_step = 3 + 1 + 2 + 3 + 1
     else:
         K = wl["ckpt"]
         S = -(-NT // K) if K else 0
@@ -329,12 +334,14 @@ def run_ours(args, rank, world, local_rank):
     cell_updates = 2 * cu                            # forward + adjoint, per step per rank
     small = B * NS * NR * NT * 4 + B * NZ_PHYS * NX_PHYS * 4 * (1 + NS + 1)
     K = wl["ckpt"]
-    if wl["path"] == "resident":
+    if path in ("resident", "cluster"):
+        # the fields stay on chip (one CTA's, or a cluster's shared memory);
         # the propagators stream the wavefield record (4 B per cell-update:
         # the forward writes it, the adjoint reads it) + traces, models and
         # per-shot gradients
         adj_bytes, fwd_bytes = cu * 4 + small, cu * 4 + B * NS * NR * NT * 4 + B * NZ_PHYS * NX_PHYS * 4
-        adj_name, fwd_name = "adjoint propagator", "forward propagator"
+        adj_name, fwd_name = (("adjoint propagator", "forward propagator") if path == "resident"
+                              else ("cluster adjoint (+ fold)", "cluster forward"))
     else:
         # tiled, per cell-update: forward reads u, v and writes u, v (16 B;
         # + 4 B record); adjoint reads psi, w, imaging sum, record and writes
@@ -351,7 +358,7 @@ def run_ours(args, rank, world, local_rank):
     hbm_peak, peak_kind = peaks()
     dom = max((adj_ms, adj_bytes, adj_name, "adjoint"), (fwd_ms, fwd_bytes, fwd_name, "forward"))
     achieved = dom[1] / (dom[0] * 1e-3) / 1e9
-    traffic = record_traffic(B * NS) if wl["path"] == "resident" else None
+    traffic = record_traffic(B * NS) if path == "resident" else None
     traffic = traffic[dom[3]] if traffic else None
     value = world * B / (ms * 1e-3)
 
@@ -372,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": f"synthetic (seeded {wl['kind'].replace('_', '/')} models)",
-        "config": {"workload": f"{B} x {NZ_PHYS}x{NX_PHYS} {wl['kind'].replace('_', '/')} models "
+        "config": {"propagators": path, "workload": f"{B} x {NZ_PHYS}x{NX_PHYS} {wl['kind'].replace('_', '/')} models "
                                f"per GPU, {NS} shots, {NR} receivers, {NT} steps, 40-cell "
                                f"absorbing layer, {record}",
                    "batch_per_gpu": B, "global_batch": B * world,

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 10200  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 10300  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -99,7 +99,24 @@ typedef struct fwi_problem {
     int space_order;     /* 0 or 4: 4th-order Laplacian (the default); 8: the 8th-order
                             stencil of the paper's solver (Sec. 6.1), run on the
                             global-memory tiled kernels for every grid size         */
+    int kernels;         /* propagator family: FWI_KERNELS_AUTO (0) picks by grid size;
+                            the others force one and fail with FWI_ERR_UNSUPPORTED
+                            where it cannot run the plan.  Every family computes the
+                            same recurrences (Sec. 2.1, Eq. 2) to float rounding.   */
 } fwi_problem;
+
+/* Propagator families (fwi_problem.kernels). */
+enum {
+    FWI_KERNELS_AUTO = 0,
+    FWI_KERNELS_RESIDENT = 1, /* one CTA holds a (model, shot)'s whole padded grid in
+                                 shared memory; 4th order; grids up to ~150 x 340 cells  */
+    FWI_KERNELS_TILED = 2,    /* global-memory fields, TMA-staged halo tiles, one launch
+                                 per time step; any grid, 4th or 8th order               */
+    FWI_KERNELS_CLUSTER = 3   /* a cluster of 8 CTAs holds the grid in their shared
+                                 memories, halo rows through distributed shared memory;
+                                 4th order, whole record (checkpoint_every = 0), padded
+                                 width <= 337, rows split 8 ways                        */
+};
 
 /* Misfit hyperparameters (Sec. 5.1, 6.2, 6.3): k = 100, c' factor 1.1,
  * eps' = 1e-9, N_xi = 1000. */
@@ -159,6 +176,10 @@ FWI_API fwi_status fwi_plan_sizes(const fwi_plan *plan, size_t *workspace_bytes,
 
 /* Padded grid of the plan: NZ = nz + nb, NX = nx + 2 nb. */
 FWI_API fwi_status fwi_plan_padded(const fwi_plan *plan, int *NZ, int *NX);
+
+/* Propagator family the plan runs: *family = FWI_KERNELS_RESIDENT, _TILED or
+ * _CLUSTER (the automatic choice resolved, or the one forced).  Host only. */
+FWI_API fwi_status fwi_plan_kernels(const fwi_plan *plan, int *family);
 
 /* Forward solve of Eq. (1) for every model and shot (Sec. 2.1, 6.1).
  *   v         [B][nz][nx] device, m/s; every value must be in (0, v_max]

@@ -33,6 +33,7 @@ FWI_ERR_UNSUPPORTED = 3
 FWI_ERR_CUDA = 4
 FWI_ERR_DEVICE_TIMEOUT = 5
 FWI_ERR_OOM = 6
+KERNELS_AUTO, KERNELS_RESIDENT, KERNELS_TILED, KERNELS_CLUSTER = 0, 1, 2, 3
 FWI_MAX_SHOTS = 256
 FWI_MAX_RECEIVERS = 1024
 
@@ -48,7 +49,8 @@ class _Problem(ctypes.Structure):
                 ("rec_ix", _ip), ("f_peak", ctypes.c_double), ("t0", ctypes.c_double),
                 ("v_ref", ctypes.c_double), ("refl_R", ctypes.c_double),
                 ("v_max", ctypes.c_double), ("batch", ctypes.c_int),
-                ("checkpoint_every", ctypes.c_int), ("space_order", ctypes.c_int)]
+                ("checkpoint_every", ctypes.c_int), ("space_order", ctypes.c_int),
+                ("kernels", ctypes.c_int)]
 
 
 class _W2(ctypes.Structure):
@@ -72,6 +74,8 @@ _lib.fwi_plan_sizes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t),
                                 ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
 _lib.fwi_plan_padded.restype = _S
 _lib.fwi_plan_padded.argtypes = [_vp, _ip, _ip]
+_lib.fwi_plan_kernels.restype = _S
+_lib.fwi_plan_kernels.argtypes = [_vp, _ip]
 _lib.fwi_forward.restype = _S
 _lib.fwi_forward.argtypes = [_vp] * 6
 _lib.fwi_w2_prepare.restype = _S
@@ -145,6 +149,7 @@ class Problem:
     top_bc: int = 0
     checkpoint_every: int = 0     # 0: keep the whole record; K: checkpoint every K steps
     space_order: int = 4          # 4 or 8 (8: the paper solver's stencil, tiled kernels)
+    kernels: int = 0              # propagator family: KERNELS_AUTO / _RESIDENT / _TILED / _CLUSTER
 
     @property
     def ns(self):
@@ -232,7 +237,7 @@ def fwi_plan_create(prob: Problem, w2: W2Params) -> _Handle:
                   len(prob.src_ix), len(prob.rec_ix),
                   *[ctypes.cast(a, _ip) for a in arrays],
                   prob.f_peak, prob.t0, prob.v_ref, prob.refl_R, prob.v_max, prob.batch,
-                  prob.checkpoint_every, prob.space_order)
+                  prob.checkpoint_every, prob.space_order, prob.kernels)
     if len(prob.src_iz) != len(prob.src_ix) or len(prob.rec_iz) != len(prob.rec_ix):
         raise ValueError("source/receiver index lists differ in length")
     cw = _W2(w2.k, w2.cshift_factor, w2.eps_density, w2.n_xi, int(w2.squared))
@@ -245,6 +250,12 @@ def fwi_plan_sizes(plan: _Handle):
     ws, ctx, snap = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
     _check(_lib.fwi_plan_sizes(plan.raw, ctypes.byref(ws), ctypes.byref(ctx), ctypes.byref(snap)))
     return ws.value, ctx.value, snap.value
+
+
+def fwi_plan_kernels(plan: _Handle) -> int:
+    fam = ctypes.c_int()
+    _check(_lib.fwi_plan_kernels(plan.raw, ctypes.byref(fam)))
+    return fam.value
 
 
 def fwi_forward(plan, v, d_syn, snapshots, workspace, stream=None):
@@ -312,6 +323,7 @@ class Plan:
         self.w2p = w2 or W2Params()
         self.handle = fwi_plan_create(prob, self.w2p)
         self.ws_bytes, self.ctx_bytes, self.snap_bytes = fwi_plan_sizes(self.handle)
+        self.kernels = fwi_plan_kernels(self.handle)   # the propagator family it runs
         self.device = torch.device(device) if device is not None else \
             torch.device("cuda", torch.cuda.current_device())
         self.workspace = torch.zeros(self.ws_bytes, dtype=torch.uint8, device=self.device)

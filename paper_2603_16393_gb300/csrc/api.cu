@@ -90,6 +90,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (!(w2->eps_density >= 0.0) || !std::isfinite(w2->eps_density))
         return fail(FWI_ERR_INVALID_ARG, "eps_density must be >= 0");
     if (w2->squared != 0 && w2->squared != 1) return fail(FWI_ERR_INVALID_ARG, "squared must be 0 or 1");
+    if (p.kernels < FWI_KERNELS_AUTO || p.kernels > FWI_KERNELS_CLUSTER)
+        return fail(FWI_ERR_INVALID_ARG, "kernels must be 0 (auto), 1, 2 or 3");
     if (p.space_order != 0 && p.space_order != 4 && p.space_order != 8)
         return fail(FWI_ERR_INVALID_ARG, "space_order must be 0, 4 or 8");
     const int order = p.space_order == 8 ? 8 : 4;
@@ -139,8 +141,9 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         delete pl;
         return fail(FWI_ERR_UNSUPPORTED, "padded grid %dx%d too large", pl->NZ, pl->NX);
     }
+    const int fam = p.kernels;
     // the resident kernels implement the 4th-order stencil only
-    pl->fast = order == 4 &&
+    pl->fast = (fam == FWI_KERNELS_AUTO || fam == FWI_KERNELS_RESIDENT) && order == 4 &&
                fwi::fast_bucket(pl->NZ, pl->NX, &pl->fast_P, &pl->fast_PR, &pl->fast_NZM);
     if (pl->fast) {
         const int nstrip = (pl->NZ + fwi::kFastRows - 1) / fwi::kFastRows;
@@ -183,9 +186,16 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     }
     if (!pl->fast) {
         pl->nzs = pl->NZ;
-        if (order == 8 ||
+        if (fam == FWI_KERNELS_TILED || fam == FWI_KERNELS_CLUSTER || order == 8 ||
             !fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, false, &pl->shape) ||
             !fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, true, &pl->shape_adj)) {
+            if (fam == FWI_KERNELS_RESIDENT) {
+                delete pl;
+                return fail(FWI_ERR_UNSUPPORTED,
+                            "the resident kernels hold 4th-order %dx%d padded grids only up to "
+                            "one CTA's shared memory",
+                            pl->NZ, pl->NX);
+            }
             // beyond one CTA's shared memory: global-memory tiled kernels
             // (one launch per step; grid z = models x shots)
             if ((long long)p.batch * p.ns > 65535) {
@@ -199,6 +209,64 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     }
     pl->NXp = (pl->NX + 3) / 4 * 4;
     pl->rec_pitch = pl->fast ? pl->fast_PR : (pl->tiled ? pl->NXp : pl->NX);
+    // store-all 4th-order plans of the tiled family run on the cluster kernels
+    // when a grid's rows fit a cluster's shared memory
+    pl->cluster = false;
+    if (pl->tiled && (fam == FWI_KERNELS_AUTO || fam == FWI_KERNELS_CLUSTER) && order == 4 &&
+        p.checkpoint_every == 0 && pl->NX + 4 <= fwi::kCluPitch) {
+        const int C = fwi::kClusterCTAs;
+        const int RC = (pl->NZ + C - 1) / C;
+        const int P = fwi::kCluPitch;
+        static const int rs_buckets[] = {13, 19};
+        int RS = 0, nstrip = 0, threads = 0;
+        for (int rs : rs_buckets) {
+            const int ns_ = (RC + rs - 1) / rs;
+            const int th = (pl->NX * ns_ + 31) / 32 * 32;
+            if (th <= fwi::clu_max_threads(rs)) {
+                RS = rs;
+                nstrip = ns_;
+                threads = th;
+                break;
+            }
+        }
+        const size_t limit = 227 * 1024;
+        int chunk[2] = {0, 0};
+        if (RS > 0) {
+            for (int adj = 0; adj < 2; ++adj) {
+                const size_t fixed = fwi::cluster_smem(nstrip * RS, RC, P, adj != 0, 0, p.nr);
+                const size_t per = ((size_t)p.nr + 1) * 4;
+                size_t c = fixed + per > limit ? 0 : (limit - fixed) / per;
+                chunk[adj] = c > 32 ? 32 : (int)c;
+            }
+        }
+        bool ok = RS > 0 && chunk[0] >= 1 && chunk[1] >= 1;
+        // the adjoint injects each receiver from the thread owning its cell:
+        // at most one receiver per column of a strip
+        for (int i = 0; ok && i < p.nr; ++i)
+            for (int k = 0; k < i; ++k)
+                if (pl->rec_px[i] == pl->rec_px[k] && pl->rec_pz[i] / RC == pl->rec_pz[k] / RC &&
+                    (pl->rec_pz[i] % RC) / RS == (pl->rec_pz[k] % RC) / RS) {
+                    ok = false;
+                    break;
+                }
+        if (ok) {
+            pl->cluster = true;
+            pl->clu = fwi::ClusterArgs{P, RC, RS, nstrip, nstrip * RS, pl->NXp, 0, nullptr, nullptr};
+            pl->clu_threads = threads;
+            pl->clu_chunk_fwd = chunk[0];
+            pl->clu_chunk_adj = chunk[1];
+            // record: kClusterCTAs RC rows per plane at the pitch P - 1
+            pl->nzs = C * RC;
+            pl->rec_pitch = P - 1;
+        }
+    }
+    if (fam == FWI_KERNELS_CLUSTER && !pl->cluster) {
+        delete pl;
+        return fail(FWI_ERR_UNSUPPORTED,
+                    "the cluster kernels take 4th-order, whole-record plans of padded width <= %d "
+                    "whose rows fit 8 CTAs' shared memory (grid %dx%d)",
+                    fwi::kCluPitch - 4, pl->NZ, pl->NX);
+    }
     // the adjoint source of a receiver enters through the level psi^{j-1}
     // scaled by 1/B, B = 1 - eta dt/2 of the receiver cell
     {
@@ -313,6 +381,14 @@ fwi_status fwi_plan_padded(const fwi_plan *plan, int *NZ, int *NX)
     if (!plan) return fail(FWI_ERR_INVALID_ARG, "plan is NULL");
     if (NZ) *NZ = as_plan(plan)->NZ;
     if (NX) *NX = as_plan(plan)->NX;
+    return FWI_OK;
+}
+
+fwi_status fwi_plan_kernels(const fwi_plan *plan, int *family)
+{
+    if (!plan || !family) return fail(FWI_ERR_INVALID_ARG, "plan or family is NULL");
+    const Plan *pl = as_plan(plan);
+    *family = pl->cluster ? FWI_KERNELS_CLUSTER : pl->tiled ? FWI_KERNELS_TILED : FWI_KERNELS_RESIDENT;
     return FWI_OK;
 }
 

@@ -38,6 +38,26 @@ struct ResidentShape {
     size_t smem;     // dynamic shared memory bytes
 };
 
+// Cluster propagators: a (model, shot) grid split by rows over this many CTAs,
+// shared-memory row pitch (compile time; padded widths up to kCluPitch - 4)
+constexpr int kClusterCTAs = 8;
+constexpr int kCluPitch = 341;
+// threads per CTA of the cluster kernels with RS rows a thread: 96 registers
+// a thread at 672 (21 warps) for the 19-row strips, 80 at 768 for 13 rows
+__host__ __device__ constexpr int clu_max_threads(int RS) { return RS > 13 ? 672 : 768; }
+
+struct ClusterArgs {
+    int P;          // shared-memory row pitch
+    int RC;         // grid rows per CTA
+    int RS;         // rows per thread strip
+    int nstrip;     // strips per column
+    int rows_cap;   // nstrip * RS (row capacity of the field arrays)
+    int NXp;        // row pitch of the record and of the imaging sums in global memory
+    int chunk;      // staged time steps
+    float *acc;     // adjoint: imaging sums [bs][NZ][NXp] (to the fold)
+    float *acc_src; // adjoint: source-cell sums [bs]
+};
+
 struct Plan {
     fwi_problem p;           // copy; index pointers below replace the caller's
     fwi_w2_params w2;
@@ -49,6 +69,9 @@ struct Plan {
     ResidentShape shape_adj;   // adjoint propagator
     bool fast;                 // compile-time pitch kernels (else the generic ones)
     bool tiled;                // global-memory tiled kernels (grids beyond shared memory)
+    bool cluster;              // cluster kernels for the store-all passes of a tiled plan
+    ClusterArgs clu;           // their shape
+    int clu_threads, clu_chunk_fwd, clu_chunk_adj;
     int NXp;                   // tiled: row pitch of the fields (NX rounded up to 4)
     int rec_pitch;             // row pitch of a record plane
     bool fwd_pair;             // forward on column pairs (even padded width)
@@ -159,6 +182,13 @@ size_t fast_smem(int P, int NZM, bool adj, int chunk, int nr);
 int fast_chunk(int P, int NZM, bool adj, int nr);   // staging steps that fit (<= 32; 0: none)
 bool fwd_pair_ok(int NX, int NZ, int NZM);
 cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st);
+// Cluster propagators (whole time loop, store-all plans): shared memory of
+// one CTA, and the launch
+size_t cluster_smem(int rows_cap, int RC, int P, bool adj, int chunk, int nr);
+cudaError_t launch_cluster(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
+                           cudaStream_t st);
+cudaError_t launch_tile_fold(const Plan &pl, const PropArgs &a, unsigned char *ws,
+                             cudaStream_t st);
 // Tiled propagators: one launch per step over [a.j_begin, a.j_end)
 cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
                          cudaStream_t st);

@@ -449,6 +449,8 @@ cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *
     a.snap = snap;
     a.status = static_cast<int *>(workspace);
     apply_window(a, w);
+    if (pl.cluster)
+        return launch_cluster(pl, false, a, static_cast<unsigned char *>(workspace), st);
     if (pl.tiled) return launch_tiled(pl, false, a, static_cast<unsigned char *>(workspace), st);
     if (pl.fast) {
         a.rows = pl.shape.rows;
@@ -471,7 +473,11 @@ cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj, con
     a.status = static_cast<int *>(workspace);
     apply_window(a, w);
     cudaError_t e;
-    if (pl.tiled) {
+    if (pl.cluster) {
+        e = launch_cluster(pl, true, a, static_cast<unsigned char *>(workspace), st);
+        if (e == cudaSuccess)
+            e = launch_tile_fold(pl, a, static_cast<unsigned char *>(workspace), st);
+    } else if (pl.tiled) {
         e = launch_tiled(pl, true, a, static_cast<unsigned char *>(workspace), st);
     } else if (pl.fast) {
         a.rows = pl.shape_adj.rows;

@@ -508,6 +508,15 @@ cudaError_t setup(const Plan &pl, const PropArgs &a, const TileBufs &t, cudaStre
 
 }  // namespace
 
+cudaError_t launch_tile_fold(const Plan &pl, const PropArgs &a, unsigned char *ws, cudaStream_t st)
+{
+    const int nbs = pl.p.batch * pl.p.ns;
+    const TileBufs t = tile_bufs(pl, ws);
+    const dim3 fg((pl.p.nz * pl.p.nx + 255) / 256, nbs);
+    k_tile_fold<<<fg, 256, 0, st>>>(a, pl.NXp, t.acc, t.acc_src, a.gshot);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
                          cudaStream_t st)
 {

@@ -2,6 +2,7 @@
 point include/fwi.h declares, and fwi_plan_create validates its arguments
 (host-only call) with the documented error codes."""
 import ctypes
+import dataclasses
 import os
 import re
 
@@ -37,7 +38,7 @@ def test_library_exports_every_declared_symbol(api):
     lib = ctypes.CDLL(LIB)
     for n in declared_functions():
         assert hasattr(lib, n), n
-    assert api.fwi_version() == 10200
+    assert api.fwi_version() == 10300
 
 
 def _prob(api, **kw):
@@ -64,15 +65,22 @@ def test_plan_of_a_grid_beyond_shared_memory_uses_the_tiled_fields(api):
     B, ns, nt = 2, 16, 200
     prob = _prob(api, nz=256, nx=256, nt=nt, batch=B, src_iz=(0,) * ns,
                  src_ix=tuple(range(0, 256, 16)), rec_iz=(0,) * 256, rec_ix=tuple(range(256)))
-    h = api.fwi_plan_create(prob, api.W2Params())
+    h = api.fwi_plan_create(dataclasses.replace(prob, kernels=api.KERNELS_TILED), api.W2Params())
+    assert api.fwi_plan_kernels(h) == api.KERNELS_TILED
     ws, ctx, snap = api.fwi_plan_sizes(h)
     NZ, NX, NXp = 296, 336, 336
     assert snap == B * ns * nt * NZ * NXp * 4
     assert ws >= 6 * B * ns * NZ * NXp * 4 + 2 * B * NZ * NXp * 4
+    # the automatic choice for this grid: a cluster of 8 CTAs, 37 rows each;
+    # record rows at the cluster kernels' pitch 340
+    h = api.fwi_plan_create(prob, api.W2Params())
+    assert api.fwi_plan_kernels(h) == api.KERNELS_CLUSTER
+    assert api.fwi_plan_sizes(h)[2] == B * ns * nt * (8 * 37) * 340 * 4
     # odd padded width: rows padded to a multiple of 4 floats
     prob = _prob(api, nz=200, nx=301, nt=nt, batch=1, src_ix=(0, 75, 150, 225, 300),
                  rec_iz=(0,) * 301, rec_ix=tuple(range(301)))
     h = api.fwi_plan_create(prob, api.W2Params())
+    assert api.fwi_plan_kernels(h) == api.KERNELS_TILED     # 381 columns: wider than a cluster's rows
     assert api.fwi_plan_sizes(h)[2] == 5 * nt * 240 * 384 * 4
     # with checkpoints: two compact NZ x NX grids per slot
     h = api.fwi_plan_create(_prob(api, nz=256, nx=256, nt=nt, batch=B, src_iz=(0,) * ns,
@@ -170,3 +178,34 @@ def test_space_order_and_its_cfl_bound(api):
     # an 8th-order plan of a 70x70 grid runs on the tiled fields (row pitch 152)
     h = api.fwi_plan_create(_prob(api, space_order=8), api.W2Params())
     assert api.fwi_plan_sizes(h)[2] == 3 * 5 * 1000 * 110 * 152 * 4
+
+
+def test_kernel_family_selection(api):
+    K = api
+    # automatic: 70 x 70 (110 x 150 padded) on the resident kernels
+    assert K.fwi_plan_kernels(K.fwi_plan_create(_prob(api), K.W2Params())) == K.KERNELS_RESIDENT
+    for fam in (K.KERNELS_RESIDENT, K.KERNELS_TILED, K.KERNELS_CLUSTER):
+        h = K.fwi_plan_create(_prob(api, kernels=fam), K.W2Params())
+        assert K.fwi_plan_kernels(h) == fam
+    # a cluster plan's record: 8 x ceil(110 / 8) = 112 rows at the pitch 340
+    h = K.fwi_plan_create(_prob(api, kernels=K.KERNELS_CLUSTER), K.W2Params())
+    assert K.fwi_plan_sizes(h)[2] == 3 * 5 * 1000 * 112 * 340 * 4
+    # checkpointed or 8th-order plans of a cluster-sized grid run tiled
+    for kw in (dict(checkpoint_every=32), dict(space_order=8)):
+        assert K.fwi_plan_kernels(K.fwi_plan_create(_prob(api, nz=200, **kw), K.W2Params())) \
+            == K.KERNELS_TILED
+    big = dict(nz=256, nx=256, src_iz=(0,), src_ix=(0,), rec_iz=(0,) * 256,
+               rec_ix=tuple(range(256)))
+    bad = [
+        (dict(big, kernels=K.KERNELS_RESIDENT), 3),          # 296 x 336 cells: not one CTA's
+        (dict(kernels=K.KERNELS_CLUSTER, checkpoint_every=8), 3),
+        (dict(kernels=K.KERNELS_CLUSTER, space_order=8), 3),
+        (dict(kernels=K.KERNELS_RESIDENT, space_order=8), 3),
+        (dict(nx=300, kernels=K.KERNELS_CLUSTER), 3),        # 380 padded columns
+        (dict(kernels=4), 1),
+        (dict(kernels=-1), 1),
+    ]
+    for kw, code in bad:
+        with pytest.raises(K.FwiError) as e:
+            K.fwi_plan_create(_prob(api, **kw), K.W2Params())
+        assert e.value.code == code, kw

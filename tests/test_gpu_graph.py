@@ -1,7 +1,7 @@
 """A whole gradient (forward, misfit, adjoint; for the tiled kernels one
 launch per time step) captured once into a CUDA graph and replayed on new
-models: bitwise the eager result, for the resident, the tiled and the
-checkpointed paths.
+models: bitwise the eager result, for the resident, the tiled, the cluster
+and the checkpointed paths.
 """
 import dataclasses
 
@@ -29,15 +29,16 @@ def T(a):
     return torch.tensor(np.asarray(a), dtype=torch.float32, device=DEV)
 
 
-@pytest.mark.parametrize("nz,nx,nb,nt,ns,K", [
-    (30, 70, 20, 300, 3, 0),      # shared-memory resident kernels
-    (100, 140, 20, 200, 2, 0),    # tiled kernels, one launch per step
-    (100, 140, 20, 200, 2, 64),   # tiled, checkpointed
-    (30, 70, 20, 300, 3, 32),     # resident, checkpointed
+@pytest.mark.parametrize("nz,nx,nb,nt,ns,K,fam", [
+    (30, 70, 20, 300, 3, 0, 0),       # shared-memory resident kernels
+    (100, 140, 20, 200, 2, 0, 2),     # tiled kernels, one launch per step
+    (100, 140, 20, 200, 2, 0, 3),     # cluster kernels
+    (100, 140, 20, 200, 2, 64, 0),    # tiled, checkpointed
+    (30, 70, 20, 300, 3, 32, 0),      # resident, checkpointed
 ])
-def test_gradient_replays_from_a_cuda_graph(api, nz, nx, nb, nt, ns, K):
+def test_gradient_replays_from_a_cuda_graph(api, nz, nx, nb, nt, ns, K, fam):
     gp, _ = problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, v_max=4600.0)
-    gp = dataclasses.replace(gp, checkpoint_every=K)
+    gp = dataclasses.replace(gp, checkpoint_every=K, kernels=fam)
     plan = api.Plan(gp, api.W2Params(n_xi=400))
     d_obs, _ = plan.forward(T(models("layered", [1, 2], nz, nx)), store=False)
     ctx = plan.w2_prepare(d_obs.clone())

@@ -1,9 +1,12 @@
-"""GPU parity of the global-memory tiled propagators (padded grids beyond one
-CTA's shared memory) against the FP64 oracle.
+"""GPU parity of the propagators for padded grids beyond one CTA's shared
+memory against the FP64 oracle: the global-memory tiled kernels and the
+cluster kernels (rows split over 8 CTAs, halos through distributed shared
+memory), each forced through fwi_problem.kernels.
 
 100 x 140 models with a 20-cell layer pad to 120 x 180 cells: 4 x 3 tiles of
-32 x 64 with ragged last tiles in both directions, and too large for the
-shared-memory resident kernels (two levels + a table = 269 KB).
+32 x 64 with ragged last tiles in both directions, 15 rows per CTA of a
+cluster, and too large for the shared-memory resident kernels (two levels + a
+table = 269 KB).
 """
 import dataclasses
 
@@ -35,23 +38,27 @@ def H(t):
     return t.double().cpu().numpy()
 
 
-def _ws_is_tiled(api, gp):
-    h = api.fwi_plan_create(gp, api.W2Params())
-    ws = api.fwi_plan_sizes(h)[0]
-    NXp = (gp.NX + 3) // 4 * 4
-    return ws >= 6 * gp.batch * gp.ns * gp.NZ * NXp * 4
+FAMILIES = ("tiled", "cluster")
 
 
+def _fam(api, name):
+    return {"tiled": api.KERNELS_TILED, "cluster": api.KERNELS_CLUSTER}[name]
+
+
+@pytest.mark.parametrize("fam", FAMILIES)
 @pytest.mark.parametrize("nz,nx,nb,nt,ns,top_bc", [
     (100, 140, 20, 500, 3, 0),
     (100, 140, 20, 500, 2, 1),
-    (90, 301, 10, 300, 2, 0),      # odd padded width (321 -> row pitch 324)
+    (90, 301, 10, 300, 2, 0),      # odd padded width (321; tiled row pitch 324)
+    (250, 60, 12, 300, 2, 1),      # 262 x 84 cells: 33 rows a CTA (the last 31), 13-row strips
+    (230, 270, 15, 300, 2, 1),     # 245 x 300 cells: 31 rows a CTA (the last 28), 19-row strips
 ])
-def test_tiled_forward_matches_oracle(api, nz, nx, nb, nt, ns, top_bc):
+def test_tiled_forward_matches_oracle(api, nz, nx, nb, nt, ns, top_bc, fam):
     gp, op = problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc)
-    assert _ws_is_tiled(api, gp)
+    gp = dataclasses.replace(gp, kernels=_fam(api, fam))
     v = models("curved_faulted", [3, 4], nz, nx)
     with api.Plan(gp) as plan:
+        assert plan.kernels == _fam(api, fam)
         d, _ = plan.forward(T(v))
         torch.cuda.synchronize()
         plan.check()
@@ -60,10 +67,12 @@ def test_tiled_forward_matches_oracle(api, nz, nx, nb, nt, ns, top_bc):
     assert err <= TOL_DATA, err
 
 
+@pytest.mark.parametrize("fam", FAMILIES)
 @pytest.mark.parametrize("top_bc", [0, 1])
-def test_tiled_gradient_matches_oracle(api, top_bc):
+def test_tiled_gradient_matches_oracle(api, top_bc, fam):
     nz, nx, nb, nt, ns = 100, 140, 20, 500, 3
     gp, op = problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc)
+    gp = dataclasses.replace(gp, kernels=_fam(api, fam))
     w2p, ow2 = api.W2Params(n_xi=500), O.W2Params(n_xi=500)
     vt = models("layered", [7, 8], nz, nx)
     v0 = initial(2, nz, nx)
@@ -86,6 +95,7 @@ def test_tiled_checkpoints_are_bitwise_store_all(api):
     w2p = api.W2Params(n_xi=400)
     vt = models("layered", [1, 2], nz, nx)
     v0 = initial(2, nz, nx)
+    gp = dataclasses.replace(gp, kernels=api.KERNELS_TILED)
     out = []
     for K in (0, 37):
         with api.Plan(dataclasses.replace(gp, checkpoint_every=K), w2p) as plan:
@@ -160,3 +170,26 @@ def test_order8_gradient_matches_oracle(api, top_bc):
     assert rel_l2(J, J_o) <= TOL_J * 10, (J, J_o)
     for b in range(2):
         assert rel_l2(g[b], g_o[b]) <= TOL_GRAD, (b, rel_l2(g[b], g_o[b]))
+
+
+@pytest.mark.parametrize("top_bc", [0, 1])
+def test_cluster_gradient_agrees_with_the_tiled_gradient(api, top_bc):
+    # the same recurrences on two kernel families: float rounding apart
+    nz, nx, nb, nt, ns = 120, 200, 16, 400, 3
+    gp, _ = problems(nz, nx, nb, nt, ns, batch=3, f_peak=25.0, top_bc=top_bc)
+    w2p = api.W2Params(n_xi=400)
+    vt = models("curved_faulted", [1, 2, 3], nz, nx)
+    v0 = initial(3, nz, nx)
+    res = {}
+    for fam in FAMILIES:
+        with api.Plan(dataclasses.replace(gp, kernels=_fam(api, fam)), w2p) as plan:
+            d_obs, _ = plan.forward(T(vt), store=False)
+            ctx = plan.w2_prepare(d_obs.clone())
+            J, g, _ = plan.gradient(T(v0), ctx)
+            torch.cuda.synchronize()
+            plan.check()
+            res[fam] = (H(d_obs), H(J), H(g))
+    assert rel_l2(res["cluster"][0], res["tiled"][0]) <= 1e-5
+    assert rel_l2(res["cluster"][1], res["tiled"][1]) <= 1e-4
+    for b in range(3):
+        assert rel_l2(res["cluster"][2][b], res["tiled"][2][b]) <= 1e-3

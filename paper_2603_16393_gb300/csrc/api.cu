@@ -214,13 +214,14 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     pl->cluster = false;
     if (pl->tiled && (fam == FWI_KERNELS_AUTO || fam == FWI_KERNELS_CLUSTER) && order == 4 &&
         p.checkpoint_every == 0 && pl->NX + 4 <= fwi::kCluPitch) {
-        const int C = fwi::kClusterCTAs;
-        const int RC = (pl->NZ + C - 1) / C;
+        // rows per thread strip RS (a compile-time bucket), strips per column,
+        // rows per CTA RC = nstrip RS and CTAs per cluster C = ceil(NZ / RC)
         const int P = fwi::kCluPitch;
+        const int rc0 = (pl->NZ + fwi::kClusterCTAs - 1) / fwi::kClusterCTAs;
         static const int rs_buckets[] = {13, 19};
         int RS = 0, nstrip = 0, threads = 0;
         for (int rs : rs_buckets) {
-            const int ns_ = (RC + rs - 1) / rs;
+            const int ns_ = (rc0 + rs - 1) / rs;
             const int th = (pl->NX * ns_ + 31) / 32 * 32;
             if (th <= fwi::clu_max_threads(rs)) {
                 RS = rs;
@@ -229,33 +230,35 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
                 break;
             }
         }
-        const size_t limit = 227 * 1024;
+        const int RC = nstrip * RS;
+        const int C = RC > 0 ? (pl->NZ + RC - 1) / RC : 0;
+        // static shared memory of the kernels: four mbarriers, a flag, one sum
+        const size_t limit = 227 * 1024 - 64;
         int chunk[2] = {0, 0};
-        if (RS > 0) {
+        if (C >= 2) {
             for (int adj = 0; adj < 2; ++adj) {
-                const size_t fixed = fwi::cluster_smem(nstrip * RS, RC, P, adj != 0, 0, p.nr);
+                const size_t fixed = fwi::cluster_smem(RC, P, adj != 0, 0, p.nr);
                 const size_t per = ((size_t)p.nr + 1) * 4;
                 size_t c = fixed + per > limit ? 0 : (limit - fixed) / per;
                 chunk[adj] = c > 32 ? 32 : (int)c;
             }
         }
-        bool ok = RS > 0 && chunk[0] >= 1 && chunk[1] >= 1;
+        bool ok = C >= 2 && chunk[0] >= 1 && chunk[1] >= 1;
         // the adjoint injects each receiver from the thread owning its cell:
         // at most one receiver per column of a strip
         for (int i = 0; ok && i < p.nr; ++i)
             for (int k = 0; k < i; ++k)
-                if (pl->rec_px[i] == pl->rec_px[k] && pl->rec_pz[i] / RC == pl->rec_pz[k] / RC &&
-                    (pl->rec_pz[i] % RC) / RS == (pl->rec_pz[k] % RC) / RS) {
+                if (pl->rec_px[i] == pl->rec_px[k] && pl->rec_pz[i] / RS == pl->rec_pz[k] / RS) {
                     ok = false;
                     break;
                 }
         if (ok) {
             pl->cluster = true;
-            pl->clu = fwi::ClusterArgs{P, RC, RS, nstrip, nstrip * RS, pl->NXp, 0, nullptr, nullptr};
+            pl->clu = fwi::ClusterArgs{P, C, RC, RS, nstrip, pl->NXp, 0, nullptr, nullptr};
             pl->clu_threads = threads;
             pl->clu_chunk_fwd = chunk[0];
             pl->clu_chunk_adj = chunk[1];
-            // record: kClusterCTAs RC rows per plane at the pitch P - 1
+            // record: C RC rows per plane at the pitch P - 1
             pl->nzs = C * RC;
             pl->rec_pitch = P - 1;
         }
@@ -264,7 +267,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         delete pl;
         return fail(FWI_ERR_UNSUPPORTED,
                     "the cluster kernels take 4th-order, whole-record plans of padded width <= %d "
-                    "whose rows fit 8 CTAs' shared memory (grid %dx%d)",
+                    "whose rows split over 2 to 8 CTAs' shared memory (grid %dx%d)",
                     fwi::kCluPitch - 4, pl->NZ, pl->NX);
     }
     // the adjoint source of a receiver enters through the level psi^{j-1}

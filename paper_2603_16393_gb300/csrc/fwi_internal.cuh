@@ -38,21 +38,23 @@ struct ResidentShape {
     size_t smem;     // dynamic shared memory bytes
 };
 
-// Cluster propagators: a (model, shot) grid split by rows over this many CTAs,
-// shared-memory row pitch (compile time; padded widths up to kCluPitch - 4)
+// Cluster propagators: a (model, shot) grid split by rows over up to
+// kClusterCTAs CTAs of one cluster; shared-memory row pitch (compile time;
+// padded widths up to kCluPitch - 4)
 constexpr int kClusterCTAs = 8;
 constexpr int kCluPitch = 341;
-// threads per CTA of the cluster kernels with RS rows a thread: 96 registers
-// a thread at 672 (21 warps) for the 19-row strips, 80 at 768 for 13 rows
+// threads per CTA of the cluster kernels with RS rows a thread (one CTA per
+// SM): 21 warps put 6 on some scheduler, whose 16K registers then give 80 a
+// thread, as 24 warps do
 __host__ __device__ constexpr int clu_max_threads(int RS) { return RS > 13 ? 672 : 768; }
 
 struct ClusterArgs {
     int P;          // shared-memory row pitch
-    int RC;         // grid rows per CTA
+    int C;          // CTAs per cluster (2..kClusterCTAs)
+    int RC;         // grid rows per CTA = nstrip * RS
     int RS;         // rows per thread strip
     int nstrip;     // strips per column
-    int rows_cap;   // nstrip * RS (row capacity of the field arrays)
-    int NXp;        // row pitch of the record and of the imaging sums in global memory
+    int NXp;        // row pitch of the imaging sums in global memory
     int chunk;      // staged time steps
     float *acc;     // adjoint: imaging sums [bs][NZ][NXp] (to the fold)
     float *acc_src; // adjoint: source-cell sums [bs]
@@ -184,7 +186,7 @@ bool fwd_pair_ok(int NX, int NZ, int NZM);
 cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st);
 // Cluster propagators (whole time loop, store-all plans): shared memory of
 // one CTA, and the launch
-size_t cluster_smem(int rows_cap, int RC, int P, bool adj, int chunk, int nr);
+size_t cluster_smem(int RC, int P, bool adj, int chunk, int nr);
 cudaError_t launch_cluster(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
                            cudaStream_t st);
 cudaError_t launch_tile_fold(const Plan &pl, const PropArgs &a, unsigned char *ws,

@@ -2,14 +2,29 @@
 // CTA's shared memory but small enough for a cluster's (for example 256 x 256
 // models with a 40-cell layer: 296 x 336 cells).
 //
-// The grid of a (model, shot) is split by rows across a cluster of kClu CTAs:
-// CTA c of the cluster keeps rows [c RC, (c+1) RC) of both time levels in its
-// shared memory, with two halo rows above and below.  A thread that computes
-// one of the two first (last) rows of its CTA also stores the new value into
-// the bottom (top) halo rows of the CTA above (below) through distributed
-// shared memory, and one cluster barrier per step (release / acquire) makes
-// those stores visible before the next step reads them.  The fields never
-// leave the chip; only the wavefield record, traces and gradients go to HBM.
+// The grid of a (model, shot) is split by rows across a cluster of C CTAs
+// (2 <= C <= 8, a launch attribute): CTA c keeps rows [c RC, (c+1) RC) of
+// both time levels in its shared memory, with two halo rows above and below.
+// RC is a whole number of RS-row thread strips.  After a step, the threads
+// of a CTA's first (last) strip put their two edge rows of the new level into
+// the bottom (top) halo rows of the CTA above (below) with st.async; each
+// store counts its bytes on the receiving CTA's mbarrier for that level, and a
+// CTA reads a level's halo rows only once its mbarrier has seen all of them.
+// No cluster-wide barrier runs per step, and the fields never leave the chip:
+// only the wavefield record, traces and gradients go to HBM.
+//
+// Ordering, with every CTA's step j ending in its wait for level j+1:
+// * a CTA writes level j+1 into a neighbour's buffer that held level j-1,
+//   whose halo rows that neighbour read only for its own edge rows of level
+//   j; it sent those edge rows (after computing them) before this CTA could
+//   finish waiting for level j, which precedes its step j;
+// * level L counts on mbarrier L mod 4, armed (expected bytes, one arrival)
+//   exactly once: levels 1, 2 before the first step, level L >= 3 at the
+//   start of step L-3, which follows the wait for level L-4 on the same
+//   mbarrier (end of step L-5) and precedes, by a CTA barrier, this CTA's
+//   step L-2 sends of level L-1, without which no neighbour computes level
+//   L.  So a phase is armed before any of its bytes arrive, and its bytes
+//   arrive after the previous phase ended.
 //
 // Same recurrences and coefficient formation as the single-CTA resident
 // kernels: forward in increment form with a difference Laplacian and the
@@ -17,14 +32,16 @@
 // (the receivers' adjoint source through the old level, imaging acc +=
 // psi^{j+1} t^{nt-1-j}, source-cell term kept apart), its imaging sums in
 // shared memory; they go to the tiled kernels' buffers, whose fold kernel
-// finishes.
-// The record of a cluster plan has kClusterCTAs RC rows per plane at the row
+// finishes.  The record of a cluster plan has C RC rows per plane at the row
 // pitch P - 1, so that every record access is a compile-time offset.
 //
-// Every CTA of a cluster executes the same sequence of cluster barriers (no
-// early exit: an invalid velocity only sets the status word).
+// Every halo wait is bounded in time; one that runs out sets
+// FWI_ERR_DEVICE_TIMEOUT and the CTA stops waiting but runs every remaining
+// step, so every CTA reaches the final cluster barrier.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 #include "fwi_device.cuh"
 #include "fwi_internal.cuh"
@@ -35,32 +52,128 @@ namespace fwi {
 
 namespace {
 
+constexpr unsigned long long kHaloWaitNs = 2000000000ull;   // 2 s per level
+constexpr int kHaloBars = 4;   // level L of the fields counts on mbarrier L mod 4
+
 using dev::e_cell;
 using dev::ex_of;
 using dev::ez_of;
 using dev::kappaA_cell;
 using dev::ricker_scaled;
 
-// Values moved through an opaque register copy are recomputed where used
-// instead of being hoisted out of the time loop.
-__device__ __forceinline__ float opaque_c(float x)
+__device__ __forceinline__ unsigned s_u32(const void *p)
 {
-    float y;
-    asm volatile("mov.b32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// The same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned at_rank(unsigned addr, int rank)
+{
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// One float into another CTA's shared memory, its 4 bytes counted on that
+// CTA's mbarrier.
+__device__ __forceinline__ void put_remote(unsigned raddr, float v, unsigned rmbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
+                     raddr),
+                 "r"(__float_as_uint(v)), "r"(rmbar)
+                 : "memory");
+}
+
+// The single arrival of a phase, with the bytes the neighbours will send.
+__device__ __forceinline__ void halo_arm(uint64_t *mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(mb)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool halo_try(uint64_t *mb, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(s_u32(mb)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits (bounded) until the neighbours' halo rows of a level have landed.
+__device__ __forceinline__ void halo_wait(uint64_t *mb, unsigned parity, volatile int *failed,
+                                          int *status)
+{
+    if (*failed || halo_try(mb, parity)) return;
+    const unsigned long long t0 = now_ns();
+    while (!halo_try(mb, parity)) {
+        if (*failed) return;
+        if (now_ns() - t0 > kHaloWaitNs) {
+            *failed = 1;
+            set_status(status, FWI_ERR_DEVICE_TIMEOUT);
+            return;
+        }
+    }
+}
+
+// One thread: set up the mbarriers and arm levels 1 and 2 (step j arms level
+// j+3, so that every level is armed exactly once).
+__device__ __forceinline__ void halo_init(uint64_t *mb, unsigned bytes, int nt)
+{
+    for (int k = 0; k < kHaloBars; ++k)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(mb + k)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int L = 1; L <= 2 && L <= nt; ++L) halo_arm(mb + L, bytes);
+}
+
+// Parity of the mbarrier phase that counts level L >= 1.
+__device__ __forceinline__ unsigned halo_parity(int L) { return (unsigned)((L - 1) >> 2) & 1u; }
+
+// Edge rows of the new level (np: this thread's first row) to the neighbours'
+// halo rows: rows 0, 1 of a first strip to rows RC, RC+1 of the CTA above,
+// rows RS-2, RS-1 of a last strip to rows -2, -1 of the CTA below.
+template <int P, int RS>
+__device__ __forceinline__ void send_edges(const float *np, int RC, int crank, bool up, bool dn,
+                                           uint64_t *mb)
+{
+    if (up) {
+        const unsigned rm = at_rank(s_u32(mb), crank - 1);
+        const unsigned ra = at_rank(s_u32(np + RC * P), crank - 1);
+        put_remote(ra, np[0], rm);
+        put_remote(ra + 4 * P, np[P], rm);
+    }
+    if (dn) {
+        const unsigned rm = at_rank(s_u32(mb), crank + 1);
+        const unsigned ra = at_rank(s_u32(np + (RS - 2 - RC) * P), crank + 1);
+        put_remote(ra, np[(RS - 2) * P], rm);
+        put_remote(ra + 4 * P, np[(RS - 1) * P], rm);
+    }
 }
 
 template <int P, int RS, int TOPBC, bool STORE>
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(clu_max_threads(RS), 1)
+__global__ void __launch_bounds__(clu_max_threads(RS), 1)
 k_clu_fwd(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArgs e)
 {
     cg::cluster_group cl = cg::this_cluster();
-    const int crank = (int)cl.block_rank();
-    const int bs = blockIdx.x / kClusterCTAs, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int C = e.C, crank = (int)cl.block_rank();
+    const int bs = blockIdx.x / C, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int NX = a.NX, NZ = a.NZ, RC = e.RC;
-    const int FS = (e.rows_cap + 4) * P;
+    const int FS = (RC + 4) * P;
     extern __shared__ float sm[];
+    __shared__ uint64_t mb[kHaloBars];
+    __shared__ int failed;
     float *U0 = sm, *U1 = U0 + FS, *ABt = U1 + FS, *ST = ABt + RC * P;
     float *RSw = ST + e.chunk * a.nr;
     const int g0 = crank * RC;                 // first grid row of this CTA
@@ -83,9 +196,9 @@ k_clu_fwd(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
     int bad = 0;
 #pragma unroll
     for (int r = 0; r < RS; ++r) {
-        const int lr = l0 + r, gz = g0 + lr;
+        const int gz = g0 + l0 + r;
         float k = 0.f;
-        if (active && lr < RC && gz < NZ) {
+        if (active && gz < NZ) {
             const float vv = vb[min(gz, a.nz - 1) * a.nx + ixc];
             if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
             k = kappaA_cell(vv, x, gz, a);
@@ -94,20 +207,28 @@ k_clu_fwd(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
         vi[r] = 0.f;
     }
     if (bad) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
-    const bool has_up = crank > 0, has_dn = crank + 1 < kClusterCTAs;
+    const bool has_up = crank > 0, has_dn = crank + 1 < C;
+    const bool send_up = active && strip == 0 && has_up;
+    const bool send_dn = active && strip == e.nstrip - 1 && has_dn;
+    const bool top_strip = active && strip == 0 && crank == 0;
+    const unsigned halo_bytes = (unsigned)((has_up ? 1 : 0) + (has_dn ? 1 : 0)) * 8u * NX;
+    if (tid == 0) {
+        halo_init(mb, halo_bytes, a.nt);
+        failed = 0;
+    }
     // source owner
     const int sz = a.src_pz[s], sx = a.src_px[s];
-    const int src_row = (active && x == sx && sz >= g0 + l0 && sz < g0 + l0 + RS && sz - g0 < RC)
-                            ? sz - g0 - l0 : -1;
+    const int src_row = (active && x == sx && sz >= g0 + l0 && sz < g0 + l0 + RS) ? sz - g0 - l0 : -1;
     float ka_src = 0.f;
 #pragma unroll
     for (int r = 0; r < RS; ++r)
         if (r == src_row) ka_src = ka[r];
-    // record plane of step j: rows [0, kClusterCTAs RC) at the compile-time pitch PRC
+    // record plane of step j: rows [0, C RC) at the compile-time pitch PRC
     constexpr int PRC = P - 1;
-    const size_t plane = (size_t)kClusterCTAs * RC * PRC;
-    float *sw = STORE ? a.snap + (size_t)bs * a.rec_planes * plane + (size_t)(g0 + l0) * PRC + x : nullptr;
-    cl.sync();   // every CTA's fields are zero before any neighbour stores into them
+    const size_t plane = (size_t)C * RC * PRC;
+    float *sw = STORE ? a.snap + (size_t)bs * a.rec_planes * plane + (size_t)(g0 + l0) * PRC + x
+                      : nullptr;
+    cl.sync();   // every CTA's fields are zero and its mbarriers set up
 
     for (int j0 = 0; j0 < a.nt; j0 += e.chunk) {
         const int nch = min(e.chunk, a.nt - j0);
@@ -117,54 +238,62 @@ k_clu_fwd(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
             const int j = j0 + jj;
             const float *cur = (j & 1) ? U1 : U0;
             float *nxt = (j & 1) ? U0 : U1;
+            if (tid == 0 && j + 3 <= a.nt) halo_arm(&mb[(j + 3) & 3], halo_bytes);
             if (active) {
                 const float *cp = cur + (l0 + 2) * P + x + 2;
+                float *np = nxt + (l0 + 2) * P + x + 2;
+                const float *abp = ABt + l0 * P + x;
                 float wm2 = cp[-2 * P], wm1 = cp[-P], w0 = cp[0], wp1 = cp[P];
+                float Dp = w0 - wm1, Em2 = w0 - wm2, Em1 = wp1 - wm1;
 #pragma unroll
                 for (int r = 0; r < RS; ++r) {
-                    const int lr = l0 + r;
                     const float *c = cp + r * P;
                     const float wp2 = c[2 * P];
-                    const float dzA = (wm1 - w0) + (wp1 - w0);
-                    const float dzB = (wm2 - w0) + (wp2 - w0);
+                    const float Dn = wp1 - w0;
+                    const float E0 = wp2 - w0;
+                    const float dzA = Dn - Dp;
+                    const float dzB = E0 - Em2;
                     const float dxA = (c[-1] - w0) + (c[1] - w0);
                     const float dxB = (c[-2] - w0) + (c[2] - w0);
                     float lap = a.cx1 * dxA;
                     lap = fmaf(a.cx2, dxB, lap);
                     lap = fmaf(a.cz1, dzA, lap);
                     lap = fmaf(a.cz2, dzB, lap);
-                    if (lr < RC) {
-                        const float ab = ABt[lr * P + x];
-                        vi[r] = fmaf(ka[r], lap, ab * vi[r]);
-                        float un = w0 + vi[r];
-                        if (r == src_row) {
-                            // point source: + kappa A s (increment and field)
-                            const float d = ka_src * RSw[jj];
-                            vi[r] += d;
-                            un += d;
-                        }
-                        nxt[(lr + 2) * P + x + 2] = un;
-                        // halo rows of the neighbours (their copies of this level)
-                        if (lr < 2 && has_up)
-                            cl.map_shared_rank(nxt, crank - 1)[(RC + lr + 2) * P + x + 2] = un;
-                        if (lr >= RC - 2 && has_dn)
-                            cl.map_shared_rank(nxt, crank + 1)[(lr - RC + 2) * P + x + 2] = un;
-                        if (TOPBC == 1 && crank == 0 && (lr == 1 || lr == 2))
-                            nxt[(2 - lr) * P + x + 2] = un;   // mirrored ghost row -lr
-                        if (STORE) sw[r * PRC] = lap;
+                    vi[r] = fmaf(ka[r], lap, abp[r * P] * vi[r]);
+                    const float un = w0 + vi[r];
+                    np[r * P] = un;
+                    if (TOPBC == 1 && (r == 1 || r == 2)) {
+                        if (top_strip) np[-r * P] = un;   // mirrored ghost rows -1, -2
                     }
+                    if (STORE) sw[r * PRC] = lap;
+                    Dp = Dn;
+                    Em2 = Em1;
+                    Em1 = E0;
                     wm2 = wm1;
                     wm1 = w0;
                     w0 = wp1;
                     wp1 = wp2;
                 }
+                if (src_row >= 0) {
+                    // point source: + kappa A s at the source cell (increment and field)
+                    const float d = ka_src * RSw[jj];
+#pragma unroll
+                    for (int r = 0; r < RS; ++r)
+                        if (r == src_row) vi[r] += d;
+                    np[src_row * P] += d;
+                    if (TOPBC == 1 && top_strip && (src_row == 1 || src_row == 2))
+                        np[-src_row * P] += d;
+                }
+                send_edges<P, RS>(np, RC, crank, send_up, send_dn, &mb[(j + 1) & 3]);
             }
             if (STORE) sw += plane;
-            cl.sync();
+            __syncthreads();
             for (int i = tid; i < a.nr; i += nth) {
                 const int rz = a.rec_pz[i] - g0;
                 if (rz >= 0 && rz < RC) ST[jj * a.nr + i] = nxt[(rz + 2) * P + a.rec_px[i] + 2];
             }
+            // the neighbours' edge rows of level j+1 in this CTA's halo rows
+            halo_wait(&mb[(j + 1) & 3], halo_parity(j + 1), &failed, a.status);
         }
         __syncthreads();
         float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
@@ -175,20 +304,24 @@ k_clu_fwd(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
         }
         __syncthreads();
     }
+    cl.sync();   // no CTA leaves while a neighbour may still write into it
 }
 
 template <int P, int RS, int TOPBC>
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(clu_max_threads(RS), 1)
+__global__ void __launch_bounds__(clu_max_threads(RS), 1)
 k_clu_adj(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArgs e)
 {
     cg::cluster_group cl = cg::this_cluster();
-    const int crank = (int)cl.block_rank();
-    const int bs = blockIdx.x / kClusterCTAs, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int C = e.C, crank = (int)cl.block_rank();
+    const int bs = blockIdx.x / C, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int NX = a.NX, NZ = a.NZ, RC = e.RC;
-    const int FS = (e.rows_cap + 4) * P;
-    extern __shared__ float sm[];
+    const int FS = (RC + 4) * P;
     constexpr int PRC = P - 1;
+    extern __shared__ float sm[];
+    __shared__ uint64_t mb[kHaloBars];
+    __shared__ int failed;
+    __shared__ float acc_src;
     // imaging sums acc of this CTA's cells live in shared memory (row pitch PRC)
     float *U0 = sm, *U1 = U0 + FS, *K = U1 + FS, *ACC = K + RC * P, *IC = ACC + RC * PRC;
     float *ST = IC + a.nr, *RSw = ST + e.chunk * a.nr;
@@ -219,25 +352,35 @@ k_clu_adj(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
     const int l0 = strip * RS;
     const float ex = ex_of(x, a);
     const float zbf = (float)(g0 + l0 - (a.nz - 1));
-    const bool has_up = crank > 0, has_dn = crank + 1 < kClusterCTAs;
+    const bool has_up = crank > 0, has_dn = crank + 1 < C;
+    const bool send_up = active && strip == 0 && has_up;
+    const bool send_dn = active && strip == e.nstrip - 1 && has_dn;
+    const bool top_strip = active && strip == 0 && crank == 0;
+    const unsigned halo_bytes = (unsigned)((has_up ? 1 : 0) + (has_dn ? 1 : 0)) * 8u * NX;
+    if (tid == 0) {
+        halo_init(mb, halo_bytes, a.nt);
+        failed = 0;
+        acc_src = 0.f;
+    }
     // receiver owned by this thread (at most one per column of a strip)
     int inj_slot = -1;
     for (int i = 0; i < a.nr; ++i) {
         const int rz = a.rec_pz[i] - g0, rx = a.rec_px[i];
-        if (active && x == rx && rz >= l0 && rz < l0 + RS && rz < RC) inj_slot = i;
+        if (active && x == rx && rz >= l0 && rz < l0 + RS) inj_slot = i;
     }
+    const int inj_off = inj_slot >= 0 ? (a.rec_pz[inj_slot] - g0 + 2) * P + x + 2 : 0;
     const int sz = a.src_pz[s], sx = a.src_px[s];
     const bool src_here = sz >= g0 && sz < g0 + RC;
-    __shared__ float acc_src;
-    if (tid == 0) acc_src = 0.f;
-    const size_t plane = (size_t)kClusterCTAs * RC * PRC;
+    const size_t plane = (size_t)C * RC * PRC;
     float sv[RS];
     // record plane read next: forward step nt-1, then one plane back per step
-    const float *sr = a.snap + ((size_t)bs * a.rec_planes + (a.nt - 1)) * plane + (size_t)(g0 + l0) * PRC + x;
+    const float *sr =
+        a.snap + ((size_t)bs * a.rec_planes + (a.nt - 1)) * plane + (size_t)(g0 + l0) * PRC + x;
 #pragma unroll
-    for (int r = 0; r < RS; ++r) sv[r] = (active && l0 + r < RC) ? sr[r * PRC] : 0.f;
+    for (int r = 0; r < RS; ++r) sv[r] = active ? sr[r * PRC] : 0.f;
     float *ac = ACC + l0 * PRC + x;
-    cl.sync();
+    const float *kp = K + l0 * P + x;
+    cl.sync();   // every CTA's fields are zero and its mbarriers set up
 
     for (int j0 = 0; j0 < a.nt; j0 += e.chunk) {
         const int nch = min(e.chunk, a.nt - j0);
@@ -252,19 +395,15 @@ k_clu_adj(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
             const int j = j0 + jj;
             const float *cur = (j & 1) ? U1 : U0;
             float *nxt = (j & 1) ? U0 : U1;
-            if (inj_slot >= 0) {
-                const int rz = a.rec_pz[inj_slot] - g0, rx = a.rec_px[inj_slot];
-                nxt[(rz + 2) * P + rx + 2] -= ST[jj * a.nr + inj_slot];   // (kappa/B) q
-            }
+            if (tid == 0 && j + 3 <= a.nt) halo_arm(&mb[(j + 3) & 3], halo_bytes);
+            if (inj_slot >= 0) nxt[inj_off] -= ST[jj * a.nr + inj_slot];   // (kappa/B) q
             if (j + 1 < a.nt) sr -= plane;
             if (active) {
                 const float *cp = cur + (l0 + 2) * P + x + 2;
                 float *np = nxt + (l0 + 2) * P + x + 2;
-                const float exs = opaque_c(ex), zb = opaque_c(zbf);
                 float wm2 = cp[-2 * P], wm1 = cp[-P], w0 = cp[0], wp1 = cp[P];
 #pragma unroll
                 for (int r = 0; r < RS; ++r) {
-                    const int lr = l0 + r;
                     const float *c = cp + r * P;
                     const float wp2 = c[2 * P];
                     float lap = a.c0 * w0;
@@ -272,32 +411,29 @@ k_clu_adj(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
                     lap = fmaf(a.cx2, c[-2] + c[2], lap);
                     lap = fmaf(a.cz1, wm1 + wp1, lap);
                     lap = fmaf(a.cz2, wm2 + wp2, lap);
-                    if (TOPBC == 1 && crank == 0 && (lr == 1 || lr == 2))
+                    if (TOPBC == 1 && (r == 1 || r == 2)) {
                         // transpose of the mirrored top: reflected weights onto rows 1, 2
-                        lap += (lr == 1) ? a.cz1 * wm1 + a.cz2 * w0 : a.cz2 * wm2;
-                    if (lr < RC) {
-                        const float ee = exs + ez_of(zb + (float)r, a);
-                        const float A2 = __fdividef(2.f, 1.f + ee);   // 2A
-                        const float AB = A2 - 1.f;                     // A B
-                        const float fo = np[r * P];
-                        const float fn = fmaf(K[lr * P + x], lap, fmaf(A2, w0, -AB * fo));
-                        np[r * P] = fn;
-                        if (lr < 2 && has_up)
-                            cl.map_shared_rank(nxt, crank - 1)[(RC + lr + 2) * P + x + 2] = fn;
-                        if (lr >= RC - 2 && has_dn)
-                            cl.map_shared_rank(nxt, crank + 1)[(lr - RC + 2) * P + x + 2] = fn;
-                        ac[r * PRC] = fmaf(fn, sv[r], ac[r * PRC]);
-                        sv[r] = sr[r * PRC];
+                        if (top_strip) lap += (r == 1) ? a.cz1 * wm1 + a.cz2 * w0 : a.cz2 * wm2;
                     }
+                    const float ee = ex + ez_of(zbf + (float)r, a);
+                    const float A2 = __fdividef(2.f, 1.f + ee);   // 2A
+                    const float AB = A2 - 1.f;                     // A B
+                    const float fo = np[r * P];
+                    const float fn = fmaf(kp[r * P], lap, fmaf(A2, w0, -AB * fo));
+                    np[r * P] = fn;
+                    ac[r * PRC] = fmaf(fn, sv[r], ac[r * PRC]);
+                    sv[r] = sr[r * PRC];
                     wm2 = wm1;
                     wm1 = w0;
                     w0 = wp1;
                     wp1 = wp2;
                 }
+                send_edges<P, RS>(np, RC, crank, send_up, send_dn, &mb[(j + 1) & 3]);
             }
-            cl.sync();
+            __syncthreads();
             if (tid == nth - 1 && src_here)
                 acc_src = fmaf(nxt[(sz - g0 + 2) * P + sx + 2], RSw[jj], acc_src);
+            halo_wait(&mb[(j + 1) & 3], halo_parity(j + 1), &failed, a.status);
         }
         __syncthreads();
     }
@@ -307,6 +443,7 @@ k_clu_adj(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
         if (gz < NZ) e.acc[((size_t)bs * NZ + gz) * e.NXp + px] = ACC[lr * PRC + px];
     }
     if (tid == 0 && src_here) e.acc_src[bs] = acc_src;
+    cl.sync();   // no CTA leaves while a neighbour may still write into it
 }
 
 template <typename Kern>
@@ -316,19 +453,31 @@ cudaError_t launch_clu(Kern kern, const PropArgs &a, const ClusterArgs &e, int n
     cudaError_t err =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    kern<<<nbs * kClusterCTAs, threads, smem, st>>>(a, e);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nbs * e.C));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)e.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a, e);
 }
 
 }  // namespace
 
-size_t cluster_smem(int rows_cap, int RC, int P, bool adj, int chunk, int nr)
+size_t cluster_smem(int RC, int P, bool adj, int chunk, int nr)
 {
     // two levels with halo rows + one per-cell table (+ the imaging sums and
     // kappa/B per receiver for the adjoint) + staging of receiver samples and
     // the wavelet
-    return ((size_t)2 * (rows_cap + 4) * P + (size_t)RC * P +
-            (adj ? (size_t)RC * (P - 1) + nr : 0) + (size_t)chunk * (nr + 1)) * sizeof(float);
+    return ((size_t)2 * (RC + 4) * P + (size_t)RC * P + (adj ? (size_t)RC * (P - 1) + nr : 0) +
+            (size_t)chunk * (nr + 1)) *
+           sizeof(float);
 }
 
 cudaError_t launch_cluster(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
@@ -339,7 +488,7 @@ cudaError_t launch_cluster(const Plan &pl, bool adj, const PropArgs &a, unsigned
     e.acc = (float *)(ws + pl.ws_t_acc);
     e.acc_src = (float *)(ws + pl.ws_t_accsrc);
     e.chunk = adj ? pl.clu_chunk_adj : pl.clu_chunk_fwd;
-    const size_t smem = cluster_smem(e.rows_cap, e.RC, e.P, adj, e.chunk, pl.p.nr);
+    const size_t smem = cluster_smem(e.RC, e.P, adj, e.chunk, pl.p.nr);
     const int threads = pl.clu_threads;
     const int tb = pl.p.top_bc;
     const bool store = a.snap != nullptr;

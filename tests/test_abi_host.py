@@ -71,11 +71,12 @@ def test_plan_of_a_grid_beyond_shared_memory_uses_the_tiled_fields(api):
     NZ, NX, NXp = 296, 336, 336
     assert snap == B * ns * nt * NZ * NXp * 4
     assert ws >= 6 * B * ns * NZ * NXp * 4 + 2 * B * NZ * NXp * 4
-    # the automatic choice for this grid: a cluster of 8 CTAs, 37 rows each;
-    # record rows at the cluster kernels' pitch 340
+    # the automatic choice for this grid: a cluster of 8 CTAs of 38 rows (two
+    # 19-row thread strips; the last CTA holds 30 grid rows); record rows at
+    # the cluster kernels' pitch 340
     h = api.fwi_plan_create(prob, api.W2Params())
     assert api.fwi_plan_kernels(h) == api.KERNELS_CLUSTER
-    assert api.fwi_plan_sizes(h)[2] == B * ns * nt * (8 * 37) * 340 * 4
+    assert api.fwi_plan_sizes(h)[2] == B * ns * nt * (8 * 38) * 340 * 4
     # odd padded width: rows padded to a multiple of 4 floats
     prob = _prob(api, nz=200, nx=301, nt=nt, batch=1, src_ix=(0, 75, 150, 225, 300),
                  rec_iz=(0,) * 301, rec_ix=tuple(range(301)))
@@ -187,9 +188,15 @@ def test_kernel_family_selection(api):
     for fam in (K.KERNELS_RESIDENT, K.KERNELS_TILED, K.KERNELS_CLUSTER):
         h = K.fwi_plan_create(_prob(api, kernels=fam), K.W2Params())
         assert K.fwi_plan_kernels(h) == fam
-    # a cluster plan's record: 8 x ceil(110 / 8) = 112 rows at the pitch 340
+    # a cluster plan's record: ceil(110 / 8) = 14 rows a CTA round up to two
+    # 13-row strips, so 5 CTAs of 26 rows: 130 rows at the pitch 340
     h = K.fwi_plan_create(_prob(api, kernels=K.KERNELS_CLUSTER), K.W2Params())
-    assert K.fwi_plan_sizes(h)[2] == 3 * 5 * 1000 * 112 * 340 * 4
+    assert K.fwi_plan_sizes(h)[2] == 3 * 5 * 1000 * 130 * 340 * 4
+    # a grid of 13 rows or fewer would need a cluster of one CTA
+    with pytest.raises(K.FwiError) as e:
+        K.fwi_plan_create(_prob(api, nz=10, nb=3, src_iz=(0,), src_ix=(0,),
+                                kernels=K.KERNELS_CLUSTER), K.W2Params())
+    assert e.value.code == 3
     # checkpointed or 8th-order plans of a cluster-sized grid run tiled
     for kw in (dict(checkpoint_every=32), dict(space_order=8)):
         assert K.fwi_plan_kernels(K.fwi_plan_create(_prob(api, nz=200, **kw), K.W2Params())) \

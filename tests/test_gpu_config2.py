@@ -96,7 +96,7 @@ def test_8_models_256x256_16_shots_2000_steps(api):
     adj = np.random.default_rng(0).standard_normal((B, ns, gp.nr, nt))
     adj = adj.astype(np.float32).astype(np.float64)
     with api.Plan(gp) as plan:
-        assert plan.kernels == api.KERNELS_CLUSTER      # 296 x 336 cells: 8 CTAs of 37 rows
+        assert plan.kernels == api.KERNELS_CLUSTER      # 296 x 336 cells: 8 CTAs of 38 rows
         d_obs, _ = plan.forward(T(vt), store=False)
         d_obs = d_obs.clone()
         # the sampled instance observes the oracle's data

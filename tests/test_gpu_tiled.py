@@ -4,9 +4,9 @@ cluster kernels (rows split over 8 CTAs, halos through distributed shared
 memory), each forced through fwi_problem.kernels.
 
 100 x 140 models with a 20-cell layer pad to 120 x 180 cells: 4 x 3 tiles of
-32 x 64 with ragged last tiles in both directions, 15 rows per CTA of a
-cluster, and too large for the shared-memory resident kernels (two levels + a
-table = 269 KB).
+32 x 64 with ragged last tiles in both directions, a cluster of 5 CTAs of 26
+rows (the last holds 16), and too large for the shared-memory resident
+kernels (two levels + a table = 269 KB).
 """
 import dataclasses
 
@@ -49,9 +49,9 @@ def _fam(api, name):
 @pytest.mark.parametrize("nz,nx,nb,nt,ns,top_bc", [
     (100, 140, 20, 500, 3, 0),
     (100, 140, 20, 500, 2, 1),
-    (90, 301, 10, 300, 2, 0),      # odd padded width (321; tiled row pitch 324)
-    (250, 60, 12, 300, 2, 1),      # 262 x 84 cells: 33 rows a CTA (the last 31), 13-row strips
-    (230, 270, 15, 300, 2, 1),     # 245 x 300 cells: 31 rows a CTA (the last 28), 19-row strips
+    (90, 301, 10, 300, 2, 0),      # odd padded width (321; tiled row pitch 324); 8 CTAs of 13 rows
+    (250, 60, 12, 300, 2, 1),      # 262 x 84 cells: 7 CTAs of three 13-row strips, the last 28 rows
+    (230, 270, 15, 300, 2, 1),     # 245 x 300 cells: 7 CTAs of two 19-row strips, the last 17 rows
 ])
 def test_tiled_forward_matches_oracle(api, nz, nx, nb, nt, ns, top_bc, fam):
     gp, op = problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc)
@@ -175,6 +175,7 @@ def test_order8_gradient_matches_oracle(api, top_bc):
 @pytest.mark.parametrize("top_bc", [0, 1])
 def test_cluster_gradient_agrees_with_the_tiled_gradient(api, top_bc):
     # the same recurrences on two kernel families: float rounding apart
+    # (136 x 232 cells: 6 CTAs of 26 rows, the last holding 6)
     nz, nx, nb, nt, ns = 120, 200, 16, 400, 3
     gp, _ = problems(nz, nx, nb, nt, ns, batch=3, f_peak=25.0, top_bc=top_bc)
     w2p = api.W2Params(n_xi=400)

@@ -64,17 +64,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def record_traffic(units):
+def record_traffic(units, path="resident", workload="70x70", nt=0):
     """DRAM bytes per launch of the two propagators from the committed ncu
-    capture, scaled by (model, shot) units; None once the kernel source has
-    changed since the capture."""
+    capture of that kernel family, scaled by (model, shot) units (and, for
+    the cluster kernels, captured per time step, by the steps); None once the
+    kernel source has changed since the capture, or for a workload that was
+    not captured."""
     import hashlib
+    name = {"resident": "propagators_traffic.json",
+            "cluster": f"cluster_traffic_{workload}.json"}.get(path)
     try:
-        with open(os.path.join(ROOT, "profiles", "propagators_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             rec = json.load(f)
         with open(os.path.join(ROOT, rec["source"]), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
                 return None
+        if "dram_bytes_per_unit_step" in rec:
+            return {k: v * units * nt for k, v in rec["dram_bytes_per_unit_step"].items()}
         return {k: v * units for k, v in rec["dram_bytes_per_unit"].items()}
     except Exception:
         return None
@@ -260,20 +266,21 @@ def run_ours(args, rank, world, local_rank):
         # preconditioned update (no network: v' = v0hat = v, g = h = dJ/dv)
         api.fwi_guided_step(B, NZ_PHYS, NX_PHYS, gparams, v_in, v_in, grad, grad, v_out, rho)
 
-    # library kernels per step: prepare (3), forward, misfit (2), adjoint +
-    # shot sum, guided (1); the cluster adjoint adds a fold; the tiled
-    # propagators launch once per time step, plus a set-up (and a resume per
-    # recomputed segment) and a final gather or fold
+    # library kernels per step: prepare (4: observation max, per-trace
+    # preparation, two sums), forward, misfit (2), adjoint + shot sum, guided
+    # (1); the cluster adjoint adds a fold; the tiled propagators launch once
+    # per time step, plus a set-up (and a resume per recomputed segment) and a
+    # final gather or fold
     if path == "resident":
-        kernels_per_step = 3 + 1 + 2 + 2 + 1
+        kernels_per_step = 4 + 1 + 2 + 2 + 1
     elif path == "cluster":
-        kernels_per_step = 3 + 1 + 2 + 3 + 1
+        kernels_per_step = 4 + 1 + 2 + 3 + 1
     else:
         K = wl["ckpt"]
         S = -(-NT // K) if K else 0
         fwd_k = 1 + NT + 1
         adj_k = (2 * S + (S - 1) + 2 * NT + 2) if K else (1 + NT + 2)
-        kernels_per_step = 3 + fwd_k + 2 + adj_k + 1
+        kernels_per_step = 4 + fwd_k + 2 + adj_k + 1
 
     def barrier():
         if world > 1:
@@ -358,7 +365,7 @@ def run_ours(args, rank, world, local_rank):
     hbm_peak, peak_kind = peaks()
     dom = max((adj_ms, adj_bytes, adj_name, "adjoint"), (fwd_ms, fwd_bytes, fwd_name, "forward"))
     achieved = dom[1] / (dom[0] * 1e-3) / 1e9
-    traffic = record_traffic(B * NS) if path == "resident" else None
+    traffic = record_traffic(B * NS, path, args.workload, NT)
     traffic = traffic[dom[3]] if traffic else None
     value = world * B / (ms * 1e-3)
 

@@ -311,16 +311,23 @@ __device__ __forceinline__ void quantile(const df *G, const df *Gm, int nt, df u
 }
 
 // ------------------------------------------------------------------ kernels
-// M[b] = max |d_obs| over the instance
-__global__ void __launch_bounds__(1024) k_obs_max(const float *__restrict__ d, size_t per_inst,
-                                                  float *__restrict__ M)
+// M[b] = max |d_obs| of instance b (blockIdx.y) over its slices (blockIdx.x):
+// each CTA reduces one slice and folds it in with an integer atomicMax on the
+// float bits (M zeroed first; |d| >= 0, whose bit patterns order as the
+// values do, so the result does not depend on the order of the CTAs).
+constexpr int kObsMaxThreads = 256;
+__global__ void __launch_bounds__(kObsMaxThreads)
+    k_obs_max(const float *__restrict__ d, size_t per_inst, size_t slice, float *__restrict__ M)
 {
-    __shared__ float red[40];
-    const float *db = d + (size_t)blockIdx.x * per_inst;
+    __shared__ float red[kObsMaxThreads / 32 + 1];
+    const float *db = d + (size_t)blockIdx.y * per_inst;
+    const size_t i0 = (size_t)blockIdx.x * slice;
+    const size_t i1 = i0 + slice < per_inst ? i0 + slice : per_inst;
     float m = 0.f;
-    for (size_t i = threadIdx.x; i < per_inst; i += blockDim.x) m = fmaxf(m, fabsf(db[i]));
-    m = block_reduce<1, 1024>(m, red);
-    if (threadIdx.x == 0) M[blockIdx.x] = m;
+    for (size_t i = i0 + threadIdx.x; i < i1; i += kObsMaxThreads) m = fmaxf(m, fabsf(db[i]));
+    m = block_reduce<1, kObsMaxThreads>(m, red);
+    if (threadIdx.x == 0)
+        atomicMax(reinterpret_cast<unsigned *>(M) + blockIdx.y, __float_as_uint(m));
 }
 
 __global__ void __launch_bounds__(NT_W2) k_obs_trace(const float *__restrict__ d_obs, W2Args a)
@@ -497,7 +504,19 @@ cudaError_t launch_w2_prepare(const Plan &pl, const float *d_obs, unsigned char 
 {
     W2Args a = make_w2(pl, ctx);
     const int B = pl.p.batch;
-    k_obs_max<<<B, 1024, 0, st>>>(d_obs, (size_t)a.ntr * a.nt, a.c.M);
+    {
+        // about eight CTAs per SM over all instances, slices of >= 4096 samples
+        const size_t per_inst = (size_t)a.ntr * a.nt;
+        size_t nsl = (per_inst + 4095) / 4096;
+        const size_t cap = (size_t)(B < 1216 ? 1216 / B : 1);
+        if (nsl > cap) nsl = cap;
+        if (nsl < 1) nsl = 1;
+        const size_t slice = (per_inst + nsl - 1) / nsl;
+        cudaError_t e0 = cudaMemsetAsync(a.c.M, 0, (size_t)B * sizeof(float), st);
+        if (e0 != cudaSuccess) return e0;
+        k_obs_max<<<dim3((unsigned)nsl, (unsigned)B), kObsMaxThreads, 0, st>>>(d_obs, per_inst,
+                                                                             slice, a.c.M);
+    }
     const size_t sm = obs_trace_smem(a.nt);
     cudaError_t e = cudaFuncSetAttribute(k_obs_trace, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);

@@ -64,12 +64,12 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def record_traffic(units, path="resident", workload="70x70", nt=0):
-    """DRAM bytes per launch of the two propagators from the committed ncu
-    capture of that kernel family, scaled by (model, shot) units (and, for
-    the cluster kernels, captured per time step, by the steps); None once the
-    kernel source has changed since the capture, or for a workload that was
-    not captured."""
+def record_traffic(units, path="resident", workload="70x70", nt=0, what="dram_bytes"):
+    """Counts per launch of the two propagators from the committed ncu capture
+    of that kernel family (what = "dram_bytes" or "smem_wavefronts"), scaled
+    by (model, shot) units (and, for the cluster kernels, captured per time
+    step, by the steps); None once the kernel source has changed since the
+    capture, or for a workload that was not captured."""
     import hashlib
     name = {"resident": "propagators_traffic.json",
             "cluster": f"cluster_traffic_{workload}.json"}.get(path)
@@ -79,9 +79,9 @@ def record_traffic(units, path="resident", workload="70x70", nt=0):
         with open(os.path.join(ROOT, rec["source"]), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
                 return None
-        if "dram_bytes_per_unit_step" in rec:
-            return {k: v * units * nt for k, v in rec["dram_bytes_per_unit_step"].items()}
-        return {k: v * units for k, v in rec["dram_bytes_per_unit"].items()}
+        if f"{what}_per_unit_step" in rec:
+            return {k: v * units * nt for k, v in rec[f"{what}_per_unit_step"].items()}
+        return {k: v * units for k, v in rec[f"{what}_per_unit"].items()}
     except Exception:
         return None
 
@@ -368,6 +368,23 @@ def run_ours(args, rank, world, local_rank):
     traffic = record_traffic(B * NS, path, args.workload, NT)
     traffic = traffic[dom[3]] if traffic else None
     value = world * B / (ms * 1e-3)
+    # the on-chip propagators (fields in shared memory) are bound inside the
+    # SM, by the shared-memory pipe: one wavefront (up to 128 B) per clock per
+    # SM; the wavefronts per launch come from the committed capture
+    roof_smem = None
+    wf = record_traffic(B * NS, path, args.workload, NT, what="smem_wavefronts")
+    if wf and path in ("resident", "cluster"):
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_wf = n_sm * mhz * 1e6
+        per = {k: wf[k] / (t * 1e-3) for k, t in (("forward", fwd_ms), ("adjoint", adj_ms))}
+        roof_smem = {"bound": "smem", "kernel": dom[2], "achieved": per[dom[3]],
+                     "peak": peak_wf, "unit": "shared-memory wavefronts/s",
+                     "frac": per[dom[3]] / peak_wf,
+                     "frac_forward": per["forward"] / peak_wf,
+                     "frac_adjoint": per["adjoint"] / peak_wf,
+                     "peak_source": f"1 wavefront per clock per SM x {n_sm} SMs x {mhz:.0f} MHz "
+                                    "(sampled clock)"}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.workload != "512x1024":
@@ -398,6 +415,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": traffic, "algorithmic_bytes": dom[1],
                      "peak_source": peak_kind, "ms_per_launch": dom[0]},
+        "roofline_smem": roof_smem,
         "kernel_ms": {"forward": fwd_ms, "adjoint": adj_ms},
         "e2e": {"value": world * B / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

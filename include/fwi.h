@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 10300  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 10400  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -309,6 +309,39 @@ FWI_API fwi_status fwi_image_metrics(int batch, int nz, int nx, double data_rang
 FWI_API fwi_status fwi_w2_misfit_static(const fwi_plan *plan, const void *obs_ctx,
                                         const float *d_syn, float *J, float *w2,
                                         float *adj_src, void *stream);
+
+/* Measured choice of the propagator family (a tuning utility; the paper has
+ * no counterpart).  For every family that can run the problem (resident,
+ * tiled, cluster; see fwi_problem.kernels) it creates a plan on the first
+ * trial_steps steps, runs one untimed and two timed gradient passes
+ * (fwi_forward with the record, then fwi_adjoint_grad with the synthetic
+ * data as adjoint source) in `scratch`, and reports the fastest.  The cost
+ * per step does not depend on nt, so a few dozen steps rank the families.
+ * Blocks the host until the stream's trial work is done.
+ *   prob, w2     the problem (its `kernels` field is ignored)
+ *   v            [B][nz][nx] device, representative models in (0, v_max]
+ *   trial_steps  steps per trial, in [2, prob->nt]
+ *   scratch      device buffer, 256-byte aligned, of at least
+ *                fwi_autotune_scratch_bytes; overwritten
+ *   family       written: FWI_KERNELS_RESIDENT, _TILED or _CLUSTER
+ *   ms           [3] host, written: best time of one trial pass for resident,
+ *                tiled, cluster (-1 where the family cannot run the problem);
+ *                NULL to skip
+ * Set kernels = *family in the problem before fwi_plan_create.  Errors:
+ * those of fwi_plan_create for the problem, FWI_ERR_INVALID_ARG,
+ * FWI_ERR_OOM (scratch too small), FWI_ERR_CUDA, and device statuses of
+ * the trials (fwi_check). */
+FWI_API fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2,
+                                        const float *v, int trial_steps, void *scratch,
+                                        size_t scratch_bytes, int *family, float *ms,
+                                        void *stream);
+
+/* Scratch bytes fwi_autotune_kernels needs for this problem and trial length
+ * (the largest over the families of workspace + snapshots + data + gradient
+ * of the trial plan).  Host only.  Errors: as fwi_plan_create, and
+ * FWI_ERR_INVALID_ARG for trial_steps outside [2, nt]. */
+FWI_API fwi_status fwi_autotune_scratch_bytes(const fwi_problem *prob, const fwi_w2_params *w2,
+                                              int trial_steps, size_t *bytes);
 
 /* Wait for `stream` and return the device status word of `workspace`
  * (FWI_OK, FWI_ERR_UNSTABLE_CFL, FWI_ERR_DEVICE_TIMEOUT), then clear it. */

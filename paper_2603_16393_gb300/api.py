@@ -97,6 +97,12 @@ _lib.fwi_tv_grad.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_
 _lib.fwi_image_metrics.restype = _S
 _lib.fwi_image_metrics.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                    _vp, _vp, _vp, _vp]
+_lib.fwi_autotune_scratch_bytes.restype = _S
+_lib.fwi_autotune_scratch_bytes.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+_lib.fwi_autotune_kernels.restype = _S
+_lib.fwi_autotune_kernels.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t,
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                      _vp]
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -230,7 +236,11 @@ class _Handle:
             self.raw = None
 
 
-def fwi_plan_create(prob: Problem, w2: W2Params) -> _Handle:
+def _c_problem(prob: Problem, w2: W2Params):
+    """C structs of a problem and its W2 parameters (the index arrays are
+    returned too: they must outlive the call)."""
+    if len(prob.src_iz) != len(prob.src_ix) or len(prob.rec_iz) != len(prob.rec_ix):
+        raise ValueError("source/receiver index lists differ in length")
     arrays = [(ctypes.c_int * len(a))(*[int(x) for x in a])
               for a in (prob.src_iz, prob.src_ix, prob.rec_iz, prob.rec_ix)]
     cp = _Problem(prob.nz, prob.nx, prob.dz, prob.dx, prob.nb, prob.top_bc, prob.nt, prob.dt,
@@ -238,12 +248,35 @@ def fwi_plan_create(prob: Problem, w2: W2Params) -> _Handle:
                   *[ctypes.cast(a, _ip) for a in arrays],
                   prob.f_peak, prob.t0, prob.v_ref, prob.refl_R, prob.v_max, prob.batch,
                   prob.checkpoint_every, prob.space_order, prob.kernels)
-    if len(prob.src_iz) != len(prob.src_ix) or len(prob.rec_iz) != len(prob.rec_ix):
-        raise ValueError("source/receiver index lists differ in length")
     cw = _W2(w2.k, w2.cshift_factor, w2.eps_density, w2.n_xi, int(w2.squared))
+    return cp, cw, arrays
+
+
+def fwi_plan_create(prob: Problem, w2: W2Params) -> _Handle:
+    cp, cw, _arrays = _c_problem(prob, w2)
     out = _vp()
     _check(_lib.fwi_plan_create(ctypes.byref(cp), ctypes.byref(cw), ctypes.byref(out)))
     return _Handle(out)
+
+
+def fwi_autotune_scratch_bytes(prob: Problem, w2: W2Params, trial_steps: int) -> int:
+    cp, cw, _arrays = _c_problem(prob, w2)
+    n = ctypes.c_size_t()
+    _check(_lib.fwi_autotune_scratch_bytes(ctypes.byref(cp), ctypes.byref(cw), int(trial_steps),
+                                           ctypes.byref(n)))
+    return n.value
+
+
+def fwi_autotune_kernels(prob: Problem, w2: W2Params, v, trial_steps: int, scratch, stream=None):
+    """(fastest family, [ms resident, ms tiled, ms cluster]) -- -1 where a
+    family cannot run the problem."""
+    cp, cw, _arrays = _c_problem(prob, w2)
+    fam = ctypes.c_int()
+    ms = (ctypes.c_float * 3)()
+    _check(_lib.fwi_autotune_kernels(ctypes.byref(cp), ctypes.byref(cw), _ptr(v), int(trial_steps),
+                                     _ptr(scratch), scratch.numel() * scratch.element_size(),
+                                     ctypes.byref(fam), ms, _stream(stream)))
+    return fam.value, [float(t) for t in ms]
 
 
 def fwi_plan_sizes(plan: _Handle):
@@ -445,3 +478,23 @@ def image_metrics(v_true, v_rec, data_range, stream=None):
     out = torch.empty((B, 3), dtype=torch.float32, device=v_true.device)
     fwi_image_metrics(B, nz, nx, data_range, v_true, v_rec, out, stream)
     return out
+
+
+def autotune(prob: Problem, w2: W2Params | None = None, v=None, trial_steps: int = 64,
+             stream=None):
+    """The problem with `kernels` set to the family fwi_autotune_kernels
+    measured fastest, and the measured milliseconds per trial pass
+    [resident, tiled, cluster] (-1: the family cannot run it).  `v`
+    ([B][nz][nx] on the device) defaults to the linear v(z) ramp from 1500 m/s
+    to min(4500, v_max) m/s; the scratch is a temporary torch buffer."""
+    import dataclasses
+    w2 = w2 or W2Params()
+    if v is None:
+        top = min(4500.0, float(prob.v_max))
+        z = torch.linspace(0.0, 1.0, prob.nz, device="cuda")
+        v = (min(1500.0, top) + (top - min(1500.0, top)) * z)[None, :, None].expand(
+            prob.batch, prob.nz, prob.nx).contiguous()
+    n = fwi_autotune_scratch_bytes(prob, w2, trial_steps)
+    scratch = torch.empty(max(n, 256), dtype=torch.uint8, device=v.device)
+    fam, ms = fwi_autotune_kernels(prob, w2, v, trial_steps, scratch, stream)
+    return dataclasses.replace(prob, kernels=fam), ms

@@ -1,0 +1,155 @@
+// autotune.cu -- measured choice of the propagator family for a problem.
+//
+// Built on the public entry points only: for every family that accepts the
+// problem (one CTA per grid, a cluster of CTAs, global-memory tiles) it
+// creates a plan on a shortened time axis, runs one untimed and two timed
+// gradient passes (forward with the record, adjoint) in caller-provided
+// scratch, and keeps the faster of the two timings.  The per-step cost of
+// every family is independent of nt, so a few dozen steps rank them.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "fwi_internal.cuh"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kFamilies[3] = {FWI_KERNELS_RESIDENT, FWI_KERNELS_TILED, FWI_KERNELS_CLUSTER};
+
+size_t up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+struct Trial {
+    fwi_plan *plan = nullptr;
+    size_t ws = 0, snap = 0, data = 0, grad = 0;
+    size_t total() const { return up(ws) + up(snap) + up(data) + up(grad); }
+};
+
+// Plan of family `fam` for the problem on trial_steps steps; false if the
+// family cannot run it (FWI_ERR_UNSUPPORTED), the other errors returned.
+fwi_status make_trial(const fwi_problem &p, const fwi_w2_params &w2, int steps, int fam,
+                      Trial *t, bool *ok)
+{
+    fwi_problem q = p;
+    q.nt = steps;
+    q.kernels = fam;
+    *ok = false;
+    fwi_status s = fwi_plan_create(&q, &w2, &t->plan);
+    if (s == FWI_ERR_UNSUPPORTED) return FWI_OK;
+    if (s != FWI_OK) return s;
+    s = fwi_plan_sizes(t->plan, &t->ws, nullptr, &t->snap);
+    if (s != FWI_OK) return s;
+    t->data = (size_t)p.batch * p.ns * p.nr * steps * sizeof(float);
+    t->grad = (size_t)p.batch * p.nz * p.nx * sizeof(float);
+    *ok = true;
+    return FWI_OK;
+}
+
+fwi_status check_args(const fwi_problem *prob, const fwi_w2_params *w2, int trial_steps)
+{
+    if (!prob || !w2) return fwi::record_error(FWI_ERR_INVALID_ARG, "problem or w2 params is NULL");
+    if (trial_steps < 2 || trial_steps > prob->nt)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "trial_steps must be in [2, nt = %d]",
+                                 prob->nt);
+    // the problem itself must be valid (any family)
+    fwi_problem q = *prob;
+    q.kernels = FWI_KERNELS_AUTO;
+    fwi_plan *pl = nullptr;
+    const fwi_status s = fwi_plan_create(&q, w2, &pl);
+    fwi_plan_destroy(pl);
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+fwi_status fwi_autotune_scratch_bytes(const fwi_problem *prob, const fwi_w2_params *w2,
+                                      int trial_steps, size_t *bytes)
+{
+    if (!bytes) return fwi::record_error(FWI_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = 0;
+    fwi_status s = check_args(prob, w2, trial_steps);
+    if (s != FWI_OK) return s;
+    for (int fam : kFamilies) {
+        Trial t;
+        bool ok = false;
+        s = make_trial(*prob, *w2, trial_steps, fam, &t, &ok);
+        if (ok && t.total() > *bytes) *bytes = t.total();
+        fwi_plan_destroy(t.plan);
+        if (s != FWI_OK) return s;
+    }
+    return FWI_OK;
+}
+
+fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2, const float *v,
+                                int trial_steps, void *scratch, size_t scratch_bytes,
+                                int *family, float *ms, void *stream)
+{
+    if (!v || !scratch || !family)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "v, scratch or family is NULL");
+    fwi_status s = check_args(prob, w2, trial_steps);
+    if (s != FWI_OK) return s;
+    if ((uintptr_t)scratch % kAlign != 0)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "scratch must be 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float best = -1.f;
+    *family = FWI_KERNELS_AUTO;
+    float times[3] = {-1.f, -1.f, -1.f};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fwi::record_error(FWI_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(ce));
+    }
+    for (int k = 0; k < 3 && s == FWI_OK; ++k) {
+        Trial t;
+        bool ok = false;
+        s = make_trial(*prob, *w2, trial_steps, kFamilies[k], &t, &ok);
+        if (s == FWI_OK && ok && t.total() > scratch_bytes)
+            s = fwi::record_error(FWI_ERR_OOM, "scratch of %zu bytes < %zu (fwi_autotune_scratch_bytes)",
+                                  scratch_bytes, t.total());
+        if (s == FWI_OK && ok) {
+            unsigned char *base = static_cast<unsigned char *>(scratch);
+            void *ws = base;
+            float *snap = reinterpret_cast<float *>(base + up(t.ws));
+            float *data = reinterpret_cast<float *>(base + up(t.ws) + up(t.snap));
+            float *grad = reinterpret_cast<float *>(base + up(t.ws) + up(t.snap) + up(t.data));
+            float tk = -1.f;
+            for (int rep = 0; rep < 3 && s == FWI_OK; ++rep) {
+                // rep 0 warms up (first launches, shared-memory carve-out)
+                if (rep > 0 && (ce = cudaEventRecord(e0, st)) != cudaSuccess) break;
+                s = fwi_forward(t.plan, v, data, snap, ws, stream);
+                if (s == FWI_OK) s = fwi_adjoint_grad(t.plan, v, data, snap, grad, ws, stream);
+                if (s != FWI_OK) break;
+                if (rep > 0) {
+                    if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) break;
+                    if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                    float m = 0.f;
+                    if ((ce = cudaEventElapsedTime(&m, e0, e1)) != cudaSuccess) break;
+                    if (tk < 0.f || m < tk) tk = m;
+                }
+            }
+            if (s == FWI_OK && ce != cudaSuccess)
+                s = fwi::record_error(FWI_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(ce));
+            if (s == FWI_OK) s = fwi_check(t.plan, ws, stream);
+            if (s == FWI_OK) {
+                times[k] = tk;
+                if (best < 0.f || tk < best) {
+                    best = tk;
+                    *family = kFamilies[k];
+                }
+            }
+        }
+        fwi_plan_destroy(t.plan);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ms) std::memcpy(ms, times, sizeof(times));
+    if (s == FWI_OK) fwi::record_error(FWI_OK, "%s", "");   // families that declined left a message
+    return s;
+}
+
+}  // extern "C"

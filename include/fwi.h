@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 10400  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 10500  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -103,7 +103,19 @@ typedef struct fwi_problem {
                             the others force one and fail with FWI_ERR_UNSUPPORTED
                             where it cannot run the plan.  Every family computes the
                             same recurrences (Sec. 2.1, Eq. 2) to float rounding.   */
+    int absorber;        /* FWI_ABSORBER_SPONGE (0): the damping layer of Eq. (1)
+                            with A, B (the default); FWI_ABSORBER_CPML (1): a
+                            convolutional PML in the same nb cells (the paper's
+                            solver absorbs with a PML, Sec. 6.1): the layer stretches
+                            d/dx, d/dz by s = 1 + sigma/(i omega), sigma = d0 (d/nb)^2,
+                            d0 = 3 v_ref ln(1/refl_R) / (2 nb h), each 1/s a memory
+                            variable advanced per step.  CPML plans: 4th order,
+                            top_bc = 0, checkpoint_every = 0, distinct receiver cells;
+                            they run on FWI_KERNELS_CPML.                           */
 } fwi_problem;
+
+/* Absorbing layers (fwi_problem.absorber). */
+enum { FWI_ABSORBER_SPONGE = 0, FWI_ABSORBER_CPML = 1 };
 
 /* Propagator families (fwi_problem.kernels). */
 enum {
@@ -112,10 +124,12 @@ enum {
                                  shared memory; 4th order; grids up to ~150 x 340 cells  */
     FWI_KERNELS_TILED = 2,    /* global-memory fields, TMA-staged halo tiles, one launch
                                  per time step; any grid, 4th or 8th order               */
-    FWI_KERNELS_CLUSTER = 3   /* a cluster of 8 CTAs holds the grid in their shared
+    FWI_KERNELS_CLUSTER = 3,  /* a cluster of 2-8 CTAs holds the grid in their shared
                                  memories, halo rows through distributed shared memory;
                                  4th order, whole record (checkpoint_every = 0), padded
-                                 width <= 337, rows split 8 ways                        */
+                                 width <= 337                                           */
+    FWI_KERNELS_CPML = 4      /* global-memory kernels of the CPML absorber (the only
+                                 family of absorber = FWI_ABSORBER_CPML plans)         */
 };
 
 /* Misfit hyperparameters (Sec. 5.1, 6.2, 6.3): k = 100, c' factor 1.1,
@@ -177,8 +191,9 @@ FWI_API fwi_status fwi_plan_sizes(const fwi_plan *plan, size_t *workspace_bytes,
 /* Padded grid of the plan: NZ = nz + nb, NX = nx + 2 nb. */
 FWI_API fwi_status fwi_plan_padded(const fwi_plan *plan, int *NZ, int *NX);
 
-/* Propagator family the plan runs: *family = FWI_KERNELS_RESIDENT, _TILED or
- * _CLUSTER (the automatic choice resolved, or the one forced).  Host only. */
+/* Propagator family the plan runs: *family = FWI_KERNELS_RESIDENT, _TILED,
+ * _CLUSTER or _CPML (the automatic choice resolved, or the one forced).
+ * Host only. */
 FWI_API fwi_status fwi_plan_kernels(const fwi_plan *plan, int *family);
 
 /* Forward solve of Eq. (1) for every model and shot (Sec. 2.1, 6.1).
@@ -312,21 +327,23 @@ FWI_API fwi_status fwi_w2_misfit_static(const fwi_plan *plan, const void *obs_ct
 
 /* Measured choice of the propagator family (a tuning utility; the paper has
  * no counterpart).  For every family that can run the problem (resident,
- * tiled, cluster; see fwi_problem.kernels) it creates a plan on the first
- * trial_steps steps, runs one untimed and two timed gradient passes
- * (fwi_forward with the record, then fwi_adjoint_grad with the synthetic
- * data as adjoint source) in `scratch`, and reports the fastest.  The cost
- * per step does not depend on nt, so a few dozen steps rank the families.
- * Blocks the host until the stream's trial work is done.
+ * tiled, cluster, CPML; see fwi_problem.kernels) it creates plans on T =
+ * trial_steps and min(2T, nt) steps, times a gradient pass on each (the
+ * faster of two after an untimed one: fwi_forward with the record, then
+ * fwi_adjoint_grad with the synthetic data as adjoint source) in `scratch`,
+ * and predicts the pass at the problem's nt as fixed cost + nt x cost per
+ * step from the two timings (the families differ in both).  Reports the
+ * family with the smallest prediction.  Blocks the host until the trial
+ * work on the stream is done.
  *   prob, w2     the problem (its `kernels` field is ignored)
  *   v            [B][nz][nx] device, representative models in (0, v_max]
  *   trial_steps  steps per trial, in [2, prob->nt]
  *   scratch      device buffer, 256-byte aligned, of at least
  *                fwi_autotune_scratch_bytes; overwritten
- *   family       written: FWI_KERNELS_RESIDENT, _TILED or _CLUSTER
- *   ms           [3] host, written: best time of one trial pass for resident,
- *                tiled, cluster (-1 where the family cannot run the problem);
- *                NULL to skip
+ *   family       written: FWI_KERNELS_RESIDENT, _TILED, _CLUSTER or _CPML
+ *   ms           [4] host, written: predicted milliseconds of one pass at nt
+ *                steps for resident, tiled, cluster, CPML (-1 where the family
+ *                cannot run the problem); NULL to skip
  * Set kernels = *family in the problem before fwi_plan_create.  Errors:
  * those of fwi_plan_create for the problem, FWI_ERR_INVALID_ARG,
  * FWI_ERR_OOM (scratch too small), FWI_ERR_CUDA, and device statuses of
@@ -338,7 +355,7 @@ FWI_API fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_pa
 
 /* Scratch bytes fwi_autotune_kernels needs for this problem and trial length
  * (the largest over the families of workspace + snapshots + data + gradient
- * of the trial plan).  Host only.  Errors: as fwi_plan_create, and
+ * of the min(2 trial_steps, nt)-step trial plan).  Host only.  Errors: as fwi_plan_create, and
  * FWI_ERR_INVALID_ARG for trial_steps outside [2, nt]. */
 FWI_API fwi_status fwi_autotune_scratch_bytes(const fwi_problem *prob, const fwi_w2_params *w2,
                                               int trial_steps, size_t *bytes);

@@ -33,7 +33,8 @@ FWI_ERR_UNSUPPORTED = 3
 FWI_ERR_CUDA = 4
 FWI_ERR_DEVICE_TIMEOUT = 5
 FWI_ERR_OOM = 6
-KERNELS_AUTO, KERNELS_RESIDENT, KERNELS_TILED, KERNELS_CLUSTER = 0, 1, 2, 3
+KERNELS_AUTO, KERNELS_RESIDENT, KERNELS_TILED, KERNELS_CLUSTER, KERNELS_CPML = 0, 1, 2, 3, 4
+ABSORBER_SPONGE, ABSORBER_CPML = 0, 1
 FWI_MAX_SHOTS = 256
 FWI_MAX_RECEIVERS = 1024
 
@@ -50,7 +51,7 @@ class _Problem(ctypes.Structure):
                 ("v_ref", ctypes.c_double), ("refl_R", ctypes.c_double),
                 ("v_max", ctypes.c_double), ("batch", ctypes.c_int),
                 ("checkpoint_every", ctypes.c_int), ("space_order", ctypes.c_int),
-                ("kernels", ctypes.c_int)]
+                ("kernels", ctypes.c_int), ("absorber", ctypes.c_int)]
 
 
 class _W2(ctypes.Structure):
@@ -155,7 +156,8 @@ class Problem:
     top_bc: int = 0
     checkpoint_every: int = 0     # 0: keep the whole record; K: checkpoint every K steps
     space_order: int = 4          # 4 or 8 (8: the paper solver's stencil, tiled kernels)
-    kernels: int = 0              # propagator family: KERNELS_AUTO / _RESIDENT / _TILED / _CLUSTER
+    kernels: int = 0              # propagator family: KERNELS_AUTO / _RESIDENT / _TILED / _CLUSTER / _CPML
+    absorber: int = 0             # ABSORBER_SPONGE (damping layer) or ABSORBER_CPML
 
     @property
     def ns(self):
@@ -247,7 +249,7 @@ def _c_problem(prob: Problem, w2: W2Params):
                   len(prob.src_ix), len(prob.rec_ix),
                   *[ctypes.cast(a, _ip) for a in arrays],
                   prob.f_peak, prob.t0, prob.v_ref, prob.refl_R, prob.v_max, prob.batch,
-                  prob.checkpoint_every, prob.space_order, prob.kernels)
+                  prob.checkpoint_every, prob.space_order, prob.kernels, prob.absorber)
     cw = _W2(w2.k, w2.cshift_factor, w2.eps_density, w2.n_xi, int(w2.squared))
     return cp, cw, arrays
 
@@ -268,11 +270,11 @@ def fwi_autotune_scratch_bytes(prob: Problem, w2: W2Params, trial_steps: int) ->
 
 
 def fwi_autotune_kernels(prob: Problem, w2: W2Params, v, trial_steps: int, scratch, stream=None):
-    """(fastest family, [ms resident, ms tiled, ms cluster]) -- -1 where a
-    family cannot run the problem."""
+    """(fastest family, predicted ms of a pass at nt for [resident, tiled,
+    cluster, CPML]) -- -1 where a family cannot run the problem."""
     cp, cw, _arrays = _c_problem(prob, w2)
     fam = ctypes.c_int()
-    ms = (ctypes.c_float * 3)()
+    ms = (ctypes.c_float * 4)()
     _check(_lib.fwi_autotune_kernels(ctypes.byref(cp), ctypes.byref(cw), _ptr(v), int(trial_steps),
                                      _ptr(scratch), scratch.numel() * scratch.element_size(),
                                      ctypes.byref(fam), ms, _stream(stream)))
@@ -483,8 +485,8 @@ def image_metrics(v_true, v_rec, data_range, stream=None):
 def autotune(prob: Problem, w2: W2Params | None = None, v=None, trial_steps: int = 64,
              stream=None):
     """The problem with `kernels` set to the family fwi_autotune_kernels
-    measured fastest, and the measured milliseconds per trial pass
-    [resident, tiled, cluster] (-1: the family cannot run it).  `v`
+    measured fastest, and the predicted milliseconds of one pass at nt steps
+    [resident, tiled, cluster, CPML] (-1: the family cannot run it).  `v`
     ([B][nz][nx] on the device) defaults to the linear v(z) ramp from 1500 m/s
     to min(4500, v_max) m/s; the scratch is a temporary torch buffer."""
     import dataclasses

@@ -90,8 +90,10 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (!(w2->eps_density >= 0.0) || !std::isfinite(w2->eps_density))
         return fail(FWI_ERR_INVALID_ARG, "eps_density must be >= 0");
     if (w2->squared != 0 && w2->squared != 1) return fail(FWI_ERR_INVALID_ARG, "squared must be 0 or 1");
-    if (p.kernels < FWI_KERNELS_AUTO || p.kernels > FWI_KERNELS_CLUSTER)
-        return fail(FWI_ERR_INVALID_ARG, "kernels must be 0 (auto), 1, 2 or 3");
+    if (p.kernels < FWI_KERNELS_AUTO || p.kernels > FWI_KERNELS_CPML)
+        return fail(FWI_ERR_INVALID_ARG, "kernels must be 0 (auto), 1, 2, 3 or 4");
+    if (p.absorber != FWI_ABSORBER_SPONGE && p.absorber != FWI_ABSORBER_CPML)
+        return fail(FWI_ERR_INVALID_ARG, "absorber must be 0 (sponge) or 1 (CPML)");
     if (p.space_order != 0 && p.space_order != 4 && p.space_order != 8)
         return fail(FWI_ERR_INVALID_ARG, "space_order must be 0, 4 or 8");
     const int order = p.space_order == 8 ? 8 : 4;
@@ -142,8 +144,31 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         return fail(FWI_ERR_UNSUPPORTED, "padded grid %dx%d too large", pl->NZ, pl->NX);
     }
     const int fam = p.kernels;
+    // the CPML absorber runs on its own kernels
+    pl->cpml = p.absorber == FWI_ABSORBER_CPML;
+    pl->ws_c = 0;
+    if (pl->cpml || fam == FWI_KERNELS_CPML) {
+        const char *need = nullptr;
+        if (!pl->cpml) need = "absorber = FWI_ABSORBER_CPML";
+        else if (order != 4) need = "space_order 4";
+        else if (p.top_bc != 0) need = "top_bc = 0";
+        else if (p.checkpoint_every != 0) need = "checkpoint_every = 0";
+        else if (fam != FWI_KERNELS_AUTO && fam != FWI_KERNELS_CPML)
+            need = "kernels = FWI_KERNELS_AUTO or FWI_KERNELS_CPML";
+        else if ((long long)p.batch * p.ns > 65535) need = "batch x ns <= 65535";
+        for (int i = 0; !need && i < p.nr; ++i)
+            for (int k = 0; k < i; ++k)
+                if (pl->rec_px[i] == pl->rec_px[k] && pl->rec_pz[i] == pl->rec_pz[k]) {
+                    need = "distinct receiver cells";
+                    break;
+                }
+        if (need) {
+            delete pl;
+            return fail(FWI_ERR_UNSUPPORTED, "CPML plans (FWI_KERNELS_CPML) need %s", need);
+        }
+    }
     // the resident kernels implement the 4th-order stencil only
-    pl->fast = (fam == FWI_KERNELS_AUTO || fam == FWI_KERNELS_RESIDENT) && order == 4 &&
+    pl->fast = !pl->cpml && (fam == FWI_KERNELS_AUTO || fam == FWI_KERNELS_RESIDENT) && order == 4 &&
                fwi::fast_bucket(pl->NZ, pl->NX, &pl->fast_P, &pl->fast_PR, &pl->fast_NZM);
     if (pl->fast) {
         const int nstrip = (pl->NZ + fwi::kFastRows - 1) / fwi::kFastRows;
@@ -184,7 +209,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
             sh.smem = fwi::fast_smem(pl->fast_P, pl->fast_NZM, false, chunk, p.nr);
         }
     }
-    if (!pl->fast) {
+    if (pl->cpml) pl->nzs = pl->NZ;
+    if (!pl->fast && !pl->cpml) {
         pl->nzs = pl->NZ;
         if (fam == FWI_KERNELS_TILED || fam == FWI_KERNELS_CLUSTER || order == 8 ||
             !fwi::choose_resident_shape(pl->NZ, pl->NX, p.nr, false, &pl->shape) ||
@@ -292,7 +318,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     }
     // the resident adjoint injects each receiver from the thread that owns
     // its cell: receivers must sit in distinct column strips
-    for (int i = 0; i < (pl->tiled ? 0 : p.nr); ++i)
+    for (int i = 0; i < ((pl->tiled || pl->cpml) ? 0 : p.nr); ++i)
         for (int k = 0; k < i; ++k)
             if (pl->rec_px[i] == pl->rec_px[k] &&
                 pl->rec_pz[i] / pl->shape_adj.rows == pl->rec_pz[k] / pl->shape_adj.rows) {
@@ -349,6 +375,10 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         pl->ws_t_rec = o; o += align_up((size_t)p.nr * 4);
         pl->ws_t_src = o; o += align_up((size_t)p.ns * 4);
     }
+    if (pl->cpml) {
+        pl->ws_c = o;   // fields, memory variables, kappa and the layer profiles
+        o += align_up(fwi::cpml_workspace(*pl));
+    }
     pl->ws_bytes = o;
     o = 0;
     pl->ctx_M = o;      o += align_up(B * 4);
@@ -391,7 +421,10 @@ fwi_status fwi_plan_kernels(const fwi_plan *plan, int *family)
 {
     if (!plan || !family) return fail(FWI_ERR_INVALID_ARG, "plan or family is NULL");
     const Plan *pl = as_plan(plan);
-    *family = pl->cluster ? FWI_KERNELS_CLUSTER : pl->tiled ? FWI_KERNELS_TILED : FWI_KERNELS_RESIDENT;
+    *family = pl->cpml      ? FWI_KERNELS_CPML
+              : pl->cluster ? FWI_KERNELS_CLUSTER
+              : pl->tiled   ? FWI_KERNELS_TILED
+                            : FWI_KERNELS_RESIDENT;
     return FWI_OK;
 }
 

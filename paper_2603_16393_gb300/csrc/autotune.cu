@@ -1,11 +1,14 @@
 // autotune.cu -- measured choice of the propagator family for a problem.
 //
 // Built on the public entry points only: for every family that accepts the
-// problem (one CTA per grid, a cluster of CTAs, global-memory tiles) it
-// creates a plan on a shortened time axis, runs one untimed and two timed
-// gradient passes (forward with the record, adjoint) in caller-provided
-// scratch, and keeps the faster of the two timings.  The per-step cost of
-// every family is independent of nt, so a few dozen steps rank them.
+// problem (one CTA per grid, a cluster of CTAs, global-memory tiles, and
+// for the CPML absorber its own kernels) it
+// creates plans on two shortened time axes (T and 2T steps), times one
+// gradient pass (forward with the record, adjoint) on each after an untimed
+// one, in caller-provided scratch, and predicts the pass at the problem's nt
+// from the fixed cost and the cost per step the two timings give.  The
+// families differ in both: the cluster kernels set up per-CTA tables in
+// shared memory once per pass, the tiled kernels launch once per step.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -16,7 +19,8 @@
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kFamilies[3] = {FWI_KERNELS_RESIDENT, FWI_KERNELS_TILED, FWI_KERNELS_CLUSTER};
+constexpr int kFamilies[4] = {FWI_KERNELS_RESIDENT, FWI_KERNELS_TILED, FWI_KERNELS_CLUSTER,
+                               FWI_KERNELS_CPML};
 
 size_t up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
@@ -61,6 +65,12 @@ fwi_status check_args(const fwi_problem *prob, const fwi_w2_params *w2, int tria
     return s;
 }
 
+// The longer of the two trial lengths.
+int long_trial(const fwi_problem &p, int trial_steps)
+{
+    return 2 * trial_steps < p.nt ? 2 * trial_steps : p.nt;
+}
+
 }  // namespace
 
 extern "C" {
@@ -75,7 +85,7 @@ fwi_status fwi_autotune_scratch_bytes(const fwi_problem *prob, const fwi_w2_para
     for (int fam : kFamilies) {
         Trial t;
         bool ok = false;
-        s = make_trial(*prob, *w2, trial_steps, fam, &t, &ok);
+        s = make_trial(*prob, *w2, long_trial(*prob, trial_steps), fam, &t, &ok);
         if (ok && t.total() > *bytes) *bytes = t.total();
         fwi_plan_destroy(t.plan);
         if (s != FWI_OK) return s;
@@ -96,7 +106,7 @@ fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float best = -1.f;
     *family = FWI_KERNELS_AUTO;
-    float times[3] = {-1.f, -1.f, -1.f};
+    float times[4] = {-1.f, -1.f, -1.f, -1.f};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
@@ -104,46 +114,61 @@ fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2
         if (e0) cudaEventDestroy(e0);
         return fwi::record_error(FWI_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(ce));
     }
-    for (int k = 0; k < 3 && s == FWI_OK; ++k) {
-        Trial t;
-        bool ok = false;
-        s = make_trial(*prob, *w2, trial_steps, kFamilies[k], &t, &ok);
-        if (s == FWI_OK && ok && t.total() > scratch_bytes)
-            s = fwi::record_error(FWI_ERR_OOM, "scratch of %zu bytes < %zu (fwi_autotune_scratch_bytes)",
-                                  scratch_bytes, t.total());
-        if (s == FWI_OK && ok) {
-            unsigned char *base = static_cast<unsigned char *>(scratch);
-            void *ws = base;
-            float *snap = reinterpret_cast<float *>(base + up(t.ws));
-            float *data = reinterpret_cast<float *>(base + up(t.ws) + up(t.snap));
-            float *grad = reinterpret_cast<float *>(base + up(t.ws) + up(t.snap) + up(t.data));
-            float tk = -1.f;
-            for (int rep = 0; rep < 3 && s == FWI_OK; ++rep) {
-                // rep 0 warms up (first launches, shared-memory carve-out)
-                if (rep > 0 && (ce = cudaEventRecord(e0, st)) != cudaSuccess) break;
-                s = fwi_forward(t.plan, v, data, snap, ws, stream);
-                if (s == FWI_OK) s = fwi_adjoint_grad(t.plan, v, data, snap, grad, ws, stream);
-                if (s != FWI_OK) break;
-                if (rep > 0) {
-                    if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) break;
-                    if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
-                    float m = 0.f;
-                    if ((ce = cudaEventElapsedTime(&m, e0, e1)) != cudaSuccess) break;
-                    if (tk < 0.f || m < tk) tk = m;
+    const int n1 = trial_steps, n2 = long_trial(*prob, trial_steps);
+    for (int k = 0; k < 4 && s == FWI_OK; ++k) {
+        float tl[2] = {-1.f, -1.f};   // best time of one pass at n1 and n2 steps
+        bool ran = false;
+        for (int L = 0; L < (n2 > n1 ? 2 : 1) && s == FWI_OK; ++L) {
+            Trial t;
+            bool ok = false;
+            s = make_trial(*prob, *w2, L ? n2 : n1, kFamilies[k], &t, &ok);
+            if (s == FWI_OK && ok && t.total() > scratch_bytes)
+                s = fwi::record_error(FWI_ERR_OOM,
+                                      "scratch of %zu bytes < %zu (fwi_autotune_scratch_bytes)",
+                                      scratch_bytes, t.total());
+            if (s == FWI_OK && ok) {
+                unsigned char *base = static_cast<unsigned char *>(scratch);
+                void *ws = base;
+                float *snap = reinterpret_cast<float *>(base + up(t.ws));
+                float *data = reinterpret_cast<float *>(base + up(t.ws) + up(t.snap));
+                float *grad =
+                    reinterpret_cast<float *>(base + up(t.ws) + up(t.snap) + up(t.data));
+                for (int rep = 0; rep < 3 && s == FWI_OK; ++rep) {
+                    // rep 0 warms up (first launches, shared-memory carve-out)
+                    if (rep > 0 && (ce = cudaEventRecord(e0, st)) != cudaSuccess) break;
+                    s = fwi_forward(t.plan, v, data, snap, ws, stream);
+                    if (s == FWI_OK) s = fwi_adjoint_grad(t.plan, v, data, snap, grad, ws, stream);
+                    if (s != FWI_OK) break;
+                    if (rep > 0) {
+                        if ((ce = cudaEventRecord(e1, st)) != cudaSuccess) break;
+                        if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                        float m = 0.f;
+                        if ((ce = cudaEventElapsedTime(&m, e0, e1)) != cudaSuccess) break;
+                        if (tl[L] < 0.f || m < tl[L]) tl[L] = m;
+                    }
                 }
+                if (s == FWI_OK && ce != cudaSuccess)
+                    s = fwi::record_error(FWI_ERR_CUDA, "autotune timing: %s",
+                                          cudaGetErrorString(ce));
+                if (s == FWI_OK) s = fwi_check(t.plan, ws, stream);
+                ran = s == FWI_OK;
             }
-            if (s == FWI_OK && ce != cudaSuccess)
-                s = fwi::record_error(FWI_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(ce));
-            if (s == FWI_OK) s = fwi_check(t.plan, ws, stream);
-            if (s == FWI_OK) {
-                times[k] = tk;
-                if (best < 0.f || tk < best) {
-                    best = tk;
-                    *family = kFamilies[k];
-                }
+            fwi_plan_destroy(t.plan);
+        }
+        if (s == FWI_OK && ran) {
+            // predicted pass at nt steps: fixed + nt x per-step cost
+            float pred = tl[0];
+            if (n2 > n1) {
+                float per = (tl[1] - tl[0]) / (float)(n2 - n1);
+                if (per < 0.f) per = 0.f;
+                pred = tl[0] + per * (float)(prob->nt - n1);
+            }
+            times[k] = pred;
+            if (best < 0.f || pred < best) {
+                best = pred;
+                *family = kFamilies[k];
             }
         }
-        fwi_plan_destroy(t.plan);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

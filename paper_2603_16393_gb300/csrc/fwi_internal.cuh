@@ -72,6 +72,8 @@ struct Plan {
     bool fast;                 // compile-time pitch kernels (else the generic ones)
     bool tiled;                // global-memory tiled kernels (grids beyond shared memory)
     bool cluster;              // cluster kernels for the store-all passes of a tiled plan
+    bool cpml;                 // convolutional PML absorber (its own global-memory kernels)
+    size_t ws_c;               // CPML: workspace offset of its fields and tables
     ClusterArgs clu;           // their shape
     int clu_threads, clu_chunk_fwd, clu_chunk_adj;
     int NXp;                   // tiled: row pitch of the fields (NX rounded up to 4)
@@ -191,6 +193,11 @@ cudaError_t launch_cluster(const Plan &pl, bool adj, const PropArgs &a, unsigned
                            cudaStream_t st);
 cudaError_t launch_tile_fold(const Plan &pl, const PropArgs &a, unsigned char *ws,
                              cudaStream_t st);
+// CPML propagators (absorber = FWI_ABSORBER_CPML): workspace bytes of their
+// fields and tables, and the whole forward or adjoint time loop
+size_t cpml_workspace(const Plan &pl);
+cudaError_t launch_cpml(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
+                        cudaStream_t st);
 // Tiled propagators: one launch per step over [a.j_begin, a.j_end)
 cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
                          cudaStream_t st);

@@ -449,6 +449,7 @@ cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *
     a.snap = snap;
     a.status = static_cast<int *>(workspace);
     apply_window(a, w);
+    if (pl.cpml) return launch_cpml(pl, false, a, static_cast<unsigned char *>(workspace), st);
     if (pl.cluster)
         return launch_cluster(pl, false, a, static_cast<unsigned char *>(workspace), st);
     if (pl.tiled) return launch_tiled(pl, false, a, static_cast<unsigned char *>(workspace), st);
@@ -473,7 +474,9 @@ cudaError_t launch_adjoint(const Plan &pl, const float *v, const float *adj, con
     a.status = static_cast<int *>(workspace);
     apply_window(a, w);
     cudaError_t e;
-    if (pl.cluster) {
+    if (pl.cpml) {
+        e = launch_cpml(pl, true, a, static_cast<unsigned char *>(workspace), st);
+    } else if (pl.cluster) {
         e = launch_cluster(pl, true, a, static_cast<unsigned char *>(workspace), st);
         if (e == cudaSuccess)
             e = launch_tile_fold(pl, a, static_cast<unsigned char *>(workspace), st);

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(api):
     lib = ctypes.CDLL(LIB)
     for n in declared_functions():
         assert hasattr(lib, n), n
-    assert api.fwi_version() == 10400
+    assert api.fwi_version() == 10500
 
 
 def _prob(api, **kw):
@@ -209,10 +209,32 @@ def test_kernel_family_selection(api):
         (dict(kernels=K.KERNELS_CLUSTER, space_order=8), 3),
         (dict(kernels=K.KERNELS_RESIDENT, space_order=8), 3),
         (dict(nx=300, kernels=K.KERNELS_CLUSTER), 3),        # 380 padded columns
-        (dict(kernels=4), 1),
+        (dict(kernels=5), 1),
         (dict(kernels=-1), 1),
     ]
     for kw, code in bad:
         with pytest.raises(K.FwiError) as e:
             K.fwi_plan_create(_prob(api, **kw), K.W2Params())
         assert e.value.code == code, kw
+
+
+def test_cpml_plans():
+    K = api = __import__("paper_2603_16393_gb300.api", fromlist=["api"])
+    h = K.fwi_plan_create(_prob(api, absorber=K.ABSORBER_CPML), K.W2Params())
+    assert K.fwi_plan_kernels(h) == K.KERNELS_CPML
+    ws, _, snap = K.fwi_plan_sizes(h)
+    B, ns, nt, NZ, NX = 3, 5, 1000, 110, 150
+    assert snap == B * ns * nt * NZ * NX * 4          # record B^n, compact rows
+    assert ws >= 12 * B * ns * NZ * NX * 4 + B * NZ * NX * 4
+    for kw in (dict(top_bc=1), dict(checkpoint_every=16), dict(space_order=8),
+               dict(kernels=K.KERNELS_RESIDENT), dict(kernels=K.KERNELS_CLUSTER),
+               dict(rec_iz=(0, 0), rec_ix=(3, 3))):
+        with pytest.raises(K.FwiError) as e:
+            K.fwi_plan_create(_prob(api, absorber=K.ABSORBER_CPML, **kw), K.W2Params())
+        assert e.value.code == 3, kw
+    with pytest.raises(K.FwiError) as e:               # the CPML family needs the CPML absorber
+        K.fwi_plan_create(_prob(api, kernels=K.KERNELS_CPML), K.W2Params())
+    assert e.value.code == 3
+    with pytest.raises(K.FwiError) as e:
+        K.fwi_plan_create(_prob(api, absorber=2), K.W2Params())
+    assert e.value.code == 1

@@ -39,15 +39,22 @@ def _trial_bytes(prob, steps, fam):
     (dict(nz=100, nx=140, nb=20, src_ix=(0, 70, 139), src_iz=(0,) * 3,
           rec_iz=(0,) * 140, rec_ix=tuple(range(140))), 2),   # beyond one CTA: tiled, cluster
     (dict(space_order=8), 1),                      # 8th order: tiled only
+    (dict(absorber=1), 1),                         # CPML absorber: its own kernels only
 ])
 def test_scratch_covers_every_family(kw, families):
     prob = _prob(**kw)
-    steps = 48
-    need = [_trial_bytes(prob, steps, f) for f in (api.KERNELS_RESIDENT, api.KERNELS_TILED,
-                                                   api.KERNELS_CLUSTER)]
+    steps = 48              # the trials run 48 and 96 steps: the scratch fits the longer
+    need = [_trial_bytes(prob, 2 * steps, f) for f in (api.KERNELS_RESIDENT, api.KERNELS_TILED,
+                                                       api.KERNELS_CLUSTER, api.KERNELS_CPML)]
     ok = [n for n in need if n is not None]
     assert len(ok) == families
     assert api.fwi_autotune_scratch_bytes(prob, api.W2Params(), steps) == max(ok)
+    # a trial of more than half the steps is capped at nt
+    short = dataclasses.replace(prob, nt=60)
+    cap = [_trial_bytes(short, 60, f) for f in (api.KERNELS_RESIDENT, api.KERNELS_TILED,
+                                                api.KERNELS_CLUSTER, api.KERNELS_CPML)]
+    assert api.fwi_autotune_scratch_bytes(short, api.W2Params(), 40) == max(
+        n for n in cap if n is not None)
 
 
 def test_autotune_rejects_bad_arguments():

@@ -39,6 +39,7 @@ def test_autotune_times_every_family_and_picks_the_fastest(api, nz, nx, nb, n_fa
         fam, ms = api.fwi_autotune_kernels(gp, api.W2Params(), v, 40, scratch)
         ran = [t for t in ms if t >= 0]
         assert len(ran) == n_fam and all(t > 0 for t in ran)
+        assert len(ms) == 4 and ms[3] == -1      # CPML runs CPML-absorber problems only
         assert ms[[api.KERNELS_RESIDENT, api.KERNELS_TILED, api.KERNELS_CLUSTER].index(fam)] \
             == min(ran)
     # the scratch must cover the trial plans

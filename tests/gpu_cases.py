@@ -12,6 +12,11 @@ TOL_DATA = 1e-5
 TOL_J = 1e-5
 TOL_ADJ = 1e-4
 TOL_GRAD = 1e-4
+# End to end through W2 where the quantile map is ill-conditioned (long or
+# reverberant traces): a float32-level data difference can move an adjoint
+# source by ~1e-3 (interpolated quantiles change bracket), so gradients are
+# held to this bound there while every stage keeps its own bar above.
+TOL_GRAD_W2 = 5e-3
 
 
 def rel_l2(a, b):

@@ -225,10 +225,11 @@ def run_ours(args, rank, world, local_rank):
     vt, v0, geo = workload_inputs(wl, B, seed0=rank_seed0(rank, B))
     prob = api.Problem(nz=NZ_PHYS, nx=NX_PHYS, nb=NB, nt=NT, dz=DX, dx=DX, dt=DT,
                        src_iz=geo.src_iz, src_ix=geo.src_ix, rec_iz=geo.rec_iz,
-                       rec_ix=geo.rec_ix, v_max=4500.0, batch=B, checkpoint_every=wl["ckpt"])
+                       rec_ix=geo.rec_ix, v_max=4500.0, batch=B, checkpoint_every=wl["ckpt"],
+                       absorber=api.ABSORBER_CPML if args.absorber == "cpml" else api.ABSORBER_SPONGE)
     plan = api.Plan(prob, api.W2Params(), device=dev)
     path = {api.KERNELS_RESIDENT: "resident", api.KERNELS_TILED: "tiled",
-            api.KERNELS_CLUSTER: "cluster"}[plan.kernels]
+            api.KERNELS_CLUSTER: "cluster", api.KERNELS_CPML: "cpml"}[plan.kernels]
     # Table 1 (CurveVel-A) rho0, gamma; Sec. 6.3 c, tau, eps; the diffusion's
     # normalised space (v - 3000)/1500 has a unit of 1500 m/s
     gparams = api.GuideParams(rho0=1.15, gamma=0.55, unit=1500.0)
@@ -273,6 +274,10 @@ def run_ours(args, rank, world, local_rank):
     # final gather or fold
     if path == "resident":
         kernels_per_step = 4 + 1 + 2 + 2 + 1
+    elif path == "cpml":
+        # set-up 2 + 2 a step (forward); set-up 2 + init + 3 a step (2 at the
+        # last) + fold (adjoint), + shot sum
+        kernels_per_step = 4 + (2 + 2 * NT) + 2 + (2 + 1 + 3 * NT - 2 + 1 + 1) + 1
     elif path == "cluster":
         kernels_per_step = 4 + 1 + 2 + 3 + 1
     else:
@@ -306,22 +311,44 @@ def run_ours(args, rank, world, local_rank):
     fwd_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(ev["fwd0"], ev["fwd1"]))
     adj_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(ev["adj0"], ev["adj1"]))
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers: every
+    # step's inputs go host -> device on a copy stream into one of two buffer
+    # sets while the previous step computes (a user's pipeline); the step
+    # waits for its copy, and its results come back on the compute stream
     v_h = torch.tensor(v0, dtype=torch.float32).pin_memory()
     dobs_h = d_obs.cpu().pin_memory()
     out_grad_h = torch.empty(shape, dtype=torch.float32).pin_memory()
     out_J_h = torch.empty(B, dtype=torch.float32).pin_memory()
     out_v_h = torch.empty(shape, dtype=torch.float32).pin_memory()
-    v_e = torch.empty_like(v_d)
-    dobs_e = torch.empty_like(d_obs)
+    v_e = [torch.empty_like(v_d) for _ in range(2)]
+    dobs_e = [torch.empty_like(d_obs) for _ in range(2)]
+    copy_st = torch.cuda.Stream(device=dev)
+    loaded = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+    used = [False, False]
     barrier()
     e_s = torch.cuda.Event(enable_timing=True)
     e_e = torch.cuda.Event(enable_timing=True)
     e_s.record(stream)
-    for _ in range(args.steps):
-        v_e.copy_(v_h, non_blocking=True)
-        dobs_e.copy_(dobs_h, non_blocking=True)
-        step(v_e, dobs_e, False)
+    copy_st.wait_event(e_s)          # every copy falls inside the timed region
+
+    def load(k):
+        if used[k]:
+            copy_st.wait_event(freed[k])     # the step that read this set is done
+        with torch.cuda.stream(copy_st):
+            v_e[k].copy_(v_h, non_blocking=True)
+            dobs_e[k].copy_(dobs_h, non_blocking=True)
+        loaded[k].record(copy_st)
+        used[k] = True
+
+    load(0)
+    for i in range(args.steps):
+        k = i & 1
+        if i + 1 < args.steps:
+            load(1 - k)
+        stream.wait_event(loaded[k])
+        step(v_e[k], dobs_e[k], False)
+        freed[k].record(stream)
         out_grad_h.copy_(grad, non_blocking=True)
         out_J_h.copy_(J, non_blocking=True)
         out_v_h.copy_(v_out, non_blocking=True)
@@ -349,6 +376,19 @@ def run_ours(args, rank, world, local_rank):
         adj_bytes, fwd_bytes = cu * 4 + small, cu * 4 + B * NS * NR * NT * 4 + B * NZ_PHYS * NX_PHYS * 4
         adj_name, fwd_name = (("adjoint propagator", "forward propagator") if path == "resident"
                               else ("cluster adjoint (+ fold)", "cluster forward"))
+    elif path == "cpml":
+        # CPML kernels, compulsory bytes per cell-update: forward u read,
+        # u' written, increment read + written, record written (20 B) and, in
+        # the layer's share f of the cells, psi_x, psi_z, zeta_x, zeta_z read
+        # + written (32 B); adjoint mu, nu, imaging sum read + written, record
+        # read, h_x, h_z written + read (44 B) and in the layer psi, zeta
+        # adjoints read + written and t_x, t_z written + read (48 B); kappa
+        # once per model and step
+        f = 1.0 - NZ_PHYS * NX_PHYS / plane
+        tables = B * NT * plane * 4
+        fwd_bytes = int(cu * (20 + 32 * f)) + tables + B * NS * NR * NT * 4
+        adj_bytes = int(cu * (44 + 48 * f)) + tables + small
+        fwd_name, adj_name = "CPML forward (2 launches a step)", "CPML adjoint (3 launches a step)"
     else:
         # tiled, per cell-update: forward reads u, v and writes u, v (16 B;
         # + 4 B record); adjoint reads psi, w, imaging sum, record and writes
@@ -405,7 +445,7 @@ def run_ours(args, rank, world, local_rank):
         "data": f"synthetic (seeded {wl['kind'].replace('_', '/')} models)",
         "config": {"propagators": path, "workload": f"{B} x {NZ_PHYS}x{NX_PHYS} {wl['kind'].replace('_', '/')} models "
                                f"per GPU, {NS} shots, {NR} receivers, {NT} steps, 40-cell "
-                               f"absorbing layer, {record}",
+                               f"{'CPML' if path == 'cpml' else 'absorbing'} layer, {record}",
                    "batch_per_gpu": B, "global_batch": B * world,
                    "l2": ("inputs larger than L2 (wavefield record %.1f GB per step)" if not K
                           else "inputs larger than L2 (propagator fields %.1f GB)")
@@ -440,6 +480,8 @@ def main():
                     help="time steps (0: the workload's); shorter runs size profiler captures")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--absorber", choices=["sponge", "cpml"], default="sponge",
+                    help="absorbing layer: the damping sponge (default) or the CPML variant")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -434,6 +434,12 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": n_models / t, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{n_models} full {NZ_PHYS}x{NX_PHYS} gradients ({NS} shots x {NT} "
                          f"steps, FP64) on {threads} threads, {t:.1f} s wall"}
+        if args.workload == "70x70":
+            # the same oracle on one thread: one full gradient
+            t1 = oracle_sample(1, 1, wl=wl)
+            cpu["single_thread"] = {"value": 1.0 / t1, "unit": UNIT, "cores": 1,
+                                    "sample": f"1 full {NZ_PHYS}x{NX_PHYS} gradient on 1 thread, "
+                                              f"{t1:.1f} s wall"}
 
     record = (f"checkpoints every {K} steps" if K else "store-all wavefield record")
     resident_gb = (B * NS * NT * plane * 4 if not K else B * NS * 6 * plane * 4) / 1e9

@@ -232,6 +232,37 @@ __device__ __forceinline__ int lower_bound_i(const int *a, int n, int x)
     return lo;
 }
 
+// The same first index with a[i] >= x, given that every a[i] < x for i < k
+// (a nondecreasing, x no smaller than at an earlier search that returned k):
+// a few steps forward from k, then a binary search of what is left.  The
+// threads of a trace take contiguous blocks of increasing x, so a thread
+// searches once in full and then mostly steps.
+constexpr int kWalk = 8;
+__device__ __forceinline__ int lower_bound_df_from(const df *a, int n, df x, int k)
+{
+    for (int s = 0; s < kWalk && k < n; ++s, ++k)
+        if (!df_lt(a[k], x)) return k;
+    int lo = k, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (df_lt(a[mid], x)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+__device__ __forceinline__ int lower_bound_i_from(const int *a, int n, int x, int k)
+{
+    for (int s = 0; s < kWalk && k < n; ++s, ++k)
+        if (a[k] >= x) return k;
+    int lo = k, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 struct CtxPtrs {
     float *M;        // [B]
     float *S;        // [B] sum of s_tr (Eq. final_objective denominator)
@@ -297,11 +328,22 @@ __device__ df build_cdf(const float *y, df *G, df *Gm, int nt, int nxi, float ep
 }
 
 // Quantile of node j as (base, frac): Q = (base + frac) dt.  Writes k*.
+// Contiguous block [*i0, *i1) of 0..n-1 for this thread of an NT_W2 block.
+__device__ __forceinline__ void thread_block(int n, int *i0, int *i1)
+{
+    const int c = (n + NT_W2 - 1) / NT_W2;
+    *i0 = min(n, (int)threadIdx.x * c);
+    *i1 = min(n, *i0 + c);
+}
+
+// Quantile node j of the CDF G (running maximum Gm) by the generalised
+// inverse: bracket k = first index with Gm[k] >= t_j = unit j; kfrom = k of
+// an earlier node of this thread (or 0: full search).
 __device__ __forceinline__ void quantile(const df *G, const df *Gm, int nt, df unit, int j,
-                                         int *kst, int *base, float *frac, df *tj)
+                                         int kfrom, int *kst, int *base, float *frac, df *tj)
 {
     const df t = df_mul_f(unit, (float)j);
-    const int k = lower_bound_df(Gm, nt, t);
+    const int k = kfrom > 0 ? lower_bound_df_from(Gm, nt, t, kfrom) : lower_bound_df(Gm, nt, t);
     *kst = k;
     *tj = t;
     if (k == 0) { *base = 0; *frac = 0.f; return; }
@@ -359,11 +401,14 @@ __global__ void __launch_bounds__(NT_W2) k_obs_trace(const float *__restrict__ d
     int *Qb = a.c.Qb + (size_t)tr_g * a.nxi;
     float *Qf = a.c.Qf + (size_t)tr_g * a.nxi;
     float part = 0.f;
-    for (int j = threadIdx.x; j < a.nxi; j += NT_W2) {
+    int j0, j1, kprev = 0;
+    thread_block(a.nxi, &j0, &j1);
+    for (int j = j0; j < j1; ++j) {
         int k, base;
         float frac;
         df t;
-        quantile(G, Gm, a.nt, unit, j, &k, &base, &frac, &t);
+        quantile(G, Gm, a.nt, unit, j, kprev, &k, &base, &frac, &t);
+        kprev = k;
         Qb[j] = base;
         Qf[j] = frac;
         const float q = ((float)base + frac) * a.dt;
@@ -412,11 +457,14 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
     const int *Qb = a.c.Qb + (size_t)tr_g * nxi;
     const float *Qf = a.c.Qf + (size_t)tr_g * nxi;
     float part = 0.f;
-    for (int j = threadIdx.x; j < nxi; j += NT_W2) {
+    int j0, j1, kprev = 0;
+    thread_block(nxi, &j0, &j1);
+    for (int j = j0; j < j1; ++j) {
         int k, base;
         float frac;
         df t;
-        quantile(G, Gm, nt, unit, j, &k, &base, &frac, &t);
+        quantile(G, Gm, nt, unit, j, kprev, &k, &base, &frac, &t);
+        kprev = k;
         // (base - base_obs) is exact; the fractions are in [0, 1]
         const float diff = ((float)(base - Qb[j]) + (frac - Qf[j])) * a.dt;
         dq[j] = diff;
@@ -457,14 +505,20 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
     const df C = block_sum_df(cpart, red);
     block_scan_df<0, true>(SA, nxi, red);
     block_scan_df<0, true>(SB, nxi, red);
-    // H_k into Gm (no longer needed), k = 0..nt-1 (H_nt = 0)
-    for (int k = threadIdx.x; k < nt; k += NT_W2) {
-        const int jk = lower_bound_i(ks, nxi, k);
-        const int jk1 = lower_bound_i(ks, nxi, k + 1);
-        df h = C;
-        if (jk1 < nxi) h = df_add(h, SA[jk1]);
-        if (jk < nxi) h = df_add(h, SB[jk]);
-        Gm[k] = h;
+    // H_k into Gm (no longer needed), k = 0..nt-1 (H_nt = 0); j(k) = first
+    // node whose bracket is >= k grows with k: a block of k per thread
+    int k0, k1;
+    thread_block(nt, &k0, &k1);
+    if (k0 < k1) {
+        int jk = lower_bound_i(ks, nxi, k0);
+        for (int k = k0; k < k1; ++k) {
+            const int jk1 = lower_bound_i_from(ks, nxi, k + 1, jk);
+            df h = C;
+            if (jk1 < nxi) h = df_add(h, SA[jk1]);
+            if (jk < nxi) h = df_add(h, SB[jk]);
+            Gm[k] = h;
+            jk = jk1;
+        }
     }
     __syncthreads();
     for (int m = threadIdx.x; m < nt; m += NT_W2) {

@@ -592,6 +592,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
                 acc_src = fmaf(nxt[(sz + 2) * P + sx + 2], RS[jj], acc_src);
             }
         }
+        __syncthreads();   // the last step's source-cell term reads RS before it is restaged
     }
 
     __syncthreads();

@@ -238,3 +238,33 @@ def test_cpml_plans():
     with pytest.raises(K.FwiError) as e:
         K.fwi_plan_create(_prob(api, absorber=2), K.W2Params())
     assert e.value.code == 1
+
+
+def test_compute_entry_points_reject_null_and_bad_sizes_without_a_gpu():
+    # argument checks run on the host before any CUDA call: every call below
+    # returns FWI_ERR_INVALID_ARG (1) on a machine with no GPU at all
+    K = __import__("paper_2603_16393_gb300.api", fromlist=["api"])
+    lib = K._lib
+    h = K.fwi_plan_create(_prob(K), K.W2Params())
+    p = h.raw
+    g = K._Guide(1.0, 0.1, 0.0, 0.5, 1e-4, 0.0, 0.0, 1.0)
+    calls = [
+        lambda: lib.fwi_forward(p, None, None, None, None, None),
+        lambda: lib.fwi_forward(None, None, None, None, None, None),
+        lambda: lib.fwi_w2_prepare(p, None, None, None),
+        lambda: lib.fwi_w2_misfit(p, None, None, None, None, None, None, None),
+        lambda: lib.fwi_adjoint_grad(p, None, None, None, None, None, None),
+        lambda: lib.fwi_w2_misfit_static(p, None, None, None, None, None, None),
+        lambda: lib.fwi_l2_misfit(p, None, None, 1.0, None, None, None),
+        lambda: lib.fwi_guided_step(0, 4, 4, ctypes.byref(g), *([None] * 7)),
+        lambda: lib.fwi_guided_step(1, 4, 4, None, *([None] * 7)),
+        lambda: lib.fwi_tv_grad(1, 4, 4, 0.1, 1.0, None, None, None, None, None),
+        lambda: lib.fwi_tv_grad(0, 4, 4, 0.1, 1.0, None, None, None, None, None),
+        lambda: lib.fwi_image_metrics(1, 4, 4, 1.0, None, None, None, None),
+        lambda: lib.fwi_check(p, None, None),
+        lambda: lib.fwi_plan_sizes(None, None, None, None),
+        lambda: lib.fwi_plan_kernels(p, None),
+    ]
+    for i, call in enumerate(calls):
+        assert call() == 1, i
+        assert K.fwi_last_error() != ""

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 10500  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 10600  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -359,6 +359,33 @@ FWI_API fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_pa
  * FWI_ERR_INVALID_ARG for trial_steps outside [2, nt]. */
 FWI_API fwi_status fwi_autotune_scratch_bytes(const fwi_problem *prob, const fwi_w2_params *w2,
                                               int trial_steps, size_t *bytes);
+
+/* Plan groups: uneven instances as one unit (a batching utility; the paper
+ * has no counterpart).  A group holds plans of any grid sizes and propagator
+ * families; fwi_group_gradient runs every plan's whole gradient (fwi_forward
+ * with its record or checkpoints, fwi_w2_misfit, fwi_adjoint_grad) on a
+ * stream of its own, forked from `stream` by an event and joined back to it,
+ * so that the plans' kernels overlap on the GPU and a capture of `stream`
+ * (cudaStreamBeginCapture) records the whole uneven set as one CUDA graph,
+ * replayed with one launch.  Results are those of the per-plan calls.
+ * fwi_group_create needs the current CUDA device (it creates the streams and
+ * events, owned by the group); the plans stay owned by the caller and must
+ * outlive the group.  Errors: FWI_ERR_INVALID_ARG, FWI_ERR_CUDA. */
+typedef struct fwi_group fwi_group;
+FWI_API fwi_status fwi_group_create(const fwi_plan *const *plans, int n, fwi_group **out);
+FWI_API void fwi_group_destroy(fwi_group *group);
+
+/* Every list has one entry per plan of the group, with the layout of the
+ * corresponding single-plan call: v [B][nz][nx]; obs_ctx from fwi_w2_prepare;
+ * d_syn and adj_src [B][ns][nr][nt] (written); snapshots of snapshot_bytes;
+ * grad [B][nz][nx] and J [B] (written); workspace of workspace_bytes.  The
+ * plans' buffers must not overlap.  Errors: FWI_ERR_INVALID_ARG for a NULL
+ * list or entry, otherwise those of the single-plan calls. */
+FWI_API fwi_status fwi_group_gradient(fwi_group *group, const float *const *v,
+                                      const void *const *obs_ctx, float *const *d_syn,
+                                      float *const *adj_src, float *const *snapshots,
+                                      float *const *grad, float *const *J,
+                                      void *const *workspace, void *stream);
 
 /* Wait for `stream` and return the device status word of `workspace`
  * (FWI_OK, FWI_ERR_UNSTABLE_CFL, FWI_ERR_DEVICE_TIMEOUT), then clear it. */

@@ -104,6 +104,12 @@ _lib.fwi_autotune_kernels.restype = _S
 _lib.fwi_autotune_kernels.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                       _vp]
+_lib.fwi_group_create.restype = _S
+_lib.fwi_group_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)]
+_lib.fwi_group_destroy.restype = None
+_lib.fwi_group_destroy.argtypes = [_vp]
+_lib.fwi_group_gradient.restype = _S
+_lib.fwi_group_gradient.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 8 + [_vp]
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -500,3 +506,52 @@ def autotune(prob: Problem, w2: W2Params | None = None, v=None, trial_steps: int
     scratch = torch.empty(max(n, 256), dtype=torch.uint8, device=v.device)
     fam, ms = fwi_autotune_kernels(prob, w2, v, trial_steps, scratch, stream)
     return dataclasses.replace(prob, kernels=fam), ms
+
+
+class Group:
+    """Plans of uneven grid sizes whose gradients run as one unit
+    (fwi_group_gradient): each plan's forward -> misfit -> adjoint on a stream
+    of its own, forked from and joined back to the calling stream, so a CUDA
+    graph capture of one call records the whole set.  The Plan objects keep
+    their own workspaces and snapshot buffers; outputs are allocated here once
+    and reused by every call."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        raw = (_vp * len(self.plans))(*[p.handle.raw for p in self.plans])
+        out = _vp()
+        _check(_lib.fwi_group_create(raw, len(self.plans), ctypes.byref(out)))
+        self.raw = out
+        self.d_syn = [torch.empty(p.data_shape, dtype=torch.float32, device=p.device)
+                      for p in self.plans]
+        self.adj = [torch.empty_like(d) for d in self.d_syn]
+        self.grad = [torch.empty(p.model_shape, dtype=torch.float32, device=p.device)
+                     for p in self.plans]
+        self.J = [torch.empty(p.prob.batch, dtype=torch.float32, device=p.device)
+                  for p in self.plans]
+
+    def gradient(self, vs, ctxs, stream=None):
+        """(J list, dJ/dv list) for models vs[i] against observation contexts
+        ctxs[i] (from plans[i].w2_prepare)."""
+        for p, v in zip(self.plans, vs):
+            _f32(v, p.model_shape, "v")
+        lists = [
+            [_ptr(v) for v in vs], [_ptr(c) for c in ctxs], [_ptr(t) for t in self.d_syn],
+            [_ptr(t) for t in self.adj], [_ptr(p.snapshots) for p in self.plans],
+            [_ptr(t) for t in self.grad], [_ptr(t) for t in self.J],
+            [_ptr(p.workspace) for p in self.plans]]
+        arrs = [(_vp * len(lst))(*[ctypes.cast(x, _vp) if x is not None else None for x in lst])
+                for lst in lists]
+        _check(_lib.fwi_group_gradient(self.raw, *arrs, _stream(stream)))
+        return self.J, self.grad
+
+    def close(self):
+        if self.raw:
+            _lib.fwi_group_destroy(self.raw)
+            self.raw = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(api):
     lib = ctypes.CDLL(LIB)
     for n in declared_functions():
         assert hasattr(lib, n), n
-    assert api.fwi_version() == 10500
+    assert api.fwi_version() == 10600
 
 
 def _prob(api, **kw):
@@ -268,3 +268,17 @@ def test_compute_entry_points_reject_null_and_bad_sizes_without_a_gpu():
     for i, call in enumerate(calls):
         assert call() == 1, i
         assert K.fwi_last_error() != ""
+
+
+def test_group_create_rejects_bad_arguments_without_a_gpu():
+    K = __import__("paper_2603_16393_gb300.api", fromlist=["api"])
+    lib = K._lib
+    h = K.fwi_plan_create(_prob(K), K.W2Params())
+    out = ctypes.c_void_p()
+    plans = (ctypes.c_void_p * 2)(h.raw, None)
+    assert lib.fwi_group_create(plans, 0, ctypes.byref(out)) == 1
+    assert lib.fwi_group_create(plans, 2, ctypes.byref(out)) == 1      # plan 1 is NULL
+    assert lib.fwi_group_create(None, 1, ctypes.byref(out)) == 1
+    assert lib.fwi_group_create(plans, 1, None) == 1
+    nul = (ctypes.c_void_p * 1)(None)
+    assert lib.fwi_group_gradient(None, *([nul] * 8), None) == 1

@@ -475,6 +475,115 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+# the batched uneven workload: (workload, models) -- curved/faulted models,
+# observed data with Gaussian noise at 10 dB SNR
+MIXED = (("70x70", 64), ("256x256", 8), ("512x1024", 2))
+
+
+def run_mixed(args, rank, world, local_rank):
+    """--mixed: 64 x 70x70 + 8 x 256x256 + 2 x 512x1024 models in one plan
+    group; a step (observation preparation, the group's gradients, guided
+    step per plan) is captured once into a CUDA graph and replayed.  Also
+    times the same work as per-plan calls in sequence on one stream."""
+    import torch
+    from paper_2603_16393_gb300 import api
+    from paper_2603_16393_gb300 import inputs as I
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    plans, dobs, vs, outs = [], [], [], []
+    n_models = 0
+    for i, (name, B) in enumerate(MIXED):
+        wl = dict(WORKLOADS[name], kind="curved_faulted")
+        vt, v0, geo = workload_inputs(wl, B, seed0=rank_seed0(rank, B) + 1000 * i)
+        prob = api.Problem(nz=wl["nz"], nx=wl["nx"], nb=NB, nt=wl["nt"], dz=DX, dx=DX, dt=DT,
+                           src_iz=geo.src_iz, src_ix=geo.src_ix, rec_iz=geo.rec_iz,
+                           rec_ix=geo.rec_ix, v_max=4500.0, batch=B,
+                           checkpoint_every=wl["ckpt"])
+        plan = api.Plan(prob, api.W2Params(), device=dev)
+        d, _ = plan.forward(torch.tensor(vt, dtype=torch.float32, device=dev), store=False)
+        noise = I.gaussian_noise_like(d.cpu().numpy(), 10.0, seed=77 + i)
+        dobs.append(d + torch.tensor(noise, dtype=torch.float32, device=dev))
+        vs.append(torch.tensor(v0, dtype=torch.float32, device=dev))
+        outs.append((plan.new_ctx(), torch.empty_like(vs[-1]),
+                     torch.empty(B, dtype=torch.float32, device=dev)))
+        plans.append(plan)
+        n_models += B
+    group = api.Group(plans)
+    gparams = api.GuideParams(rho0=1.15, gamma=0.55, unit=1500.0)
+    stream = torch.cuda.current_stream(dev)
+
+    def prepare():
+        for plan, d, (ctx, _, _) in zip(plans, dobs, outs):
+            plan.w2_prepare(d, ctx)
+
+    def guide(grads):
+        for v, g, (_, v_out, rho) in zip(vs, grads, outs):
+            api.guided_step(v, v, g, g, gparams, v_out=v_out)
+
+    def step_group():
+        prepare()
+        _, grads = group.gradient(vs, [o[0] for o in outs])
+        guide(grads)
+
+    def step_sequential():
+        prepare()
+        grads = [plan.gradient(v, o[0])[1] for plan, v, o in zip(plans, vs, outs)]
+        guide(grads)
+
+    def timed(fn, steps):
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / steps
+
+    for _ in range(args.warmup):
+        step_sequential()
+    seq_ms = timed(step_sequential, max(1, args.steps // 2))
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            step_group()
+    stream.wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_group()
+    for _ in range(args.warmup):
+        graph.replay()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    ms = timed(graph.replay, args.steps)
+    clk = clocks.stop() if clocks else None
+    for plan in plans:
+        plan.check()
+    ms = max_over_ranks([ms], world, dev)[0]
+    if rank != 0:
+        return
+    line = {
+        "metric": "uneven batch models/s (64x70x70 + 8x256x256 + 2x512x1024, 5/16/32 shots, "
+                  "1000/2000/4000 steps)",
+        "value": world * n_models / (ms * 1e-3), "unit": "models/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded curved/faulted models, observed data at 10 dB SNR)",
+        "config": {"workload": "plan group: 64 x 70x70 (resident kernels), 8 x 256x256 (cluster "
+                               "kernels), 2 x 512x1024 (tiled, checkpoints every 32 steps); one "
+                               "CUDA graph per step (observation preparation, group gradients "
+                               "on forked streams, guided steps)",
+                   "propagators": [p.kernels for p in plans],
+                   "sequential_ms_per_step": seq_ms,
+                   "speedup_vs_sequential": seq_ms / ms},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,6 +597,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--absorber", choices=["sponge", "cpml"], default="sponge",
                     help="absorbing layer: the damping sponge (default) or the CPML variant")
+    ap.add_argument("--mixed", action="store_true",
+                    help="the batched uneven workload (64 x 70x70 + 8 x 256x256 + 2 x 512x1024) "
+                         "as one graph-captured plan group")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -498,6 +610,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, rank, world)
+        elif args.mixed:
+            run_mixed(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

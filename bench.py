@@ -584,6 +584,135 @@ def run_mixed(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_sampler(args, rank, world, local_rank):
+    """--sampler: reverse steps of Algorithm 2 (Sec. 5.2) on B models of the
+    70x70 workload: per step the Gaussian-prior score, the clean estimate and
+    proposal (fwi_ddpm_proposal), the W2 gradient at the clamped physical
+    model (forward -> misfit -> adjoint), the chain rule (fwi_ddpm_guidance)
+    and the preconditioned update (fwi_guided_step).  The observation is
+    fixed through the sampling, so its preparation runs once, untimed; the
+    draws z of every step are on the device before the timed region."""
+    import torch
+    from paper_2603_16393_gb300 import api
+    from paper_2603_16393_gb300 import inputs as I
+    from paper_2603_16393_gb300 import sampler as S
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = WORKLOADS["70x70"]
+    B = args.batch or wl["batch"]
+    nz, nx = wl["nz"], wl["nx"]
+    vt, _, geo = workload_inputs(wl, B, seed0=rank_seed0(rank, B))
+    prob = api.Problem(nz=nz, nx=nx, nb=NB, nt=args.nt or wl["nt"], dz=DX, dx=DX, dt=DT,
+                       src_iz=geo.src_iz, src_ix=geo.src_ix, rec_iz=geo.rec_iz,
+                       rec_ix=geo.rec_ix, v_max=4500.0, batch=B)
+    plan = api.Plan(prob, api.W2Params(), device=dev)
+    d_obs, _ = plan.forward(torch.tensor(vt, dtype=torch.float32, device=dev), store=False)
+    ctx = plan.w2_prepare(d_obs)
+    # the prior: per-cell moments of 64 seeded models of the same family,
+    # disjoint from the models that made the observations
+    prior = S.GaussianPrior.from_models(I.model_batch(wl["kind"], range(90_000, 90_064), nz, nx),
+                                        device=dev)
+    betas = S.linear_betas(1000)
+    smp = S.Sampler(plan, betas, ctx=ctx, prior=prior,
+                    guide=api.GuideParams(rho0=1.15, gamma=0.55))
+    total = args.warmup + args.steps
+    i0 = 400
+    gen = torch.Generator(device=dev).manual_seed(1234 + rank)
+    zs = torch.randn((total, B, nz, nx), device=dev, generator=gen)
+    ab = smp.steps[i0].abar
+    v = (ab ** 0.5) * prior.mu + (1 - ab) ** 0.5 * torch.randn((B, nz, nx), device=dev,
+                                                                generator=gen)
+    bufs = [torch.empty_like(v) for _ in range(2)]
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier(world):
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for w in range(args.warmup):
+        v, _ = smp.step(v, i0 - w, zs[w], v_out=bufs[w % 2])
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    a.record(stream)
+    for k in range(args.steps):
+        w = args.warmup + k
+        v, info = smp.step(v, i0 - w, zs[w], v_out=bufs[w % 2])
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    ms = a.elapsed_time(b) / args.steps
+    plan.check()
+    ms = max_over_ranks([ms], world, dev)[0]
+
+    # the two elementwise kernels alone, at this batch (bytes: v_i, z read,
+    # v0hat, v', v_phys written; v0hat, g_phys read, g, h written; the
+    # per-cell prior arrays are read once per launch)
+    st = smp.steps[i0]
+    n = B * nz * nx
+    reps = 50
+
+    def per_launch(fn):
+        # the launches replayed from one CUDA graph: device time per launch,
+        # not the host's launch rate
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            fn()
+        stream.wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(reps):
+                fn()
+        graph.replay()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    t_prop = per_launch(lambda: api.fwi_ddpm_proposal(
+        B, nz * nx, st, smp.space, v, None, prior.mu, prior.tau2, zs[0], smp.v0hat, smp.v_prime,
+        smp.v_phys))
+    t_guid = per_launch(lambda: api.fwi_ddpm_guidance(
+        B, nz * nx, st, smp.space, smp.v0hat, smp.g, None, prior.tau2, bufs[0], smp.h))
+    if rank != 0:
+        return
+    by_prop, by_guid = 20 * n + 8 * nz * nx, 16 * n + 4 * nz * nx
+    line = {
+        "metric": "Algorithm 2 reverse steps x models/s (70x70, 5 shots, 1000 steps, W2 guidance)",
+        "value": world * B / (ms * 1e-3), "unit": "model-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded layered models; Gaussian prior fitted to 64 seeded models)",
+        "config": {"workload": f"{B} x 70x70 models per GPU, reverse steps {i0}..{i0 - total + 1} "
+                               "of a 1000-step linear schedule; per step: prior score, clean "
+                               "estimate, proposal, W2 gradient (5 shots, 1000 steps), chain "
+                               "rule, preconditioned update",
+                   "batch_per_gpu": B,
+                   "l2": "inputs larger than L2 (wavefield record 10 GB per step)"},
+        "elementwise_kernels": {
+            "proposal": {"ms": t_prop, "gb_s": by_prop / (t_prop * 1e-3) / 1e9,
+                         "bytes": by_prop},
+            "guidance": {"ms": t_guid, "gb_s": by_guid / (t_guid * 1e-3) / 1e9,
+                         "bytes": by_guid},
+            "share_of_step": (t_prop + t_guid) / ms,
+            "timing": "50 launches replayed from one CUDA graph; HBM peak "
+                      f"{peaks()[0]:.0f} GB/s (of measured)"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -600,6 +729,9 @@ def main():
     ap.add_argument("--mixed", action="store_true",
                     help="the batched uneven workload (64 x 70x70 + 8 x 256x256 + 2 x 512x1024) "
                          "as one graph-captured plan group")
+    ap.add_argument("--sampler", action="store_true",
+                    help="reverse steps of Algorithm 2 (score, proposal, W2 guidance gradient, "
+                         "chain rule, preconditioned update) on the 70x70 workload")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -612,6 +744,8 @@ def main():
             run_reference(args, rank, world)
         elif args.mixed:
             run_mixed(args, rank, world, local_rank)
+        elif args.sampler:
+            run_sampler(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

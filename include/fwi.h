@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 10600  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 10700  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -390,6 +390,77 @@ FWI_API fwi_status fwi_group_gradient(fwi_group *group, const float *const *v,
 /* Wait for `stream` and return the device status word of `workspace`
  * (FWI_OK, FWI_ERR_UNSTABLE_CFL, FWI_ERR_DEVICE_TIMEOUT), then clear it. */
 FWI_API fwi_status fwi_check(const fwi_plan *plan, void *workspace, void *stream);
+
+/* ---------------------------------------------------------------- reverse diffusion
+ * The elementwise steps of one reverse step i -> i-1 of Algorithm 1 (DPS) and
+ * Algorithm 2 (OT-guided preconditioned DPS) around the physics gradient:
+ *   s      = score of v_i (given, or of a Gaussian prior, below)
+ *   v0hat  = (v_i + (1 - abar_i) s) / sqrt(abar_i)                  (Eq. v0hat)
+ *   v'     = c_v v_i + c_0 v0hat + sigma_i z                (Algorithms 1-2)
+ *   v_phys = clamp(shift + unit v0hat, v_lo, v_hi)          (the physics model)
+ *   then, after the caller's fwi_forward -> misfit -> fwi_adjoint_grad at v_phys:
+ *   g      = unit dPhi/dv_phys [v_lo <= shift + unit v0hat <= v_hi]  (dPhi/dv0hat)
+ *   h      = (g + (1 - abar_i) (ds/dv_i)^T g) / sqrt(abar_i)    (Eq. chain_rule)
+ *   and fwi_guided_step(v', v0hat, g, h) with unit = 1 gives v_{i-1}
+ *   (Algorithm 2); rho0 = zeta, gamma = 0 and an unreachable tau give
+ *   P_i = zeta I, the DPS step of Algorithm 1 (Sec. 5.2).
+ * The diffusion state v_i, v0hat, v', g and h live in the normalised space
+ * x = (v - shift) / unit; v_phys and dPhi/dv_phys are in m/s.
+ * Gaussian prior (a closed-form score model): x_0 ~ N(mu, diag tau2), with
+ * the step-i marginal N(sqrt(abar_i) mu, abar_i tau2 + 1 - abar_i) of
+ * Eq. vp_transition, so s = -(v_i - sqrt(abar_i) mu) / (abar_i tau2 + 1 - abar_i)
+ * and (ds/dv_i)^T g = -g / (abar_i tau2 + 1 - abar_i); the kernels evaluate
+ * its v0hat and h in the equivalent cancellation-free forms
+ * (sqrt(abar_i) tau2 v_i + (1 - abar_i) mu) / D and sqrt(abar_i) tau2 g / D,
+ * D = abar_i tau2 + 1 - abar_i, because the forms above lose most float32
+ * digits at high noise (abar_i near 0). */
+typedef struct fwi_ddpm_step {
+    double abar;    /* abar_i = prod_{j<=i} (1 - beta_j), in (0, 1)              */
+    double c_v;     /* sqrt(alpha_i) (1 - abar_{i-1}) / (1 - abar_i)             */
+    double c_0;     /* sqrt(abar_{i-1}) beta_i / (1 - abar_i)                    */
+    double sigma;   /* sigma_i >= 0                                              */
+} fwi_ddpm_step;
+
+typedef struct fwi_diffusion_space {
+    double shift, unit;   /* v = shift + unit x (3000, 1500 map 1500..4500 to [-1, 1]) */
+    double v_lo, v_hi;    /* clamp of the physics model, v_lo < v_hi                    */
+} fwi_diffusion_space;
+
+#define FWI_SIGMA_POSTERIOR 0   /* sigma_i^2 = (1 - abar_{i-1}) beta_i / (1 - abar_i) */
+#define FWI_SIGMA_BETA 1        /* sigma_i^2 = beta_i                                 */
+
+/* Coefficients of reverse step i (1 <= i <= n_steps) from the schedule
+ * betas[0..n_steps) = beta_1..beta_N (host memory, each in (0, 1)), formed in
+ * FP64 on the host (no CUDA call).  Errors: FWI_ERR_INVALID_ARG. */
+FWI_API fwi_status fwi_ddpm_coefficients(const double *betas, int n_steps, int i,
+                                         int sigma_mode, fwi_ddpm_step *out);
+
+/* v0hat, v' and v_phys of reverse step `step` for B instances of ncell cells
+ * (all [B][ncell] device arrays, float32).
+ *   v_i    the current state; z the standard normal draws of this step
+ *   score  the score at v_i, or NULL for the Gaussian prior of mu, tau2
+ *          ([ncell] device arrays shared by the batch; ignored when score is
+ *          given; tau2 >= 0)
+ *   v0hat, v_prime, v_phys  written (none may alias an input)
+ * Errors: FWI_ERR_INVALID_ARG before any launch, FWI_ERR_CUDA. */
+FWI_API fwi_status fwi_ddpm_proposal(int batch, int ncell, const fwi_ddpm_step *step,
+                                     const fwi_diffusion_space *space, const float *v_i,
+                                     const float *score, const float *mu, const float *tau2,
+                                     const float *z, float *v0hat, float *v_prime,
+                                     float *v_phys, void *stream);
+
+/* g and h of reverse step `step` ([B][ncell] device arrays, float32).
+ *   v0hat   from fwi_ddpm_proposal; g_phys = dPhi/dv at v_phys (1/(m/s))
+ *   vjp     (ds/dv_i)^T g of the caller's score model, or NULL: then the
+ *           Gaussian prior's, from tau2 ([ncell]), or 0 when tau2 is NULL too
+ *           (a score that does not depend on v_i).  A network's vjp needs g
+ *           first: call once with both NULL, form the vjp from g, call again.
+ *   g, h    written (may not alias an input)
+ * Errors: FWI_ERR_INVALID_ARG before any launch, FWI_ERR_CUDA. */
+FWI_API fwi_status fwi_ddpm_guidance(int batch, int ncell, const fwi_ddpm_step *step,
+                                     const fwi_diffusion_space *space, const float *v0hat,
+                                     const float *g_phys, const float *vjp, const float *tau2,
+                                     float *g, float *h, void *stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 FWI_API const char *fwi_last_error(void);

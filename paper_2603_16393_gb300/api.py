@@ -35,6 +35,7 @@ FWI_ERR_DEVICE_TIMEOUT = 5
 FWI_ERR_OOM = 6
 KERNELS_AUTO, KERNELS_RESIDENT, KERNELS_TILED, KERNELS_CLUSTER, KERNELS_CPML = 0, 1, 2, 3, 4
 ABSORBER_SPONGE, ABSORBER_CPML = 0, 1
+SIGMA_POSTERIOR, SIGMA_BETA = 0, 1
 FWI_MAX_SHOTS = 256
 FWI_MAX_RECEIVERS = 1024
 
@@ -63,6 +64,14 @@ class _W2(ctypes.Structure):
 class _Guide(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("rho0", "c", "tau", "gamma", "eps", "kappa_min", "kappa_max", "unit")]
+
+
+class _DdpmStep(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("abar", "c_v", "c_0", "sigma")]
+
+
+class _Space(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("shift", "unit", "v_lo", "v_hi")]
 
 
 _S = ctypes.c_int
@@ -110,6 +119,15 @@ _lib.fwi_group_destroy.restype = None
 _lib.fwi_group_destroy.argtypes = [_vp]
 _lib.fwi_group_gradient.restype = _S
 _lib.fwi_group_gradient.argtypes = [_vp] + [ctypes.POINTER(_vp)] * 8 + [_vp]
+_lib.fwi_ddpm_coefficients.restype = _S
+_lib.fwi_ddpm_coefficients.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(_DdpmStep)]
+_lib.fwi_ddpm_proposal.restype = _S
+_lib.fwi_ddpm_proposal.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_DdpmStep),
+                                   ctypes.POINTER(_Space)] + [_vp] * 9
+_lib.fwi_ddpm_guidance.restype = _S
+_lib.fwi_ddpm_guidance.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_DdpmStep),
+                                   ctypes.POINTER(_Space)] + [_vp] * 7
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -206,6 +224,32 @@ class GuideParams:
 
     def _c(self):
         return _Guide(*(float(getattr(self, f)) for f, _ in _Guide._fields_))
+
+
+@dataclasses.dataclass(frozen=True)
+class DdpmStep:
+    """Coefficients of one reverse step (fwi_ddpm_step): abar_i and
+    v' = c_v v_i + c_0 v0hat + sigma z."""
+    abar: float
+    c_v: float
+    c_0: float
+    sigma: float
+
+    def _c(self):
+        return _DdpmStep(self.abar, self.c_v, self.c_0, self.sigma)
+
+
+@dataclasses.dataclass(frozen=True)
+class DiffusionSpace:
+    """Normalised diffusion space x = (v - shift) / unit and the clamp of the
+    physics model (fwi_diffusion_space)."""
+    shift: float = 3000.0
+    unit: float = 1500.0
+    v_lo: float = 1500.0
+    v_hi: float = 4500.0
+
+    def _c(self):
+        return _Space(self.shift, self.unit, self.v_lo, self.v_hi)
 
 
 # ----------------------------------------------------------------- marshalling helpers
@@ -346,6 +390,30 @@ def fwi_tv_grad(batch, nz, nx, alpha, unit, v, g, h, tv, stream=None):
 def fwi_image_metrics(batch, nz, nx, data_range, v_true, v_rec, out, stream=None):
     _check(_lib.fwi_image_metrics(batch, nz, nx, ctypes.c_double(data_range), _ptr(v_true),
                                   _ptr(v_rec), _ptr(out), _stream(stream)))
+
+
+def fwi_ddpm_coefficients(betas: Sequence[float], i: int,
+                          sigma_mode: int = SIGMA_POSTERIOR) -> DdpmStep:
+    b = (ctypes.c_double * len(betas))(*[float(x) for x in betas])
+    out = _DdpmStep()
+    _check(_lib.fwi_ddpm_coefficients(b, len(betas), int(i), int(sigma_mode), ctypes.byref(out)))
+    return DdpmStep(out.abar, out.c_v, out.c_0, out.sigma)
+
+
+def fwi_ddpm_proposal(batch, ncell, step: DdpmStep, space: DiffusionSpace, v_i, score, mu, tau2,
+                      z, v0hat, v_prime, v_phys, stream=None):
+    st, sp = step._c(), space._c()
+    _check(_lib.fwi_ddpm_proposal(batch, ncell, ctypes.byref(st), ctypes.byref(sp), _ptr(v_i),
+                                  _ptr(score), _ptr(mu), _ptr(tau2), _ptr(z), _ptr(v0hat),
+                                  _ptr(v_prime), _ptr(v_phys), _stream(stream)))
+
+
+def fwi_ddpm_guidance(batch, ncell, step: DdpmStep, space: DiffusionSpace, v0hat, g_phys, vjp,
+                      tau2, g, h, stream=None):
+    st, sp = step._c(), space._c()
+    _check(_lib.fwi_ddpm_guidance(batch, ncell, ctypes.byref(st), ctypes.byref(sp), _ptr(v0hat),
+                                  _ptr(g_phys), _ptr(vjp), _ptr(tau2), _ptr(g), _ptr(h),
+                                  _stream(stream)))
 
 
 def fwi_check(plan, workspace, stream=None):

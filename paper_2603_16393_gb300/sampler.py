@@ -1,0 +1,166 @@
+"""Reverse-diffusion sampling with physics guidance on the library's kernels:
+Algorithm 2 (OT-guided preconditioned DPS, Sec. 5.2) and Algorithm 1 (DPS
+with the least-squares potential, Sec. 4.2).
+
+One reverse step i -> i-1 for B states v_i [B][nz][nx] in the normalised
+space x = (v - shift) / unit:
+  1. the score s(v_i, i): a Gaussian prior (closed form, evaluated inside
+     fwi_ddpm_proposal) or a caller's score model ``score_fn``;
+  2. fwi_ddpm_proposal: v0hat (Eq. v0hat), the proposal v' and the clamped
+     physical model v_phys in m/s;
+  3. the potential's gradient at v_phys: J of Eq. final_objective
+     (fwi_forward -> fwi_w2_misfit -> fwi_adjoint_grad) or Phi_l2;
+  4. fwi_ddpm_guidance: g = dPhi/dv0hat and h = dPhi/dv_i (Eq. chain_rule);
+  5. fwi_guided_step: v_{i-1} = v' - P_i h, P_i = rho_i D_i (Eq. precond_step),
+     or P_i = zeta I (Algorithm 1).
+Argument marshalling only: every step runs in the CUDA library (a caller's
+``score_fn`` runs wherever the caller's model does).
+
+A ``score_fn(v_i, i)`` returns ``(s, vjp)`` with ``s`` the score at v_i
+([B][nz][nx] float32 on the device) and ``vjp(g)`` = (ds/dv_i)^T g.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Callable, Sequence
+
+import numpy as np
+import torch
+
+from . import api
+
+# P_i = zeta I through fwi_guided_step: gamma = 0 makes every kappa 1 and an
+# unreachable TV threshold makes rho = rho0 = zeta
+_TAU_NEVER = 1e30
+
+
+def linear_betas(n: int, beta_1: float = 1e-4, beta_n: float = 0.02) -> list[float]:
+    """beta_1..beta_N, linear from beta_1 to beta_N (the DDPM schedule; the
+    paper fixes no values)."""
+    return [float(b) for b in np.linspace(beta_1, beta_n, n)]
+
+
+@dataclasses.dataclass
+class GaussianPrior:
+    """x_0 ~ N(mu, diag tau2) in the normalised space: a closed-form score
+    model (the score of its step-i marginal, Eq. vp_transition).  ``mu`` and
+    ``tau2`` are [nz][nx] float32 device tensors."""
+    mu: torch.Tensor
+    tau2: torch.Tensor
+
+    @classmethod
+    def from_models(cls, models, space: api.DiffusionSpace = api.DiffusionSpace(),
+                    floor: float = 1e-3, device=None) -> "GaussianPrior":
+        """Per-cell mean and variance of a set of velocity models [M][nz][nx]
+        (m/s, host or device), mapped to the normalised space; the variance is
+        kept >= ``floor``."""
+        m = np.asarray(models.cpu() if torch.is_tensor(models) else models, dtype=np.float64)
+        x = (m - space.shift) / space.unit
+        mu = x.mean(axis=0)
+        tau2 = np.maximum(x.var(axis=0), floor)
+        dev = device or torch.device("cuda")
+        return cls(torch.tensor(mu, dtype=torch.float32, device=dev),
+                   torch.tensor(tau2, dtype=torch.float32, device=dev))
+
+
+class Sampler:
+    """Algorithm 2 (``guide`` = GuideParams) or Algorithm 1 (``dps_zeta``) on
+    a plan of B models.
+
+    potential: "w2" (J of Eq. final_objective; needs ``ctx`` from
+    plan.w2_prepare), "l2" (Phi_l2 with ``d_obs`` and ``sigma_l2``) or None
+    (no guidance: v_{i-1} = v').  Exactly one of ``prior`` and ``score_fn``."""
+
+    def __init__(self, plan: api.Plan, betas: Sequence[float], *, potential: str | None = "w2",
+                 ctx=None, d_obs=None, sigma_l2: float = 1.0, prior: GaussianPrior | None = None,
+                 score_fn: Callable | None = None, guide: api.GuideParams | None = None,
+                 dps_zeta: float | None = None,
+                 space: api.DiffusionSpace = api.DiffusionSpace(),
+                 sigma_mode: int = api.SIGMA_POSTERIOR):
+        if (prior is None) == (score_fn is None):
+            raise ValueError("give exactly one of prior and score_fn")
+        if potential not in ("w2", "l2", None):
+            raise ValueError(f"unknown potential {potential!r}")
+        if potential == "w2" and ctx is None:
+            raise ValueError("the W2 potential needs the observation context ctx")
+        if potential == "l2" and d_obs is None:
+            raise ValueError("the l2 potential needs d_obs")
+        if potential is not None and (guide is None) == (dps_zeta is None):
+            raise ValueError("give exactly one of guide (Algorithm 2) and dps_zeta (Algorithm 1)")
+        self.plan, self.potential, self.ctx, self.d_obs = plan, potential, ctx, d_obs
+        self.sigma_l2, self.prior, self.score_fn, self.space = sigma_l2, prior, score_fn, space
+        self.N = len(betas)
+        self.steps = [None] + [api.fwi_ddpm_coefficients(betas, i, sigma_mode)
+                               for i in range(1, self.N + 1)]
+        if dps_zeta is not None:
+            self.gparams = api.GuideParams(rho0=float(dps_zeta), c=1.0, tau=_TAU_NEVER,
+                                           gamma=0.0, eps=1.0, unit=1.0)
+        elif guide is not None:
+            self.gparams = dataclasses.replace(guide, unit=1.0)
+        else:
+            self.gparams = None
+        B, nz, nx = plan.model_shape
+        self.B, self.ncell = B, nz * nx
+        dev = plan.device
+        new = lambda: torch.empty((B, nz, nx), dtype=torch.float32, device=dev)  # noqa: E731
+        self.v0hat, self.v_prime, self.v_phys, self.g, self.h = (new() for _ in range(5))
+
+    def _physics_gradient(self, stream):
+        if self.potential == "w2":
+            J, g_phys, _ = self.plan.gradient(self.v_phys, self.ctx, stream=stream)
+        else:
+            d_syn, _ = self.plan.forward(self.v_phys, stream=stream)
+            J, adj = self.plan.l2_misfit(self.d_obs, d_syn, self.sigma_l2, stream=stream)
+            g_phys = self.plan.adjoint_grad(self.v_phys, adj, stream=stream)
+        return J, g_phys
+
+    def step(self, v_i: torch.Tensor, i: int, z: torch.Tensor, v_out: torch.Tensor | None = None,
+             stream=None):
+        """v_{i-1} from v_i and this step's standard normal draws z (both
+        [B][nz][nx]).  Returns (v_{i-1}, {"J", "rho"}); J and rho are None
+        without a potential."""
+        if not 1 <= i <= self.N:
+            raise ValueError(f"step {i} outside 1..{self.N}")
+        st = self.steps[i]
+        shape = (self.B,) + tuple(self.plan.model_shape[1:])
+        api._f32(v_i, shape, "v_i")
+        api._f32(z, shape, "z")
+        if v_out is None:
+            v_out = torch.empty_like(v_i)
+        if self.prior is not None:
+            score, vjp, mu, tau2 = None, None, self.prior.mu, self.prior.tau2
+        else:
+            score, vjp = self.score_fn(v_i, i)
+            score = score.contiguous()
+            api._f32(score, shape, "score")
+            mu = tau2 = None
+        api.fwi_ddpm_proposal(self.B, self.ncell, st, self.space, v_i, score, mu, tau2, z,
+                              self.v0hat, self.v_prime, self.v_phys, stream)
+        if self.potential is None:
+            v_out.copy_(self.v_prime)
+            return v_out, {"J": None, "rho": None}
+        J, g_phys = self._physics_gradient(stream)
+        if vjp is None:
+            api.fwi_ddpm_guidance(self.B, self.ncell, st, self.space, self.v0hat, g_phys, None,
+                                  tau2, self.g, self.h, stream)
+        else:
+            # the network's vjp needs g first: g (and h without the score
+            # term), then h with (ds/dv_i)^T g
+            api.fwi_ddpm_guidance(self.B, self.ncell, st, self.space, self.v0hat, g_phys, None,
+                                  None, self.g, self.h, stream)
+            u = vjp(self.g).contiguous()
+            api._f32(u, shape, "vjp")
+            api.fwi_ddpm_guidance(self.B, self.ncell, st, self.space, self.v0hat, g_phys, u,
+                                  None, self.g, self.h, stream)
+        v_out, rho = api.guided_step(self.v_prime, self.v0hat, self.g, self.h, self.gparams,
+                                     v_out=v_out, stream=stream)
+        return v_out, {"J": J, "rho": rho}
+
+    def sample(self, v_start: torch.Tensor, noise: Callable[[int], torch.Tensor],
+               i_start: int | None = None, i_stop: int = 1, stream=None) -> torch.Tensor:
+        """Reverse steps i_start..i_stop (default N..1) from v_start; ``noise(i)``
+        gives step i's draws z.  Returns the state after step i_stop."""
+        v = v_start
+        for i in range(i_start or self.N, i_stop - 1, -1):
+            v, _ = self.step(v, i, noise(i), stream=stream)
+        return v

@@ -1,0 +1,90 @@
+"""Reverse-diffusion entry points on the host (no GPU): the per-step
+coefficients of Algorithms 1-2 that fwi_ddpm_coefficients forms in FP64
+agree with the oracle's schedule, and the elementwise calls reject bad
+arguments before any CUDA call."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import diffusion as D
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2603_16393_gb300 import api as A
+    return A
+
+
+@pytest.mark.parametrize("mode,name", [(0, "posterior"), (1, "beta")])
+def test_coefficients_match_the_oracle_schedule(api, mode, name):
+    betas = D.linear_betas(1000)
+    sched = D.Schedule(betas, sigma=name)
+    for i in (1, 2, 3, 17, 250, 999, 1000):
+        st = api.fwi_ddpm_coefficients(list(betas), i, mode)
+        c_v, c_0, sg = sched.proposal_coefficients(i)
+        assert math.isclose(st.abar, sched.abar[i], rel_tol=1e-14)
+        assert math.isclose(st.c_v, c_v, rel_tol=1e-12, abs_tol=1e-300)
+        assert math.isclose(st.c_0, c_0, rel_tol=1e-12)
+        assert math.isclose(st.sigma, sg, rel_tol=1e-12, abs_tol=1e-300)
+
+
+def test_coefficients_of_a_cosine_like_schedule(api):
+    # any schedule in (0, 1): abar is the product of the alphas up to i
+    rng = np.random.default_rng(2)
+    betas = np.sort(rng.uniform(1e-5, 0.3, 64))
+    sched = D.Schedule(betas)
+    for i in (1, 8, 64):
+        st = api.fwi_ddpm_coefficients(list(betas), i)
+        assert math.isclose(st.abar, sched.abar[i], rel_tol=1e-13)
+        assert math.isclose(st.c_0, sched.proposal_coefficients(i)[1], rel_tol=1e-12)
+
+
+def test_coefficients_reject_bad_arguments(api):
+    lib = api._lib
+    out = api._DdpmStep()
+    b = (ctypes.c_double * 3)(0.1, 0.2, 0.3)
+    bad = (ctypes.c_double * 3)(0.1, 1.0, 0.3)
+    assert lib.fwi_ddpm_coefficients(None, 3, 1, 0, ctypes.byref(out)) == 1
+    assert lib.fwi_ddpm_coefficients(b, 3, 1, 0, None) == 1
+    assert lib.fwi_ddpm_coefficients(b, 3, 0, 0, ctypes.byref(out)) == 1
+    assert lib.fwi_ddpm_coefficients(b, 3, 4, 0, ctypes.byref(out)) == 1
+    assert lib.fwi_ddpm_coefficients(b, 3, 1, 2, ctypes.byref(out)) == 1
+    assert lib.fwi_ddpm_coefficients(bad, 3, 2, 0, ctypes.byref(out)) == 1
+    assert lib.fwi_ddpm_coefficients(bad, 3, 1, 0, ctypes.byref(out)) == 0   # only beta_1 is read
+    with pytest.raises(api.FwiError):
+        api.fwi_ddpm_coefficients([0.1, -0.2], 2)
+
+
+def test_elementwise_calls_reject_bad_arguments_without_a_gpu(api):
+    lib = api._lib
+    st = api._DdpmStep(0.5, 0.3, 0.6, 0.1)
+    sp = api._Space(3000.0, 1500.0, 1500.0, 4500.0)
+    x = ctypes.c_void_p(16)   # never dereferenced: every call below fails its host checks
+    S, P = ctypes.byref(st), ctypes.byref(sp)
+    calls = [
+        lambda: lib.fwi_ddpm_proposal(0, 4, S, P, x, x, x, x, x, x, x, x, None),
+        lambda: lib.fwi_ddpm_proposal(1, 0, S, P, x, x, x, x, x, x, x, x, None),
+        lambda: lib.fwi_ddpm_proposal(1, 4, None, P, x, x, x, x, x, x, x, x, None),
+        lambda: lib.fwi_ddpm_proposal(1, 4, S, None, x, x, x, x, x, x, x, x, None),
+        lambda: lib.fwi_ddpm_proposal(1, 4, S, P, None, x, x, x, x, x, x, x, None),
+        lambda: lib.fwi_ddpm_proposal(1, 4, S, P, x, None, None, x, x, x, x, x, None),  # no mu
+        lambda: lib.fwi_ddpm_proposal(1, 4, S, P, x, x, x, x, None, x, x, x, None),
+        lambda: lib.fwi_ddpm_proposal(1, 4, S, P, x, x, x, x, x, x, None, x, None),
+        lambda: lib.fwi_ddpm_guidance(1, 4, S, P, None, x, None, None, x, x, None),
+        lambda: lib.fwi_ddpm_guidance(1, 4, S, P, x, x, None, None, x, None, None),
+        lambda: lib.fwi_ddpm_guidance(-1, 4, S, P, x, x, None, None, x, x, None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == 1, k
+        assert api.fwi_last_error() != ""
+    for bad_step in (api._DdpmStep(0.0, 0.3, 0.6, 0.1), api._DdpmStep(1.5, 0.3, 0.6, 0.1),
+                     api._DdpmStep(0.5, math.nan, 0.6, 0.1), api._DdpmStep(0.5, 0.3, 0.6, -1.0)):
+        assert lib.fwi_ddpm_guidance(1, 4, ctypes.byref(bad_step), P, x, x, None, None, x, x,
+                                     None) == 1
+    for bad_space in (api._Space(3000.0, 0.0, 1500.0, 4500.0),
+                      api._Space(3000.0, 1500.0, 4500.0, 1500.0),
+                      api._Space(math.inf, 1500.0, 1500.0, 4500.0)):
+        assert lib.fwi_ddpm_guidance(1, 4, S, ctypes.byref(bad_space), x, x, None, None, x, x,
+                                     None) == 1

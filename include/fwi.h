@@ -391,6 +391,28 @@ FWI_API fwi_status fwi_group_gradient(fwi_group *group, const float *const *v,
  * (FWI_OK, FWI_ERR_UNSTABLE_CFL, FWI_ERR_DEVICE_TIMEOUT), then clear it. */
 FWI_API fwi_status fwi_check(const fwi_plan *plan, void *workspace, void *stream);
 
+/* ---------------------------------------------------------------- tensor-core convolution
+ * 3x3 convolution, stride 1, zero padding 1, the dense contraction of a
+ * convolutional score model or surrogate used for the guidance of
+ * Algorithms 1-2 (the paper's score network is a U-Net, Sec. 6; its surrogate
+ * idea is in Sec. 7):
+ *   y[b][p][co] = act(bias[co] + sum_{t in 3x3, ci} x[b][p + t][ci] w[co][t][ci])
+ * with x outside the image read as 0; act 0: identity, 1: SiLU v / (1 + e^-v).
+ * Runs on the tcgen05 tensor cores: BF16 operands, FP32 accumulation.
+ *   x    [n][h][w][cin]  bf16 device (NHWC), 16-byte aligned
+ *   wt   [cout][3][3][cin] bf16 device (tap t = 3 ky + kx, offsets ky-1, kx-1)
+ *   bias [cout] fp32 device, or NULL
+ *   y    [n][h][w][cout] device, fp32 (y_bf16 = 0) or bf16 (y_bf16 = 1, round to
+ *        nearest even), 16-byte aligned, not aliasing x
+ *   status  device int, or NULL: set to FWI_ERR_DEVICE_TIMEOUT if a device-side
+ *        wait ran out (the outputs are then not written)
+ * cin and cout are positive multiples of 64.
+ * Errors: FWI_ERR_INVALID_ARG, FWI_ERR_UNSUPPORTED before any launch,
+ * FWI_ERR_CUDA. */
+FWI_API fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *x,
+                                    const void *wt, const float *bias, int act, void *y,
+                                    int y_bf16, int *status, void *stream);
+
 /* ---------------------------------------------------------------- reverse diffusion
  * The elementwise steps of one reverse step i -> i-1 of Algorithm 1 (DPS) and
  * Algorithm 2 (OT-guided preconditioned DPS) around the physics gradient:

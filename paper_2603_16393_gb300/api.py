@@ -128,6 +128,9 @@ _lib.fwi_ddpm_proposal.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D
 _lib.fwi_ddpm_guidance.restype = _S
 _lib.fwi_ddpm_guidance.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_DdpmStep),
                                    ctypes.POINTER(_Space)] + [_vp] * 7
+_lib.fwi_conv3x3_bf16.restype = _S
+_lib.fwi_conv3x3_bf16.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, ctypes.c_int, _vp,
+                                                       ctypes.c_int, _vp, _vp]
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -414,6 +417,33 @@ def fwi_ddpm_guidance(batch, ncell, step: DdpmStep, space: DiffusionSpace, v0hat
     _check(_lib.fwi_ddpm_guidance(batch, ncell, ctypes.byref(st), ctypes.byref(sp), _ptr(v0hat),
                                   _ptr(g_phys), _ptr(vjp), _ptr(tau2), _ptr(g), _ptr(h),
                                   _stream(stream)))
+
+
+def fwi_conv3x3_bf16(x, wt, bias, act, y, status=None, stream=None):
+    """3x3 convolution on the tensor cores: x [n][h][w][cin] bf16, wt
+    [cout][3][3][cin] bf16, bias [cout] fp32 or None, y [n][h][w][cout] fp32 or
+    bf16 (all contiguous CUDA tensors); act 0 identity, 1 SiLU."""
+    n, h, w, cin = x.shape
+    cout = wt.shape[0]
+    if x.dtype != torch.bfloat16 or wt.dtype != torch.bfloat16:
+        raise TypeError("x and wt must be bfloat16")
+    if tuple(wt.shape) != (cout, 3, 3, cin):
+        raise ValueError(f"wt must have shape {(cout, 3, 3, cin)}, got {tuple(wt.shape)}")
+    if tuple(y.shape) != (n, h, w, cout) or y.dtype not in (torch.float32, torch.bfloat16):
+        raise ValueError("y must be [n][h][w][cout] float32 or bfloat16")
+    if bias is not None:
+        _f32(bias, (cout,), "bias")
+    _check(_lib.fwi_conv3x3_bf16(n, h, w, cin, cout, _ptr(x), _ptr(wt), _ptr(bias), int(act),
+                                 _ptr(y), int(y.dtype == torch.bfloat16), _ptr(status),
+                                 _stream(stream)))
+
+
+def conv3x3(x, wt, bias=None, act=0, out_dtype=torch.float32, status=None, stream=None):
+    """Allocating form of fwi_conv3x3_bf16; returns y."""
+    n, h, w, _ = x.shape
+    y = torch.empty((n, h, w, wt.shape[0]), dtype=out_dtype, device=x.device)
+    fwi_conv3x3_bf16(x, wt, bias, act, y, status, stream)
+    return y
 
 
 def fwi_check(plan, workspace, stream=None):

@@ -1,0 +1,518 @@
+// conv_tc.cu -- 3x3 convolution (stride 1, zero padding 1) on the fifth-
+// generation tensor cores, the dense contraction of a convolutional score or
+// surrogate network for the guidance of Algorithms 1-2:
+//
+//   y[n][p][co] = act(bias[co] + sum_{tap, ci} x[n][p + tap][ci] w[co][tap][ci])
+//
+// as an implicit GEMM: M = 128 output pixels (an 8 x 16 tile of one image),
+// N = BN output channels (64 or 128), K = 9 taps x cin.  Layouts: x NHWC bf16,
+// w [cout][3][3][cin] bf16 (K-major), y NHWC fp32 or bf16.
+//
+// Operand A comes from one halo box per 64-channel block: the 16 x 18 pixels
+// around the tile (a 4D cp.async.bulk.tensor load, 128-byte swizzled, one
+// 128-byte row per pixel; pixels outside the image read the zero fill, which
+// is the padding).  The nine tap-shifted 128 x 64 operands are views into it:
+// view (dy, dx) starts at halo row 16 (dy + 1) + dx + 1 and its 8-row groups
+// (one image row of the tile each) are 16 rows = 2048 bytes apart; the
+// swizzle follows the absolute address, so the unaligned start rows need no
+// base offset.  A is thus read once per channel block instead of nine times.
+// Operand B, the weight block of one tap and channel block, streams through
+// its own ring.
+//
+// A persistent kernel, one CTA of eighteen warps per SM, tiles handed out
+// round-robin:
+//   * warp 0 (one thread) is the TMA producer, loading halo boxes and weight
+//     blocks in the order the MMAs consume them;
+//   * warp 1 allocates the tensor memory, and one of its threads issues the
+//     tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators of 128 lanes x
+//     BN columns) into one of two accumulators, returning ring stages and
+//     handing finished accumulators on through tcgen05.commit;
+//   * warps 2-17 are the epilogue: they read an accumulator back (tcgen05.ld;
+//     warp w owns lanes 32 (w mod 4) .. +31, i.e. those pixels, and a quarter
+//     of the columns), add the bias, apply the activation, store the pixels
+//     inside the image and release the accumulator, while the MMAs of the
+//     next tile fill the other one.  Sixteen warps, because with four the
+//     epilogue (not the MMAs) set the pace: 0.51 against 0.29 ms at 152 x
+//     70 x 70 x 128 -> 128.
+// Every mbarrier wait is bounded in time; a wait that runs out records
+// FWI_ERR_DEVICE_TIMEOUT in the caller's status word, and every role then
+// stops (the outputs are incomplete) and the CTA releases its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "fwi_internal.cuh"
+
+namespace {
+
+constexpr int kTW = 8, kTH = 16, kBM = kTW * kTH;   // output pixels per tile (the MMA's M)
+constexpr int kBK = 64;                              // channels per K block (128 bytes of bf16)
+constexpr int kHX = 16, kHY = kTH + 2;               // halo box: 16 x 18 pixels (x0-1 .. x0+14)
+constexpr int kHaloBytes = kHX * kHY * kBK * 2;      // 36 KB
+constexpr int kAStages = 2, kBStages = 8;
+constexpr int kThreads = 576;                        // producer, MMA, sixteen epilogue warps
+constexpr int kEpiWarps = 16;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // bound of one mbarrier wait: 2 s
+
+struct ConvArgs {
+    int n, h, w, cin, cout;
+    int act;       // 0: none, 1: SiLU
+    int y_bf16;    // output type: 0 fp32, 1 bf16
+    int tiles_x, tiles_y, tiles;   // pixel tiles per image row / column, tiles in all
+    const float *bias;
+    void *y;
+    int *status;
+};
+
+__device__ __forceinline__ unsigned su32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mb_init(uint64_t *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mb_try(uint64_t *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the completion of the barrier phase of the given parity; false
+// once *failed is set or after kWaitNs (then it sets *failed).
+__device__ __forceinline__ bool mb_wait(uint64_t *b, unsigned parity, volatile int *failed)
+{
+    if (mb_try(b, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mb_try(b, parity)) return true;
+        if (*failed) return false;
+        if (now_ns() - t0 > kWaitNs) {
+            *failed = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mb_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+
+__device__ __forceinline__ void mb_expect(uint64_t *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_4d(void *dst, const CUtensorMap *m, int c0, int c1, int c2,
+                                       int c3, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *m, int c0, int c1,
+                                       uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(m)), "r"(c0), "r"(c1), "r"(su32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand in a 128-byte-swizzled
+// buffer written by TMA: rows of 128 bytes, 8-row groups `group_bytes` apart
+// (stride byte offset), descriptor version 1, swizzle mode 128 B, base offset
+// 0.  The swizzle pattern follows the absolute shared-memory address (the
+// TMA wrote it that way into a 1024-byte-aligned buffer), so a view may start
+// at any 128-byte row of the buffer.
+__device__ __forceinline__ uint64_t sw128_desc(const void *start, uint32_t group_bytes)
+{
+    const uint64_t a = su32(start);
+    return ((a & 0x3FFFFull) >> 4) | (1ull << 16) | ((uint64_t)(group_bytes >> 4) << 32) |
+           (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N = n, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// Arrives on the mbarrier once every tcgen05.mma issued so far by this
+// thread has completed.
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// 16 consecutive fp32 columns of this warp's 32 accumulator lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float silu(float v) { return __fdividef(v, 1.f + __expf(-v)); }
+
+// Tile t -> image, pixel-tile origin and output-channel block (channel block
+// slowest, so the CTAs running at once share the weight blocks)
+struct Tile {
+    int img, x0, y0, n0;
+};
+__device__ __forceinline__ Tile tile_of(int t, const ConvArgs &a, int BN)
+{
+    const int per_block = a.tiles;
+    Tile r;
+    const int cbk = t / per_block;
+    t -= cbk * per_block;
+    const int tx = t % a.tiles_x;
+    t /= a.tiles_x;
+    const int ty = t % a.tiles_y;
+    r.img = t / a.tiles_y;
+    r.x0 = tx * kTW;
+    r.y0 = ty * kTH;
+    r.n0 = cbk * BN;
+    return r;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
+                 const ConvArgs a)
+{
+    constexpr int kBBytes = BN * kBK * 2;
+    constexpr uint32_t kIdesc = idesc_bf16(BN);
+    constexpr uint32_t kTmemCols = 2 * BN;   // two accumulators
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char *sA = base;                           // kAStages halo boxes
+    unsigned char *sB = base + kAStages * kHaloBytes;   // kBStages weight blocks
+    __shared__ uint64_t a_full[kAStages], a_empty[kAStages], b_full[kBStages], b_empty[kBStages];
+    __shared__ uint64_t acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    volatile int *vfailed = &failed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cbs = a.cin / kBK;
+    const int total = a.tiles * (a.cout / BN);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kAStages; ++s) {
+            mb_init(&a_full[s], 1);
+            mb_init(&a_empty[s], 1);
+        }
+        for (int s = 0; s < kBStages; ++s) {
+            mb_init(&b_full[s], 1);
+            mb_init(&b_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mb_init(&acc_full[b], 1);
+            mb_init(&acc_empty[b], kEpiWarps);
+        }
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer, in the MMAs' order: per tile and channel block the
+            // halo box, then the nine weight blocks of that channel block
+            int ga = 0, gb = 0;
+            for (int t = blockIdx.x; t < total && !*vfailed; t += gridDim.x) {
+                const Tile tl = tile_of(t, a, BN);
+                for (int cb = 0; cb < cbs && !*vfailed; ++cb) {
+                    const int sa = ga % kAStages, ra = ga / kAStages;
+                    if (ra > 0 && !mb_wait(&a_empty[sa], (unsigned)((ra - 1) & 1), vfailed)) break;
+                    mb_expect(&a_full[sa], kHaloBytes);
+                    tma_4d(sA + sa * kHaloBytes, &tmx, cb * kBK, tl.x0 - 1, tl.y0 - 1, tl.img,
+                           &a_full[sa]);
+                    ++ga;
+                    for (int tap = 0; tap < 9; ++tap, ++gb) {
+                        const int sb = gb % kBStages, rb = gb / kBStages;
+                        if (rb > 0 && !mb_wait(&b_empty[sb], (unsigned)((rb - 1) & 1), vfailed))
+                            break;
+                        mb_expect(&b_full[sb], kBBytes);
+                        tma_2d(sB + sb * kBBytes, &tmw, tap * a.cin + cb * kBK, tl.n0, &b_full[sb]);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: tile number it fills accumulator it & 1 once the
+            // epilogue has released its previous use; per tap four K = 16
+            // steps, advancing the start address by 32 bytes inside the
+            // swizzled 128-byte rows
+            int ga = 0, gb = 0, it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok && !*vfailed; t += gridDim.x, ++it) {
+                const int b = it & 1, u = it >> 1;
+                if (u > 0 && !mb_wait(&acc_empty[b], (unsigned)((u - 1) & 1), vfailed)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                for (int cb = 0; cb < cbs && ok; ++cb, ++ga) {
+                    const int sa = ga % kAStages, ra = ga / kAStages;
+                    if (!mb_wait(&a_full[sa], (unsigned)(ra & 1), vfailed)) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned char *halo = sA + sa * kHaloBytes;
+                    for (int tap = 0; tap < 9; ++tap, ++gb) {
+                        const int sb = gb % kBStages, rb = gb / kBStages;
+                        if (!mb_wait(&b_full[sb], (unsigned)(rb & 1), vfailed)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int row = (tap / 3) * kHX + tap % 3;   // (dy + 1) 16 + dx + 1
+                        const uint64_t ad = sw128_desc(halo + row * 128, kHX * 128);
+                        const uint64_t bd = sw128_desc(sB + sb * kBBytes, 1024);
+#pragma unroll
+                        for (int k = 0; k < kBK / 16; ++k)
+                            umma_bf16(d, ad + 2 * k, bd + 2 * k, kIdesc,
+                                      (cb | tap | k) != 0);
+                        umma_commit(&b_empty[sb]);
+                    }
+                    if (ok) umma_commit(&a_empty[sa]);
+                }
+                if (ok) umma_commit(&acc_full[b]);
+            }
+        }
+    } else {
+        // epilogue warps 2..17: lanes 32 (warp mod 4) .. +31 of the accumulator
+        // (the lane quarter a warp may access), and one quarter of its columns
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        const int part = (warp - 2) >> 2;
+        const int cbeg = part * (BN / 4), cend = cbeg + BN / 4;
+        int it = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+            const int b = it & 1, u = it >> 1;
+            if (!mb_wait(&acc_full[b], (unsigned)(u & 1), vfailed)) break;
+            tc_fence_after();
+            const Tile tl = tile_of(t, a, BN);
+            const int px = tl.x0 + (m % kTW), py = tl.y0 + m / kTW;
+            const bool store = px < a.w && py < a.h;
+            const size_t pix = ((size_t)tl.img * a.h + (store ? py : 0)) * a.w + (store ? px : 0);
+#pragma unroll 1
+            for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c0), v);
+                if (!store) continue;
+                const int co = tl.n0 + c0;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float x = v[i] + (a.bias ? __ldg(a.bias + co + i) : 0.f);
+                    v[i] = a.act == 1 ? silu(x) : x;
+                }
+                if (a.y_bf16) {
+                    __nv_bfloat162 h2[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        h2[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                    uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) +
+                                                           pix * a.cout + co);
+                    dst[0] = *reinterpret_cast<uint4 *>(&h2[0]);
+                    dst[1] = *reinterpret_cast<uint4 *>(&h2[4]);
+                } else {
+                    float4 *dst =
+                        reinterpret_cast<float4 *>(static_cast<float *>(a.y) + pix * a.cout + co);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                }
+            }
+            // this warp's reads of accumulator b are complete: release it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mb_arrive(&acc_empty[b]);
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *vfailed && a.status) atomicExch(a.status, (int)FWI_ERR_DEVICE_TIMEOUT);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+template <int BN>
+size_t conv_smem()
+{
+    return (size_t)kAStages * kHaloBytes + (size_t)kBStages * BN * kBK * 2 + 1024;
+}
+
+template <int BN>
+cudaError_t launch_conv(const CUtensorMap &tmx, const CUtensorMap &tmw, const ConvArgs &a,
+                        cudaStream_t st)
+{
+    const size_t smem = conv_smem<BN>();
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // persistent: one CTA per SM (the kernel's shared memory allows no second)
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const long long total = (long long)a.tiles * (a.cout / BN);
+    const unsigned grid = (unsigned)(total < sms ? total : sms);
+    k_conv3x3_tc<BN><<<grid, kThreads, smem, st>>>(tmx, tmw, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *x, const void *wt,
+                            const float *bias, int act, void *y, int y_bf16, int *status,
+                            void *stream)
+{
+    if (n < 1 || h < 1 || w < 1)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "n, h, w must be >= 1");
+    if (cin < kBK || cin % kBK != 0 || cout < 64 || cout % 64 != 0)
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "cin and cout must be positive multiples of 64 (cin %d, cout %d)",
+                                 cin, cout);
+    if (act != 0 && act != 1) return fwi::record_error(FWI_ERR_INVALID_ARG, "act must be 0 or 1");
+    if (y_bf16 != 0 && y_bf16 != 1)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "y_bf16 must be 0 or 1");
+    if (!x || !wt || !y) return fwi::record_error(FWI_ERR_INVALID_ARG, "x, w and y must not be NULL");
+    if (((uintptr_t)x | (uintptr_t)wt | (uintptr_t)y) & 15)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "x, w and y must be 16-byte aligned");
+    const int tiles_x = (w + kTW - 1) / kTW, tiles_y = (h + kTH - 1) / kTH;
+    if ((size_t)n * tiles_y * tiles_x * (cout / 64) > 0x7fffffffull ||
+        (size_t)9 * cin > 0x7fffffffull ||
+        (size_t)n * h * w > ((size_t)1 << 40))
+        return fwi::record_error(FWI_ERR_UNSUPPORTED, "tensor too large for this build");
+    auto enc = tmap_encoder();
+    if (!enc) return fwi::record_error(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int BN = cout % 128 == 0 ? 128 : 64;
+    CUtensorMap tmx, tmw;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+        const cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)w * cin * 2,
+                                       (cuuint64_t)h * w * cin * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)kHX, (cuuint32_t)kHY, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc(&tmx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(x), dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return fwi::record_error(FWI_ERR_CUDA, "tensor map of x rejected");
+    }
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)9 * cin, (cuuint64_t)cout};
+        const cuuint64_t strides[1] = {(cuuint64_t)9 * cin * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)BN};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&tmw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(wt), dims, strides,
+                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return fwi::record_error(FWI_ERR_CUDA, "tensor map of w rejected");
+    }
+    ConvArgs a{n, h, w, cin, cout, act, y_bf16, tiles_x, tiles_y, n * tiles_y * tiles_x,
+               bias, y, status};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const cudaError_t e = BN == 128 ? launch_conv<128>(tmx, tmw, a, st)
+                                    : launch_conv<64>(tmx, tmw, a, st);
+    if (e != cudaSuccess)
+        return fwi::record_error(FWI_ERR_CUDA, "fwi_conv3x3_bf16 launch: %s", cudaGetErrorString(e));
+    return FWI_OK;
+}
+
+}  // extern "C"

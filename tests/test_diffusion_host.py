@@ -88,3 +88,21 @@ def test_elementwise_calls_reject_bad_arguments_without_a_gpu(api):
                       api._Space(math.inf, 1500.0, 1500.0, 4500.0)):
         assert lib.fwi_ddpm_guidance(1, 4, S, ctypes.byref(bad_space), x, x, None, None, x, x,
                                      None) == 1
+
+
+def test_conv_rejects_bad_arguments_without_a_gpu(api):
+    lib = api._lib
+    p = ctypes.c_void_p(4096)          # never dereferenced: every call fails its host checks
+    odd = ctypes.c_void_p(4096 + 8)
+    calls = [
+        lambda: lib.fwi_conv3x3_bf16(0, 4, 4, 64, 64, p, p, None, 0, p, 0, None, None),
+        lambda: lib.fwi_conv3x3_bf16(1, 4, 4, 32, 64, p, p, None, 0, p, 0, None, None),
+        lambda: lib.fwi_conv3x3_bf16(1, 4, 4, 64, 96, p, p, None, 0, p, 0, None, None),
+        lambda: lib.fwi_conv3x3_bf16(1, 4, 4, 64, 64, None, p, None, 0, p, 0, None, None),
+        lambda: lib.fwi_conv3x3_bf16(1, 4, 4, 64, 64, p, p, None, 2, p, 0, None, None),
+        lambda: lib.fwi_conv3x3_bf16(1, 4, 4, 64, 64, p, p, None, 0, p, 3, None, None),
+        lambda: lib.fwi_conv3x3_bf16(1, 4, 4, 64, 64, odd, p, None, 0, p, 0, None, None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == 1, k
+        assert api.fwi_last_error() != ""

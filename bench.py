@@ -726,7 +726,7 @@ def run_conv(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     n = args.batch or WORKLOADS["70x70"]["batch"]
     h = w = 70
-    c = 128
+    c = args.conv_channels
     gen = torch.Generator(device=dev).manual_seed(11 + rank)
     x = torch.randn((n, h, w, c), device=dev, generator=gen).to(torch.bfloat16)
     wt = (torch.randn((c, 3, 3, c), device=dev, generator=gen) / (9 * c) ** 0.5).to(torch.bfloat16)
@@ -780,16 +780,18 @@ def run_conv(args, rank, world, local_rank):
     except Exception:
         peak, src = 1900.0, "fallback"
     line = {
-        "metric": "3x3 conv TFLOP/s (152 x 70x70, 128->128 channels, bf16, bias + SiLU)",
+        "metric": f"3x3 conv TFLOP/s ({n} x 70x70, {c}->{c} channels, bf16, bias + SiLU)",
         "value": world * tf, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic (seeded normal)",
-        "config": {"workload": f"{n} x 70x70 x 128 -> 128, 3x3, stride 1, zero padding",
-                   "l2": "inputs larger than L2 (x and y 190 MB each)",
-                   "tiles": "128 pixels (8 x 16) x 128 channels per tile, one persistent CTA "
+        "config": {"workload": f"{n} x 70x70 x {c} -> {c}, 3x3, stride 1, zero padding",
+                   "l2": f"inputs larger than L2 (x and y {n * h * w * c * 2 / 1e6:.0f} MB each)",
+                   "tiles": f"128 pixels (8 x 16) x {min(c, 256) if c % 256 == 0 else (128 if c % 128 == 0 else 64)} channels per tile, one persistent CTA "
                             "per SM; 15 % of the MMA rows fall outside the 70 x 70 images and "
                             "are not credited"},
-        "roofline": {"bound": "tensor", "kernel": "k_conv3x3_tc<128>", "achieved": tf,
+        "roofline": {"bound": "tensor",
+                     "kernel": f"k_conv3x3_tc<{256 if c % 256 == 0 else (128 if c % 128 == 0 else 64)}>",
+                     "achieved": tf,
                      "peak": peak, "unit": "TFLOP/s", "frac": tf / peak, "peak_source": src,
                      "hbm_gb_s": byts / (ms * 1e-3) / 1e9, "algorithmic_bytes": byts},
         "cudnn_ms": ms_cudnn, "speedup_vs_cudnn": ms_cudnn / ms,
@@ -818,6 +820,8 @@ def main():
     ap.add_argument("--conv", action="store_true",
                     help="the tensor-core 3x3 convolution of a score-model layer "
                          "(152 x 70x70, 128 -> 128 channels, bf16)")
+    ap.add_argument("--conv-channels", type=int, default=128,
+                    help="--conv: input and output channels (a multiple of 64)")
     ap.add_argument("--sampler", action="store_true",
                     help="reverse steps of Algorithm 2 (score, proposal, W2 guidance gradient, "
                          "chain rule, preconditioned update) on the 70x70 workload")

@@ -406,7 +406,8 @@ FWI_API fwi_status fwi_check(const fwi_plan *plan, void *workspace, void *stream
  *        nearest even), 16-byte aligned, not aliasing x
  *   status  device int, or NULL: set to FWI_ERR_DEVICE_TIMEOUT if a device-side
  *        wait ran out (the outputs are then not written)
- * cin and cout are positive multiples of 64.
+ * cin and cout are positive multiples of 64 (a cout that is a multiple of 256 runs
+ * the widest, fastest MMA shape).
  * Errors: FWI_ERR_INVALID_ARG, FWI_ERR_UNSUPPORTED before any launch,
  * FWI_ERR_CUDA. */
 FWI_API fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *x,

@@ -5,17 +5,20 @@
 //   y[n][p][co] = act(bias[co] + sum_{tap, ci} x[n][p + tap][ci] w[co][tap][ci])
 //
 // as an implicit GEMM: M = 128 output pixels (an 8 x 16 tile of one image),
-// N = BN output channels (64 or 128), K = 9 taps x cin.  Layouts: x NHWC bf16,
-// w [cout][3][3][cin] bf16 (K-major), y NHWC fp32 or bf16.
+// N = BN output channels (256, 128 or 64: the largest that divides cout), K =
+// 9 taps x cin.  Layouts: x NHWC bf16, w [cout][3][3][cin] bf16 (K-major), y
+// NHWC fp32 or bf16.  The MMA rate per SM grows with N: 1.50 PFLOP/s at
+// N = 256 (a 256 -> 256 layer), 0.76 at N = 128 (128 -> 128), 152 x 70 x 70.
 //
-// Operand A comes from one halo box per 64-channel block: the 16 x 18 pixels
+// Operand A comes from one halo box per 64-channel block: the 10 x 18 pixels
 // around the tile (a 4D cp.async.bulk.tensor load, 128-byte swizzled, one
 // 128-byte row per pixel; pixels outside the image read the zero fill, which
 // is the padding).  The nine tap-shifted 128 x 64 operands are views into it:
-// view (dy, dx) starts at halo row 16 (dy + 1) + dx + 1 and its 8-row groups
-// (one image row of the tile each) are 16 rows = 2048 bytes apart; the
-// swizzle follows the absolute address, so the unaligned start rows need no
-// base offset.  A is thus read once per channel block instead of nine times.
+// view (dy, dx) starts at halo row 10 (dy + 1) + dx + 1 and its 8-row groups
+// (one image row of the tile each) are 10 rows = 1280 bytes apart; the
+// swizzle follows the absolute address, so neither the unaligned start rows
+// nor the 1280-byte group stride needs a base offset.  A is thus read once
+// per channel block instead of nine times.
 // Operand B, the weight block of one tap and channel block, streams through
 // its own ring.
 //
@@ -51,9 +54,12 @@ namespace {
 
 constexpr int kTW = 8, kTH = 16, kBM = kTW * kTH;   // output pixels per tile (the MMA's M)
 constexpr int kBK = 64;                              // channels per K block (128 bytes of bf16)
-constexpr int kHX = 16, kHY = kTH + 2;               // halo box: 16 x 18 pixels (x0-1 .. x0+14)
-constexpr int kHaloBytes = kHX * kHY * kBK * 2;      // 36 KB
-constexpr int kAStages = 2, kBStages = 8;
+constexpr int kHX = kTW + 2, kHY = kTH + 2;          // halo box: 10 x 18 pixels (x0-1 .. x0+8)
+constexpr int kHaloTx = kHX * kHY * kBK * 2;          // bytes one halo load delivers (22.5 KB)
+constexpr int kHaloBytes = (kHaloTx + 1023) / 1024 * 1024;   // its 1024-aligned slot (23 KB)
+constexpr int kAStages = 2;
+// weight-block ring: 8 stages of BN x 64 channels, 5 when BN = 256 (32 KB each)
+template <int BN> __host__ __device__ constexpr int b_stages() { return BN == 256 ? 5 : 8; }
 constexpr int kThreads = 576;                        // producer, MMA, sixteen epilogue warps
 constexpr int kEpiWarps = 16;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bound of one mbarrier wait: 2 s
@@ -241,6 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  const ConvArgs a)
 {
     constexpr int kBBytes = BN * kBK * 2;
+    constexpr int kBStages = b_stages<BN>();
     constexpr uint32_t kIdesc = idesc_bf16(BN);
     constexpr uint32_t kTmemCols = 2 * BN;   // two accumulators
     extern __shared__ unsigned char smem_raw[];
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int cb = 0; cb < cbs && !*vfailed; ++cb) {
                     const int sa = ga % kAStages, ra = ga / kAStages;
                     if (ra > 0 && !mb_wait(&a_empty[sa], (unsigned)((ra - 1) & 1), vfailed)) break;
-                    mb_expect(&a_full[sa], kHaloBytes);
+                    mb_expect(&a_full[sa], kHaloTx);
                     tma_4d(sA + sa * kHaloBytes, &tmx, cb * kBK, tl.x0 - 1, tl.y0 - 1, tl.img,
                            &a_full[sa]);
                     ++ga;
@@ -337,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             break;
                         }
                         tc_fence_after();
-                        const int row = (tap / 3) * kHX + tap % 3;   // (dy + 1) 16 + dx + 1
+                        const int row = (tap / 3) * kHX + tap % 3;   // (dy + 1) 10 + dx + 1
                         const uint64_t ad = sw128_desc(halo + row * 128, kHX * 128);
                         const uint64_t bd = sw128_desc(sB + sb * kBBytes, 1024);
 #pragma unroll
@@ -431,7 +438,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
 template <int BN>
 size_t conv_smem()
 {
-    return (size_t)kAStages * kHaloBytes + (size_t)kBStages * BN * kBK * 2 + 1024;
+    return (size_t)kAStages * kHaloBytes + (size_t)b_stages<BN>() * BN * kBK * 2 + 1024;
 }
 
 template <int BN>
@@ -480,7 +487,7 @@ fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *
         return fwi::record_error(FWI_ERR_UNSUPPORTED, "tensor too large for this build");
     auto enc = tmap_encoder();
     if (!enc) return fwi::record_error(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-    const int BN = cout % 128 == 0 ? 128 : 64;
+    const int BN = cout % 256 == 0 ? 256 : (cout % 128 == 0 ? 128 : 64);
     CUtensorMap tmx, tmw;
     {
         const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
@@ -508,7 +515,8 @@ fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *
     ConvArgs a{n, h, w, cin, cout, act, y_bf16, tiles_x, tiles_y, n * tiles_y * tiles_x,
                bias, y, status};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const cudaError_t e = BN == 128 ? launch_conv<128>(tmx, tmw, a, st)
+    const cudaError_t e = BN == 256 ? launch_conv<256>(tmx, tmw, a, st)
+                        : BN == 128 ? launch_conv<128>(tmx, tmw, a, st)
                                     : launch_conv<64>(tmx, tmw, a, st);
     if (e != cudaSuccess)
         return fwi::record_error(FWI_ERR_CUDA, "fwi_conv3x3_bf16 launch: %s", cudaGetErrorString(e));

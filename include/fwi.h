@@ -391,6 +391,31 @@ FWI_API fwi_status fwi_group_gradient(fwi_group *group, const float *const *v,
  * (FWI_OK, FWI_ERR_UNSTABLE_CFL, FWI_ERR_DEVICE_TIMEOUT), then clear it. */
 FWI_API fwi_status fwi_check(const fwi_plan *plan, void *workspace, void *stream);
 
+/* ---------------------------------------------------------------- low-fidelity guidance
+ * Grid transfers of the low-fidelity guidance surrogate (the multi-fidelity
+ * route to cheaper physics guidance, Sec. 7): the W2 potential of the problem
+ * coarsened by two (grid spacing and time step doubled, sources and the even
+ * receivers at the coarse cells index / 2, nb and nz, nx rounded up, nt / 2
+ * samples) is evaluated at R v, and its gradient with respect to v is R^T of
+ * the coarse gradient.  All arrays are float32 device arrays; outputs may not
+ * alias inputs.  Errors: FWI_ERR_INVALID_ARG before any launch, FWI_ERR_CUDA. */
+
+/* R: vc[b][I][J] = mean of v[b][2I..2I+1][2J..2J+1] inside the grid;
+ * v [B][nz][nx], vc [B][ceil(nz/2)][ceil(nx/2)]. */
+FWI_API fwi_status fwi_restrict2(int batch, int nz, int nx, const float *v, float *vc,
+                                 void *stream);
+
+/* R^T: g[b][i][j] = gc[b][i/2][j/2] / (the number of fine cells averaged into
+ * that coarse cell); gc [B][ceil(nz/2)][ceil(nx/2)], g [B][nz][nx]. */
+FWI_API fwi_status fwi_restrict2_transpose(int batch, int nz, int nx, const float *gc, float *g,
+                                           void *stream);
+
+/* Observations of the coarse problem: dc[b][s][r][m] = d[b][s][2r][2m + 1] for
+ * m < nt/2 (fine sample n holds the field at (n+1) dt, coarse sample m at
+ * (m+1) 2 dt); d [B][ns][nr][nt], dc [B][ns][ceil(nr/2)][nt/2]. */
+FWI_API fwi_status fwi_decimate2(int batch, int ns, int nr, int nt, const float *d, float *dc,
+                                 void *stream);
+
 /* ---------------------------------------------------------------- tensor-core convolution
  * 3x3 convolution, stride 1, zero padding 1, the dense contraction of a
  * convolutional score model or surrogate used for the guidance of

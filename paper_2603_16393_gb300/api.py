@@ -131,6 +131,12 @@ _lib.fwi_ddpm_guidance.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_D
 _lib.fwi_conv3x3_bf16.restype = _S
 _lib.fwi_conv3x3_bf16.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, ctypes.c_int, _vp,
                                                        ctypes.c_int, _vp, _vp]
+_lib.fwi_restrict2.restype = _S
+_lib.fwi_restrict2.argtypes = [ctypes.c_int] * 3 + [_vp] * 3
+_lib.fwi_restrict2_transpose.restype = _S
+_lib.fwi_restrict2_transpose.argtypes = [ctypes.c_int] * 3 + [_vp] * 3
+_lib.fwi_decimate2.restype = _S
+_lib.fwi_decimate2.argtypes = [ctypes.c_int] * 4 + [_vp] * 3
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -444,6 +450,55 @@ def conv3x3(x, wt, bias=None, act=0, out_dtype=torch.float32, status=None, strea
     y = torch.empty((n, h, w, wt.shape[0]), dtype=out_dtype, device=x.device)
     fwi_conv3x3_bf16(x, wt, bias, act, y, status, stream)
     return y
+
+
+def fwi_restrict2(v, vc=None, stream=None):
+    """R of the low-fidelity surrogate: 2 x 2 block means of [B][nz][nx] float32."""
+    B, nz, nx = v.shape
+    shape = (B, (nz + 1) // 2, (nx + 1) // 2)
+    _f32(v, (B, nz, nx), "v")
+    if vc is None:
+        vc = torch.empty(shape, dtype=torch.float32, device=v.device)
+    _f32(vc, shape, "vc")
+    _check(_lib.fwi_restrict2(B, nz, nx, _ptr(v), _ptr(vc), _stream(stream)))
+    return vc
+
+
+def fwi_restrict2_transpose(gc, nz, nx, g=None, stream=None):
+    """R^T: the fine-grid gradient of a function of R v from its coarse gradient."""
+    B = gc.shape[0]
+    _f32(gc, (B, (nz + 1) // 2, (nx + 1) // 2), "gc")
+    if g is None:
+        g = torch.empty((B, nz, nx), dtype=torch.float32, device=gc.device)
+    _f32(g, (B, nz, nx), "g")
+    _check(_lib.fwi_restrict2_transpose(B, nz, nx, _ptr(gc), _ptr(g), _stream(stream)))
+    return g
+
+
+def fwi_decimate2(d, dc=None, stream=None):
+    """The coarse problem's observations: even receivers, samples 2m + 1."""
+    B, ns, nr, nt = d.shape
+    shape = (B, ns, (nr + 1) // 2, nt // 2)
+    _f32(d, (B, ns, nr, nt), "d")
+    if dc is None:
+        dc = torch.empty(shape, dtype=torch.float32, device=d.device)
+    _f32(dc, shape, "dc")
+    _check(_lib.fwi_decimate2(B, ns, nr, nt, _ptr(d), _ptr(dc), _stream(stream)))
+    return dc
+
+
+def coarse_problem(prob: Problem) -> Problem:
+    """The low-fidelity twin of a problem (fwi_restrict2 and friends): grid,
+    spacing and time step doubled, nb rounded up, nt / 2 steps, sources at the
+    coarse cells index / 2, the even receivers likewise."""
+    rec = [(int(z) // 2, int(x) // 2)
+           for k, (z, x) in enumerate(zip(prob.rec_iz, prob.rec_ix)) if k % 2 == 0]
+    return dataclasses.replace(
+        prob, nz=(prob.nz + 1) // 2, nx=(prob.nx + 1) // 2, nb=(prob.nb + 1) // 2,
+        nt=prob.nt // 2, dz=2 * prob.dz, dx=2 * prob.dx, dt=2 * prob.dt,
+        src_iz=[int(z) // 2 for z in prob.src_iz], src_ix=[int(x) // 2 for x in prob.src_ix],
+        rec_iz=[r[0] for r in rec], rec_ix=[r[1] for r in rec],
+        checkpoint_every=(prob.checkpoint_every + 1) // 2 if prob.checkpoint_every else 0)
 
 
 def fwi_check(plan, workspace, stream=None):

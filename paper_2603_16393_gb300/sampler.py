@@ -9,7 +9,8 @@ space x = (v - shift) / unit:
   2. fwi_ddpm_proposal: v0hat (Eq. v0hat), the proposal v' and the clamped
      physical model v_phys in m/s;
   3. the potential's gradient at v_phys: J of Eq. final_objective
-     (fwi_forward -> fwi_w2_misfit -> fwi_adjoint_grad) or Phi_l2;
+     (fwi_forward -> fwi_w2_misfit -> fwi_adjoint_grad) or Phi_l2; in the
+     first reverse steps optionally the low-fidelity surrogate (LowFidelity);
   4. fwi_ddpm_guidance: g = dPhi/dv0hat and h = dPhi/dv_i (Eq. chain_rule);
   5. fwi_guided_step: v_{i-1} = v' - P_i h, P_i = rho_i D_i (Eq. precond_step),
      or P_i = zeta I (Algorithm 1).
@@ -63,20 +64,43 @@ class GaussianPrior:
                    torch.tensor(tau2, dtype=torch.float32, device=dev))
 
 
+class LowFidelity:
+    """The low-fidelity guidance surrogate (the multi-fidelity route to cheaper
+    physics guidance, Sec. 7): the W2 potential of the problem coarsened by
+    two in space and time (api.coarse_problem; about 8x fewer cell-updates),
+    evaluated at R v with the observations decimated to the coarse
+    acquisition, its gradient returned to the fine grid through R^T."""
+
+    def __init__(self, plan: api.Plan, d_obs: torch.Tensor, w2: api.W2Params | None = None):
+        self.fine = plan.prob
+        self.plan = api.Plan(api.coarse_problem(plan.prob), w2 or plan.w2p, device=plan.device)
+        self.ctx = self.plan.w2_prepare(api.fwi_decimate2(d_obs))
+
+    def gradient(self, v_phys: torch.Tensor, stream=None):
+        """(J_c(R v) [B], R^T dJ_c/dv_c [B][nz][nx])."""
+        vc = api.fwi_restrict2(v_phys, stream=stream)
+        J, gc, _ = self.plan.gradient(vc, self.ctx, stream=stream)
+        return J, api.fwi_restrict2_transpose(gc, self.fine.nz, self.fine.nx, stream=stream)
+
+
 class Sampler:
     """Algorithm 2 (``guide`` = GuideParams) or Algorithm 1 (``dps_zeta``) on
     a plan of B models.
 
     potential: "w2" (J of Eq. final_objective; needs ``ctx`` from
     plan.w2_prepare), "l2" (Phi_l2 with ``d_obs`` and ``sigma_l2``) or None
-    (no guidance: v_{i-1} = v').  Exactly one of ``prior`` and ``score_fn``."""
+    (no guidance: v_{i-1} = v').  Exactly one of ``prior`` and ``score_fn``.
+    surrogate: a LowFidelity W2 potential used instead of the full one in the
+    first ``surrogate_fraction`` of the reverse steps (i > N - round(fraction
+    N)), the full physics after."""
 
     def __init__(self, plan: api.Plan, betas: Sequence[float], *, potential: str | None = "w2",
                  ctx=None, d_obs=None, sigma_l2: float = 1.0, prior: GaussianPrior | None = None,
                  score_fn: Callable | None = None, guide: api.GuideParams | None = None,
                  dps_zeta: float | None = None,
                  space: api.DiffusionSpace = api.DiffusionSpace(),
-                 sigma_mode: int = api.SIGMA_POSTERIOR):
+                 sigma_mode: int = api.SIGMA_POSTERIOR, surrogate: LowFidelity | None = None,
+                 surrogate_fraction: float = 0.4):
         if (prior is None) == (score_fn is None):
             raise ValueError("give exactly one of prior and score_fn")
         if potential not in ("w2", "l2", None):
@@ -87,9 +111,16 @@ class Sampler:
             raise ValueError("the l2 potential needs d_obs")
         if potential is not None and (guide is None) == (dps_zeta is None):
             raise ValueError("give exactly one of guide (Algorithm 2) and dps_zeta (Algorithm 1)")
+        if surrogate is not None and potential != "w2":
+            raise ValueError("the low-fidelity surrogate stands in for the W2 potential")
+        if not 0.0 <= surrogate_fraction <= 1.0:
+            raise ValueError("surrogate_fraction must lie in [0, 1]")
         self.plan, self.potential, self.ctx, self.d_obs = plan, potential, ctx, d_obs
         self.sigma_l2, self.prior, self.score_fn, self.space = sigma_l2, prior, score_fn, space
         self.N = len(betas)
+        self.surrogate = surrogate
+        # reverse steps i > i_switch use the surrogate (the first fraction of them)
+        self.i_switch = self.N - int(round(surrogate_fraction * self.N)) if surrogate else self.N
         self.steps = [None] + [api.fwi_ddpm_coefficients(betas, i, sigma_mode)
                                for i in range(1, self.N + 1)]
         if dps_zeta is not None:
@@ -105,7 +136,12 @@ class Sampler:
         new = lambda: torch.empty((B, nz, nx), dtype=torch.float32, device=dev)  # noqa: E731
         self.v0hat, self.v_prime, self.v_phys, self.g, self.h = (new() for _ in range(5))
 
-    def _physics_gradient(self, stream):
+    def uses_surrogate(self, i: int) -> bool:
+        return self.surrogate is not None and i > self.i_switch
+
+    def _physics_gradient(self, i, stream):
+        if self.uses_surrogate(i):
+            return self.surrogate.gradient(self.v_phys, stream)
         if self.potential == "w2":
             J, g_phys, _ = self.plan.gradient(self.v_phys, self.ctx, stream=stream)
         else:
@@ -139,7 +175,7 @@ class Sampler:
         if self.potential is None:
             v_out.copy_(self.v_prime)
             return v_out, {"J": None, "rho": None}
-        J, g_phys = self._physics_gradient(stream)
+        J, g_phys = self._physics_gradient(i, stream)
         if vjp is None:
             api.fwi_ddpm_guidance(self.B, self.ncell, st, self.space, self.v0hat, g_phys, None,
                                   tau2, self.g, self.h, stream)

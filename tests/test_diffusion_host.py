@@ -106,3 +106,30 @@ def test_conv_rejects_bad_arguments_without_a_gpu(api):
     for k, call in enumerate(calls):
         assert call() == 1, k
         assert api.fwi_last_error() != ""
+
+
+def test_grid_transfers_reject_bad_arguments_without_a_gpu(api):
+    lib = api._lib
+    p = ctypes.c_void_p(4096)
+    calls = [
+        lambda: lib.fwi_restrict2(0, 4, 4, p, p, None),
+        lambda: lib.fwi_restrict2(1, 4, 4, None, p, None),
+        lambda: lib.fwi_restrict2_transpose(1, 0, 4, p, p, None),
+        lambda: lib.fwi_restrict2_transpose(1, 4, 4, p, None, None),
+        lambda: lib.fwi_decimate2(1, 1, 1, 1, p, p, None),
+        lambda: lib.fwi_decimate2(1, 1, 2, 4, None, p, None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == 1, k
+        assert api.fwi_last_error() != ""
+
+
+def test_coarse_problem_of_the_benchmark(api):
+    prob = api.Problem(nz=70, nx=70, nb=40, nt=1000, dz=10.0, dx=10.0, dt=1e-3,
+                       src_iz=(0,) * 5, src_ix=(0, 17, 34, 52, 69), rec_iz=(0,) * 70,
+                       rec_ix=tuple(range(70)), batch=4)
+    c = api.coarse_problem(prob)
+    assert (c.nz, c.nx, c.nb, c.nt, c.dx, c.dz, c.dt) == (35, 35, 20, 500, 20.0, 20.0, 2e-3)
+    assert list(c.src_ix) == [0, 8, 17, 26, 34] and len(c.rec_ix) == 35
+    assert list(c.rec_ix) == list(range(35))
+    api.fwi_plan_create(c, api.W2Params())     # a valid plan (CFL bound unchanged)

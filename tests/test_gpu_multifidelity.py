@@ -1,0 +1,119 @@
+"""GPU parity of the low-fidelity guidance surrogate: the grid transfers
+against the oracle (bit-exact where the arithmetic allows), the surrogate's
+W2 gradient against the oracle's, and Algorithm 2 switching from the
+surrogate to the full physics after the first 40% of the reverse steps."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_cases import TOL_GRAD, TOL_J, models, problems, rel_l2  # noqa: E402
+from oracle import diffusion as D  # noqa: E402
+from oracle import multifidelity as M  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_16393_gb300 import api as A
+    from paper_2603_16393_gb300 import sampler as S
+    return A, S
+
+
+def T(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device=DEV)
+
+
+def H(t):
+    return t.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("B,nz,nx", [(3, 70, 70), (2, 33, 17), (1, 1, 5)])
+def test_transfers_match_oracle(mods, B, nz, nx):
+    A, _ = mods
+    rng = np.random.default_rng(nz + nx)
+    v = rng.standard_normal((B, nz, nx)).astype(np.float32).astype(np.float64)
+    vc = H(A.fwi_restrict2(T(v)))
+    # at most four float32 additions and a division: a few roundings of the
+    # block's magnitude (the mean itself may cancel to near zero)
+    assert np.all(np.abs(vc - M.restrict(v)) <= 2.0 ** -21 * M.restrict(np.abs(v)))
+    nzc, nxc = M.coarse_shape(nz, nx)
+    gc = rng.standard_normal((B, nzc, nxc)).astype(np.float32).astype(np.float64)
+    # dividing a float by 1, 2 or 4 is exact in both precisions
+    np.testing.assert_array_equal(H(A.fwi_restrict2_transpose(T(gc), nz, nx)),
+                                  M.restrict_transpose(gc, nz, nx))
+
+
+@pytest.mark.parametrize("nr,nt", [(70, 1000), (5, 7), (1, 2)])
+def test_decimation_is_exact(mods, nr, nt):
+    A, _ = mods
+    d = np.random.default_rng(nr * nt).standard_normal((2, 3, nr, nt)).astype(np.float32)
+    np.testing.assert_array_equal(H(A.fwi_decimate2(T(d))), M.decimate(d.astype(np.float64)))
+
+
+def test_coarse_problem_matches_oracle(mods):
+    A, _ = mods
+    gp, op = problems(70, 70, 40, 1000, 5, batch=2)
+    cg, co = A.coarse_problem(gp), M.coarse_problem(op)
+    for f in ("nz", "nx", "nb", "nt", "dz", "dx", "dt"):
+        assert getattr(cg, f) == getattr(co, f), f
+    for f in ("src_iz", "src_ix", "rec_iz", "rec_ix"):
+        assert list(getattr(cg, f)) == list(getattr(co, f)), f
+
+
+def test_surrogate_gradient_matches_oracle(mods):
+    A, S = mods
+    B, nz, nx = 2, 32, 32
+    gp, op = problems(nz, nx, 12, 400, 2, batch=B, f_peak=15.0)
+    vt = models("layered", [0, 1], nz, nx)
+    v = models("layered", [5, 6], nz, nx) * 0.9 + 250.0
+    d_obs = O.forward(op, vt)
+    w2p = O.W2Params()
+    J_o, g_o = M.surrogate_potential(op, d_obs, w2p)(v)
+    with A.Plan(gp) as plan:
+        lf = S.LowFidelity(plan, T(d_obs))
+        assert lf.plan.model_shape == (B, 16, 16)
+        J, g = lf.gradient(T(v))
+        torch.cuda.synchronize()
+        lf.plan.check()
+    assert rel_l2(H(J), J_o) <= TOL_J
+    assert rel_l2(H(g), g_o) <= TOL_GRAD
+
+
+def test_algorithm2_switches_from_the_surrogate(mods):
+    A, S = mods
+    B, nz, nx = 2, 32, 32
+    gp, op = problems(nz, nx, 12, 400, 2, batch=B, f_peak=15.0)
+    vt = models("layered", [0, 1], nz, nx)
+    d_obs = O.forward(op, vt)
+    fam = models("layered", list(range(20, 36)), nz, nx)
+    mu = ((fam.mean(axis=0) - D.SHIFT) / D.UNIT).astype(np.float32).astype(np.float64)
+    tau2 = np.full((nz, nx), 0.05)
+    betas = D.linear_betas(1000)
+    sched = D.Schedule(betas)
+    gparams_o = O.GuideParams(rho0=2.0, gamma=0.5)
+    with A.Plan(gp) as plan:
+        ctx = plan.w2_prepare(T(d_obs))
+        smp = S.Sampler(plan, betas, ctx=ctx, prior=S.GaussianPrior(T(mu), T(tau2)),
+                        guide=A.GuideParams(rho0=2.0, gamma=0.5),
+                        surrogate=S.LowFidelity(plan, T(d_obs)), surrogate_fraction=0.4)
+        assert smp.uses_surrogate(601) and not smp.uses_surrogate(600)
+        assert smp.uses_surrogate(1000) and not smp.uses_surrogate(1)
+        rng = np.random.default_rng(3)
+        for i, pot in ((700, M.surrogate_potential(op, d_obs, O.W2Params())),
+                       (500, D.w2_potential(op, O.w2_prepare(d_obs, op.dt, O.W2Params()),
+                                            O.W2Params()))):
+            ab = sched.abar[i]
+            v = (np.sqrt(ab) * mu + np.sqrt(1 - ab) * rng.standard_normal((B, nz, nx)))
+            v = v.astype(np.float32).astype(np.float64)
+            z = rng.standard_normal((B, nz, nx)).astype(np.float32).astype(np.float64)
+            _, info = smp.step(T(v), i, T(z))
+            torch.cuda.synchronize()
+            _, inter = D.reverse_step(sched, i, v, z, pot, mu, tau2, gparams_o)
+            assert rel_l2(H(info["J"]), inter["J"]) <= TOL_J, i
+            assert rel_l2(H(smp.h), inter["h"]) <= TOL_GRAD, i

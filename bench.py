@@ -614,8 +614,12 @@ def run_sampler(args, rank, world, local_rank):
                                         device=dev)
     betas = S.linear_betas(1000)
     frac = args.surrogate_fraction
+    net = None
+    if args.score == "conv":
+        from paper_2603_16393_gb300 import score_net as SN
+        net = SN.ConvScore((B, nz, nx), betas, device=dev)
     lowfi = S.LowFidelity(plan, d_obs) if frac > 0 else None
-    smp = S.Sampler(plan, betas, ctx=ctx, prior=prior,
+    smp = S.Sampler(plan, betas, ctx=ctx, prior=None if net else prior, score_fn=net,
                     guide=api.GuideParams(rho0=1.15, gamma=0.55), surrogate=lowfi,
                     surrogate_fraction=frac if frac > 0 else 0.4)
     total = args.warmup + args.steps
@@ -705,6 +709,13 @@ def run_sampler(args, rank, world, local_rank):
         smp.v_phys))
     t_guid = per_launch(lambda: api.fwi_ddpm_guidance(
         B, nz * nx, st, smp.space, smp.v0hat, smp.g, None, prior.tau2, bufs[0], smp.h))
+    net_ms = None
+    if net is not None:
+        # the score network alone: eps and its vector-Jacobian product
+        def net_step():
+            net(v, i0)
+            net.eps_vjp(smp.g, 1.0)
+        net_ms = per_launch(net_step)
     if rank != 0:
         return
     by_prop, by_guid = 20 * n + 8 * nz * nx, 16 * n + 4 * nz * nx
@@ -725,6 +736,10 @@ def run_sampler(args, rank, world, local_rank):
                                "rule, preconditioned update",
                    "batch_per_gpu": B,
                    "l2": "inputs larger than L2 (wavefield record 10 GB per step)",
+                   "score": ("3-layer 64-channel convolutional noise-prediction network on the "
+                             "tensor cores (seeded weights)" if net else "Gaussian prior fitted "
+                             "to 64 seeded models"),
+                   "score_network_ms_per_step": net_ms,
                    "surrogate_fraction": frac,
                    "ms_per_step_full_physics": ms,
                    "ms_per_step_low_fidelity": ms_sur,
@@ -849,6 +864,8 @@ def main():
     ap.add_argument("--conv", action="store_true",
                     help="the tensor-core 3x3 convolution of a score-model layer "
                          "(152 x 70x70, 128 -> 128 channels, bf16)")
+    ap.add_argument("--score", choices=["prior", "conv"], default="prior",
+                    help="--sampler: the score model (Gaussian prior or a convolutional network)")
     ap.add_argument("--surrogate-fraction", type=float, default=0.0,
                     help="--sampler: low-fidelity guidance (2x coarser grid and time step) in "
                          "this fraction of the first reverse steps")

@@ -391,6 +391,31 @@ FWI_API fwi_status fwi_group_gradient(fwi_group *group, const float *const *v,
  * (FWI_OK, FWI_ERR_UNSTABLE_CFL, FWI_ERR_DEVICE_TIMEOUT), then clear it. */
 FWI_API fwi_status fwi_check(const fwi_plan *plan, void *workspace, void *stream);
 
+/* ---------------------------------------------------------------- convolutional score model
+ * Elementwise pieces of a convolutional score model built on
+ * fwi_conv3x3_bf16: s(x, i) = -eps(x) / sqrt(1 - abar_i) from a
+ * noise-prediction network eps (Sec. 3.4), and its vector-Jacobian product
+ * for Eq. chain_rule.  Activations are NHWC bf16 with `channels` channels per
+ * pixel; npix = B nz nx.  Errors: FWI_ERR_INVALID_ARG before any launch,
+ * FWI_ERR_CUDA. */
+
+/* X[p][0] = bf16(scale x[p]), X[p][c] = 0 for c >= 1; x [npix] fp32, X
+ * [npix][channels] bf16 (16-byte aligned, channels a multiple of 8). */
+FWI_API fwi_status fwi_pack_channel0(long long npix, int channels, float scale, const float *x,
+                                     void *X, void *stream);
+
+/* y[p] = scale Y[p][0]; Y [npix][channels] fp32, y [npix] fp32. */
+FWI_API fwi_status fwi_unpack_channel0(long long npix, int channels, float scale, const float *Y,
+                                       float *y, void *stream);
+
+/* A = bf16(silu(P)), silu(p) = p / (1 + e^-p); P, A [n] bf16 (may alias). */
+FWI_API fwi_status fwi_silu_bf16(long long n, const void *P, void *A, void *stream);
+
+/* dP = bf16(dA silu'(P)), silu'(p) = sg (1 + p (1 - sg)), sg = 1 / (1 + e^-p);
+ * dA, P, dP [n] bf16 (dP may alias dA). */
+FWI_API fwi_status fwi_silu_grad_bf16(long long n, const void *dA, const void *P, void *dP,
+                                      void *stream);
+
 /* ---------------------------------------------------------------- low-fidelity guidance
  * Grid transfers of the low-fidelity guidance surrogate (the multi-fidelity
  * route to cheaper physics guidance, Sec. 7): the W2 potential of the problem

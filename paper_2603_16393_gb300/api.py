@@ -137,6 +137,15 @@ _lib.fwi_restrict2_transpose.restype = _S
 _lib.fwi_restrict2_transpose.argtypes = [ctypes.c_int] * 3 + [_vp] * 3
 _lib.fwi_decimate2.restype = _S
 _lib.fwi_decimate2.argtypes = [ctypes.c_int] * 4 + [_vp] * 3
+_lib.fwi_pack_channel0.restype = _S
+_lib.fwi_pack_channel0.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_float, _vp, _vp, _vp]
+_lib.fwi_unpack_channel0.restype = _S
+_lib.fwi_unpack_channel0.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_float, _vp, _vp,
+                                     _vp]
+_lib.fwi_silu_bf16.restype = _S
+_lib.fwi_silu_bf16.argtypes = [ctypes.c_longlong, _vp, _vp, _vp]
+_lib.fwi_silu_grad_bf16.restype = _S
+_lib.fwi_silu_grad_bf16.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp]
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -499,6 +508,35 @@ def coarse_problem(prob: Problem) -> Problem:
         src_iz=[int(z) // 2 for z in prob.src_iz], src_ix=[int(x) // 2 for x in prob.src_ix],
         rec_iz=[r[0] for r in rec], rec_ix=[r[1] for r in rec],
         checkpoint_every=(prob.checkpoint_every + 1) // 2 if prob.checkpoint_every else 0)
+
+
+def fwi_pack_channel0(x, X, scale=1.0, stream=None):
+    """X[..., 0] = bf16(scale x), other channels 0 (x [B][nz][nx] fp32, X [B][nz][nx][C] bf16)."""
+    if X.dtype != torch.bfloat16 or tuple(X.shape[:-1]) != tuple(x.shape):
+        raise ValueError("X must be bfloat16 of shape x.shape + (C,)")
+    _f32(x, tuple(x.shape), "x")
+    _check(_lib.fwi_pack_channel0(x.numel(), X.shape[-1], ctypes.c_float(scale), _ptr(x), _ptr(X),
+                                  _stream(stream)))
+
+
+def fwi_unpack_channel0(Y, y, scale=1.0, stream=None):
+    """y = scale Y[..., 0] (Y [B][nz][nx][C] fp32, y [B][nz][nx] fp32)."""
+    _f32(Y, tuple(Y.shape), "Y")
+    _f32(y, tuple(Y.shape[:-1]), "y")
+    _check(_lib.fwi_unpack_channel0(y.numel(), Y.shape[-1], ctypes.c_float(scale), _ptr(Y),
+                                    _ptr(y), _stream(stream)))
+
+
+def fwi_silu_bf16(P, A, stream=None):
+    if P.dtype != torch.bfloat16 or A.dtype != torch.bfloat16 or P.shape != A.shape:
+        raise ValueError("P and A must be bfloat16 tensors of one shape")
+    _check(_lib.fwi_silu_bf16(P.numel(), _ptr(P), _ptr(A), _stream(stream)))
+
+
+def fwi_silu_grad_bf16(dA, P, dP, stream=None):
+    if not (dA.dtype == P.dtype == dP.dtype == torch.bfloat16) or not (dA.shape == P.shape == dP.shape):
+        raise ValueError("dA, P and dP must be bfloat16 tensors of one shape")
+    _check(_lib.fwi_silu_grad_bf16(P.numel(), _ptr(dA), _ptr(P), _ptr(dP), _stream(stream)))
 
 
 def fwi_check(plan, workspace, stream=None):

@@ -1,0 +1,112 @@
+"""GPU parity of the convolutional score model (``score_net.ConvScore``) on
+the tensor-core convolution: the elementwise kernels, the network's eps and
+its vector-Jacobian product against the FP64 oracle with the same bf16
+storage points, and Algorithm 2 driven by it."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_cases import problems, rel_l2  # noqa: E402
+from oracle import diffusion as D  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+from oracle import score_net as N  # noqa: E402
+
+DEV = "cuda:0"
+# one bf16 ulp (2^-8 relative) where the FP32-accumulated and the FP64 value
+# round differently, at each of the network's storage points
+BF16_ULP = 2.0 ** -8
+
+
+@pytest.fixture(scope="module")
+def mods():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_16393_gb300 import api as A
+    from paper_2603_16393_gb300 import sampler as S
+    from paper_2603_16393_gb300 import score_net as SN
+    return A, S, SN
+
+
+def T(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device=DEV)
+
+
+def H(t):
+    return t.double().cpu().numpy()
+
+
+def test_elementwise_kernels(mods):
+    A, _, _ = mods
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, 5, 7)).astype(np.float32)
+    X = torch.full((2, 5, 7, 64), 7.0, dtype=torch.bfloat16, device=DEV)
+    A.fwi_pack_channel0(T(x), X, 0.5)
+    Xh = X.float().cpu().numpy()
+    np.testing.assert_array_equal(Xh[..., 0], N.bf16(0.5 * x.astype(np.float64)))
+    assert np.all(Xh[..., 1:] == 0)
+    Y = T(rng.standard_normal((2, 5, 7, 64)))
+    y = torch.empty((2, 5, 7), device=DEV)
+    A.fwi_unpack_channel0(Y, y, -3.0)
+    np.testing.assert_array_equal(H(y), (-3.0 * Y[..., 0].cpu().numpy()).astype(np.float64))
+    p = torch.tensor(8 * rng.standard_normal(4096), dtype=torch.float32).to(torch.bfloat16)
+    da = torch.tensor(rng.standard_normal(4096), dtype=torch.float32).to(torch.bfloat16)
+    a, dp = torch.empty_like(p, device=DEV), torch.empty_like(p, device=DEV)
+    A.fwi_silu_bf16(p.to(DEV), a)
+    A.fwi_silu_grad_bf16(da.to(DEV), p.to(DEV), dp)
+    ph, dah = p.double().numpy(), da.double().numpy()
+    for got, ref in ((a, N.bf16(N.silu(ph))), (dp, N.bf16(dah * N.silu_grad(ph)))):
+        err = np.abs(got.double().cpu().numpy() - ref)
+        assert np.all(err <= BF16_ULP * np.abs(ref) + 1e-30)
+
+
+def test_network_and_vjp_match_oracle(mods):
+    A, _, SN = mods
+    B, nz, nx = 2, 33, 47
+    betas = D.linear_betas(1000)
+    w = SN.seeded_weights(64, 3, seed=4)
+    net = SN.ConvScore((B, nz, nx), betas, weights=w)
+    ref = N.ConvScore(w, round_bf16=True)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal((B, nz, nx)).astype(np.float32).astype(np.float64)
+    g = rng.standard_normal((B, nz, nx)).astype(np.float32).astype(np.float64)
+    i = 300
+    ab = D.Schedule(betas).abar[i]
+    s, vjp = net(T(x), i)
+    u = vjp(T(g))
+    torch.cuda.synchronize()
+    s_o = ref.score(x, ab)
+    u_o = ref.score_vjp(g, ab)
+    bound = 5 * BF16_ULP      # 2 (L - 1) + 1 storage points on either path
+    assert rel_l2(H(s), s_o) <= bound, rel_l2(H(s), s_o)
+    assert rel_l2(H(u), u_o) <= bound, rel_l2(H(u), u_o)
+    # an unrounded FP64 network is farther than the bf16 twin: the bf16
+    # storage points, not the tensor cores, set the difference
+    exact = N.ConvScore(w, round_bf16=False)
+    assert rel_l2(H(s), exact.score(x, ab)) < 0.1
+
+
+def test_algorithm2_with_the_convolutional_score(mods):
+    A, S, SN = mods
+    from gpu_cases import models
+    B, nz, nx = 2, 32, 32
+    gp, op = problems(nz, nx, 12, 300, 2, batch=B, f_peak=25.0)
+    d_obs = O.forward(op, models("layered", [0, 1], nz, nx))
+    betas = D.linear_betas(1000)
+    with A.Plan(gp) as plan:
+        ctx = plan.w2_prepare(T(d_obs))
+        net = SN.ConvScore(plan.model_shape, betas)
+        smp = S.Sampler(plan, betas, ctx=ctx, score_fn=net, guide=A.GuideParams(rho0=1.0))
+        rng = np.random.default_rng(6)
+        v = T(rng.standard_normal((B, nz, nx)) * 0.3)
+        i = 250
+        v_next, info = smp.step(v, i, T(rng.standard_normal((B, nz, nx))))
+        torch.cuda.synchronize()
+        plan.check()
+        # the step used the network: h = (g + (1 - abar) (ds/dv)^T g) / sqrt(abar)
+        ab = smp.steps[i].abar
+        u = net.eps_vjp(smp.g, -1.0 / np.sqrt(1 - ab))
+        h_ref = (H(smp.g) + (1 - ab) * H(u)) / np.sqrt(ab)
+        assert rel_l2(H(smp.h), h_ref) <= 1e-6
+        assert torch.isfinite(v_next).all() and torch.isfinite(info["J"]).all()

@@ -34,22 +34,38 @@ def silu_grad(p):
     return sg * (1.0 + p * (1.0 - sg))
 
 
+def time_features(i: int, dim: int = 16):
+    """[sin(i w_k), cos(i w_k)], w_k = 10000^(-k / (dim/2)): the step's embedding."""
+    k = np.arange(dim // 2, dtype=np.float64)
+    w = 10000.0 ** (-k / (dim // 2))
+    return np.concatenate([np.sin(i * w), np.cos(i * w)])
+
+
 class ConvScore:
+    """weights: [(W [C][3][3][C], b [C], E [C][dim])]; layer l's bias at step i
+    is b_l + E_l phi(i), rounded to float32 as the kernels receive it."""
+
     def __init__(self, weights, round_bf16: bool = True):
         self.r = bf16 if round_bf16 else (lambda a: np.asarray(a, np.float64))
-        self.W = [self.r(w) for w, _ in weights]
-        self.b = [np.asarray(b, np.float64) for _, b in weights]
+        self.W = [self.r(w) for w, _, _ in weights]
+        self.b = [np.asarray(b, np.float64) for _, b, _ in weights]
+        self.E = [np.asarray(e, np.float64) for _, _, e in weights]
+        self.f32 = round_bf16
         self.Cn = self.W[0].shape[0]
 
-    def eps(self, x):
-        """eps(x) for x [B][nz][nx]; keeps the pre-activations for vjp."""
+    def bias(self, l, i):
+        b = self.b[l] + self.E[l] @ time_features(i, self.E[l].shape[1])
+        return b.astype(np.float32).astype(np.float64) if self.f32 else b
+
+    def eps(self, x, i=0):
+        """eps(x, i) for x [B][nz][nx]; keeps the pre-activations for vjp."""
         x = np.asarray(x, np.float64)
         h = np.zeros(x.shape + (self.Cn,))
         h[..., 0] = self.r(x)
         self.P = []
         L = len(self.W)
         for l in range(L):
-            p = C.conv3x3(h, self.W[l], self.b[l])
+            p = C.conv3x3(h, self.W[l], self.bias(l, i))
             if l < L - 1:
                 p = self.r(p)
                 self.P.append(p)
@@ -71,8 +87,8 @@ class ConvScore:
                 d = self.r(self.r(d) * silu_grad(self.P[l - 1]))
         return d[..., 0]
 
-    def score(self, x, abar):
-        return -self.eps(x) / np.sqrt(1.0 - abar)
+    def score(self, x, abar, i=0):
+        return -self.eps(x, i) / np.sqrt(1.0 - abar)
 
     def score_vjp(self, g, abar):
         return self.eps_vjp(g, -1.0 / np.sqrt(1.0 - abar))

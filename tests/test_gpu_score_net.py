@@ -76,7 +76,7 @@ def test_network_and_vjp_match_oracle(mods):
     s, vjp = net(T(x), i)
     u = vjp(T(g))
     torch.cuda.synchronize()
-    s_o = ref.score(x, ab)
+    s_o = ref.score(x, ab, i)
     u_o = ref.score_vjp(g, ab)
     bound = 5 * BF16_ULP      # 2 (L - 1) + 1 storage points on either path
     assert rel_l2(H(s), s_o) <= bound, rel_l2(H(s), s_o)
@@ -84,7 +84,11 @@ def test_network_and_vjp_match_oracle(mods):
     # an unrounded FP64 network is farther than the bf16 twin: the bf16
     # storage points, not the tensor cores, set the difference
     exact = N.ConvScore(w, round_bf16=False)
-    assert rel_l2(H(s), exact.score(x, ab)) < 0.1
+    assert rel_l2(H(s), exact.score(x, ab, i)) < 0.1
+    # the step enters through the biases: another step, another score
+    s2, _ = net(T(x), 700)
+    assert rel_l2(H(s2) * np.sqrt(1 - D.Schedule(betas).abar[700]),
+                  H(s) * np.sqrt(1 - ab)) > 1e-3
 
 
 def test_algorithm2_with_the_convolutional_score(mods):

@@ -11,8 +11,8 @@ from oracle import score_net as N
 
 def _weights(seed=0, c=8, layers=3):
     rng = np.random.default_rng(seed)
-    return [(rng.standard_normal((c, 3, 3, c)) / np.sqrt(9 * c), 0.1 * rng.standard_normal(c))
-            for _ in range(layers)]
+    return [(rng.standard_normal((c, 3, 3, c)) / np.sqrt(9 * c), 0.1 * rng.standard_normal(c),
+             0.1 * rng.standard_normal((c, 16))) for _ in range(layers)]
 
 
 def test_vjp_matches_central_differences():
@@ -20,7 +20,8 @@ def test_vjp_matches_central_differences():
     rng = np.random.default_rng(1)
     x = rng.standard_normal((1, 6, 7))
     g = rng.standard_normal((1, 6, 7))
-    net.eps(x)
+    step = 321
+    net.eps(x, step)
     u = net.eps_vjp(g)
     e = 1e-6
     fd = np.zeros_like(x)
@@ -28,8 +29,18 @@ def test_vjp_matches_central_differences():
         for j in range(7):
             d = np.zeros_like(x)
             d[0, i, j] = e
-            fd[0, i, j] = (np.vdot(net.eps(x + d), g) - np.vdot(net.eps(x - d), g)) / (2 * e)
+            fd[0, i, j] = (np.vdot(net.eps(x + d, step), g) -
+                           np.vdot(net.eps(x - d, step), g)) / (2 * e)
     assert np.linalg.norm(fd - u) <= 1e-7 * np.linalg.norm(fd)
+
+
+def test_time_features_closed_form():
+    f = N.time_features(0)
+    np.testing.assert_array_equal(f, [0.0] * 8 + [1.0] * 8)
+    f = N.time_features(7)
+    assert f[0] == np.sin(7.0) and f[8] == np.cos(7.0)              # w_0 = 1
+    np.testing.assert_allclose(f[:8] ** 2 + f[8:] ** 2, 1.0, rtol=0, atol=1e-15)
+    assert abs(f[7] - np.sin(7 * 10000.0 ** (-7 / 8))) < 1e-15
 
 
 def test_transposed_convolution_is_the_adjoint():

@@ -830,11 +830,16 @@ def run_conv(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic (seeded normal)",
         "config": {"workload": f"{n} x 70x70 x {c} -> {c}, 3x3, stride 1, zero padding",
                    "l2": f"inputs larger than L2 (x and y {n * h * w * c * 2 / 1e6:.0f} MB each)",
-                   "tiles": f"128 pixels (8 x 16) x {min(c, 256) if c % 256 == 0 else (128 if c % 128 == 0 else 64)} channels per tile, one persistent CTA "
-                            "per SM; 15 % of the MMA rows fall outside the 70 x 70 images and "
+                   "tiles": ("192 pixels (8 x 24) as the MMA's N x 128 channels as its M per "
+                             "tile; 6 % of the pixels fall outside the 70 x 70 images"
+                             if c % 256 != 0 and c % 128 == 0 else
+                             f"128 pixels (8 x 16) as the MMA's M x {256 if c % 256 == 0 else 64} "
+                             "channels as its N per tile; 15 % of the pixels fall outside the "
+                             "70 x 70 images") + "; one persistent CTA per SM; outside pixels "
                             "are not credited"},
         "roofline": {"bound": "tensor",
-                     "kernel": f"k_conv3x3_tc<{256 if c % 256 == 0 else (128 if c % 128 == 0 else 64)}>",
+                     "kernel": ("k_conv3x3_tc<256>" if c % 256 == 0 else
+                                "k_conv3x3_tc_pn" if c % 128 == 0 else "k_conv3x3_tc<64>"),
                      "achieved": tf,
                      "peak": peak, "unit": "TFLOP/s", "frac": tf / peak, "peak_source": src,
                      "hbm_gb_s": byts / (ms * 1e-3) / 1e9, "algorithmic_bytes": byts},

@@ -420,6 +420,201 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && *vfailed && a.status) atomicExch(a.status, (int)FWI_ERR_DEVICE_TIMEOUT);
 }
 
+// ---------------------------------------------------------------------------
+// Pixels-as-N variant for 128-channel output blocks whose width is not a
+// multiple of 256: the MMA's rate per SM grows with N, so the roles swap --
+// M = 128 output channels (the weight block, operand A), N = 192 output
+// pixels (an 8 x 24 tile, operand B: the tap views of a 10 x 26 halo box,
+// 24 groups of 8 rows 1280 bytes apart).  The accumulator holds channels in
+// its lanes and pixels in its columns, so an epilogue warp (one lane quarter =
+// 32 channels, a quarter of the 192 columns) stores 32 consecutive channels
+// of a pixel per instruction.  Producer, MMA issuer, rings, double
+// accumulators and bounded waits as in k_conv3x3_tc.
+constexpr int kPW = 8, kPH = 24, kPN = kPW * kPH;          // 192 output pixels per tile
+constexpr int kPHX = kPW + 2, kPHY = kPH + 2;               // halo box 10 x 26
+constexpr int kPHaloTx = kPHX * kPHY * kBK * 2;             // 33,280 bytes
+constexpr int kPHaloBytes = (kPHaloTx + 1023) / 1024 * 1024;
+constexpr int kPM = 128;                                    // output channels per tile
+constexpr int kPWBytes = kPM * kBK * 2;                     // 16 KB weight block
+constexpr int kPWStages = 8;
+constexpr uint32_t kPTmemCols = 512;                        // two 192-column accumulators
+
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ Tile tile_of_pn(int t, const ConvArgs &a)
+{
+    Tile r;
+    const int cbk = t / a.tiles;
+    t -= cbk * a.tiles;
+    const int tx = t % a.tiles_x;
+    t /= a.tiles_x;
+    const int ty = t % a.tiles_y;
+    r.img = t / a.tiles_y;
+    r.x0 = tx * kPW;
+    r.y0 = ty * kPH;
+    r.n0 = cbk * kPM;
+    return r;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv3x3_tc_pn(const __grid_constant__ CUtensorMap tmx,
+                    const __grid_constant__ CUtensorMap tmw, const ConvArgs a)
+{
+    constexpr uint32_t kIdesc = idesc_bf16_mn(kPM, kPN);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char *sX = base;                              // kAStages halo boxes (operand B)
+    unsigned char *sW = base + kAStages * kPHaloBytes;     // kPWStages weight blocks (operand A)
+    __shared__ uint64_t x_full[kAStages], x_empty[kAStages], w_full[kPWStages], w_empty[kPWStages];
+    __shared__ uint64_t acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    volatile int *vfailed = &failed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cbs = a.cin / kBK;
+    const int total = a.tiles * (a.cout / kPM);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kAStages; ++s) {
+            mb_init(&x_full[s], 1);
+            mb_init(&x_empty[s], 1);
+        }
+        for (int s = 0; s < kPWStages; ++s) {
+            mb_init(&w_full[s], 1);
+            mb_init(&w_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mb_init(&acc_full[b], 1);
+            mb_init(&acc_empty[b], kEpiWarps);
+        }
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&tmem_slot)),
+                     "r"(kPTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int gx = 0, gw = 0;
+            for (int t = blockIdx.x; t < total && !*vfailed; t += gridDim.x) {
+                const Tile tl = tile_of_pn(t, a);
+                for (int cb = 0; cb < cbs && !*vfailed; ++cb) {
+                    const int sx = gx % kAStages, rx = gx / kAStages;
+                    if (rx > 0 && !mb_wait(&x_empty[sx], (unsigned)((rx - 1) & 1), vfailed)) break;
+                    mb_expect(&x_full[sx], kPHaloTx);
+                    tma_4d(sX + sx * kPHaloBytes, &tmx, cb * kBK, tl.x0 - 1, tl.y0 - 1, tl.img,
+                           &x_full[sx]);
+                    ++gx;
+                    for (int tap = 0; tap < 9; ++tap, ++gw) {
+                        const int sw = gw % kPWStages, rw = gw / kPWStages;
+                        if (rw > 0 && !mb_wait(&w_empty[sw], (unsigned)((rw - 1) & 1), vfailed))
+                            break;
+                        mb_expect(&w_full[sw], kPWBytes);
+                        tma_2d(sW + sw * kPWBytes, &tmw, tap * a.cin + cb * kBK, tl.n0, &w_full[sw]);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int gx = 0, gw = 0, it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok && !*vfailed; t += gridDim.x, ++it) {
+                const int b = it & 1, u = it >> 1;
+                if (u > 0 && !mb_wait(&acc_empty[b], (unsigned)((u - 1) & 1), vfailed)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * 256);
+                for (int cb = 0; cb < cbs && ok; ++cb, ++gx) {
+                    const int sx = gx % kAStages, rx = gx / kAStages;
+                    if (!mb_wait(&x_full[sx], (unsigned)(rx & 1), vfailed)) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned char *halo = sX + sx * kPHaloBytes;
+                    for (int tap = 0; tap < 9; ++tap, ++gw) {
+                        const int sw = gw % kPWStages, rw = gw / kPWStages;
+                        if (!mb_wait(&w_full[sw], (unsigned)(rw & 1), vfailed)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int row = (tap / 3) * kPHX + tap % 3;   // (dy + 1) 10 + dx + 1
+                        const uint64_t ad = sw128_desc(sW + sw * kPWBytes, 1024);
+                        const uint64_t bd = sw128_desc(halo + row * 128, kPHX * 128);
+#pragma unroll
+                        for (int k = 0; k < kBK / 16; ++k)
+                            umma_bf16(d, ad + 2 * k, bd + 2 * k, kIdesc, (cb | tap | k) != 0);
+                        umma_commit(&w_empty[sw]);
+                    }
+                    if (ok) umma_commit(&x_empty[sx]);
+                }
+                if (ok) umma_commit(&acc_full[b]);
+            }
+        }
+    } else {
+        // epilogue warps 2..17: lane quarter q = 32 output channels, and a
+        // quarter of the 192 pixel columns
+        const int q = warp & 3;
+        const int part = (warp - 2) >> 2;
+        const int cbeg = part * (kPN / 4), cend = cbeg + kPN / 4;
+        int it = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
+            const int b = it & 1, u = it >> 1;
+            if (!mb_wait(&acc_full[b], (unsigned)(u & 1), vfailed)) break;
+            tc_fence_after();
+            const Tile tl = tile_of_pn(t, a);
+            const int co = tl.n0 + q * 32 + lane;
+            const float bias = a.bias ? __ldg(a.bias + co) : 0.f;
+#pragma unroll 1
+            for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256 + c0), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int m = c0 + j;
+                    const int px = tl.x0 + (m % kPW), py = tl.y0 + m / kPW;
+                    if (px >= a.w || py >= a.h) continue;
+                    const size_t pix = ((size_t)tl.img * a.h + py) * a.w + px;
+                    const float x = v[j] + bias;
+                    const float yv = a.act == 1 ? silu(x) : x;
+                    if (a.y_bf16)
+                        static_cast<__nv_bfloat16 *>(a.y)[pix * a.cout + co] = __float2bfloat16_rn(yv);
+                    else
+                        static_cast<float *>(a.y)[pix * a.cout + co] = yv;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mb_arrive(&acc_empty[b]);
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kPTmemCols)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *vfailed && a.status) atomicExch(a.status, (int)FWI_ERR_DEVICE_TIMEOUT);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -460,6 +655,23 @@ cudaError_t launch_conv(const CUtensorMap &tmx, const CUtensorMap &tmw, const Co
     return cudaGetLastError();
 }
 
+cudaError_t launch_conv_pn(const CUtensorMap &tmx, const CUtensorMap &tmw, const ConvArgs &a,
+                           cudaStream_t st)
+{
+    const size_t smem = (size_t)kAStages * kPHaloBytes + (size_t)kPWStages * kPWBytes + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc_pn,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const long long total = (long long)a.tiles * (a.cout / kPM);
+    const unsigned grid = (unsigned)(total < sms ? total : sms);
+    k_conv3x3_tc_pn<<<grid, kThreads, smem, st>>>(tmx, tmw, a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -480,7 +692,10 @@ fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *
     if (!x || !wt || !y) return fwi::record_error(FWI_ERR_INVALID_ARG, "x, w and y must not be NULL");
     if (((uintptr_t)x | (uintptr_t)wt | (uintptr_t)y) & 15)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "x, w and y must be 16-byte aligned");
-    const int tiles_x = (w + kTW - 1) / kTW, tiles_y = (h + kTH - 1) / kTH;
+    // 128-channel blocks (cout not a multiple of 256) run pixels-as-N
+    const bool pn = cout % 256 != 0 && cout % 128 == 0;
+    const int TW = pn ? kPW : kTW, TH = pn ? kPH : kTH;
+    const int tiles_x = (w + TW - 1) / TW, tiles_y = (h + TH - 1) / TH;
     if ((size_t)n * tiles_y * tiles_x * (cout / 64) > 0x7fffffffull ||
         (size_t)9 * cin > 0x7fffffffull ||
         (size_t)n * h * w > ((size_t)1 << 40))
@@ -493,7 +708,8 @@ fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *
         const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
         const cuuint64_t strides[3] = {(cuuint64_t)cin * 2, (cuuint64_t)w * cin * 2,
                                        (cuuint64_t)h * w * cin * 2};
-        const cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)kHX, (cuuint32_t)kHY, 1};
+        const cuuint32_t box[4] = {(cuuint32_t)kBK, (cuuint32_t)(pn ? kPHX : kHX),
+                                   (cuuint32_t)(pn ? kPHY : kHY), 1};
         const cuuint32_t estr[4] = {1, 1, 1, 1};
         if (enc(&tmx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(x), dims, strides,
                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -515,7 +731,8 @@ fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *
     ConvArgs a{n, h, w, cin, cout, act, y_bf16, tiles_x, tiles_y, n * tiles_y * tiles_x,
                bias, y, status};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const cudaError_t e = BN == 256 ? launch_conv<256>(tmx, tmw, a, st)
+    const cudaError_t e = pn          ? launch_conv_pn(tmx, tmw, a, st)
+                        : BN == 256 ? launch_conv<256>(tmx, tmw, a, st)
                         : BN == 128 ? launch_conv<128>(tmx, tmw, a, st)
                                     : launch_conv<64>(tmx, tmw, a, st);
     if (e != cudaSuccess)

@@ -51,6 +51,7 @@ def bound(x, w, y_ref, cin, out_bf16, act):
     (1, 9, 20, 192, 192, 0, True, True),       # 64-channel blocks (192 = 3 x 64), bf16 output
     (1, 1, 1, 64, 64, 0, False, False),        # one pixel: the centre tap only
     (3, 64, 64, 64, 128, 1, True, False),      # tiles cover the image exactly
+    (1, 9, 20, 128, 384, 1, True, True),       # three 128-channel blocks, pixels as the MMA's N
     (1, 21, 19, 256, 256, 1, True, True),      # 256-channel blocks (the widest MMA)
     (2, 16, 24, 64, 512, 0, True, False),      # two 256-channel blocks from 64 input channels
 ])

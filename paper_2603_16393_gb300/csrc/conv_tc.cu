@@ -8,7 +8,9 @@
 // N = BN output channels (256, 128 or 64: the largest that divides cout), K =
 // 9 taps x cin.  Layouts: x NHWC bf16, w [cout][3][3][cin] bf16 (K-major), y
 // NHWC fp32 or bf16.  The MMA rate per SM grows with N: 1.50 PFLOP/s at
-// N = 256 (a 256 -> 256 layer), 0.76 at N = 128 (128 -> 128), 152 x 70 x 70.
+// N = 256 (a 256 -> 256 layer), 0.76 at N = 128 (128 -> 128), 152 x 70 x 70;
+// 128-channel blocks therefore run k_conv3x3_tc_pn below, pixels as N = 192
+// (1.03 PFLOP/s on the 128 -> 128 layer).
 //
 // Operand A comes from one halo box per 64-channel block: the 10 x 18 pixels
 // around the tile (a 4D cp.async.bulk.tensor load, 128-byte swizzled, one

@@ -736,7 +736,7 @@ def run_sampler(args, rank, world, local_rank):
                                "rule, preconditioned update",
                    "batch_per_gpu": B,
                    "l2": "inputs larger than L2 (wavefield record 10 GB per step)",
-                   "score": ("3-layer 64-channel convolutional noise-prediction network on the "
+                   "score": ("3-layer 128-channel convolutional noise-prediction network on the "
                              "tensor cores (seeded weights)" if net else "Gaussian prior fitted "
                              "to 64 seeded models"),
                    "score_network_ms_per_step": net_ms,

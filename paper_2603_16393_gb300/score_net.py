@@ -35,7 +35,7 @@ def time_features(i: int, dim: int = TIME_DIM) -> np.ndarray:
     return np.concatenate([np.sin(i * w), np.cos(i * w)])
 
 
-def seeded_weights(channels: int = 64, layers: int = 3, seed: int = 0):
+def seeded_weights(channels: int = 128, layers: int = 3, seed: int = 0):
     """[(W [C][3][3][C], b [C], E [C][TIME_DIM])] float32 with zero-mean normal
     entries: W of variance 1/(9 C) (1/9 for the first layer, whose input is one
     channel), b and the time projection E of standard deviation 0.1."""
@@ -54,10 +54,10 @@ class ConvScore:
     """Callable score model (v_i, i) -> (s, vjp) for the Sampler."""
 
     def __init__(self, model_shape: Sequence[int], betas: Sequence[float], weights=None,
-                 channels: int = 64, layers: int = 3, seed: int = 0, device=None):
+                 channels: int = 128, layers: int = 3, seed: int = 0, device=None):
         B, nz, nx = model_shape
         self.shape = (B, nz, nx)
-        self.C = channels
+        self.C = weights[0][0].shape[0] if weights is not None else channels
         self.dev = torch.device(device) if device is not None else torch.device("cuda")
         weights = weights if weights is not None else seeded_weights(channels, layers, seed)
         self.L = len(weights)
@@ -75,7 +75,7 @@ class ConvScore:
             # per-step biases b + E phi(i) for every i, formed once in FP64
             bi = np.asarray(b, np.float64)[None, :] + phi @ np.asarray(e, np.float64).T
             self.bias.append(torch.as_tensor(bi.astype(np.float32)).to(self.dev))
-        act = (B, nz, nx, channels)
+        act = (B, nz, nx, self.C)
         bf = dict(dtype=torch.bfloat16, device=self.dev)
         self.X0 = torch.empty(act, **bf)
         self.P = [torch.empty(act, **bf) for _ in range(self.L - 1)]   # pre-activations

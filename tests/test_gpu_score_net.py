@@ -61,11 +61,12 @@ def test_elementwise_kernels(mods):
         assert np.all(err <= BF16_ULP * np.abs(ref) + 1e-30)
 
 
-def test_network_and_vjp_match_oracle(mods):
+@pytest.mark.parametrize("channels", [64, 128])
+def test_network_and_vjp_match_oracle(mods, channels):
     A, _, SN = mods
     B, nz, nx = 2, 33, 47
     betas = D.linear_betas(1000)
-    w = SN.seeded_weights(64, 3, seed=4)
+    w = SN.seeded_weights(channels, 3, seed=4)
     net = SN.ConvScore((B, nz, nx), betas, weights=w)
     ref = N.ConvScore(w, round_bf16=True)
     rng = np.random.default_rng(5)

@@ -54,7 +54,7 @@ extern "C" {
 #define FWI_API
 #endif
 
-/* Limits of this build. */
+/* Limits of this library. */
 #define FWI_MAX_SHOTS 256
 #define FWI_MAX_RECEIVERS 1024
 
@@ -64,7 +64,7 @@ typedef enum fwi_status {
     FWI_ERR_UNSTABLE_CFL = 2,   /* v_max dt sqrt(1/dx^2+1/dz^2) > sqrt(3)/2, or a
                                    velocity above v_max / not positive was found
                                    on the device                                   */
-    FWI_ERR_UNSUPPORTED = 3,    /* valid but outside what this build implements */
+    FWI_ERR_UNSUPPORTED = 3,    /* valid but outside what this library implements */
     FWI_ERR_CUDA = 4,           /* a CUDA runtime call or launch failed         */
     FWI_ERR_DEVICE_TIMEOUT = 5, /* a device-side wait ran out of its budget     */
     FWI_ERR_OOM = 6             /* a caller buffer is too small                 */
@@ -164,7 +164,7 @@ typedef struct fwi_plan fwi_plan;   /* opaque, host memory only */
  * Checks every field above, the CFL bound for v_max (v_max dt sqrt(1/dx^2 +
  * 1/dz^2) <= 2 / sqrt(lambda), lambda the largest symbol of the 1D stencil:
  * 16/3 at 4th order (bound sqrt(3)/2), 6.5016 at 8th order (bound 0.7844)),
- * that sources and receivers lie on the physical grid, and that this build
+ * that sources and receivers lie on the physical grid, and that this library
  * can run the grid (FWI_ERR_UNSUPPORTED otherwise).  *out receives the plan
  * or NULL.  Errors: FWI_ERR_INVALID_ARG, FWI_ERR_UNSTABLE_CFL,
  * FWI_ERR_UNSUPPORTED. */

@@ -701,7 +701,7 @@ fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *
     if ((size_t)n * tiles_y * tiles_x * (cout / 64) > 0x7fffffffull ||
         (size_t)9 * cin > 0x7fffffffull ||
         (size_t)n * h * w > ((size_t)1 << 40))
-        return fwi::record_error(FWI_ERR_UNSUPPORTED, "tensor too large for this build");
+        return fwi::record_error(FWI_ERR_UNSUPPORTED, "tensor too large for this library");
     auto enc = tmap_encoder();
     if (!enc) return fwi::record_error(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     const int BN = cout % 256 == 0 ? 256 : (cout % 128 == 0 ? 128 : 64);

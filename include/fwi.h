@@ -416,6 +416,18 @@ FWI_API fwi_status fwi_silu_bf16(long long n, const void *P, void *A, void *stre
 FWI_API fwi_status fwi_silu_grad_bf16(long long n, const void *dA, const void *P, void *dP,
                                       void *stream);
 
+/* Self-check of the convolution's bounded waits (failure detection without a
+ * fault): the same launch as fwi_conv3x3_bf16 with the weight blocks never
+ * loaded and a wait bound of 20 ms, so that every device-side wait runs out.
+ * The kernel then waits (bounded) for the input copies it started, releases
+ * its tensor memory, writes nothing to y and sets *status (device int, not
+ * NULL) to FWI_ERR_DEVICE_TIMEOUT; the device stays usable.  Arguments as for
+ * fwi_conv3x3_bf16.  Errors: as fwi_conv3x3_bf16, FWI_ERR_INVALID_ARG for a
+ * NULL status. */
+FWI_API fwi_status fwi_conv3x3_bf16_wait_check(int n, int h, int w, int cin, int cout,
+                                               const void *x, const void *wt, void *y, int y_bf16,
+                                               int *status, void *stream);
+
 /* ---------------------------------------------------------------- low-fidelity guidance
  * Grid transfers of the low-fidelity guidance surrogate (the multi-fidelity
  * route to cheaper physics guidance, Sec. 7): the W2 potential of the problem

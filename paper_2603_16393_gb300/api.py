@@ -146,6 +146,9 @@ _lib.fwi_silu_bf16.restype = _S
 _lib.fwi_silu_bf16.argtypes = [ctypes.c_longlong, _vp, _vp, _vp]
 _lib.fwi_silu_grad_bf16.restype = _S
 _lib.fwi_silu_grad_bf16.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp]
+_lib.fwi_conv3x3_bf16_wait_check.restype = _S
+_lib.fwi_conv3x3_bf16_wait_check.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, ctypes.c_int,
+                                                                  _vp, _vp]
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -451,6 +454,15 @@ def fwi_conv3x3_bf16(x, wt, bias, act, y, status=None, stream=None):
     _check(_lib.fwi_conv3x3_bf16(n, h, w, cin, cout, _ptr(x), _ptr(wt), _ptr(bias), int(act),
                                  _ptr(y), int(y.dtype == torch.bfloat16), _ptr(status),
                                  _stream(stream)))
+
+
+def fwi_conv3x3_bf16_wait_check(x, wt, y, status, stream=None):
+    """The convolution's bounded-wait self-check (see include/fwi.h): sets
+    status[0] to FWI_ERR_DEVICE_TIMEOUT and leaves y unwritten."""
+    n, h, w, cin = x.shape
+    _check(_lib.fwi_conv3x3_bf16_wait_check(n, h, w, cin, wt.shape[0], _ptr(x), _ptr(wt),
+                                            _ptr(y), int(y.dtype == torch.bfloat16),
+                                            _ptr(status), _stream(stream)))
 
 
 def conv3x3(x, wt, bias=None, act=0, out_dtype=torch.float32, status=None, stream=None):

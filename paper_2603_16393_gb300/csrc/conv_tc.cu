@@ -65,8 +65,11 @@ template <int BN> __host__ __device__ constexpr int b_stages() { return BN == 25
 constexpr int kThreads = 576;                        // producer, MMA, sixteen epilogue warps
 constexpr int kEpiWarps = 16;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bound of one mbarrier wait: 2 s
+constexpr unsigned long long kCheckWaitNs = 20000000ull; // the wait self-check: 20 ms
 
 struct ConvArgs {
+    unsigned long long wait_ns;    // bound of one mbarrier wait
+    int withhold;                  // 1: never load the weight blocks (the wait self-check)
     int n, h, w, cin, cout;
     int act;       // 0: none, 1: SiLU
     int y_bf16;    // output type: 0 fp32, 1 bf16
@@ -106,20 +109,34 @@ __device__ __forceinline__ unsigned long long now_ns()
 }
 
 // Waits for the completion of the barrier phase of the given parity; false
-// once *failed is set or after kWaitNs (then it sets *failed).
-__device__ __forceinline__ bool mb_wait(uint64_t *b, unsigned parity, volatile int *failed)
+// once *failed is set (failed may be NULL) or after limit_ns (then it sets
+// *failed).
+__device__ __forceinline__ bool mb_wait(uint64_t *b, unsigned parity, volatile int *failed,
+                                        unsigned long long limit_ns)
 {
     if (mb_try(b, parity)) return true;
     const unsigned long long t0 = now_ns();
     for (;;) {
         for (int i = 0; i < 256; ++i)
             if (mb_try(b, parity)) return true;
-        if (*failed) return false;
-        if (now_ns() - t0 > kWaitNs) {
-            *failed = 1;
+        if (failed && *failed) return false;
+        if (now_ns() - t0 > limit_ns) {
+            if (failed) *failed = 1;
             return false;
         }
     }
+}
+
+// After a failed wait the producer waits (bounded) for the loads it issued
+// into each stage, so that no copy still writes into this CTA's shared memory
+// when it exits: stage s last received load number last[s] (-1: none), whose
+// full barrier completes phase last[s] / stages.
+template <int S>
+__device__ __forceinline__ void drain_loads(uint64_t *full, const int (&last)[S],
+                                            unsigned long long limit_ns)
+{
+    for (int s = 0; s < S; ++s)
+        if (last[s] >= 0) mb_wait(&full[s], (unsigned)((last[s] / S) & 1), nullptr, limit_ns);
 }
 
 __device__ __forceinline__ void mb_arrive(uint64_t *b)
@@ -300,23 +317,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             // TMA producer, in the MMAs' order: per tile and channel block the
             // halo box, then the nine weight blocks of that channel block
             int ga = 0, gb = 0;
+            int last_a[kAStages], last_b[kBStages];
+            for (int s = 0; s < kAStages; ++s) last_a[s] = -1;
+            for (int s = 0; s < kBStages; ++s) last_b[s] = -1;
             for (int t = blockIdx.x; t < total && !*vfailed; t += gridDim.x) {
                 const Tile tl = tile_of(t, a, BN);
                 for (int cb = 0; cb < cbs && !*vfailed; ++cb) {
                     const int sa = ga % kAStages, ra = ga / kAStages;
-                    if (ra > 0 && !mb_wait(&a_empty[sa], (unsigned)((ra - 1) & 1), vfailed)) break;
+                    if (ra > 0 && !mb_wait(&a_empty[sa], (unsigned)((ra - 1) & 1), vfailed, a.wait_ns)) break;
                     mb_expect(&a_full[sa], kHaloTx);
                     tma_4d(sA + sa * kHaloBytes, &tmx, cb * kBK, tl.x0 - 1, tl.y0 - 1, tl.img,
                            &a_full[sa]);
-                    ++ga;
+                    last_a[sa] = ga++;
                     for (int tap = 0; tap < 9; ++tap, ++gb) {
                         const int sb = gb % kBStages, rb = gb / kBStages;
-                        if (rb > 0 && !mb_wait(&b_empty[sb], (unsigned)((rb - 1) & 1), vfailed))
+                        if (rb > 0 && !mb_wait(&b_empty[sb], (unsigned)((rb - 1) & 1), vfailed, a.wait_ns))
                             break;
+                        if (a.withhold) continue;
                         mb_expect(&b_full[sb], kBBytes);
                         tma_2d(sB + sb * kBBytes, &tmw, tap * a.cin + cb * kBK, tl.n0, &b_full[sb]);
+                        last_b[sb] = gb;
                     }
                 }
+            }
+            if (*vfailed) {
+                drain_loads(a_full, last_a, a.wait_ns);
+                drain_loads(b_full, last_b, a.wait_ns);
             }
         }
     } else if (warp == 1) {
@@ -329,19 +355,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok && !*vfailed; t += gridDim.x, ++it) {
                 const int b = it & 1, u = it >> 1;
-                if (u > 0 && !mb_wait(&acc_empty[b], (unsigned)((u - 1) & 1), vfailed)) break;
+                if (u > 0 && !mb_wait(&acc_empty[b], (unsigned)((u - 1) & 1), vfailed, a.wait_ns)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * BN);
                 for (int cb = 0; cb < cbs && ok; ++cb, ++ga) {
                     const int sa = ga % kAStages, ra = ga / kAStages;
-                    if (!mb_wait(&a_full[sa], (unsigned)(ra & 1), vfailed)) {
+                    if (!mb_wait(&a_full[sa], (unsigned)(ra & 1), vfailed, a.wait_ns)) {
                         ok = false;
                         break;
                     }
                     const unsigned char *halo = sA + sa * kHaloBytes;
                     for (int tap = 0; tap < 9; ++tap, ++gb) {
                         const int sb = gb % kBStages, rb = gb / kBStages;
-                        if (!mb_wait(&b_full[sb], (unsigned)(rb & 1), vfailed)) {
+                        if (!mb_wait(&b_full[sb], (unsigned)(rb & 1), vfailed, a.wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -370,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int it = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
             const int b = it & 1, u = it >> 1;
-            if (!mb_wait(&acc_full[b], (unsigned)(u & 1), vfailed)) break;
+            if (!mb_wait(&acc_full[b], (unsigned)(u & 1), vfailed, a.wait_ns)) break;
             tc_fence_after();
             const Tile tl = tile_of(t, a, BN);
             const int px = tl.x0 + (m % kTW), py = tl.y0 + m / kTW;
@@ -513,23 +539,32 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             int gx = 0, gw = 0;
+            int last_x[kAStages], last_w[kPWStages];
+            for (int s = 0; s < kAStages; ++s) last_x[s] = -1;
+            for (int s = 0; s < kPWStages; ++s) last_w[s] = -1;
             for (int t = blockIdx.x; t < total && !*vfailed; t += gridDim.x) {
                 const Tile tl = tile_of_pn(t, a);
                 for (int cb = 0; cb < cbs && !*vfailed; ++cb) {
                     const int sx = gx % kAStages, rx = gx / kAStages;
-                    if (rx > 0 && !mb_wait(&x_empty[sx], (unsigned)((rx - 1) & 1), vfailed)) break;
+                    if (rx > 0 && !mb_wait(&x_empty[sx], (unsigned)((rx - 1) & 1), vfailed, a.wait_ns)) break;
                     mb_expect(&x_full[sx], kPHaloTx);
                     tma_4d(sX + sx * kPHaloBytes, &tmx, cb * kBK, tl.x0 - 1, tl.y0 - 1, tl.img,
                            &x_full[sx]);
-                    ++gx;
+                    last_x[sx] = gx++;
                     for (int tap = 0; tap < 9; ++tap, ++gw) {
                         const int sw = gw % kPWStages, rw = gw / kPWStages;
-                        if (rw > 0 && !mb_wait(&w_empty[sw], (unsigned)((rw - 1) & 1), vfailed))
+                        if (rw > 0 && !mb_wait(&w_empty[sw], (unsigned)((rw - 1) & 1), vfailed, a.wait_ns))
                             break;
+                        if (a.withhold) continue;
                         mb_expect(&w_full[sw], kPWBytes);
                         tma_2d(sW + sw * kPWBytes, &tmw, tap * a.cin + cb * kBK, tl.n0, &w_full[sw]);
+                        last_w[sw] = gw;
                     }
                 }
+            }
+            if (*vfailed) {
+                drain_loads(x_full, last_x, a.wait_ns);
+                drain_loads(w_full, last_w, a.wait_ns);
             }
         }
     } else if (warp == 1) {
@@ -538,19 +573,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < total && ok && !*vfailed; t += gridDim.x, ++it) {
                 const int b = it & 1, u = it >> 1;
-                if (u > 0 && !mb_wait(&acc_empty[b], (unsigned)((u - 1) & 1), vfailed)) break;
+                if (u > 0 && !mb_wait(&acc_empty[b], (unsigned)((u - 1) & 1), vfailed, a.wait_ns)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * 256);
                 for (int cb = 0; cb < cbs && ok; ++cb, ++gx) {
                     const int sx = gx % kAStages, rx = gx / kAStages;
-                    if (!mb_wait(&x_full[sx], (unsigned)(rx & 1), vfailed)) {
+                    if (!mb_wait(&x_full[sx], (unsigned)(rx & 1), vfailed, a.wait_ns)) {
                         ok = false;
                         break;
                     }
                     const unsigned char *halo = sX + sx * kPHaloBytes;
                     for (int tap = 0; tap < 9; ++tap, ++gw) {
                         const int sw = gw % kPWStages, rw = gw / kPWStages;
-                        if (!mb_wait(&w_full[sw], (unsigned)(rw & 1), vfailed)) {
+                        if (!mb_wait(&w_full[sw], (unsigned)(rw & 1), vfailed, a.wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -577,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int it = 0;
         for (int t = blockIdx.x; t < total; t += gridDim.x, ++it) {
             const int b = it & 1, u = it >> 1;
-            if (!mb_wait(&acc_full[b], (unsigned)(u & 1), vfailed)) break;
+            if (!mb_wait(&acc_full[b], (unsigned)(u & 1), vfailed, a.wait_ns)) break;
             tc_fence_after();
             const Tile tl = tile_of_pn(t, a);
             const int co = tl.n0 + q * 32 + lane;
@@ -678,9 +713,13 @@ cudaError_t launch_conv_pn(const CUtensorMap &tmx, const CUtensorMap &tmw, const
 
 extern "C" {
 
-fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *x, const void *wt,
-                            const float *bias, int act, void *y, int y_bf16, int *status,
-                            void *stream)
+}  // extern "C"
+
+namespace {
+
+fwi_status conv_call(int n, int h, int w, int cin, int cout, const void *x, const void *wt,
+                     const float *bias, int act, void *y, int y_bf16, int *status, void *stream,
+                     int withhold, unsigned long long wait_ns)
 {
     if (n < 1 || h < 1 || w < 1)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "n, h, w must be >= 1");
@@ -730,8 +769,8 @@ fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return fwi::record_error(FWI_ERR_CUDA, "tensor map of w rejected");
     }
-    ConvArgs a{n, h, w, cin, cout, act, y_bf16, tiles_x, tiles_y, n * tiles_y * tiles_x,
-               bias, y, status};
+    ConvArgs a{wait_ns, withhold, n, h, w, cin, cout, act, y_bf16, tiles_x, tiles_y,
+               n * tiles_y * tiles_x, bias, y, status};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const cudaError_t e = pn          ? launch_conv_pn(tmx, tmw, a, st)
                         : BN == 256 ? launch_conv<256>(tmx, tmw, a, st)
@@ -740,6 +779,27 @@ fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *
     if (e != cudaSuccess)
         return fwi::record_error(FWI_ERR_CUDA, "fwi_conv3x3_bf16 launch: %s", cudaGetErrorString(e));
     return FWI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *x, const void *wt,
+                            const float *bias, int act, void *y, int y_bf16, int *status,
+                            void *stream)
+{
+    return conv_call(n, h, w, cin, cout, x, wt, bias, act, y, y_bf16, status, stream, 0, kWaitNs);
+}
+
+fwi_status fwi_conv3x3_bf16_wait_check(int n, int h, int w, int cin, int cout, const void *x,
+                                       const void *wt, void *y, int y_bf16, int *status,
+                                       void *stream)
+{
+    if (!status)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "the wait check needs a status word");
+    return conv_call(n, h, w, cin, cout, x, wt, nullptr, 0, y, y_bf16, status, stream, 1,
+                     kCheckWaitNs);
 }
 
 }  // extern "C"

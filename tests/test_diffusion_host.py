@@ -133,3 +133,9 @@ def test_coarse_problem_of_the_benchmark(api):
     assert list(c.src_ix) == [0, 8, 17, 26, 34] and len(c.rec_ix) == 35
     assert list(c.rec_ix) == list(range(35))
     api.fwi_plan_create(c, api.W2Params())     # a valid plan (CFL bound unchanged)
+
+
+def test_conv_wait_check_needs_a_status_word(api):
+    p = ctypes.c_void_p(4096)
+    assert api._lib.fwi_conv3x3_bf16_wait_check(1, 4, 4, 64, 64, p, p, p, 0, None, None) == 1
+    assert "status" in api.fwi_last_error()

@@ -91,3 +91,23 @@ def test_conv_benchmark_launch_sampled(api):
         lim = 1.1 * 9 * c * 2.0 ** -23 * s + 2.0 ** -8 * np.abs(ref[k]) + 1e-30
         assert np.all(np.abs(got[k] - ref[k]) <= lim), (k, float((np.abs(got[k] - ref[k]) / lim).max()))
     assert np.isfinite(yh).all()
+
+
+@pytest.mark.parametrize("cout", [64, 128, 256])
+def test_bounded_waits_report_a_timeout_and_leave_the_device_usable(api, cout):
+    # failure detection without a fault: the self-check launch never loads
+    # the weights, every device-side wait runs out (20 ms), the kernel drains
+    # its own copies, frees its tensor memory and reports the timeout
+    x, wt, b, xo, wo, bo = bf16_inputs(9, 1, 20, 24, 128, cout)
+    y = torch.full((1, 20, 24, cout), 7.0, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    api.fwi_conv3x3_bf16_wait_check(x, wt, y, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == api.FWI_ERR_DEVICE_TIMEOUT
+    assert bool((y == 7.0).all())
+    status.zero_()
+    y2 = api.conv3x3(x, wt, b, 0, torch.float32, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = C.conv3x3(xo, wo, bo)
+    assert np.all(np.abs(y2.double().cpu().numpy() - ref) <= bound(xo, wo, ref, 128, False, 0))

@@ -7,8 +7,7 @@ surrogate idea in Sec. 7):
 
 with x read as 0 outside the image and act the identity or SiLU v/(1 + e^-v).
 
-TEST INFRASTRUCTURE ONLY: imported by ``tests/`` and by ``bench.py``'s CPU
-baseline; never by the product path.  numpy in float64: the definition
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``; never by the product path.  numpy in float64: the definition
 written out, one tap at a time, each tap a matrix product over channels.
 """
 from __future__ import annotations

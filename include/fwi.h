@@ -209,6 +209,17 @@ FWI_API fwi_status fwi_plan_kernels(const fwi_plan *plan, int *family);
 FWI_API fwi_status fwi_forward(const fwi_plan *plan, const float *v, float *d_syn,
                        float *snapshots, void *workspace, void *stream);
 
+/* Self-check of the cluster kernels' bounded halo waits (failure detection
+ * without a fault): fwi_forward on a plan that runs FWI_KERNELS_CLUSTER, with
+ * every halo row withheld and each wait bounded by 20 ms, so that the waits run
+ * out.  The kernels finish (their outputs are not meaningful) and the status
+ * word in the workspace reads FWI_ERR_DEVICE_TIMEOUT, which fwi_check()
+ * returns; the device stays usable.  Arguments as fwi_forward.  Errors:
+ * FWI_ERR_INVALID_ARG, FWI_ERR_UNSUPPORTED for plans of other families,
+ * FWI_ERR_CUDA. */
+FWI_API fwi_status fwi_forward_wait_check(const fwi_plan *plan, const float *v, float *d_syn,
+                                          float *snapshots, void *workspace, void *stream);
+
 /* Observation-only part of the misfit for B observed data cubes
  * (Sec. 5.1 (I)-(III), Sec. 6.2):
  *   M = max_{s,r,t} |d_obs|, omega = 1/(1 + k |d_obs| / M)      (Eq. omega_def)

@@ -149,6 +149,8 @@ _lib.fwi_silu_grad_bf16.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp]
 _lib.fwi_conv3x3_bf16_wait_check.restype = _S
 _lib.fwi_conv3x3_bf16_wait_check.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, ctypes.c_int,
                                                                   _vp, _vp]
+_lib.fwi_forward_wait_check.restype = _S
+_lib.fwi_forward_wait_check.argtypes = [_vp] * 6
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -367,6 +369,12 @@ def fwi_plan_kernels(plan: _Handle) -> int:
 def fwi_forward(plan, v, d_syn, snapshots, workspace, stream=None):
     _check(_lib.fwi_forward(plan.raw, _ptr(v), _ptr(d_syn), _ptr(snapshots), _ptr(workspace),
                             _stream(stream)))
+
+
+def fwi_forward_wait_check(plan, v, d_syn, snapshots, workspace, stream=None):
+    """The cluster kernels' bounded-wait self-check (see include/fwi.h)."""
+    _check(_lib.fwi_forward_wait_check(plan.raw, _ptr(v), _ptr(d_syn), _ptr(snapshots),
+                                       _ptr(workspace), _stream(stream)))
 
 
 def fwi_w2_prepare(plan, d_obs, obs_ctx, stream=None):

@@ -280,7 +280,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
                 }
         if (ok) {
             pl->cluster = true;
-            pl->clu = fwi::ClusterArgs{P, C, RC, RS, nstrip, pl->NXp, 0, nullptr, nullptr};
+            pl->clu = fwi::ClusterArgs{P, C, RC, RS, nstrip, pl->NXp, 0, nullptr, nullptr, 0, 0ull};
             pl->clu_threads = threads;
             pl->clu_chunk_fwd = chunk[0];
             pl->clu_chunk_adj = chunk[1];
@@ -446,6 +446,24 @@ fwi_status fwi_forward(const fwi_plan *plan, const float *v, float *d_syn, float
         e = fwi::launch_forward(pl, v, d_syn, snapshots, workspace, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "fwi_forward launch");
+    return FWI_OK;
+}
+
+fwi_status fwi_forward_wait_check(const fwi_plan *plan, const float *v, float *d_syn,
+                                  float *snapshots, void *workspace, void *stream)
+{
+    if (!plan || !v || !d_syn || !workspace)
+        return fail(FWI_ERR_INVALID_ARG, "plan, v, d_syn and workspace must not be NULL");
+    const Plan &pl = *as_plan(plan);
+    if (!pl.cluster)
+        return fail(FWI_ERR_UNSUPPORTED, "the wait self-check runs the cluster kernels only");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_forward_wait_check status reset");
+    fwi::Window w;
+    w.wait_check = true;
+    e = fwi::launch_forward(pl, v, d_syn, snapshots, workspace, st, w);
+    if (e != cudaSuccess) return cuda_fail(e, "fwi_forward_wait_check launch");
     return FWI_OK;
 }
 

@@ -58,6 +58,8 @@ struct ClusterArgs {
     int chunk;      // staged time steps
     float *acc;     // adjoint: imaging sums [bs][NZ][NXp] (to the fold)
     float *acc_src; // adjoint: source-cell sums [bs]
+    int withhold;   // 1: send no halo rows (the bounded-wait self-check)
+    unsigned long long wait_ns;   // bound of one halo wait
 };
 
 struct Plan {
@@ -155,6 +157,7 @@ struct Window {
     float *ckpt = nullptr;
     int ckpt_every = 0;
     float *astate = nullptr, *asrc = nullptr;
+    bool wait_check = false;              // cluster kernels: withhold the halo rows
 };
 
 // Launchers (return cudaGetLastError() of the launches they made).
@@ -190,7 +193,7 @@ cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_
 // one CTA, and the launch
 size_t cluster_smem(int RC, int P, bool adj, int chunk, int nr);
 cudaError_t launch_cluster(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
-                           cudaStream_t st);
+                           cudaStream_t st, bool wait_check = false);
 cudaError_t launch_tile_fold(const Plan &pl, const PropArgs &a, unsigned char *ws,
                              cudaStream_t st);
 // CPML propagators (absorber = FWI_ABSORBER_CPML): workspace bytes of their

@@ -451,7 +451,8 @@ cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *
     apply_window(a, w);
     if (pl.cpml) return launch_cpml(pl, false, a, static_cast<unsigned char *>(workspace), st);
     if (pl.cluster)
-        return launch_cluster(pl, false, a, static_cast<unsigned char *>(workspace), st);
+        return launch_cluster(pl, false, a, static_cast<unsigned char *>(workspace), st,
+                              w.wait_check);
     if (pl.tiled) return launch_tiled(pl, false, a, static_cast<unsigned char *>(workspace), st);
     if (pl.fast) {
         a.rows = pl.shape.rows;

@@ -139,3 +139,13 @@ def test_conv_wait_check_needs_a_status_word(api):
     p = ctypes.c_void_p(4096)
     assert api._lib.fwi_conv3x3_bf16_wait_check(1, 4, 4, 64, 64, p, p, p, 0, None, None) == 1
     assert "status" in api.fwi_last_error()
+
+
+def test_forward_wait_check_needs_a_cluster_plan(api):
+    prob = api.Problem(nz=70, nx=70, nb=40, nt=1000, dz=10.0, dx=10.0, dt=1e-3,
+                       src_iz=(0,) * 5, src_ix=(0, 17, 34, 52, 69), rec_iz=(0,) * 70,
+                       rec_ix=tuple(range(70)), batch=2)
+    h = api.fwi_plan_create(prob, api.W2Params())     # resident kernels
+    p = ctypes.c_void_p(4096)
+    assert api._lib.fwi_forward_wait_check(h.raw, p, p, p, p, None) == api.FWI_ERR_UNSUPPORTED
+    assert api._lib.fwi_forward_wait_check(None, p, p, p, p, None) == api.FWI_ERR_INVALID_ARG

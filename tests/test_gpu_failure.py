@@ -1,0 +1,46 @@
+"""Failure detection on the GPU without a fault: the cluster propagators'
+bounded halo waits run out under the self-check (every halo row withheld,
+20 ms per wait), the status word reports FWI_ERR_DEVICE_TIMEOUT through
+fwi_check, and the device stays usable: the next forward is exact."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_cases import TOL_DATA, models, rel_l2  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+from paper_2603_16393_gb300 import inputs as I  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_16393_gb300 import api as A
+    return A
+
+
+def test_cluster_halo_waits_time_out_and_recover(api):
+    nz, nx, nb, nt, ns, B = 64, 96, 20, 150, 2, 2
+    geo = I.surface_geometry(nx, ns)
+    kw = dict(nz=nz, nx=nx, nb=nb, nt=nt, dz=10.0, dx=10.0, dt=1e-3, src_iz=geo.src_iz,
+              src_ix=geo.src_ix, rec_iz=geo.rec_iz, rec_ix=geo.rec_ix, f_peak=20.0)
+    gp = api.Problem(**kw, batch=B, kernels=api.KERNELS_CLUSTER)
+    op = O.Problem(**kw)
+    v = models("layered", [1, 2], nz, nx)
+    with api.Plan(gp) as plan:
+        assert plan.kernels == api.KERNELS_CLUSTER
+        vt = torch.tensor(v, dtype=torch.float32, device=DEV)
+        d = torch.empty(plan.data_shape, dtype=torch.float32, device=DEV)
+        api.fwi_forward_wait_check(plan.handle, vt, d, plan.snapshots, plan.workspace)
+        torch.cuda.synchronize()
+        with pytest.raises(api.FwiError) as err:
+            plan.check()
+        assert err.value.code == api.FWI_ERR_DEVICE_TIMEOUT
+        d2, _ = plan.forward(vt)
+        torch.cuda.synchronize()
+        plan.check()
+    assert rel_l2(d2.double().cpu().numpy(), O.forward(op, v)) <= TOL_DATA

@@ -239,7 +239,11 @@ k_clu_fwd(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
             const int j = j0 + jj;
             const float *cur = (j & 1) ? U1 : U0;
             float *nxt = (j & 1) ? U0 : U1;
-            if (tid == 0 && j + 3 <= a.nt) halo_arm(&mb[(j + 3) & 3], halo_bytes);
+            // after a halo wait has run out (the flag only goes 0 -> 1) no phase
+            // is armed again: an arm by thread 0 implies its own wait for the
+            // barrier's previous phase (level j-1, two steps ago) succeeded
+            if (tid == 0 && j + 3 <= a.nt && !*(volatile int *)&failed)
+                halo_arm(&mb[(j + 3) & 3], halo_bytes);
             if (active) {
                 const float *cp = cur + (l0 + 2) * P + x + 2;
                 float *np = nxt + (l0 + 2) * P + x + 2;
@@ -285,14 +289,13 @@ k_clu_fwd(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
                     if (TOPBC == 1 && top_strip && (src_row == 1 || src_row == 2))
                         np[-src_row * P] += d;
                 }
-                if (!e.withhold)
+                // a CTA whose wait ran out sends no more halo rows, so that its
+                // neighbours' waits run out too, within a level or two
+                if (!e.withhold && !*(volatile int *)&failed)
                     send_edges<P, RS>(np, RC, crank, send_up, send_dn, &mb[(j + 1) & 3]);
             }
             if (STORE) sw += plane;
-            // the step's barrier; a halo wait that ran out (the flag is set
-            // only inside the waits) makes every thread leave the time loop
-            // here, together, before another mbarrier phase is armed
-            if (__syncthreads_or(*(volatile int *)&failed)) break;
+            __syncthreads();
             for (int i = tid; i < a.nr; i += nth) {
                 const int rz = a.rec_pz[i] - g0;
                 if (rz >= 0 && rz < RC) ST[jj * a.nr + i] = nxt[(rz + 2) * P + a.rec_px[i] + 2];
@@ -307,7 +310,7 @@ k_clu_fwd(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
             const int rz = a.rec_pz[i] - g0;
             if (rz >= 0 && rz < RC) db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
         }
-        if (__syncthreads_or(*(volatile int *)&failed)) break;
+        __syncthreads();
     }
     cl.sync();   // no CTA leaves while a neighbour may still write into it
 }
@@ -400,7 +403,11 @@ k_clu_adj(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
             const int j = j0 + jj;
             const float *cur = (j & 1) ? U1 : U0;
             float *nxt = (j & 1) ? U0 : U1;
-            if (tid == 0 && j + 3 <= a.nt) halo_arm(&mb[(j + 3) & 3], halo_bytes);
+            // after a halo wait has run out (the flag only goes 0 -> 1) no phase
+            // is armed again: an arm by thread 0 implies its own wait for the
+            // barrier's previous phase (level j-1, two steps ago) succeeded
+            if (tid == 0 && j + 3 <= a.nt && !*(volatile int *)&failed)
+                halo_arm(&mb[(j + 3) & 3], halo_bytes);
             if (inj_slot >= 0) nxt[inj_off] -= ST[jj * a.nr + inj_slot];   // (kappa/B) q
             if (j + 1 < a.nt) sr -= plane;
             if (active) {
@@ -433,17 +440,17 @@ k_clu_adj(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
                     w0 = wp1;
                     wp1 = wp2;
                 }
-                if (!e.withhold)
+                // a CTA whose wait ran out sends no more halo rows, so that its
+                // neighbours' waits run out too, within a level or two
+                if (!e.withhold && !*(volatile int *)&failed)
                     send_edges<P, RS>(np, RC, crank, send_up, send_dn, &mb[(j + 1) & 3]);
             }
-            // the step's barrier; leaves the time loop together after a halo
-            // wait ran out (see the forward)
-            if (__syncthreads_or(*(volatile int *)&failed)) break;
+            __syncthreads();
             if (tid == nth - 1 && src_here)
                 acc_src = fmaf(nxt[(sz - g0 + 2) * P + sx + 2], RSw[jj], acc_src);
             halo_wait(&mb[(j + 1) & 3], halo_parity(j + 1), &failed, a.status, e.wait_ns);
         }
-        if (__syncthreads_or(*(volatile int *)&failed)) break;
+        __syncthreads();
     }
     // imaging sums of this CTA's rows and the source-cell sum to the fold
     for (int i = tid; i < RC * NX; i += nth) {

@@ -209,9 +209,10 @@ FWI_API fwi_status fwi_plan_kernels(const fwi_plan *plan, int *family);
 FWI_API fwi_status fwi_forward(const fwi_plan *plan, const float *v, float *d_syn,
                        float *snapshots, void *workspace, void *stream);
 
-/* Self-check of the cluster kernels' bounded halo waits (failure detection
- * without a fault): fwi_forward on a plan that runs FWI_KERNELS_CLUSTER, with
- * every halo row withheld and each wait bounded by 20 ms, so that the waits run
+/* Self-check of the propagators' bounded waits (failure detection without a
+ * fault): fwi_forward on a plan that runs FWI_KERNELS_CLUSTER (every halo row
+ * withheld, each wait bounded by 20 ms) or FWI_KERNELS_TILED (no halo tile
+ * loaded, each wait bounded by 1024 mbarrier polls), so that the waits run
  * out.  The kernels finish (their outputs are not meaningful) and the status
  * word in the workspace reads FWI_ERR_DEVICE_TIMEOUT, which fwi_check()
  * returns; the device stays usable.  Arguments as fwi_forward.  Errors:

@@ -455,8 +455,9 @@ fwi_status fwi_forward_wait_check(const fwi_plan *plan, const float *v, float *d
     if (!plan || !v || !d_syn || !workspace)
         return fail(FWI_ERR_INVALID_ARG, "plan, v, d_syn and workspace must not be NULL");
     const Plan &pl = *as_plan(plan);
-    if (!pl.cluster)
-        return fail(FWI_ERR_UNSUPPORTED, "the wait self-check runs the cluster kernels only");
+    if (!pl.cluster && !(pl.tiled && !pl.cpml))
+        return fail(FWI_ERR_UNSUPPORTED,
+                    "the wait self-check runs the cluster and tiled kernels only");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(e, "fwi_forward_wait_check status reset");

@@ -157,7 +157,7 @@ struct Window {
     float *ckpt = nullptr;
     int ckpt_every = 0;
     float *astate = nullptr, *asrc = nullptr;
-    bool wait_check = false;              // cluster kernels: withhold the halo rows
+    bool wait_check = false;              // cluster / tiled kernels: withhold the halos
 };
 
 // Launchers (return cudaGetLastError() of the launches they made).
@@ -203,6 +203,6 @@ cudaError_t launch_cpml(const Plan &pl, bool adj, const PropArgs &a, unsigned ch
                         cudaStream_t st);
 // Tiled propagators: one launch per step over [a.j_begin, a.j_end)
 cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
-                         cudaStream_t st);
+                         cudaStream_t st, bool wait_check = false);
 
 }  // namespace fwi

@@ -453,7 +453,9 @@ cudaError_t launch_forward(const Plan &pl, const float *v, float *d_syn, float *
     if (pl.cluster)
         return launch_cluster(pl, false, a, static_cast<unsigned char *>(workspace), st,
                               w.wait_check);
-    if (pl.tiled) return launch_tiled(pl, false, a, static_cast<unsigned char *>(workspace), st);
+    if (pl.tiled)
+        return launch_tiled(pl, false, a, static_cast<unsigned char *>(workspace), st,
+                            w.wait_check);
     if (pl.fast) {
         a.rows = pl.shape.rows;
         a.nstrip = pl.shape.nstrip;

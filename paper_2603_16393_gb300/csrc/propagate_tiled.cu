@@ -67,6 +67,8 @@ struct TileArgs {
     const float *adj;           // adjoint source [bs][nr][nt]
     const float *rec_in;        // record read by the adjoint
     int *status;
+    int withhold;               // 1: load no halo tile (the bounded-wait self-check)
+    long long wait_polls;       // bound of one tile wait, in mbarrier polls
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -105,13 +107,13 @@ __device__ __forceinline__ bool mbar_try(uint64_t *mbar)
 // CTA if the copy did not land in time: the status word then holds
 // FWI_ERR_DEVICE_TIMEOUT, and the CTA waits once more (bounded) so that no
 // copy is left writing into its shared memory when it exits.
-__device__ __forceinline__ bool tile_wait(uint64_t *mbar, int *status)
+__device__ __forceinline__ bool tile_wait(uint64_t *mbar, int *status, long long polls)
 {
     bool done = false;
-    for (long it = 0; it < kWaitLimit && !done; ++it) done = mbar_try(mbar);
+    for (long long it = 0; it < polls && !done; ++it) done = mbar_try(mbar);
     if (__syncthreads_and(done)) return true;
     if (threadIdx.x == 0) set_status(status, FWI_ERR_DEVICE_TIMEOUT);
-    for (long it = 0; it < kWaitLimit && !done; ++it) done = mbar_try(mbar);
+    for (long long it = 0; it < polls && !done; ++it) done = mbar_try(mbar);
     return false;
 }
 
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
     const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
     if (tid == 0) mbar_init(&mbar);
     __syncthreads();
-    if (tid == 0) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
+    if (tid == 0 && !a.withhold) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
 
     const int x = x0 + tx, zr = z0 + g * TROWS;
     const bool colok = x < a.NX;
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
         ab[r] = ok ? abb[i] : 0.f;
         vi[r] = ok ? vb[i] : 0.f;
     }
-    if (!tile_wait(&mbar, a.status)) return;
+    if (!tile_wait(&mbar, a.status, a.wait_polls)) return;
     if (TOPBC == 1 && z0 == 0) {
         // mirrored ghost rows: row -k = row k, k = 1..R
         for (int c = tid; c < HX; c += TTHREADS) {
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
     const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
     if (tid == 0) mbar_init(&mbar);
     __syncthreads();
-    if (tid == 0) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
+    if (tid == 0 && !a.withhold) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
 
     const int x = x0 + tx, zr = z0 + g * TROWS;
     const bool colok = x < a.NX;
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
 #pragma unroll
         for (int r = 0; r < TROWS; ++r) inj[(g * TROWS + r) * TX + tx] = 0.f;
     }
-    if (!tile_wait(&mbar, a.status)) return;
+    if (!tile_wait(&mbar, a.status, a.wait_polls)) return;
     if (has_rec) {
         for (int r = tid; r < a.nr; r += TTHREADS) {
             const int pz = a.rec[r] >> 16, px = a.rec[r] & 0xffff;
@@ -471,6 +473,7 @@ TileBufs tile_bufs(const Plan &pl, unsigned char *ws)
 TileArgs tile_args(const Plan &pl, const PropArgs &a, const TileBufs &t)
 {
     TileArgs s{};
+    s.wait_polls = kWaitLimit;
     s.nz = a.nz; s.nx = a.nx; s.nb = a.nb; s.NZ = a.NZ; s.NX = a.NX; s.NXp = pl.NXp;
     s.nt = a.nt; s.ns = a.ns; s.nr = a.nr;
     s.dtd = a.dtd; s.t0d = a.t0d; s.ex0d = a.ex0d; s.ez0d = a.ez0d;
@@ -518,7 +521,7 @@ cudaError_t launch_tile_fold(const Plan &pl, const PropArgs &a, unsigned char *w
 }
 
 cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
-                         cudaStream_t st)
+                         cudaStream_t st, bool wait_check)
 {
     const int nbs = pl.p.batch * pl.p.ns;
     const size_t plane = (size_t)pl.NZ * pl.NXp, field = (size_t)nbs * plane * sizeof(float);
@@ -526,6 +529,10 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
     cudaError_t e = setup(pl, a, t, st);
     if (e != cudaSuccess) return e;
     TileArgs s = tile_args(pl, a, t);
+    if (wait_check) {   // the self-check: no tile is loaded, every wait runs out quickly
+        s.withhold = 1;
+        s.wait_polls = 1024;
+    }
     s.rec_base = a.rec_base;
     s.rec_planes = a.rec_planes;
     const dim3 grid((pl.NX + TX - 1) / TX, (pl.NZ + TZ - 1) / TZ, nbs);

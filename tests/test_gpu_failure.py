@@ -1,6 +1,6 @@
-"""Failure detection on the GPU without a fault: the cluster propagators'
-bounded halo waits run out under the self-check (every halo row withheld,
-20 ms per wait), the status word reports FWI_ERR_DEVICE_TIMEOUT through
+"""Failure detection on the GPU without a fault: the cluster and tiled
+propagators' bounded halo waits run out under the self-check (every halo row
+or tile withheld), the status word reports FWI_ERR_DEVICE_TIMEOUT through
 fwi_check, and the device stays usable: the next forward is exact."""
 import numpy as np
 import pytest
@@ -23,16 +23,18 @@ def api():
     return A
 
 
-def test_cluster_halo_waits_time_out_and_recover(api):
+@pytest.mark.parametrize("family", ["CLUSTER", "TILED"])
+def test_halo_waits_time_out_and_recover(api, family):
     nz, nx, nb, nt, ns, B = 64, 96, 20, 150, 2, 2
     geo = I.surface_geometry(nx, ns)
     kw = dict(nz=nz, nx=nx, nb=nb, nt=nt, dz=10.0, dx=10.0, dt=1e-3, src_iz=geo.src_iz,
               src_ix=geo.src_ix, rec_iz=geo.rec_iz, rec_ix=geo.rec_ix, f_peak=20.0)
-    gp = api.Problem(**kw, batch=B, kernels=api.KERNELS_CLUSTER)
+    fam = getattr(api, "KERNELS_" + family)
+    gp = api.Problem(**kw, batch=B, kernels=fam)
     op = O.Problem(**kw)
     v = models("layered", [1, 2], nz, nx)
     with api.Plan(gp) as plan:
-        assert plan.kernels == api.KERNELS_CLUSTER
+        assert plan.kernels == fam
         vt = torch.tensor(v, dtype=torch.float32, device=DEV)
         d = torch.empty(plan.data_shape, dtype=torch.float32, device=DEV)
         api.fwi_forward_wait_check(plan.handle, vt, d, plan.snapshots, plan.workspace)

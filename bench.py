@@ -850,6 +850,94 @@ def run_conv(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_dsm_train(args, rank, world, local_rank):
+    """--dsm-train: denoising-score-matching training steps (Eq. L2_rewrite) of
+    the convolutional score model (3 layers, --conv-channels wide) on the
+    70x70 workload's batch of 152 normalised models: x_t, the network, the
+    loss, the parameter gradients and Adam, all in library kernels.  Reports
+    training images/s and the FP32 roofline of the weight-gradient kernel,
+    timed alone on the middle layer's operands."""
+    import numpy as np
+    import torch
+    from paper_2603_16393_gb300 import api
+    from paper_2603_16393_gb300 import score_net as SN
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n = args.batch or WORKLOADS["70x70"]["batch"]
+    h = w = 70
+    c, L = args.conv_channels, 3
+    betas = [float(b) for b in np.linspace(1e-4, 0.02, 1000)]
+    net = SN.ConvScore((n, h, w), betas, channels=c, layers=L, seed=5 + rank, device=dev)
+    tr = SN.DSMTrainer(net, lr=1e-3)
+    gen = torch.Generator(device=dev).manual_seed(13 + rank)
+    x0 = 0.3 * torch.randn((n, h, w), device=dev, generator=gen)
+    zs = [torch.randn((n, h, w), device=dev, generator=gen) for _ in range(4)]
+    rng = np.random.default_rng(17 + rank)
+    ts = [int(t) for t in rng.integers(1, 1001, args.warmup + args.steps)]
+    stream = torch.cuda.current_stream(dev)
+    for k in range(args.warmup):
+        tr.step(x0, zs[k % 4], ts[k])
+    torch.cuda.synchronize(dev)
+    loss0 = float(tr.loss.item())
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for k in range(args.steps):
+        tr.step(x0, zs[k % 4], ts[args.warmup + k])
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks else None
+    ms = a.elapsed_time(b) / args.steps
+    loss1 = float(tr.loss.item())
+    ms = max_over_ranks([ms], world, dev)[0]
+    # the weight-gradient kernel alone (layer 1: input A[0], output gradient dH)
+    X, dP, dW = net.A[0], net.dH[0], tr.grads[1][0]
+    reps = max(args.steps, 3)
+    a.record(stream)
+    for _ in range(reps):
+        api.fwi_conv3x3_wgrad(X, dP, dW, tr.work)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_w = a.elapsed_time(b) / reps
+    # one forward convolution of the same layer, for scale
+    a.record(stream)
+    for _ in range(reps):
+        api.fwi_conv3x3_bf16(X, net.W[1], net.bias[1][1], 0, net.P[0])
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_f = a.elapsed_time(b) / reps
+    if rank != 0:
+        return
+    splits = api.fwi_conv3x3_wgrad_splits(n, h, w, c, tr.work.numel())
+    flops_w = 2.0 * n * h * w * 9 * c * c
+    f_mhz = float((clk or {}).get("sm_max_mhz") or 2070.0)
+    # FP32 FMA: 128 lanes per SM, 2 flops each per cycle
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * 2 * f_mhz * 1e6 / 1e12
+    tfw = flops_w / (ms_w * 1e-3) / 1e12
+    launches = 1 + (2 + L + (L - 1)) + 1 + (1 + (4 if splits > 1 else 3) * L + 2 * (L - 1)) + 1 + 2 * L
+    line = {
+        "metric": f"DSM training images/s ({n} x 70x70, {L} conv layers x {c} channels)",
+        "value": world * n * 1e3 / ms, "unit": "images/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 activations, fp32 parameters, gradients and Adam",
+        "data": "synthetic (seeded normal models, one seeded t per step)",
+        "config": {"workload": f"{n} x 70x70, {L} x conv3x3 {c} -> {c} + SiLU, Adam",
+                   "l2": f"activations larger than L2 ({n * h * w * c * 2 / 1e6:.0f} MB each)"},
+        "loss": {"after_warmup": loss0, "last": loss1},
+        "kernels_ms": {"k_conv3x3_wgrad (one layer)": ms_w, "conv forward (one layer)": ms_f},
+        "roofline": {"bound": "alu", "kernel": "k_wgrad", "achieved": tfw, "peak": peak,
+                     "unit": "TFLOP/s", "frac": tfw / peak,
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {f_mhz:.0f} MHz",
+                     "splits": splits, "traffic": None},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -876,6 +964,9 @@ def main():
                          "this fraction of the first reverse steps")
     ap.add_argument("--conv-channels", type=int, default=128,
                     help="--conv: input and output channels (a multiple of 64)")
+    ap.add_argument("--dsm-train", action="store_true",
+                    help="denoising-score-matching training steps of the convolutional score "
+                         "model (152 x 70x70, 3 layers of --conv-channels)")
     ap.add_argument("--sampler", action="store_true",
                     help="reverse steps of Algorithm 2 (score, proposal, W2 guidance gradient, "
                          "chain rule, preconditioned update) on the 70x70 workload")
@@ -895,6 +986,8 @@ def main():
             run_sampler(args, rank, world, local_rank)
         elif args.conv:
             run_conv(args, rank, world, local_rank)
+        elif args.dsm_train:
+            run_dsm_train(args, rank, world, local_rank)
         else:
             run_ours(args, rank, world, local_rank)
     finally:

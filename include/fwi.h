@@ -440,6 +440,63 @@ FWI_API fwi_status fwi_conv3x3_bf16_wait_check(int n, int h, int w, int cin, int
                                                const void *x, const void *wt, void *y, int y_bf16,
                                                int *status, void *stream);
 
+/* Denoising score matching (Sec. 3.4, Eq. L2_rewrite) of the convolutional
+ * score model: with x_t = sqrt(abar) x_0 + sqrt(1 - abar) z the conditional
+ * score is -z / sqrt(1 - abar), and with the weight kappa(t) = 1 - abar the
+ * objective is the regression of eps(x_t, t) on z.  Float32 device arrays
+ * unless stated; bf16 tensors are NHWC with `channels` per pixel.  Errors:
+ * FWI_ERR_INVALID_ARG before any launch, FWI_ERR_CUDA. */
+
+/* xt = sqrt(abar) x0 + sqrt(1 - abar) z over n elements, 0 < abar < 1. */
+FWI_API fwi_status fwi_dsm_noisy(long long n, double abar, const float *x0, const float *z,
+                                 float *xt, void *stream);
+
+/* *loss = mean over n of (eps - z)^2 (one device float, a fixed-order sum)
+ * and grad = d loss / d eps = 2 (eps - z) / n. */
+FWI_API fwi_status fwi_dsm_loss(long long n, const float *eps, const float *z, float *loss,
+                                float *grad, void *stream);
+
+/* Weight gradient of the 3x3 convolution (stride 1, zero padding 1):
+ * dW[co][ky][kx][ci] = sum_{b,y,x} dP[b][y][x][co] X[b][y+ky-1][x+kx-1][ci],
+ * X and dP bf16 [n][h][w][channels], dW float32 [channels][3][3][channels]
+ * (written), channels a multiple of 64; X, dP, dW and work 16-byte aligned.
+ * The pixels are split into fwi_conv3x3_wgrad_splits(...) contiguous ranges
+ * whose partial sums go to `work` (work_floats floats, caller-owned; NULL or
+ * too small for two splits means one range written straight to dW) and are
+ * then added in range order: a fixed summation order for given sizes,
+ * work_floats and SM count. */
+FWI_API fwi_status fwi_conv3x3_wgrad(int n, int h, int w, int channels, const void *X,
+                                     const void *dP, float *dW, float *work,
+                                     long long work_floats, void *stream);
+
+/* The number of pixel ranges fwi_conv3x3_wgrad uses (1..16; about four CTAs
+ * per SM, at most work_floats / (9 channels^2)); 0 for invalid sizes. */
+FWI_API int fwi_conv3x3_wgrad_splits(int n, int h, int w, int channels, long long work_floats);
+
+/* db[c] = sum_p dP[p][c] over npix pixels (dP bf16 [npix][channels]). */
+FWI_API fwi_status fwi_channel_sum(long long npix, int channels, const void *dP, float *db,
+                                   void *stream);
+
+/* One Adam step (step >= 1) on n float32 parameters: m = b1 m + (1 - b1) g,
+ * v = b2 v + (1 - b2) g^2, p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
+FWI_API fwi_status fwi_adam_step(long long n, double lr, double beta1, double beta2, double eps,
+                                 int step, float *param, const float *grad, float *m, float *v,
+                                 void *stream);
+
+/* bf16 weights Wb = W and their transpose for the backward pass,
+ * WTb[ci][ky][kx][co] = W[co][2-ky][2-kx][ci]; W float32 [cout][3][3][cin]. */
+FWI_API fwi_status fwi_conv3x3_weights_prep(int cout, int cin, const float *W, void *Wb,
+                                            void *WTb, void *stream);
+
+/* Per-step biases of a layer: out[i][c] = b[c] + sum_k E[c][k] phi[i][k]
+ * (b [channels], E [channels][dim], phi [nsteps][dim], out [nsteps][channels]). */
+FWI_API fwi_status fwi_time_bias(int nsteps, int channels, int dim, const float *b, const float *E,
+                                 const float *phi, float *out, void *stream);
+
+/* dE[c][k] = db[c] phi[k]: the gradient with respect to E of a bias b + E phi. */
+FWI_API fwi_status fwi_time_bias_grad(int channels, int dim, const float *db, const float *phi,
+                                      float *dE, void *stream);
+
 /* ---------------------------------------------------------------- low-fidelity guidance
  * Grid transfers of the low-fidelity guidance surrogate (the multi-fidelity
  * route to cheaper physics guidance, Sec. 7): the W2 potential of the problem

@@ -74,13 +74,12 @@ def time_bias(b, E, phi):
     return np.asarray(b, np.float64) + np.asarray(phi, np.float64) @ np.asarray(E, np.float64).T
 
 
-def dsm_gradients(weights, x0, z, abar, t, round_bf16: bool = True, xt=None):
+def dsm_gradients(weights, x0, z, abar, t, round_bf16: bool = True):
     """(loss, [(dW, db, dE)] per layer) of one minibatch x0, z [B][nz][nx] at
-    step t.  ``xt`` overrides the noisy input (to share its float32 value
-    with another implementation)."""
+    step t."""
     net = N.ConvScore(weights, round_bf16=round_bf16)
     r = net.r
-    xt = noisy(x0, z, abar) if xt is None else np.asarray(xt, np.float64)
+    xt = noisy(x0, z, abar)
     eps = net.eps(xt, t)
     loss, g = dsm_loss(eps, z)
     L = len(net.W)

@@ -151,6 +151,26 @@ _lib.fwi_conv3x3_bf16_wait_check.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp,
                                                                   _vp, _vp]
 _lib.fwi_forward_wait_check.restype = _S
 _lib.fwi_forward_wait_check.argtypes = [_vp] * 6
+_lib.fwi_dsm_noisy.restype = _S
+_lib.fwi_dsm_noisy.argtypes = [ctypes.c_longlong, ctypes.c_double, _vp, _vp, _vp, _vp]
+_lib.fwi_dsm_loss.restype = _S
+_lib.fwi_dsm_loss.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp]
+_lib.fwi_conv3x3_wgrad.restype = _S
+_lib.fwi_conv3x3_wgrad.argtypes = [ctypes.c_int] * 4 + [_vp, _vp, _vp, _vp, ctypes.c_longlong,
+                                                         _vp]
+_lib.fwi_conv3x3_wgrad_splits.restype = ctypes.c_int
+_lib.fwi_conv3x3_wgrad_splits.argtypes = [ctypes.c_int] * 4 + [ctypes.c_longlong]
+_lib.fwi_channel_sum.restype = _S
+_lib.fwi_channel_sum.argtypes = [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp]
+_lib.fwi_adam_step.restype = _S
+_lib.fwi_adam_step.argtypes = [ctypes.c_longlong] + [ctypes.c_double] * 4 + [ctypes.c_int] + \
+    [_vp] * 5
+_lib.fwi_conv3x3_weights_prep.restype = _S
+_lib.fwi_conv3x3_weights_prep.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+_lib.fwi_time_bias.restype = _S
+_lib.fwi_time_bias.argtypes = [ctypes.c_int] * 3 + [_vp] * 5
+_lib.fwi_time_bias_grad.restype = _S
+_lib.fwi_time_bias_grad.argtypes = [ctypes.c_int] * 2 + [_vp] * 4
 _lib.fwi_check.restype = _S
 _lib.fwi_check.argtypes = [_vp, _vp, _vp]
 _lib.fwi_last_error.restype = ctypes.c_char_p
@@ -557,6 +577,68 @@ def fwi_silu_grad_bf16(dA, P, dP, stream=None):
     if not (dA.dtype == P.dtype == dP.dtype == torch.bfloat16) or not (dA.shape == P.shape == dP.shape):
         raise ValueError("dA, P and dP must be bfloat16 tensors of one shape")
     _check(_lib.fwi_silu_grad_bf16(P.numel(), _ptr(dA), _ptr(P), _ptr(dP), _stream(stream)))
+
+
+def fwi_dsm_noisy(x0, z, abar, xt, stream=None):
+    _check(_lib.fwi_dsm_noisy(x0.numel(), float(abar), _ptr(x0), _ptr(z), _ptr(xt),
+                              _stream(stream)))
+
+
+def fwi_dsm_loss(eps, z, loss, grad, stream=None):
+    _check(_lib.fwi_dsm_loss(eps.numel(), _ptr(eps), _ptr(z), _ptr(loss), _ptr(grad),
+                             _stream(stream)))
+
+
+WGRAD_MAX_SPLITS = 16
+
+
+def fwi_conv3x3_wgrad(X, dP, dW, work=None, stream=None):
+    """dW [C][3][3][C] float32 from X, dP bf16 [n][h][w][C]; ``work`` a float32
+    device buffer for the per-range partial sums (WGRAD_MAX_SPLITS 9 C^2
+    floats use every split the library wants; None: one range)."""
+    n, h, w, c = X.shape
+    if X.dtype != torch.bfloat16 or dP.dtype != torch.bfloat16 or tuple(dP.shape) != (n, h, w, c):
+        raise ValueError("X and dP must be bfloat16 [n][h][w][C]")
+    if not (X.is_contiguous() and dP.is_contiguous()):
+        raise ValueError("X and dP must be contiguous")
+    _f32(dW, (c, 3, 3, c), "dW")
+    wf = 0 if work is None else work.numel()
+    if work is not None and (work.dtype != torch.float32 or not work.is_contiguous()):
+        raise ValueError("work must be a contiguous float32 tensor")
+    _check(_lib.fwi_conv3x3_wgrad(n, h, w, c, _ptr(X), _ptr(dP), _ptr(dW), _ptr(work), wf,
+                                  _stream(stream)))
+
+
+def fwi_conv3x3_wgrad_splits(n, h, w, channels, work_floats):
+    return _lib.fwi_conv3x3_wgrad_splits(n, h, w, channels, work_floats)
+
+
+def fwi_channel_sum(dP, db, stream=None):
+    c = dP.shape[-1]
+    _f32(db, (c,), "db")
+    _check(_lib.fwi_channel_sum(dP.numel() // c, c, _ptr(dP), _ptr(db), _stream(stream)))
+
+
+def fwi_adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(_lib.fwi_adam_step(param.numel(), float(lr), float(beta1), float(beta2), float(eps),
+                              int(step), _ptr(param), _ptr(grad), _ptr(m), _ptr(v),
+                              _stream(stream)))
+
+
+def fwi_conv3x3_weights_prep(W, Wb, WTb, stream=None):
+    cout, _, _, cin = W.shape
+    _check(_lib.fwi_conv3x3_weights_prep(cout, cin, _ptr(W), _ptr(Wb), _ptr(WTb),
+                                         _stream(stream)))
+
+
+def fwi_time_bias(b, E, phi, out, stream=None):
+    _check(_lib.fwi_time_bias(phi.shape[0], b.shape[0], E.shape[1], _ptr(b), _ptr(E), _ptr(phi),
+                              _ptr(out), _stream(stream)))
+
+
+def fwi_time_bias_grad(db, phi_row, dE, stream=None):
+    _check(_lib.fwi_time_bias_grad(db.shape[0], phi_row.shape[0], _ptr(db), _ptr(phi_row),
+                                   _ptr(dE), _stream(stream)))
 
 
 def fwi_check(plan, workspace, stream=None):

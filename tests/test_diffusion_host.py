@@ -124,6 +124,34 @@ def test_grid_transfers_reject_bad_arguments_without_a_gpu(api):
         assert api.fwi_last_error() != ""
 
 
+def test_training_calls_reject_bad_arguments_without_a_gpu(api):
+    lib = api._lib
+    p = ctypes.c_void_p(4096)
+    calls = [
+        lambda: lib.fwi_dsm_noisy(4, 1.0, p, p, p, None),             # abar must be < 1
+        lambda: lib.fwi_dsm_noisy(4, 0.5, None, p, p, None),
+        lambda: lib.fwi_dsm_loss(0, p, p, p, p, None),
+        lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 96, p, p, p, None, 0, None),   # channels % 64
+        lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, p, None, p, None, 0, None),
+        lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, ctypes.c_void_p(4100), p, p, None, 0, None),
+        lambda: lib.fwi_channel_sum(16, 0, p, p, None),
+        lambda: lib.fwi_adam_step(8, 1e-3, 0.9, 0.999, 1e-8, 0, p, p, p, p, None),   # step >= 1
+        lambda: lib.fwi_adam_step(8, 1e-3, 1.0, 0.999, 1e-8, 1, p, p, p, p, None),
+        lambda: lib.fwi_adam_step(8, 0.0, 0.9, 0.999, 1e-8, 1, p, p, p, p, None),
+        lambda: lib.fwi_conv3x3_weights_prep(64, 64, p, None, p, None),
+        lambda: lib.fwi_time_bias(0, 64, 16, p, p, p, p, None),
+        lambda: lib.fwi_time_bias_grad(64, 16, p, None, p, None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == 1, k
+        assert api.fwi_last_error() != ""
+    # the split count: 1 without room for a second range, at most 16
+    assert lib.fwi_conv3x3_wgrad_splits(2, 33, 47, 64, 0) == 1
+    assert lib.fwi_conv3x3_wgrad_splits(2, 33, 47, 64, 9 * 64 * 64 * 3) in (2, 3)
+    assert 1 <= lib.fwi_conv3x3_wgrad_splits(152, 70, 70, 128, 10 ** 9) <= 16
+    assert lib.fwi_conv3x3_wgrad_splits(1, 4, 4, 96, 10 ** 9) == 0
+
+
 def test_coarse_problem_of_the_benchmark(api):
     prob = api.Problem(nz=70, nx=70, nb=40, nt=1000, dz=10.0, dx=10.0, dt=1e-3,
                        src_iz=(0,) * 5, src_ix=(0, 17, 34, 52, 69), rec_iz=(0,) * 70,

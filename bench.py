@@ -892,32 +892,53 @@ def run_dsm_train(args, rank, world, local_rank):
     ms = a.elapsed_time(b) / args.steps
     loss1 = float(tr.loss.item())
     ms = max_over_ranks([ms], world, dev)[0]
-    # the weight-gradient kernel alone (layer 1: input A[0], output gradient dH)
+    # the weight gradient alone (layer 1: input A[0], output gradient dH), on
+    # the tensor cores (staging + k_wgrad_tc + split reduction) and, for
+    # context, on the CUDA cores
     X, dP, dW = net.A[0], net.dH[0], tr.grads[1][0]
     reps = max(args.steps, 3)
-    a.record(stream)
-    for _ in range(reps):
-        api.fwi_conv3x3_wgrad(X, dP, dW, tr.work)
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_w = a.elapsed_time(b) / reps
-    # one forward convolution of the same layer, for scale
-    a.record(stream)
-    for _ in range(reps):
-        api.fwi_conv3x3_bf16(X, net.W[1], net.bias[1][1], 0, net.P[0])
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_f = a.elapsed_time(b) / reps
+
+    def timed(fn):
+        fn()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    tc = tr.stage is not None
+    ms_tc = timed(lambda: api.fwi_conv3x3_wgrad_tc(X, dP, dW, tr.stage, tr.work)) if tc else None
+    ms_cc = timed(lambda: api.fwi_conv3x3_wgrad(X, dP, dW, tr.work))
+    ms_f = timed(lambda: api.fwi_conv3x3_bf16(X, net.W[1], net.bias[1][1], 0, net.P[0]))
     if rank != 0:
         return
-    splits = api.fwi_conv3x3_wgrad_splits(n, h, w, c, tr.work.numel())
     flops_w = 2.0 * n * h * w * 9 * c * c
-    f_mhz = float((clk or {}).get("sm_max_mhz") or 2070.0)
-    # FP32 FMA: 128 lanes per SM, 2 flops each per cycle
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * 128 * 2 * f_mhz * 1e6 / 1e12
-    tfw = flops_w / (ms_w * 1e-3) / 1e12
-    launches = 1 + (2 + L + (L - 1)) + 1 + (1 + (4 if splits > 1 else 3) * L + 2 * (L - 1)) + 1 + 2 * L
+    if tc:
+        splits = api.fwi_conv3x3_wgrad_tc_splits(n, h, w, c, tr.work.numel())
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peak, src = float(json.load(f)["bf16_tflops"]), "measured (bf16 burst)"
+        except Exception:
+            peak, src = 1900.0, "fallback"
+        ach = flops_w / (ms_tc * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "fwi_conv3x3_wgrad_tc (4 x k_stage_kmajor + "
+                                             "k_wgrad_tc + k_wgrad_tc_reduce)",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": src, "splits": splits, "traffic": None}
+        per_layer = 4 + 1 + (1 if splits > 1 else 0)
+    else:
+        splits = api.fwi_conv3x3_wgrad_splits(n, h, w, c, tr.work.numel())
+        f_mhz = float((clk or {}).get("sm_max_mhz") or 2070.0)
+        peak = sms * 128 * 2 * f_mhz * 1e6 / 1e12        # FP32 FMA: 128 lanes per SM
+        ach = flops_w / (ms_cc * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_wgrad", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {f_mhz:.0f} MHz",
+                "splits": splits, "traffic": None}
+        per_layer = 1 + (1 if splits > 1 else 0)
+    launches = 1 + (2 + L + (L - 1)) + 1 + (1 + (per_layer + 2) * L + 2 * (L - 1)) + 1 + 2 * L
     line = {
         "metric": f"DSM training images/s ({n} x 70x70, {L} conv layers x {c} channels)",
         "value": world * n * 1e3 / ms, "unit": "images/s", "n_gpus": world, "steps": args.steps,
@@ -927,11 +948,10 @@ def run_dsm_train(args, rank, world, local_rank):
         "config": {"workload": f"{n} x 70x70, {L} x conv3x3 {c} -> {c} + SiLU, Adam",
                    "l2": f"activations larger than L2 ({n * h * w * c * 2 / 1e6:.0f} MB each)"},
         "loss": {"after_warmup": loss0, "last": loss1},
-        "kernels_ms": {"k_conv3x3_wgrad (one layer)": ms_w, "conv forward (one layer)": ms_f},
-        "roofline": {"bound": "alu", "kernel": "k_wgrad", "achieved": tfw, "peak": peak,
-                     "unit": "TFLOP/s", "frac": tfw / peak,
-                     "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {f_mhz:.0f} MHz",
-                     "splits": splits, "traffic": None},
+        "kernels_ms": {"weight gradient, tensor cores (one layer)": ms_tc,
+                       "weight gradient, CUDA cores (one layer)": ms_cc,
+                       "conv forward (one layer)": ms_f},
+        "roofline": roof,
         "gpu_launches": launches * args.steps,
         "clocks": clk,
     }

@@ -473,6 +473,28 @@ FWI_API fwi_status fwi_conv3x3_wgrad(int n, int h, int w, int channels, const vo
  * per SM, at most work_floats / (9 channels^2)); 0 for invalid sizes. */
 FWI_API int fwi_conv3x3_wgrad_splits(int n, int h, int w, int channels, long long work_floats);
 
+/* The same weight gradient on the tensor cores (tcgen05, BF16 products, FP32
+ * accumulation), channels a multiple of 128.  Over the zero-padded pixel
+ * domain q (rows of wp = w + 2 rounded up to a multiple of 8 pixels) the
+ * operands are first staged K-major in `stage` (caller-owned, at least
+ * fwi_conv3x3_wgrad_tc_stage_bytes(...) bytes): dP^T[co][q] and three copies
+ * X_s^T[ci][q] = Xpad(q + s), s = -1, 0, 1; each tap (ky, kx) is then the
+ * GEMM sum_q dP^T[co][q] X_{kx-1}^T[ci][q + (ky-1) wp].  The padded pixels
+ * are split into fwi_conv3x3_wgrad_tc_splits(...) ranges whose partial tiles
+ * go to `work` (NULL: one range) and are added in range order.  *status (may
+ * be NULL) receives FWI_ERR_DEVICE_TIMEOUT if a device-side wait ran out. */
+FWI_API fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int channels, const void *X,
+                                        const void *dP, float *dW, void *stage,
+                                        long long stage_bytes, float *work,
+                                        long long work_floats, int *status, void *stream);
+
+/* Bytes of the K-major staging buffer (0 for invalid sizes). */
+FWI_API long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int channels);
+
+/* Pixel ranges of fwi_conv3x3_wgrad_tc: about one CTA per SM, at most
+ * work_floats / (9 channels^2); 0 for invalid sizes. */
+FWI_API int fwi_conv3x3_wgrad_tc_splits(int n, int h, int w, int channels, long long work_floats);
+
 /* db[c] = sum_p dP[p][c] over npix pixels (dP bf16 [npix][channels]). */
 FWI_API fwi_status fwi_channel_sum(long long npix, int channels, const void *dP, float *db,
                                    void *stream);

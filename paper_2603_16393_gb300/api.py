@@ -158,6 +158,13 @@ _lib.fwi_dsm_loss.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp]
 _lib.fwi_conv3x3_wgrad.restype = _S
 _lib.fwi_conv3x3_wgrad.argtypes = [ctypes.c_int] * 4 + [_vp, _vp, _vp, _vp, ctypes.c_longlong,
                                                          _vp]
+_lib.fwi_conv3x3_wgrad_tc.restype = _S
+_lib.fwi_conv3x3_wgrad_tc.argtypes = [ctypes.c_int] * 4 + [_vp, _vp, _vp, _vp, ctypes.c_longlong,
+                                                            _vp, ctypes.c_longlong, _vp, _vp]
+_lib.fwi_conv3x3_wgrad_tc_stage_bytes.restype = ctypes.c_longlong
+_lib.fwi_conv3x3_wgrad_tc_stage_bytes.argtypes = [ctypes.c_int] * 4
+_lib.fwi_conv3x3_wgrad_tc_splits.restype = ctypes.c_int
+_lib.fwi_conv3x3_wgrad_tc_splits.argtypes = [ctypes.c_int] * 4 + [ctypes.c_longlong]
 _lib.fwi_conv3x3_wgrad_splits.restype = ctypes.c_int
 _lib.fwi_conv3x3_wgrad_splits.argtypes = [ctypes.c_int] * 4 + [ctypes.c_longlong]
 _lib.fwi_channel_sum.restype = _S
@@ -589,7 +596,7 @@ def fwi_dsm_loss(eps, z, loss, grad, stream=None):
                              _stream(stream)))
 
 
-WGRAD_MAX_SPLITS = 16
+WGRAD_MAX_SPLITS = 32   # partial tiles a work buffer of WGRAD_MAX_SPLITS 9 C^2 floats holds
 
 
 def fwi_conv3x3_wgrad(X, dP, dW, work=None, stream=None):
@@ -611,6 +618,32 @@ def fwi_conv3x3_wgrad(X, dP, dW, work=None, stream=None):
 
 def fwi_conv3x3_wgrad_splits(n, h, w, channels, work_floats):
     return _lib.fwi_conv3x3_wgrad_splits(n, h, w, channels, work_floats)
+
+
+def fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, channels):
+    return _lib.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, channels)
+
+
+def fwi_conv3x3_wgrad_tc_splits(n, h, w, channels, work_floats):
+    return _lib.fwi_conv3x3_wgrad_tc_splits(n, h, w, channels, work_floats)
+
+
+def fwi_conv3x3_wgrad_tc(X, dP, dW, stage, work=None, status=None, stream=None):
+    """The weight gradient on the tensor cores (C a multiple of 128): ``stage``
+    a uint8/bf16 device buffer of at least fwi_conv3x3_wgrad_tc_stage_bytes
+    bytes, ``work`` float32 for the partial tiles (None: one range)."""
+    n, h, w, c = X.shape
+    if X.dtype != torch.bfloat16 or dP.dtype != torch.bfloat16 or tuple(dP.shape) != (n, h, w, c):
+        raise ValueError("X and dP must be bfloat16 [n][h][w][C]")
+    if not (X.is_contiguous() and dP.is_contiguous() and stage.is_contiguous()):
+        raise ValueError("X, dP and stage must be contiguous")
+    _f32(dW, (c, 3, 3, c), "dW")
+    wf = 0 if work is None else work.numel()
+    if work is not None and (work.dtype != torch.float32 or not work.is_contiguous()):
+        raise ValueError("work must be a contiguous float32 tensor")
+    _check(_lib.fwi_conv3x3_wgrad_tc(n, h, w, c, _ptr(X), _ptr(dP), _ptr(dW), _ptr(stage),
+                                     stage.numel() * stage.element_size(), _ptr(work), wf,
+                                     _ptr(status), _stream(stream)))
 
 
 def fwi_channel_sum(dP, db, stream=None):

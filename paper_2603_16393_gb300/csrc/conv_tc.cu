@@ -709,6 +709,248 @@ cudaError_t launch_conv_pn(const CUtensorMap &tmx, const CUtensorMap &tmw, const
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores.  Over the zero-padded pixel domain q =
+// (b (h + 2) + yy) wp + xx (row pitch wp = w + 2 rounded up to a multiple of
+// 8, yy, xx = y + 1, x + 1 inside the image), with dP^T[co][q] and X_s^T[ci][q]
+// = Xpad(q + s) staged K-major (k_stage_kmajor, s = kx - 1 for kx = 0, 1, 2),
+//   dW[co][ky][kx][ci] = sum_q dP^T[co][q] X_{kx-1}^T[ci][q + (ky - 1) wp]
+// is, per tap, a plain K-major GEMM: M = 128 output channels (operand A),
+// N = 128 input channels of a tap, K = the padded pixels.  dP^T vanishes off
+// the image, so a shifted read that leaves the image (or [0, Q): the TMA fills
+// zeros) contributes nothing.  A job pairs two consecutive (tap, 128-channel
+// block) units into N = 256 (the MMA's rate per SM grows with N); the K range
+// is split over CTAs (job fastest in the grid, so the CTAs of one split run
+// together and share the dP^T and X^T blocks in L2), each writing its FP32
+// partial tile, which k_wgrad_tc_reduce then adds in split order.  Warp 0
+// lane 0 issues the TMA copies, warp 1 lane 0 the MMAs, warps 2..17 read the
+// accumulator; every wait is bounded as in k_conv3x3_tc.
+constexpr int kGStages = 4;
+constexpr int kGABytes = 128 * kBK * 2;          // 16 KB: 128 output channels x 64 pixels
+constexpr int kGUBytes = 128 * kBK * 2;          // 16 KB: one unit's 128 input channels
+constexpr int kGBBytes = 2 * kGUBytes;
+constexpr uint32_t kGTmemCols = 256;
+
+struct WgradTcArgs {
+    unsigned long long wait_ns;
+    int C, cbs, wp;        // channels, 128-channel blocks, padded row pitch
+    int units, pairs, jobs;
+    long long kblocks, per_split;
+    float *out;            // [split][C][9][C]
+    int *status;
+};
+
+// out[c][q] = Xpad(q + shift)[c] for q < Q (0 outside the image and [0, Q)):
+// a 64 (q) x 64 (c) tile per CTA through shared memory, 16-byte loads along c
+// and 16-byte stores along q
+__global__ void __launch_bounds__(256)
+    k_stage_kmajor(int h, int w, int C, int wp, long long Q, int shift,
+                   const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out)
+{
+    __shared__ __align__(16) __nv_bfloat16 tile[64][72];
+    const long long q0 = (long long)blockIdx.x * 64;
+    const int c0 = blockIdx.y * 64;
+    const long long img = (long long)(h + 2) * wp;
+    for (int e = threadIdx.x; e < 512; e += 256) {
+        const int ql = e >> 3, j = e & 7;
+        const long long p = q0 + ql + shift;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (p >= 0 && p < Q) {
+            const long long b = p / img;
+            const int r = (int)(p - b * img);
+            const int yy = r / wp, xx = r - (r / wp) * wp;
+            if (yy >= 1 && yy <= h && xx >= 1 && xx <= w)
+                v = *reinterpret_cast<const uint4 *>(
+                    in + ((b * h + (yy - 1)) * (long long)w + (xx - 1)) * C + c0 + 8 * j);
+        }
+        *reinterpret_cast<uint4 *>(&tile[ql][8 * j]) = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 512; e += 256) {
+        const int cl = e & 63, j = e >> 6;
+        if (q0 + 8 * j >= Q) continue;
+        __nv_bfloat16 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = tile[8 * j + i][cl];
+        *reinterpret_cast<uint4 *>(out + (size_t)(c0 + cl) * Q + q0 + 8 * j) =
+            *reinterpret_cast<uint4 *>(v);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb0,
+               const __grid_constant__ CUtensorMap tmb1, const __grid_constant__ CUtensorMap tmb2,
+               const WgradTcArgs a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char *sA = base;
+    unsigned char *sB = base + kGStages * kGABytes;
+    __shared__ uint64_t full[kGStages], empty[kGStages], acc_full;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    volatile int *vfailed = &failed;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int job = blockIdx.x % a.jobs, split = blockIdx.x / a.jobs;
+    const int cot = job / a.pairs, pair = job % a.pairs;
+    const int co0 = cot * 128;
+    const int u0 = 2 * pair;
+    const int nb = u0 + 1 < a.units ? 2 : 1;     // units in this job
+    const long long k0 = (long long)split * a.per_split;
+    const long long k1 = k0 + a.per_split < a.kblocks ? k0 + a.per_split : a.kblocks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGStages; ++s) {
+            mb_init(&full[s], 1);
+            mb_init(&empty[s], 1);
+        }
+        mb_init(&acc_full, 1);
+        failed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&tmem_slot)),
+                     "r"(kGTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int last[kGStages];
+            for (int s = 0; s < kGStages; ++s) last[s] = -1;
+            int i = 0;
+            for (long long kb = k0; kb < k1 && !*vfailed; ++kb, ++i) {
+                const int s = i % kGStages, r = i / kGStages;
+                if (r > 0 && !mb_wait(&empty[s], (unsigned)((r - 1) & 1), vfailed, a.wait_ns)) break;
+                mb_expect(&full[s], (unsigned)(kGABytes + nb * kGUBytes));
+                const int q0 = (int)(kb * kBK);
+                tma_2d(sA + s * kGABytes, &tma, q0, co0, &full[s]);
+                for (int j = 0; j < nb; ++j) {
+                    const int u = u0 + j, tap = u / a.cbs, cb = u % a.cbs;
+                    const int ky = tap / 3, kx = tap % 3;
+                    const CUtensorMap *mb = kx == 0 ? &tmb0 : (kx == 1 ? &tmb1 : &tmb2);
+                    tma_2d(sB + s * kGBBytes + j * kGUBytes, mb, q0 + (ky - 1) * a.wp, cb * 128,
+                           &full[s]);
+                }
+                last[s] = i;
+            }
+            if (*vfailed) drain_loads(full, last, a.wait_ns);
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && k0 < k1) {
+            const uint32_t idesc = idesc_bf16(nb * 128);
+            bool ok = true;
+            int i = 0;
+            for (long long kb = k0; kb < k1; ++kb, ++i) {
+                const int s = i % kGStages, r = i / kGStages;
+                if (!mb_wait(&full[s], (unsigned)(r & 1), vfailed, a.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t ad = sw128_desc(sA + s * kGABytes, 1024);
+                const uint64_t bd = sw128_desc(sB + s * kGBBytes, 1024);
+#pragma unroll
+                for (int k = 0; k < kBK / 16; ++k)
+                    umma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (i | k) != 0);
+                umma_commit(&empty[s]);
+            }
+            if (ok) umma_commit(&acc_full);
+        }
+    } else {
+        // warps 2..17: lane quarter q (32 output channels), a quarter of the columns
+        const int q = warp & 3;
+        const int co = co0 + q * 32 + lane;
+        const int part = (warp - 2) >> 2;
+        const int ncols = nb * 128;
+        const int cbeg = part * (ncols / 4), cend = cbeg + ncols / 4;
+        const bool has = k0 < k1;
+        if (!has || mb_wait(&acc_full, 0u, vfailed, a.wait_ns)) {
+            tc_fence_after();
+            float *o = a.out + (size_t)split * 9 * a.C * a.C;
+#pragma unroll 1
+            for (int c = cbeg; c < cend; c += 16) {
+                float v[16];
+                if (has) {
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                }
+                const int u = u0 + c / 128, tap = u / a.cbs, cb = u % a.cbs;
+                const int ci = cb * 128 + c % 128;
+                float4 *dst = reinterpret_cast<float4 *>(o + ((size_t)co * 9 + tap) * a.C + ci);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kGTmemCols)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *vfailed && a.status) atomicExch(a.status, (int)FWI_ERR_DEVICE_TIMEOUT);
+}
+
+// dW[e] = sum_s part[s][e], s in order
+__global__ void __launch_bounds__(256)
+    k_wgrad_tc_reduce(size_t n, int splits, const float *__restrict__ part, float *__restrict__ dW)
+{
+    for (size_t e = (size_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (size_t)gridDim.x * 256) {
+        float s = part[e];
+        for (int k = 1; k < splits; ++k) s += part[(size_t)k * n + e];
+        dW[e] = s;
+    }
+}
+
+struct WgradTcShape {
+    int wp;
+    long long Q, kblocks;
+    int cbs, units, pairs, jobs;
+};
+
+WgradTcShape wgrad_tc_shape(int n, int h, int w, int C)
+{
+    WgradTcShape s;
+    s.wp = (w + 2 + 7) / 8 * 8;
+    s.Q = (long long)n * (h + 2) * s.wp;
+    s.kblocks = (s.Q + kBK - 1) / kBK;
+    s.cbs = C / 128;
+    s.units = 9 * s.cbs;
+    s.pairs = (s.units + 1) / 2;
+    s.jobs = s.cbs * s.pairs;
+    return s;
+}
+
+int wgrad_tc_splits(const WgradTcShape &g, int C, long long work_floats)
+{
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long s = sms / g.jobs;                      // one CTA per SM
+    if (s < 1) s = 1;
+    if (s > g.kblocks) s = g.kblocks;
+    const long long fit = work_floats / (9LL * C * C);
+    if (s > fit) s = fit;
+    if (s < 1) return 1;
+    const long long per = (g.kblocks + s - 1) / s;
+    return (int)((g.kblocks + per - 1) / per);      // no empty range
+}
+
 }  // namespace
 
 extern "C" {
@@ -800,6 +1042,97 @@ fwi_status fwi_conv3x3_bf16_wait_check(int n, int h, int w, int cin, int cout, c
         return fwi::record_error(FWI_ERR_INVALID_ARG, "the wait check needs a status word");
     return conv_call(n, h, w, cin, cout, x, wt, nullptr, 0, y, y_bf16, status, stream, 1,
                      kCheckWaitNs);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int channels)
+{
+    if (n < 1 || h < 1 || w < 1 || channels < 128 || channels % 128 != 0) return 0;
+    const WgradTcShape g = wgrad_tc_shape(n, h, w, channels);
+    return 4LL * channels * g.Q * 2;
+}
+
+int fwi_conv3x3_wgrad_tc_splits(int n, int h, int w, int channels, long long work_floats)
+{
+    if (n < 1 || h < 1 || w < 1 || channels < 128 || channels % 128 != 0) return 0;
+    return wgrad_tc_splits(wgrad_tc_shape(n, h, w, channels), channels, work_floats);
+}
+
+fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int channels, const void *X, const void *dP,
+                                float *dW, void *stage, long long stage_bytes, float *work,
+                                long long work_floats, int *status, void *stream)
+{
+    if (n < 1 || h < 1 || w < 1 || channels < 128 || channels % 128 != 0)
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "n, h, w >= 1 and channels a multiple of 128");
+    if (!X || !dP || !dW || !stage)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "X, dP, dW and stage are needed");
+    if (((uintptr_t)X | (uintptr_t)dP | (uintptr_t)dW | (uintptr_t)stage | (uintptr_t)work) & 15)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "all arrays must be 16-byte aligned");
+    const WgradTcShape g = wgrad_tc_shape(n, h, w, channels);
+    if (g.Q + g.wp + kBK >= 0x7fffffffLL)
+        return fwi::record_error(FWI_ERR_UNSUPPORTED, "too many pixels for one weight gradient");
+    const long long need = 4LL * channels * g.Q * 2;
+    if (stage_bytes < need)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "stage needs %lld bytes", need);
+    const int splits = wgrad_tc_splits(g, channels, work ? work_floats : 0);
+    auto enc = tmap_encoder();
+    if (!enc) return fwi::record_error(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    __nv_bfloat16 *arr[4];
+    for (int k = 0; k < 4; ++k)
+        arr[k] = static_cast<__nv_bfloat16 *>(stage) + (size_t)k * channels * g.Q;
+    const dim3 sgrid((unsigned)((g.Q + 63) / 64), (unsigned)(channels / 64));
+    k_stage_kmajor<<<sgrid, 256, 0, st>>>(h, w, channels, g.wp, g.Q, 0,
+                                           static_cast<const __nv_bfloat16 *>(dP), arr[0]);
+    for (int kx = 0; kx < 3; ++kx)
+        k_stage_kmajor<<<sgrid, 256, 0, st>>>(h, w, channels, g.wp, g.Q, kx - 1,
+                                               static_cast<const __nv_bfloat16 *>(X), arr[1 + kx]);
+    CUtensorMap tm[4];
+    for (int k = 0; k < 4; ++k) {
+        const cuuint64_t dims[2] = {(cuuint64_t)g.Q, (cuuint64_t)channels};
+        const cuuint64_t strides[1] = {(cuuint64_t)g.Q * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)kBK, 128u};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&tm[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, arr[k], dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return fwi::record_error(FWI_ERR_CUDA, "tensor map of the staged operands rejected");
+    }
+    WgradTcArgs a;
+    a.wait_ns = kWaitNs;
+    a.C = channels;
+    a.cbs = g.cbs;
+    a.wp = g.wp;
+    a.units = g.units;
+    a.pairs = g.pairs;
+    a.jobs = g.jobs;
+    a.kblocks = g.kblocks;
+    a.per_split = (g.kblocks + splits - 1) / splits;
+    a.out = splits > 1 ? work : dW;
+    a.status = status;
+    const size_t smem = (size_t)kGStages * (kGABytes + kGBBytes) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess) {
+        k_wgrad_tc<<<(unsigned)(g.jobs * splits), kThreads, smem, st>>>(tm[0], tm[1], tm[2], tm[3],
+                                                                         a);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && splits > 1) {
+        const size_t nw = (size_t)9 * channels * channels;
+        k_wgrad_tc_reduce<<<(unsigned)((nw + 255) / 256 < 1216 ? (nw + 255) / 256 : 1216), 256, 0,
+                            st>>>(nw, splits, work, dW);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return fwi::record_error(FWI_ERR_CUDA, "fwi_conv3x3_wgrad_tc launch: %s",
+                                 cudaGetErrorString(e));
+    return FWI_OK;
 }
 
 }  // extern "C"

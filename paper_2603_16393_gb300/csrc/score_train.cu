@@ -194,8 +194,10 @@ __global__ void __launch_bounds__(kThreads)
     if (threadIdx.x == 0) db[c] = red[0];
 }
 
+// 1 - b1 and 1 - b2 formed in double on the host: 1 - (float)0.999 in float
+// would be off by 1.3e-5 relative
 struct AdamF {
-    float lr, b1, b2, eps, c1, c2;   // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
+    float lr, b1, b2, omb1, omb2, eps, c1, c2;   // c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t)
 };
 
 __global__ void __launch_bounds__(kThreads)
@@ -205,8 +207,8 @@ __global__ void __launch_bounds__(kThreads)
     for (size_t e = (size_t)blockIdx.x * kThreads + threadIdx.x; e < n;
          e += (size_t)gridDim.x * kThreads) {
         const float ge = g[e];
-        const float me = fmaf(k.b1, m[e], (1.f - k.b1) * ge);
-        const float ve = fmaf(k.b2, v[e], (1.f - k.b2) * ge * ge);
+        const float me = fmaf(k.b1, m[e], k.omb1 * ge);
+        const float ve = fmaf(k.b2, v[e], k.omb2 * ge * ge);
         m[e] = me;
         v[e] = ve;
         p[e] -= k.lr * (me * k.c1) / (sqrtf(ve * k.c2) + k.eps);
@@ -341,7 +343,8 @@ fwi_status fwi_adam_step(long long n, double lr, double beta1, double beta2, dou
     if (n < 1 || step < 1 || !(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) ||
         !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || !param || !grad || !m || !v)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "invalid Adam arguments");
-    AdamF k{(float)lr, (float)beta1, (float)beta2, (float)eps,
+    AdamF k{(float)lr, (float)beta1, (float)beta2, (float)(1.0 - beta1), (float)(1.0 - beta2),
+            (float)eps,
             (float)(1.0 / (1.0 - std::pow(beta1, step))),
             (float)(1.0 / (1.0 - std::pow(beta2, step)))};
     k_adam<<<grid_for((size_t)n), kThreads, 0, (cudaStream_t)stream>>>((size_t)n, k, param, grad,

@@ -150,19 +150,26 @@ class ConvScore:
         return out
 
     def param_grads(self, g: torch.Tensor, i: int, grads, work: torch.Tensor | None = None,
-                    stream=None):
+                    stage: torch.Tensor | None = None, stream=None):
         """The gradient of <eps(x, i), g> with respect to every (W, b, E),
         written into ``grads`` (layer_views of a flat buffer), at the x of the
         last eps() call: per layer the weight gradient from the layer's input
         and its output gradient (fwi_conv3x3_wgrad), the bias gradient
         (fwi_channel_sum) and E's (fwi_time_bias_grad), then the output
         gradient of the layer below as in eps_vjp.  ``work``: float32 scratch
-        for the weight gradient's partial sums (see api.fwi_conv3x3_wgrad)."""
+        for the weight gradient's partial sums; with ``stage`` (the K-major
+        staging buffer, channels a multiple of 128) the weight gradient runs on
+        the tensor cores (api.fwi_conv3x3_wgrad_tc), else on the CUDA cores
+        (api.fwi_conv3x3_wgrad)."""
         api.fwi_pack_channel0(g.contiguous(), self.dH[0], 1.0, stream)
         d, k = self.dH[0], 0
         for l in range(self.L - 1, -1, -1):
             dW, db, dE = grads[l]
-            api.fwi_conv3x3_wgrad(self.X0 if l == 0 else self.A[l - 1], d, dW, work, stream)
+            src = self.X0 if l == 0 else self.A[l - 1]
+            if stage is not None:
+                api.fwi_conv3x3_wgrad_tc(src, d, dW, stage, work, stream=stream)
+            else:
+                api.fwi_conv3x3_wgrad(src, d, dW, work, stream)
             api.fwi_channel_sum(d, db, stream)
             api.fwi_time_bias_grad(db, self.phi[i], dE, stream)
             if l > 0:
@@ -206,6 +213,11 @@ class DSMTrainer:
         self.g = torch.empty(net.shape, **f32)
         self.loss = torch.empty((1,), **f32)
         self.work = torch.empty(api.WGRAD_MAX_SPLITS * 9 * net.C * net.C, **f32)
+        # the K-major staging buffer of the tensor-core weight gradient
+        self.stage = None
+        if net.C % 128 == 0:
+            nbytes = api.fwi_conv3x3_wgrad_tc_stage_bytes(*net.shape, net.C)
+            self.stage = torch.empty(nbytes, dtype=torch.uint8, device=net.dev)
         self.k = 0
 
     def gradients(self, x0: torch.Tensor, z: torch.Tensor, t: int, stream=None) -> torch.Tensor:
@@ -218,7 +230,7 @@ class DSMTrainer:
         api.fwi_dsm_noisy(x0, z, net.abar[t], self.xt, stream)
         net.eps(self.xt, t, 1.0, self.e, stream)
         api.fwi_dsm_loss(self.e, z, self.loss, self.g, stream)
-        net.param_grads(self.g, t, self.grads, self.work, stream)
+        net.param_grads(self.g, t, self.grads, self.work, self.stage, stream)
         return self.loss
 
     def step(self, x0: torch.Tensor, z: torch.Tensor, t: int, stream=None) -> torch.Tensor:

@@ -78,7 +78,42 @@ def test_weight_gradient_and_channel_sum(mods, n, h, w, c, use_work):
     assert torch.equal(dW, dW2)
 
 
-def test_weight_gradient_sampled_at_the_benchmark_size(mods):
+# (1, 2, 70): 5 blocks of 64 padded pixels; room for 4 ranges, 3 used (2, 2, 1)
+@pytest.mark.parametrize("n,h,w,c,splits", [(2, 33, 47, 128, 32), (2, 33, 47, 128, 0),
+                                            (1, 9, 13, 256, 32), (3, 5, 70, 128, 32),
+                                            (1, 2, 70, 128, 4)])
+def test_weight_gradient_on_the_tensor_cores(mods, n, h, w, c, splits):
+    A, _ = mods
+    rng = np.random.default_rng(n * 7 + c + w)
+    x, dp = _bf16_pair(rng, (n, h, w, c))
+    X, dP = BF(x), BF(dp)
+    dW = torch.empty((c, 3, 3, c), dtype=torch.float32, device=DEV)
+    stage = torch.empty(A.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, c), dtype=torch.uint8,
+                        device=DEV)
+    work = torch.empty(splits * 9 * c * c, dtype=torch.float32, device=DEV) if splits else None
+    if splits == 4:
+        assert A.fwi_conv3x3_wgrad_tc_splits(n, h, w, c, work.numel()) == 3
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    dW.fill_(float("nan"))
+    A.fwi_conv3x3_wgrad_tc(X, dP, dW, stage, work, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = T.conv3x3_wgrad(x, dp)
+    # exact bf16 products, FP32 accumulation in an order the hardware picks
+    # along the padded pixels Q, then the splits
+    wp = (w + 2 + 7) // 8 * 8
+    Q = n * (h + 2) * wp
+    scale = T.conv3x3_wgrad(np.abs(x), np.abs(dp))
+    err = np.abs(H(dW) - ref)
+    assert np.all(err <= 2 * (Q + 64) * U32 * scale + 1e-30), err.max()
+    assert rel_l2(H(dW), ref) < 1e-5
+    dW2 = torch.empty_like(dW)
+    A.fwi_conv3x3_wgrad_tc(X, dP, dW2, stage, work, status)
+    assert torch.equal(dW, dW2)
+
+
+@pytest.mark.parametrize("impl", ["cuda_cores", "tensor_cores"])
+def test_weight_gradient_sampled_at_the_benchmark_size(mods, impl):
     """152 models of 70 x 70 at 128 channels (the training benchmark's batch),
     16 pixel ranges: sampled outputs summed one by one in FP64."""
     A, _ = mods
@@ -92,8 +127,16 @@ def test_weight_gradient_sampled_at_the_benchmark_size(mods):
     xb, pb = X.float().cpu().numpy(), dP.float().cpu().numpy()      # the bf16 values, exact
     dW = torch.empty((c, 3, 3, c), dtype=torch.float32, device=DEV)
     work = torch.empty(A.WGRAD_MAX_SPLITS * 9 * c * c, dtype=torch.float32, device=DEV)
-    assert A.fwi_conv3x3_wgrad_splits(n, h, w, c, work.numel()) > 1
-    A.fwi_conv3x3_wgrad(X, dP, dW, work)
+    if impl == "cuda_cores":
+        assert A.fwi_conv3x3_wgrad_splits(n, h, w, c, work.numel()) > 1
+        A.fwi_conv3x3_wgrad(X, dP, dW, work)
+        chain = n * h * w + 16
+    else:
+        assert A.fwi_conv3x3_wgrad_tc_splits(n, h, w, c, work.numel()) > 1
+        stage = torch.empty(A.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, c), dtype=torch.uint8,
+                            device=DEV)
+        A.fwi_conv3x3_wgrad_tc(X, dP, dW, stage, work)
+        chain = 2 * (n * (h + 2) * 72 + 64)
     torch.cuda.synchronize()
     got = H(dW)
     for co, ky, kx, ci in [(0, 0, 0, 0), (127, 2, 2, 127), (5, 1, 1, 77), (64, 0, 2, 3),
@@ -103,7 +146,7 @@ def test_weight_gradient_sampled_at_the_benchmark_size(mods):
         a = pb[..., co].astype(np.float64).ravel()
         b = xs[:, ky:ky + h, kx:kx + w].ravel()
         ref = float(a @ b)
-        bound = (n * h * w + 16) * U32 * float(np.abs(a) @ np.abs(b))
+        bound = chain * U32 * float(np.abs(a) @ np.abs(b))
         assert abs(got[co, ky, kx, ci] - ref) <= bound, (co, ky, kx, ci)
 
 
@@ -173,13 +216,15 @@ def test_adam_weight_prep_and_time_bias(mods):
     np.testing.assert_allclose(H(dE), np.outer(H(db), phi[700]), rtol=U32, atol=0)
 
 
-def test_minibatch_gradients_match_oracle(mods):
+@pytest.mark.parametrize("c", [64, 128])     # 128: the tensor-core weight gradient
+def test_minibatch_gradients_match_oracle(mods, c):
     A, SN = mods
-    B, nz, nx, c = 2, 33, 47, 64
+    B, nz, nx = 2, 33, 47
     betas = D.linear_betas(1000)
     w = SN.seeded_weights(c, 3, seed=7)
     net = SN.ConvScore((B, nz, nx), betas, weights=w)
     tr = SN.DSMTrainer(net)
+    assert (tr.stage is not None) == (c % 128 == 0)
     rng = np.random.default_rng(8)
     x0 = rng.standard_normal((B, nz, nx)).astype(np.float32).astype(np.float64)
     z = rng.standard_normal((B, nz, nx)).astype(np.float32).astype(np.float64)

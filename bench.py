@@ -938,7 +938,9 @@ def run_dsm_train(args, rank, world, local_rank):
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flops x {f_mhz:.0f} MHz",
                 "splits": splits, "traffic": None}
         per_layer = 1 + (1 if splits > 1 else 0)
-    launches = 1 + (2 + L + (L - 1)) + 1 + (1 + (per_layer + 2) * L + 2 * (L - 1)) + 1 + 2 * L
+    # x_t; forward; loss (+ ordered sum); per layer the weight gradient, the
+    # channel sum (+ ordered sum) and dE, the data gradients; Adam; refresh
+    launches = 1 + (2 + L + (L - 1)) + 2 + (1 + (per_layer + 3) * L + 2 * (L - 1)) + 1 + 2 * L
     line = {
         "metric": f"DSM training images/s ({n} x 70x70, {L} conv layers x {c} channels)",
         "value": world * n * 1e3 / ms, "unit": "images/s", "n_gpus": world, "steps": args.steps,

@@ -451,10 +451,12 @@ FWI_API fwi_status fwi_conv3x3_bf16_wait_check(int n, int h, int w, int cin, int
 FWI_API fwi_status fwi_dsm_noisy(long long n, double abar, const float *x0, const float *z,
                                  float *xt, void *stream);
 
-/* *loss = mean over n of (eps - z)^2 (one device float, a fixed-order sum)
- * and grad = d loss / d eps = 2 (eps - z) / n. */
+/* *loss = mean over n of (eps - z)^2 (one device float) and grad = d loss /
+ * d eps = 2 (eps - z) / n.  The sum runs over per-CTA partials written to
+ * `work` (up to 608 of them, work_floats floats, caller-owned; NULL: one CTA)
+ * and added in order: a fixed summation order for given n and work_floats. */
 FWI_API fwi_status fwi_dsm_loss(long long n, const float *eps, const float *z, float *loss,
-                                float *grad, void *stream);
+                                float *grad, float *work, long long work_floats, void *stream);
 
 /* Weight gradient of the 3x3 convolution (stride 1, zero padding 1):
  * dW[co][ky][kx][ci] = sum_{b,y,x} dP[b][y][x][co] X[b][y+ky-1][x+kx-1][ci],
@@ -495,9 +497,12 @@ FWI_API long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int chan
  * work_floats / (9 channels^2); 0 for invalid sizes. */
 FWI_API int fwi_conv3x3_wgrad_tc_splits(int n, int h, int w, int channels, long long work_floats);
 
-/* db[c] = sum_p dP[p][c] over npix pixels (dP bf16 [npix][channels]). */
+/* db[c] = sum_p dP[p][c] over npix pixels (dP bf16 [npix][channels]): the
+ * pixels split into up to 4 x SM-count ranges whose partial sums go to `work`
+ * (work_floats / channels ranges at most; NULL: one range) and are added in
+ * range order. */
 FWI_API fwi_status fwi_channel_sum(long long npix, int channels, const void *dP, float *db,
-                                   void *stream);
+                                   float *work, long long work_floats, void *stream);
 
 /* One Adam step (step >= 1) on n float32 parameters: m = b1 m + (1 - b1) g,
  * v = b2 v + (1 - b2) g^2, p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */

@@ -154,7 +154,7 @@ _lib.fwi_forward_wait_check.argtypes = [_vp] * 6
 _lib.fwi_dsm_noisy.restype = _S
 _lib.fwi_dsm_noisy.argtypes = [ctypes.c_longlong, ctypes.c_double, _vp, _vp, _vp, _vp]
 _lib.fwi_dsm_loss.restype = _S
-_lib.fwi_dsm_loss.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp]
+_lib.fwi_dsm_loss.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, ctypes.c_longlong, _vp]
 _lib.fwi_conv3x3_wgrad.restype = _S
 _lib.fwi_conv3x3_wgrad.argtypes = [ctypes.c_int] * 4 + [_vp, _vp, _vp, _vp, ctypes.c_longlong,
                                                          _vp]
@@ -168,7 +168,8 @@ _lib.fwi_conv3x3_wgrad_tc_splits.argtypes = [ctypes.c_int] * 4 + [ctypes.c_longl
 _lib.fwi_conv3x3_wgrad_splits.restype = ctypes.c_int
 _lib.fwi_conv3x3_wgrad_splits.argtypes = [ctypes.c_int] * 4 + [ctypes.c_longlong]
 _lib.fwi_channel_sum.restype = _S
-_lib.fwi_channel_sum.argtypes = [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp]
+_lib.fwi_channel_sum.argtypes = [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, ctypes.c_longlong,
+                                 _vp]
 _lib.fwi_adam_step.restype = _S
 _lib.fwi_adam_step.argtypes = [ctypes.c_longlong] + [ctypes.c_double] * 4 + [ctypes.c_int] + \
     [_vp] * 5
@@ -591,8 +592,17 @@ def fwi_dsm_noisy(x0, z, abar, xt, stream=None):
                               _stream(stream)))
 
 
-def fwi_dsm_loss(eps, z, loss, grad, stream=None):
-    _check(_lib.fwi_dsm_loss(eps.numel(), _ptr(eps), _ptr(z), _ptr(loss), _ptr(grad),
+def _work(work):
+    if work is None:
+        return None, 0
+    if work.dtype != torch.float32 or not work.is_contiguous():
+        raise ValueError("work must be a contiguous float32 tensor")
+    return _ptr(work), work.numel()
+
+
+def fwi_dsm_loss(eps, z, loss, grad, work=None, stream=None):
+    wp, wf = _work(work)
+    _check(_lib.fwi_dsm_loss(eps.numel(), _ptr(eps), _ptr(z), _ptr(loss), _ptr(grad), wp, wf,
                              _stream(stream)))
 
 
@@ -646,10 +656,11 @@ def fwi_conv3x3_wgrad_tc(X, dP, dW, stage, work=None, status=None, stream=None):
                                      _ptr(status), _stream(stream)))
 
 
-def fwi_channel_sum(dP, db, stream=None):
+def fwi_channel_sum(dP, db, work=None, stream=None):
     c = dP.shape[-1]
     _f32(db, (c,), "db")
-    _check(_lib.fwi_channel_sum(dP.numel() // c, c, _ptr(dP), _ptr(db), _stream(stream)))
+    wp, wf = _work(work)
+    _check(_lib.fwi_channel_sum(dP.numel() // c, c, _ptr(dP), _ptr(db), wp, wf, _stream(stream)))
 
 
 def fwi_adam_step(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

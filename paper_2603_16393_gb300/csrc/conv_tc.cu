@@ -777,6 +777,45 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// the three shifted copies of X at once: out_k[c][q] = Xpad(q + k - 1), k = 0, 1, 2,
+// from one 66-row tile (q0 - 1 .. q0 + 64) read once
+__global__ void __launch_bounds__(256)
+    k_stage_kmajor3(int h, int w, int C, int wp, long long Q, const __nv_bfloat16 *__restrict__ in,
+                    __nv_bfloat16 *__restrict__ out0, __nv_bfloat16 *__restrict__ out1,
+                    __nv_bfloat16 *__restrict__ out2)
+{
+    __shared__ __align__(16) __nv_bfloat16 tile[66][72];
+    const long long q0 = (long long)blockIdx.x * 64;
+    const int c0 = blockIdx.y * 64;
+    const long long img = (long long)(h + 2) * wp;
+    for (int e = threadIdx.x; e < 66 * 8; e += 256) {
+        const int ql = e >> 3, j = e & 7;
+        const long long p = q0 - 1 + ql;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (p >= 0 && p < Q) {
+            const long long b = p / img;
+            const int r = (int)(p - b * img);
+            const int yy = r / wp, xx = r - (r / wp) * wp;
+            if (yy >= 1 && yy <= h && xx >= 1 && xx <= w)
+                v = *reinterpret_cast<const uint4 *>(
+                    in + ((b * h + (yy - 1)) * (long long)w + (xx - 1)) * C + c0 + 8 * j);
+        }
+        *reinterpret_cast<uint4 *>(&tile[ql][8 * j]) = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 3 * 512; e += 256) {
+        const int k = e / 512, f = e % 512;
+        const int cl = f & 63, j = f >> 6;
+        if (q0 + 8 * j >= Q) continue;
+        __nv_bfloat16 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = tile[8 * j + i + k][cl];
+        __nv_bfloat16 *out = k == 0 ? out0 : (k == 1 ? out1 : out2);
+        *reinterpret_cast<uint4 *>(out + (size_t)(c0 + cl) * Q + q0 + 8 * j) =
+            *reinterpret_cast<uint4 *>(v);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_wgrad_tc(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb0,
                const __grid_constant__ CUtensorMap tmb1, const __grid_constant__ CUtensorMap tmb2,
@@ -1088,9 +1127,9 @@ fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int channels, const void *X
     const dim3 sgrid((unsigned)((g.Q + 63) / 64), (unsigned)(channels / 64));
     k_stage_kmajor<<<sgrid, 256, 0, st>>>(h, w, channels, g.wp, g.Q, 0,
                                            static_cast<const __nv_bfloat16 *>(dP), arr[0]);
-    for (int kx = 0; kx < 3; ++kx)
-        k_stage_kmajor<<<sgrid, 256, 0, st>>>(h, w, channels, g.wp, g.Q, kx - 1,
-                                               static_cast<const __nv_bfloat16 *>(X), arr[1 + kx]);
+    k_stage_kmajor3<<<sgrid, 256, 0, st>>>(h, w, channels, g.wp, g.Q,
+                                            static_cast<const __nv_bfloat16 *>(X), arr[1], arr[2],
+                                            arr[3]);
     CUtensorMap tm[4];
     for (int k = 0; k < 4; ++k) {
         const cuuint64_t dims[2] = {(cuuint64_t)g.Q, (cuuint64_t)channels};

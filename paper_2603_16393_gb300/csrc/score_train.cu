@@ -4,13 +4,14 @@
 // abar), so matching s = -eps / sqrt(1 - abar) to it with the weight
 // kappa(t) = 1 - abar is the regression of eps(x_t, t) on z.  Pieces:
 //   k_noisy:      x_t = sqrt(abar) x_0 + sqrt(1 - abar) z
-//   k_dsm:        loss = mean (eps - z)^2 (fixed-order reduction) and
-//                 d loss / d eps = 2 (eps - z) / N
+//   k_dsm:        loss = mean (eps - z)^2 (per-CTA partials added in order by
+//                 k_dsm_final) and d loss / d eps = 2 (eps - z) / N
 //   k_wgrad:      dW[co][ky][kx][ci] = sum_{b,p} dP[b][p][co] X[b][p + (ky-1, kx-1)][ci]
 //                 (X zero outside the image), 64 x 64 (co, ci) tiles of one tap
 //                 over a split of the pixels, the splits then summed in order
 //                 (k_wgrad_reduce): a fixed summation order for a given split count
-//   k_colsum:     db[c] = sum_p dP[p][c]
+//   k_colsum:     db[c] = sum_p dP[p][c] (coalesced per-range partials added in
+//                 order by k_colsum_final)
 //   k_adam:       Adam on float32 parameters (bias-corrected moments)
 //   k_wprep:      bf16 weights W and the transposed W^T[ci][ky][kx][co] =
 //                 W[co][2-ky][2-kx][ci] for the backward pass, from float32
@@ -49,27 +50,47 @@ __global__ void __launch_bounds__(kThreads)
         xt[e] = fmaf(sa, x0[e], s1 * z[e]);
 }
 
-// one CTA: the loss sum in a fixed order (thread-strided partial sums, then a
-// tree over the block) and the gradient elementwise
+// the loss in a fixed order: CTA k sums the elements e = k 256 + t (mod G 256)
+// thread-wise, then over its threads in a tree, into part[k]; k_dsm_final adds
+// the G partials in order.  The gradient is elementwise.
+constexpr int kLossCtas = 608;
 __global__ void __launch_bounds__(kThreads)
     k_dsm(size_t n, const float *__restrict__ eps, const float *__restrict__ z,
-          float *__restrict__ loss, float *__restrict__ grad)
+          float *__restrict__ part, float *__restrict__ grad)
 {
     __shared__ float red[kThreads];
     const float inv = 1.f / (float)n;
-    float part = 0.f;
-    for (size_t e = threadIdx.x; e < n; e += kThreads) {
+    float acc = 0.f;
+    for (size_t e = (size_t)blockIdx.x * kThreads + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * kThreads) {
         const float d = eps[e] - z[e];
-        part = fmaf(d, d, part);
+        acc = fmaf(d, d, acc);
         grad[e] = 2.f * d * inv;
     }
-    red[threadIdx.x] = part;
+    red[threadIdx.x] = acc;
     __syncthreads();
     for (int s = kThreads / 2; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *loss = red[0] * inv;
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// thread t adds the partials t, t + 256, ... in order, then the block adds the
+// 256 sums in a fixed tree
+__global__ void __launch_bounds__(kThreads)
+    k_dsm_final(int parts, size_t n, const float *__restrict__ part, float *__restrict__ loss)
+{
+    __shared__ float red[kThreads];
+    float acc = 0.f;
+    for (int k = threadIdx.x; k < parts; k += kThreads) acc += part[k];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0] / (float)n;
 }
 
 // CTA (tap, co tile, ci tile, pixel split): a 64 x 64 (co, ci) tile of one tap
@@ -177,21 +198,57 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// one CTA per channel: fixed-order sum over the pixels
+// db[c] = sum_p dP[p][c]: CTA k sums the pixels of range k, its threads laid
+// out as `lanes` pixel lanes x channels (consecutive threads read consecutive
+// channels of one pixel), the lanes then added in order into part[k][c];
+// k_colsum_final adds the ranges in order.
 __global__ void __launch_bounds__(kThreads)
-    k_colsum(long long npix, int C, const __nv_bfloat16 *__restrict__ dP, float *__restrict__ db)
+    k_colsum(long long npix, int C, int lanes, long long per, const __nv_bfloat16 *__restrict__ dP,
+             float *__restrict__ part)
 {
     __shared__ float red[kThreads];
-    const int c = blockIdx.x;
-    float part = 0.f;
-    for (long long p = threadIdx.x; p < npix; p += kThreads) part += __bfloat162float(dP[p * C + c]);
-    red[threadIdx.x] = part;
-    __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    const int lane = threadIdx.x / C, c = threadIdx.x % C;
+    const long long p0 = (long long)blockIdx.x * per;
+    const long long p1 = p0 + per < npix ? p0 + per : npix;
+    for (int c0 = 0; c0 < C; c0 += kThreads) {
+        // C > 256: one lane, channel blocks of 256
+        const int cc = lanes > 1 ? c : c0 + (int)threadIdx.x;
+        float acc = 0.f;
+        if (lane < lanes && cc < C)
+            for (long long p = p0 + lane; p < p1; p += lanes) acc += __bfloat162float(dP[p * C + cc]);
+        red[threadIdx.x] = acc;
         __syncthreads();
+        if (lanes > 1) {
+            if ((int)threadIdx.x < C) {
+                float s2 = red[threadIdx.x];
+                for (int l = 1; l < lanes; ++l) s2 += red[l * C + threadIdx.x];
+                part[(size_t)blockIdx.x * C + threadIdx.x] = s2;
+            }
+        } else if (cc < C) {
+            part[(size_t)blockIdx.x * C + cc] = red[threadIdx.x];
+        }
+        __syncthreads();
+        if (lanes > 1) break;
     }
-    if (threadIdx.x == 0) db[c] = red[0];
+}
+
+// CTA: 32 channels x 8 groups; group g adds the ranges g, g + 8, ... in order,
+// then the 8 group sums are added in order
+__global__ void __launch_bounds__(kThreads)
+    k_colsum_final(int parts, int C, const float *__restrict__ part, float *__restrict__ db)
+{
+    __shared__ float red[8][32];
+    const int g = threadIdx.x / 32, c = blockIdx.x * 32 + threadIdx.x % 32;
+    float acc = 0.f;
+    if (c < C)
+        for (int k = g; k < parts; k += 8) acc += part[(size_t)k * C + c];
+    red[g][threadIdx.x % 32] = acc;
+    __syncthreads();
+    if (g == 0 && c < C) {
+        float s2 = red[0][threadIdx.x];
+        for (int k = 1; k < 8; ++k) s2 += red[k][threadIdx.x];
+        db[c] = s2;
+    }
 }
 
 // 1 - b1 and 1 - b2 formed in double on the host: 1 - (float)0.999 in float
@@ -279,11 +336,19 @@ fwi_status fwi_dsm_noisy(long long n, double abar, const float *x0, const float 
 }
 
 fwi_status fwi_dsm_loss(long long n, const float *eps, const float *z, float *loss, float *grad,
-                        void *stream)
+                        float *work, long long work_floats, void *stream)
 {
     if (n < 1 || !eps || !z || !loss || !grad)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "n >= 1 and arrays needed");
-    k_dsm<<<1, kThreads, 0, (cudaStream_t)stream>>>((size_t)n, eps, z, loss, grad);
+    cudaStream_t st = (cudaStream_t)stream;
+    // without room for the partials: one CTA, its partial written to loss
+    long long g = work ? (work_floats < kLossCtas ? work_floats : kLossCtas) : 1;
+    const long long need = ((long long)n + kThreads - 1) / kThreads;
+    if (g > need) g = need;
+    if (g < 1) g = 1;
+    float *part = g > 1 ? work : loss;
+    k_dsm<<<(unsigned)g, kThreads, 0, st>>>((size_t)n, eps, z, part, grad);
+    k_dsm_final<<<1, kThreads, 0, st>>>((int)g, (size_t)n, part, loss);
     return done("fwi_dsm_loss");
 }
 
@@ -328,12 +393,31 @@ fwi_status fwi_conv3x3_wgrad(int n, int h, int w, int channels, const void *X, c
     return done("fwi_conv3x3_wgrad");
 }
 
-fwi_status fwi_channel_sum(long long npix, int channels, const void *dP, float *db, void *stream)
+fwi_status fwi_channel_sum(long long npix, int channels, const void *dP, float *db, float *work,
+                           long long work_floats, void *stream)
 {
     if (npix < 1 || channels < 1 || !dP || !db)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "npix, channels >= 1 and arrays needed");
-    k_colsum<<<channels, kThreads, 0, (cudaStream_t)stream>>>(
-        npix, channels, static_cast<const __nv_bfloat16 *>(dP), db);
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int lanes = channels <= kThreads && kThreads % channels == 0 ? kThreads / channels : 1;
+    long long parts = work ? work_floats / channels : 0;
+    if (parts > 4LL * sms) parts = 4LL * sms;
+    if (parts > npix) parts = npix;
+    float *part = work;
+    if (parts < 2) {
+        // one range: its partial is the result
+        parts = 1;
+        part = db;
+    }
+    const long long per = (npix + parts - 1) / parts;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_colsum<<<(unsigned)parts, kThreads, 0, st>>>(npix, channels, lanes, per,
+                                                  static_cast<const __nv_bfloat16 *>(dP), part);
+    if (parts > 1)
+        k_colsum_final<<<(unsigned)((channels + 31) / 32), kThreads, 0, st>>>((int)parts, channels,
+                                                                              part, db);
     return done("fwi_channel_sum");
 }
 

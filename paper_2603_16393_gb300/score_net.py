@@ -170,7 +170,7 @@ class ConvScore:
                 api.fwi_conv3x3_wgrad_tc(src, d, dW, stage, work, stream=stream)
             else:
                 api.fwi_conv3x3_wgrad(src, d, dW, work, stream)
-            api.fwi_channel_sum(d, db, stream)
+            api.fwi_channel_sum(d, db, work, stream)
             api.fwi_time_bias_grad(db, self.phi[i], dE, stream)
             if l > 0:
                 nxt = self.dH[1 - k]
@@ -229,7 +229,7 @@ class DSMTrainer:
         api._f32(z, net.shape, "z")
         api.fwi_dsm_noisy(x0, z, net.abar[t], self.xt, stream)
         net.eps(self.xt, t, 1.0, self.e, stream)
-        api.fwi_dsm_loss(self.e, z, self.loss, self.g, stream)
+        api.fwi_dsm_loss(self.e, z, self.loss, self.g, self.work, stream)
         net.param_grads(self.g, t, self.grads, self.work, self.stage, stream)
         return self.loss
 

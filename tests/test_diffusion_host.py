@@ -130,11 +130,11 @@ def test_training_calls_reject_bad_arguments_without_a_gpu(api):
     calls = [
         lambda: lib.fwi_dsm_noisy(4, 1.0, p, p, p, None),             # abar must be < 1
         lambda: lib.fwi_dsm_noisy(4, 0.5, None, p, p, None),
-        lambda: lib.fwi_dsm_loss(0, p, p, p, p, None),
+        lambda: lib.fwi_dsm_loss(0, p, p, p, p, None, 0, None),
         lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 96, p, p, p, None, 0, None),   # channels % 64
         lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, p, None, p, None, 0, None),
         lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, ctypes.c_void_p(4100), p, p, None, 0, None),
-        lambda: lib.fwi_channel_sum(16, 0, p, p, None),
+        lambda: lib.fwi_channel_sum(16, 0, p, p, None, 0, None),
         lambda: lib.fwi_adam_step(8, 1e-3, 0.9, 0.999, 1e-8, 0, p, p, p, p, None),   # step >= 1
         lambda: lib.fwi_adam_step(8, 1e-3, 1.0, 0.999, 1e-8, 1, p, p, p, p, None),
         lambda: lib.fwi_adam_step(8, 0.0, 0.9, 0.999, 1e-8, 1, p, p, p, p, None),

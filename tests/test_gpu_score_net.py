@@ -50,15 +50,17 @@ def test_elementwise_kernels(mods):
     y = torch.empty((2, 5, 7), device=DEV)
     A.fwi_unpack_channel0(Y, y, -3.0)
     np.testing.assert_array_equal(H(y), (-3.0 * Y[..., 0].cpu().numpy()).astype(np.float64))
-    p = torch.tensor(8 * rng.standard_normal(4096), dtype=torch.float32).to(torch.bfloat16)
-    da = torch.tensor(rng.standard_normal(4096), dtype=torch.float32).to(torch.bfloat16)
-    a, dp = torch.empty_like(p, device=DEV), torch.empty_like(p, device=DEV)
-    A.fwi_silu_bf16(p.to(DEV), a)
-    A.fwi_silu_grad_bf16(da.to(DEV), p.to(DEV), dp)
-    ph, dah = p.double().numpy(), da.double().numpy()
-    for got, ref in ((a, N.bf16(N.silu(ph))), (dp, N.bf16(dah * N.silu_grad(ph)))):
-        err = np.abs(got.double().cpu().numpy() - ref)
-        assert np.all(err <= BF16_ULP * np.abs(ref) + 1e-30)
+    # 4096: eight elements per thread (16-byte accesses); 4093: one per thread
+    for m in (4096, 4093):
+        p = torch.tensor(8 * rng.standard_normal(m), dtype=torch.float32).to(torch.bfloat16)
+        da = torch.tensor(rng.standard_normal(m), dtype=torch.float32).to(torch.bfloat16)
+        a, dp = torch.empty_like(p, device=DEV), torch.empty_like(p, device=DEV)
+        A.fwi_silu_bf16(p.to(DEV), a)
+        A.fwi_silu_grad_bf16(da.to(DEV), p.to(DEV), dp)
+        ph, dah = p.double().numpy(), da.double().numpy()
+        for got, ref in ((a, N.bf16(N.silu(ph))), (dp, N.bf16(dah * N.silu_grad(ph)))):
+            err = np.abs(got.double().cpu().numpy() - ref)
+            assert np.all(err <= BF16_ULP * np.abs(ref) + 1e-30)
 
 
 @pytest.mark.parametrize("channels", [64, 128])

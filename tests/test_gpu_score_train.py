@@ -59,7 +59,7 @@ def test_weight_gradient_and_channel_sum(mods, n, h, w, c, use_work):
     X, dP = BF(x), BF(dp)
     A.fwi_conv3x3_wgrad(X, dP, dW, work)
     db = torch.empty(c, dtype=torch.float32, device=DEV)
-    A.fwi_channel_sum(dP, db)
+    A.fwi_channel_sum(dP, db, work)
     torch.cuda.synchronize()
     ref = T.conv3x3_wgrad(x, dp)
     # a float32 sum of exact bf16 x bf16 products: |err| <= m u sum|terms|,
@@ -71,7 +71,8 @@ def test_weight_gradient_and_channel_sum(mods, n, h, w, c, use_work):
     # the transposed-operand mistake would show: the tap read at (y-1, x-1)
     assert rel_l2(H(dW), ref) < 1e-5
     err_b = np.abs(H(db) - T.channel_sum(dp))
-    assert np.all(err_b <= npix * U32 * T.channel_sum(np.abs(dp)) + 1e-30)
+    # chain: a range's pixels per lane, the lanes, the ranges
+    assert np.all(err_b <= (npix + 1024) * U32 * T.channel_sum(np.abs(dp)) + 1e-30)
     # a fixed summation order: a second launch is bit-identical
     dW2 = torch.empty_like(dW)
     A.fwi_conv3x3_wgrad(X, dP, dW2, work)
@@ -164,10 +165,11 @@ def test_dsm_noisy_and_loss(mods):
     assert np.all(np.abs(H(xt) - ref) <= 3 * U32 * mag)
     loss = torch.empty(1, dtype=torch.float32, device=DEV)
     g = torch.empty(shape, dtype=torch.float32, device=DEV)
-    A.fwi_dsm_loss(F(eps), F(z), loss, g)
-    torch.cuda.synchronize()
     l_ref, g_ref = T.dsm_loss(eps, z)
-    assert abs(float(loss.item()) - l_ref) <= 1e-5 * l_ref
+    for work in (None, torch.empty(1024, dtype=torch.float32, device=DEV)):
+        A.fwi_dsm_loss(F(eps), F(z), loss, g, work)
+        torch.cuda.synchronize()
+        assert abs(float(loss.item()) - l_ref) <= 1e-5 * l_ref
     assert np.all(np.abs(H(g) - g_ref) <= 4 * U32 * (np.abs(eps) + np.abs(z)) * 2 / eps.size)
     A.fwi_dsm_loss(F(z), F(z), loss, g)
     assert float(loss.item()) == 0.0 and not torch.any(g)

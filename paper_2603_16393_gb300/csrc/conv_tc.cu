@@ -740,6 +740,30 @@ struct WgradTcArgs {
     int *status;
 };
 
+// Writes rows c of one 64 x 64 output tile: tT[c][q - q0] = tile[q - q0 + k][c]
+// (a transpose in shared memory, lanes along c: conflict-free 2-byte reads and
+// 16-byte writes at a 144-byte pitch), then out[c][q0 ..] with 8 lanes per
+// 128-byte row, so that a warp stores four whole rows.
+__device__ __forceinline__ void stage_store(const __nv_bfloat16 (*tile)[72], int k,
+                                            __nv_bfloat16 (*tT)[72], long long q0, long long Q,
+                                            __nv_bfloat16 *__restrict__ out)
+{
+    for (int e = threadIdx.x; e < 512; e += 256) {
+        const int cl = e & 63, j = e >> 6;
+        __nv_bfloat16 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = tile[8 * j + i + k][cl];
+        *reinterpret_cast<uint4 *>(&tT[cl][8 * j]) = *reinterpret_cast<uint4 *>(v);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 512; e += 256) {
+        const int cl = e >> 3, j = e & 7;
+        if (q0 + 8 * j < Q)
+            *reinterpret_cast<uint4 *>(out + (size_t)cl * Q + q0 + 8 * j) =
+                *reinterpret_cast<const uint4 *>(&tT[cl][8 * j]);
+    }
+}
+
 // out[c][q] = Xpad(q + shift)[c] for q < Q (0 outside the image and [0, Q)):
 // a 64 (q) x 64 (c) tile per CTA through shared memory, 16-byte loads along c
 // and 16-byte stores along q
@@ -747,7 +771,8 @@ __global__ void __launch_bounds__(256)
     k_stage_kmajor(int h, int w, int C, int wp, long long Q, int shift,
                    const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out)
 {
-    __shared__ __align__(16) __nv_bfloat16 tile[64][72];
+    __shared__ __align__(16) __nv_bfloat16 tile[66][72];
+    __shared__ __align__(16) __nv_bfloat16 tileT[1][64][72];
     const long long q0 = (long long)blockIdx.x * 64;
     const int c0 = blockIdx.y * 64;
     const long long img = (long long)(h + 2) * wp;
@@ -766,25 +791,16 @@ __global__ void __launch_bounds__(256)
         *reinterpret_cast<uint4 *>(&tile[ql][8 * j]) = v;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 512; e += 256) {
-        const int cl = e & 63, j = e >> 6;
-        if (q0 + 8 * j >= Q) continue;
-        __nv_bfloat16 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = tile[8 * j + i][cl];
-        *reinterpret_cast<uint4 *>(out + (size_t)(c0 + cl) * Q + q0 + 8 * j) =
-            *reinterpret_cast<uint4 *>(v);
-    }
+    stage_store(tile, 0, tileT[0], q0, Q, out + (size_t)c0 * Q);
 }
 
-// the three shifted copies of X at once: out_k[c][q] = Xpad(q + k - 1), k = 0, 1, 2,
-// from one 66-row tile (q0 - 1 .. q0 + 64) read once
 __global__ void __launch_bounds__(256)
     k_stage_kmajor3(int h, int w, int C, int wp, long long Q, const __nv_bfloat16 *__restrict__ in,
                     __nv_bfloat16 *__restrict__ out0, __nv_bfloat16 *__restrict__ out1,
                     __nv_bfloat16 *__restrict__ out2)
 {
     __shared__ __align__(16) __nv_bfloat16 tile[66][72];
+    __shared__ __align__(16) __nv_bfloat16 tileT[3][64][72];
     const long long q0 = (long long)blockIdx.x * 64;
     const int c0 = blockIdx.y * 64;
     const long long img = (long long)(h + 2) * wp;
@@ -803,17 +819,9 @@ __global__ void __launch_bounds__(256)
         *reinterpret_cast<uint4 *>(&tile[ql][8 * j]) = v;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 3 * 512; e += 256) {
-        const int k = e / 512, f = e % 512;
-        const int cl = f & 63, j = f >> 6;
-        if (q0 + 8 * j >= Q) continue;
-        __nv_bfloat16 v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = tile[8 * j + i + k][cl];
-        __nv_bfloat16 *out = k == 0 ? out0 : (k == 1 ? out1 : out2);
-        *reinterpret_cast<uint4 *>(out + (size_t)(c0 + cl) * Q + q0 + 8 * j) =
-            *reinterpret_cast<uint4 *>(v);
-    }
+    stage_store(tile, 0, tileT[0], q0, Q, out0 + (size_t)c0 * Q);
+    stage_store(tile, 1, tileT[1], q0, Q, out1 + (size_t)c0 * Q);
+    stage_store(tile, 2, tileT[2], q0, Q, out2 + (size_t)c0 * Q);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)

@@ -618,6 +618,9 @@ def run_sampler(args, rank, world, local_rank):
     if args.score == "conv":
         from paper_2603_16393_gb300 import score_net as SN
         net = SN.ConvScore((B, nz, nx), betas, device=dev)
+    elif args.score == "unet":
+        from paper_2603_16393_gb300 import score_net as SN
+        net = SN.UNetScore((B, nz, nx), betas, device=dev)
     lowfi = S.LowFidelity(plan, d_obs) if frac > 0 else None
     smp = S.Sampler(plan, betas, ctx=ctx, prior=None if net else prior, score_fn=net,
                     guide=api.GuideParams(rho0=1.15, gamma=0.55), surrogate=lowfi,
@@ -867,7 +870,11 @@ def run_dsm_train(args, rank, world, local_rank):
     h = w = 70
     c, L = args.conv_channels, 3
     betas = [float(b) for b in np.linspace(1e-4, 0.02, 1000)]
-    net = SN.ConvScore((n, h, w), betas, channels=c, layers=L, seed=5 + rank, device=dev)
+    unet = args.score == "unet"
+    if unet:
+        net = SN.UNetScore((n, h, w), betas, seed=5 + rank, device=dev)
+    else:
+        net = SN.ConvScore((n, h, w), betas, channels=c, layers=L, seed=5 + rank, device=dev)
     tr = SN.DSMTrainer(net, lr=1e-3)
     gen = torch.Generator(device=dev).manual_seed(13 + rank)
     x0 = 0.3 * torch.randn((n, h, w), device=dev, generator=gen)
@@ -892,6 +899,26 @@ def run_dsm_train(args, rank, world, local_rank):
     ms = a.elapsed_time(b) / args.steps
     loss1 = float(tr.loss.item())
     ms = max_over_ranks([ms], world, dev)[0]
+    if unet:
+        if rank != 0:
+            return
+        flops = 0.0
+        for _, k, ci, co in net.layers:
+            hh, ww = net.sizes[k]
+            flops += 2.0 * n * hh * ww * 9 * ci * co
+        print(json.dumps({
+            "metric": f"DSM training images/s ({n} x 70x70, 4-level U-Net {net.widths})",
+            "value": world * n * 1e3 / ms, "unit": "images/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 activations, fp32 parameters, gradients and Adam",
+            "data": "synthetic (seeded normal models, one seeded t per step)",
+            "config": {"workload": f"{n} x 70x70, U-Net widths {net.widths}, 15 conv layers, "
+                                   "Adam", "conv_tflop_per_step": 3 * flops / 1e12},
+            "loss": {"after_warmup": loss0, "last": loss1},
+            "conv_tflops_per_s": 3 * flops / (ms * 1e-3) / 1e12,
+            "clocks": clk}), flush=True)
+        return
     # the weight gradient alone (layer 1: input A[0], output gradient dH), on
     # the tensor cores (staging + k_wgrad_tc + split reduction) and, for
     # context, on the CUDA cores
@@ -916,7 +943,7 @@ def run_dsm_train(args, rank, world, local_rank):
     flops_w = 2.0 * n * h * w * 9 * c * c
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if tc:
-        splits = api.fwi_conv3x3_wgrad_tc_splits(n, h, w, c, tr.work.numel())
+        splits = api.fwi_conv3x3_wgrad_tc_splits(n, h, w, c, c, tr.work.numel())
         try:
             with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
                 peak, src = float(json.load(f)["bf16_tflops"]), "measured (bf16 burst)"
@@ -929,7 +956,7 @@ def run_dsm_train(args, rank, world, local_rank):
                 "peak_source": src, "splits": splits, "traffic": None}
         per_layer = 4 + 1 + (1 if splits > 1 else 0)
     else:
-        splits = api.fwi_conv3x3_wgrad_splits(n, h, w, c, tr.work.numel())
+        splits = api.fwi_conv3x3_wgrad_splits(n, h, w, c, c, tr.work.numel())
         f_mhz = float((clk or {}).get("sm_max_mhz") or 2070.0)
         peak = sms * 128 * 2 * f_mhz * 1e6 / 1e12        # FP32 FMA: 128 lanes per SM
         ach = flops_w / (ms_cc * 1e-3) / 1e12
@@ -979,8 +1006,9 @@ def main():
     ap.add_argument("--conv", action="store_true",
                     help="the tensor-core 3x3 convolution of a score-model layer "
                          "(152 x 70x70, 128 -> 128 channels, bf16)")
-    ap.add_argument("--score", choices=["prior", "conv"], default="prior",
-                    help="--sampler: the score model (Gaussian prior or a convolutional network)")
+    ap.add_argument("--score", choices=["prior", "conv", "unet"], default="prior",
+                    help="--sampler: the score model (Gaussian prior, a convolutional network "
+                         "or the 4-level U-Net); --dsm-train: conv or unet")
     ap.add_argument("--surrogate-fraction", type=float, default=0.0,
                     help="--sampler: low-fidelity guidance (2x coarser grid and time step) in "
                          "this fraction of the first reverse steps")

@@ -460,23 +460,24 @@ FWI_API fwi_status fwi_dsm_loss(long long n, const float *eps, const float *z, f
 
 /* Weight gradient of the 3x3 convolution (stride 1, zero padding 1):
  * dW[co][ky][kx][ci] = sum_{b,y,x} dP[b][y][x][co] X[b][y+ky-1][x+kx-1][ci],
- * X and dP bf16 [n][h][w][channels], dW float32 [channels][3][3][channels]
- * (written), channels a multiple of 64; X, dP, dW and work 16-byte aligned.
- * The pixels are split into fwi_conv3x3_wgrad_splits(...) contiguous ranges
- * whose partial sums go to `work` (work_floats floats, caller-owned; NULL or
- * too small for two splits means one range written straight to dW) and are
- * then added in range order: a fixed summation order for given sizes,
- * work_floats and SM count. */
-FWI_API fwi_status fwi_conv3x3_wgrad(int n, int h, int w, int channels, const void *X,
+ * X bf16 [n][h][w][cin], dP bf16 [n][h][w][cout], dW float32 [cout][3][3][cin]
+ * (written), cin and cout multiples of 64; X, dP, dW and work 16-byte aligned.
+ * On the CUDA cores (64 x 64 register-tiled outputs).  The pixels are split
+ * into fwi_conv3x3_wgrad_splits(...) contiguous ranges whose partial sums go
+ * to `work` (work_floats floats, caller-owned; NULL or too small for two
+ * splits means one range written straight to dW) and are then added in range
+ * order: a fixed summation order for given sizes, work_floats and SM count. */
+FWI_API fwi_status fwi_conv3x3_wgrad(int n, int h, int w, int cin, int cout, const void *X,
                                      const void *dP, float *dW, float *work,
                                      long long work_floats, void *stream);
 
 /* The number of pixel ranges fwi_conv3x3_wgrad uses (1..16; about four CTAs
- * per SM, at most work_floats / (9 channels^2)); 0 for invalid sizes. */
-FWI_API int fwi_conv3x3_wgrad_splits(int n, int h, int w, int channels, long long work_floats);
+ * per SM, at most work_floats / (9 cin cout)); 0 for invalid sizes. */
+FWI_API int fwi_conv3x3_wgrad_splits(int n, int h, int w, int cin, int cout,
+                                     long long work_floats);
 
 /* The same weight gradient on the tensor cores (tcgen05, BF16 products, FP32
- * accumulation), channels a multiple of 128.  Over the zero-padded pixel
+ * accumulation), cin and cout multiples of 128.  Over the zero-padded pixel
  * domain q (rows of wp = w + 2 rounded up to a multiple of 8 pixels) the
  * operands are first staged K-major in `stage` (caller-owned, at least
  * fwi_conv3x3_wgrad_tc_stage_bytes(...) bytes): dP^T[co][q] and three copies
@@ -485,17 +486,19 @@ FWI_API int fwi_conv3x3_wgrad_splits(int n, int h, int w, int channels, long lon
  * are split into fwi_conv3x3_wgrad_tc_splits(...) ranges whose partial tiles
  * go to `work` (NULL: one range) and are added in range order.  *status (may
  * be NULL) receives FWI_ERR_DEVICE_TIMEOUT if a device-side wait ran out. */
-FWI_API fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int channels, const void *X,
+FWI_API fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int cin, int cout, const void *X,
                                         const void *dP, float *dW, void *stage,
                                         long long stage_bytes, float *work,
                                         long long work_floats, int *status, void *stream);
 
-/* Bytes of the K-major staging buffer (0 for invalid sizes). */
-FWI_API long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int channels);
+/* Bytes of the K-major staging buffer, (cout + 3 cin) x padded pixels x 2
+ * (0 for invalid sizes). */
+FWI_API long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int cin, int cout);
 
 /* Pixel ranges of fwi_conv3x3_wgrad_tc: about one CTA per SM, at most
- * work_floats / (9 channels^2); 0 for invalid sizes. */
-FWI_API int fwi_conv3x3_wgrad_tc_splits(int n, int h, int w, int channels, long long work_floats);
+ * work_floats / (9 cin cout); 0 for invalid sizes. */
+FWI_API int fwi_conv3x3_wgrad_tc_splits(int n, int h, int w, int cin, int cout,
+                                        long long work_floats);
 
 /* db[c] = sum_p dP[p][c] over npix pixels (dP bf16 [npix][channels]): the
  * pixels split into up to 4 x SM-count ranges whose partial sums go to `work`
@@ -523,6 +526,23 @@ FWI_API fwi_status fwi_time_bias(int nsteps, int channels, int dim, const float 
 /* dE[c][k] = db[c] phi[k]: the gradient with respect to E of a bias b + E phi. */
 FWI_API fwi_status fwi_time_bias_grad(int channels, int dim, const float *db, const float *phi,
                                       float *dE, void *stream);
+
+/* U-Net resampling (the score model of Sec. 6 is a U-Net), NHWC bf16, FP32
+ * arithmetic, channels a multiple of 8, arrays 16-byte aligned.
+ * fwi_pool2_bf16: y [n][(h+1)/2][(w+1)/2][C] = s * the sum of x [n][h][w][C]
+ *   over each 2 x 2 block inside the image, s = 1 / (cells in the block) for
+ *   mode 0 (the mean) and 1 for mode 1 (the sum: the adjoint of mode-0 up2).
+ * fwi_up2_bf16: y [n][ho][wo][C] = s * x[n][i/2][j/2] with x [n][(ho+1)/2][(wo+1)/2][C],
+ *   s = 1 for mode 0 (nearest neighbour) and 1 / (cells of the block inside
+ *   ho x wo) for mode 1 (the adjoint of mode-0 pooling).
+ * fwi_add_bf16: z = x + y over `count` elements (a multiple of 8).
+ * Errors: FWI_ERR_INVALID_ARG before any launch, FWI_ERR_CUDA. */
+FWI_API fwi_status fwi_pool2_bf16(int n, int h, int w, int channels, int mode, const void *x,
+                                  void *y, void *stream);
+FWI_API fwi_status fwi_up2_bf16(int n, int ho, int wo, int channels, int mode, const void *x,
+                                void *y, void *stream);
+FWI_API fwi_status fwi_add_bf16(long long count, const void *x, const void *y, void *z,
+                                void *stream);
 
 /* ---------------------------------------------------------------- low-fidelity guidance
  * Grid transfers of the low-fidelity guidance surrogate (the multi-fidelity

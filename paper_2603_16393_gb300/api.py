@@ -156,17 +156,23 @@ _lib.fwi_dsm_noisy.argtypes = [ctypes.c_longlong, ctypes.c_double, _vp, _vp, _vp
 _lib.fwi_dsm_loss.restype = _S
 _lib.fwi_dsm_loss.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp, ctypes.c_longlong, _vp]
 _lib.fwi_conv3x3_wgrad.restype = _S
-_lib.fwi_conv3x3_wgrad.argtypes = [ctypes.c_int] * 4 + [_vp, _vp, _vp, _vp, ctypes.c_longlong,
+_lib.fwi_conv3x3_wgrad.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, _vp, ctypes.c_longlong,
                                                          _vp]
 _lib.fwi_conv3x3_wgrad_tc.restype = _S
-_lib.fwi_conv3x3_wgrad_tc.argtypes = [ctypes.c_int] * 4 + [_vp, _vp, _vp, _vp, ctypes.c_longlong,
+_lib.fwi_conv3x3_wgrad_tc.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, _vp, ctypes.c_longlong,
                                                             _vp, ctypes.c_longlong, _vp, _vp]
 _lib.fwi_conv3x3_wgrad_tc_stage_bytes.restype = ctypes.c_longlong
-_lib.fwi_conv3x3_wgrad_tc_stage_bytes.argtypes = [ctypes.c_int] * 4
+_lib.fwi_conv3x3_wgrad_tc_stage_bytes.argtypes = [ctypes.c_int] * 5
 _lib.fwi_conv3x3_wgrad_tc_splits.restype = ctypes.c_int
-_lib.fwi_conv3x3_wgrad_tc_splits.argtypes = [ctypes.c_int] * 4 + [ctypes.c_longlong]
+_lib.fwi_conv3x3_wgrad_tc_splits.argtypes = [ctypes.c_int] * 5 + [ctypes.c_longlong]
 _lib.fwi_conv3x3_wgrad_splits.restype = ctypes.c_int
-_lib.fwi_conv3x3_wgrad_splits.argtypes = [ctypes.c_int] * 4 + [ctypes.c_longlong]
+_lib.fwi_conv3x3_wgrad_splits.argtypes = [ctypes.c_int] * 5 + [ctypes.c_longlong]
+_lib.fwi_pool2_bf16.restype = _S
+_lib.fwi_pool2_bf16.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp]
+_lib.fwi_up2_bf16.restype = _S
+_lib.fwi_up2_bf16.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp]
+_lib.fwi_add_bf16.restype = _S
+_lib.fwi_add_bf16.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp]
 _lib.fwi_channel_sum.restype = _S
 _lib.fwi_channel_sum.argtypes = [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, ctypes.c_longlong,
                                  _vp]
@@ -609,51 +615,86 @@ def fwi_dsm_loss(eps, z, loss, grad, work=None, stream=None):
 WGRAD_MAX_SPLITS = 32   # partial tiles a work buffer of WGRAD_MAX_SPLITS 9 C^2 floats holds
 
 
-def fwi_conv3x3_wgrad(X, dP, dW, work=None, stream=None):
-    """dW [C][3][3][C] float32 from X, dP bf16 [n][h][w][C]; ``work`` a float32
-    device buffer for the per-range partial sums (WGRAD_MAX_SPLITS 9 C^2
-    floats use every split the library wants; None: one range)."""
-    n, h, w, c = X.shape
-    if X.dtype != torch.bfloat16 or dP.dtype != torch.bfloat16 or tuple(dP.shape) != (n, h, w, c):
-        raise ValueError("X and dP must be bfloat16 [n][h][w][C]")
+def _wgrad_operands(X, dP, dW, work):
+    n, h, w, cin = X.shape
+    cout = dP.shape[-1]
+    if X.dtype != torch.bfloat16 or dP.dtype != torch.bfloat16 or tuple(dP.shape[:3]) != (n, h, w):
+        raise ValueError("X and dP must be bfloat16 [n][h][w][C] of one image shape")
     if not (X.is_contiguous() and dP.is_contiguous()):
         raise ValueError("X and dP must be contiguous")
-    _f32(dW, (c, 3, 3, c), "dW")
-    wf = 0 if work is None else work.numel()
-    if work is not None and (work.dtype != torch.float32 or not work.is_contiguous()):
-        raise ValueError("work must be a contiguous float32 tensor")
-    _check(_lib.fwi_conv3x3_wgrad(n, h, w, c, _ptr(X), _ptr(dP), _ptr(dW), _ptr(work), wf,
+    _f32(dW, (cout, 3, 3, cin), "dW")
+    wp, wf = _work(work)
+    return n, h, w, cin, cout, wp, wf
+
+
+def fwi_conv3x3_wgrad(X, dP, dW, work=None, stream=None):
+    """dW [cout][3][3][cin] float32 from X bf16 [n][h][w][cin] and dP bf16
+    [n][h][w][cout] on the CUDA cores; ``work`` a float32 device buffer for the
+    per-range partial sums (WGRAD_MAX_SPLITS 9 cin cout floats use every split
+    the library wants; None: one range)."""
+    n, h, w, cin, cout, wp, wf = _wgrad_operands(X, dP, dW, work)
+    _check(_lib.fwi_conv3x3_wgrad(n, h, w, cin, cout, _ptr(X), _ptr(dP), _ptr(dW), wp, wf,
                                   _stream(stream)))
 
 
-def fwi_conv3x3_wgrad_splits(n, h, w, channels, work_floats):
-    return _lib.fwi_conv3x3_wgrad_splits(n, h, w, channels, work_floats)
+def fwi_conv3x3_wgrad_splits(n, h, w, cin, cout, work_floats):
+    return _lib.fwi_conv3x3_wgrad_splits(n, h, w, cin, cout, work_floats)
 
 
-def fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, channels):
-    return _lib.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, channels)
+def fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, cin, cout):
+    return _lib.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, cin, cout)
 
 
-def fwi_conv3x3_wgrad_tc_splits(n, h, w, channels, work_floats):
-    return _lib.fwi_conv3x3_wgrad_tc_splits(n, h, w, channels, work_floats)
+def fwi_conv3x3_wgrad_tc_splits(n, h, w, cin, cout, work_floats):
+    return _lib.fwi_conv3x3_wgrad_tc_splits(n, h, w, cin, cout, work_floats)
 
 
 def fwi_conv3x3_wgrad_tc(X, dP, dW, stage, work=None, status=None, stream=None):
-    """The weight gradient on the tensor cores (C a multiple of 128): ``stage``
-    a uint8/bf16 device buffer of at least fwi_conv3x3_wgrad_tc_stage_bytes
+    """The weight gradient on the tensor cores (cin, cout multiples of 128):
+    ``stage`` a device buffer of at least fwi_conv3x3_wgrad_tc_stage_bytes
     bytes, ``work`` float32 for the partial tiles (None: one range)."""
-    n, h, w, c = X.shape
-    if X.dtype != torch.bfloat16 or dP.dtype != torch.bfloat16 or tuple(dP.shape) != (n, h, w, c):
-        raise ValueError("X and dP must be bfloat16 [n][h][w][C]")
-    if not (X.is_contiguous() and dP.is_contiguous() and stage.is_contiguous()):
-        raise ValueError("X, dP and stage must be contiguous")
-    _f32(dW, (c, 3, 3, c), "dW")
-    wf = 0 if work is None else work.numel()
-    if work is not None and (work.dtype != torch.float32 or not work.is_contiguous()):
-        raise ValueError("work must be a contiguous float32 tensor")
-    _check(_lib.fwi_conv3x3_wgrad_tc(n, h, w, c, _ptr(X), _ptr(dP), _ptr(dW), _ptr(stage),
-                                     stage.numel() * stage.element_size(), _ptr(work), wf,
-                                     _ptr(status), _stream(stream)))
+    n, h, w, cin, cout, wp, wf = _wgrad_operands(X, dP, dW, work)
+    if not stage.is_contiguous():
+        raise ValueError("stage must be contiguous")
+    _check(_lib.fwi_conv3x3_wgrad_tc(n, h, w, cin, cout, _ptr(X), _ptr(dP), _ptr(dW), _ptr(stage),
+                                     stage.numel() * stage.element_size(), wp, wf, _ptr(status),
+                                     _stream(stream)))
+
+
+def _bf16_nhwc(t, name):
+    if t.dtype != torch.bfloat16 or t.dim() != 4 or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError(f"{name} must be a contiguous bfloat16 CUDA tensor [n][h][w][C]")
+
+
+def fwi_pool2_bf16(x, y, mode=0, stream=None):
+    """y [n][(h+1)/2][(w+1)/2][C] from x [n][h][w][C]: 2 x 2 block mean (mode 0)
+    or sum (mode 1)."""
+    _bf16_nhwc(x, "x")
+    _bf16_nhwc(y, "y")
+    n, h, w, c = x.shape
+    if tuple(y.shape) != (n, (h + 1) // 2, (w + 1) // 2, c):
+        raise ValueError("y must be [n][(h+1)/2][(w+1)/2][C]")
+    _check(_lib.fwi_pool2_bf16(n, h, w, c, mode, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def fwi_up2_bf16(x, y, mode=0, stream=None):
+    """y [n][ho][wo][C] from x [n][(ho+1)/2][(wo+1)/2][C]: nearest neighbour
+    (mode 0) or divided by the block's cell count (mode 1)."""
+    _bf16_nhwc(x, "x")
+    _bf16_nhwc(y, "y")
+    n, ho, wo, c = y.shape
+    if tuple(x.shape) != (n, (ho + 1) // 2, (wo + 1) // 2, c):
+        raise ValueError("x must be [n][(ho+1)/2][(wo+1)/2][C]")
+    _check(_lib.fwi_up2_bf16(n, ho, wo, c, mode, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def fwi_add_bf16(x, y, z, stream=None):
+    for t, name in ((x, "x"), (y, "y"), (z, "z")):
+        if t.dtype != torch.bfloat16 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"{name} must be a contiguous bfloat16 CUDA tensor")
+    if not (x.shape == y.shape == z.shape):
+        raise ValueError("x, y and z must have one shape")
+    _check(_lib.fwi_add_bf16(x.numel(), _ptr(x), _ptr(y), _ptr(z), _stream(stream)))
 
 
 def fwi_channel_sum(dP, db, work=None, stream=None):

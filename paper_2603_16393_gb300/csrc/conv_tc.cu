@@ -733,7 +733,7 @@ constexpr uint32_t kGTmemCols = 256;
 
 struct WgradTcArgs {
     unsigned long long wait_ns;
-    int C, cbs, wp;        // channels, 128-channel blocks, padded row pitch
+    int cin, cout, cbs, wp;   // channels, 128-channel blocks of cin, padded row pitch
     int units, pairs, jobs;
     long long kblocks, per_split;
     float *out;            // [split][C][9][C]
@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool has = k0 < k1;
         if (!has || mb_wait(&acc_full, 0u, vfailed, a.wait_ns)) {
             tc_fence_after();
-            float *o = a.out + (size_t)split * 9 * a.C * a.C;
+            float *o = a.out + (size_t)split * 9 * a.cin * a.cout;
 #pragma unroll 1
             for (int c = cbeg; c < cend; c += 16) {
                 float v[16];
@@ -934,7 +934,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 const int u = u0 + c / 128, tap = u / a.cbs, cb = u % a.cbs;
                 const int ci = cb * 128 + c % 128;
-                float4 *dst = reinterpret_cast<float4 *>(o + ((size_t)co * 9 + tap) * a.C + ci);
+                float4 *dst = reinterpret_cast<float4 *>(o + ((size_t)co * 9 + tap) * a.cin + ci);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
                     dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
@@ -970,20 +970,20 @@ struct WgradTcShape {
     int cbs, units, pairs, jobs;
 };
 
-WgradTcShape wgrad_tc_shape(int n, int h, int w, int C)
+WgradTcShape wgrad_tc_shape(int n, int h, int w, int cin, int cout)
 {
     WgradTcShape s;
     s.wp = (w + 2 + 7) / 8 * 8;
     s.Q = (long long)n * (h + 2) * s.wp;
     s.kblocks = (s.Q + kBK - 1) / kBK;
-    s.cbs = C / 128;
+    s.cbs = cin / 128;
     s.units = 9 * s.cbs;
     s.pairs = (s.units + 1) / 2;
-    s.jobs = s.cbs * s.pairs;
+    s.jobs = (cout / 128) * s.pairs;
     return s;
 }
 
-int wgrad_tc_splits(const WgradTcShape &g, int C, long long work_floats)
+int wgrad_tc_splits(const WgradTcShape &g, int cin, int cout, long long work_floats)
 {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
@@ -991,7 +991,7 @@ int wgrad_tc_splits(const WgradTcShape &g, int C, long long work_floats)
     long long s = sms / g.jobs;                      // one CTA per SM
     if (s < 1) s = 1;
     if (s > g.kblocks) s = g.kblocks;
-    const long long fit = work_floats / (9LL * C * C);
+    const long long fit = work_floats / (9LL * cin * cout);
     if (s > fit) s = fit;
     if (s < 1) return 1;
     const long long per = (g.kblocks + s - 1) / s;
@@ -1095,52 +1095,54 @@ fwi_status fwi_conv3x3_bf16_wait_check(int n, int h, int w, int cin, int cout, c
 
 extern "C" {
 
-long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int channels)
+long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int cin, int cout)
 {
-    if (n < 1 || h < 1 || w < 1 || channels < 128 || channels % 128 != 0) return 0;
-    const WgradTcShape g = wgrad_tc_shape(n, h, w, channels);
-    return 4LL * channels * g.Q * 2;
+    if (n < 1 || h < 1 || w < 1 || cin < 128 || cin % 128 != 0 || cout < 128 || cout % 128 != 0)
+        return 0;
+    const WgradTcShape g = wgrad_tc_shape(n, h, w, cin, cout);
+    return ((long long)cout + 3LL * cin) * g.Q * 2;
 }
 
-int fwi_conv3x3_wgrad_tc_splits(int n, int h, int w, int channels, long long work_floats)
+int fwi_conv3x3_wgrad_tc_splits(int n, int h, int w, int cin, int cout, long long work_floats)
 {
-    if (n < 1 || h < 1 || w < 1 || channels < 128 || channels % 128 != 0) return 0;
-    return wgrad_tc_splits(wgrad_tc_shape(n, h, w, channels), channels, work_floats);
+    if (n < 1 || h < 1 || w < 1 || cin < 128 || cin % 128 != 0 || cout < 128 || cout % 128 != 0)
+        return 0;
+    return wgrad_tc_splits(wgrad_tc_shape(n, h, w, cin, cout), cin, cout, work_floats);
 }
 
-fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int channels, const void *X, const void *dP,
-                                float *dW, void *stage, long long stage_bytes, float *work,
-                                long long work_floats, int *status, void *stream)
+fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int cin, int cout, const void *X,
+                                const void *dP, float *dW, void *stage, long long stage_bytes,
+                                float *work, long long work_floats, int *status, void *stream)
 {
-    if (n < 1 || h < 1 || w < 1 || channels < 128 || channels % 128 != 0)
+    if (n < 1 || h < 1 || w < 1 || cin < 128 || cin % 128 != 0 || cout < 128 || cout % 128 != 0)
         return fwi::record_error(FWI_ERR_INVALID_ARG,
-                                 "n, h, w >= 1 and channels a multiple of 128");
+                                 "n, h, w >= 1 and cin, cout multiples of 128");
     if (!X || !dP || !dW || !stage)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "X, dP, dW and stage are needed");
     if (((uintptr_t)X | (uintptr_t)dP | (uintptr_t)dW | (uintptr_t)stage | (uintptr_t)work) & 15)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "all arrays must be 16-byte aligned");
-    const WgradTcShape g = wgrad_tc_shape(n, h, w, channels);
+    const WgradTcShape g = wgrad_tc_shape(n, h, w, cin, cout);
     if (g.Q + g.wp + kBK >= 0x7fffffffLL)
         return fwi::record_error(FWI_ERR_UNSUPPORTED, "too many pixels for one weight gradient");
-    const long long need = 4LL * channels * g.Q * 2;
+    const long long need = ((long long)cout + 3LL * cin) * g.Q * 2;
     if (stage_bytes < need)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "stage needs %lld bytes", need);
-    const int splits = wgrad_tc_splits(g, channels, work ? work_floats : 0);
+    const int splits = wgrad_tc_splits(g, cin, cout, work ? work_floats : 0);
     auto enc = tmap_encoder();
     if (!enc) return fwi::record_error(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // dP^T [cout][Q], then the three X^T copies [cin][Q]
     __nv_bfloat16 *arr[4];
-    for (int k = 0; k < 4; ++k)
-        arr[k] = static_cast<__nv_bfloat16 *>(stage) + (size_t)k * channels * g.Q;
-    const dim3 sgrid((unsigned)((g.Q + 63) / 64), (unsigned)(channels / 64));
-    k_stage_kmajor<<<sgrid, 256, 0, st>>>(h, w, channels, g.wp, g.Q, 0,
-                                           static_cast<const __nv_bfloat16 *>(dP), arr[0]);
-    k_stage_kmajor3<<<sgrid, 256, 0, st>>>(h, w, channels, g.wp, g.Q,
-                                            static_cast<const __nv_bfloat16 *>(X), arr[1], arr[2],
-                                            arr[3]);
+    arr[0] = static_cast<__nv_bfloat16 *>(stage);
+    for (int k = 0; k < 3; ++k) arr[1 + k] = arr[0] + (size_t)cout * g.Q + (size_t)k * cin * g.Q;
+    const unsigned qt = (unsigned)((g.Q + 63) / 64);
+    k_stage_kmajor<<<dim3(qt, (unsigned)(cout / 64)), 256, 0, st>>>(
+        h, w, cout, g.wp, g.Q, 0, static_cast<const __nv_bfloat16 *>(dP), arr[0]);
+    k_stage_kmajor3<<<dim3(qt, (unsigned)(cin / 64)), 256, 0, st>>>(
+        h, w, cin, g.wp, g.Q, static_cast<const __nv_bfloat16 *>(X), arr[1], arr[2], arr[3]);
     CUtensorMap tm[4];
     for (int k = 0; k < 4; ++k) {
-        const cuuint64_t dims[2] = {(cuuint64_t)g.Q, (cuuint64_t)channels};
+        const cuuint64_t dims[2] = {(cuuint64_t)g.Q, (cuuint64_t)(k == 0 ? cout : cin)};
         const cuuint64_t strides[1] = {(cuuint64_t)g.Q * 2};
         const cuuint32_t box[2] = {(cuuint32_t)kBK, 128u};
         const cuuint32_t estr[2] = {1, 1};
@@ -1152,7 +1154,8 @@ fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int channels, const void *X
     }
     WgradTcArgs a;
     a.wait_ns = kWaitNs;
-    a.C = channels;
+    a.cin = cin;
+    a.cout = cout;
     a.cbs = g.cbs;
     a.wp = g.wp;
     a.units = g.units;
@@ -1171,7 +1174,7 @@ fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int channels, const void *X
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && splits > 1) {
-        const size_t nw = (size_t)9 * channels * channels;
+        const size_t nw = (size_t)9 * cin * cout;
         k_wgrad_tc_reduce<<<(unsigned)((nw + 255) / 256 < 1216 ? (nw + 255) / 256 : 1216), 256, 0,
                             st>>>(nw, splits, work, dW);
         e = cudaGetLastError();

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads)
 constexpr int kWT = 64, kWP = 32, kMaxSplit = 16;
 
 __device__ __forceinline__ void wgrad_fetch(long long p, long long npix, long long hw, int h,
-                                            int w, int C, int ky, int kx, int co, int ci,
+                                            int w, int Cin, int Cout, int ky, int kx, int co, int ci,
                                             const __nv_bfloat16 *__restrict__ X,
                                             const __nv_bfloat16 *__restrict__ dP, uint4 &vp,
                                             uint4 &vx)
@@ -111,12 +111,12 @@ __device__ __forceinline__ void wgrad_fetch(long long p, long long npix, long lo
     vp = make_uint4(0u, 0u, 0u, 0u);
     vx = vp;
     if (p >= npix) return;
-    vp = *reinterpret_cast<const uint4 *>(dP + p * C + co);
+    vp = *reinterpret_cast<const uint4 *>(dP + p * Cout + co);
     const long long b = p / hw;
     const int r = (int)(p - b * hw);
     const int y = r / w + ky - 1, x = r % w + kx - 1;
     if (y >= 0 && y < h && x >= 0 && x < w)
-        vx = *reinterpret_cast<const uint4 *>(X + ((b * h + y) * (long long)w + x) * C + ci);
+        vx = *reinterpret_cast<const uint4 *>(X + ((b * h + y) * (long long)w + x) * Cin + ci);
 }
 
 __device__ __forceinline__ void stage8(float *dst, uint4 v)
@@ -133,17 +133,17 @@ __device__ __forceinline__ void stage8(float *dst, uint4 v)
 }
 
 __global__ void __launch_bounds__(kThreads)
-    k_wgrad(int n, int h, int w, int C, long long chunks_per_split,
+    k_wgrad(int n, int h, int w, int Cin, int Cout, long long chunks_per_split,
             const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ dP,
             float *__restrict__ out)
 {
     __shared__ __align__(16) float sP[kWP][kWT];
     __shared__ __align__(16) float sX[kWP][kWT];
-    const int tiles = C / kWT;
+    const int ci_tiles = Cin / kWT;
     int t = blockIdx.x;
     const int tap = t % 9;
     t /= 9;
-    const int ci0 = (t % tiles) * kWT, co0 = (t / tiles) * kWT;
+    const int ci0 = (t % ci_tiles) * kWT, co0 = (t / ci_tiles) * kWT;
     const int ky = tap / 3, kx = tap % 3;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int lp = threadIdx.x / 8, lq = (threadIdx.x % 8) * 8;   // loader: pixel, 8 channels
@@ -157,14 +157,16 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     uint4 vp, vx;
-    if (c0 < c1) wgrad_fetch(c0 * kWP + lp, npix, hw, h, w, C, ky, kx, co0 + lq, ci0 + lq, X, dP, vp, vx);
+    if (c0 < c1)
+        wgrad_fetch(c0 * kWP + lp, npix, hw, h, w, Cin, Cout, ky, kx, co0 + lq, ci0 + lq, X, dP, vp,
+                    vx);
     for (long long ch = c0; ch < c1; ++ch) {
         stage8(&sP[lp][lq], vp);
         stage8(&sX[lp][lq], vx);
         __syncthreads();
         if (ch + 1 < c1)
-            wgrad_fetch((ch + 1) * kWP + lp, npix, hw, h, w, C, ky, kx, co0 + lq, ci0 + lq, X, dP,
-                        vp, vx);
+            wgrad_fetch((ch + 1) * kWP + lp, npix, hw, h, w, Cin, Cout, ky, kx, co0 + lq, ci0 + lq,
+                        X, dP, vp, vx);
 #pragma unroll 8
         for (int pl = 0; pl < kWP; ++pl) {
             const float4 a = *reinterpret_cast<const float4 *>(&sP[pl][4 * ty]);
@@ -177,11 +179,11 @@ __global__ void __launch_bounds__(kThreads)
         }
         __syncthreads();
     }
-    float *o = out + (size_t)blockIdx.y * 9 * C * C;
+    float *o = out + (size_t)blockIdx.y * 9 * Cin * Cout;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int co = co0 + 4 * ty + i;
-        *reinterpret_cast<float4 *>(o + ((size_t)co * 9 + tap) * C + ci0 + 4 * tx) =
+        *reinterpret_cast<float4 *>(o + ((size_t)co * 9 + tap) * Cin + ci0 + 4 * tx) =
             make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     }
 }
@@ -384,42 +386,43 @@ fwi_status fwi_dsm_loss(long long n, const float *eps, const float *z, float *lo
     return done("fwi_dsm_loss");
 }
 
-int fwi_conv3x3_wgrad_splits(int n, int h, int w, int channels, long long work_floats)
+int fwi_conv3x3_wgrad_splits(int n, int h, int w, int cin, int cout, long long work_floats)
 {
-    if (n < 1 || h < 1 || w < 1 || channels < kWT || channels % kWT != 0) return 0;
+    if (n < 1 || h < 1 || w < 1 || cin < kWT || cin % kWT != 0 || cout < kWT || cout % kWT != 0)
+        return 0;
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long tiles = channels / kWT, ctas = 9 * tiles * tiles;
+    const long long ctas = 9LL * (cin / kWT) * (cout / kWT);
     const long long nchunks = ((long long)n * h * w + kWP - 1) / kWP;
     long long s = (4LL * sms + ctas - 1) / ctas;       // about 4 CTAs per SM
     if (s > kMaxSplit) s = kMaxSplit;
     if (s > nchunks) s = nchunks;
-    const long long fit = work_floats / (9LL * channels * channels);
+    const long long fit = work_floats / (9LL * cin * cout);
     if (s > fit) s = fit;
     return s < 1 ? 1 : (int)s;
 }
 
-fwi_status fwi_conv3x3_wgrad(int n, int h, int w, int channels, const void *X, const void *dP,
+fwi_status fwi_conv3x3_wgrad(int n, int h, int w, int cin, int cout, const void *X, const void *dP,
                              float *dW, float *work, long long work_floats, void *stream)
 {
-    if (n < 1 || h < 1 || w < 1 || channels < kWT || channels % kWT != 0)
-        return fwi::record_error(FWI_ERR_INVALID_ARG, "n, h, w >= 1 and channels a multiple of 64");
+    if (n < 1 || h < 1 || w < 1 || cin < kWT || cin % kWT != 0 || cout < kWT || cout % kWT != 0)
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "n, h, w >= 1 and cin, cout multiples of 64");
     if (!X || !dP || !dW) return fwi::record_error(FWI_ERR_INVALID_ARG, "X, dP and dW are needed");
     if (((uintptr_t)X & 15) || ((uintptr_t)dP & 15) || ((uintptr_t)dW & 15) ||
         ((uintptr_t)work & 15))
         return fwi::record_error(FWI_ERR_INVALID_ARG, "X, dP, dW and work must be 16-byte aligned");
-    const int splits = fwi_conv3x3_wgrad_splits(n, h, w, channels, work ? work_floats : 0);
+    const int splits = fwi_conv3x3_wgrad_splits(n, h, w, cin, cout, work ? work_floats : 0);
     const long long nchunks = ((long long)n * h * w + kWP - 1) / kWP;
     const long long per = (nchunks + splits - 1) / splits;
-    const int tiles = channels / kWT;
-    const dim3 grid(9 * tiles * tiles, splits);
+    const dim3 grid(9 * (cin / kWT) * (cout / kWT), splits);
     float *out = splits > 1 ? work : dW;
     k_wgrad<<<grid, kThreads, 0, (cudaStream_t)stream>>>(
-        n, h, w, channels, per, static_cast<const __nv_bfloat16 *>(X),
+        n, h, w, cin, cout, per, static_cast<const __nv_bfloat16 *>(X),
         static_cast<const __nv_bfloat16 *>(dP), out);
     if (splits > 1) {
-        const size_t nw = (size_t)9 * channels * channels;
+        const size_t nw = (size_t)9 * cin * cout;
         k_wgrad_reduce<<<grid_for(nw), kThreads, 0, (cudaStream_t)stream>>>(nw, splits, work, dW);
     }
     return done("fwi_conv3x3_wgrad");

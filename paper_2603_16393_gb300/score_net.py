@@ -106,6 +106,14 @@ class ConvScore:
             out.append(tuple(views))
         return out
 
+    def work_floats(self) -> int:
+        return api.WGRAD_MAX_SPLITS * 9 * self.C * self.C
+
+    def stage_bytes(self) -> int:
+        if self.C % 128:
+            return 0
+        return api.fwi_conv3x3_wgrad_tc_stage_bytes(*self.shape, self.C, self.C)
+
     def refresh(self, stream=None):
         """bf16 W, W^T[ci][ky][kx][co] = W[co][2-ky][2-kx][ci] and the per-step
         biases b + E phi(i) of every layer, from the FP32 master parameters."""
@@ -189,7 +197,8 @@ class ConvScore:
 
 
 class DSMTrainer:
-    """Denoising score matching (Eq. L2_rewrite) of a ConvScore with Adam.
+    """Denoising score matching (Eq. L2_rewrite) of a ConvScore or UNetScore
+    with Adam.
 
     One step on a minibatch x_0 [B][nz][nx] (normalised models), its noise z
     and one step index t (every sample of the minibatch shares t): x_t =
@@ -200,7 +209,7 @@ class DSMTrainer:
     flat FP32 parameters (fwi_adam_step) and the refresh of the bf16 weights
     and bias tables.  ``step`` returns the loss as a device scalar."""
 
-    def __init__(self, net: ConvScore, lr: float = 1e-3, beta1: float = 0.9,
+    def __init__(self, net, lr: float = 1e-3, beta1: float = 0.9,
                  beta2: float = 0.999, eps: float = 1e-8):
         self.net, self.lr, self.beta1, self.beta2, self.eps_adam = net, lr, beta1, beta2, eps
         f32 = dict(dtype=torch.float32, device=net.dev)
@@ -212,12 +221,10 @@ class DSMTrainer:
         self.e = torch.empty(net.shape, **f32)
         self.g = torch.empty(net.shape, **f32)
         self.loss = torch.empty((1,), **f32)
-        self.work = torch.empty(api.WGRAD_MAX_SPLITS * 9 * net.C * net.C, **f32)
+        self.work = torch.empty(net.work_floats(), **f32)
         # the K-major staging buffer of the tensor-core weight gradient
-        self.stage = None
-        if net.C % 128 == 0:
-            nbytes = api.fwi_conv3x3_wgrad_tc_stage_bytes(*net.shape, net.C)
-            self.stage = torch.empty(nbytes, dtype=torch.uint8, device=net.dev)
+        nbytes = net.stage_bytes()
+        self.stage = torch.empty(nbytes, dtype=torch.uint8, device=net.dev) if nbytes else None
         self.k = 0
 
     def gradients(self, x0: torch.Tensor, z: torch.Tensor, t: int, stream=None) -> torch.Tensor:
@@ -240,3 +247,234 @@ class DSMTrainer:
                           self.beta2, self.eps_adam, stream)
         self.net.refresh(stream)
         return loss
+
+
+# --------------------------------------------------------------------------
+# A 4-level U-Net noise-prediction network (the score model of Sec. 6 is a
+# U-Net; no architecture is given): level widths c_0..c_3, two 3x3
+# convolution + SiLU layers per encoder level with 2 x 2 mean pooling between
+# levels, and per decoder level nearest upsampling, a convolution + SiLU, the
+# additive skip from the encoder layer of that level and a second convolution
+# + SiLU; a last linear convolution whose channel 0 is eps.  The step enters
+# every layer's bias as b + E phi(i).
+
+UNET_WIDTHS = (64, 128, 256, 256)
+
+
+def unet_layers(widths=UNET_WIDTHS):
+    """[(name, level, cin, cout)] of the U-Net's convolutions, in parameter order."""
+    c = tuple(widths)
+    if len(c) != 4 or any(w % 64 for w in c):
+        raise ValueError("four level widths, each a multiple of 64")
+    out = []
+    for k in range(4):
+        out += [(f"enc{k}a", k, c[0] if k == 0 else c[k - 1], c[k]), (f"enc{k}b", k, c[k], c[k])]
+    for k in (2, 1, 0):
+        out += [(f"dec{k}u", k, c[k + 1], c[k]), (f"dec{k}c", k, c[k], c[k])]
+    out.append(("out", 0, c[0], c[0]))
+    return out
+
+
+def unet_seeded_weights(widths=UNET_WIDTHS, seed: int = 0):
+    """[(W [cout][3][3][cin], b [cout], E [cout][TIME_DIM])] float32, W of
+    variance 1/(9 cin) (1/9 for the first layer, whose input is one channel),
+    b and E of standard deviation 0.1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, _, cin, cout in unet_layers(widths):
+        fan = 9 if name == "enc0a" else 9 * cin
+        w = rng.standard_normal((cout, 3, 3, cin)) / np.sqrt(fan)
+        b = 0.1 * rng.standard_normal(cout)
+        e = 0.1 * rng.standard_normal((cout, TIME_DIM))
+        out.append((w.astype(np.float32), b.astype(np.float32), e.astype(np.float32)))
+    return out
+
+
+class UNetScore:
+    """Callable score model (v_i, i) -> (s, vjp) for the Sampler, and a
+    network DSMTrainer can train: the 4-level U-Net above on the library's
+    kernels (tcgen05 convolutions, fwi_pool2_bf16, fwi_up2_bf16, fwi_add_bf16,
+    SiLU kernels), bf16 activations and gradients, FP32 master parameters."""
+
+    def __init__(self, model_shape: Sequence[int], betas: Sequence[float], weights=None,
+                 widths=UNET_WIDTHS, seed: int = 0, device=None):
+        B, nz, nx = model_shape
+        self.shape = (B, nz, nx)
+        self.widths = tuple(widths)
+        self.layers = unet_layers(widths)
+        self.idx = {name: l for l, (name, _, _, _) in enumerate(self.layers)}
+        self.L = len(self.layers)
+        self.dev = torch.device(device) if device is not None else torch.device("cuda")
+        weights = weights if weights is not None else unet_seeded_weights(widths, seed)
+        if len(weights) != self.L:
+            raise ValueError(f"the U-Net has {self.L} layers")
+        self.abar = [None] + [api.fwi_ddpm_coefficients(list(betas), i).abar
+                              for i in range(1, len(betas) + 1)]
+        self.sizes = [(nz, nx)]
+        for _ in range(3):
+            h, w = self.sizes[-1]
+            self.sizes.append(((h + 1) // 2, (w + 1) // 2))
+        N1 = len(betas) + 1
+        shapes = [((co, 3, 3, ci), (co,), (co, TIME_DIM)) for _, _, ci, co in self.layers]
+        self._shapes = shapes
+        self.theta = torch.empty(sum(int(np.prod(s)) for sh in shapes for s in sh),
+                                 dtype=torch.float32, device=self.dev)
+        self.params = self.layer_views(self.theta)
+        for (w, b, e), views in zip(weights, self.params):
+            for src, dst in zip((w, b, e), views):
+                dst.copy_(torch.as_tensor(np.asarray(src, np.float32)))
+        self.phi = torch.tensor(np.stack([time_features(i) for i in range(N1)]),
+                                dtype=torch.float32, device=self.dev)
+        bf = dict(dtype=torch.bfloat16, device=self.dev)
+        self.W = [torch.empty(sh[0], **bf) for sh in shapes]
+        self.WT = [torch.empty((sh[0][3], 3, 3, sh[0][0]), **bf) for sh in shapes]
+        self.bias = [torch.empty((N1, sh[1][0]), dtype=torch.float32, device=self.dev)
+                     for sh in shapes]
+        self.refresh()
+
+        def act(k, c, dtype=torch.bfloat16):
+            h, w = self.sizes[k]
+            return torch.empty((B, h, w, c), dtype=dtype, device=self.dev)
+
+        c = self.widths
+        self.X0 = act(0, c[0])
+        self.P = {n: act(k, co) for n, k, _, co in self.layers if n != "out"}
+        self.A = {n: act(k, co) for n, k, _, co in self.layers if n != "out"}
+        self.D = {k: act(k, c[k - 1]) for k in (1, 2, 3)}         # pooled encoder inputs
+        self.U = {k: act(k, c[k + 1]) for k in (0, 1, 2)}         # upsampled decoder inputs
+        self.S = {k: act(k, c[k]) for k in (0, 1, 2)}             # after the additive skip
+        self.Y = act(0, c[0], torch.float32)
+        self.dP = {n: act(k, co) for n, k, _, co in self.layers}
+        self.dIn = {n: act(k, ci) for n, k, ci, _ in self.layers if n != "enc0a"}
+        self.dUp = {k: act(k, c[k]) for k in (1, 2, 3)}           # d/d(an up2 input)
+        self.dAcc = {k: act(k, c[k]) for k in (0, 1, 2)}          # encoder output: pool + skip
+        self.dPool = {k: act(k, c[k]) for k in (0, 1, 2)}         # d/d(a pool2 input)
+        self.dX = act(0, c[0], torch.float32)
+        self.s = torch.empty(self.shape, dtype=torch.float32, device=self.dev)
+        self.u = torch.empty(self.shape, dtype=torch.float32, device=self.dev)
+
+    # the interface DSMTrainer uses
+    def layer_views(self, flat: torch.Tensor):
+        out, o = [], 0
+        for sh in self._shapes:
+            views = []
+            for s in sh:
+                n = int(np.prod(s))
+                views.append(flat[o:o + n].view(s))
+                o += n
+            out.append(tuple(views))
+        return out
+
+    def work_floats(self) -> int:
+        return api.WGRAD_MAX_SPLITS * 9 * max(ci * co for _, _, ci, co in self.layers)
+
+    def stage_bytes(self) -> int:
+        B = self.shape[0]
+        return max([api.fwi_conv3x3_wgrad_tc_stage_bytes(B, *self.sizes[k], ci, co)
+                    for _, k, ci, co in self.layers if ci % 128 == 0 and co % 128 == 0] or [0])
+
+    def refresh(self, stream=None):
+        for l, (w, b, e) in enumerate(self.params):
+            api.fwi_conv3x3_weights_prep(w, self.W[l], self.WT[l], stream)
+            api.fwi_time_bias(b, e, self.phi, self.bias[l], stream)
+
+    def _conv(self, name, x, i, stream):
+        l = self.idx[name]
+        api.fwi_conv3x3_bf16(x, self.W[l], self.bias[l][i], 0, self.P[name], stream=stream)
+        api.fwi_silu_bf16(self.P[name], self.A[name], stream)
+        return self.A[name]
+
+    def eps(self, x: torch.Tensor, i: int, scale: float = 1.0, out: torch.Tensor | None = None,
+            stream=None) -> torch.Tensor:
+        """scale * eps(x, i) for x [B][nz][nx] (keeps the activations for the
+        backward pass)."""
+        api.fwi_pack_channel0(x, self.X0, 1.0, stream)
+        h = self.X0
+        for k in range(4):
+            if k > 0:
+                api.fwi_pool2_bf16(h, self.D[k], 0, stream)
+                h = self.D[k]
+            h = self._conv(f"enc{k}a", h, i, stream)
+            h = self._conv(f"enc{k}b", h, i, stream)
+        for k in (2, 1, 0):
+            api.fwi_up2_bf16(h, self.U[k], 0, stream)
+            a = self._conv(f"dec{k}u", self.U[k], i, stream)
+            api.fwi_add_bf16(a, self.A[f"enc{k}b"], self.S[k], stream)
+            h = self._conv(f"dec{k}c", self.S[k], i, stream)
+        l = self.idx["out"]
+        api.fwi_conv3x3_bf16(h, self.W[l], self.bias[l][i], 0, self.Y, stream=stream)
+        out = out if out is not None else torch.empty(self.shape, dtype=torch.float32,
+                                                      device=self.dev)
+        api.fwi_unpack_channel0(self.Y, out, scale, stream)
+        return out
+
+    def _layer_back(self, name, d, src, i, grads, work, stage, stream, act=True, dst=None):
+        """Through one layer from the gradient d at its output: SiLU', the
+        parameter gradients (if ``grads``), and the gradient at its input
+        (into ``dst`` or dIn[name]; skipped when dst is False)."""
+        l = self.idx[name]
+        dp = self.dP[name]
+        if act:
+            api.fwi_silu_grad_bf16(d, self.P[name], dp, stream)
+        if grads is not None:
+            dW, db, dE = grads[l]
+            _, _, ci, co = self.layers[l]
+            if stage is not None and ci % 128 == 0 and co % 128 == 0:
+                api.fwi_conv3x3_wgrad_tc(src, dp, dW, stage, work, stream=stream)
+            else:
+                api.fwi_conv3x3_wgrad(src, dp, dW, work, stream)
+            api.fwi_channel_sum(dp, db, work, stream)
+            api.fwi_time_bias_grad(db, self.phi[i], dE, stream)
+        if dst is False:
+            return None
+        dst = self.dIn[name] if dst is None else dst
+        api.fwi_conv3x3_bf16(dp, self.WT[l], None, 0, dst, stream=stream)
+        return dst
+
+    def _backward(self, g, scale, i, grads=None, work=None, stage=None, need_input=True,
+                  stream=None):
+        api.fwi_pack_channel0(g.contiguous(), self.dP["out"], scale, stream)
+        d = self._layer_back("out", None, self.A["dec0c"], i, grads, work, stage, stream,
+                             act=False)
+        for k in (0, 1, 2):
+            ds = self._layer_back(f"dec{k}c", d, self.S[k], i, grads, work, stage, stream)
+            du = self._layer_back(f"dec{k}u", ds, self.U[k], i, grads, work, stage, stream)
+            api.fwi_pool2_bf16(du, self.dUp[k + 1], 1, stream)      # the adjoint of up2
+            d = self.dUp[k + 1]
+        for k in (3, 2, 1, 0):
+            if k < 3:      # the encoder output also feeds the skip of its level
+                api.fwi_add_bf16(d, self.dIn[f"dec{k}c"], self.dAcc[k], stream)
+                d = self.dAcc[k]
+            da = self._layer_back(f"enc{k}b", d, self.A[f"enc{k}a"], i, grads, work, stage,
+                                  stream)
+            if k > 0:
+                dd = self._layer_back(f"enc{k}a", da, self.D[k], i, grads, work, stage, stream)
+                api.fwi_up2_bf16(dd, self.dPool[k - 1], 1, stream)   # the adjoint of pool2
+                d = self.dPool[k - 1]
+            else:
+                self._layer_back("enc0a", da, self.X0, i, grads, work, stage, stream,
+                                 dst=self.dX if need_input else False)
+
+    def eps_vjp(self, g: torch.Tensor, scale: float = 1.0, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+        """scale * J_eps(x)^T g at the x of the last eps() call."""
+        self._backward(g, scale, None, stream=stream)
+        out = out if out is not None else torch.empty(self.shape, dtype=torch.float32,
+                                                      device=self.dev)
+        api.fwi_unpack_channel0(self.dX, out, 1.0, stream)
+        return out
+
+    def param_grads(self, g: torch.Tensor, i: int, grads, work: torch.Tensor | None = None,
+                    stage: torch.Tensor | None = None, stream=None):
+        """The gradient of <eps(x, i), g> with respect to every (W, b, E) into
+        ``grads`` (layer_views of a flat buffer), at the x of the last eps()."""
+        self._backward(g, 1.0, i, grads, work, stage, need_input=False, stream=stream)
+
+    def __call__(self, v_i: torch.Tensor, i: int):
+        c = -1.0 / float(np.sqrt(1.0 - self.abar[i]))
+        s = self.eps(v_i, i, c, self.s)
+
+        def vjp(g):
+            return self.eps_vjp(g, c, self.u)
+
+        return s, vjp

@@ -131,9 +131,17 @@ def test_training_calls_reject_bad_arguments_without_a_gpu(api):
         lambda: lib.fwi_dsm_noisy(4, 1.0, p, p, p, None),             # abar must be < 1
         lambda: lib.fwi_dsm_noisy(4, 0.5, None, p, p, None),
         lambda: lib.fwi_dsm_loss(0, p, p, p, p, None, 0, None),
-        lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 96, p, p, p, None, 0, None),   # channels % 64
-        lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, p, None, p, None, 0, None),
-        lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, ctypes.c_void_p(4100), p, p, None, 0, None),
+        lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 96, 64, p, p, p, None, 0, None),   # cin % 64
+        lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, 64, p, None, p, None, 0, None),
+        lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, 64, ctypes.c_void_p(4100), p, p, None, 0, None),
+        lambda: lib.fwi_conv3x3_wgrad_tc(1, 4, 4, 64, 128, p, p, p, p, 1 << 20, None, 0, None,
+                                         None),                          # cin % 128
+        lambda: lib.fwi_conv3x3_wgrad_tc(1, 4, 4, 128, 128, p, p, p, p, 16, None, 0, None,
+                                         None),                          # stage too small
+        lambda: lib.fwi_pool2_bf16(1, 4, 4, 12, 0, p, p, None),           # channels % 8
+        lambda: lib.fwi_pool2_bf16(1, 4, 4, 16, 2, p, p, None),           # mode
+        lambda: lib.fwi_up2_bf16(1, 4, 4, 16, 0, ctypes.c_void_p(4100), p, None),
+        lambda: lib.fwi_add_bf16(12, p, p, p, None),
         lambda: lib.fwi_channel_sum(16, 0, p, p, None, 0, None),
         lambda: lib.fwi_adam_step(8, 1e-3, 0.9, 0.999, 1e-8, 0, p, p, p, p, None),   # step >= 1
         lambda: lib.fwi_adam_step(8, 1e-3, 1.0, 0.999, 1e-8, 1, p, p, p, p, None),
@@ -146,10 +154,15 @@ def test_training_calls_reject_bad_arguments_without_a_gpu(api):
         assert call() == 1, k
         assert api.fwi_last_error() != ""
     # the split count: 1 without room for a second range, at most 16
-    assert lib.fwi_conv3x3_wgrad_splits(2, 33, 47, 64, 0) == 1
-    assert lib.fwi_conv3x3_wgrad_splits(2, 33, 47, 64, 9 * 64 * 64 * 3) in (2, 3)
-    assert 1 <= lib.fwi_conv3x3_wgrad_splits(152, 70, 70, 128, 10 ** 9) <= 16
-    assert lib.fwi_conv3x3_wgrad_splits(1, 4, 4, 96, 10 ** 9) == 0
+    assert lib.fwi_conv3x3_wgrad_splits(2, 33, 47, 64, 64, 0) == 1
+    assert lib.fwi_conv3x3_wgrad_splits(2, 33, 47, 64, 64, 9 * 64 * 64 * 3) in (2, 3)
+    assert 1 <= lib.fwi_conv3x3_wgrad_splits(152, 70, 70, 128, 128, 10 ** 9) <= 16
+    assert lib.fwi_conv3x3_wgrad_splits(1, 4, 4, 96, 64, 10 ** 9) == 0
+    # the tensor-core staging buffer: (cout + 3 cin) x padded pixels x 2 bytes
+    wp = 72
+    assert lib.fwi_conv3x3_wgrad_tc_stage_bytes(152, 70, 70, 128, 256) == \
+        (256 + 3 * 128) * 152 * 72 * wp * 2
+    assert lib.fwi_conv3x3_wgrad_tc_stage_bytes(1, 4, 4, 64, 128) == 0
 
 
 def test_coarse_problem_of_the_benchmark(api):

@@ -89,11 +89,11 @@ def test_weight_gradient_on_the_tensor_cores(mods, n, h, w, c, splits):
     x, dp = _bf16_pair(rng, (n, h, w, c))
     X, dP = BF(x), BF(dp)
     dW = torch.empty((c, 3, 3, c), dtype=torch.float32, device=DEV)
-    stage = torch.empty(A.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, c), dtype=torch.uint8,
+    stage = torch.empty(A.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, c, c), dtype=torch.uint8,
                         device=DEV)
     work = torch.empty(splits * 9 * c * c, dtype=torch.float32, device=DEV) if splits else None
     if splits == 4:
-        assert A.fwi_conv3x3_wgrad_tc_splits(n, h, w, c, work.numel()) == 3
+        assert A.fwi_conv3x3_wgrad_tc_splits(n, h, w, c, c, work.numel()) == 3
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     dW.fill_(float("nan"))
     A.fwi_conv3x3_wgrad_tc(X, dP, dW, stage, work, status)
@@ -129,12 +129,12 @@ def test_weight_gradient_sampled_at_the_benchmark_size(mods, impl):
     dW = torch.empty((c, 3, 3, c), dtype=torch.float32, device=DEV)
     work = torch.empty(A.WGRAD_MAX_SPLITS * 9 * c * c, dtype=torch.float32, device=DEV)
     if impl == "cuda_cores":
-        assert A.fwi_conv3x3_wgrad_splits(n, h, w, c, work.numel()) > 1
+        assert A.fwi_conv3x3_wgrad_splits(n, h, w, c, c, work.numel()) > 1
         A.fwi_conv3x3_wgrad(X, dP, dW, work)
         chain = n * h * w + 16
     else:
-        assert A.fwi_conv3x3_wgrad_tc_splits(n, h, w, c, work.numel()) > 1
-        stage = torch.empty(A.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, c), dtype=torch.uint8,
+        assert A.fwi_conv3x3_wgrad_tc_splits(n, h, w, c, c, work.numel()) > 1
+        stage = torch.empty(A.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, c, c), dtype=torch.uint8,
                             device=DEV)
         A.fwi_conv3x3_wgrad_tc(X, dP, dW, stage, work)
         chain = 2 * (n * (h + 2) * 72 + 64)

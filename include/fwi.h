@@ -477,7 +477,8 @@ FWI_API int fwi_conv3x3_wgrad_splits(int n, int h, int w, int cin, int cout,
                                      long long work_floats);
 
 /* The same weight gradient on the tensor cores (tcgen05, BF16 products, FP32
- * accumulation), cin and cout multiples of 128.  Over the zero-padded pixel
+ * accumulation), cin and cout multiples of 64 (a 64-channel remainder of a
+ * 128-channel block is computed on zero rows).  Over the zero-padded pixel
  * domain q (rows of wp = w + 2 rounded up to a multiple of 8 pixels) the
  * operands are first staged K-major in `stage` (caller-owned, at least
  * fwi_conv3x3_wgrad_tc_stage_bytes(...) bytes): dP^T[co][q] and three copies

@@ -650,7 +650,7 @@ def fwi_conv3x3_wgrad_tc_splits(n, h, w, cin, cout, work_floats):
 
 
 def fwi_conv3x3_wgrad_tc(X, dP, dW, stage, work=None, status=None, stream=None):
-    """The weight gradient on the tensor cores (cin, cout multiples of 128):
+    """The weight gradient on the tensor cores (cin, cout multiples of 64):
     ``stage`` a device buffer of at least fwi_conv3x3_wgrad_tc_stage_bytes
     bytes, ``work`` float32 for the partial tiles (None: one range)."""
     n, h, w, cin, cout, wp, wf = _wgrad_operands(X, dP, dW, work)

@@ -718,7 +718,9 @@ cudaError_t launch_conv_pn(const CUtensorMap &tmx, const CUtensorMap &tmw, const
 // is, per tap, a plain K-major GEMM: M = 128 output channels (operand A),
 // N = 128 input channels of a tap, K = the padded pixels.  dP^T vanishes off
 // the image, so a shifted read that leaves the image (or [0, Q): the TMA fills
-// zeros) contributes nothing.  A job pairs two consecutive (tap, 128-channel
+// zeros) contributes nothing.  A 64-channel remainder of cin or cout loads as a
+// 128-row box whose rows past the tensor read zero; the epilogue stores only
+// the rows and columns inside cout x cin.  A job pairs two consecutive (tap, 128-channel
 // block) units into N = 256 (the MMA's rate per SM grows with N); the K range
 // is split over CTAs (job fastest in the grid, so the CTAs of one split run
 // together and share the dP^T and X^T blocks in L2), each writing its FP32
@@ -934,6 +936,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 const int u = u0 + c / 128, tap = u / a.cbs, cb = u % a.cbs;
                 const int ci = cb * 128 + c % 128;
+                // rows past cout and columns past cin came from zero-filled TMA rows
+                if (co >= a.cout || ci >= a.cin) continue;
                 float4 *dst = reinterpret_cast<float4 *>(o + ((size_t)co * 9 + tap) * a.cin + ci);
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
@@ -976,10 +980,10 @@ WgradTcShape wgrad_tc_shape(int n, int h, int w, int cin, int cout)
     s.wp = (w + 2 + 7) / 8 * 8;
     s.Q = (long long)n * (h + 2) * s.wp;
     s.kblocks = (s.Q + kBK - 1) / kBK;
-    s.cbs = cin / 128;
+    s.cbs = (cin + 127) / 128;          // a 64-channel remainder reads zero rows past cin
     s.units = 9 * s.cbs;
     s.pairs = (s.units + 1) / 2;
-    s.jobs = (cout / 128) * s.pairs;
+    s.jobs = ((cout + 127) / 128) * s.pairs;
     return s;
 }
 
@@ -1097,7 +1101,7 @@ extern "C" {
 
 long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int cin, int cout)
 {
-    if (n < 1 || h < 1 || w < 1 || cin < 128 || cin % 128 != 0 || cout < 128 || cout % 128 != 0)
+    if (n < 1 || h < 1 || w < 1 || cin < 64 || cin % 64 != 0 || cout < 64 || cout % 64 != 0)
         return 0;
     const WgradTcShape g = wgrad_tc_shape(n, h, w, cin, cout);
     return ((long long)cout + 3LL * cin) * g.Q * 2;
@@ -1105,7 +1109,7 @@ long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int cin, int cou
 
 int fwi_conv3x3_wgrad_tc_splits(int n, int h, int w, int cin, int cout, long long work_floats)
 {
-    if (n < 1 || h < 1 || w < 1 || cin < 128 || cin % 128 != 0 || cout < 128 || cout % 128 != 0)
+    if (n < 1 || h < 1 || w < 1 || cin < 64 || cin % 64 != 0 || cout < 64 || cout % 64 != 0)
         return 0;
     return wgrad_tc_splits(wgrad_tc_shape(n, h, w, cin, cout), cin, cout, work_floats);
 }
@@ -1114,9 +1118,8 @@ fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int cin, int cout, const vo
                                 const void *dP, float *dW, void *stage, long long stage_bytes,
                                 float *work, long long work_floats, int *status, void *stream)
 {
-    if (n < 1 || h < 1 || w < 1 || cin < 128 || cin % 128 != 0 || cout < 128 || cout % 128 != 0)
-        return fwi::record_error(FWI_ERR_INVALID_ARG,
-                                 "n, h, w >= 1 and cin, cout multiples of 128");
+    if (n < 1 || h < 1 || w < 1 || cin < 64 || cin % 64 != 0 || cout < 64 || cout % 64 != 0)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "n, h, w >= 1 and cin, cout multiples of 64");
     if (!X || !dP || !dW || !stage)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "X, dP, dW and stage are needed");
     if (((uintptr_t)X | (uintptr_t)dP | (uintptr_t)dW | (uintptr_t)stage | (uintptr_t)work) & 15)

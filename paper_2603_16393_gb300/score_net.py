@@ -110,8 +110,6 @@ class ConvScore:
         return api.WGRAD_MAX_SPLITS * 9 * self.C * self.C
 
     def stage_bytes(self) -> int:
-        if self.C % 128:
-            return 0
         return api.fwi_conv3x3_wgrad_tc_stage_bytes(*self.shape, self.C, self.C)
 
     def refresh(self, stream=None):
@@ -166,8 +164,8 @@ class ConvScore:
         (fwi_channel_sum) and E's (fwi_time_bias_grad), then the output
         gradient of the layer below as in eps_vjp.  ``work``: float32 scratch
         for the weight gradient's partial sums; with ``stage`` (the K-major
-        staging buffer, channels a multiple of 128) the weight gradient runs on
-        the tensor cores (api.fwi_conv3x3_wgrad_tc), else on the CUDA cores
+        staging buffer) the weight gradient runs on the tensor cores
+        (api.fwi_conv3x3_wgrad_tc), else on the CUDA cores
         (api.fwi_conv3x3_wgrad)."""
         api.fwi_pack_channel0(g.contiguous(), self.dH[0], 1.0, stream)
         d, k = self.dH[0], 0
@@ -370,8 +368,8 @@ class UNetScore:
 
     def stage_bytes(self) -> int:
         B = self.shape[0]
-        return max([api.fwi_conv3x3_wgrad_tc_stage_bytes(B, *self.sizes[k], ci, co)
-                    for _, k, ci, co in self.layers if ci % 128 == 0 and co % 128 == 0] or [0])
+        return max(api.fwi_conv3x3_wgrad_tc_stage_bytes(B, *self.sizes[k], ci, co)
+                   for _, k, ci, co in self.layers)
 
     def refresh(self, stream=None):
         for l, (w, b, e) in enumerate(self.params):
@@ -419,7 +417,7 @@ class UNetScore:
         if grads is not None:
             dW, db, dE = grads[l]
             _, _, ci, co = self.layers[l]
-            if stage is not None and ci % 128 == 0 and co % 128 == 0:
+            if stage is not None:
                 api.fwi_conv3x3_wgrad_tc(src, dp, dW, stage, work, stream=stream)
             else:
                 api.fwi_conv3x3_wgrad(src, dp, dW, work, stream)

@@ -134,8 +134,8 @@ def test_training_calls_reject_bad_arguments_without_a_gpu(api):
         lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 96, 64, p, p, p, None, 0, None),   # cin % 64
         lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, 64, p, None, p, None, 0, None),
         lambda: lib.fwi_conv3x3_wgrad(1, 4, 4, 64, 64, ctypes.c_void_p(4100), p, p, None, 0, None),
-        lambda: lib.fwi_conv3x3_wgrad_tc(1, 4, 4, 64, 128, p, p, p, p, 1 << 20, None, 0, None,
-                                         None),                          # cin % 128
+        lambda: lib.fwi_conv3x3_wgrad_tc(1, 4, 4, 96, 128, p, p, p, p, 1 << 20, None, 0, None,
+                                         None),                          # cin % 64
         lambda: lib.fwi_conv3x3_wgrad_tc(1, 4, 4, 128, 128, p, p, p, p, 16, None, 0, None,
                                          None),                          # stage too small
         lambda: lib.fwi_pool2_bf16(1, 4, 4, 12, 0, p, p, None),           # channels % 8
@@ -162,7 +162,8 @@ def test_training_calls_reject_bad_arguments_without_a_gpu(api):
     wp = 72
     assert lib.fwi_conv3x3_wgrad_tc_stage_bytes(152, 70, 70, 128, 256) == \
         (256 + 3 * 128) * 152 * 72 * wp * 2
-    assert lib.fwi_conv3x3_wgrad_tc_stage_bytes(1, 4, 4, 64, 128) == 0
+    assert lib.fwi_conv3x3_wgrad_tc_stage_bytes(1, 4, 4, 96, 128) == 0
+    assert lib.fwi_conv3x3_wgrad_tc_stage_bytes(1, 4, 4, 64, 128) == (128 + 3 * 64) * 6 * 8 * 2
 
 
 def test_coarse_problem_of_the_benchmark(api):

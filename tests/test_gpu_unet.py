@@ -142,7 +142,7 @@ def test_unet_training_lowers_the_held_out_loss(mods):
     x0 = F((v - space.shift) / space.unit)
     net = SN.UNetScore((B, nz, nx), betas, seed=2)
     tr = SN.DSMTrainer(net, lr=1e-3)
-    assert tr.stage is not None           # the 128- and 256-channel levels use the tensor cores
+    assert tr.stage is not None           # every level's weight gradient on the tensor cores
     rng = np.random.default_rng(9)
     held = [(int(t), F(rng.standard_normal((B, nz, nx)))) for t in (50, 250, 500, 900)]
 

@@ -19,6 +19,7 @@ numpy in float64, each function the definition written out:
   dsm_gradients: the loss of one minibatch at one step t and its gradient
                with respect to every (W, b, E), by the chain rule through the
                network of ``oracle/score_net.py`` (bf16 storage points as there)
+  regression_gradients: the same for the supervised loss mean (eps(x) - y)^2
 """
 from __future__ import annotations
 
@@ -77,9 +78,18 @@ def time_bias(b, E, phi):
 def dsm_gradients(weights, x0, z, abar, t, round_bf16: bool = True):
     """(loss, [(dW, db, dE)] per layer) of one minibatch x0, z [B][nz][nx] at
     step t."""
+    return _gradients(weights, noisy(x0, z, abar), z, t, round_bf16)
+
+
+def regression_gradients(weights, x, y, i=0, in_scale=1.0, round_bf16: bool = True):
+    """(loss, [(dW, db, dE)]) of the supervised regression mean (eps(in_scale x, i) - y)^2
+    (a network surrogate trained on pairs)."""
+    return _gradients(weights, in_scale * np.asarray(x, np.float64), y, i, round_bf16)
+
+
+def _gradients(weights, xt, z, t, round_bf16):
     net = N.ConvScore(weights, round_bf16=round_bf16)
     r = net.r
-    xt = noisy(x0, z, abar)
     eps = net.eps(xt, t)
     loss, g = dsm_loss(eps, z)
     L = len(net.W)

@@ -83,6 +83,22 @@ class LowFidelity:
         return J, api.fwi_restrict2_transpose(gc, self.fine.nz, self.fine.nx, stream=stream)
 
 
+class NetworkSurrogate:
+    """A learned surrogate of the physics guidance gradient (the surrogate
+    route to cheaper guidance, Sec. 7): a convolutional network (ConvScore or
+    UNetScore) trained on FD-generated pairs (v, dJ/dv) by
+    DSMTrainer.regression_step, evaluated as
+    dJ/dv ~ out_scale * net(in_scale * v, 0).  Its J is not available (None)."""
+
+    def __init__(self, net, in_scale: float, out_scale: float):
+        self.net, self.in_scale, self.out_scale = net, float(in_scale), float(out_scale)
+        self.g = torch.empty(net.shape, dtype=torch.float32, device=net.dev)
+
+    def gradient(self, v_phys: torch.Tensor, stream=None):
+        self.net.eps(v_phys, 0, self.out_scale, self.g, stream, in_scale=self.in_scale)
+        return None, self.g
+
+
 class Sampler:
     """Algorithm 2 (``guide`` = GuideParams) or Algorithm 1 (``dps_zeta``) on
     a plan of B models.
@@ -90,9 +106,9 @@ class Sampler:
     potential: "w2" (J of Eq. final_objective; needs ``ctx`` from
     plan.w2_prepare), "l2" (Phi_l2 with ``d_obs`` and ``sigma_l2``) or None
     (no guidance: v_{i-1} = v').  Exactly one of ``prior`` and ``score_fn``.
-    surrogate: a LowFidelity W2 potential used instead of the full one in the
-    first ``surrogate_fraction`` of the reverse steps (i > N - round(fraction
-    N)), the full physics after."""
+    surrogate: a LowFidelity W2 potential or a NetworkSurrogate used instead of
+    the full one in the first ``surrogate_fraction`` of the reverse steps
+    (i > N - round(fraction N)), the full physics after."""
 
     def __init__(self, plan: api.Plan, betas: Sequence[float], *, potential: str | None = "w2",
                  ctx=None, d_obs=None, sigma_l2: float = 1.0, prior: GaussianPrior | None = None,
@@ -112,7 +128,7 @@ class Sampler:
         if potential is not None and (guide is None) == (dps_zeta is None):
             raise ValueError("give exactly one of guide (Algorithm 2) and dps_zeta (Algorithm 1)")
         if surrogate is not None and potential != "w2":
-            raise ValueError("the low-fidelity surrogate stands in for the W2 potential")
+            raise ValueError("a surrogate stands in for the W2 potential")
         if not 0.0 <= surrogate_fraction <= 1.0:
             raise ValueError("surrogate_fraction must lie in [0, 1]")
         self.plan, self.potential, self.ctx, self.d_obs = plan, potential, ctx, d_obs

@@ -120,9 +120,9 @@ class ConvScore:
             api.fwi_time_bias(b, e, self.phi, self.bias[l], stream)
 
     def eps(self, x: torch.Tensor, i: int, scale: float = 1.0, out: torch.Tensor | None = None,
-            stream=None) -> torch.Tensor:
-        """scale * eps(x, i) for x [B][nz][nx] (keeps the activations for vjp)."""
-        api.fwi_pack_channel0(x, self.X0, 1.0, stream)
+            stream=None, in_scale: float = 1.0) -> torch.Tensor:
+        """scale * eps(in_scale x, i) for x [B][nz][nx] (keeps the activations for vjp)."""
+        api.fwi_pack_channel0(x, self.X0, in_scale, stream)
         h = self.X0
         for l in range(self.L):
             b = self.bias[l][i]
@@ -205,7 +205,9 @@ class DSMTrainer:
     L2_rewrite for s = -eps / sqrt(1 - abar) weighted by kappa = 1 - abar --
     the parameter gradients (ConvScore.param_grads), one Adam step over the
     flat FP32 parameters (fwi_adam_step) and the refresh of the bf16 weights
-    and bias tables.  ``step`` returns the loss as a device scalar."""
+    and bias tables.  ``step`` returns the loss as a device scalar.
+    ``regression_step`` trains the same network on supervised pairs instead
+    (a network surrogate of the physics gradient, sampler.NetworkSurrogate)."""
 
     def __init__(self, net, lr: float = 1e-3, beta1: float = 0.9,
                  beta2: float = 0.999, eps: float = 1e-8):
@@ -237,6 +239,32 @@ class DSMTrainer:
         api.fwi_dsm_loss(self.e, z, self.loss, self.g, self.work, stream)
         net.param_grads(self.g, t, self.grads, self.work, self.stage, stream)
         return self.loss
+
+    def regression_gradients(self, x: torch.Tensor, y: torch.Tensor, i: int = 0,
+                             in_scale: float = 1.0, stream=None) -> torch.Tensor:
+        """Supervised regression of the network on pairs (x, y), both
+        [B][nz][nx]: the loss mean (eps(in_scale x, i) - y)^2 (the same
+        fwi_dsm_loss) and its gradient in ``grad``; i selects the bias row
+        (0 for a network that is not step-conditioned)."""
+        net = self.net
+        api._f32(x, net.shape, "x")
+        api._f32(y, net.shape, "y")
+        net.eps(x, i, 1.0, self.e, stream, in_scale=in_scale)
+        api.fwi_dsm_loss(self.e, y, self.loss, self.g, self.work, stream)
+        net.param_grads(self.g, i, self.grads, self.work, self.stage, stream)
+        return self.loss
+
+    def regression_step(self, x: torch.Tensor, y: torch.Tensor, i: int = 0,
+                        in_scale: float = 1.0, stream=None) -> torch.Tensor:
+        loss = self.regression_gradients(x, y, i, in_scale, stream)
+        self._update(stream)
+        return loss
+
+    def _update(self, stream=None):
+        self.k += 1
+        api.fwi_adam_step(self.net.theta, self.grad, self.m, self.v, self.k, self.lr, self.beta1,
+                          self.beta2, self.eps_adam, stream)
+        self.net.refresh(stream)
 
     def step(self, x0: torch.Tensor, z: torch.Tensor, t: int, stream=None) -> torch.Tensor:
         loss = self.gradients(x0, z, t, stream)
@@ -383,10 +411,10 @@ class UNetScore:
         return self.A[name]
 
     def eps(self, x: torch.Tensor, i: int, scale: float = 1.0, out: torch.Tensor | None = None,
-            stream=None) -> torch.Tensor:
-        """scale * eps(x, i) for x [B][nz][nx] (keeps the activations for the
-        backward pass)."""
-        api.fwi_pack_channel0(x, self.X0, 1.0, stream)
+            stream=None, in_scale: float = 1.0) -> torch.Tensor:
+        """scale * eps(in_scale x, i) for x [B][nz][nx] (keeps the activations for
+        the backward pass)."""
+        api.fwi_pack_channel0(x, self.X0, in_scale, stream)
         h = self.X0
         for k in range(4):
             if k > 0:

@@ -293,3 +293,77 @@ def test_training_lowers_the_held_out_loss(mods):
     after = held_out()
     assert np.isfinite(after) and torch.isfinite(net.theta).all()
     assert after < 0.7 * before, (before, after)
+
+
+def test_regression_gradients_match_oracle(mods):
+    A, SN = mods
+    B, nz, nx, c = 2, 33, 47, 64
+    betas = D.linear_betas(1000)
+    w = SN.seeded_weights(c, 3, seed=12)
+    net = SN.ConvScore((B, nz, nx), betas, weights=w)
+    tr = SN.DSMTrainer(net)
+    v = models("layered", [3, 4], nz, nx)
+    rng = np.random.default_rng(13)
+    y = rng.standard_normal((B, nz, nx)).astype(np.float32).astype(np.float64)
+    s = 1.0 / 3000.0
+    loss = tr.regression_gradients(F(v), F(y), 0, s)
+    torch.cuda.synchronize()
+    l_ref, g_ref = T.regression_gradients(w, v, y, 0, s)
+    assert abs(float(loss.item()) - l_ref) <= 5 * BF16_ULP * l_ref
+    for l, (got, ref) in enumerate(zip(tr.grads, g_ref)):
+        for k in range(3):
+            assert rel_l2(H(got[k]), ref[k]) <= 8 * BF16_ULP, (l, k)
+
+
+def test_network_surrogate_trained_on_fd_pairs(mods):
+    """A convolutional surrogate of dJ/dv trained on pairs the FD path
+    generates, then standing in for the physics in Algorithm 2's first steps."""
+    A, SN = mods
+    from gpu_cases import problems
+    from paper_2603_16393_gb300 import sampler as S
+    from oracle import oracle as O
+    B, nz, nx = 4, 32, 32
+    gp, op = problems(nz, nx, 12, 300, 2, batch=B, f_peak=25.0)
+    d_obs = O.forward(op, models("layered", list(range(B)), nz, nx))
+    betas = D.linear_betas(1000)
+    rng = np.random.default_rng(14)
+    with A.Plan(gp) as plan:
+        ctx = plan.w2_prepare(F(d_obs))
+        # pairs: smoothed perturbations of a linear model and their W2 gradients
+        pairs = []
+        for _ in range(6):
+            v = 2000.0 + 1500.0 * np.linspace(0, 1, nz)[None, :, None] * np.ones((B, 1, nx))
+            v = v + 150.0 * rng.standard_normal((B, nz, nx))
+            vt = F(v)
+            _, g, _ = plan.gradient(vt, ctx)
+            pairs.append((vt, g.clone()))
+        torch.cuda.synchronize()
+        out_scale = max(float(g.abs().max()) for _, g in pairs)
+        ys = [(g / out_scale).contiguous() for _, g in pairs]
+        net = SN.ConvScore((B, nz, nx), betas, channels=64, seed=3)
+        tr = SN.DSMTrainer(net, lr=2e-3)
+        s = 1.0 / 3000.0
+
+        def loss_all():
+            return float(np.mean([tr.regression_gradients(v, y, 0, s).item()
+                                  for (v, _), y in zip(pairs, ys)]))
+
+        before = loss_all()
+        for k in range(200):
+            j = k % len(pairs)
+            tr.regression_step(pairs[j][0], ys[j], 0, s)
+        torch.cuda.synchronize()
+        after = loss_all()
+        assert np.isfinite(after) and after < 0.5 * before, (before, after)
+        sur = S.NetworkSurrogate(net, s, out_scale)
+        smp = S.Sampler(plan, betas, ctx=ctx, prior=S.GaussianPrior(F(np.zeros((nz, nx))),
+                                                                    F(np.full((nz, nx), 0.1))),
+                        guide=A.GuideParams(rho0=1.0), surrogate=sur, surrogate_fraction=0.4)
+        x = F(0.3 * rng.standard_normal((B, nz, nx)))
+        z = F(rng.standard_normal((B, nz, nx)))
+        v1, info1 = smp.step(x, 900, z)          # the surrogate's phase: no J
+        v2, info2 = smp.step(x, 100, z)          # the physics' phase
+        torch.cuda.synchronize()
+        assert smp.uses_surrogate(900) and not smp.uses_surrogate(100)
+        assert info1["J"] is None and torch.isfinite(info2["J"]).all()
+        assert torch.isfinite(v1).all() and torch.isfinite(v2).all()

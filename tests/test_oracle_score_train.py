@@ -118,3 +118,16 @@ def test_time_bias_at_step_zero():
     # phi(0) = [0 (sines), 1 (cosines)]
     np.testing.assert_allclose(T.time_bias(b, E, N.time_features(0)), b + E[:, 8:].sum(axis=1),
                                rtol=1e-14)
+
+
+def test_regression_at_its_own_output_is_stationary():
+    w = _weights(seed=7)
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((2, 5, 6))
+    y = N.ConvScore(w, round_bf16=False).eps(0.5 * x, 0)
+    loss, grads = T.regression_gradients(w, x, y, 0, 0.5, round_bf16=False)
+    assert loss == 0.0
+    assert all(not np.any(g) for layer in grads for g in layer)
+    # and a shifted target gives the loss of the shift
+    loss2, _ = T.regression_gradients(w, x, y + 0.25, 0, 0.5, round_bf16=False)
+    assert abs(loss2 - 0.0625) < 1e-12

@@ -835,14 +835,14 @@ def run_conv(args, rank, world, local_rank):
                    "l2": f"inputs larger than L2 (x and y {n * h * w * c * 2 / 1e6:.0f} MB each)",
                    "tiles": ("192 pixels (8 x 24) as the MMA's N x 128 channels as its M per "
                              "tile; 6 % of the pixels fall outside the 70 x 70 images"
-                             if c % 256 != 0 and c % 128 == 0 else
+                             if c % 256 != 0 else
                              f"128 pixels (8 x 16) as the MMA's M x {256 if c % 256 == 0 else 64} "
                              "channels as its N per tile; 15 % of the pixels fall outside the "
                              "70 x 70 images") + "; one persistent CTA per SM; outside pixels "
                             "are not credited"},
         "roofline": {"bound": "tensor",
                      "kernel": ("k_conv3x3_tc<256>" if c % 256 == 0 else
-                                "k_conv3x3_tc_pn" if c % 128 == 0 else "k_conv3x3_tc<64>"),
+                                "k_conv3x3_tc_pn"),
                      "achieved": tf,
                      "peak": peak, "unit": "TFLOP/s", "frac": tf / peak, "peak_source": src,
                      "hbm_gb_s": byts / (ms * 1e-3) / 1e9, "algorithmic_bytes": byts},

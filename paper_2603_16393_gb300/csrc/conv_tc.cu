@@ -5,11 +5,12 @@
 //   y[n][p][co] = act(bias[co] + sum_{tap, ci} x[n][p + tap][ci] w[co][tap][ci])
 //
 // as an implicit GEMM: M = 128 output pixels (an 8 x 16 tile of one image),
-// N = BN output channels (256, 128 or 64: the largest that divides cout), K =
-// 9 taps x cin.  Layouts: x NHWC bf16, w [cout][3][3][cin] bf16 (K-major), y
-// NHWC fp32 or bf16.  The MMA rate per SM grows with N: 1.50 PFLOP/s at
-// N = 256 (a 256 -> 256 layer), 0.76 at N = 128 (128 -> 128), 152 x 70 x 70;
-// 128-channel blocks therefore run k_conv3x3_tc_pn below, pixels as N = 192
+// N = 256 output channels (cout a multiple of 256), K = 9 taps x cin.
+// Layouts: x NHWC bf16, w [cout][3][3][cin] bf16 (K-major), y NHWC fp32 or
+// bf16.  The MMA rate per SM grows with N: 1.50 PFLOP/s at N = 256 (a 256 ->
+// 256 layer), 0.76 at N = 128 (128 -> 128), 152 x 70 x 70; every other cout
+// therefore runs k_conv3x3_tc_pn below in 128-channel blocks (a 64-channel
+// remainder on zero-filled weight rows), pixels as N = 192
 // (1.03 PFLOP/s on the 128 -> 128 layer).
 //
 // Operand A comes from one halo box per 64-channel block: the 10 x 18 pixels
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cbs = a.cin / kBK;
-    const int total = a.tiles * (a.cout / kPM);
+    const int total = a.tiles * (((a.cout + kPM - 1) / kPM));
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kAStages; ++s) {
@@ -616,7 +617,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const Tile tl = tile_of_pn(t, a);
             const int co = tl.n0 + q * 32 + lane;
-            const float bias = a.bias ? __ldg(a.bias + co) : 0.f;
+            // a 64-channel remainder: lanes past cout hold the zero rows of the
+            // weight box and store nothing (the TMEM loads stay warp-wide)
+            const bool live = co < a.cout;
+            const float bias = a.bias && live ? __ldg(a.bias + co) : 0.f;
 #pragma unroll 1
             for (int c0 = cbeg; c0 < cend; c0 += 16) {
                 float v[16];
@@ -625,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int j = 0; j < 16; ++j) {
                     const int m = c0 + j;
                     const int px = tl.x0 + (m % kPW), py = tl.y0 + m / kPW;
-                    if (px >= a.w || py >= a.h) continue;
+                    if (!live || px >= a.w || py >= a.h) continue;
                     const size_t pix = ((size_t)tl.img * a.h + py) * a.w + px;
                     const float x = v[j] + bias;
                     const float yv = a.act == 1 ? silu(x) : x;
@@ -703,7 +707,7 @@ cudaError_t launch_conv_pn(const CUtensorMap &tmx, const CUtensorMap &tmw, const
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    const long long total = (long long)a.tiles * (a.cout / kPM);
+    const long long total = (long long)a.tiles * (((a.cout + kPM - 1) / kPM));
     const unsigned grid = (unsigned)(total < sms ? total : sms);
     k_conv3x3_tc_pn<<<grid, kThreads, smem, st>>>(tmx, tmw, a);
     return cudaGetLastError();
@@ -1026,8 +1030,9 @@ fwi_status conv_call(int n, int h, int w, int cin, int cout, const void *x, cons
     if (!x || !wt || !y) return fwi::record_error(FWI_ERR_INVALID_ARG, "x, w and y must not be NULL");
     if (((uintptr_t)x | (uintptr_t)wt | (uintptr_t)y) & 15)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "x, w and y must be 16-byte aligned");
-    // 128-channel blocks (cout not a multiple of 256) run pixels-as-N
-    const bool pn = cout % 256 != 0 && cout % 128 == 0;
+    // cout not a multiple of 256 runs pixels-as-N in 128-channel blocks (a
+    // 64-channel remainder on zero-filled weight rows)
+    const bool pn = cout % 256 != 0;
     const int TW = pn ? kPW : kTW, TH = pn ? kPH : kTH;
     const int tiles_x = (w + TW - 1) / TW, tiles_y = (h + TH - 1) / TH;
     if ((size_t)n * tiles_y * tiles_x * (cout / 64) > 0x7fffffffull ||
@@ -1036,7 +1041,7 @@ fwi_status conv_call(int n, int h, int w, int cin, int cout, const void *x, cons
         return fwi::record_error(FWI_ERR_UNSUPPORTED, "tensor too large for this library");
     auto enc = tmap_encoder();
     if (!enc) return fwi::record_error(FWI_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-    const int BN = cout % 256 == 0 ? 256 : (cout % 128 == 0 ? 128 : 64);
+    const int BN = 256;                  // the pixels-as-M kernel: 256-channel blocks
     CUtensorMap tmx, tmw;
     {
         const cuuint64_t dims[4] = {(cuuint64_t)cin, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
@@ -1054,7 +1059,8 @@ fwi_status conv_call(int n, int h, int w, int cin, int cout, const void *x, cons
     {
         const cuuint64_t dims[2] = {(cuuint64_t)9 * cin, (cuuint64_t)cout};
         const cuuint64_t strides[1] = {(cuuint64_t)9 * cin * 2};
-        const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)BN};
+        // the pixels-as-N kernel reads 128-row weight blocks (rows past cout: zeros)
+        const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)(pn ? kPM : BN)};
         const cuuint32_t estr[2] = {1, 1};
         if (enc(&tmw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(wt), dims, strides,
                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1065,10 +1071,7 @@ fwi_status conv_call(int n, int h, int w, int cin, int cout, const void *x, cons
     ConvArgs a{wait_ns, withhold, n, h, w, cin, cout, act, y_bf16, tiles_x, tiles_y,
                n * tiles_y * tiles_x, bias, y, status};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const cudaError_t e = pn          ? launch_conv_pn(tmx, tmw, a, st)
-                        : BN == 256 ? launch_conv<256>(tmx, tmw, a, st)
-                        : BN == 128 ? launch_conv<128>(tmx, tmw, a, st)
-                                    : launch_conv<64>(tmx, tmw, a, st);
+    const cudaError_t e = pn ? launch_conv_pn(tmx, tmw, a, st) : launch_conv<256>(tmx, tmw, a, st);
     if (e != cudaSuccess)
         return fwi::record_error(FWI_ERR_CUDA, "fwi_conv3x3_bf16 launch: %s", cudaGetErrorString(e));
     return FWI_OK;

@@ -48,7 +48,7 @@ def bound(x, w, y_ref, cin, out_bf16, act):
 @pytest.mark.parametrize("n,h,w,cin,cout,act,use_bias,out_bf16", [
     (2, 70, 70, 64, 64, 0, False, False),      # 70 = 4 x 16 + 6 and 8 x 8 + 6: ragged tiles
     (1, 13, 37, 128, 128, 1, True, False),     # 128-channel blocks, bias + SiLU
-    (1, 9, 20, 192, 192, 0, True, True),       # 64-channel blocks (192 = 3 x 64), bf16 output
+    (1, 9, 20, 192, 192, 0, True, True),       # a 128-channel block + a 64-channel remainder
     (1, 1, 1, 64, 64, 0, False, False),        # one pixel: the centre tap only
     (3, 64, 64, 64, 128, 1, True, False),      # tiles cover the image exactly
     (1, 9, 20, 128, 384, 1, True, True),       # three 128-channel blocks, pixels as the MMA's N

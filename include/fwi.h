@@ -492,6 +492,15 @@ FWI_API fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int cin, int cout, 
                                         long long stage_bytes, float *work,
                                         long long work_floats, int *status, void *stream);
 
+/* Self-check of fwi_conv3x3_wgrad_tc's bounded waits: the same launch with
+ * every copy withheld and a 20 ms bound, so that the MMA issuer's first wait
+ * runs out; the kernel then frees its TMEM and returns, and *status (needed)
+ * reads FWI_ERR_DEVICE_TIMEOUT.  dW is left unspecified; one range. */
+FWI_API fwi_status fwi_conv3x3_wgrad_tc_wait_check(int n, int h, int w, int cin, int cout,
+                                                   const void *X, const void *dP, float *dW,
+                                                   void *stage, long long stage_bytes,
+                                                   int *status, void *stream);
+
 /* Bytes of the K-major staging buffer, (cout + 3 cin) x padded pixels x 2
  * (0 for invalid sizes). */
 FWI_API long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int cin, int cout);

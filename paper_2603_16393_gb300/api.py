@@ -161,6 +161,10 @@ _lib.fwi_conv3x3_wgrad.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, _vp, ctyp
 _lib.fwi_conv3x3_wgrad_tc.restype = _S
 _lib.fwi_conv3x3_wgrad_tc.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, _vp, ctypes.c_longlong,
                                                             _vp, ctypes.c_longlong, _vp, _vp]
+_lib.fwi_conv3x3_wgrad_tc_wait_check.restype = _S
+_lib.fwi_conv3x3_wgrad_tc_wait_check.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, _vp,
+                                                                       ctypes.c_longlong, _vp,
+                                                                       _vp]
 _lib.fwi_conv3x3_wgrad_tc_stage_bytes.restype = ctypes.c_longlong
 _lib.fwi_conv3x3_wgrad_tc_stage_bytes.argtypes = [ctypes.c_int] * 5
 _lib.fwi_conv3x3_wgrad_tc_splits.restype = ctypes.c_int
@@ -659,6 +663,15 @@ def fwi_conv3x3_wgrad_tc(X, dP, dW, stage, work=None, status=None, stream=None):
     _check(_lib.fwi_conv3x3_wgrad_tc(n, h, w, cin, cout, _ptr(X), _ptr(dP), _ptr(dW), _ptr(stage),
                                      stage.numel() * stage.element_size(), wp, wf, _ptr(status),
                                      _stream(stream)))
+
+
+def fwi_conv3x3_wgrad_tc_wait_check(X, dP, dW, stage, status, stream=None):
+    """The weight gradient's bounded-wait self-check: *status becomes
+    FWI_ERR_DEVICE_TIMEOUT and the call returns normally."""
+    n, h, w, cin, cout, _, _ = _wgrad_operands(X, dP, dW, None)
+    _check(_lib.fwi_conv3x3_wgrad_tc_wait_check(n, h, w, cin, cout, _ptr(X), _ptr(dP), _ptr(dW),
+                                                _ptr(stage), stage.numel() * stage.element_size(),
+                                                _ptr(status), _stream(stream)))
 
 
 def _bf16_nhwc(t, name):

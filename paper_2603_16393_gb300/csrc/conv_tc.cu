@@ -739,6 +739,7 @@ constexpr uint32_t kGTmemCols = 256;
 
 struct WgradTcArgs {
     unsigned long long wait_ns;
+    int withhold;             // 1: issue no copies (the bounded-wait self-check)
     int cin, cout, cbs, wp;   // channels, 128-channel blocks of cin, padded row pitch
     int units, pairs, jobs;
     long long kblocks, per_split;
@@ -883,6 +884,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (long long kb = k0; kb < k1 && !*vfailed; ++kb, ++i) {
                 const int s = i % kGStages, r = i / kGStages;
                 if (r > 0 && !mb_wait(&empty[s], (unsigned)((r - 1) & 1), vfailed, a.wait_ns)) break;
+                if (a.withhold) continue;
                 mb_expect(&full[s], (unsigned)(kGABytes + nb * kGUBytes));
                 const int q0 = (int)(kb * kBK);
                 tma_2d(sA + s * kGABytes, &tma, q0, co0, &full[s]);
@@ -1100,6 +1102,15 @@ fwi_status fwi_conv3x3_bf16_wait_check(int n, int h, int w, int cin, int cout, c
 
 }  // extern "C"
 
+namespace {
+
+fwi_status wgrad_tc_call(int n, int h, int w, int cin, int cout, const void *X, const void *dP,
+                         float *dW, void *stage, long long stage_bytes, float *work,
+                         long long work_floats, int *status, void *stream, int withhold,
+                         unsigned long long wait_ns);
+
+}  // namespace
+
 extern "C" {
 
 long long fwi_conv3x3_wgrad_tc_stage_bytes(int n, int h, int w, int cin, int cout)
@@ -1120,6 +1131,29 @@ int fwi_conv3x3_wgrad_tc_splits(int n, int h, int w, int cin, int cout, long lon
 fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int cin, int cout, const void *X,
                                 const void *dP, float *dW, void *stage, long long stage_bytes,
                                 float *work, long long work_floats, int *status, void *stream)
+{
+    return wgrad_tc_call(n, h, w, cin, cout, X, dP, dW, stage, stage_bytes, work, work_floats,
+                         status, stream, 0, kWaitNs);
+}
+
+fwi_status fwi_conv3x3_wgrad_tc_wait_check(int n, int h, int w, int cin, int cout, const void *X,
+                                           const void *dP, float *dW, void *stage,
+                                           long long stage_bytes, int *status, void *stream)
+{
+    if (!status)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "the wait check needs a status word");
+    return wgrad_tc_call(n, h, w, cin, cout, X, dP, dW, stage, stage_bytes, nullptr, 0, status,
+                         stream, 1, kCheckWaitNs);
+}
+
+}  // extern "C"
+
+namespace {
+
+fwi_status wgrad_tc_call(int n, int h, int w, int cin, int cout, const void *X, const void *dP,
+                         float *dW, void *stage, long long stage_bytes, float *work,
+                         long long work_floats, int *status, void *stream, int withhold,
+                         unsigned long long wait_ns)
 {
     if (n < 1 || h < 1 || w < 1 || cin < 64 || cin % 64 != 0 || cout < 64 || cout % 64 != 0)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "n, h, w >= 1 and cin, cout multiples of 64");
@@ -1159,7 +1193,8 @@ fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int cin, int cout, const vo
             return fwi::record_error(FWI_ERR_CUDA, "tensor map of the staged operands rejected");
     }
     WgradTcArgs a;
-    a.wait_ns = kWaitNs;
+    a.wait_ns = wait_ns;
+    a.withhold = withhold;
     a.cin = cin;
     a.cout = cout;
     a.cbs = g.cbs;
@@ -1191,4 +1226,4 @@ fwi_status fwi_conv3x3_wgrad_tc(int n, int h, int w, int cin, int cout, const vo
     return FWI_OK;
 }
 
-}  // extern "C"
+}  // namespace

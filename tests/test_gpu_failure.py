@@ -46,3 +46,32 @@ def test_halo_waits_time_out_and_recover(api, family):
         torch.cuda.synchronize()
         plan.check()
     assert rel_l2(d2.double().cpu().numpy(), O.forward(op, v)) <= TOL_DATA
+
+
+def test_weight_gradient_wait_runs_out_and_reports():
+    """The tensor-core weight gradient with every copy withheld: its bounded
+    waits run out, the launch returns, the status word says so, and the next
+    weight gradient on the same context is correct."""
+    import numpy as np
+    from paper_2603_16393_gb300 import api as A
+    from oracle import score_train as T
+    dev = "cuda:0"
+    n, h, w, c = 1, 9, 13, 128
+    rng = np.random.default_rng(21)
+    x = torch.tensor(rng.standard_normal((n, h, w, c)), dtype=torch.float32).to(torch.bfloat16)
+    dp = torch.tensor(rng.standard_normal((n, h, w, c)), dtype=torch.float32).to(torch.bfloat16)
+    X, dP = x.to(dev), dp.to(dev)
+    dW = torch.empty((c, 3, 3, c), dtype=torch.float32, device=dev)
+    stage = torch.empty(A.fwi_conv3x3_wgrad_tc_stage_bytes(n, h, w, c, c), dtype=torch.uint8,
+                        device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    A.fwi_conv3x3_wgrad_tc_wait_check(X, dP, dW, stage, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == A.FWI_ERR_DEVICE_TIMEOUT
+    status.zero_()
+    A.fwi_conv3x3_wgrad_tc(X, dP, dW, stage, None, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = T.conv3x3_wgrad(x.double().numpy(), dp.double().numpy())
+    got = dW.double().cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)

@@ -734,14 +734,18 @@ def run_sampler(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded layered models; Gaussian prior fitted to 64 seeded models)",
         "config": {"workload": f"{B} x 70x70 models per GPU, reverse steps {i0}..{i0 - total + 1} "
-                               "of a 1000-step linear schedule; per step: prior score, clean "
-                               "estimate, proposal, W2 gradient (5 shots, 1000 steps), chain "
-                               "rule, preconditioned update",
+                               "of a 1000-step linear schedule; per step: "
+                               + ("network score and its vector-Jacobian product"
+                                  if net else "prior score")
+                               + ", clean estimate, proposal, W2 gradient (5 shots, 1000 steps), "
+                               "chain rule, preconditioned update",
                    "batch_per_gpu": B,
                    "l2": "inputs larger than L2 (wavefield record 10 GB per step)",
-                   "score": ("3-layer 128-channel convolutional noise-prediction network on the "
-                             "tensor cores (seeded weights)" if net else "Gaussian prior fitted "
-                             "to 64 seeded models"),
+                   "score": ({"conv": "3-layer 128-channel convolutional noise-prediction "
+                                      "network on the tensor cores (seeded weights)",
+                              "unet": "4-level U-Net noise-prediction network (widths 64-256) "
+                                      "on the tensor cores (seeded weights)"}[args.score]
+                             if net else "Gaussian prior fitted to 64 seeded models"),
                    "score_network_ms_per_step": net_ms,
                    "surrogate_fraction": frac,
                    "ms_per_step_full_physics": ms,

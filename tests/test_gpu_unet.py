@@ -157,3 +157,38 @@ def test_unet_training_lowers_the_held_out_loss(mods):
     after = held_out()
     assert np.isfinite(after) and torch.isfinite(net.theta).all()
     assert after < 0.7 * before, (before, after)
+
+
+@pytest.mark.parametrize("net_kind", ["unet", "conv"])
+def test_full_batch_sampled_images_match_oracle(mods, net_kind):
+    """152 models of 70 x 70 (the benchmark's batch and launch shapes): every
+    layer acts on each image alone, so sampled images of eps and of the
+    vector-Jacobian product are checked against the oracle run on them."""
+    from oracle import score_net as NO
+    A, _, SN = mods
+    B, nz, nx = 152, 70, 70
+    betas = D.linear_betas(1000)
+    if net_kind == "unet":
+        w = SN.unet_seeded_weights(SN.UNET_WIDTHS, seed=5)
+        net = SN.UNetScore((B, nz, nx), betas, weights=w)
+    else:
+        w = SN.seeded_weights(128, 3, seed=5)
+        net = SN.ConvScore((B, nz, nx), betas, weights=w)
+    rng = np.random.default_rng(15)
+    x = rng.standard_normal((B, nz, nx)).astype(np.float32).astype(np.float64)
+    g = rng.standard_normal((B, nz, nx)).astype(np.float32).astype(np.float64)
+    i = 640
+    e = H(net.eps(F(x), i))
+    u = H(net.eps_vjp(F(g), 1.0))
+    torch.cuda.synchronize()
+    for b in (0, 77, 151):
+        if net_kind == "unet":
+            ref = U.UNet(w, SN.UNET_WIDTHS, round_bf16=True)
+            e_o = ref.eps(x[b:b + 1], i)
+            u_o = ref.backward(g[b:b + 1], 1.0)
+        else:
+            ref = NO.ConvScore(w, round_bf16=True)
+            e_o = ref.eps(x[b:b + 1], i)
+            u_o = ref.eps_vjp(g[b:b + 1], 1.0)
+        assert rel_l2(e[b:b + 1], e_o) <= 8 * BF16_ULP, (b, rel_l2(e[b:b + 1], e_o))
+        assert rel_l2(u[b:b + 1], u_o) <= 8 * BF16_ULP, (b, rel_l2(u[b:b + 1], u_o))

@@ -621,7 +621,15 @@ def run_sampler(args, rank, world, local_rank):
     elif args.score == "unet":
         from paper_2603_16393_gb300 import score_net as SN
         net = SN.UNetScore((B, nz, nx), betas, device=dev)
-    lowfi = S.LowFidelity(plan, d_obs) if frac > 0 else None
+    lowfi = None
+    if frac > 0 and args.surrogate == "net":
+        # a 3-layer 128-channel convolutional surrogate of dJ/dv (seeded weights: the
+        # cost of a trained one; scales as a trained surrogate would use them)
+        from paper_2603_16393_gb300 import score_net as SN
+        lowfi = S.NetworkSurrogate(SN.ConvScore((B, nz, nx), betas, seed=9, device=dev),
+                                   1.0 / 3000.0, 1e-3)
+    elif frac > 0:
+        lowfi = S.LowFidelity(plan, d_obs)
     smp = S.Sampler(plan, betas, ctx=ctx, prior=None if net else prior, score_fn=net,
                     guide=api.GuideParams(rho0=1.15, gamma=0.55), surrogate=lowfi,
                     surrogate_fraction=frac if frac > 0 else 0.4)
@@ -676,7 +684,8 @@ def run_sampler(args, rank, world, local_rank):
         b.record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
-        lowfi.plan.check()
+        if isinstance(lowfi, S.LowFidelity):
+            lowfi.plan.check()
         ms_sur = max_over_ranks([a.elapsed_time(b) / args.steps], world, dev)[0]
 
     # the two elementwise kernels alone, at this batch (bytes: v_i, z read,
@@ -726,8 +735,8 @@ def run_sampler(args, rank, world, local_rank):
     chain_ms = (n_sur * ms_sur if ms_sur else 0.0) + (1000 - n_sur) * ms
     line = {
         "metric": "Algorithm 2 reverse steps x models/s (70x70, 5 shots, 1000 steps, W2 guidance"
-                  + (f"; low-fidelity guidance in the first {frac:.0%} of 1000 steps)" if lowfi
-                     else ")"),
+                  + (f"; {'network-surrogate' if args.surrogate == 'net' else 'low-fidelity'} "
+                     f"guidance in the first {frac:.0%} of 1000 steps)" if lowfi else ")"),
         "value": world * B * 1000 / (chain_ms * 1e-3), "unit": "model-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": chain_ms / 1000,
         "higher_is_better": True,
@@ -1016,6 +1025,9 @@ def main():
     ap.add_argument("--surrogate-fraction", type=float, default=0.0,
                     help="--sampler: low-fidelity guidance (2x coarser grid and time step) in "
                          "this fraction of the first reverse steps")
+    ap.add_argument("--surrogate", choices=["lowfi", "net"], default="lowfi",
+                    help="--sampler with --surrogate-fraction: the physics-based low-fidelity "
+                         "surrogate or a convolutional network surrogate of dJ/dv")
     ap.add_argument("--conv-channels", type=int, default=128,
                     help="--conv: input and output channels (a multiple of 64)")
     ap.add_argument("--dsm-train", action="store_true",

@@ -113,6 +113,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     Plan *pl = new (std::nothrow) Plan();
     if (!pl) return fail(FWI_ERR_INVALID_ARG, "out of host memory");
     pl->fwd_pair = false;
+    pl->adj_pair = false;
     pl->tiled = false;
     pl->p = p;
     pl->p.space_order = order;
@@ -197,6 +198,16 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
             sh.smem = fwi::fast_smem(fwi::kPairPitch, pl->fast_NZM, false, chunk, p.nr);
             if (chunk < 1) pl->fwd_pair = false;
             if (nstrip2 * sh.rows > pl->nzs) pl->nzs = nstrip2 * sh.rows;
+        }
+        if (pl->fwd_pair) {   // the adjoint on the same column pairs
+            fwi::ResidentShape sh = pl->shape;
+            const int chunk = fwi::fast_chunk(fwi::kPairPitch, pl->fast_NZM, true, p.nr);
+            sh.chunk = chunk;
+            sh.smem = fwi::fast_smem(fwi::kPairPitch, pl->fast_NZM, true, chunk, p.nr);
+            if (chunk >= 1) {
+                pl->shape_adj = sh;
+                pl->adj_pair = true;
+            }
         }
         if (!pl->fwd_pair && pl->fast) {   // restore the single-column forward shape
             fwi::ResidentShape &sh = pl->shape;

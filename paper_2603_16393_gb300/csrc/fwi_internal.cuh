@@ -81,6 +81,7 @@ struct Plan {
     int NXp;                   // tiled: row pitch of the fields (NX rounded up to 4)
     int rec_pitch;             // row pitch of a record plane
     bool fwd_pair;             // forward on column pairs (even padded width)
+    bool adj_pair;             // adjoint on column pairs (same condition)
     int fast_P, fast_PR, fast_NZM;  // their shared-memory pitch, record pitch, row capacity
     int nzs;                   // rows of one wavefield-record plane (>= NZ)
     // byte offsets inside the caller buffers
@@ -109,6 +110,8 @@ struct PropArgs {
                                          // times are formed in double, rounded once
     double ex0d, ez0d;                   // eta0 * dt / 2 per axis, double
     float c0, cx1, cx2, cz1, cz2;        // Laplacian weights divided by h^2
+    float2 w2[5];                        // the same weights in pairs (c0, cx1, cx2, cz1,
+                                         // cz2), operands of the packed instructions
     float ex0, ez0;                      // eta0 * dt / 2 per axis
     float inv_nb;
     float fp, t0, src_scale;             // Ricker and 1/(dx dz)

@@ -328,6 +328,10 @@ PropArgs make_args(const Plan &pl)
     a.cx2 = (float)(-1.0 / 12.0 * ix2);
     a.cz1 = (float)(4.0 / 3.0 * iz2);
     a.cz2 = (float)(-1.0 / 12.0 * iz2);
+    {
+        const float w[5] = {a.c0, a.cx1, a.cx2, a.cz1, a.cz2};
+        for (int k = 0; k < 5; ++k) a.w2[k] = make_float2(w[k], w[k]);
+    }
     const double lnR = std::log(1.0 / (double)p.refl_R);
     const double eta0x = p.nb > 0 ? 3.0 * p.v_ref * lnR / (p.nb * (double)p.dx) : 0.0;
     const double eta0z = p.nb > 0 ? 3.0 * p.v_ref * lnR / (p.nb * (double)p.dz) : 0.0;

@@ -28,6 +28,7 @@
 
 #include <cmath>
 
+#include "f32x2.cuh"
 #include "fwi_device.cuh"
 #include "fwi_internal.cuh"
 
@@ -225,49 +226,46 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
 // Same arithmetic as k_fwd_fast, but each thread owns two adjacent columns
 // (x, x+1) and 11 rows, and moves them as float2: per row three 8-byte
 // loads ((x-2, x-1), the window row z+2, (x+2, x+3)) and one 8-byte store
-// serve two cell-updates.  Needs an even padded width.
+// serve two cell-updates.  The two columns go through the packed f32x2
+// instructions (one instruction per operation for both cells; results
+// bitwise those of the scalar code).  Needs an even padded width.
 constexpr int ROWS2 = kFastRows / 2;
 
 template <int P, int PR, int TOPBC, bool STORE>
 __device__ __forceinline__ void fwd_rows_pair(const float *__restrict__ cp, float *__restrict__ np,
                                               const float *__restrict__ abp,
                                               float *__restrict__ sw, bool top_strip,
-                                              float (&ka)[2 * ROWS2], float (&vi)[2 * ROWS2],
+                                              const float2 (&ka)[ROWS2], float2 (&vi)[ROWS2],
                                               const PropArgs &a)
 {
-    float2 wm2 = *(const float2 *)(cp - 2 * P), wm1 = *(const float2 *)(cp - P);
-    float2 w0 = *(const float2 *)cp, wp1 = *(const float2 *)(cp + P);
+    using namespace f2;
+    const float2 CX1 = splat(a.cx1), CX2 = splat(a.cx2), CZ1 = splat(a.cz1), CZ2 = splat(a.cz2);
+    float2 wm2 = ld(cp - 2 * P), wm1 = ld(cp - P), w0 = ld(cp), wp1 = ld(cp + P);
 #pragma unroll
     for (int r = 0; r < ROWS2; ++r) {
         const float *c = cp + r * P;
-        const float2 wp2 = *(const float2 *)(c + 2 * P);
-        const float2 L = *(const float2 *)(c - 2);     // u[x-2], u[x-1]
-        const float2 R = *(const float2 *)(c + 2);     // u[x+2], u[x+3]
+        const float2 wp2 = ld(c + 2 * P);
+        const float2 L = ld(c - 2);     // u[x-2], u[x-1]
+        const float2 R = ld(c + 2);     // u[x+2], u[x+3]
+        // x, first neighbours: (u[x-1] - u[x]) + (u[x+1] - u[x]) per column
         const float d01 = w0.y - w0.x;
-        const float dxA0 = (L.y - w0.x) + d01;
-        const float dxB0 = (L.x - w0.x) + (R.x - w0.x);
-        const float dxA1 = (R.x - w0.y) - d01;
-        const float dxB1 = (L.y - w0.y) + (R.y - w0.y);
-        const float dzA0 = (wm1.x - w0.x) + (wp1.x - w0.x);
-        const float dzA1 = (wm1.y - w0.y) + (wp1.y - w0.y);
-        const float dzB0 = (wm2.x - w0.x) + (wp2.x - w0.x);
-        const float dzB1 = (wm2.y - w0.y) + (wp2.y - w0.y);
-        float lap0 = a.cx1 * dxA0, lap1 = a.cx1 * dxA1;
-        lap0 = fmaf(a.cx2, dxB0, lap0);
-        lap1 = fmaf(a.cx2, dxB1, lap1);
-        lap0 = fmaf(a.cz1, dzA0, lap0);
-        lap1 = fmaf(a.cz1, dzA1, lap1);
-        lap0 = fmaf(a.cz2, dzB0, lap0);
-        lap1 = fmaf(a.cz2, dzB1, lap1);
-        const float2 ab = *(const float2 *)(abp + r * P);
-        vi[2 * r] = fmaf(ka[2 * r], lap0, ab.x * vi[2 * r]);
-        vi[2 * r + 1] = fmaf(ka[2 * r + 1], lap1, ab.y * vi[2 * r + 1]);
-        const float2 un = make_float2(w0.x + vi[2 * r], w0.y + vi[2 * r + 1]);
-        *(float2 *)(np + r * P) = un;
+        const float2 dxA = make_float2((L.y - w0.x) + d01, (R.x - w0.y) - d01);
+        // x, second neighbours; z
+        const float2 dxB = add(sub(L, w0), sub(R, w0));
+        const float2 dzA = add(sub(wm1, w0), sub(wp1, w0));
+        const float2 dzB = add(sub(wm2, w0), sub(wp2, w0));
+        float2 lap = mul(CX1, dxA);
+        lap = fma(CX2, dxB, lap);
+        lap = fma(CZ1, dzA, lap);
+        lap = fma(CZ2, dzB, lap);
+        const float2 ab = ld(abp + r * P);
+        vi[r] = fma(ka[r], lap, mul(ab, vi[r]));
+        const float2 un = add(w0, vi[r]);
+        st(np + r * P, un);
         if (TOPBC == 1 && (r == 1 || r == 2)) {
-            if (top_strip) *(float2 *)(np - r * P) = un;  // mirrored ghost rows -1, -2
+            if (top_strip) st(np - r * P, un);   // mirrored ghost rows -1, -2
         }
-        if (STORE) *(float2 *)(sw + r * PR) = make_float2(lap0, lap1);
+        if (STORE) st(sw + r * PR, lap);
         wm2 = wm1;
         wm1 = w0;
         w0 = wp1;
@@ -297,23 +295,23 @@ k_fwd_pair(const __grid_constant__ PropArgs a)
     const bool active = strip < a.nstrip;
     const int x = 2 * xp, z0 = strip * ROWS2;
     const float *vb = a.v + (size_t)b * a.nz * a.nx;
-    float ka[2 * ROWS2], vi[2 * ROWS2];
+    float2 ka[ROWS2], vi[ROWS2];
     int bad = 0;
 #pragma unroll
     for (int r = 0; r < ROWS2; ++r) {
+        float k[2] = {0.f, 0.f};
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int z = z0 + r;
-            float k = 0.f;
             if (active && z < NZ) {
                 const int ixc = min(max(x + c - a.nb, 0), a.nx - 1);
                 const float vv = vb[min(z, a.nz - 1) * a.nx + ixc];
                 if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
-                k = kappaA_cell(vv, x + c, z, a);
+                k[c] = kappaA_cell(vv, x + c, z, a);
             }
-            ka[2 * r + c] = k;
-            vi[2 * r + c] = 0.f;
         }
+        ka[r] = make_float2(k[0], k[1]);
+        vi[r] = make_float2(0.f, 0.f);
     }
     if (__syncthreads_or(bad)) {
         if (tid == 0) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
@@ -345,11 +343,7 @@ k_fwd_pair(const __grid_constant__ PropArgs a)
 #pragma unroll
             for (int r = 0; r < ROWS2; ++r) {
                 const int z = z0 + r;
-                if (z < NZ) {
-                    const float2 w = *(const float2 *)(st + cells + z * NX + x);
-                    vi[2 * r] = w.x;
-                    vi[2 * r + 1] = w.y;
-                }
+                if (z < NZ) vi[r] = *(const float2 *)(st + cells + z * NX + x);
             }
         }
         __syncthreads();
@@ -373,9 +367,7 @@ k_fwd_pair(const __grid_constant__ PropArgs a)
 #pragma unroll
                     for (int r = 0; r < ROWS2; ++r) {
                         const int z = z0 + r;
-                        if (z < NZ)
-                            *(float2 *)(st + cl + z * NX + x) =
-                                make_float2(vi[2 * r], vi[2 * r + 1]);
+                        if (z < NZ) *(float2 *)(st + cl + z * NX + x) = vi[r];
                     }
                 }
             }
@@ -393,12 +385,16 @@ k_fwd_pair(const __grid_constant__ PropArgs a)
                     // point source: + kappa A s at the source cell (increment and field)
                     float kas = 0.f;
 #pragma unroll
-                    for (int k = 0; k < 2 * ROWS2; ++k)
-                        if (k == src_k) kas = ka[k];
+                    for (int k = 0; k < ROWS2; ++k) {
+                        if (2 * k == src_k) kas = ka[k].x;
+                        if (2 * k + 1 == src_k) kas = ka[k].y;
+                    }
                     const float d = kas * ricker_scaled(j, a);
 #pragma unroll
-                    for (int k = 0; k < 2 * ROWS2; ++k)
-                        if (k == src_k) vi[k] += d;
+                    for (int k = 0; k < ROWS2; ++k) {
+                        if (2 * k == src_k) vi[k].x += d;
+                        if (2 * k + 1 == src_k) vi[k].y += d;
+                    }
                     const int sz = a.src_pz[s], sx = a.src_px[s];
                     nxt[(sz + 2) * P + sx + 2] += d;
                     if (TOPBC == 1 && (sz == 1 || sz == 2)) nxt[(2 - sz) * P + sx + 2] += d;
@@ -656,6 +652,274 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
     }
 }
 
+// ------------------------------------------------------------------ adjoint, column pairs
+// k_adj_fast with the column-pair ownership of k_fwd_pair: each thread owns
+// columns (x, x+1) x 11 rows, moves them as float2 and updates both columns
+// with the packed f32x2 instructions.  Per column the operations and their
+// order are those of adj_rows, so the results are bitwise k_adj_fast's
+// (the mirrored-top correction apart, whose two products k_adj_fast leaves
+// to the compiler's contraction).  A thread may own the receivers of both
+// of its columns (one per column and strip).
+//
+// Record reads: a whole record plane is prefetched into L2 two steps before
+// it is used (one bulk prefetch per step), and each thread keeps a ring of
+// KR rows in flight (the record of row r + KR is loaded when row r is
+// updated), which holds 2 KR registers instead of a whole strip's 22.
+constexpr int KR = 4;
+
+// L2 prefetch of a record plane (16-byte aligned, size a multiple of 16) in
+// 4 KB pieces, one piece per thread of the first warps
+__device__ __forceinline__ void prefetch_plane_l2(const float *p, size_t bytes, int tid)
+{
+    const size_t off = (size_t)tid * 4096;
+    if (off < bytes) {
+        const unsigned n = (unsigned)min((size_t)4096, bytes - off);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((const char *)p + off),
+                     "r"(n)
+                     : "memory");
+    }
+}
+
+template <int P, int PR, int TOPBC>
+__device__ __forceinline__ void adj_rows_pair(const float *__restrict__ cp,
+                                              float *__restrict__ np,
+                                              const float *__restrict__ kp,
+                                              const float *__restrict__ sr,
+                                              const float *__restrict__ sr_next, float zbf,
+                                              float2 ex, bool top_strip, bool active,
+                                              float2 (&acc)[ROWS2], float2 (&rq)[KR],
+                                              const PropArgs &a)
+{
+    using namespace f2;
+    const float2 &C0 = a.w2[0], &CX1 = a.w2[1], &CX2 = a.w2[2], &CZ1 = a.w2[3], &CZ2 = a.w2[4];
+    float2 wm2 = ld(cp - 2 * P), wm1 = ld(cp - P), w0 = ld(cp), wp1 = ld(cp + P);
+#pragma unroll
+    for (int r = 0; r < ROWS2; ++r) {
+        const float *c = cp + r * P;
+        const float2 wp2 = ld(c + 2 * P);
+        const float2 L = ld(c - 2);     // u[x-2], u[x-1]
+        const float2 R = ld(c + 2);     // u[x+2], u[x+3]
+        float2 lap = mul(C0, w0);
+        lap = fma(CX1, make_float2(L.y + w0.y, w0.x + R.x), lap);
+        lap = fma(CX2, add(L, R), lap);
+        lap = fma(CZ1, add(wm1, wp1), lap);
+        lap = fma(CZ2, add(wm2, wp2), lap);
+        if (TOPBC == 1 && (r == 1 || r == 2)) {
+            // transpose of the mirrored top: reflected weights back onto rows 1, 2
+            if (top_strip) lap = (r == 1) ? add(lap, fma(CZ2, w0, mul(CZ1, wm1)))
+                                          : fma(CZ2, wm2, lap);
+        }
+        const float ez = ez_of(zbf + (float)r, a);
+        const float2 h = add(splat(1.f), add(ex, splat(ez)));          // 1 + e
+        const float2 A2 = make_float2(__fdividef(2.f, h.x), __fdividef(2.f, h.y));   // 2A
+        const float2 nAB = fma(A2, splat(-1.f), splat(1.f));            // -A B = 1 - 2A
+        const float2 fo = ld(np + r * P);
+        const float2 fn = fma(ld(kp + r * P), lap, fma(A2, w0, mul(nAB, fo)));
+        if (active) st(np + r * P, fn);
+        acc[r] = fma(fn, rq[0], acc[r]);
+#pragma unroll
+        for (int i = 0; i + 1 < KR; ++i) rq[i] = rq[i + 1];
+        rq[KR - 1] = (r + KR < ROWS2) ? ld(sr + (r + KR) * PR) : ld(sr_next + (r + KR - ROWS2) * PR);
+        wm2 = wm1;
+        wm1 = w0;
+        w0 = wp1;
+        wp1 = wp2;
+    }
+}
+
+template <int P, int PR, int NZM, int TOPBC>
+__global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_constant__ PropArgs a)
+{
+    extern __shared__ __align__(16) float sm[];
+    constexpr int FSZ = (NZM + 4) * P;
+    static_assert(P % 2 == 0 && PR % 4 == 0 && FSZ % 2 == 0,
+                  "float2 rows need even pitches; record planes are prefetched in 16-byte units");
+    float *U0 = sm, *U1 = sm + FSZ, *K = sm + 2 * FSZ, *IC = K + NZM * P, *ST = IC + a.nr;
+    float *RS = ST + a.chunk * a.nr;
+    const int NX = a.NX, NZ = a.NZ;
+    const int bs = blockIdx.x, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < 2 * FSZ; i += nth) sm[i] = 0.f;
+    const float *vb = a.v + (size_t)b * a.nz * a.nx;
+    // kappa / B at each receiver cell (its adjoint source enters through the
+    // old level)
+    for (int i = tid; i < a.nr; i += nth) {
+        const int rz = a.rec_pz[i], rx = a.rec_px[i];
+        const float vv = vb[min(rz, a.nz - 1) * a.nx + min(max(rx - a.nb, 0), a.nx - 1)];
+        const double vdt = (double)vv * a.dtd;
+        IC[i] = (float)(vdt * vdt / (1.0 - e_cell(rx, rz, a)));
+    }
+    int bad = 0;
+    for (int i = tid; i < NZM * P; i += nth) {
+        const int pz = i / P, px = i - (i / P) * P;
+        float k = 0.f;
+        if (pz < NZ && px < NX) {
+            const float vv = vb[min(pz, a.nz - 1) * a.nx + min(max(px - a.nb, 0), a.nx - 1)];
+            if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
+            k = kappaA_cell(vv, px, pz, a);
+        }
+        K[i] = k;   // kappa A per cell (0 outside the grid: dead rows stay zero)
+    }
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
+        return;
+    }
+
+    // inactive threads (past the last strip) run the same instructions on the
+    // addresses of strip 0, columns 0 and 1, with every write gated
+    const int NXP = NX / 2;
+    const int strip = tid / NXP;
+    const bool active = strip < a.nstrip;
+    const int x = active ? 2 * (tid % NXP) : 0;
+    const int z0 = active ? strip * ROWS2 : 0;
+    const float2 ex = make_float2(ex_of(x, a), ex_of(x + 1, a));
+    const float zbf = (float)(z0 - (a.nz - 1));
+    const bool top_strip = active && z0 == 0;
+
+    // receivers owned by this thread (one per column at most)
+    int inj0 = -1, inj1 = -1;
+    for (int i = 0; i < a.nr; ++i) {
+        const int rz = a.rec_pz[i], rx = a.rec_px[i];
+        if (active && rz >= z0 && rz < z0 + ROWS2) {
+            if (rx == x) inj0 = i;
+            if (rx == x + 1) inj1 = i;
+        }
+    }
+    const int inj0_off = inj0 >= 0 ? (a.rec_pz[inj0] + 2) * P + x + 2 : 0;
+    const int inj1_off = inj1 >= 0 ? (a.rec_pz[inj1] + 2) * P + x + 3 : 0;
+    __shared__ float acc_src;
+    if (tid == 0) acc_src = 0.f;
+
+    const size_t plane = (size_t)a.nzs * PR;
+    const int jb = a.j_begin;
+    float2 acc[ROWS2], rq[KR];
+    // record plane of adjoint step j: forward step nt-1-j
+    const float *plane_jb =
+        a.snap + ((size_t)bs * a.rec_planes + (a.nt - 1 - jb - a.rec_base)) * plane;
+    const float *sr = plane_jb + z0 * PR + x;
+#pragma unroll
+    for (int r = 0; r < ROWS2; ++r) acc[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < KR; ++i) rq[i] = f2::ld(sr + i * PR);
+    if (jb + 1 < a.j_end) prefetch_plane_l2(plane_jb - plane, plane * 4, tid);
+    if (jb > 0) {
+        // resume: levels psi^jb, psi^(jb-1) and the imaging sums
+        const size_t cells = (size_t)NZ * NX;
+        const float *st = a.astate + (size_t)bs * 3 * cells;
+        float *cur = (jb & 1) ? U1 : U0, *old = (jb & 1) ? U0 : U1;
+        for (int i = tid; i < NZ * NX; i += nth) {
+            const int z = i / NX, xx = i - (i / NX) * NX;
+            cur[(z + 2) * P + xx + 2] = st[i];
+            old[(z + 2) * P + xx + 2] = st[cells + i];
+        }
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < ROWS2; ++r) {
+                const int z = z0 + r;
+                if (z < NZ) acc[r] = f2::ld(st + 2 * cells + z * NX + x);
+            }
+        }
+        if (tid == 0) acc_src = a.asrc[bs];
+    }
+    __syncthreads();
+
+    for (int j0 = jb; j0 < a.j_end; j0 += a.chunk) {
+        const int nch = min(a.chunk, a.j_end - j0);
+        const float *ab = a.adj + (size_t)bs * a.nr * a.nt;
+        for (int e = tid; e < nch * a.nr; e += nth) {
+            const int i = e / nch, jj = e - (e / nch) * nch;
+            ST[jj * a.nr + i] = IC[i] * ab[(size_t)i * a.nt + (a.nt - 1 - (j0 + jj))];
+        }
+        for (int e = tid; e < nch; e += nth) RS[e] = ricker_scaled(a.nt - 1 - (j0 + e), a);
+        __syncthreads();
+        for (int jj = 0; jj < nch; ++jj) {
+            const int j = j0 + jj;
+            const float *cur = (j & 1) ? U1 : U0;
+            float *nxt = (j & 1) ? U0 : U1;
+            if (inj0 >= 0) nxt[inj0_off] -= ST[jj * a.nr + inj0];   // (kappa/B) q
+            if (inj1 >= 0) nxt[inj1_off] -= ST[jj * a.nr + inj1];
+            if (j + 2 < a.j_end)
+                prefetch_plane_l2(plane_jb - (size_t)(j - jb + 2) * plane, plane * 4, tid);
+            const float *sr_next = (j + 1 < a.j_end) ? sr - plane : sr;
+            adj_rows_pair<P, PR, TOPBC>(cur + (z0 + 2) * P + x + 2, nxt + (z0 + 2) * P + x + 2,
+                                        K + z0 * P + x, sr, sr_next, opaque(zbf),
+                                        make_float2(opaque(ex.x), opaque(ex.y)), top_strip,
+                                        active, acc, rq, a);
+            sr = sr_next;
+            __syncthreads();
+            if (tid == nth - 1) {   // (its warp holds no receivers of the top rows)
+                const int sz = a.src_pz[s], sx = a.src_px[s];
+                acc_src = fmaf(nxt[(sz + 2) * P + sx + 2], RS[jj], acc_src);
+            }
+        }
+        __syncthreads();   // the last step's source-cell term reads RS before it is restaged
+    }
+
+    __syncthreads();
+    if (a.j_end < a.nt) {
+        // suspend: levels psi^je, psi^(je-1) and the imaging sums
+        const int je = a.j_end;
+        const size_t cells = (size_t)NZ * NX;
+        float *st = a.astate + (size_t)blockIdx.x * 3 * cells;
+        const float *cur = (je & 1) ? U1 : U0, *old = (je & 1) ? U0 : U1;
+        for (int i = tid; i < NZ * NX; i += nth) {
+            const int z = i / NX, xx = i - (i / NX) * NX;
+            st[i] = cur[(z + 2) * P + xx + 2];
+            st[cells + i] = old[(z + 2) * P + xx + 2];
+        }
+        if (active) {
+#pragma unroll
+            for (int r = 0; r < ROWS2; ++r) {
+                const int z = z0 + r;
+                if (z < NZ) f2::st(st + 2 * cells + z * NX + x, acc[r]);
+            }
+        }
+        if (tid == 0) a.asrc[bs] = acc_src;
+        return;
+    }
+
+    // dJ/dv_pad = 2 acc / v_pad, fold of the absorbing layer onto the edge
+    // cells (transpose of the edge replication), then per-shot gradient
+    float *G = U0;   // [NZ][NX]
+    float *T = U1;   // [NZ][nx]
+    if (active) {
+        const int ix0 = min(max(x - a.nb, 0), a.nx - 1), ix1 = min(max(x + 1 - a.nb, 0), a.nx - 1);
+#pragma unroll
+        for (int r = 0; r < ROWS2; ++r) {
+            const int z = z0 + r;
+            if (z < NZ) {
+                const float *vrow = vb + min(z, a.nz - 1) * a.nx;
+                G[z * NX + x] = 2.f * acc[r].x / vrow[ix0];
+                G[z * NX + x + 1] = 2.f * acc[r].y / vrow[ix1];
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int sz = a.src_pz[s], sx = a.src_px[s];
+        const float vsrc = vb[min(sz, a.nz - 1) * a.nx + min(max(sx - a.nb, 0), a.nx - 1)];
+        G[sz * NX + sx] += 2.f * acc_src / vsrc;
+    }
+    __syncthreads();
+    for (int i = tid; i < NZ * a.nx; i += nth) {
+        const int pz = i / a.nx, ix = i - (i / a.nx) * a.nx;
+        const int c0 = (ix == 0) ? 0 : ix + a.nb;
+        const int c1 = (ix == a.nx - 1) ? NX - 1 : ix + a.nb;
+        float sum = 0.f;
+        for (int px = c0; px <= c1; ++px) sum += G[pz * NX + px];
+        T[i] = sum;
+    }
+    __syncthreads();
+    float *gs = a.gshot + (size_t)bs * a.nz * a.nx;
+    for (int i = tid; i < a.nz * a.nx; i += nth) {
+        const int iz = i / a.nx, ix = i - (i / a.nx) * a.nx;
+        const int r1 = (iz == a.nz - 1) ? NZ - 1 : iz;
+        float sum = 0.f;
+        for (int pz = iz; pz <= r1; ++pz) sum += T[pz * a.nx + ix];
+        gs[i] = sum;
+    }
+}
+
 template <typename K>
 cudaError_t launch_k(K kern, const PropArgs &a, const ResidentShape &sh, int nblocks,
                      cudaStream_t st)
@@ -730,6 +994,12 @@ cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_
                       : launch_k(k_fwd_fast<PP, PPR, NN, 0, true>, a, sh, nb, st);             \
         return tb ? launch_k(k_fwd_fast<PP, PPR, NN, 1, false>, a, sh, nb, st)                 \
                   : launch_k(k_fwd_fast<PP, PPR, NN, 0, false>, a, sh, nb, st);                \
+    }
+    if (adj && pl.adj_pair) {
+        if (pl.fast_NZM == 110)
+            return tb ? launch_k(k_adj_pair<kPairPitch, 160, 110, 1>, a, sh, nb, st)
+                      : launch_k(k_adj_pair<kPairPitch, 160, 110, 0>, a, sh, nb, st);
+        return cudaErrorInvalidValue;
     }
     if (!adj && pl.fwd_pair) {
         if (pl.fast_NZM == 110)

@@ -50,10 +50,16 @@ def test_static_scratch_misfit_matches_workspace_misfit(api):
             w2 = torch.empty_like(w2_ref)
             adj = torch.empty_like(adj_ref)
             api.fwi_w2_misfit_static(plan.handle, ctx, d_syn, J, w2, adj)
-            # without per-trace output the scratch alone carries W2 to J
+            # without per-trace output the scratch alone carries W2 to J; the
+            # call reserves no device memory (the driver's free-memory count
+            # and torch's allocator are unchanged across it)
             J2 = torch.full_like(J_ref, float("nan"))
+            torch.cuda.synchronize()
+            free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
             api.fwi_w2_misfit_static(plan.handle, ctx, d_syn, J2, None, None)
             torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == alloc0
             assert _rel(J, J_ref) <= TOL_J and _rel(J2, J_ref) <= TOL_J
             assert _rel(w2, w2_ref) <= TOL_J
             assert _rel(adj, adj_ref) <= TOL_ADJ
@@ -71,3 +77,25 @@ def test_static_scratch_rejects_too_many_traces(api):
         api.fwi_w2_misfit_static(h, dummy, dummy, dummy, None, None)
     assert e.value.code == api.FWI_ERR_UNSUPPORTED
     assert "exceed" in str(e.value)
+
+
+def test_static_scratch_limit_applies_only_without_w2(api):
+    # more traces than the built-in array, but the caller takes the per-trace
+    # values: the array is not used and the call matches fwi_w2_misfit
+    dev = torch.device("cuda:0")
+    nz, nx, nb, nt, ns = 12, 70, 4, 60, 5
+    batch = api.FWI_STATIC_MAX_TRACES // (ns * nx) + 1
+    gp, _ = problems(nz, nx, nb, nt, ns, batch=batch, f_peak=25.0)
+    T = lambda a: torch.tensor(np.asarray(a), dtype=torch.float32, device=dev)  # noqa: E731
+    with api.Plan(gp, api.W2Params(n_xi=60)) as plan:
+        vt = models("layered", list(range(batch)), nz, nx)
+        v0 = models("curved_faulted", list(range(1, batch + 1)), nz, nx)
+        d_obs = plan.forward(T(vt), store=False)[0].clone()
+        ctx = plan.w2_prepare(d_obs)
+        d_syn = plan.forward(T(v0), store=False)[0]
+        J_ref, w2_ref, _ = plan.w2_misfit(ctx, d_syn)
+        J = torch.empty_like(J_ref)
+        w2 = torch.empty_like(w2_ref)
+        api.fwi_w2_misfit_static(plan.handle, ctx, d_syn, J, w2, None)
+        torch.cuda.synchronize()
+        assert _rel(J, J_ref) <= TOL_J and _rel(w2, w2_ref) <= TOL_J

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 10700  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 10800  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -324,15 +324,20 @@ FWI_API fwi_status fwi_image_metrics(int batch, int nz, int nx, double data_rang
  * array compiled into the library (FWI_STATIC_MAX_TRACES floats of device
  * global memory on every GPU that loads the library, held until the process
  * exits).  The call itself allocates nothing.
- *   Arguments and results are those of fwi_w2_misfit.
+ *   Arguments and results are those of fwi_w2_misfit.  The array holds the
+ *   per-trace W2 values only when w2 is NULL; a caller that passes w2 gets
+ *   them there and the array is not used (nor the size limit applied).
  *   The first call on a device looks up the array's device address with
  *   that device current; make that first call before any stream capture.
+ *   The address belongs to the device's context: after cudaDeviceReset the
+ *   next call looks it up again (make that call before any capture too).
  *   All calls on a device share the one array and it keeps the last call's
  *   contents; every value a call reads is written by that same call first,
  *   so nothing needs clearing.  Calls whose GPU work overlaps (different
  *   streams or threads on the same device) race on the array: serialise them.
  * Errors: FWI_ERR_INVALID_ARG for NULL arguments, FWI_ERR_UNSUPPORTED when
- * batch x ns x nr exceeds FWI_STATIC_MAX_TRACES, FWI_ERR_CUDA otherwise. */
+ * w2 is NULL and batch x ns x nr exceeds FWI_STATIC_MAX_TRACES, FWI_ERR_CUDA
+ * otherwise. */
 FWI_API fwi_status fwi_w2_misfit_static(const fwi_plan *plan, const void *obs_ctx,
                                         const float *d_syn, float *J, float *w2,
                                         float *adj_src, void *stream);
@@ -579,6 +584,21 @@ FWI_API fwi_status fwi_restrict2_transpose(int batch, int nz, int nx, const floa
 FWI_API fwi_status fwi_decimate2(int batch, int ns, int nr, int nt, const float *d, float *dc,
                                  void *stream);
 
+/* The coarse problem itself (host only; no CUDA call): *coarse = *fine with
+ * nz, nx, nb halved and rounded up, dz, dx, dt doubled, nt / 2 steps and
+ * checkpoint_every halved (rounded up; 0 stays 0); shot i at cell
+ * (src_iz[i] / 2, src_ix[i] / 2); the receivers of even index k at
+ * (rec_iz[k] / 2, rec_ix[k] / 2), ceil(nr / 2) of them.  Every other field is
+ * copied.  The index arrays are the caller's HOST arrays (src_iz, src_ix of
+ * fine->ns entries, rec_iz, rec_ix of ceil(fine->nr / 2)); the coarse
+ * problem's pointers point into them, so they must outlive its use.
+ * The coarse problem is passed to fwi_plan_create, which validates it (CFL
+ * with the doubled dt included).
+ * Errors: FWI_ERR_INVALID_ARG for NULL arguments, counts out of range or
+ * nt < 4. */
+FWI_API fwi_status fwi_coarse_problem(const fwi_problem *fine, fwi_problem *coarse, int *src_iz,
+                                      int *src_ix, int *rec_iz, int *rec_ix);
+
 /* ---------------------------------------------------------------- tensor-core convolution
  * 3x3 convolution, stride 1, zero padding 1, the dense contraction of a
  * convolutional score model or surrogate used for the guidance of
@@ -672,6 +692,83 @@ FWI_API fwi_status fwi_ddpm_guidance(int batch, int ncell, const fwi_ddpm_step *
                                      const fwi_diffusion_space *space, const float *v0hat,
                                      const float *g_phys, const float *vjp, const float *tau2,
                                      float *g, float *h, void *stream);
+
+/* ---------------------------------------------------------------- learned forward surrogate
+ * Data-side steps of a convolutional encoder-decoder that maps a velocity model
+ * to the seismograms of the FD solver: the surrogate route to cheaper guidance
+ * that Sec. 7 proposes, used in the early reverse steps of Algorithm 2 (Sec.
+ * 5.2), with the FD solver as its judge and fallback.  The six convolutions run
+ * on fwi_conv3x3_bf16 (with fwi_silu_bf16, fwi_silu_grad_bf16, fwi_add_bf16,
+ * fwi_conv3x3_wgrad_tc, fwi_channel_sum and fwi_adam_step for training).
+ * Layout: model b is column (b mod m) of image (b / m), an image being nx pixels
+ * high (the model's columns x) and m pixels wide; the convolution weights keep
+ * their horizontal taps at zero (fwi_sur_weights_prep), so each model only
+ * couples its own columns x - 1, x, x + 1 and the m models of an image never
+ * mix.  nimg = ceil(nmod / m).  All arrays are device arrays; bf16 tensors are
+ * NHWC and 16-byte aligned where the convolution reads them.
+ * Errors: FWI_ERR_INVALID_ARG before any launch, FWI_ERR_CUDA. */
+
+/* X [nimg][nx][m][c0] bf16 = in_scale v[b][c][x] + in_shift for channel c < nz,
+ * G[x][c] (fp32 [nx][c0], the geometry channels) above; columns past nmod are 0.
+ * c0 is a multiple of 64 and >= nz.  v [nmod][nz][nx] fp32. */
+FWI_API fwi_status fwi_sur_pack(int nmod, int m, int nz, int nx, int c0, float in_scale,
+                                float in_shift, const float *v, const float *G, void *X,
+                                void *stream);
+
+/* dv[b][z][x] = in_scale dX[b / m][x][b mod m][z]: the gradient at the models
+ * from the fp32 gradient dX [nimg][nx][m][c0] at the packed input. */
+FWI_API fwi_status fwi_sur_unpack_grad(int nmod, int m, int nz, int nx, int c0, float in_scale,
+                                       const float *dX, float *dv, void *stream);
+
+/* d[b][s][r][t] = amp sign(y) (e^|y| - 1) with y = Y[b / m][rec_ix[r]][b mod m][s nt + t]:
+ * the traces from the fp32 output Y [nimg][nx][m][cout] (ns nt <= cout, amp > 0),
+ * rec_ix [nr] device ints (the receivers' columns, distinct). */
+FWI_API fwi_status fwi_sur_traces(int nmod, int m, int ns, int nr, int nt, int nx, int cout,
+                                  float amp, const int *rec_ix, const float *Y, float *d,
+                                  void *stream);
+
+/* dY [nimg][nx][m][cout] bf16 = scale adj[b][s][r][t] amp e^|y| at column
+ * x = rec_ix[r], channel s nt + t, and 0 at every other entry: the transpose of
+ * the derivative of fwi_sur_traces at Y applied to adj [nmod][ns][nr][nt].
+ * col_rec [nx] device ints: the receiver at column x, or -1. */
+FWI_API fwi_status fwi_sur_output_grad(int nmod, int m, int ns, int nr, int nt, int nx,
+                                       int cout, float amp, float scale, const int *col_rec,
+                                       const float *Y, const float *adj, void *dY,
+                                       void *stream);
+
+/* Yt [nimg][nx][m][cout] fp32 = sign(d) log(1 + |d| / amp) at the entries
+ * fwi_sur_traces reads (the regression target of Y), 0 elsewhere. */
+FWI_API fwi_status fwi_sur_target(int nmod, int m, int ns, int nr, int nt, int nx, int cout,
+                                  float amp, const int *col_rec, const float *d, float *Yt,
+                                  void *stream);
+
+/* loss[0] = mean over the n entries of (Y - Yt)^2 and dY = bf16(2 (Y - Yt) / n);
+ * work: fp32 scratch for up to 608 per-CTA partials, added in a fixed order. */
+FWI_API fwi_status fwi_sur_loss(long long n, const float *Y, const float *Yt, float *loss,
+                                void *dY, float *work, long long work_floats, void *stream);
+
+/* Along the image only (bf16 NHWC, channels a multiple of 8):
+ * fwi_pool_h_bf16: y [n][(h+1)/2][w][C] = s * (x[2I] + x[2I+1]) over the rows
+ *   inside the image, s = 1 / rows (mode 0, mean) or 1 (mode 1, the adjoint of
+ *   mode-0 upsampling);
+ * fwi_up_h_bf16: y [n][ho][w][C] = s * x[i / 2], s = 1 (mode 0) or 1 / (the rows
+ *   of block i / 2 inside ho) (mode 1, the adjoint of mean pooling). */
+FWI_API fwi_status fwi_pool_h_bf16(int n, int h, int w, int channels, int mode, const void *x,
+                                   void *y, void *stream);
+FWI_API fwi_status fwi_up_h_bf16(int n, int ho, int w, int channels, int mode, const void *x,
+                                 void *y, void *stream);
+
+/* From three-tap fp32 weights W3 [cout][3][cin] (tap k couples pixel x + k - 1):
+ * W [cout][3][3][cin] bf16 with W[co][ky][1][ci] = W3[co][ky][ci] and the
+ * horizontal taps zero, and its transpose WT [cin][3][3][cout] (WT[ci][ky][kx][co]
+ * = W[co][2-ky][2-kx][ci], the weights of the backward convolution). */
+FWI_API fwi_status fwi_sur_weights_prep(int cout, int cin, const float *W3, void *W, void *WT,
+                                        void *stream);
+
+/* dW3[co][ky][ci] = dW[co][ky][1][ci]: the gradient of the three-tap weights
+ * from a 3 x 3 weight gradient dW [cout][3][3][cin] (fp32). */
+FWI_API fwi_status fwi_sur_wgrad_centre(int cout, int cin, const float *dW, float *dW3,
+                                        void *stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 FWI_API const char *fwi_last_error(void);

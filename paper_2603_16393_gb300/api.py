@@ -137,6 +137,8 @@ _lib.fwi_restrict2_transpose.restype = _S
 _lib.fwi_restrict2_transpose.argtypes = [ctypes.c_int] * 3 + [_vp] * 3
 _lib.fwi_decimate2.restype = _S
 _lib.fwi_decimate2.argtypes = [ctypes.c_int] * 4 + [_vp] * 3
+_lib.fwi_coarse_problem.restype = _S
+_lib.fwi_coarse_problem.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Problem)] + [_ip] * 4
 _lib.fwi_pack_channel0.restype = _S
 _lib.fwi_pack_channel0.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_float, _vp, _vp, _vp]
 _lib.fwi_unpack_channel0.restype = _S
@@ -177,6 +179,27 @@ _lib.fwi_up2_bf16.restype = _S
 _lib.fwi_up2_bf16.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp]
 _lib.fwi_add_bf16.restype = _S
 _lib.fwi_add_bf16.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp]
+_i, _f = ctypes.c_int, ctypes.c_float
+_lib.fwi_sur_pack.restype = _S
+_lib.fwi_sur_pack.argtypes = [_i] * 5 + [_f, _f] + [_vp] * 4
+_lib.fwi_sur_unpack_grad.restype = _S
+_lib.fwi_sur_unpack_grad.argtypes = [_i] * 5 + [_f] + [_vp] * 3
+_lib.fwi_sur_traces.restype = _S
+_lib.fwi_sur_traces.argtypes = [_i] * 7 + [_f] + [_vp] * 4
+_lib.fwi_sur_output_grad.restype = _S
+_lib.fwi_sur_output_grad.argtypes = [_i] * 7 + [_f, _f] + [_vp] * 5
+_lib.fwi_sur_target.restype = _S
+_lib.fwi_sur_target.argtypes = [_i] * 7 + [_f] + [_vp] * 4
+_lib.fwi_sur_loss.restype = _S
+_lib.fwi_sur_loss.argtypes = [ctypes.c_longlong] + [_vp] * 5 + [ctypes.c_longlong, _vp]
+_lib.fwi_pool_h_bf16.restype = _S
+_lib.fwi_pool_h_bf16.argtypes = [_i] * 5 + [_vp] * 3
+_lib.fwi_up_h_bf16.restype = _S
+_lib.fwi_up_h_bf16.argtypes = [_i] * 5 + [_vp] * 3
+_lib.fwi_sur_weights_prep.restype = _S
+_lib.fwi_sur_weights_prep.argtypes = [_i, _i] + [_vp] * 4
+_lib.fwi_sur_wgrad_centre.restype = _S
+_lib.fwi_sur_wgrad_centre.argtypes = [_i, _i] + [_vp] * 3
 _lib.fwi_channel_sum.restype = _S
 _lib.fwi_channel_sum.argtypes = [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, ctypes.c_longlong,
                                  _vp]
@@ -555,17 +578,22 @@ def fwi_decimate2(d, dc=None, stream=None):
 
 
 def coarse_problem(prob: Problem) -> Problem:
-    """The low-fidelity twin of a problem (fwi_restrict2 and friends): grid,
-    spacing and time step doubled, nb rounded up, nt / 2 steps, sources at the
-    coarse cells index / 2, the even receivers likewise."""
-    rec = [(int(z) // 2, int(x) // 2)
-           for k, (z, x) in enumerate(zip(prob.rec_iz, prob.rec_ix)) if k % 2 == 0]
+    """The low-fidelity twin of a problem (fwi_restrict2 and friends), as the
+    library's fwi_coarse_problem derives it: grid, spacing and time step
+    doubled, nb rounded up, nt / 2 steps, sources at the coarse cells index / 2,
+    the even receivers likewise."""
+    cp, _cw, _arrays = _c_problem(prob, W2Params())
+    out = _Problem()
+    idx = [(ctypes.c_int * max(1, n))() for n in
+           (prob.ns, prob.ns, (prob.nr + 1) // 2, (prob.nr + 1) // 2)]
+    _check(_lib.fwi_coarse_problem(ctypes.byref(cp), ctypes.byref(out),
+                                   *[ctypes.cast(a, _ip) for a in idx]))
+    nrc = out.nr
     return dataclasses.replace(
-        prob, nz=(prob.nz + 1) // 2, nx=(prob.nx + 1) // 2, nb=(prob.nb + 1) // 2,
-        nt=prob.nt // 2, dz=2 * prob.dz, dx=2 * prob.dx, dt=2 * prob.dt,
-        src_iz=[int(z) // 2 for z in prob.src_iz], src_ix=[int(x) // 2 for x in prob.src_ix],
-        rec_iz=[r[0] for r in rec], rec_ix=[r[1] for r in rec],
-        checkpoint_every=(prob.checkpoint_every + 1) // 2 if prob.checkpoint_every else 0)
+        prob, nz=out.nz, nx=out.nx, nb=out.nb, nt=out.nt, dz=out.dz, dx=out.dx, dt=out.dt,
+        src_iz=list(idx[0][:prob.ns]), src_ix=list(idx[1][:prob.ns]),
+        rec_iz=list(idx[2][:nrc]), rec_ix=list(idx[3][:nrc]),
+        checkpoint_every=out.checkpoint_every)
 
 
 def fwi_pack_channel0(x, X, scale=1.0, stream=None):
@@ -708,6 +736,113 @@ def fwi_add_bf16(x, y, z, stream=None):
     if not (x.shape == y.shape == z.shape):
         raise ValueError("x, y and z must have one shape")
     _check(_lib.fwi_add_bf16(x.numel(), _ptr(x), _ptr(y), _ptr(z), _stream(stream)))
+
+
+def fwi_sur_pack(v, G, X, m, in_scale=1.0, in_shift=0.0, stream=None):
+    """X [nimg][nx][m][c0] bf16 from models v [nmod][nz][nx] fp32 and the
+    geometry channels G [nx][c0] fp32 (see include/fwi.h)."""
+    nmod, nz, nx = v.shape
+    nimg, c0 = -(-nmod // m), G.shape[1]
+    _f32(v, (nmod, nz, nx), "v")
+    _f32(G, (nx, c0), "G")
+    _bf16_nhwc(X, "X")
+    if tuple(X.shape) != (nimg, nx, m, c0):
+        raise ValueError(f"X must be {(nimg, nx, m, c0)}")
+    _check(_lib.fwi_sur_pack(nmod, m, nz, nx, c0, float(in_scale), float(in_shift), _ptr(v),
+                             _ptr(G), _ptr(X), _stream(stream)))
+
+
+def fwi_sur_unpack_grad(dX, dv, m, in_scale=1.0, stream=None):
+    nmod, nz, nx = dv.shape
+    nimg, c0 = dX.shape[0], dX.shape[3]
+    _f32(dX, (nimg, nx, m, c0), "dX")
+    _f32(dv, (nmod, nz, nx), "dv")
+    _check(_lib.fwi_sur_unpack_grad(nmod, m, nz, nx, c0, float(in_scale), _ptr(dX), _ptr(dv),
+                                    _stream(stream)))
+
+
+def _int_dev(t, n, name):
+    if t.dtype != torch.int32 or t.numel() != n or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous int32 CUDA tensor of {n} entries")
+
+
+def fwi_sur_traces(Y, d, m, amp, rec_ix, stream=None):
+    """d [nmod][ns][nr][nt] = amp sign(y) (e^|y| - 1) from Y [nimg][nx][m][cout]."""
+    nmod, ns, nr, nt = d.shape
+    nimg, nx, _, cout = Y.shape
+    _f32(Y, (nimg, nx, m, cout), "Y")
+    _f32(d, (nmod, ns, nr, nt), "d")
+    _int_dev(rec_ix, nr, "rec_ix")
+    _check(_lib.fwi_sur_traces(nmod, m, ns, nr, nt, nx, cout, float(amp), _ptr(rec_ix), _ptr(Y),
+                               _ptr(d), _stream(stream)))
+
+
+def fwi_sur_output_grad(Y, adj, dY, m, amp, col_rec, scale=1.0, stream=None):
+    """dY bf16 [nimg][nx][m][cout]: the trace map's transposed derivative at Y
+    applied to adj [nmod][ns][nr][nt]; 0 where no trace reads Y."""
+    nmod, ns, nr, nt = adj.shape
+    nimg, nx, _, cout = Y.shape
+    _f32(Y, (nimg, nx, m, cout), "Y")
+    _f32(adj, (nmod, ns, nr, nt), "adj")
+    _bf16_nhwc(dY, "dY")
+    _int_dev(col_rec, nx, "col_rec")
+    _check(_lib.fwi_sur_output_grad(nmod, m, ns, nr, nt, nx, cout, float(amp), float(scale),
+                                    _ptr(col_rec), _ptr(Y), _ptr(adj), _ptr(dY),
+                                    _stream(stream)))
+
+
+def fwi_sur_target(d, Yt, m, amp, col_rec, stream=None):
+    nmod, ns, nr, nt = d.shape
+    nimg, nx, _, cout = Yt.shape
+    _f32(d, (nmod, ns, nr, nt), "d")
+    _f32(Yt, (nimg, nx, m, cout), "Yt")
+    _int_dev(col_rec, nx, "col_rec")
+    _check(_lib.fwi_sur_target(nmod, m, ns, nr, nt, nx, cout, float(amp), _ptr(col_rec), _ptr(d),
+                               _ptr(Yt), _stream(stream)))
+
+
+def fwi_sur_loss(Y, Yt, loss, dY, work, stream=None):
+    if Y.shape != Yt.shape or tuple(dY.shape) != tuple(Y.shape) or dY.dtype != torch.bfloat16:
+        raise ValueError("Y, Yt (fp32) and dY (bf16) must have one shape")
+    wp, wf = _work(work)
+    _check(_lib.fwi_sur_loss(Y.numel(), _ptr(Y), _ptr(Yt), _ptr(loss), _ptr(dY), wp, wf,
+                             _stream(stream)))
+
+
+def fwi_pool_h_bf16(x, y, mode=0, stream=None):
+    """y [n][(h+1)/2][w][C]: mean (mode 0) or sum (mode 1) of row pairs of x."""
+    _bf16_nhwc(x, "x")
+    _bf16_nhwc(y, "y")
+    n, h, w, c = x.shape
+    if tuple(y.shape) != (n, (h + 1) // 2, w, c):
+        raise ValueError("y must be [n][(h+1)/2][w][C]")
+    _check(_lib.fwi_pool_h_bf16(n, h, w, c, mode, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def fwi_up_h_bf16(x, y, mode=0, stream=None):
+    """y [n][ho][w][C] from x [n][(ho+1)/2][w][C]: nearest rows (mode 0), divided
+    by the block's rows (mode 1)."""
+    _bf16_nhwc(x, "x")
+    _bf16_nhwc(y, "y")
+    n, ho, w, c = y.shape
+    if tuple(x.shape) != (n, (ho + 1) // 2, w, c):
+        raise ValueError("x must be [n][(ho+1)/2][w][C]")
+    _check(_lib.fwi_up_h_bf16(n, ho, w, c, mode, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def fwi_sur_weights_prep(W3, Wb, WTb, stream=None):
+    cout, _, cin = W3.shape
+    _f32(W3, (cout, 3, cin), "W3")
+    if tuple(Wb.shape) != (cout, 3, 3, cin) or tuple(WTb.shape) != (cin, 3, 3, cout):
+        raise ValueError("Wb [cout][3][3][cin] and WTb [cin][3][3][cout] bf16 needed")
+    _check(_lib.fwi_sur_weights_prep(cout, cin, _ptr(W3), _ptr(Wb), _ptr(WTb), _stream(stream)))
+
+
+def fwi_sur_wgrad_centre(dW, dW3, stream=None):
+    cout, _, cin = dW3.shape
+    _f32(dW, (cout, 3, 3, cin), "dW")
+    _f32(dW3, (cout, 3, cin), "dW3")
+    _check(_lib.fwi_sur_wgrad_centre(cout, cin, _ptr(dW), _ptr(dW3), _stream(stream)))
 
 
 def fwi_channel_sum(dP, db, work=None, stream=None):

@@ -120,4 +120,46 @@ fwi_status fwi_decimate2(int batch, int ns, int nr, int nt, const float *d, floa
     return launch_check("fwi_decimate2");
 }
 
+fwi_status fwi_coarse_problem(const fwi_problem *fine, fwi_problem *coarse, int *src_iz,
+                              int *src_ix, int *rec_iz, int *rec_ix)
+{
+    if (!fine || !coarse || !src_iz || !src_ix || !rec_iz || !rec_ix)
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "fine, coarse and the four index arrays must not be NULL");
+    if (!fine->src_iz || !fine->src_ix || !fine->rec_iz || !fine->rec_ix)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "the fine problem's index arrays are NULL");
+    if (fine->nz < 1 || fine->nx < 1 || fine->nb < 0 || fine->ns < 1 || fine->nr < 1 ||
+        fine->ns > FWI_MAX_SHOTS || fine->nr > FWI_MAX_RECEIVERS)
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "fine grid, layer, shot or receiver counts out of range");
+    if (fine->nt < 4)
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "nt = %d: the coarse problem needs nt / 2 >= 2 steps", fine->nt);
+    fwi_problem c = *fine;
+    c.nz = (fine->nz + 1) / 2;
+    c.nx = (fine->nx + 1) / 2;
+    c.nb = (fine->nb + 1) / 2;
+    c.nt = fine->nt / 2;
+    c.dz = 2.0 * fine->dz;
+    c.dx = 2.0 * fine->dx;
+    c.dt = 2.0 * fine->dt;
+    c.checkpoint_every = fine->checkpoint_every ? (fine->checkpoint_every + 1) / 2 : 0;
+    for (int i = 0; i < fine->ns; ++i) {
+        src_iz[i] = fine->src_iz[i] / 2;
+        src_ix[i] = fine->src_ix[i] / 2;
+    }
+    int nrc = 0;
+    for (int i = 0; i < fine->nr; i += 2, ++nrc) {   // the even receivers
+        rec_iz[nrc] = fine->rec_iz[i] / 2;
+        rec_ix[nrc] = fine->rec_ix[i] / 2;
+    }
+    c.nr = nrc;
+    c.src_iz = src_iz;
+    c.src_ix = src_ix;
+    c.rec_iz = rec_iz;
+    c.rec_ix = rec_ix;
+    *coarse = c;
+    return FWI_OK;
+}
+
 }  // extern "C"

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(api):
     lib = ctypes.CDLL(LIB)
     for n in declared_functions():
         assert hasattr(lib, n), n
-    assert api.fwi_version() == 10700
+    assert api.fwi_version() == 10800
 
 
 def _prob(api, **kw):
@@ -282,3 +282,34 @@ def test_group_create_rejects_bad_arguments_without_a_gpu():
     assert lib.fwi_group_create(plans, 1, None) == 1
     nul = (ctypes.c_void_p * 1)(None)
     assert lib.fwi_group_gradient(None, *([nul] * 8), None) == 1
+
+
+def test_coarse_problem_matches_the_oracle_twin(api):
+    # the library's derivation of the low-fidelity problem against the
+    # oracle's, on the benchmark geometry and on odd sizes and receiver counts
+    from oracle import multifidelity as MF
+    from oracle import oracle as O
+    for kw in (dict(), dict(nz=33, nx=41, nb=7, nt=301, src_ix=(0, 20, 40), src_iz=(3, 0, 5),
+                            rec_iz=tuple(range(9)), rec_ix=tuple(range(0, 41, 5)),
+                            checkpoint_every=7)):
+        fine = _prob(api, **kw)
+        c = api.coarse_problem(fine)
+        o = MF.coarse_problem(O.Problem(nz=fine.nz, nx=fine.nx, nb=fine.nb, nt=fine.nt,
+                                        dz=fine.dz, dx=fine.dx, dt=fine.dt,
+                                        src_iz=fine.src_iz, src_ix=fine.src_ix,
+                                        rec_iz=fine.rec_iz, rec_ix=fine.rec_ix))
+        assert (c.nz, c.nx, c.nb, c.nt) == (o.nz, o.nx, o.nb, o.nt)
+        assert (c.dz, c.dx, c.dt) == (o.dz, o.dx, o.dt)
+        assert list(c.src_iz) == list(o.src_iz) and list(c.src_ix) == list(o.src_ix)
+        assert list(c.rec_iz) == list(o.rec_iz) and list(c.rec_ix) == list(o.rec_ix)
+        assert c.checkpoint_every == ((fine.checkpoint_every + 1) // 2
+                                      if fine.checkpoint_every else 0)
+        assert (c.batch, c.f_peak, c.v_ref, c.v_max) == (fine.batch, fine.f_peak, fine.v_ref,
+                                                         fine.v_max)
+        api.fwi_plan_create(c, api.W2Params())   # a valid plan (freed with its handle)
+
+
+def test_coarse_problem_rejects_short_runs(api):
+    with pytest.raises(api.FwiError) as e:
+        api.coarse_problem(_prob(api, nt=3))
+    assert e.value.code == api.FWI_ERR_INVALID_ARG

@@ -16,10 +16,13 @@ The network, per model b (the architecture is a reading; the paper gives none):
           (x - src_ix[s]) / nx and its magnitude, then a constant 1)
   layers  six convolutions with three taps along the image (pixel x couples
           to x - 1, x, x + 1; weights W3 [cout][3][cin], bias b):
-            enc0 (level 0) -> mean pooling by 2 -> enc1 (level 1) -> pooling ->
-            enc2 (level 2) -> nearest upsampling -> dec1 (level 1) + enc1's
+            enc0 (level 0) -> mean pooling by 4 -> enc1 (level 1) -> pooling ->
+            enc2 (level 2) -> nearest upsampling by 4 -> dec1 (level 1) + enc1's
             output -> upsampling -> dec0 (level 0) + enc0's output -> out
-          SiLU after every layer but ``out``; level k has ceil(nx / 2^k) pixels
+          SiLU after every layer but ``out``; pooling by 4 is two poolings of
+          row pairs (ceil(h / 2) rows each), upsampling by 4 two nearest
+          doublings back through the same sizes, so level 2 of a 70-column
+          model has 5 pixels and the bottleneck sees the whole model
   output  y = Y[x][s nt + t] of the linear ``out`` layer, and the trace of
           receiver r (at column rec_ix[r]) is d[s][r][t] = amp sign(y) (e^|y| - 1),
           the inverse of the compressive map y = sign(d) log(1 + |d| / amp)
@@ -141,7 +144,11 @@ class Surrogate:
         self.amp, self.c0 = float(amp), c0
         self.in_scale, self.in_shift = float(in_scale), float(in_shift)
         self.G = geometry_channels(nz, nx, self.src_ix, c0)
-        self.sizes = [nx, (nx + 1) // 2, ((nx + 1) // 2 + 1) // 2]
+        h = [nx]
+        for _ in range(4):
+            h.append((h[-1] + 1) // 2)
+        self.half = h              # rows after 0..4 poolings of row pairs
+        self.sizes = [h[0], h[2], h[4]]
 
     def pack(self, v):
         """X0 [B][nx][1][c0] of models v [B][nz][nx] (before rounding)."""
@@ -163,13 +170,14 @@ class Surrogate:
         """Y [B][nx][1][cout] of the last layer (float, before the trace map)."""
         r = self.r
         self.P, self.In = {}, {}
+        h = self.half
         x0 = r(self.pack(v))
         a0 = self.A0 = self._layer("enc0", x0)
-        a1 = self.A1 = self._layer("enc1", r(pool_h(a0, 0)))
-        a2 = self._layer("enc2", r(pool_h(a1, 0)))
-        b1 = self._layer("dec1", up_h(a2, self.sizes[1], 0))
+        a1 = self.A1 = self._layer("enc1", r(pool_h(r(pool_h(a0, 0)), 0)))
+        a2 = self._layer("enc2", r(pool_h(r(pool_h(a1, 0)), 0)))
+        b1 = self._layer("dec1", up_h(up_h(a2, h[3], 0), h[2], 0))
         s1 = r(b1 + a1)
-        b0 = self._layer("dec0", up_h(s1, self.sizes[0], 0))
+        b0 = self._layer("dec0", up_h(up_h(s1, h[1], 0), h[0], 0))
         s0 = r(b0 + a0)
         self.Y = self._layer("out", s0, act=False)
         return self.Y
@@ -211,15 +219,16 @@ class Surrogate:
         stored precision); returns the gradient at v [B][nz][nx]."""
         r = self.r
         self.dPs = {}
+        h = self.half
         ds0 = r(self._back("out", dY, act=False))
         du0 = r(self._back("dec0", ds0))
-        ds1 = r(pool_h(du0, 1))
+        ds1 = r(pool_h(r(pool_h(du0, 1)), 1))
         du1 = r(self._back("dec1", ds1))
-        da2 = r(pool_h(du1, 1))
+        da2 = r(pool_h(r(pool_h(du1, 1)), 1))
         dd2 = r(self._back("enc2", da2))
-        da1 = r(ds1 + r(up_h(dd2, self.sizes[1], 1)))
+        da1 = r(ds1 + r(up_h(r(up_h(dd2, h[3], 1)), h[2], 1)))
         dd1 = r(self._back("enc1", da1))
-        da0 = r(ds0 + r(up_h(dd1, self.sizes[0], 1)))
+        da0 = r(ds0 + r(up_h(r(up_h(dd1, h[1], 1)), h[0], 1)))
         dx0 = self._back("enc0", da0)
         return self.in_scale * dx0[:, :, 0, :self.nz].transpose(0, 2, 1)
 

@@ -132,3 +132,43 @@ def gaussian_noise_like(d_clean: np.ndarray, snr_db: float, seed: int) -> np.nda
 def random_field(seed: int, shape, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     """Uniform random float64 array (used for dot-product tests and guided-step inputs)."""
     return np.random.default_rng(seed).uniform(lo, hi, size=shape)
+
+
+def blurred_model(v: np.ndarray, width: float) -> np.ndarray:
+    """A model smoothed by a separable Gaussian of standard deviation `width`
+    cells (edges replicated): the blurry estimates a reverse diffusion makes
+    in its early, high-noise steps.  width <= 0 returns a copy."""
+    v = np.asarray(v, dtype=np.float64)
+    if width <= 0:
+        return v.copy()
+    r = int(np.ceil(3 * width))
+    k = np.exp(-0.5 * (np.arange(-r, r + 1) / width) ** 2)
+    k /= k.sum()
+    p = np.pad(v, r, mode="edge")
+    p = np.apply_along_axis(lambda a: np.convolve(a, k, mode="valid"), 0, p)
+    return np.apply_along_axis(lambda a: np.convolve(a, k, mode="valid"), 1, p)
+
+
+def surrogate_training_models(seed0: int, n: int, nz: int = 70, nx: int = 70) -> np.ndarray:
+    """n seeded models [n][nz][nx] (float64) for fitting a forward surrogate:
+    by index k = seed0 + i, k mod 4 = 0 layered, 1 curved/faulted, 2 a
+    curved/faulted model blurred by 1-8 cells, 3 the linear gradient model
+    plus a smooth perturbation of up to 600 m/s and white noise of up to
+    150 m/s; every model clipped to [1500, 4500]."""
+    out = np.empty((n, nz, nx))
+    for i in range(n):
+        k = seed0 + i
+        rng = np.random.default_rng(1_000_003 * k + 17)
+        kind = k % 4
+        if kind == 0:
+            v = layered_model(k, nz, nx, nlayers=int(rng.integers(3, 6)))
+        elif kind == 1:
+            v = curved_faulted_model(k, nz, nx)
+        elif kind == 2:
+            v = blurred_model(curved_faulted_model(k, nz, nx), rng.uniform(1.0, 8.0))
+        else:
+            v = linear_initial_model(nz, nx) + smooth_perturbation(k, nz, nx,
+                                                                   rng.uniform(0.0, 600.0))
+            v += rng.uniform(0.0, 150.0) * rng.standard_normal((nz, nx))
+        out[i] = np.clip(v, V_MIN, V_MAX)
+    return out

@@ -17,9 +17,12 @@ FP32 accumulation and master parameters):
           magnitude, a constant 1), fwi_sur_pack
   layers  six convolutions with three taps along the image (the horizontal
           taps of the tensor-core 3 x 3 convolution fixed at zero, so the m
-          models of an image never mix): enc0 -> mean pooling of row pairs ->
-          enc1 -> pooling -> enc2 -> nearest upsampling -> dec1 + enc1 ->
-          upsampling -> dec0 + enc0 -> out; SiLU after all but ``out``
+          models of an image never mix): enc0 -> mean pooling by 4 (two
+          poolings of row pairs) -> enc1 -> pooling by 4 -> enc2 (5 pixels for
+          70 columns: the bottleneck sees the whole model, as the reflections
+          from midpoints up to half the spread away need) -> nearest
+          upsampling by 4 -> dec1 + enc1 -> upsampling by 4 -> dec0 + enc0 ->
+          out; SiLU after all but ``out``
   output  Y[x][s nt + t], and the trace of receiver r (column rec_ix[r]) is
           amp sign(y) (e^|y| - 1), fwi_sur_traces; training fits Y to
           sign(d) log(1 + |d| / amp) of the FD data (fwi_sur_target,
@@ -86,6 +89,10 @@ class ForwardSurrogate:
                  weights=None, seed: int = 0, device=None):
         if len(set(int(r) for r in rec_ix)) != len(rec_ix):
             raise ValueError("the surrogate needs receivers at distinct columns")
+        if not all(0 <= int(c) < nx for c in list(rec_ix) + list(src_ix)):
+            raise ValueError("source and receiver columns must lie in [0, nx)")
+        if nmod < 1 or m < 1 or nt < 1 or nz < 1:
+            raise ValueError("nmod, m, nt, nz must be >= 1")
         if width % 64 or c0 % 64 or c0 < nz + 2 * len(src_ix) + 1:
             raise ValueError("width and c0 must be multiples of 64, c0 >= nz + 2 ns + 1")
         self.dev = torch.device(device) if device is not None else torch.device("cuda")
@@ -97,7 +104,11 @@ class ForwardSurrogate:
         self.cout = -(-self.ns * nt // 256) * 256
         self.layers = layer_table(c0, width, self.cout)
         self.idx = {n: l for l, (n, _, _, _) in enumerate(self.layers)}
-        self.sizes = [nx, (nx + 1) // 2, ((nx + 1) // 2 + 1) // 2]
+        hs = [nx]
+        for _ in range(4):
+            hs.append((hs[-1] + 1) // 2)
+        self.half = hs                     # rows after 0..4 poolings of row pairs
+        self.sizes = [hs[0], hs[2], hs[4]]
         self.shape = (nmod, nz, nx)
         i32 = dict(dtype=torch.int32, device=self.dev)
         self.rec_ix = torch.tensor([int(r) for r in rec_ix], **i32)
@@ -122,7 +133,12 @@ class ForwardSurrogate:
         def act(k, c, dtype=torch.bfloat16):
             return torch.empty((self.nimg, self.sizes[k], m, c), dtype=dtype, device=self.dev)
 
+        def half(j, c):     # a map after j poolings of row pairs
+            return torch.empty((self.nimg, hs[j], m, c), dtype=torch.bfloat16, device=self.dev)
+
         w = width
+        self.H = {j: half(j, w) for j in (1, 3)}       # the odd (half-way) sizes, forward
+        self.dH = {j: half(j, w) for j in (1, 3)}      # and backward
         self.X0 = act(0, c0)
         self.P = {n: act(k, co) for n, k, _, co in self.layers if n != "out"}
         self.A = {n: act(k, co) for n, k, _, co in self.layers if n != "out"}
@@ -174,14 +190,18 @@ class ForwardSurrogate:
         """Y of the models v [nmod][nz][nx] (m/s); keeps the activations."""
         api.fwi_sur_pack(v, self.G, self.X0, self.m, self.in_scale, self.in_shift, stream)
         a0 = self._conv("enc0", self.X0, stream)
-        api.fwi_pool_h_bf16(a0, self.D[1], 0, stream)
+        api.fwi_pool_h_bf16(a0, self.H[1], 0, stream)
+        api.fwi_pool_h_bf16(self.H[1], self.D[1], 0, stream)
         a1 = self._conv("enc1", self.D[1], stream)
-        api.fwi_pool_h_bf16(a1, self.D[2], 0, stream)
+        api.fwi_pool_h_bf16(a1, self.H[3], 0, stream)
+        api.fwi_pool_h_bf16(self.H[3], self.D[2], 0, stream)
         a2 = self._conv("enc2", self.D[2], stream)
-        api.fwi_up_h_bf16(a2, self.U[1], 0, stream)
+        api.fwi_up_h_bf16(a2, self.H[3], 0, stream)
+        api.fwi_up_h_bf16(self.H[3], self.U[1], 0, stream)
         b1 = self._conv("dec1", self.U[1], stream)
         api.fwi_add_bf16(b1, a1, self.S[1], stream)
-        api.fwi_up_h_bf16(self.S[1], self.U[0], 0, stream)
+        api.fwi_up_h_bf16(self.S[1], self.H[1], 0, stream)
+        api.fwi_up_h_bf16(self.H[1], self.U[0], 0, stream)
         b0 = self._conv("dec0", self.U[0], stream)
         api.fwi_add_bf16(b0, a0, self.S[0], stream)
         l = self.idx["out"]
@@ -223,15 +243,19 @@ class ForwardSurrogate:
         ds0 = self._layer_back("out", self.dY, self.S[0], grads, work, stage, dW9, stream,
                                act=False)
         du0 = self._layer_back("dec0", ds0, self.U[0], grads, work, stage, dW9, stream)
-        api.fwi_pool_h_bf16(du0, self.dPool[1], 1, stream)        # adjoint of upsampling
+        api.fwi_pool_h_bf16(du0, self.dH[1], 1, stream)           # adjoint of upsampling
+        api.fwi_pool_h_bf16(self.dH[1], self.dPool[1], 1, stream)
         ds1 = self.dPool[1]
         du1 = self._layer_back("dec1", ds1, self.U[1], grads, work, stage, dW9, stream)
-        api.fwi_pool_h_bf16(du1, self.dPool[2], 1, stream)
+        api.fwi_pool_h_bf16(du1, self.dH[3], 1, stream)
+        api.fwi_pool_h_bf16(self.dH[3], self.dPool[2], 1, stream)
         dd2 = self._layer_back("enc2", self.dPool[2], self.D[2], grads, work, stage, dW9, stream)
-        api.fwi_up_h_bf16(dd2, self.dUp[1], 1, stream)            # adjoint of mean pooling
+        api.fwi_up_h_bf16(dd2, self.dH[3], 1, stream)             # adjoint of mean pooling
+        api.fwi_up_h_bf16(self.dH[3], self.dUp[1], 1, stream)
         api.fwi_add_bf16(ds1, self.dUp[1], self.dAcc[1], stream)
         dd1 = self._layer_back("enc1", self.dAcc[1], self.D[1], grads, work, stage, dW9, stream)
-        api.fwi_up_h_bf16(dd1, self.dUp[0], 1, stream)
+        api.fwi_up_h_bf16(dd1, self.dH[1], 1, stream)
+        api.fwi_up_h_bf16(self.dH[1], self.dUp[0], 1, stream)
         api.fwi_add_bf16(ds0, self.dUp[0], self.dAcc[0], stream)
         self._layer_back("enc0", self.dAcc[0], self.X0, grads, work, stage, dW9, stream,
                          dst=self.dX if need_input else False)
@@ -309,7 +333,7 @@ class SurrogateGuidance:
             raise ValueError("the plan and the surrogate must hold the same models")
         self.net, self.plan, self.ctx = net, plan, ctx
 
-    def gradient(self, v_phys: torch.Tensor, stream=None):
+    def gradient(self, v_phys: torch.Tensor, stream=None, step: int = -1):
         d = self.net.forward(v_phys, stream=stream)
         J, _, adj = self.plan.w2_misfit(self.ctx, d, stream=stream)
         return J, self.net.vjp(adj, stream=stream)
@@ -356,7 +380,7 @@ class GatedSurrogate:
         if self._since is None or self._since >= self.check_every:
             J, g_fd, _ = self.plan.gradient(v_phys, self.ctx, stream=stream)
             g_fd = g_fd.clone()
-            _, g_sur = self.sur.gradient(v_phys, stream)
+            _, g_sur = self.sur.gradient(v_phys, stream=stream)
             err = float(rel_error(g_sur, g_fd).max())
             ok = err <= self.threshold
             self.records.append(GateRecord(step, err, ok))
@@ -366,4 +390,94 @@ class GatedSurrogate:
             return J, g_fd
         self._since += 1
         self.n_surrogate += 1
-        return self.sur.gradient(v_phys, stream)
+        return self.sur.gradient(v_phys, stream=stream)
+
+
+# ----------------------------------------------------------------- training data
+def fd_pairs(plan: api.Plan, models, stream=None):
+    """(v [N][nz][nx], d [N][ns][nr][nt]) on the plan's device: the FD
+    seismograms (fwi_forward, no record) of N models (host array, m/s),
+    plan.batch at a time; N must be a multiple of the plan's batch."""
+    B = plan.model_shape[0]
+    if torch.is_tensor(models):
+        v = models.to(device=plan.device, dtype=torch.float32).contiguous()
+    else:
+        v = torch.tensor(np.asarray(models, np.float32), device=plan.device)
+    N = v.shape[0]
+    if N % B:
+        raise ValueError(f"{N} models are not a multiple of the plan's batch {B}")
+    d = torch.empty((N,) + tuple(plan.data_shape[1:]), dtype=torch.float32, device=plan.device)
+    for k in range(0, N, B):
+        dk, _ = plan.forward(v[k:k + B], store=False, stream=stream)
+        d[k:k + B].copy_(dk)
+    return v, d
+
+
+def trace_amplitude(d: torch.Tensor, k: float = 100.0) -> float:
+    """amp = max |d| / k: the trace map's scale, so that y = sign(d) log(1 + |d|/amp)
+    compresses the largest amplitude to log(1 + k) (k = 100 mirrors the W2
+    weighting's k of Eq. omega_def)."""
+    return float(d.abs().max()) / k
+
+
+def train(trainer: SurrogateTrainer, v: torch.Tensor, d: torch.Tensor, steps: int,
+          stream=None, log_every: int = 0):
+    """``steps`` Adam steps over the dataset in order, one minibatch of the
+    network's nmod consecutive pairs each (the dataset wraps around); returns
+    [(step, loss)] read back every ``log_every`` steps (0: only the last)."""
+    B, N = trainer.net.nmod, v.shape[0]
+    if N < B:
+        raise ValueError("fewer pairs than one minibatch")
+    nb = N // B
+    out = []
+    loss = None
+    for k in range(steps):
+        o = (k % nb) * B
+        loss = trainer.step(v[o:o + B], d[o:o + B], stream)
+        if log_every and (k + 1) % log_every == 0:
+            out.append((k + 1, float(loss.item())))
+    if loss is not None and (not out or out[-1][0] != steps):
+        out.append((steps, float(loss.item())))
+    return out
+
+
+def copy_weights(dst: ForwardSurrogate, src: ForwardSurrogate):
+    """Give dst (another batch size) the parameters of src."""
+    if dst.theta.numel() != src.theta.numel():
+        raise ValueError("the networks differ in architecture")
+    dst.theta.copy_(src.theta)
+    dst.amp = src.amp
+    dst.refresh()
+
+
+def early_clean_estimates(models: torch.Tensor, prior, betas: Sequence[float], i_lo: int,
+                          i_hi: int, chunk: int, seed: int = 0,
+                          space: api.DiffusionSpace = api.DiffusionSpace(),
+                          sigma_mode: int = api.SIGMA_POSTERIOR) -> torch.Tensor:
+    """The physical models a reverse diffusion hands its guidance in steps
+    i_lo..i_hi: each chunk of ``chunk`` models [N][nz][nx] (m/s, device) is
+    noised to a step i drawn uniformly from that range (fwi_dsm_noisy: x_i =
+    sqrt(abar_i) x_0 + sqrt(1 - abar_i) z, x_0 = (v - shift) / unit) and
+    mapped to its clamped clean estimate under the Gaussian prior
+    (fwi_ddpm_proposal's v_phys) -- the inputs the surrogate is queried on in
+    the early, high-noise steps, which it is trained on."""
+    N, nz, nx = models.shape
+    if N % chunk:
+        raise ValueError("the number of models must be a multiple of chunk")
+    dev = models.device
+    rng = np.random.default_rng(seed)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    x0 = ((models - space.shift) / space.unit).contiguous()
+    out = torch.empty_like(models)
+    z = torch.empty((chunk, nz, nx), dtype=torch.float32, device=dev)
+    xt = torch.empty_like(z)
+    v0, vp = torch.empty_like(z), torch.empty_like(z)
+    zero = torch.zeros_like(z)
+    for k in range(0, N, chunk):
+        i = int(rng.integers(i_lo, i_hi + 1))
+        st = api.fwi_ddpm_coefficients(list(betas), i, sigma_mode)
+        z.normal_(generator=gen)
+        api.fwi_dsm_noisy(x0[k:k + chunk], z, st.abar, xt)
+        api.fwi_ddpm_proposal(chunk, nz * nx, st, space, xt, None, prior.mu, prior.tau2, zero,
+                              v0, vp, out[k:k + chunk])
+    return out

@@ -661,11 +661,20 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
 // to the compiler's contraction).  A thread may own the receivers of both
 // of its columns (one per column and strip).
 //
+// Registers bound this kernel (unconstrained it wants 140 a thread, and 768
+// threads get 80), so two per-cell arrays live in tensor memory instead: the
+// imaging sums (read, updated and written back per row) and kappa A (read per
+// row), each thread in its own TMEM lane -- warp w owns lanes 32 (w mod 4) ..
+// + 31, the warps of one lane quarter take 44 columns each (22 of sums, 22 of
+// kappa A).  The kappa A table in shared memory is read only at set-up.
+//
 // Record reads: a whole record plane is prefetched into L2 two steps before
-// it is used (one bulk prefetch per step), and each thread keeps a ring of
-// KR rows in flight (the record of row r + KR is loaded when row r is
-// updated), which holds 2 KR registers instead of a whole strip's 22.
-constexpr int KR = 4;
+// it is used (one bulk prefetch per step, in 4 KB pieces), and each thread
+// keeps a ring of KR rows in flight (the record of row r + KR is loaded when
+// row r is updated).  KR = 6 measured fastest once the sums and kappa A left
+// the registers (13.6 ms at 152 models; 4 rows: 14.5 ms).
+constexpr int KR = 6;
+constexpr int kAdjTmemCols = 512;   // 6 warps per lane quarter x 44 columns, rounded up
 
 // L2 prefetch of a record plane (16-byte aligned, size a multiple of 16) in
 // 4 KB pieces, one piece per thread of the first warps
@@ -680,14 +689,30 @@ __device__ __forceinline__ void prefetch_plane_l2(const float *p, size_t bytes, 
     }
 }
 
+// two fp32 columns of this thread's TMEM lane (warp-collective; the values
+// are valid after tmem_wait_ld)
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t &a, uint32_t &b)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                 : "=r"(a), "=r"(b)
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr),
+                 "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 template <int P, int PR, int TOPBC>
 __device__ __forceinline__ void adj_rows_pair(const float *__restrict__ cp,
                                               float *__restrict__ np,
-                                              const float *__restrict__ kp,
                                               const float *__restrict__ sr,
                                               const float *__restrict__ sr_next, float zbf,
                                               float2 ex, bool top_strip, bool active,
-                                              float2 (&acc)[ROWS2], float2 (&rq)[KR],
+                                              uint32_t tacc, uint32_t tka, float2 (&rq)[KR],
                                               const PropArgs &a)
 {
     using namespace f2;
@@ -713,10 +738,16 @@ __device__ __forceinline__ void adj_rows_pair(const float *__restrict__ cp,
         const float2 h = add(splat(1.f), add(ex, splat(ez)));          // 1 + e
         const float2 A2 = make_float2(__fdividef(2.f, h.x), __fdividef(2.f, h.y));   // 2A
         const float2 nAB = fma(A2, splat(-1.f), splat(1.f));            // -A B = 1 - 2A
+        uint32_t s0, s1, k0, k1;
+        tmem_ld2(tacc + 2 * r, s0, s1);
+        tmem_ld2(tka + 2 * r, k0, k1);
         const float2 fo = ld(np + r * P);
-        const float2 fn = fma(ld(kp + r * P), lap, fma(A2, w0, mul(nAB, fo)));
+        tmem_wait_ld();
+        const float2 kA = make_float2(__uint_as_float(k0), __uint_as_float(k1));
+        const float2 fn = fma(kA, lap, fma(A2, w0, mul(nAB, fo)));
         if (active) st(np + r * P, fn);
-        acc[r] = fma(fn, rq[0], acc[r]);
+        tmem_st2(tacc + 2 * r,
+                 fma(fn, rq[0], make_float2(__uint_as_float(s0), __uint_as_float(s1))));
 #pragma unroll
         for (int i = 0; i + 1 < KR; ++i) rq[i] = rq[i + 1];
         rq[KR - 1] = (r + KR < ROWS2) ? ld(sr + (r + KR) * PR) : ld(sr_next + (r + KR - ROWS2) * PR);
@@ -734,6 +765,8 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
     constexpr int FSZ = (NZM + 4) * P;
     static_assert(P % 2 == 0 && PR % 4 == 0 && FSZ % 2 == 0,
                   "float2 rows need even pitches; record planes are prefetched in 16-byte units");
+    static_assert(2 * ROWS2 * 2 * (kMaxThreadsAdj / 128) <= kAdjTmemCols,
+                  "the lane quarters' columns must fit the allocation");
     float *U0 = sm, *U1 = sm + FSZ, *K = sm + 2 * FSZ, *IC = K + NZM * P, *ST = IC + a.nr;
     float *RS = ST + a.chunk * a.nr;
     const int NX = a.NX, NZ = a.NZ;
@@ -766,7 +799,8 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
     }
 
     // inactive threads (past the last strip) run the same instructions on the
-    // addresses of strip 0, columns 0 and 1, with every write gated
+    // addresses of strip 0, columns 0 and 1, with every write gated (the
+    // tensor-memory accesses are warp-collective)
     const int NXP = NX / 2;
     const int strip = tid / NXP;
     const bool active = strip < a.nstrip;
@@ -788,22 +822,50 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
     const int inj0_off = inj0 >= 0 ? (a.rec_pz[inj0] + 2) * P + x + 2 : 0;
     const int inj1_off = inj1 >= 0 ? (a.rec_pz[inj1] + 2) * P + x + 3 : 0;
     __shared__ float acc_src;
+    __shared__ uint32_t tmem_slot;
     if (tid == 0) acc_src = 0.f;
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
+                     "r"(kAdjTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int warp = tid >> 5;
+    const uint32_t tacc = tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) +
+                          (uint32_t)(4 * ROWS2 * (warp >> 2));
+    const uint32_t tka = tacc + 2 * ROWS2;
 
     const size_t plane = (size_t)a.nzs * PR;
     const int jb = a.j_begin;
-    float2 acc[ROWS2], rq[KR];
     // record plane of adjoint step j: forward step nt-1-j
     const float *plane_jb =
         a.snap + ((size_t)bs * a.rec_planes + (a.nt - 1 - jb - a.rec_base)) * plane;
     const float *sr = plane_jb + z0 * PR + x;
+    // imaging sums (zero, or resumed) and kappa A into this thread's TMEM lane
+    // (sizes are recomputed where used: a value live across the time loop
+    // costs the loop a register)
 #pragma unroll
-    for (int r = 0; r < ROWS2; ++r) acc[r] = make_float2(0.f, 0.f);
+    for (int r = 0; r < ROWS2; ++r) {
+        float2 acc0 = make_float2(0.f, 0.f);
+        const int z = z0 + r;
+        if (jb > 0 && active && z < NZ) {
+            const size_t cells = (size_t)NZ * NX;
+            acc0 = f2::ld(a.astate + (size_t)bs * 3 * cells + 2 * cells + z * NX + x);
+        }
+        tmem_st2(tacc + 2 * r, acc0);
+        tmem_st2(tka + 2 * r, f2::ld(K + z * P + x));
+    }
+    tmem_wait_st();
+    float2 rq[KR];
 #pragma unroll
     for (int i = 0; i < KR; ++i) rq[i] = f2::ld(sr + i * PR);
     if (jb + 1 < a.j_end) prefetch_plane_l2(plane_jb - plane, plane * 4, tid);
     if (jb > 0) {
-        // resume: levels psi^jb, psi^(jb-1) and the imaging sums
+        // resume: levels psi^jb, psi^(jb-1) and the source-cell sum
         const size_t cells = (size_t)NZ * NX;
         const float *st = a.astate + (size_t)bs * 3 * cells;
         float *cur = (jb & 1) ? U1 : U0, *old = (jb & 1) ? U0 : U1;
@@ -811,13 +873,6 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
             const int z = i / NX, xx = i - (i / NX) * NX;
             cur[(z + 2) * P + xx + 2] = st[i];
             old[(z + 2) * P + xx + 2] = st[cells + i];
-        }
-        if (active) {
-#pragma unroll
-            for (int r = 0; r < ROWS2; ++r) {
-                const int z = z0 + r;
-                if (z < NZ) acc[r] = f2::ld(st + 2 * cells + z * NX + x);
-            }
         }
         if (tid == 0) acc_src = a.asrc[bs];
     }
@@ -842,9 +897,10 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
                 prefetch_plane_l2(plane_jb - (size_t)(j - jb + 2) * plane, plane * 4, tid);
             const float *sr_next = (j + 1 < a.j_end) ? sr - plane : sr;
             adj_rows_pair<P, PR, TOPBC>(cur + (z0 + 2) * P + x + 2, nxt + (z0 + 2) * P + x + 2,
-                                        K + z0 * P + x, sr, sr_next, opaque(zbf),
+                                        sr, sr_next, opaque(zbf),
                                         make_float2(opaque(ex.x), opaque(ex.y)), top_strip,
-                                        active, acc, rq, a);
+                                        active, tacc, tka, rq, a);
+            tmem_wait_st();
             sr = sr_next;
             __syncthreads();
             if (tid == nth - 1) {   // (its warp holds no receivers of the top rows)
@@ -855,7 +911,23 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
         __syncthreads();   // the last step's source-cell term reads RS before it is restaged
     }
 
+    // the imaging sums back into registers, tensor memory released
+    float2 acc[ROWS2];
+#pragma unroll
+    for (int r = 0; r < ROWS2; ++r) {
+        uint32_t s0, s1;
+        tmem_ld2(tacc + 2 * r, s0, s1);
+        tmem_wait_ld();
+        acc[r] = make_float2(__uint_as_float(s0), __uint_as_float(s1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (tid < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot),
+                     "r"(kAdjTmemCols)
+                     : "memory");
+    }
     if (a.j_end < a.nt) {
         // suspend: levels psi^je, psi^(je-1) and the imaging sums
         const int je = a.j_end;

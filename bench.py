@@ -250,8 +250,12 @@ def run_ours(args, rank, world, local_rank):
     rho = torch.empty(B, dtype=torch.float32, device=dev)
     ev = {k: [] for k in ("fwd0", "fwd1", "adj0", "adj1")}
 
-    def step(v_in, dobs_in, timed):
-        api.fwi_w2_prepare(plan.handle, dobs_in, ctx)
+    def step(v_in, dobs_in, timed, prepare=True):
+        # a4 (observation preparation) runs once per observation: the device-
+        # timed steps reuse the context; the end-to-end steps take a new
+        # observation from the host each step and prepare it
+        if prepare:
+            api.fwi_w2_prepare(plan.handle, dobs_in, ctx)
         if timed:
             e0 = torch.cuda.Event(enable_timing=True); e0.record(stream)
         api.fwi_forward(plan.handle, v_in, d_syn, plan.snapshots, plan.workspace)
@@ -267,25 +271,25 @@ def run_ours(args, rank, world, local_rank):
         # preconditioned update (no network: v' = v0hat = v, g = h = dJ/dv)
         api.fwi_guided_step(B, NZ_PHYS, NX_PHYS, gparams, v_in, v_in, grad, grad, v_out, rho)
 
-    # library kernels per step: prepare (4: observation max, per-trace
-    # preparation, two sums), forward, misfit (2), adjoint + shot sum, guided
-    # (1); the cluster adjoint adds a fold; the tiled propagators launch once
-    # per time step, plus a set-up (and a resume per recomputed segment) and a
-    # final gather or fold
+    # library kernels per timed step: forward, misfit (2), adjoint + shot
+    # sum, guided (1); the cluster adjoint adds a fold; the tiled propagators
+    # launch once per time step, plus a set-up (and a resume per recomputed
+    # segment) and a final gather or fold.  (The observation preparation, 4
+    # kernels, is timed apart.)
     if path == "resident":
-        kernels_per_step = 4 + 1 + 2 + 2 + 1
+        kernels_per_step = 1 + 2 + 2 + 1
     elif path == "cpml":
         # set-up 2 + 2 a step (forward); set-up 2 + init + 3 a step (2 at the
         # last) + fold (adjoint), + shot sum
-        kernels_per_step = 4 + (2 + 2 * NT) + 2 + (2 + 1 + 3 * NT - 2 + 1 + 1) + 1
+        kernels_per_step = (2 + 2 * NT) + 2 + (2 + 1 + 3 * NT - 2 + 1 + 1) + 1
     elif path == "cluster":
-        kernels_per_step = 4 + 1 + 2 + 3 + 1
+        kernels_per_step = 1 + 2 + 3 + 1
     else:
         K = wl["ckpt"]
         S = -(-NT // K) if K else 0
         fwd_k = 1 + NT + 1
         adj_k = (2 * S + (S - 1) + 2 * NT + 2) if K else (1 + NT + 2)
-        kernels_per_step = 4 + fwd_k + 2 + adj_k + 1
+        kernels_per_step = fwd_k + 2 + adj_k + 1
 
     def barrier():
         if world > 1:
@@ -295,6 +299,15 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.warmup):
         step(v_d, d_obs, False)
     barrier()
+    # a4 alone: the observation preparation of this batch, amortised per observation
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        api.fwi_w2_prepare(plan.handle, d_obs, ctx)
+    p1.record(stream)
+    barrier()
+    prep_ms = p0.elapsed_time(p1) / args.steps
     clocks = ClockSampler(local_rank) if rank == 0 else None
     if clocks:
         clocks.start()
@@ -302,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
-        step(v_d, d_obs, True)
+        step(v_d, d_obs, True, prepare=False)
     t1.record(stream)
     barrier()
     clk = clocks.stop() if clocks else None
@@ -412,19 +425,29 @@ def run_ours(args, rank, world, local_rank):
     # SM, by the shared-memory pipe: one wavefront (up to 128 B) per clock per
     # SM; the wavefronts per launch come from the committed capture
     roof_smem = None
-    wf = record_traffic(B * NS, path, args.workload, NT, what="smem_wavefronts")
-    if wf and path in ("resident", "cluster"):
+    if path in ("resident", "cluster"):
+        # the shared-memory roof of the on-chip propagators against the
+        # algorithmic 24 bytes per cell-update (own column window, x
+        # neighbours, old level and table, store; the z neighbours come from
+        # registers): 128 B per clock per SM at the sampled clock; the
+        # measured wavefronts of the committed capture give the pipe's
+        # occupancy beside it
         mhz = (clk or {}).get("sm_mhz") or 2070.0
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_wf = n_sm * mhz * 1e6
-        per = {k: wf[k] / (t * 1e-3) for k, t in (("forward", fwd_ms), ("adjoint", adj_ms))}
-        roof_smem = {"bound": "smem", "kernel": dom[2], "achieved": per[dom[3]],
-                     "peak": peak_wf, "unit": "shared-memory wavefronts/s",
-                     "frac": per[dom[3]] / peak_wf,
-                     "frac_forward": per["forward"] / peak_wf,
-                     "frac_adjoint": per["adjoint"] / peak_wf,
-                     "peak_source": f"1 wavefront per clock per SM x {n_sm} SMs x {mhz:.0f} MHz "
+        peak_b = 128.0 * n_sm * mhz * 1e6
+        per = {k: cu * 24.0 / (t * 1e-3) for k, t in (("forward", fwd_ms), ("adjoint", adj_ms))}
+        roof_smem = {"bound": "smem", "kernel": dom[2], "achieved": per[dom[3]] / 1e9,
+                     "peak": peak_b / 1e9, "unit": "GB/s", "bytes_per_cell_update": 24,
+                     "frac": per[dom[3]] / peak_b,
+                     "frac_forward": per["forward"] / peak_b,
+                     "frac_adjoint": per["adjoint"] / peak_b,
+                     "peak_source": f"128 B per clock per SM x {n_sm} SMs x {mhz:.0f} MHz "
                                     "(sampled clock)"}
+        wf = record_traffic(B * NS, path, args.workload, NT, what="smem_wavefronts")
+        if wf:
+            roof_smem["pipe_occupancy"] = {
+                k: wf[k] / (t * 1e-3) / (n_sm * mhz * 1e6)
+                for k, t in (("forward", fwd_ms), ("adjoint", adj_ms))}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.workload != "512x1024":
@@ -463,6 +486,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": peak_kind, "ms_per_launch": dom[0]},
         "roofline_smem": roof_smem,
         "kernel_ms": {"forward": fwd_ms, "adjoint": adj_ms},
+        "obs_prepare_ms": prep_ms,
         "e2e": {"value": world * B / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": kernels_per_step * args.steps,
@@ -773,6 +797,211 @@ def run_sampler(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_posterior(args, rank, world, local_rank):
+    """--posterior: posterior sampling by Algorithm 2 (Sec. 5.2) on noisy
+    observations (10 dB), as the scope table's full guided reverse diffusion
+    states it: P posterior samples per observation, N reverse steps, W2
+    guidance batched over observations x samples x shots.  Three arms on the
+    same draws:
+      graph_fd   all-FD guidance, every reverse step replayed from one CUDA
+                 graph (sampler.GraphChain)
+      graph_sur  the learned forward surrogate in the first 40% of the steps,
+                 judged by FD every 10 steps and replaced by FD for good once
+                 its gradient error exceeds 5%; trained first on FD pairs of
+                 the clean estimates of those steps (training timed apart)
+      plain      one plan per posterior sample (batch 1, five shots), eager
+                 launches: timed over a few reverse steps of every sample; one
+                 sample runs the whole chain and is compared with the batched
+                 one bit for bit
+    Reported: posterior samples/s of each arm, velocity RMSE and relative L2
+    error of the samples and of each observation's posterior mean against the
+    true models, the surrogate's W2-gradient error against FD per noise level,
+    and the gate's record."""
+    import dataclasses as dc
+    import torch
+    from paper_2603_16393_gb300 import api
+    from paper_2603_16393_gb300 import inputs as I
+    from paper_2603_16393_gb300 import sampler as S
+    from paper_2603_16393_gb300 import surrogate as SG
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    nz = nx = 70
+    NT, NS = 1000, 5
+    n_obs, P = args.observations, args.samples
+    B = n_obs * P
+    N = args.reverse_steps
+    geo = I.surface_geometry(nx, NS)
+    prob = api.Problem(nz=nz, nx=nx, nb=NB, nt=NT, dz=DX, dx=DX, dt=DT, src_iz=geo.src_iz,
+                       src_ix=geo.src_ix, rec_iz=geo.rec_iz, rec_ix=geo.rec_ix, v_max=4500.0,
+                       batch=B)
+    plan = api.Plan(prob, api.W2Params(), device=dev)
+    seed0 = 7000 + 100 * rank
+    vt = I.model_batch("curved_faulted", range(seed0, seed0 + n_obs), nz, nx)
+    vt_rep = np.repeat(vt, P, axis=0)
+    d_clean = plan.forward(torch.tensor(vt_rep, dtype=torch.float32, device=dev),
+                           store=False)[0].cpu().numpy()
+    noise = np.concatenate([np.repeat(I.gaussian_noise_like(d_clean[o * P:o * P + 1], 10.0,
+                                                            seed0 + o), P, axis=0)
+                            for o in range(n_obs)])
+    d_obs = torch.tensor(d_clean + noise, dtype=torch.float32, device=dev)
+    ctx = plan.w2_prepare(d_obs)
+    prior = S.GaussianPrior.from_models(I.model_batch("curved_faulted", range(90_000, 90_064),
+                                                      nz, nx), device=dev)
+    # the 1000-step linear schedule's total noise spread over N steps
+    betas = S.linear_betas(N, 1e-4 * 1000 / N, 0.02 * 1000 / N)
+    guide = api.GuideParams(rho0=1.15, gamma=0.55)
+    gen = torch.Generator(device=dev).manual_seed(4321 + rank)
+    zs = torch.randn((N + 1, B, nz, nx), device=dev, generator=gen)
+    v_start = torch.randn((B, nz, nx), device=dev, generator=gen)
+    stream = torch.cuda.current_stream(dev)
+    vt_d = torch.tensor(vt_rep, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return out, a.elapsed_time(b)
+
+    def quality(v_state):
+        v = (3000.0 + 1500.0 * v_state).clamp(1500.0, 4500.0)
+        rmse = float(((v - vt_d) ** 2).mean().sqrt())
+        m = torch.empty((B, 3), dtype=torch.float32, device=dev)
+        api.fwi_image_metrics(B, nz, nx, 3000.0, vt_d, v.contiguous(), m)
+        pm = v.reshape(n_obs, P, nz, nx).mean(dim=1)
+        vt_o = vt_d.reshape(n_obs, P, nz, nx)[:, 0]
+        rmse_mean = float(((pm - vt_o) ** 2).mean().sqrt())
+        return {"rmse_m_s": rmse, "rel_l2": float(m[:, 0].mean()), "ssim": float(m[:, 2].mean()),
+                "posterior_mean_rmse_m_s": rmse_mean}
+
+    # ---- the learned surrogate: FD pairs of early clean estimates, training
+    i_switch = N - int(round(0.4 * N))
+    t_data = time.time()
+    raw = torch.tensor(I.surrogate_training_models(0, args.surrogate_models).astype(np.float32),
+                       device=dev)
+    n_early = (args.surrogate_models * 3 // 4) // B * B
+    est = SG.early_clean_estimates(raw[:n_early], prior, betas, i_switch + 1, N, B, seed=1)
+    fd_plan = plan
+    v_tr, d_tr = SG.fd_pairs(fd_plan, torch.cat([est, raw[n_early:]])[:raw.shape[0] // B * B])
+    torch.cuda.synchronize(dev)
+    t_data = time.time() - t_data
+    net = SG.ForwardSurrogate(B, nz, nx, NT, geo.src_ix, geo.rec_ix, SG.trace_amplitude(d_tr),
+                              seed=0, device=dev)
+    tr = SG.SurrogateTrainer(net)
+    sched = [(args.surrogate_steps // 2, 1e-3), (args.surrogate_steps // 4, 3e-4),
+             (args.surrogate_steps - args.surrogate_steps // 2 - args.surrogate_steps // 4, 1e-4)]
+    log = []
+
+    def train_all():
+        for n, lr in sched:
+            tr.lr = lr
+            log.extend(SG.train(tr, v_tr, d_tr, n, log_every=max(1, n)))
+    _, t_train = timed(train_all)
+    guid = SG.SurrogateGuidance(net, plan, ctx)
+    # W2-gradient error against FD per noise level, on the clean estimates of
+    # the true models noised to that step
+    levels = []
+    for i in sorted({N, int(0.9 * N), int(0.8 * N), int(0.7 * N), i_switch + 1,
+                     int(0.5 * N), int(0.3 * N), int(0.1 * N)}, reverse=True):
+        v = SG.early_clean_estimates(vt_d, prior, betas, i, i, B, seed=i)
+        _, g_fd, _ = plan.gradient(v, ctx)
+        g_fd = g_fd.clone()
+        d_fd = plan.forward(v, store=False)[0].clone()
+        d_s = net.forward(v)
+        _, g_s = guid.gradient(v)
+        e = SG.rel_error(g_s, g_fd)
+        levels.append({"step": i, "abar": float(np.prod(1.0 - np.asarray(betas[:i]))),
+                       "data_rel_l2": float((d_s - d_fd).norm() / d_fd.norm()),
+                       "grad_rel_l2_median": float(e.median()), "grad_rel_l2_max": float(e.max()),
+                       "grad_cosine": float((g_s * g_fd).sum() / (g_s.norm() * g_fd.norm()))})
+
+    # ---- arm graph_fd
+    chain_fd = S.GraphChain(plan, betas, ctx, prior, guide, zs)
+    chain_fd.capture("fd")
+    chain_fd.run(v_start, N, N - 2)          # warm-up replays
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    v_fd, ms_fd = timed(lambda: chain_fd.run(v_start).clone())
+    q_fd = quality(v_fd)
+    # ---- arm graph_sur
+    chain_sur = S.GraphChain(plan, betas, ctx, prior, guide, zs, surrogate=guid,
+                             surrogate_fraction=0.4, threshold=0.05, check_every=10)
+    for k in ("fd", "sur", "check"):
+        chain_sur.capture(k)
+    v_sur, ms_sur = timed(lambda: chain_sur.run(v_start).clone())
+    clk = clocks.stop() if clocks else None
+    q_sur = quality(v_sur)
+    plan.check()
+    # ---- arm plain: one plan per posterior sample, eager launches
+    p1 = api.Plan(dc.replace(prob, batch=1), api.W2Params(), device=dev)
+    ctxs = [p1.w2_prepare(d_obs[b:b + 1].contiguous()) for b in range(B)]
+    smps = [S.Sampler(p1, betas, ctx=c, prior=prior, guide=guide) for c in ctxs]
+    K = args.plain_steps
+    vs = [v_start[b:b + 1].clone() for b in range(B)]
+
+    def plain_steps():
+        for k in range(K):
+            i = N - k
+            for b in range(B):
+                vs[b], _ = smps[b].step(vs[b], i, zs[i, b:b + 1].contiguous())
+    _, ms_plain_k = timed(plain_steps)
+    ms_plain = ms_plain_k / K * N
+    # one sample through the whole chain on the plain path, against the batched arm
+    v1 = v_start[0:1].clone()
+
+    def plain_chain():
+        nonlocal v1
+        for i in range(N, 0, -1):
+            v1, _ = smps[0].step(v1, i, zs[i, 0:1].contiguous())
+    timed(plain_chain)
+    p1.check()
+    bitwise = bool(torch.equal(v1[0], v_fd[0]))
+    if rank != 0:
+        return
+    arms = {
+        "graph_fd": {"samples_per_s": B / (ms_fd * 1e-3), "chain_s": ms_fd * 1e-3, **q_fd},
+        "graph_sur": {"samples_per_s": B / (ms_sur * 1e-3), "chain_s": ms_sur * 1e-3, **q_sur,
+                      "steps": dict(chain_sur.counts),
+                      "gate": [{"step": i, "grad_rel_l2_max": e, "accepted": ok}
+                               for i, e, ok in chain_sur.records]},
+        "plain": {"samples_per_s": B / (ms_plain * 1e-3), "chain_s": ms_plain * 1e-3,
+                  "timed_reverse_steps": K, "chain_extrapolated_from_timed_steps": True,
+                  "one_sample_whole_chain_bitwise_equal_to_graph_fd": bitwise},
+    }
+    best = max(("graph_fd", "graph_sur"), key=lambda k: arms[k]["samples_per_s"])
+    line = {
+        "metric": f"posterior samples/s (Algorithm 2, 70x70, 5 shots x 1000 FD steps, {N} reverse "
+                  "steps, 10 dB observations)",
+        "value": arms[best]["samples_per_s"], "unit": "posterior samples/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": arms[best]["chain_s"] * 1e3 / N,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded curved/faulted true models, Gaussian noise at 10 dB; Gaussian "
+                "prior fitted to 64 seeded models)",
+        "config": {"workload": f"{n_obs} observations x {P} posterior samples = {B} models per "
+                               f"GPU, {N} reverse steps, W2 guidance (5 shots, 70 receivers, "
+                               "1000 steps, 40-cell layer)",
+                   "headline_arm": best,
+                   "l2": "inputs larger than L2 (wavefield record 44 GB per reverse step)"},
+        "arms": arms,
+        "speedup_vs_plain": {k: arms[k]["samples_per_s"] / arms["plain"]["samples_per_s"]
+                             for k in ("graph_fd", "graph_sur")},
+        "surrogate": {"training_pairs": int(v_tr.shape[0]),
+                      "pairs": "FD seismograms of clean estimates of reverse steps "
+                               f"{i_switch + 1}..{N} (3/4) and of seeded models (1/4)",
+                      "fd_pairs_s": t_data, "train_s": t_train * 1e-3,
+                      "train_steps": args.surrogate_steps,
+                      "train_models_per_s": args.surrogate_steps * B / (t_train * 1e-3),
+                      "loss_log": log, "error_by_noise_level": levels,
+                      "threshold": 0.05, "check_every": 10},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_conv(args, rank, world, local_rank):
     """--conv: the tensor-core 3x3 convolution of a convolutional score model
     or surrogate layer on the 70x70 workload's batch: 152 images of 70 x 70,
@@ -1033,6 +1262,20 @@ def main():
     ap.add_argument("--dsm-train", action="store_true",
                     help="denoising-score-matching training steps of the convolutional score "
                          "model (152 x 70x70, 3 layers of --conv-channels)")
+    ap.add_argument("--posterior", action="store_true",
+                    help="posterior sampling by Algorithm 2 on 10 dB observations: batched "
+                         "graph-replayed chains with all-FD and with gated surrogate guidance "
+                         "against one eager plan per sample")
+    ap.add_argument("--observations", type=int, default=4, help="--posterior: observations")
+    ap.add_argument("--samples", type=int, default=32,
+                    help="--posterior: posterior samples per observation")
+    ap.add_argument("--reverse-steps", type=int, default=500, help="--posterior: reverse steps")
+    ap.add_argument("--plain-steps", type=int, default=2,
+                    help="--posterior: reverse steps timed on the plain path")
+    ap.add_argument("--surrogate-models", type=int, default=16384,
+                    help="--posterior: FD pairs the surrogate trains on")
+    ap.add_argument("--surrogate-steps", type=int, default=6000,
+                    help="--posterior: Adam steps of the surrogate's training")
     ap.add_argument("--sampler", action="store_true",
                     help="reverse steps of Algorithm 2 (score, proposal, W2 guidance gradient, "
                          "chain rule, preconditioned update) on the 70x70 workload")
@@ -1050,6 +1293,8 @@ def main():
             run_mixed(args, rank, world, local_rank)
         elif args.sampler:
             run_sampler(args, rank, world, local_rank)
+        elif args.posterior:
+            run_posterior(args, rank, world, local_rank)
         elif args.conv:
             run_conv(args, rank, world, local_rank)
         elif args.dsm_train:

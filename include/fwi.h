@@ -112,7 +112,25 @@ typedef struct fwi_problem {
                             variable advanced per step.  CPML plans: 4th order,
                             top_bc = 0, checkpoint_every = 0, distinct receiver cells;
                             they run on FWI_KERNELS_CPML.                           */
+    int shape;           /* thread shape inside the family: FWI_SHAPE_DEFAULT (0) or one
+                            of the FWI_SHAPE_* of the family the plan runs on (the
+                            others fail with FWI_ERR_UNSUPPORTED); every shape computes
+                            the same results.  fwi_autotune_kernels measures them. */
 } fwi_problem;
+
+/* Thread shapes (fwi_problem.shape); the default is marked. */
+enum {
+    FWI_SHAPE_DEFAULT = 0,
+    FWI_SHAPE_RESIDENT_PAIRS = 1,    /* resident: two columns x 11 rows a thread, packed
+                                        f32x2 arithmetic (default where the padded width
+                                        is even and NZ <= 110)                          */
+    FWI_SHAPE_RESIDENT_COLUMNS = 2,  /* resident: one column x 22 rows a thread        */
+    FWI_SHAPE_CLUSTER_RS13 = 3,      /* cluster: 13-row thread strips (default if they fit) */
+    FWI_SHAPE_CLUSTER_RS19 = 4,      /* cluster: 19-row thread strips                  */
+    FWI_SHAPE_TILED_ROWS8 = 5,       /* tiled: 8 rows a thread, 256 threads a 32 x 64 tile
+                                        (default)                                       */
+    FWI_SHAPE_TILED_ROWS4 = 6        /* tiled: 4 rows a thread, 512 threads a tile      */
+};
 
 /* Absorbing layers (fwi_problem.absorber). */
 enum { FWI_ABSORBER_SPONGE = 0, FWI_ABSORBER_CPML = 1 };
@@ -342,33 +360,37 @@ FWI_API fwi_status fwi_w2_misfit_static(const fwi_plan *plan, const void *obs_ct
                                         const float *d_syn, float *J, float *w2,
                                         float *adj_src, void *stream);
 
-/* Measured choice of the propagator family (a tuning utility; the paper has
- * no counterpart).  For every family that can run the problem (resident,
- * tiled, cluster, CPML; see fwi_problem.kernels) it creates plans on T =
+/* Measured choice of the propagator family and thread shape (a tuning
+ * utility; the paper has no counterpart).  For every family that can run the
+ * problem (resident, tiled, cluster, CPML; see fwi_problem.kernels) and every
+ * shape of that family (fwi_problem.shape) it creates plans on T =
  * trial_steps and min(2T, nt) steps, times a gradient pass on each (the
  * faster of two after an untimed one: fwi_forward with the record, then
  * fwi_adjoint_grad with the synthetic data as adjoint source) in `scratch`,
  * and predicts the pass at the problem's nt as fixed cost + nt x cost per
  * step from the two timings (the families differ in both).  Reports the
- * family with the smallest prediction.  Blocks the host until the trial
- * work on the stream is done.
- *   prob, w2     the problem (its `kernels` field is ignored)
+ * family and shape with the smallest prediction.  Blocks the host until the
+ * trial work on the stream is done.
+ *   prob, w2     the problem (its `kernels` and `shape` fields are ignored)
  *   v            [B][nz][nx] device, representative models in (0, v_max]
  *   trial_steps  steps per trial, in [2, prob->nt]
  *   scratch      device buffer, 256-byte aligned, of at least
  *                fwi_autotune_scratch_bytes; overwritten
  *   family       written: FWI_KERNELS_RESIDENT, _TILED, _CLUSTER or _CPML
+ *   shape        written: the FWI_SHAPE_* of the chosen family measured fastest
  *   ms           [4] host, written: predicted milliseconds of one pass at nt
- *                steps for resident, tiled, cluster, CPML (-1 where the family
+ *                steps for resident, tiled, cluster, CPML, each at its fastest
+ *                shape (-1 where the family cannot run the problem); NULL to skip
+ *   shapes       [4] host, written: those fastest shapes (-1 where the family
  *                cannot run the problem); NULL to skip
- * Set kernels = *family in the problem before fwi_plan_create.  Errors:
- * those of fwi_plan_create for the problem, FWI_ERR_INVALID_ARG,
- * FWI_ERR_OOM (scratch too small), FWI_ERR_CUDA, and device statuses of
- * the trials (fwi_check). */
+ * Set kernels = *family and shape = *shape in the problem before
+ * fwi_plan_create.  Errors: those of fwi_plan_create for the problem,
+ * FWI_ERR_INVALID_ARG, FWI_ERR_OOM (scratch too small), FWI_ERR_CUDA, and
+ * device statuses of the trials (fwi_check). */
 FWI_API fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2,
                                         const float *v, int trial_steps, void *scratch,
-                                        size_t scratch_bytes, int *family, float *ms,
-                                        void *stream);
+                                        size_t scratch_bytes, int *family, int *shape, float *ms,
+                                        int *shapes, void *stream);
 
 /* Scratch bytes fwi_autotune_kernels needs for this problem and trial length
  * (the largest over the families of workspace + snapshots + data + gradient
@@ -692,6 +714,33 @@ FWI_API fwi_status fwi_ddpm_guidance(int batch, int ncell, const fwi_ddpm_step *
                                      const fwi_diffusion_space *space, const float *v0hat,
                                      const float *g_phys, const float *vjp, const float *tau2,
                                      float *g, float *h, void *stream);
+
+/* A reverse step whose launches replay from one CUDA graph: the step index
+ * lives in device memory and the coefficients in a device table, so the same
+ * launches serve every step of a chain.
+ * fwi_ddpm_table (host only): table [(n_steps + 1) x FWI_DDPM_RECORD_FLOATS]
+ *   floats of host memory receives record i (1 <= i <= n_steps) = the float
+ *   coefficients fwi_ddpm_proposal / fwi_ddpm_guidance use at step i with
+ *   this space (record 0 is zero); the caller copies it to the device.
+ * fwi_ddpm_proposal_at / fwi_ddpm_guidance_at: fwi_ddpm_proposal /
+ *   fwi_ddpm_guidance at step i = *step (a device int), coefficients from the
+ *   device table, the draws of the proposal at z + i z_stride; when i lies
+ *   outside 1..n_steps the kernels write nothing.
+ * fwi_ddpm_step_down: *step -= 1 (one thread), the last launch of a step.
+ * Errors: FWI_ERR_INVALID_ARG before any launch, FWI_ERR_CUDA. */
+#define FWI_DDPM_RECORD_FLOATS 12
+FWI_API fwi_status fwi_ddpm_table(const double *betas, int n_steps, int sigma_mode,
+                                  const fwi_diffusion_space *space, float *table);
+FWI_API fwi_status fwi_ddpm_proposal_at(int batch, int ncell, const float *table, const int *step,
+                                        int n_steps, const float *v_i, const float *score,
+                                        const float *mu, const float *tau2, const float *z,
+                                        long long z_stride, float *v0hat, float *v_prime,
+                                        float *v_phys, void *stream);
+FWI_API fwi_status fwi_ddpm_guidance_at(int batch, int ncell, const float *table, const int *step,
+                                        int n_steps, const float *v0hat, const float *g_phys,
+                                        const float *vjp, const float *tau2, float *g, float *h,
+                                        void *stream);
+FWI_API fwi_status fwi_ddpm_step_down(int *step, void *stream);
 
 /* ---------------------------------------------------------------- learned forward surrogate
  * Data-side steps of a convolutional encoder-decoder that maps a velocity model

@@ -35,6 +35,8 @@ FWI_ERR_DEVICE_TIMEOUT = 5
 FWI_ERR_OOM = 6
 KERNELS_AUTO, KERNELS_RESIDENT, KERNELS_TILED, KERNELS_CLUSTER, KERNELS_CPML = 0, 1, 2, 3, 4
 ABSORBER_SPONGE, ABSORBER_CPML = 0, 1
+(SHAPE_DEFAULT, SHAPE_RESIDENT_PAIRS, SHAPE_RESIDENT_COLUMNS, SHAPE_CLUSTER_RS13,
+ SHAPE_CLUSTER_RS19, SHAPE_TILED_ROWS8, SHAPE_TILED_ROWS4) = range(7)
 SIGMA_POSTERIOR, SIGMA_BETA = 0, 1
 FWI_MAX_SHOTS = 256
 FWI_MAX_RECEIVERS = 1024
@@ -52,7 +54,8 @@ class _Problem(ctypes.Structure):
                 ("v_ref", ctypes.c_double), ("refl_R", ctypes.c_double),
                 ("v_max", ctypes.c_double), ("batch", ctypes.c_int),
                 ("checkpoint_every", ctypes.c_int), ("space_order", ctypes.c_int),
-                ("kernels", ctypes.c_int), ("absorber", ctypes.c_int)]
+                ("kernels", ctypes.c_int), ("absorber", ctypes.c_int),
+                ("shape", ctypes.c_int)]
 
 
 class _W2(ctypes.Structure):
@@ -111,8 +114,9 @@ _lib.fwi_autotune_scratch_bytes.restype = _S
 _lib.fwi_autotune_scratch_bytes.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
 _lib.fwi_autotune_kernels.restype = _S
 _lib.fwi_autotune_kernels.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_size_t,
-                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
-                                      _vp]
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_int), _vp]
 _lib.fwi_group_create.restype = _S
 _lib.fwi_group_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)]
 _lib.fwi_group_destroy.restype = None
@@ -180,6 +184,15 @@ _lib.fwi_up2_bf16.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp]
 _lib.fwi_add_bf16.restype = _S
 _lib.fwi_add_bf16.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp]
 _i, _f = ctypes.c_int, ctypes.c_float
+_lib.fwi_ddpm_table.restype = _S
+_lib.fwi_ddpm_table.argtypes = [ctypes.POINTER(ctypes.c_double), _i, _i, ctypes.c_void_p, _vp]
+_lib.fwi_ddpm_proposal_at.restype = _S
+_lib.fwi_ddpm_proposal_at.argtypes = [_i, _i, _vp, _vp, _i] + [_vp] * 5 + [ctypes.c_longlong] + \
+    [_vp] * 4
+_lib.fwi_ddpm_guidance_at.restype = _S
+_lib.fwi_ddpm_guidance_at.argtypes = [_i, _i, _vp, _vp, _i] + [_vp] * 7
+_lib.fwi_ddpm_step_down.restype = _S
+_lib.fwi_ddpm_step_down.argtypes = [_vp, _vp]
 _lib.fwi_sur_pack.restype = _S
 _lib.fwi_sur_pack.argtypes = [_i] * 5 + [_f, _f] + [_vp] * 4
 _lib.fwi_sur_unpack_grad.restype = _S
@@ -266,6 +279,7 @@ class Problem:
     space_order: int = 4          # 4 or 8 (8: the paper solver's stencil, tiled kernels)
     kernels: int = 0              # propagator family: KERNELS_AUTO / _RESIDENT / _TILED / _CLUSTER / _CPML
     absorber: int = 0             # ABSORBER_SPONGE (damping layer) or ABSORBER_CPML
+    shape: int = 0                # thread shape inside the family (SHAPE_*; 0: default)
 
     @property
     def ns(self):
@@ -383,7 +397,8 @@ def _c_problem(prob: Problem, w2: W2Params):
                   len(prob.src_ix), len(prob.rec_ix),
                   *[ctypes.cast(a, _ip) for a in arrays],
                   prob.f_peak, prob.t0, prob.v_ref, prob.refl_R, prob.v_max, prob.batch,
-                  prob.checkpoint_every, prob.space_order, prob.kernels, prob.absorber)
+                  prob.checkpoint_every, prob.space_order, prob.kernels, prob.absorber,
+                  prob.shape)
     cw = _W2(w2.k, w2.cshift_factor, w2.eps_density, w2.n_xi, int(w2.squared))
     return cp, cw, arrays
 
@@ -404,15 +419,18 @@ def fwi_autotune_scratch_bytes(prob: Problem, w2: W2Params, trial_steps: int) ->
 
 
 def fwi_autotune_kernels(prob: Problem, w2: W2Params, v, trial_steps: int, scratch, stream=None):
-    """(fastest family, predicted ms of a pass at nt for [resident, tiled,
-    cluster, CPML]) -- -1 where a family cannot run the problem."""
+    """(fastest family, its fastest shape, predicted ms of a pass at nt for
+    [resident, tiled, cluster, CPML] each at its fastest shape, those shapes)
+    -- -1 where a family cannot run the problem."""
     cp, cw, _arrays = _c_problem(prob, w2)
-    fam = ctypes.c_int()
+    fam, shape = ctypes.c_int(), ctypes.c_int()
     ms = (ctypes.c_float * 4)()
+    shapes = (ctypes.c_int * 4)()
     _check(_lib.fwi_autotune_kernels(ctypes.byref(cp), ctypes.byref(cw), _ptr(v), int(trial_steps),
                                      _ptr(scratch), scratch.numel() * scratch.element_size(),
-                                     ctypes.byref(fam), ms, _stream(stream)))
-    return fam.value, [float(t) for t in ms]
+                                     ctypes.byref(fam), ctypes.byref(shape), ms, shapes,
+                                     _stream(stream)))
+    return fam.value, shape.value, [float(t) for t in ms], [int(x) for x in shapes]
 
 
 def fwi_plan_sizes(plan: _Handle):
@@ -504,6 +522,49 @@ def fwi_ddpm_guidance(batch, ncell, step: DdpmStep, space: DiffusionSpace, v0hat
     _check(_lib.fwi_ddpm_guidance(batch, ncell, ctypes.byref(st), ctypes.byref(sp), _ptr(v0hat),
                                   _ptr(g_phys), _ptr(vjp), _ptr(tau2), _ptr(g), _ptr(h),
                                   _stream(stream)))
+
+
+
+DDPM_RECORD_FLOATS = 12
+
+
+def ddpm_table(betas, sigma_mode=0, space=None, device=None) -> torch.Tensor:
+    """The device table of every step's coefficients for the graph-replayed
+    reverse step (fwi_ddpm_table; records of DDPM_RECORD_FLOATS floats, record
+    i for step i)."""
+    space = space if space is not None else DiffusionSpace()
+    b = (ctypes.c_double * len(betas))(*[float(x) for x in betas])
+    host = torch.zeros((len(betas) + 1) * DDPM_RECORD_FLOATS, dtype=torch.float32)
+    sp = _Space(space.shift, space.unit, space.v_lo, space.v_hi)
+    _check(_lib.fwi_ddpm_table(b, len(betas), int(sigma_mode), ctypes.byref(sp),
+                               ctypes.c_void_p(host.data_ptr())))
+    return host.to(device or torch.device("cuda"))
+
+
+def fwi_ddpm_proposal_at(batch, ncell, table, step, n_steps, v_i, score, mu, tau2, z, z_stride,
+                         v0hat, v_prime, v_phys, stream=None):
+    """fwi_ddpm_proposal at the device step index *step (int32 [1]); z is the
+    first of the per-step draws, step i reading z + i z_stride."""
+    if step.dtype != torch.int32 or step.numel() != 1 or not step.is_cuda:
+        raise ValueError("step must be one int32 on the device")
+    if z.numel() < (n_steps + 1) * z_stride:
+        raise ValueError("z holds fewer than (n_steps + 1) z_stride draws")
+    _check(_lib.fwi_ddpm_proposal_at(batch, ncell, _ptr(table), _ptr(step), n_steps, _ptr(v_i),
+                                     _ptr(score), _ptr(mu), _ptr(tau2), _ptr(z), int(z_stride),
+                                     _ptr(v0hat), _ptr(v_prime), _ptr(v_phys), _stream(stream)))
+
+
+def fwi_ddpm_guidance_at(batch, ncell, table, step, n_steps, v0hat, g_phys, vjp, tau2, g, h,
+                         stream=None):
+    if step.dtype != torch.int32 or step.numel() != 1 or not step.is_cuda:
+        raise ValueError("step must be one int32 on the device")
+    _check(_lib.fwi_ddpm_guidance_at(batch, ncell, _ptr(table), _ptr(step), n_steps, _ptr(v0hat),
+                                     _ptr(g_phys), _ptr(vjp), _ptr(tau2), _ptr(g), _ptr(h),
+                                     _stream(stream)))
+
+
+def fwi_ddpm_step_down(step, stream=None):
+    _check(_lib.fwi_ddpm_step_down(_ptr(step), _stream(stream)))
 
 
 def fwi_conv3x3_bf16(x, wt, bias, act, y, status=None, stream=None):
@@ -1016,8 +1077,9 @@ def image_metrics(v_true, v_rec, data_range, stream=None):
 
 def autotune(prob: Problem, w2: W2Params | None = None, v=None, trial_steps: int = 64,
              stream=None):
-    """The problem with `kernels` set to the family fwi_autotune_kernels
-    measured fastest, and the predicted milliseconds of one pass at nt steps
+    """The problem with `kernels` and `shape` set to the family and thread
+    shape fwi_autotune_kernels measured fastest, and the predicted
+    milliseconds of one pass at nt steps
     [resident, tiled, cluster, CPML] (-1: the family cannot run it).  `v`
     ([B][nz][nx] on the device) defaults to the linear v(z) ramp from 1500 m/s
     to min(4500, v_max) m/s; the scratch is a temporary torch buffer."""
@@ -1030,8 +1092,8 @@ def autotune(prob: Problem, w2: W2Params | None = None, v=None, trial_steps: int
             prob.batch, prob.nz, prob.nx).contiguous()
     n = fwi_autotune_scratch_bytes(prob, w2, trial_steps)
     scratch = torch.empty(max(n, 256), dtype=torch.uint8, device=v.device)
-    fam, ms = fwi_autotune_kernels(prob, w2, v, trial_steps, scratch, stream)
-    return dataclasses.replace(prob, kernels=fam), ms
+    fam, shape, ms, _ = fwi_autotune_kernels(prob, w2, v, trial_steps, scratch, stream)
+    return dataclasses.replace(prob, kernels=fam, shape=shape), ms
 
 
 class Group:

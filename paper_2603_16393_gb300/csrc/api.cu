@@ -90,6 +90,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (!(w2->eps_density >= 0.0) || !std::isfinite(w2->eps_density))
         return fail(FWI_ERR_INVALID_ARG, "eps_density must be >= 0");
     if (w2->squared != 0 && w2->squared != 1) return fail(FWI_ERR_INVALID_ARG, "squared must be 0 or 1");
+    if (p.shape < FWI_SHAPE_DEFAULT || p.shape > FWI_SHAPE_TILED_ROWS4)
+        return fail(FWI_ERR_INVALID_ARG, "shape %d is not an FWI_SHAPE_* value", p.shape);
     if (p.kernels < FWI_KERNELS_AUTO || p.kernels > FWI_KERNELS_CPML)
         return fail(FWI_ERR_INVALID_ARG, "kernels must be 0 (auto), 1, 2, 3 or 4");
     if (p.absorber != FWI_ABSORBER_SPONGE && p.absorber != FWI_ABSORBER_CPML)
@@ -115,6 +117,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     pl->fwd_pair = false;
     pl->adj_pair = false;
     pl->tiled = false;
+    pl->tile_rows = p.shape == FWI_SHAPE_TILED_ROWS4 ? 4 : 8;
     pl->p = p;
     pl->p.space_order = order;
     pl->w2 = *w2;
@@ -185,7 +188,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
             if (chunk < 1) pl->fast = false;
         }
         pl->nzs = nstrip * fwi::kFastRows;
-        pl->fwd_pair = pl->fast && fwi::fwd_pair_ok(pl->NX, pl->NZ, pl->fast_NZM);
+        pl->fwd_pair = pl->fast && p.shape != FWI_SHAPE_RESIDENT_COLUMNS &&
+                       fwi::fwd_pair_ok(pl->NX, pl->NZ, pl->fast_NZM);
         if (pl->fwd_pair) {
             fwi::ResidentShape &sh = pl->shape;
             const int nstrip2 = (pl->NZ + fwi::kFastRows / 2 - 1) / (fwi::kFastRows / 2);
@@ -258,6 +262,9 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
         static const int rs_buckets[] = {13, 19};
         int RS = 0, nstrip = 0, threads = 0;
         for (int rs : rs_buckets) {
+            if ((p.shape == FWI_SHAPE_CLUSTER_RS13 && rs != 13) ||
+                (p.shape == FWI_SHAPE_CLUSTER_RS19 && rs != 19))
+                continue;
             const int ns_ = (rc0 + rs - 1) / rs;
             const int th = (pl->NX * ns_ + 31) / 32 * 32;
             if (th <= fwi::clu_max_threads(rs)) {
@@ -298,6 +305,29 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
             // record: C RC rows per plane at the pitch P - 1
             pl->nzs = C * RC;
             pl->rec_pitch = P - 1;
+        }
+    }
+    // the shape must be one of the family the plan runs on
+    {
+        const int sh = p.shape;
+        bool ok = sh == FWI_SHAPE_DEFAULT;
+        const char *family = "CPML";
+        if (pl->cpml) {
+        } else if (pl->fast) {
+            family = "resident";
+            ok = ok || sh == FWI_SHAPE_RESIDENT_COLUMNS ||
+                 (sh == FWI_SHAPE_RESIDENT_PAIRS && pl->fwd_pair);
+        } else if (pl->cluster) {
+            family = "cluster";
+            ok = ok || sh == FWI_SHAPE_CLUSTER_RS13 || sh == FWI_SHAPE_CLUSTER_RS19;
+        } else if (pl->tiled) {
+            family = "tiled";
+            ok = ok || sh == FWI_SHAPE_TILED_ROWS8 || sh == FWI_SHAPE_TILED_ROWS4;
+        }
+        if (!ok) {
+            delete pl;
+            return fail(FWI_ERR_UNSUPPORTED,
+                        "shape %d is not a shape of the %s kernels this plan runs on", sh, family);
         }
     }
     if (fam == FWI_KERNELS_CLUSTER && !pl->cluster) {

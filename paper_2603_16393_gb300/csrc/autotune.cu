@@ -2,7 +2,10 @@
 //
 // Built on the public entry points only: for every family that accepts the
 // problem (one CTA per grid, a cluster of CTAs, global-memory tiles, and
-// for the CPML absorber its own kernels) it
+// for the CPML absorber its own kernels) and every thread shape of the
+// family (fwi_problem.shape: column pairs or single columns for the resident
+// kernels, 13- or 19-row strips for the cluster kernels, 8 or 4 rows a
+// thread for the tiled kernels) it
 // creates plans on two shortened time axes (T and 2T steps), times one
 // gradient pass (forward with the record, adjoint) on each after an untimed
 // one, in caller-provided scratch, and predicts the pass at the problem's nt
@@ -21,6 +24,11 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kFamilies[4] = {FWI_KERNELS_RESIDENT, FWI_KERNELS_TILED, FWI_KERNELS_CLUSTER,
                                FWI_KERNELS_CPML};
+// the shapes tried per family (in kFamilies order), default first
+constexpr int kShapes[4][2] = {{FWI_SHAPE_RESIDENT_PAIRS, FWI_SHAPE_RESIDENT_COLUMNS},
+                               {FWI_SHAPE_TILED_ROWS8, FWI_SHAPE_TILED_ROWS4},
+                               {FWI_SHAPE_CLUSTER_RS13, FWI_SHAPE_CLUSTER_RS19},
+                               {FWI_SHAPE_DEFAULT, -1}};
 
 size_t up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
@@ -33,11 +41,12 @@ struct Trial {
 // Plan of family `fam` for the problem on trial_steps steps; false if the
 // family cannot run it (FWI_ERR_UNSUPPORTED), the other errors returned.
 fwi_status make_trial(const fwi_problem &p, const fwi_w2_params &w2, int steps, int fam,
-                      Trial *t, bool *ok)
+                      int shape, Trial *t, bool *ok)
 {
     fwi_problem q = p;
     q.nt = steps;
     q.kernels = fam;
+    q.shape = shape;
     *ok = false;
     fwi_status s = fwi_plan_create(&q, &w2, &t->plan);
     if (s == FWI_ERR_UNSUPPORTED) return FWI_OK;
@@ -59,6 +68,7 @@ fwi_status check_args(const fwi_problem *prob, const fwi_w2_params *w2, int tria
     // the problem itself must be valid (any family)
     fwi_problem q = *prob;
     q.kernels = FWI_KERNELS_AUTO;
+    q.shape = FWI_SHAPE_DEFAULT;
     fwi_plan *pl = nullptr;
     const fwi_status s = fwi_plan_create(&q, w2, &pl);
     fwi_plan_destroy(pl);
@@ -82,23 +92,25 @@ fwi_status fwi_autotune_scratch_bytes(const fwi_problem *prob, const fwi_w2_para
     *bytes = 0;
     fwi_status s = check_args(prob, w2, trial_steps);
     if (s != FWI_OK) return s;
-    for (int fam : kFamilies) {
-        Trial t;
-        bool ok = false;
-        s = make_trial(*prob, *w2, long_trial(*prob, trial_steps), fam, &t, &ok);
-        if (ok && t.total() > *bytes) *bytes = t.total();
-        fwi_plan_destroy(t.plan);
-        if (s != FWI_OK) return s;
-    }
+    for (int k = 0; k < 4; ++k)
+        for (int sh : kShapes[k]) {
+            if (sh < 0) continue;
+            Trial t;
+            bool ok = false;
+            s = make_trial(*prob, *w2, long_trial(*prob, trial_steps), kFamilies[k], sh, &t, &ok);
+            if (ok && t.total() > *bytes) *bytes = t.total();
+            fwi_plan_destroy(t.plan);
+            if (s != FWI_OK) return s;
+        }
     return FWI_OK;
 }
 
 fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2, const float *v,
                                 int trial_steps, void *scratch, size_t scratch_bytes,
-                                int *family, float *ms, void *stream)
+                                int *family, int *shape, float *ms, int *shapes, void *stream)
 {
-    if (!v || !scratch || !family)
-        return fwi::record_error(FWI_ERR_INVALID_ARG, "v, scratch or family is NULL");
+    if (!v || !scratch || !family || !shape)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "v, scratch, family or shape is NULL");
     fwi_status s = check_args(prob, w2, trial_steps);
     if (s != FWI_OK) return s;
     if ((uintptr_t)scratch % kAlign != 0)
@@ -106,7 +118,9 @@ fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     float best = -1.f;
     *family = FWI_KERNELS_AUTO;
+    *shape = FWI_SHAPE_DEFAULT;
     float times[4] = {-1.f, -1.f, -1.f, -1.f};
+    int best_shape[4] = {-1, -1, -1, -1};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
@@ -115,13 +129,15 @@ fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2
         return fwi::record_error(FWI_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(ce));
     }
     const int n1 = trial_steps, n2 = long_trial(*prob, trial_steps);
-    for (int k = 0; k < 4 && s == FWI_OK; ++k) {
+    for (int cand = 0; cand < 8 && s == FWI_OK; ++cand) {
+        const int k = cand / 2, sh = kShapes[k][cand % 2];
+        if (sh < 0) continue;
         float tl[2] = {-1.f, -1.f};   // best time of one pass at n1 and n2 steps
         bool ran = false;
         for (int L = 0; L < (n2 > n1 ? 2 : 1) && s == FWI_OK; ++L) {
             Trial t;
             bool ok = false;
-            s = make_trial(*prob, *w2, L ? n2 : n1, kFamilies[k], &t, &ok);
+            s = make_trial(*prob, *w2, L ? n2 : n1, kFamilies[k], sh, &t, &ok);
             if (s == FWI_OK && ok && t.total() > scratch_bytes)
                 s = fwi::record_error(FWI_ERR_OOM,
                                       "scratch of %zu bytes < %zu (fwi_autotune_scratch_bytes)",
@@ -163,16 +179,21 @@ fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2
                 if (per < 0.f) per = 0.f;
                 pred = tl[0] + per * (float)(prob->nt - n1);
             }
-            times[k] = pred;
+            if (times[k] < 0.f || pred < times[k]) {
+                times[k] = pred;
+                best_shape[k] = sh;
+            }
             if (best < 0.f || pred < best) {
                 best = pred;
                 *family = kFamilies[k];
+                *shape = sh;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (ms) std::memcpy(ms, times, sizeof(times));
+    if (shapes) std::memcpy(shapes, best_shape, sizeof(best_shape));
     if (s == FWI_OK) fwi::record_error(FWI_OK, "%s", "");   // families that declined left a message
     return s;
 }

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstring>
 
 #include "fwi_internal.cuh"
 
@@ -60,14 +61,26 @@ __device__ __forceinline__ float prior_clean_estimate(float x, float mu, float t
 }
 
 // IDX: 32-bit element indices (and cell modulo) when B ncell < 2^32
-template <typename IDX>
+// DEV: the coefficients are record *step of the device table and the draws
+// are z + *step z_stride (a reverse step whose launches replay from a CUDA
+// graph); an index outside 1..n_steps writes nothing
+template <typename IDX, bool DEV>
 __global__ void __launch_bounds__(kThreads)
-    k_ddpm_proposal(IDX n, IDX ncell, StepF k, const float *__restrict__ v_i,
+    k_ddpm_proposal(IDX n, IDX ncell, StepF kv, const float *__restrict__ table,
+                    const int *__restrict__ step, int n_steps, size_t z_stride,
+                    const float *__restrict__ v_i,
                     const float *__restrict__ score, const float *__restrict__ mu,
                     const float *__restrict__ tau2, const float *__restrict__ z,
                     float *__restrict__ v0hat, float *__restrict__ v_prime,
                     float *__restrict__ v_phys)
 {
+    StepF k = kv;
+    if (DEV) {
+        const int i = *step;
+        if (i < 1 || i > n_steps) return;
+        k = *reinterpret_cast<const StepF *>(table + (size_t)i * FWI_DDPM_RECORD_FLOATS);
+        z += (size_t)i * z_stride;
+    }
     for (IDX e = (IDX)blockIdx.x * kThreads + threadIdx.x; e < n; e += (IDX)gridDim.x * kThreads) {
         const float x = v_i[e];
         float x0;
@@ -83,13 +96,20 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-template <typename IDX>
+template <typename IDX, bool DEV>
 __global__ void __launch_bounds__(kThreads)
-    k_ddpm_guidance(IDX n, IDX ncell, StepF k, const float *__restrict__ v0hat,
+    k_ddpm_guidance(IDX n, IDX ncell, StepF kv, const float *__restrict__ table,
+                    const int *__restrict__ step, int n_steps, const float *__restrict__ v0hat,
                     const float *__restrict__ g_phys, const float *__restrict__ vjp,
                     const float *__restrict__ tau2, float *__restrict__ g,
                     float *__restrict__ h)
 {
+    StepF k = kv;
+    if (DEV) {
+        const int i = *step;
+        if (i < 1 || i > n_steps) return;
+        k = *reinterpret_cast<const StepF *>(table + (size_t)i * FWI_DDPM_RECORD_FLOATS);
+    }
     for (IDX e = (IDX)blockIdx.x * kThreads + threadIdx.x; e < n; e += (IDX)gridDim.x * kThreads) {
         // the clamp passes the gradient only where it is the identity
         const float vp = fmaf(k.unit, v0hat[e], k.shift);
@@ -120,7 +140,23 @@ unsigned grid_for(size_t n)
     return (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+__global__ void k_step_down(int *step) { *step -= 1; }
+
 bool finite(double x) { return std::isfinite(x); }
+
+static_assert(sizeof(StepF) == FWI_DDPM_RECORD_FLOATS * sizeof(float) - sizeof(float),
+              "a table record is one StepF and one float of padding");
+
+fwi_status check_space(const fwi_diffusion_space *space)
+{
+    if (!space) return fwi::record_error(FWI_ERR_INVALID_ARG, "space must not be NULL");
+    const fwi_diffusion_space &sp = *space;
+    if (!finite(sp.shift) || !(sp.unit > 0.0) || !finite(sp.unit) || !finite(sp.v_lo) ||
+        !finite(sp.v_hi) || !(sp.v_lo < sp.v_hi))
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "need finite shift, unit > 0 and finite v_lo < v_hi");
+    return FWI_OK;
+}
 
 fwi_status check_common(int batch, int ncell, const fwi_ddpm_step *step,
                         const fwi_diffusion_space *space)
@@ -189,11 +225,13 @@ fwi_status fwi_ddpm_proposal(int batch, int ncell, const fwi_ddpm_step *step,
     const StepF k = step_f(*step, *space);
     cudaStream_t st = (cudaStream_t)stream;
     if (n + (size_t)grid_for(n) * kThreads < ((size_t)1 << 32))
-        k_ddpm_proposal<unsigned><<<grid_for(n), kThreads, 0, st>>>(
-            (unsigned)n, (unsigned)ncell, k, v_i, score, mu, tau2, z, v0hat, v_prime, v_phys);
+        k_ddpm_proposal<unsigned, false><<<grid_for(n), kThreads, 0, st>>>(
+            (unsigned)n, (unsigned)ncell, k, nullptr, nullptr, 0, 0, v_i, score, mu, tau2, z,
+            v0hat, v_prime, v_phys);
     else
-        k_ddpm_proposal<size_t><<<grid_for(n), kThreads, 0, st>>>(
-            n, (size_t)ncell, k, v_i, score, mu, tau2, z, v0hat, v_prime, v_phys);
+        k_ddpm_proposal<size_t, false><<<grid_for(n), kThreads, 0, st>>>(
+            n, (size_t)ncell, k, nullptr, nullptr, 0, 0, v_i, score, mu, tau2, z, v0hat, v_prime,
+            v_phys);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return fwi::record_error(FWI_ERR_CUDA, "fwi_ddpm_proposal launch: %s", cudaGetErrorString(e));
@@ -213,14 +251,105 @@ fwi_status fwi_ddpm_guidance(int batch, int ncell, const fwi_ddpm_step *step,
     const StepF k = step_f(*step, *space);
     cudaStream_t st = (cudaStream_t)stream;
     if (n + (size_t)grid_for(n) * kThreads < ((size_t)1 << 32))
-        k_ddpm_guidance<unsigned><<<grid_for(n), kThreads, 0, st>>>(
-            (unsigned)n, (unsigned)ncell, k, v0hat, g_phys, vjp, tau2, g, h);
+        k_ddpm_guidance<unsigned, false><<<grid_for(n), kThreads, 0, st>>>(
+            (unsigned)n, (unsigned)ncell, k, nullptr, nullptr, 0, v0hat, g_phys, vjp, tau2, g, h);
     else
-        k_ddpm_guidance<size_t><<<grid_for(n), kThreads, 0, st>>>(
-            n, (size_t)ncell, k, v0hat, g_phys, vjp, tau2, g, h);
+        k_ddpm_guidance<size_t, false><<<grid_for(n), kThreads, 0, st>>>(
+            n, (size_t)ncell, k, nullptr, nullptr, 0, v0hat, g_phys, vjp, tau2, g, h);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return fwi::record_error(FWI_ERR_CUDA, "fwi_ddpm_guidance launch: %s", cudaGetErrorString(e));
+    return FWI_OK;
+}
+
+fwi_status fwi_ddpm_table(const double *betas, int n_steps, int sigma_mode,
+                          const fwi_diffusion_space *space, float *table)
+{
+    if (!table) return fwi::record_error(FWI_ERR_INVALID_ARG, "table must not be NULL");
+    fwi_status s = check_space(space);
+    if (s != FWI_OK) return s;
+    float *rec = table;
+    for (int f = 0; f < FWI_DDPM_RECORD_FLOATS; ++f) rec[f] = 0.f;   // record 0 is unused
+    for (int i = 1; i <= n_steps; ++i) {
+        fwi_ddpm_step st;
+        s = fwi_ddpm_coefficients(betas, n_steps, i, sigma_mode, &st);
+        if (s != FWI_OK) return s;
+        const StepF k = step_f(st, *space);
+        float *r = table + (size_t)i * FWI_DDPM_RECORD_FLOATS;
+        std::memcpy(r, &k, sizeof(StepF));
+        r[FWI_DDPM_RECORD_FLOATS - 1] = 0.f;
+    }
+    return FWI_OK;
+}
+
+fwi_status fwi_ddpm_proposal_at(int batch, int ncell, const float *table, const int *step,
+                                int n_steps, const float *v_i, const float *score,
+                                const float *mu, const float *tau2, const float *z,
+                                long long z_stride, float *v0hat, float *v_prime, float *v_phys,
+                                void *stream)
+{
+    if (batch < 1 || ncell < 1 || n_steps < 1 || z_stride < 0)
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "batch, ncell, n_steps >= 1 and z_stride >= 0 needed");
+    if (!table || !step || !v_i || !z || !v0hat || !v_prime || !v_phys)
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "table, step, v_i, z and the outputs must not be NULL");
+    if (!score && (!mu || !tau2))
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "without a score, mu and tau2 are needed");
+    const size_t n = (size_t)batch * (size_t)ncell;
+    const float *tab = table;
+    static_assert(alignof(StepF) == alignof(float), "records are float arrays");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n + (size_t)grid_for(n) * kThreads < ((size_t)1 << 32))
+        k_ddpm_proposal<unsigned, true><<<grid_for(n), kThreads, 0, st>>>(
+            (unsigned)n, (unsigned)ncell, StepF{}, tab, step, n_steps, (size_t)z_stride, v_i,
+            score, mu, tau2, z, v0hat, v_prime, v_phys);
+    else
+        k_ddpm_proposal<size_t, true><<<grid_for(n), kThreads, 0, st>>>(
+            n, (size_t)ncell, StepF{}, tab, step, n_steps, (size_t)z_stride, v_i, score, mu, tau2,
+            z, v0hat, v_prime, v_phys);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fwi::record_error(FWI_ERR_CUDA, "fwi_ddpm_proposal_at launch: %s",
+                                 cudaGetErrorString(e));
+    return FWI_OK;
+}
+
+fwi_status fwi_ddpm_guidance_at(int batch, int ncell, const float *table, const int *step,
+                                int n_steps, const float *v0hat, const float *g_phys,
+                                const float *vjp, const float *tau2, float *g, float *h,
+                                void *stream)
+{
+    if (batch < 1 || ncell < 1 || n_steps < 1)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "batch, ncell, n_steps must be >= 1");
+    if (!table || !step || !v0hat || !g_phys || !g || !h)
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "table, step, v0hat, g_phys, g and h must not be NULL");
+    const size_t n = (size_t)batch * (size_t)ncell;
+    const float *tab = table;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n + (size_t)grid_for(n) * kThreads < ((size_t)1 << 32))
+        k_ddpm_guidance<unsigned, true><<<grid_for(n), kThreads, 0, st>>>(
+            (unsigned)n, (unsigned)ncell, StepF{}, tab, step, n_steps, v0hat, g_phys, vjp, tau2,
+            g, h);
+    else
+        k_ddpm_guidance<size_t, true><<<grid_for(n), kThreads, 0, st>>>(
+            n, (size_t)ncell, StepF{}, tab, step, n_steps, v0hat, g_phys, vjp, tau2, g, h);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fwi::record_error(FWI_ERR_CUDA, "fwi_ddpm_guidance_at launch: %s",
+                                 cudaGetErrorString(e));
+    return FWI_OK;
+}
+
+fwi_status fwi_ddpm_step_down(int *step, void *stream)
+{
+    if (!step) return fwi::record_error(FWI_ERR_INVALID_ARG, "step must not be NULL");
+    k_step_down<<<1, 1, 0, (cudaStream_t)stream>>>(step);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fwi::record_error(FWI_ERR_CUDA, "fwi_ddpm_step_down launch: %s",
+                                 cudaGetErrorString(e));
     return FWI_OK;
 }
 

@@ -36,7 +36,10 @@ namespace fwi {
 
 namespace {
 
-constexpr int TX = 64, TZ = 32, TROWS = 8, TTHREADS = 256;
+constexpr int TX = 64, TZ = 32;
+// rows a thread owns (a template bucket the plan's shape picks: 8 -> 256
+// threads a CTA, 4 -> 512); a CTA always covers one TZ x TX tile
+template <int TRW> __host__ __device__ constexpr int tile_threads() { return TX * TZ / TRW; }
 // halo tile: x from x0 - 4 (16-byte aligned start, covers a radius up to 4),
 // z from z0 - R for a stencil of radius R (2: 4th order, 4: 8th order)
 constexpr int HX = TX + 8;
@@ -159,8 +162,8 @@ __global__ void __launch_bounds__(256) k_tile_setup(const __grid_constant__ Prop
 }
 
 // ------------------------------------------------------------------ forward step
-template <int R, int TOPBC, bool STORE>
-__global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ CUtensorMap tm,
+template <int R, int TOPBC, bool STORE, int TRW>
+__global__ void __launch_bounds__(tile_threads<TRW>()) k_tile_fwd(const __grid_constant__ CUtensorMap tm,
                                                        const __grid_constant__ TileArgs a)
 {
     constexpr int HZ = halo_rows<R>();
@@ -173,14 +176,14 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
     __syncthreads();
     if (tid == 0 && !a.withhold) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
 
-    const int x = x0 + tx, zr = z0 + g * TROWS;
+    const int x = x0 + tx, zr = z0 + g * TRW;
     const bool colok = x < a.NX;
     const size_t plane = (size_t)a.NZ * a.NXp;
     const float *kab = a.ka + (size_t)b * plane, *abb = a.ab + (size_t)b * plane;
     float *vb = a.vinc + (size_t)bs * plane;
-    float ka[TROWS], ab[TROWS], vi[TROWS];
+    float ka[TRW], ab[TRW], vi[TRW];
 #pragma unroll
-    for (int r = 0; r < TROWS; ++r) {
+    for (int r = 0; r < TRW; ++r) {
         const int z = zr + r;
         const bool ok = colok && z < a.NZ;
         const size_t i = (size_t)z * a.NXp + x;
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
     if (!tile_wait(&mbar, a.status, a.wait_polls)) return;
     if (TOPBC == 1 && z0 == 0) {
         // mirrored ghost rows: row -k = row k, k = 1..R
-        for (int c = tid; c < HX; c += TTHREADS) {
+        for (int c = tid; c < HX; c += tile_threads<TRW>()) {
 #pragma unroll
             for (int k = 1; k <= R; ++k) tile[(R - k) * HX + c] = tile[(R + k) * HX + c];
         }
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
     }
     // data sample of the previous step at the receivers inside this tile
     if (a.d_syn && a.j > 0 && z0 <= a.rzmax && z0 + TZ > a.rzmin) {
-        for (int r = tid; r < a.nr; r += TTHREADS) {
+        for (int r = tid; r < a.nr; r += tile_threads<TRW>()) {
             const int pz = a.rec[r] >> 16, px = a.rec[r] & 0xffff;
             if (pz >= z0 && pz < z0 + TZ && px >= x0 && px < x0 + TX)
                 a.d_syn[((size_t)bs * a.nr + r) * a.nt + a.j - 1] =
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
         const size_t cells = (size_t)a.NZ * a.NX;
         float *st = a.ckpt + ((size_t)(a.j / a.ckpt_every) * gridDim.z + bs) * 2 * cells;
 #pragma unroll
-        for (int r = 0; r < TROWS; ++r) {
+        for (int r = 0; r < TRW; ++r) {
             const int z = zr + r;
             if (colok && z < a.NZ) {
                 st[(size_t)z * a.NX + x] = tile[(z - z0 + R) * HX + tx + 4];
@@ -224,12 +227,12 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_fwd(const __grid_constant__ C
     float *ub = a.unext + (size_t)bs * plane;
     float *rb = STORE ? a.rec_out + ((size_t)bs * a.rec_planes + (a.j - a.rec_base)) * plane
                       : nullptr;
-    const float *cp = tile + (g * TROWS + R) * HX + tx + 4;
+    const float *cp = tile + (g * TRW + R) * HX + tx + 4;
     float w[2 * R + 1];     // z window: w[R + k] = row z + k
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) w[k] = cp[(k - R) * HX];
 #pragma unroll
-    for (int r = 0; r < TROWS; ++r) {
+    for (int r = 0; r < TRW; ++r) {
         const float *c = cp + r * HX;
         w[2 * R] = c[R * HX];
         const float w0 = w[R];
@@ -294,8 +297,8 @@ __global__ void k_tile_resume(const float *__restrict__ st, int nbs, int NZ, int
 // part of psi to float32 round-off, as the forward's standard form does.
 // With the mirrored top, L^T adds the reflected weights back onto rows
 // 1..R: (L^T psi)_k += sum_{r=0}^{R-k} c_{r+k} psi_r.
-template <int R, int TOPBC>
-__global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ CUtensorMap tm,
+template <int R, int TOPBC, int TRW>
+__global__ void __launch_bounds__(tile_threads<TRW>()) k_tile_adj(const __grid_constant__ CUtensorMap tm,
                                                        const __grid_constant__ TileArgs a)
 {
     constexpr int HZ = halo_rows<R>();
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
     __syncthreads();
     if (tid == 0 && !a.withhold) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
 
-    const int x = x0 + tx, zr = z0 + g * TROWS;
+    const int x = x0 + tx, zr = z0 + g * TRW;
     const bool colok = x < a.NX;
     const size_t plane = (size_t)a.NZ * a.NXp;
     const float *kab = a.ka + (size_t)b * plane, *abb = a.ab + (size_t)b * plane;
@@ -317,9 +320,9 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
     float *pn = a.unext + (size_t)bs * plane;
     const float *rb =
         a.rec_in + ((size_t)bs * a.rec_planes + (a.nt - 1 - a.j - a.rec_base)) * plane;
-    float ka[TROWS], ab[TROWS], wi[TROWS], ac[TROWS], sv[TROWS];
+    float ka[TRW], ab[TRW], wi[TRW], ac[TRW], sv[TRW];
 #pragma unroll
-    for (int r = 0; r < TROWS; ++r) {
+    for (int r = 0; r < TRW; ++r) {
         const int z = zr + r;
         const bool ok = colok && z < a.NZ;
         const size_t i = (size_t)z * a.NXp + x;
@@ -333,11 +336,11 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
     const bool has_rec = z0 <= a.rzmax && z0 + TZ > a.rzmin;
     if (has_rec) {
 #pragma unroll
-        for (int r = 0; r < TROWS; ++r) inj[(g * TROWS + r) * TX + tx] = 0.f;
+        for (int r = 0; r < TRW; ++r) inj[(g * TRW + r) * TX + tx] = 0.f;
     }
     if (!tile_wait(&mbar, a.status, a.wait_polls)) return;
     if (has_rec) {
-        for (int r = tid; r < a.nr; r += TTHREADS) {
+        for (int r = tid; r < a.nr; r += tile_threads<TRW>()) {
             const int pz = a.rec[r] >> 16, px = a.rec[r] & 0xffff;
             if (pz >= z0 && pz < z0 + TZ && px >= x0 && px < x0 + TX)
                 inj[(pz - z0) * TX + px - x0] =
@@ -347,12 +350,12 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
     }
 
     const int sp = a.src[s], sz = sp >> 16, sx = sp & 0xffff;
-    const float *cp = tile + (g * TROWS + R) * HX + tx + 4;
+    const float *cp = tile + (g * TRW + R) * HX + tx + 4;
     float w[2 * R + 1];     // z window: w[R + k] = row z + k
 #pragma unroll
     for (int k = 0; k < 2 * R; ++k) w[k] = cp[(k - R) * HX];
 #pragma unroll
-    for (int r = 0; r < TROWS; ++r) {
+    for (int r = 0; r < TRW; ++r) {
         const float *c = cp + r * HX;
         w[2 * R] = c[R * HX];
         const float w0 = w[R];
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_adj(const __grid_constant__ C
             lap += extra;
         }
         float wn = fmaf(ka[r], lap, ab[r] * wi[r]);
-        if (has_rec) wn = fmaf(ka[r], inj[(g * TROWS + r) * TX + tx], wn);
+        if (has_rec) wn = fmaf(ka[r], inj[(g * TRW + r) * TX + tx], wn);
         const float pnv = w0 + wn;
         if (colok && z < a.NZ) {
             const size_t i = (size_t)z * a.NXp + x;
@@ -568,14 +571,22 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
         for (int j = jb; j < a.j_end; ++j) {
             s.j = j;
             s.unext = t.u[(j + 1) & 1];
-#define FWI_TFWD(RR, TB, ST) k_tile_fwd<RR, TB, ST><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
-            if (R == 4) {
-                if (store) tb ? FWI_TFWD(4, 1, true) : FWI_TFWD(4, 0, true);
-                else tb ? FWI_TFWD(4, 1, false) : FWI_TFWD(4, 0, false);
+#define FWI_TFWD(RR, TB, ST, TR)                                                              \
+    k_tile_fwd<RR, TB, ST, TR><<<grid, tile_threads<TR>(), 0, st>>>(maps[j & 1], s)
+#define FWI_TFWD_R(TR)                                                                         \
+    if (R == 4) {                                                                              \
+        if (store) tb ? FWI_TFWD(4, 1, true, TR) : FWI_TFWD(4, 0, true, TR);                   \
+        else tb ? FWI_TFWD(4, 1, false, TR) : FWI_TFWD(4, 0, false, TR);                       \
+    } else {                                                                                   \
+        if (store) tb ? FWI_TFWD(2, 1, true, TR) : FWI_TFWD(2, 0, true, TR);                   \
+        else tb ? FWI_TFWD(2, 1, false, TR) : FWI_TFWD(2, 0, false, TR);                       \
+    }
+            if (pl.tile_rows == 4) {
+                FWI_TFWD_R(4)
             } else {
-                if (store) tb ? FWI_TFWD(2, 1, true) : FWI_TFWD(2, 0, true);
-                else tb ? FWI_TFWD(2, 1, false) : FWI_TFWD(2, 0, false);
+                FWI_TFWD_R(8)
             }
+#undef FWI_TFWD_R
 #undef FWI_TFWD
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
@@ -609,12 +620,15 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
     for (int j = jb; j < a.j_end; ++j) {
         s.j = j;
         s.unext = t.p[(j + 1) & 1];
-        if (R == 4)
-            tb ? k_tile_adj<4, 1><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
-               : k_tile_adj<4, 0><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
-        else
-            tb ? k_tile_adj<2, 1><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s)
-               : k_tile_adj<2, 0><<<grid, TTHREADS, 0, st>>>(maps[j & 1], s);
+#define FWI_TADJ(RR, TB, TR) k_tile_adj<RR, TB, TR><<<grid, tile_threads<TR>(), 0, st>>>(maps[j & 1], s)
+        if (pl.tile_rows == 4) {
+            if (R == 4) tb ? FWI_TADJ(4, 1, 4) : FWI_TADJ(4, 0, 4);
+            else tb ? FWI_TADJ(2, 1, 4) : FWI_TADJ(2, 0, 4);
+        } else {
+            if (R == 4) tb ? FWI_TADJ(4, 1, 8) : FWI_TADJ(4, 0, 8);
+            else tb ? FWI_TADJ(2, 1, 8) : FWI_TADJ(2, 0, 8);
+        }
+#undef FWI_TADJ
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (a.j_end == a.nt) {

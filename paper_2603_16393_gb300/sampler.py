@@ -76,7 +76,7 @@ class LowFidelity:
         self.plan = api.Plan(api.coarse_problem(plan.prob), w2 or plan.w2p, device=plan.device)
         self.ctx = self.plan.w2_prepare(api.fwi_decimate2(d_obs))
 
-    def gradient(self, v_phys: torch.Tensor, stream=None):
+    def gradient(self, v_phys: torch.Tensor, stream=None, step: int = -1):
         """(J_c(R v) [B], R^T dJ_c/dv_c [B][nz][nx])."""
         vc = api.fwi_restrict2(v_phys, stream=stream)
         J, gc, _ = self.plan.gradient(vc, self.ctx, stream=stream)
@@ -94,7 +94,7 @@ class NetworkSurrogate:
         self.net, self.in_scale, self.out_scale = net, float(in_scale), float(out_scale)
         self.g = torch.empty(net.shape, dtype=torch.float32, device=net.dev)
 
-    def gradient(self, v_phys: torch.Tensor, stream=None):
+    def gradient(self, v_phys: torch.Tensor, stream=None, step: int = -1):
         self.net.eps(v_phys, 0, self.out_scale, self.g, stream, in_scale=self.in_scale)
         return None, self.g
 
@@ -106,9 +106,11 @@ class Sampler:
     potential: "w2" (J of Eq. final_objective; needs ``ctx`` from
     plan.w2_prepare), "l2" (Phi_l2 with ``d_obs`` and ``sigma_l2``) or None
     (no guidance: v_{i-1} = v').  Exactly one of ``prior`` and ``score_fn``.
-    surrogate: a LowFidelity W2 potential or a NetworkSurrogate used instead of
-    the full one in the first ``surrogate_fraction`` of the reverse steps
-    (i > N - round(fraction N)), the full physics after."""
+    surrogate: a LowFidelity W2 potential, a NetworkSurrogate or a
+    surrogate.GatedSurrogate (the learned forward surrogate judged by FD) used
+    instead of the full one in the first ``surrogate_fraction`` of the reverse
+    steps (i > N - round(fraction N)), the full physics after; its
+    ``gradient(v_phys, stream=, step=)`` returns (J or None, dJ/dv)."""
 
     def __init__(self, plan: api.Plan, betas: Sequence[float], *, potential: str | None = "w2",
                  ctx=None, d_obs=None, sigma_l2: float = 1.0, prior: GaussianPrior | None = None,
@@ -157,7 +159,7 @@ class Sampler:
 
     def _physics_gradient(self, i, stream):
         if self.uses_surrogate(i):
-            return self.surrogate.gradient(self.v_phys, stream)
+            return self.surrogate.gradient(self.v_phys, stream=stream, step=i)
         if self.potential == "w2":
             J, g_phys, _ = self.plan.gradient(self.v_phys, self.ctx, stream=stream)
         else:
@@ -216,3 +218,118 @@ class Sampler:
         for i in range(i_start or self.N, i_stop - 1, -1):
             v, _ = self.step(v, i, noise(i), stream=stream)
         return v
+
+
+class GraphChain:
+    """Algorithm 2 with the Gaussian prior, one CUDA graph per kind of reverse
+    step.  The step index lives in device memory (the step's last launch
+    decrements it), the coefficients in a device table (api.ddpm_table) and the
+    draws of every step in ``zs`` [N + 1][B][nz][nx] (row i for step i), so the
+    launches of a reverse step -- proposal (fwi_ddpm_proposal_at), the guidance
+    gradient, the chain rule (fwi_ddpm_guidance_at) and the preconditioned
+    update written over the state -- are captured once per kind and replayed
+    for every step of that kind:
+      "fd"     the full W2 gradient (forward -> misfit -> adjoint)
+      "sur"    a surrogate's gradient (surrogate.SurrogateGuidance)
+      "check"  the full gradient drives the update, and the surrogate's
+               gradient at the same model is compared with it: per-model
+               relative L2 errors into ``err`` (the FD solver as judge)
+    ``run`` replays the chain; with a surrogate, the steps i > i_switch (the
+    first ``surrogate_fraction`` of the chain) run "check" every
+    ``check_every`` steps and "sur" between checks until a check's largest
+    error exceeds ``threshold``, then "fd" for the rest (FD as fallback)."""
+
+    def __init__(self, plan: api.Plan, betas: Sequence[float], ctx, prior: GaussianPrior,
+                 guide: api.GuideParams, zs: torch.Tensor,
+                 space: api.DiffusionSpace = api.DiffusionSpace(),
+                 sigma_mode: int = api.SIGMA_POSTERIOR, surrogate=None,
+                 surrogate_fraction: float = 0.4, threshold: float = 0.05,
+                 check_every: int = 10):
+        B, nz, nx = plan.model_shape
+        self.N, self.B, self.ncell = len(betas), B, nz * nx
+        if tuple(zs.shape) != (self.N + 1, B, nz, nx):
+            raise ValueError(f"zs must be [{self.N + 1}][{B}][{nz}][{nx}]")
+        self.plan, self.ctx, self.prior, self.zs = plan, ctx, prior, zs
+        self.gparams = dataclasses.replace(guide, unit=1.0)
+        dev = plan.device
+        self.table = api.ddpm_table(list(betas), sigma_mode, space, dev)
+        self.step = torch.full((1,), self.N, dtype=torch.int32, device=dev)
+        new = lambda: torch.empty((B, nz, nx), dtype=torch.float32, device=dev)  # noqa: E731
+        self.v, self.v0hat, self.v_prime, self.v_phys, self.g, self.h = (new() for _ in range(6))
+        self.surrogate = surrogate
+        self.i_switch = self.N - int(round(surrogate_fraction * self.N)) if surrogate else self.N
+        self.threshold, self.check_every = float(threshold), int(check_every)
+        self.err = torch.zeros(B, dtype=torch.float32, device=dev)
+        self.graphs = {}
+        self.records: list = []
+        self.counts = {"fd": 0, "sur": 0, "check": 0}
+
+    def _launches(self, kind: str, stream):
+        B, n, N = self.B, self.ncell, self.N
+        api.fwi_ddpm_proposal_at(B, n, self.table, self.step, N, self.v, None, self.prior.mu,
+                                 self.prior.tau2, self.zs, B * n, self.v0hat, self.v_prime,
+                                 self.v_phys, stream)
+        if kind == "sur":
+            _, g_phys = self.surrogate.gradient(self.v_phys, stream=stream)
+        else:
+            _, g_phys, _ = self.plan.gradient(self.v_phys, self.ctx, stream=stream)
+            if kind == "check":
+                _, g_sur = self.surrogate.gradient(self.v_phys, stream=stream)
+                num = (g_sur - g_phys).reshape(B, -1).norm(dim=1)
+                den = g_phys.reshape(B, -1).norm(dim=1).clamp_min(1e-30)
+                self.err.copy_(num / den)
+        api.fwi_ddpm_guidance_at(B, n, self.table, self.step, N, self.v0hat, g_phys, None,
+                                 self.prior.tau2, self.g, self.h, stream)
+        api.guided_step(self.v_prime, self.v0hat, self.g, self.h, self.gparams, v_out=self.v,
+                        stream=stream)
+        api.fwi_ddpm_step_down(self.step, stream)
+
+    def capture(self, kind: str):
+        """Capture one reverse step of ``kind`` (the state and step index are
+        restored after the untimed warm-up launches)."""
+        if kind != "fd" and self.surrogate is None:
+            raise ValueError(f"step kind {kind!r} needs a surrogate")
+        v0, s0 = self.v.clone(), self.step.clone()
+        cur = torch.cuda.current_stream(self.plan.device)
+        side = torch.cuda.Stream(device=self.plan.device)
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            self._launches(kind, side)
+        cur.wait_stream(side)
+        self.v.copy_(v0)
+        self.step.copy_(s0)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self._launches(kind, torch.cuda.current_stream(self.plan.device))
+        self.graphs[kind] = graph
+        self.v.copy_(v0)
+        self.step.copy_(s0)
+        return graph
+
+    def run(self, v_start: torch.Tensor, i_start: int | None = None, i_stop: int = 1):
+        """Reverse steps i_start..i_stop (default N..1) from v_start by graph
+        replays; returns the state after step i_stop (self.v)."""
+        i_start = i_start or self.N
+        for k in (["fd"] + (["sur", "check"] if self.surrogate is not None else [])):
+            if k not in self.graphs:
+                self.capture(k)
+        self.v.copy_(v_start)
+        self.step.fill_(i_start)
+        rejected, since = False, None
+        for i in range(i_start, i_stop - 1, -1):
+            if i > self.i_switch and not rejected:
+                if since is None or since >= self.check_every:
+                    self.graphs["check"].replay()
+                    err = float(self.err.max())           # the judge's verdict (a host read)
+                    rejected = err > self.threshold
+                    self.records.append((i, err, not rejected))
+                    self.counts["check"] += 1
+                    since = 1
+                    continue
+                self.graphs["sur"].replay()
+                self.counts["sur"] += 1
+                since += 1
+            else:
+                self.graphs["fd"].replay()
+                self.counts["fd"] += 1
+        return self.v

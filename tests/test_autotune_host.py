@@ -21,8 +21,21 @@ def _up(n):
     return -(-n // 256) * 256
 
 
+SHAPES = {api.KERNELS_RESIDENT: (api.SHAPE_RESIDENT_PAIRS, api.SHAPE_RESIDENT_COLUMNS),
+          api.KERNELS_TILED: (api.SHAPE_TILED_ROWS8, api.SHAPE_TILED_ROWS4),
+          api.KERNELS_CLUSTER: (api.SHAPE_CLUSTER_RS13, api.SHAPE_CLUSTER_RS19),
+          api.KERNELS_CPML: (api.SHAPE_DEFAULT,)}
+
+
 def _trial_bytes(prob, steps, fam):
-    q = dataclasses.replace(prob, nt=steps, kernels=fam)
+    """The largest trial buffer over the family's shapes (None: the family
+    cannot run the problem)."""
+    sizes = [b for b in (_shape_bytes(prob, steps, fam, sh) for sh in SHAPES[fam]) if b]
+    return max(sizes) if sizes else None
+
+
+def _shape_bytes(prob, steps, fam, shape):
+    q = dataclasses.replace(prob, nt=steps, kernels=fam, shape=shape)
     try:
         h = api.fwi_plan_create(q, api.W2Params())
     except api.FwiError as e:
@@ -66,3 +79,27 @@ def test_autotune_rejects_bad_arguments():
     with pytest.raises(api.FwiError) as e:          # the problem itself is unstable
         api.fwi_autotune_scratch_bytes(_prob(v_max=9000.0), api.W2Params(), 32)
     assert e.value.code == 2
+
+
+def test_shapes_belong_to_their_family():
+    prob = _prob()
+    for fam, shapes in SHAPES.items():
+        if fam == api.KERNELS_CPML:
+            continue
+        for sh in shapes:
+            api.fwi_plan_create(dataclasses.replace(prob, kernels=fam, shape=sh), api.W2Params())
+        others = [x for f, ss in SHAPES.items() if f != fam for x in ss if x]
+        for sh in others:
+            with pytest.raises(api.FwiError) as e:
+                api.fwi_plan_create(dataclasses.replace(prob, kernels=fam, shape=sh),
+                                    api.W2Params())
+            assert e.value.code == 3 and "shape" in str(e.value)
+    with pytest.raises(api.FwiError) as e:
+        api.fwi_plan_create(dataclasses.replace(prob, shape=7), api.W2Params())
+    assert e.value.code == 1
+    # an odd padded width has no column pairs
+    odd = _prob(nx=69, src_ix=(0, 17, 34, 51, 68), rec_ix=tuple(range(69)), rec_iz=(0,) * 69)
+    with pytest.raises(api.FwiError):
+        api.fwi_plan_create(dataclasses.replace(odd, shape=api.SHAPE_RESIDENT_PAIRS),
+                            api.W2Params())
+    api.fwi_plan_create(dataclasses.replace(odd, shape=api.SHAPE_RESIDENT_COLUMNS), api.W2Params())

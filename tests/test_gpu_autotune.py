@@ -35,13 +35,20 @@ def test_autotune_times_every_family_and_picks_the_fastest(api, nz, nx, nb, n_fa
     v = T(initial(2, nz, nx))
     n = api.fwi_autotune_scratch_bytes(gp, api.W2Params(), 40)
     scratch = torch.empty(n, dtype=torch.uint8, device=DEV)
+    fams = [api.KERNELS_RESIDENT, api.KERNELS_TILED, api.KERNELS_CLUSTER, api.KERNELS_CPML]
+    family_shapes = {api.KERNELS_RESIDENT: (api.SHAPE_RESIDENT_PAIRS, api.SHAPE_RESIDENT_COLUMNS),
+                     api.KERNELS_TILED: (api.SHAPE_TILED_ROWS8, api.SHAPE_TILED_ROWS4),
+                     api.KERNELS_CLUSTER: (api.SHAPE_CLUSTER_RS13, api.SHAPE_CLUSTER_RS19)}
     for _ in range(2):                      # twice in a row on the same scratch
-        fam, ms = api.fwi_autotune_kernels(gp, api.W2Params(), v, 40, scratch)
+        fam, shape, ms, shapes = api.fwi_autotune_kernels(gp, api.W2Params(), v, 40, scratch)
         ran = [t for t in ms if t >= 0]
         assert len(ran) == n_fam and all(t > 0 for t in ran)
-        assert len(ms) == 4 and ms[3] == -1      # CPML runs CPML-absorber problems only
-        assert ms[[api.KERNELS_RESIDENT, api.KERNELS_TILED, api.KERNELS_CLUSTER].index(fam)] \
-            == min(ran)
+        assert len(ms) == 4 and ms[3] == -1 and shapes[3] == -1   # CPML: CPML problems only
+        assert ms[fams.index(fam)] == min(ran)
+        # every family that ran names one of its own shapes, the chosen one too
+        for f, t, sh in zip(fams[:3], ms, shapes):
+            assert (t < 0 and sh == -1) or sh in family_shapes[f]
+        assert shape == shapes[fams.index(fam)]
     # the scratch must cover the trial plans
     with pytest.raises(api.FwiError) as e:
         api.fwi_autotune_kernels(gp, api.W2Params(), v, 40, scratch[: n // 2])

@@ -797,6 +797,101 @@ def run_sampler(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_uneven(args, rank, world, local_rank):
+    """--uneven: gradients of uneven instances that the resident kernels hold
+    -- 64 curved/faulted models of 70 x 70 (5 shots), 48 of 60 x 50 (3 shots)
+    and 32 of 40 x 90 (4 shots), dx = 10 m, 1000 steps, a 40-cell layer on
+    the 70 x 70 grids and 20 cells on the others -- three ways: each plan's
+    gradient in turn, the plans as a group on forked streams (one CUDA graph),
+    and the forward and adjoint of all plans each in one persistent launch
+    (api.Queue; every (model, shot) unit of every plan on one list that the
+    CTAs draw from).  The metric is gradients (models) per second."""
+    import torch
+    from paper_2603_16393_gb300 import api
+    from paper_2603_16393_gb300 import inputs as I
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    sizes = [(70, 70, 40, 5, 64), (60, 50, 20, 3, 48), (40, 90, 20, 4, 32)]
+    plans, vs, ctxs = [], [], []
+    for k, (nz, nx, nb, ns, B) in enumerate(sizes):
+        geo = I.surface_geometry(nx, ns)
+        prob = api.Problem(nz=nz, nx=nx, nb=nb, nt=args.nt or 1000, dz=DX, dx=DX, dt=DT,
+                           src_iz=geo.src_iz, src_ix=geo.src_ix, rec_iz=geo.rec_iz,
+                           rec_ix=geo.rec_ix, v_max=4500.0, batch=B)
+        p = api.Plan(prob, api.W2Params(), device=dev)
+        seed0 = rank_seed0(rank, 1000) + 1000 * k
+        vt = torch.tensor(I.model_batch("curved_faulted", range(seed0, seed0 + B), nz, nx),
+                          dtype=torch.float32, device=dev)
+        ctxs.append(p.w2_prepare(p.forward(vt, store=False)[0].clone()))
+        vs.append(torch.tensor(np.stack([I.linear_initial_model(nz, nx)] * B),
+                               dtype=torch.float32, device=dev))
+        plans.append(p)
+    models = sum(B for *_, B in sizes)
+    group = api.Group(plans)
+    queue = api.Queue(plans)
+    stream = torch.cuda.current_stream(dev)
+
+    def sequential():
+        for p, v, c in zip(plans, vs, ctxs):
+            p.gradient(v, c)
+
+    def grouped():
+        group.gradient(vs, ctxs)
+
+    def queued():
+        queue.gradient(vs, ctxs)
+
+    def timed(fn):
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(args.warmup):
+                fn()
+        stream.wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            fn()
+        graph.replay()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / args.steps
+
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    ms = {k: timed(f) for k, f in (("sequential", sequential), ("group", grouped),
+                                   ("queue", queued))}
+    clk = clocks.stop() if clocks else None
+    for p in plans:
+        p.check()
+    ms = dict(zip(ms, max_over_ranks(list(ms.values()), world, dev)))
+    if rank != 0:
+        return
+    line = {
+        "metric": "W2-FWI gradients/s of uneven resident instances (64 x 70x70 + 48 x 60x50 + "
+                  "32 x 40x90, 1000 steps)",
+        "value": world * models / (ms["queue"] * 1e-3), "unit": "gradients/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["queue"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded curved/faulted models)",
+        "config": {"workload": "; ".join(f"{B} x {nz}x{nx}, {ns} shots, {nb}-cell layer"
+                                         for nz, nx, nb, ns, B in sizes),
+                   "forms": "each form captured in one CUDA graph and replayed",
+                   "l2": "inputs larger than L2 (wavefield record 28 GB per step)"},
+        "ms": ms,
+        "models_per_s": {k: world * models / (t * 1e-3) for k, t in ms.items()},
+        "queue_vs_sequential": ms["sequential"] / ms["queue"],
+        "queue_vs_group": ms["group"] / ms["queue"],
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_posterior(args, rank, world, local_rank):
     """--posterior: posterior sampling by Algorithm 2 (Sec. 5.2) on noisy
     observations (10 dB), as the scope table's full guided reverse diffusion
@@ -1262,6 +1357,9 @@ def main():
     ap.add_argument("--dsm-train", action="store_true",
                     help="denoising-score-matching training steps of the convolutional score "
                          "model (152 x 70x70, 3 layers of --conv-channels)")
+    ap.add_argument("--uneven", action="store_true",
+                    help="uneven resident instances: per-plan gradients, a plan group, and one "
+                         "persistent launch per direction (api.Queue)")
     ap.add_argument("--posterior", action="store_true",
                     help="posterior sampling by Algorithm 2 on 10 dB observations: batched "
                          "graph-replayed chains with all-FD and with gated surrogate guidance "
@@ -1295,6 +1393,8 @@ def main():
             run_sampler(args, rank, world, local_rank)
         elif args.posterior:
             run_posterior(args, rank, world, local_rank)
+        elif args.uneven:
+            run_uneven(args, rank, world, local_rank)
         elif args.conv:
             run_conv(args, rank, world, local_rank)
         elif args.dsm_train:

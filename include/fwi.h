@@ -426,6 +426,32 @@ FWI_API fwi_status fwi_group_gradient(fwi_group *group, const float *const *v,
                                       float *const *grad, float *const *J,
                                       void *const *workspace, void *stream);
 
+/* Persistent passes over uneven instances (a batching utility; the paper has
+ * no counterpart).  The forward (record on) or the adjoint of up to
+ * FWI_QUEUE_MAX_PLANS plans of different grid sizes in ONE launch: every
+ * (model, shot) unit of every plan goes on one numbered list (plan by plan, in
+ * the order given: put the largest first), and each CTA of the resident
+ * column-pair propagators draws the next unit from *counter until the list is
+ * done, so units of different grids run side by side and no SM waits for the
+ * tail of one plan.  Results are bitwise those of fwi_forward /
+ * fwi_adjoint_grad on each plan.
+ *   plans     store-all plans (checkpoint_every 0) of the resident column-pair
+ *             kernels (padded NZ <= 110 and an even padded width <= 156), one
+ *             top_bc; others fail with FWI_ERR_UNSUPPORTED
+ *   lists     one entry per plan, with the layout of the single-plan call
+ *   counter   one int of device memory, owned by the caller; the call zeroes it
+ *             on the stream before the launch (no allocation)
+ * fwi_queue_adjoint also sums each plan's shots into grad.
+ * Errors: FWI_ERR_INVALID_ARG, FWI_ERR_UNSUPPORTED, FWI_ERR_CUDA. */
+#define FWI_QUEUE_MAX_PLANS 4
+FWI_API fwi_status fwi_queue_forward(const fwi_plan *const *plans, int n, const float *const *v,
+                                     float *const *d_syn, float *const *snapshots,
+                                     void *const *workspace, int *counter, void *stream);
+FWI_API fwi_status fwi_queue_adjoint(const fwi_plan *const *plans, int n, const float *const *v,
+                                     const float *const *adj_src, const float *const *snapshots,
+                                     float *const *grad, void *const *workspace, int *counter,
+                                     void *stream);
+
 /* Wait for `stream` and return the device status word of `workspace`
  * (FWI_OK, FWI_ERR_UNSTABLE_CFL, FWI_ERR_DEVICE_TIMEOUT), then clear it. */
 FWI_API fwi_status fwi_check(const fwi_plan *plan, void *workspace, void *stream);

@@ -40,6 +40,7 @@ ABSORBER_SPONGE, ABSORBER_CPML = 0, 1
 SIGMA_POSTERIOR, SIGMA_BETA = 0, 1
 FWI_MAX_SHOTS = 256
 FWI_MAX_RECEIVERS = 1024
+FWI_QUEUE_MAX_PLANS = 4
 
 _ip = ctypes.POINTER(ctypes.c_int)
 _vp = ctypes.c_void_p
@@ -117,6 +118,12 @@ _lib.fwi_autotune_kernels.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_int), _vp]
+_lib.fwi_queue_forward.restype = _S
+_lib.fwi_queue_forward.argtypes = [ctypes.POINTER(_vp), ctypes.c_int] + [ctypes.POINTER(_vp)] * 4 + \
+    [_vp, _vp]
+_lib.fwi_queue_adjoint.restype = _S
+_lib.fwi_queue_adjoint.argtypes = [ctypes.POINTER(_vp), ctypes.c_int] + [ctypes.POINTER(_vp)] * 5 + \
+    [_vp, _vp]
 _lib.fwi_group_create.restype = _S
 _lib.fwi_group_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp)]
 _lib.fwi_group_destroy.restype = None
@@ -1094,6 +1101,59 @@ def autotune(prob: Problem, w2: W2Params | None = None, v=None, trial_steps: int
     scratch = torch.empty(max(n, 256), dtype=torch.uint8, device=v.device)
     fam, shape, ms, _ = fwi_autotune_kernels(prob, w2, v, trial_steps, scratch, stream)
     return dataclasses.replace(prob, kernels=fam, shape=shape), ms
+
+
+class Queue:
+    """Plans of uneven grid sizes whose forward and adjoint passes each run as
+    ONE persistent launch (fwi_queue_forward / fwi_queue_adjoint): every
+    (model, shot) unit of every plan on one list, drawn by the CTAs from a
+    device counter.  Plans are taken largest first.  ``gradient`` runs the
+    queued forward, each plan's W2 misfit, the queued adjoint (with the shot
+    sums); outputs are allocated here once and reused."""
+
+    def __init__(self, plans):
+        if not 1 <= len(plans) <= FWI_QUEUE_MAX_PLANS:
+            raise ValueError(f"1 to {FWI_QUEUE_MAX_PLANS} plans")
+        self.plans = list(plans)
+        dev = self.plans[0].device
+        self.counter = torch.zeros(1, dtype=torch.int32, device=dev)
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.d_syn = [torch.empty(p.data_shape, **f32) for p in self.plans]
+        self.grad = [torch.empty(p.model_shape, **f32) for p in self.plans]
+
+    @staticmethod
+    def _arr(ts):
+        return (_vp * len(ts))(*[ctypes.cast(_ptr(t), _vp) for t in ts])
+
+    def forward(self, vs, stream=None):
+        for p, v in zip(self.plans, vs):
+            _f32(v, p.model_shape, "v")
+        _check(_lib.fwi_queue_forward((_vp * len(self.plans))(*[p.handle.raw for p in self.plans]),
+                                      len(self.plans), self._arr(vs), self._arr(self.d_syn),
+                                      self._arr([p.snapshots for p in self.plans]),
+                                      self._arr([p.workspace for p in self.plans]),
+                                      _ptr(self.counter), _stream(stream)))
+        return self.d_syn
+
+    def adjoint(self, vs, adjs, stream=None):
+        _check(_lib.fwi_queue_adjoint((_vp * len(self.plans))(*[p.handle.raw for p in self.plans]),
+                                      len(self.plans), self._arr(vs), self._arr(adjs),
+                                      self._arr([p.snapshots for p in self.plans]),
+                                      self._arr(self.grad),
+                                      self._arr([p.workspace for p in self.plans]),
+                                      _ptr(self.counter), _stream(stream)))
+        return self.grad
+
+    def gradient(self, vs, ctxs, stream=None):
+        """(J list, dJ/dv list) for models vs[i] against contexts ctxs[i]."""
+        self.forward(vs, stream)
+        Js, adjs = [], []
+        for p, c, d in zip(self.plans, ctxs, self.d_syn):
+            J, _, adj = p.w2_misfit(c, d, want_w2=False, stream=stream)
+            Js.append(J)
+            adjs.append(adj)
+        self.adjoint(vs, adjs, stream)
+        return Js, self.grad
 
 
 class Group:

@@ -104,6 +104,7 @@ struct Plan {
 struct PropArgs {
     int nz, nx, nb, NZ, NX, nt, ns, nr;
     int nzs;                             // rows of one wavefield-record plane
+    int units;                           // (model, shot) units of the plan: batch x ns
     int rows, nstrip, chunk;
     float dt;
     double dtd, t0d;                     // dt and the Ricker delay in double: the
@@ -141,6 +142,29 @@ struct PropArgs {
     int16_t src_pz[FWI_MAX_SHOTS], src_px[FWI_MAX_SHOTS];
     int16_t rec_pz[FWI_MAX_RECEIVERS], rec_px[FWI_MAX_RECEIVERS];
 };
+
+// Persistent launch over the (model, shot) units of several resident
+// column-pair plans (k_fwd_pair_queue / k_adj_pair_queue): plan p owns units
+// start[p] .. start[p+1]-1, CTAs draw unit numbers from *counter
+constexpr int kQueuePlans = FWI_QUEUE_MAX_PLANS;
+struct QueueArgs {
+    int n, total;
+    int start[kQueuePlans + 1];
+    int *counter;
+    PropArgs a[kQueuePlans];
+};
+
+PropArgs make_args(const Plan &pl);
+__global__ void k_shot_sum(int B, int ns, int n, const float *__restrict__ gshot,
+                           float *__restrict__ grad);
+// Whether a plan can take part in a persistent launch (store-all resident
+// column-pair plans of the 110-row bucket)
+bool queue_ok(const Plan &pl);
+// One persistent launch of the forward (adj false; a[i] with v, d_syn, snap,
+// status set) or adjoint (adj true; v, adj, snap, gshot, status set) of the
+// plans, on at most one CTA per SM; *counter is zeroed first
+cudaError_t launch_fast_queue(const Plan *const *plans, int n, bool adj, const PropArgs *a,
+                              int *counter, cudaStream_t st);
 
 // Records the message returned by fwi_last_error() for the calling thread
 // and returns code.

@@ -301,6 +301,8 @@ k_propagate(const __grid_constant__ PropArgs a)
     }
 }
 
+}  // namespace
+
 // grad[b][i] = sum_s gshot[b][s][i], s in increasing order.
 __global__ void k_shot_sum(int B, int ns, int n, const float *__restrict__ gshot,
                            float *__restrict__ grad)
@@ -321,6 +323,7 @@ PropArgs make_args(const Plan &pl)
     a.nz = p.nz; a.nx = p.nx; a.nb = p.nb; a.NZ = pl.NZ; a.NX = pl.NX;
     a.nt = p.nt; a.ns = p.ns; a.nr = p.nr;
     a.nzs = pl.nzs;
+    a.units = p.batch * p.ns;
     a.dt = (float)p.dt;
     const double ix2 = 1.0 / ((double)p.dx * p.dx), iz2 = 1.0 / ((double)p.dz * p.dz);
     a.c0 = (float)(-2.5 * (ix2 + iz2));
@@ -356,6 +359,9 @@ PropArgs make_args(const Plan &pl)
     }
     return a;
 }
+
+namespace {
+
 
 template <int MR, bool ADJ, int TBC>
 cudaError_t launch_one(const PropArgs &a, const ResidentShape &sh, int nblocks, cudaStream_t st)

@@ -273,15 +273,17 @@ __device__ __forceinline__ void fwd_rows_pair(const float *__restrict__ cp, floa
     }
 }
 
+// One (model, shot) unit bs of a plan: the whole forward time loop of the
+// column-pair kernel (k_fwd_pair runs one unit a CTA, k_fwd_pair_queue draws
+// units of several plans from a counter)
 template <int P, int PR, int NZM, int TOPBC, bool STORE>
-__global__ void __launch_bounds__(kMaxThreadsAdj, 1)
-k_fwd_pair(const __grid_constant__ PropArgs a)
+__device__ __forceinline__ void fwd_pair_unit(const PropArgs &a, const int bs)
 {
     extern __shared__ __align__(16) float sm[];
     constexpr int FSZ = (NZM + 4) * P;
     float *U0 = sm, *U1 = sm + FSZ, *ABt = sm + 2 * FSZ, *ST = ABt + NZM * P;
     const int NX = a.NX, NZ = a.NZ;
-    const int bs = blockIdx.x, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < 2 * FSZ; i += nth) sm[i] = 0.f;
     for (int i = tid; i < NZM * P; i += nth) {
@@ -358,7 +360,7 @@ k_fwd_pair(const __grid_constant__ PropArgs a)
             if (j0 % a.ckpt_every == 0) {
                 const float *cur = (j0 & 1) ? U1 : U0;
                 const size_t cl = (size_t)NZ * NX;
-                float *st = a.ckpt + ((size_t)(j0 / a.ckpt_every) * gridDim.x + bs) * 2 * cl;
+                float *st = a.ckpt + ((size_t)(j0 / a.ckpt_every) * a.units + bs) * 2 * cl;
                 for (int i = tid; i < NZ * NX; i += nth) {
                     const int z = i / NX, xx = i - (i / NX) * NX;
                     st[i] = cur[(z + 2) * P + xx + 2];
@@ -413,6 +415,34 @@ k_fwd_pair(const __grid_constant__ PropArgs a)
             }
         }
         __syncthreads();
+    }
+}
+
+template <int P, int PR, int NZM, int TOPBC, bool STORE>
+__global__ void __launch_bounds__(kMaxThreadsAdj, 1)
+k_fwd_pair(const __grid_constant__ PropArgs a)
+{
+    fwd_pair_unit<P, PR, NZM, TOPBC, STORE>(a, blockIdx.x);
+}
+
+// Persistent: every CTA draws units (plan p, unit bs) from the counter until
+// all q.total are taken; units are numbered plan by plan (q.start), the
+// caller orders the plans largest first
+template <int P, int PR, int NZM, int TOPBC, bool STORE>
+__global__ void __launch_bounds__(kMaxThreadsAdj, 1)
+k_fwd_pair_queue(const __grid_constant__ QueueArgs q)
+{
+    __shared__ int unit;
+    for (;;) {
+        if (threadIdx.x == 0) unit = atomicAdd(q.counter, 1);
+        __syncthreads();
+        const int u = unit;
+        __syncthreads();   // every thread has read it before thread 0 draws again
+        if (u >= q.total) return;
+        int p = 0;
+        while (p + 1 < q.n && u >= q.start[p + 1]) ++p;
+        fwd_pair_unit<P, PR, NZM, TOPBC, STORE>(q.a[p], u - q.start[p]);
+        __syncthreads();   // shared memory is reset by the next unit
     }
 }
 
@@ -596,7 +626,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
         // suspend: levels psi^je, psi^(je-1) and the imaging sums
         const int je = a.j_end;
         const size_t cells = (size_t)NZ * NX;
-        float *st = a.astate + (size_t)blockIdx.x * 3 * cells;
+        float *st = a.astate + (size_t)bs * 3 * cells;
         const float *cur = (je & 1) ? U1 : U0, *old = (je & 1) ? U0 : U1;
         for (int i = tid; i < NZ * NX; i += nth) {
             const int z = i / NX, xx = i - (i / NX) * NX;
@@ -758,8 +788,13 @@ __device__ __forceinline__ void adj_rows_pair(const float *__restrict__ cp,
     }
 }
 
+// One (model, shot) unit bs of a plan: the whole adjoint time loop of the
+// column-pair kernel with its epilogue; `tmem` is the CTA's tensor-memory
+// allocation of kAdjTmemCols columns (k_adj_pair allocates it for its one
+// unit, k_adj_pair_queue once for all the units it draws)
 template <int P, int PR, int NZM, int TOPBC>
-__global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_constant__ PropArgs a)
+__device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const int bs,
+                                              const uint32_t tmem)
 {
     extern __shared__ __align__(16) float sm[];
     constexpr int FSZ = (NZM + 4) * P;
@@ -770,7 +805,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
     float *U0 = sm, *U1 = sm + FSZ, *K = sm + 2 * FSZ, *IC = K + NZM * P, *ST = IC + a.nr;
     float *RS = ST + a.chunk * a.nr;
     const int NX = a.NX, NZ = a.NZ;
-    const int bs = blockIdx.x, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < 2 * FSZ; i += nth) sm[i] = 0.f;
     const float *vb = a.v + (size_t)b * a.nz * a.nx;
@@ -822,20 +857,9 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
     const int inj0_off = inj0 >= 0 ? (a.rec_pz[inj0] + 2) * P + x + 2 : 0;
     const int inj1_off = inj1 >= 0 ? (a.rec_pz[inj1] + 2) * P + x + 3 : 0;
     __shared__ float acc_src;
-    __shared__ uint32_t tmem_slot;
     if (tid == 0) acc_src = 0.f;
-    if (tid < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
-                     "r"(kAdjTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int warp = tid >> 5;
-    const uint32_t tacc = tmem_slot + ((uint32_t)(32 * (warp & 3)) << 16) +
+    const uint32_t tacc = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
                           (uint32_t)(4 * ROWS2 * (warp >> 2));
     const uint32_t tka = tacc + 2 * ROWS2;
 
@@ -911,7 +935,8 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
         __syncthreads();   // the last step's source-cell term reads RS before it is restaged
     }
 
-    // the imaging sums back into registers, tensor memory released
+    // the imaging sums back into registers (each thread reads only its own
+    // lane and columns, so the next unit may write them at once)
     float2 acc[ROWS2];
 #pragma unroll
     for (int r = 0; r < ROWS2; ++r) {
@@ -920,19 +945,11 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
         tmem_wait_ld();
         acc[r] = make_float2(__uint_as_float(s0), __uint_as_float(s1));
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (tid < 32) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_slot),
-                     "r"(kAdjTmemCols)
-                     : "memory");
-    }
     if (a.j_end < a.nt) {
         // suspend: levels psi^je, psi^(je-1) and the imaging sums
         const int je = a.j_end;
         const size_t cells = (size_t)NZ * NX;
-        float *st = a.astate + (size_t)blockIdx.x * 3 * cells;
+        float *st = a.astate + (size_t)bs * 3 * cells;
         const float *cur = (je & 1) ? U1 : U0, *old = (je & 1) ? U0 : U1;
         for (int i = tid; i < NZ * NX; i += nth) {
             const int z = i / NX, xx = i - (i / NX) * NX;
@@ -992,6 +1009,67 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
     }
 }
 
+// the CTA's tensor memory for the pair adjoint (one warp allocates; every
+// thread sees the base address after the barrier)
+__device__ __forceinline__ uint32_t adj_tmem_alloc(uint32_t *slot)
+{
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(slot)),
+                     "r"(kAdjTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return *slot;
+}
+
+__device__ __forceinline__ void adj_tmem_free(uint32_t tmem)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kAdjTmemCols)
+                     : "memory");
+    }
+}
+
+template <int P, int PR, int NZM, int TOPBC>
+__global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_constant__ PropArgs a)
+{
+    __shared__ uint32_t tmem_slot;
+    const uint32_t tmem = adj_tmem_alloc(&tmem_slot);
+    adj_pair_unit<P, PR, NZM, TOPBC>(a, blockIdx.x, tmem);
+    adj_tmem_free(tmem);
+}
+
+// Persistent: units drawn from the counter as in k_fwd_pair_queue, one
+// tensor-memory allocation for all of them
+template <int P, int PR, int NZM, int TOPBC>
+__global__ void __launch_bounds__(kMaxThreadsAdj, 1)
+k_adj_pair_queue(const __grid_constant__ QueueArgs q)
+{
+    __shared__ uint32_t tmem_slot;
+    __shared__ int unit;
+    const uint32_t tmem = adj_tmem_alloc(&tmem_slot);
+    for (;;) {
+        if (threadIdx.x == 0) unit = atomicAdd(q.counter, 1);
+        __syncthreads();
+        const int u = unit;
+        __syncthreads();
+        if (u >= q.total) break;
+        int p = 0;
+        while (p + 1 < q.n && u >= q.start[p + 1]) ++p;
+        adj_pair_unit<P, PR, NZM, TOPBC>(q.a[p], u - q.start[p], tmem);
+        __syncthreads();
+    }
+    adj_tmem_free(tmem);
+}
+
 template <typename K>
 cudaError_t launch_k(K kern, const PropArgs &a, const ResidentShape &sh, int nblocks,
                      cudaStream_t st)
@@ -1048,6 +1126,57 @@ int fast_chunk(int P, int NZM, bool adj, int nr)
     if (fixed + per > limit) return 0;
     const size_t c = (limit - fixed) / per;
     return c > 32 ? 32 : (int)c;
+}
+
+bool queue_ok(const Plan &pl)
+{
+    return pl.fast && pl.fwd_pair && pl.adj_pair && pl.fast_NZM == 110 && pl.ckpt_every == 0 &&
+           !pl.cpml;
+}
+
+cudaError_t launch_fast_queue(const Plan *const *plans, int n, bool adj, const PropArgs *a,
+                              int *counter, cudaStream_t st)
+{
+    if (n < 1 || n > kQueuePlans) return cudaErrorInvalidValue;
+    QueueArgs q{};
+    q.n = n;
+    q.counter = counter;
+    size_t smem = 0;
+    const int tb = plans[0]->p.top_bc;
+    for (int i = 0; i < n; ++i) {
+        const Plan &pl = *plans[i];
+        if (!queue_ok(pl) || pl.p.top_bc != tb) return cudaErrorInvalidValue;
+        const ResidentShape &sh = adj ? pl.shape_adj : pl.shape;
+        q.start[i] = q.total;
+        q.total += pl.p.batch * pl.p.ns;
+        q.a[i] = a[i];
+        q.a[i].rows = sh.rows;
+        q.a[i].nstrip = sh.nstrip;
+        q.a[i].chunk = sh.chunk;
+        if (sh.smem > smem) smem = sh.smem;
+    }
+    q.start[n] = q.total;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 152;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const int grid = q.total < sms ? q.total : sms;
+    auto go = [&](auto kern) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (r != cudaSuccess) return r;
+        kern<<<grid, kMaxThreadsAdj, smem, st>>>(q);
+        return cudaGetLastError();
+    };
+    const bool store = a[0].snap != nullptr;
+    if (adj) return tb ? go(k_adj_pair_queue<kPairPitch, 160, 110, 1>)
+                       : go(k_adj_pair_queue<kPairPitch, 160, 110, 0>);
+    if (store) return tb ? go(k_fwd_pair_queue<kPairPitch, 160, 110, 1, true>)
+                         : go(k_fwd_pair_queue<kPairPitch, 160, 110, 0, true>);
+    return tb ? go(k_fwd_pair_queue<kPairPitch, 160, 110, 1, false>)
+              : go(k_fwd_pair_queue<kPairPitch, 160, 110, 0, false>);
 }
 
 cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st)

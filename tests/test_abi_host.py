@@ -313,3 +313,23 @@ def test_coarse_problem_rejects_short_runs(api):
     with pytest.raises(api.FwiError) as e:
         api.coarse_problem(_prob(api, nt=3))
     assert e.value.code == api.FWI_ERR_INVALID_ARG
+
+
+def test_queue_rejects_plans_outside_the_column_pair_kernels(api):
+    # an odd padded width (no column pairs) and a checkpointed plan: refused
+    # before any CUDA call
+    odd = api.fwi_plan_create(_prob(api, nx=69, src_ix=(0, 17, 34, 51, 68),
+                                    rec_ix=tuple(range(69)), rec_iz=(0,) * 69), api.W2Params())
+    ck = api.fwi_plan_create(_prob(api, checkpoint_every=32), api.W2Params())
+    ok = api.fwi_plan_create(_prob(api), api.W2Params())
+    vp = ctypes.c_void_p
+    dummy = (vp * 2)(vp(256), vp(256))
+    cnt = ctypes.c_void_p(256)
+    for bad in (odd, ck):
+        plans = (vp * 2)(ok.raw, bad.raw)
+        rc = api._lib.fwi_queue_forward(plans, 2, dummy, dummy, dummy, dummy, cnt, None)
+        assert rc == api.FWI_ERR_UNSUPPORTED
+        assert "column-pair" in api.fwi_last_error()
+    plans = (vp * 5)(*([ok.raw] * 5))
+    assert api._lib.fwi_queue_forward(plans, 5, dummy, dummy, dummy, dummy, cnt, None) == \
+        api.FWI_ERR_INVALID_ARG

@@ -10,17 +10,19 @@ Sampled instances are compared with the FP64 oracle on the same inputs (the
 noisy observations are the oracle's clean data plus seeded noise, rounded to
 float32, handed to both sides).  The 512 x 1024 run is checked by properties
 that hold at any size (finite outputs; checkpoint interval and batch
-composition change no bit of J or dJ/dv); its grid is compared with the
-oracle over 600 steps and 8 shots.
+composition change no bit of J or dJ/dv), and one of its shots against the
+oracle over the whole 4000 steps.
 
-End-to-end parity bound of dJ/dv on the 256 x 256 / 2000-step workload: the
-FP64 objective's own gradient moves by 2.3e-3 (rel-L2) when its synthetic
-data carry white noise of 7e-7 RMS -- the accuracy of a float32 forward solve
-there (the same perturbation moves it by 1e-5 at 70 x 70 / 1000 steps): the
-quantile map of the W2 misfit amplifies data errors where a CDF crosses xi_j
-at low density.  So that workload's stages are held to the usual bars on
-their own (forward data 1e-5, adjoint on a shared adjoint source 1e-4) and the
-end-to-end gradient to 5e-3.
+End-to-end parity of dJ/dv on the long runs (256 x 256 / 2000 steps, 512 x
+1024 / 4000 steps): the W2 misfit's quantile map amplifies data errors where a
+CDF crosses xi_j at low density, so a float32 forward's data error (a few
+1e-7 RMS there; 1e-5 is the bar) moves the FP64 objective's own gradient by
+more than 1e-4.  The end-to-end bar on those runs is therefore an envelope
+measured in the test itself: the spread of the oracle's gradient when its own
+synthetic data carry white noise as large as the GPU's measured data error;
+the GPU gradient must lie within a few of those spreads.  The stages keep the
+usual bars on their own (forward data 1e-5, adjoint on a shared adjoint source
+1e-4).
 """
 import dataclasses
 from concurrent.futures import ThreadPoolExecutor
@@ -75,7 +77,20 @@ def test_64_curved_models_with_10db_noise(api):
         assert rel_l2(H(g)[b], g_o[0]) <= TOL_GRAD, (b, rel_l2(H(g)[b], g_o[0]))
 
 
-TOL_GRAD_256 = 5e-3     # see the module docstring
+ENVELOPE = 4.0     # GPU error <= ENVELOPE x the oracle's spread (see the module docstring)
+
+
+def _oracle_envelope(op, v, octx, ow2, g_o, data_err, seeds=(1, 2)):
+    """The largest rel-L2 change of the oracle's gradient at v when its
+    synthetic data carry white noise of relative RMS data_err."""
+    d = O.forward(op, v[None])
+    rms = float(np.sqrt(np.mean(d * d)))
+    out = 0.0
+    for sd in seeds:
+        noise = data_err * rms * np.random.default_rng(sd).standard_normal(d.shape)
+        _, _, adj = O.w2_misfit(octx, d + noise, op.dt, ow2)
+        out = max(out, rel_l2(_oracle_adjoint_stage(op, v, adj[0]), g_o))
+    return out
 
 
 def _oracle_adjoint_stage(op, v, adj):
@@ -111,14 +126,17 @@ def test_8_models_256x256_16_shots_2000_steps(api):
         plan.check()
     assert np.isfinite(g).all() and np.isfinite(J).all()
     # each stage at its own bar
-    assert rel_l2(d_syn[b_s], O.forward(op, v0[b_s:b_s + 1])[0]) <= TOL_DATA
+    data_err = rel_l2(d_syn[b_s], O.forward(op, v0[b_s:b_s + 1])[0])
+    assert data_err <= TOL_DATA
     assert rel_l2(g_adj[b_s], _oracle_adjoint_stage(op, v0[b_s], adj[b_s])) <= TOL_GRAD
-    # end to end
+    # end to end, within the oracle's own envelope at that data error
     ow2 = O.W2Params()
     octx = O.w2_prepare(d_o, op.dt, ow2)
     J_o, g_o, _ = O.gradient(op, v0[b_s:b_s + 1], octx, ow2)
     assert abs(J[b_s] - J_o[0]) <= TOL_J * 10 * abs(J_o[0]), (J[b_s], J_o[0])
-    assert rel_l2(g[b_s], g_o[0]) <= TOL_GRAD_256, rel_l2(g[b_s], g_o[0])
+    spread = _oracle_envelope(op, v0[b_s], octx, ow2, g_o[0], data_err)
+    err = rel_l2(g[b_s], g_o[0])
+    assert err <= max(ENVELOPE * spread, TOL_GRAD), (err, spread, data_err)
 
 
 def test_512x1024_grid_against_the_oracle_over_600_steps(api):
@@ -163,3 +181,29 @@ def test_2_models_512x1024_32_shots_4000_steps_checkpointed(api):
     assert float(g.abs().max()) > 0 and float(J.min()) > 0
     assert torch.equal(J, out[(64, B)][0]) and torch.equal(g, out[(64, B)][1])
     assert torch.equal(J[1:], out[(32, 1)][0]) and torch.equal(g[1:], out[(32, 1)][1])
+
+
+def test_512x1024_one_shot_4000_steps_against_the_oracle(api):
+    # the whole time axis of the 512 x 1024 workload for one model and one
+    # shot (the oracle keeps every wavefield level: 19.5 GB in FP64)
+    nz, nx, ns, nt = 512, 1024, 1, 4000
+    geo = I.surface_geometry(nx, 1)
+    gp, op = problems(nz, nx, 40, nt, ns, batch=1, geo=geo)
+    vt = models("curved_faulted", [4], nz, nx)
+    v0 = initial(1, nz, nx)
+    d_o = O.forward(op, vt).astype(np.float32).astype(np.float64)
+    with api.Plan(dataclasses.replace(gp, checkpoint_every=32)) as plan:
+        ctx = plan.w2_prepare(T(d_o))
+        J, g, _ = plan.gradient(T(v0), ctx)
+        d_syn = H(plan.forward(T(v0), store=False)[0])
+        torch.cuda.synchronize()
+        plan.check()
+    data_err = rel_l2(d_syn[0], O.forward(op, v0)[0])
+    assert data_err <= TOL_DATA
+    ow2 = O.W2Params()
+    octx = O.w2_prepare(d_o, op.dt, ow2)
+    J_o, g_o, _ = O.gradient(op, v0, octx, ow2)
+    assert abs(float(J[0]) - J_o[0]) <= TOL_J * 10 * abs(J_o[0]), (float(J[0]), J_o[0])
+    spread = _oracle_envelope(op, v0[0], octx, ow2, g_o[0], data_err, seeds=(1,))
+    err = rel_l2(H(g)[0], g_o[0])
+    assert err <= max(ENVELOPE * spread, TOL_GRAD), (err, spread, data_err)

@@ -436,8 +436,10 @@ FWI_API fwi_status fwi_group_gradient(fwi_group *group, const float *const *v,
  * tail of one plan.  Results are bitwise those of fwi_forward /
  * fwi_adjoint_grad on each plan.
  *   plans     store-all plans (checkpoint_every 0) of the resident column-pair
- *             kernels (padded NZ <= 110 and an even padded width <= 156), one
- *             top_bc; others fail with FWI_ERR_UNSUPPORTED
+ *             kernels (padded NZ <= 110 and an even padded width <= 156) with one
+ *             physics: the same dx, dz, dt, nb, top_bc, v_ref, refl_R, f_peak and
+ *             t0 (grids, batches, shots and receivers may differ); others fail
+ *             with FWI_ERR_UNSUPPORTED
  *   lists     one entry per plan, with the layout of the single-plan call
  *   counter   one int of device memory, owned by the caller; the call zeroes it
  *             on the stream before the launch (no allocation)

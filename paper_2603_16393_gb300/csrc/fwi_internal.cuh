@@ -160,6 +160,9 @@ __global__ void k_shot_sum(int B, int ns, int n, const float *__restrict__ gshot
 // Whether a plan can take part in a persistent launch (store-all resident
 // column-pair plans of the 110-row bucket)
 bool queue_ok(const Plan &pl);
+// Whether two plans share spacing, time step, layer, top boundary and source
+// (a persistent launch takes its time-loop coefficients from its first plan)
+bool queue_same_physics(const Plan &a, const Plan &b);
 // One persistent launch of the forward (adj false; a[i] with v, d_syn, snap,
 // status set) or adjoint (adj true; v, adj, snap, gshot, status set) of the
 // plans, on at most one CTA per SM; *counter is zeroed first

@@ -277,7 +277,7 @@ __device__ __forceinline__ void fwd_rows_pair(const float *__restrict__ cp, floa
 // column-pair kernel (k_fwd_pair runs one unit a CTA, k_fwd_pair_queue draws
 // units of several plans from a counter)
 template <int P, int PR, int NZM, int TOPBC, bool STORE>
-__device__ __forceinline__ void fwd_pair_unit(const PropArgs &a, const int bs)
+__device__ __forceinline__ void fwd_pair_unit(const PropArgs &a, const PropArgs &c, const int bs)
 {
     extern __shared__ __align__(16) float sm[];
     constexpr int FSZ = (NZM + 4) * P;
@@ -382,7 +382,7 @@ __device__ __forceinline__ void fwd_pair_unit(const PropArgs &a, const int bs)
                 const float *cp = cur + (z0 + 2) * P + x + 2;
                 float *np = nxt + (z0 + 2) * P + x + 2;
                 fwd_rows_pair<P, PR, TOPBC, STORE>(cp, np, ABt + z0 * P + x, sw, top_strip, ka,
-                                                   vi, a);
+                                                   vi, c);
                 if (src_k >= 0) {
                     // point source: + kappa A s at the source cell (increment and field)
                     float kas = 0.f;
@@ -391,7 +391,7 @@ __device__ __forceinline__ void fwd_pair_unit(const PropArgs &a, const int bs)
                         if (2 * k == src_k) kas = ka[k].x;
                         if (2 * k + 1 == src_k) kas = ka[k].y;
                     }
-                    const float d = kas * ricker_scaled(j, a);
+                    const float d = kas * ricker_scaled(j, c);
 #pragma unroll
                     for (int k = 0; k < ROWS2; ++k) {
                         if (2 * k == src_k) vi[k].x += d;
@@ -422,12 +422,15 @@ template <int P, int PR, int NZM, int TOPBC, bool STORE>
 __global__ void __launch_bounds__(kMaxThreadsAdj, 1)
 k_fwd_pair(const __grid_constant__ PropArgs a)
 {
-    fwd_pair_unit<P, PR, NZM, TOPBC, STORE>(a, blockIdx.x);
+    fwd_pair_unit<P, PR, NZM, TOPBC, STORE>(a, a, blockIdx.x);
 }
 
 // Persistent: every CTA draws units (plan p, unit bs) from the counter until
 // all q.total are taken; units are numbered plan by plan (q.start), the
-// caller orders the plans largest first
+// caller orders the plans largest first.  The plans share their physics
+// (spacing, time step, layer, source), so the time loop takes its
+// coefficients from plan 0 (constant-bank operands, as in k_fwd_pair) and
+// only the geometry and pointers from the unit's plan.
 template <int P, int PR, int NZM, int TOPBC, bool STORE>
 __global__ void __launch_bounds__(kMaxThreadsAdj, 1)
 k_fwd_pair_queue(const __grid_constant__ QueueArgs q)
@@ -441,7 +444,7 @@ k_fwd_pair_queue(const __grid_constant__ QueueArgs q)
         if (u >= q.total) return;
         int p = 0;
         while (p + 1 < q.n && u >= q.start[p + 1]) ++p;
-        fwd_pair_unit<P, PR, NZM, TOPBC, STORE>(q.a[p], u - q.start[p]);
+        fwd_pair_unit<P, PR, NZM, TOPBC, STORE>(q.a[p], q.a[0], u - q.start[p]);
         __syncthreads();   // shared memory is reset by the next unit
     }
 }
@@ -793,7 +796,7 @@ __device__ __forceinline__ void adj_rows_pair(const float *__restrict__ cp,
 // allocation of kAdjTmemCols columns (k_adj_pair allocates it for its one
 // unit, k_adj_pair_queue once for all the units it draws)
 template <int P, int PR, int NZM, int TOPBC>
-__device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const int bs,
+__device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const PropArgs &c, const int bs,
                                               const uint32_t tmem)
 {
     extern __shared__ __align__(16) float sm[];
@@ -909,7 +912,7 @@ __device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const int bs,
             const int i = e / nch, jj = e - (e / nch) * nch;
             ST[jj * a.nr + i] = IC[i] * ab[(size_t)i * a.nt + (a.nt - 1 - (j0 + jj))];
         }
-        for (int e = tid; e < nch; e += nth) RS[e] = ricker_scaled(a.nt - 1 - (j0 + e), a);
+        for (int e = tid; e < nch; e += nth) RS[e] = ricker_scaled(a.nt - 1 - (j0 + e), c);
         __syncthreads();
         for (int jj = 0; jj < nch; ++jj) {
             const int j = j0 + jj;
@@ -923,7 +926,7 @@ __device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const int bs,
             adj_rows_pair<P, PR, TOPBC>(cur + (z0 + 2) * P + x + 2, nxt + (z0 + 2) * P + x + 2,
                                         sr, sr_next, opaque(zbf),
                                         make_float2(opaque(ex.x), opaque(ex.y)), top_strip,
-                                        active, tacc, tka, rq, a);
+                                        active, tacc, tka, rq, c);
             tmem_wait_st();
             sr = sr_next;
             __syncthreads();
@@ -1043,7 +1046,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_con
 {
     __shared__ uint32_t tmem_slot;
     const uint32_t tmem = adj_tmem_alloc(&tmem_slot);
-    adj_pair_unit<P, PR, NZM, TOPBC>(a, blockIdx.x, tmem);
+    adj_pair_unit<P, PR, NZM, TOPBC>(a, a, blockIdx.x, tmem);
     adj_tmem_free(tmem);
 }
 
@@ -1064,7 +1067,7 @@ k_adj_pair_queue(const __grid_constant__ QueueArgs q)
         if (u >= q.total) break;
         int p = 0;
         while (p + 1 < q.n && u >= q.start[p + 1]) ++p;
-        adj_pair_unit<P, PR, NZM, TOPBC>(q.a[p], u - q.start[p], tmem);
+        adj_pair_unit<P, PR, NZM, TOPBC>(q.a[p], q.a[0], u - q.start[p], tmem);
         __syncthreads();
     }
     adj_tmem_free(tmem);
@@ -1128,6 +1131,13 @@ int fast_chunk(int P, int NZM, bool adj, int nr)
     return c > 32 ? 32 : (int)c;
 }
 
+bool queue_same_physics(const Plan &a, const Plan &b)
+{
+    const fwi_problem &p = a.p, &q = b.p;
+    return p.dx == q.dx && p.dz == q.dz && p.dt == q.dt && p.nb == q.nb && p.top_bc == q.top_bc &&
+           p.v_ref == q.v_ref && p.refl_R == q.refl_R && p.f_peak == q.f_peak && a.t0 == b.t0;
+}
+
 bool queue_ok(const Plan &pl)
 {
     return pl.fast && pl.fwd_pair && pl.adj_pair && pl.fast_NZM == 110 && pl.ckpt_every == 0 &&
@@ -1145,7 +1155,7 @@ cudaError_t launch_fast_queue(const Plan *const *plans, int n, bool adj, const P
     const int tb = plans[0]->p.top_bc;
     for (int i = 0; i < n; ++i) {
         const Plan &pl = *plans[i];
-        if (!queue_ok(pl) || pl.p.top_bc != tb) return cudaErrorInvalidValue;
+        if (!queue_ok(pl) || !queue_same_physics(pl, *plans[0])) return cudaErrorInvalidValue;
         const ResidentShape &sh = adj ? pl.shape_adj : pl.shape;
         q.start[i] = q.total;
         q.total += pl.p.batch * pl.p.ns;

@@ -31,8 +31,11 @@ fwi_status check_plans(const fwi_plan *const *plans, int n, const void *const *l
                                      "column-pair kernels (padded grid NZ <= 110, even NX <= 156)",
                                      what, i);
         const fwi::Plan &p0 = *reinterpret_cast<const fwi::Plan *>(plans[0]);
-        if (pl.p.top_bc != p0.p.top_bc)
-            return fwi::record_error(FWI_ERR_UNSUPPORTED, "%s: plans differ in top_bc", what);
+        if (!fwi::queue_same_physics(pl, p0))
+            return fwi::record_error(FWI_ERR_UNSUPPORTED,
+                                     "%s: plan %d differs from plan 0 in dx, dz, dt, nb, top_bc, "
+                                     "v_ref, refl_R or the source wavelet",
+                                     what, i);
     }
     return FWI_OK;
 }

@@ -330,6 +330,10 @@ def test_queue_rejects_plans_outside_the_column_pair_kernels(api):
         rc = api._lib.fwi_queue_forward(plans, 2, dummy, dummy, dummy, dummy, cnt, None)
         assert rc == api.FWI_ERR_UNSUPPORTED
         assert "column-pair" in api.fwi_last_error()
+    other = api.fwi_plan_create(_prob(api, nb=20), api.W2Params())     # another layer width
+    plans = (vp * 2)(ok.raw, other.raw)
+    assert api._lib.fwi_queue_forward(plans, 2, dummy, dummy, dummy, dummy, cnt, None) == \
+        api.FWI_ERR_UNSUPPORTED
     plans = (vp * 5)(*([ok.raw] * 5))
     assert api._lib.fwi_queue_forward(plans, 5, dummy, dummy, dummy, dummy, cnt, None) == \
         api.FWI_ERR_INVALID_ARG

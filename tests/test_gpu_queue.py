@@ -12,10 +12,10 @@ pytestmark = pytest.mark.gpu
 from gpu_cases import initial, models, problems  # noqa: E402
 
 DEV = "cuda:0"
-SIZES = [  # nz, nx, nb, ns, batch -- largest first
+SIZES = [  # nz, nx, nb, ns, batch -- largest first; one physics (dx, dt, nb, source)
     (70, 70, 40, 5, 3),
-    (60, 50, 20, 2, 4),
-    (40, 90, 20, 3, 2),
+    (60, 50, 40, 2, 4),
+    (40, 70, 40, 3, 2),
 ]
 
 

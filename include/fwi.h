@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 10800  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 10900  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -846,6 +846,16 @@ FWI_API fwi_status fwi_sur_weights_prep(int cout, int cin, const float *W3, void
  * from a 3 x 3 weight gradient dW [cout][3][3][cin] (fp32). */
 FWI_API fwi_status fwi_sur_wgrad_centre(int cout, int cin, const float *dW, float *dW3,
                                         void *stream);
+
+/* The FD solver as judge of a surrogate's guidance gradient (Sec. 7's
+ * surrogate route, gated per noise level of Algorithm 2): per model b,
+ *   err[b] = ||g_b - g_ref_b||_2 / ||g_ref_b||_2
+ * over the n floats of model b (g, g_ref [nmod][n] fp32, device; err [nmod]
+ * fp32, device).  Sums in double in a fixed order (one CTA a model): a second
+ * call gives the same bits.  A zero reference gives 0 if g_b is zero too,
+ * else +inf.  nmod, n >= 1 and non-NULL pointers, else FWI_ERR_INVALID_ARG. */
+FWI_API fwi_status fwi_rel_error(int nmod, long long n, const float *g, const float *g_ref,
+                                 float *err, void *stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 FWI_API const char *fwi_last_error(void);

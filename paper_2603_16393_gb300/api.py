@@ -220,6 +220,8 @@ _lib.fwi_sur_weights_prep.restype = _S
 _lib.fwi_sur_weights_prep.argtypes = [_i, _i] + [_vp] * 4
 _lib.fwi_sur_wgrad_centre.restype = _S
 _lib.fwi_sur_wgrad_centre.argtypes = [_i, _i] + [_vp] * 3
+_lib.fwi_rel_error.restype = _S
+_lib.fwi_rel_error.argtypes = [_i, ctypes.c_longlong] + [_vp] * 4
 _lib.fwi_channel_sum.restype = _S
 _lib.fwi_channel_sum.argtypes = [ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp, ctypes.c_longlong,
                                  _vp]
@@ -911,6 +913,19 @@ def fwi_sur_wgrad_centre(dW, dW3, stream=None):
     _f32(dW, (cout, 3, 3, cin), "dW")
     _f32(dW3, (cout, 3, cin), "dW3")
     _check(_lib.fwi_sur_wgrad_centre(cout, cin, _ptr(dW), _ptr(dW3), _stream(stream)))
+
+
+def fwi_rel_error(g, g_ref, err=None, stream=None):
+    """err [B] = ||g_b - g_ref_b|| / ||g_ref_b|| per model of g, g_ref [B][...] (fp32,
+    device); a zero reference gives 0 for a zero g_b, else inf."""
+    B = g.shape[0]
+    _f32(g_ref, tuple(g.shape), "g_ref")
+    _f32(g, tuple(g.shape), "g")
+    if err is None:
+        err = torch.empty((B,), dtype=torch.float32, device=g.device)
+    _f32(err, (B,), "err")
+    _check(_lib.fwi_rel_error(B, g[0].numel(), _ptr(g), _ptr(g_ref), _ptr(err), _stream(stream)))
+    return err
 
 
 def fwi_channel_sum(dP, db, work=None, stream=None):

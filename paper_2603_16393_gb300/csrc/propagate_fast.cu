@@ -695,11 +695,14 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
 // of its columns (one per column and strip).
 //
 // Registers bound this kernel (unconstrained it wants 140 a thread, and 768
-// threads get 80), so two per-cell arrays live in tensor memory instead: the
-// imaging sums (read, updated and written back per row) and kappa A (read per
-// row), each thread in its own TMEM lane -- warp w owns lanes 32 (w mod 4) ..
-// + 31, the warps of one lane quarter take 44 columns each (22 of sums, 22 of
-// kappa A).  The kappa A table in shared memory is read only at set-up.
+// threads get 80), so the per-cell arrays live in tensor memory instead: the
+// imaging sums (read, updated and written back per row) and, side by side,
+// kappa A and the damping factor 2A = 2 / (1 + e) (one 4-column read per
+// row, which replaces the per-row damping arithmetic: two approximate
+// divisions and the layer profile), each thread in its own TMEM lane -- warp
+// w owns lanes 32 (w mod 4) .. + 31, the warps of one lane quarter take 68
+// columns each (24 of sums, 44 of kappa A and 2A).  The kappa A table in
+// shared memory is read only at set-up.
 //
 // Record reads: a whole record plane is prefetched into L2 two steps before
 // it is used (one bulk prefetch per step, in 4 KB pieces), and each thread
@@ -707,7 +710,9 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_fast(const __grid_con
 // row r is updated).  KR = 6 measured fastest once the sums and kappa A left
 // the registers (13.6 ms at 152 models; 4 rows: 14.5 ms).
 constexpr int KR = 6;
-constexpr int kAdjTmemCols = 512;   // 6 warps per lane quarter x 44 columns, rounded up
+constexpr int kAdjSumCols = 24;     // a warp's imaging sums: 2 x 11 rows, padded to 4
+constexpr int kAdjWarpCols = kAdjSumCols + 4 * ROWS2;   // + (kappa A, 2A) of two cells a row
+constexpr int kAdjTmemCols = 512;   // 6 warps per lane quarter x 68 columns, rounded up
 
 // L2 prefetch of a record plane (16-byte aligned, size a multiple of 16) in
 // 4 KB pieces, one piece per thread of the first warps
@@ -730,6 +735,20 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t &a, uint32_t &
                  : "=r"(a), "=r"(b)
                  : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t &a, uint32_t &b, uint32_t &c,
+                                         uint32_t &d)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, float2 u, float2 v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+                 "r"(__float_as_uint(u.x)), "r"(__float_as_uint(u.y)), "r"(__float_as_uint(v.x)),
+                 "r"(__float_as_uint(v.y))
+                 : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v)
 {
@@ -743,10 +762,9 @@ template <int P, int PR, int TOPBC>
 __device__ __forceinline__ void adj_rows_pair(const float *__restrict__ cp,
                                               float *__restrict__ np,
                                               const float *__restrict__ sr,
-                                              const float *__restrict__ sr_next, float zbf,
-                                              float2 ex, bool top_strip, bool active,
-                                              uint32_t tacc, uint32_t tka, float2 (&rq)[KR],
-                                              const PropArgs &a)
+                                              const float *__restrict__ sr_next,
+                                              bool top_strip, bool active, uint32_t tacc,
+                                              uint32_t tkd, float2 (&rq)[KR], const PropArgs &a)
 {
     using namespace f2;
     const float2 &C0 = a.w2[0], &CX1 = a.w2[1], &CX2 = a.w2[2], &CZ1 = a.w2[3], &CZ2 = a.w2[4];
@@ -767,16 +785,14 @@ __device__ __forceinline__ void adj_rows_pair(const float *__restrict__ cp,
             if (top_strip) lap = (r == 1) ? add(lap, fma(CZ2, w0, mul(CZ1, wm1)))
                                           : fma(CZ2, wm2, lap);
         }
-        const float ez = ez_of(zbf + (float)r, a);
-        const float2 h = add(splat(1.f), add(ex, splat(ez)));          // 1 + e
-        const float2 A2 = make_float2(__fdividef(2.f, h.x), __fdividef(2.f, h.y));   // 2A
-        const float2 nAB = fma(A2, splat(-1.f), splat(1.f));            // -A B = 1 - 2A
-        uint32_t s0, s1, k0, k1;
+        uint32_t s0, s1, k0, k1, d0, d1;
         tmem_ld2(tacc + 2 * r, s0, s1);
-        tmem_ld2(tka + 2 * r, k0, k1);
+        tmem_ld4(tkd + 4 * r, k0, k1, d0, d1);
         const float2 fo = ld(np + r * P);
         tmem_wait_ld();
         const float2 kA = make_float2(__uint_as_float(k0), __uint_as_float(k1));
+        const float2 A2 = make_float2(__uint_as_float(d0), __uint_as_float(d1));   // 2A
+        const float2 nAB = fma(A2, splat(-1.f), splat(1.f));            // -A B = 1 - 2A
         const float2 fn = fma(kA, lap, fma(A2, w0, mul(nAB, fo)));
         if (active) st(np + r * P, fn);
         tmem_st2(tacc + 2 * r,
@@ -803,7 +819,7 @@ __device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const PropArgs 
     constexpr int FSZ = (NZM + 4) * P;
     static_assert(P % 2 == 0 && PR % 4 == 0 && FSZ % 2 == 0,
                   "float2 rows need even pitches; record planes are prefetched in 16-byte units");
-    static_assert(2 * ROWS2 * 2 * (kMaxThreadsAdj / 128) <= kAdjTmemCols,
+    static_assert(kAdjWarpCols * (kMaxThreadsAdj / 128) <= kAdjTmemCols,
                   "the lane quarters' columns must fit the allocation");
     float *U0 = sm, *U1 = sm + FSZ, *K = sm + 2 * FSZ, *IC = K + NZM * P, *ST = IC + a.nr;
     float *RS = ST + a.chunk * a.nr;
@@ -844,8 +860,6 @@ __device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const PropArgs 
     const bool active = strip < a.nstrip;
     const int x = active ? 2 * (tid % NXP) : 0;
     const int z0 = active ? strip * ROWS2 : 0;
-    const float2 ex = make_float2(ex_of(x, a), ex_of(x + 1, a));
-    const float zbf = (float)(z0 - (a.nz - 1));
     const bool top_strip = active && z0 == 0;
 
     // receivers owned by this thread (one per column at most)
@@ -863,8 +877,8 @@ __device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const PropArgs 
     if (tid == 0) acc_src = 0.f;
     const int warp = tid >> 5;
     const uint32_t tacc = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
-                          (uint32_t)(4 * ROWS2 * (warp >> 2));
-    const uint32_t tka = tacc + 2 * ROWS2;
+                          (uint32_t)(kAdjWarpCols * (warp >> 2));
+    const uint32_t tkd = tacc + kAdjSumCols;
 
     const size_t plane = (size_t)a.nzs * PR;
     const int jb = a.j_begin;
@@ -884,7 +898,12 @@ __device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const PropArgs 
             acc0 = f2::ld(a.astate + (size_t)bs * 3 * cells + 2 * cells + z * NX + x);
         }
         tmem_st2(tacc + 2 * r, acc0);
-        tmem_st2(tka + 2 * r, f2::ld(K + z * P + x));
+        // 2A = 2 / (1 + e) of the two cells, e = e_x + e_z (side and bottom layer)
+        const float ez = ez_of((float)(z0 - (a.nz - 1)) + (float)r, c);
+        const float2 h = f2::add(f2::splat(1.f),
+                                 f2::add(make_float2(ex_of(x, a), ex_of(x + 1, a)), f2::splat(ez)));
+        tmem_st4(tkd + 4 * r, f2::ld(K + z * P + x),
+                 make_float2(__fdividef(2.f, h.x), __fdividef(2.f, h.y)));
     }
     tmem_wait_st();
     float2 rq[KR];
@@ -924,9 +943,7 @@ __device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const PropArgs 
                 prefetch_plane_l2(plane_jb - (size_t)(j - jb + 2) * plane, plane * 4, tid);
             const float *sr_next = (j + 1 < a.j_end) ? sr - plane : sr;
             adj_rows_pair<P, PR, TOPBC>(cur + (z0 + 2) * P + x + 2, nxt + (z0 + 2) * P + x + 2,
-                                        sr, sr_next, opaque(zbf),
-                                        make_float2(opaque(ex.x), opaque(ex.y)), top_strip,
-                                        active, tacc, tka, rq, c);
+                                        sr, sr_next, top_strip, active, tacc, tkd, rq, c);
             tmem_wait_st();
             sr = sr_next;
             __syncthreads();

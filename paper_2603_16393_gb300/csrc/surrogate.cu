@@ -29,6 +29,9 @@
 //            transpose W^T[ci][ky][kx][co] = W[co][2-ky][2-kx][ci], from the
 //            three-tap float32 weights W3[co][ky][ci]
 //   k_wcentre dW3[co][ky][ci] = dW[co][ky][1][ci] (the taps the network has)
+//   k_rel_err err[b] = ||g_b - r_b|| / ||r_b|| per model (the FD judge's
+//            measure of the surrogate's gradient), sums in double, one CTA a
+//            model, a fixed order
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -299,6 +302,35 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+__global__ void __launch_bounds__(kThreads)
+    k_rel_err(size_t n, const float *__restrict__ g, const float *__restrict__ r,
+              float *__restrict__ err)
+{
+    __shared__ double rn[kThreads], rd[kThreads];
+    const size_t off = (size_t)blockIdx.x * n;
+    double num = 0.0, den = 0.0;
+    for (size_t i = threadIdx.x; i < n; i += kThreads) {
+        const double ri = (double)r[off + i];
+        const double d = (double)g[off + i] - ri;
+        num += d * d;
+        den += ri * ri;
+    }
+    rn[threadIdx.x] = num;
+    rd[threadIdx.x] = den;
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            rn[threadIdx.x] += rn[threadIdx.x + s];
+            rd[threadIdx.x] += rd[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double a = rn[0], b = rd[0];
+        err[blockIdx.x] = b > 0.0 ? (float)sqrt(a / b) : (a > 0.0 ? INFINITY : 0.f);
+    }
+}
+
 fwi_status launch_check(const char *what)
 {
     const cudaError_t e = cudaGetLastError();
@@ -450,6 +482,16 @@ fwi_status fwi_sur_wgrad_centre(int cout, int cin, const float *dW, float *dW3, 
     const size_t n = (size_t)cout * 3 * cin;
     k_wcentre<<<grid_for(n), kThreads, 0, (cudaStream_t)stream>>>(cout, cin, dW, dW3);
     return launch_check("fwi_sur_wgrad_centre");
+}
+
+fwi_status fwi_rel_error(int nmod, long long n, const float *g, const float *g_ref, float *err,
+                         void *stream)
+{
+    if (nmod < 1 || n < 1) return fwi::record_error(FWI_ERR_INVALID_ARG, "nmod, n >= 1");
+    if (!g || !g_ref || !err)
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "g, g_ref and err must not be NULL");
+    k_rel_err<<<(unsigned)nmod, kThreads, 0, (cudaStream_t)stream>>>((size_t)n, g, g_ref, err);
+    return launch_check("fwi_rel_error");
 }
 
 }  // extern "C"

@@ -275,9 +275,7 @@ class GraphChain:
             _, g_phys, _ = self.plan.gradient(self.v_phys, self.ctx, stream=stream)
             if kind == "check":
                 _, g_sur = self.surrogate.gradient(self.v_phys, stream=stream)
-                num = (g_sur - g_phys).reshape(B, -1).norm(dim=1)
-                den = g_phys.reshape(B, -1).norm(dim=1).clamp_min(1e-30)
-                self.err.copy_(num / den)
+                api.fwi_rel_error(g_sur, g_phys, self.err, stream)
         api.fwi_ddpm_guidance_at(B, n, self.table, self.step, N, self.v0hat, g_phys, None,
                                  self.prior.tau2, self.g, self.h, stream)
         api.guided_step(self.v_prime, self.v0hat, self.g, self.h, self.gparams, v_out=self.v,

@@ -339,13 +339,10 @@ class SurrogateGuidance:
         return J, self.net.vjp(adj, stream=stream)
 
 
-def rel_error(g: torch.Tensor, g_ref: torch.Tensor) -> torch.Tensor:
-    """Per-model relative L2 error ||g - g_ref|| / ||g_ref|| [nmod] (torch
-    reductions on the device; a diagnostic, not a step of the path)."""
-    B = g.shape[0]
-    num = (g - g_ref).reshape(B, -1).norm(dim=1)
-    den = g_ref.reshape(B, -1).norm(dim=1).clamp_min(1e-30)
-    return num / den
+def rel_error(g: torch.Tensor, g_ref: torch.Tensor, stream=None) -> torch.Tensor:
+    """Per-model relative L2 error ||g - g_ref|| / ||g_ref|| [nmod] (fwi_rel_error:
+    the FD judge's measure)."""
+    return api.fwi_rel_error(g.contiguous(), g_ref.contiguous(), stream=stream)
 
 
 @dataclasses.dataclass
@@ -364,8 +361,9 @@ class GatedSurrogate:
     gradient it has and the steps until the next check use the surrogate."""
 
     def __init__(self, surrogate: SurrogateGuidance, threshold: float = 0.05,
-                 check_every: int = 10):
+                 check_every: int = 10, measure=rel_error):
         self.sur, self.threshold, self.check_every = surrogate, float(threshold), int(check_every)
+        self.measure = measure          # per-model relative error (fwi_rel_error)
         self.plan, self.ctx = surrogate.plan, surrogate.ctx
         self.records: list[GateRecord] = []
         self.rejected = False
@@ -381,7 +379,7 @@ class GatedSurrogate:
             J, g_fd, _ = self.plan.gradient(v_phys, self.ctx, stream=stream)
             g_fd = g_fd.clone()
             _, g_sur = self.sur.gradient(v_phys, stream=stream)
-            err = float(rel_error(g_sur, g_fd).max())
+            err = float(self.measure(g_sur, g_fd).max())
             ok = err <= self.threshold
             self.records.append(GateRecord(step, err, ok))
             self.rejected = not ok

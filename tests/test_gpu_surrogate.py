@@ -178,3 +178,22 @@ def test_production_sizes_sampled_models(mods):
     g_o = ref.vjp(adj[pick].astype(np.float64))
     assert rel_l2(H(d)[pick], d_o) <= 8 * BF16_ULP
     assert rel_l2(H(g)[pick], g_o) <= 8 * BF16_ULP
+
+
+def test_relative_error_per_model(mods):
+    # the FD judge's measure: ||g_b - r_b|| / ||r_b|| per model, FP64 sums
+    A, _ = mods
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal((5, 70, 70)).astype(np.float32) * 1e-7
+    g = r * (1.0 + rng.standard_normal(r.shape).astype(np.float32) * 0.3)
+    r[3] = 0.0                       # zero reference: inf for a nonzero g ...
+    g[4] = 0.0
+    r[4] = 0.0                       # ... and 0 when both are zero
+    e = A.fwi_rel_error(F(g), F(r))
+    e2 = A.fwi_rel_error(F(g), F(r))
+    torch.cuda.synchronize()
+    gd, rd = g.astype(np.float64), r.astype(np.float64)
+    ref = [np.linalg.norm(gd[b] - rd[b]) / np.linalg.norm(rd[b]) for b in range(3)]
+    np.testing.assert_allclose(H(e)[:3], ref, rtol=1e-6)
+    assert np.isinf(H(e)[3]) and H(e)[4] == 0.0
+    assert torch.equal(e, e2)

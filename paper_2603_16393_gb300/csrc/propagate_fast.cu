@@ -109,7 +109,6 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
     const float *vb = a.v + (size_t)b * a.nz * a.nx;
     const int ixc = min(max(x - a.nb, 0), a.nx - 1);
     const float ex = ex_of(x, a);
-    const float zbf = (float)(z0 - (a.nz - 1));
     float ka[ROWS], vi[ROWS];
     int bad = 0;
 #pragma unroll
@@ -231,7 +230,7 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
 // bitwise those of the scalar code).  Needs an even padded width.
 constexpr int ROWS2 = kFastRows / 2;
 
-template <int P, int PR, int TOPBC, bool STORE>
+template <int P, int PR, int TOPBC, bool STORE, bool AHEAD>
 __device__ __forceinline__ void fwd_rows_pair(const float *__restrict__ cp, float *__restrict__ np,
                                               const float *__restrict__ abp,
                                               float *__restrict__ sw, bool top_strip,
@@ -241,12 +240,25 @@ __device__ __forceinline__ void fwd_rows_pair(const float *__restrict__ cp, floa
     using namespace f2;
     const float2 CX1 = splat(a.cx1), CX2 = splat(a.cx2), CZ1 = splat(a.cz1), CZ2 = splat(a.cz2);
     float2 wm2 = ld(cp - 2 * P), wm1 = ld(cp - P), w0 = ld(cp), wp1 = ld(cp + P);
+    // AHEAD: the shared-memory operands of row r + 1 are loaded while row r
+    // is updated (a row's arithmetic is a chain of dependent packed
+    // operations); the queue kernel, whose plan-indexed arguments hold more
+    // registers, loads each row's operands in its own iteration
+    float2 nwp2 = {}, nL = {}, nR = {}, nab = {};
+    if (AHEAD) nwp2 = ld(cp + 2 * P), nL = ld(cp - 2), nR = ld(cp + 2), nab = ld(abp);
 #pragma unroll
     for (int r = 0; r < ROWS2; ++r) {
         const float *c = cp + r * P;
-        const float2 wp2 = ld(c + 2 * P);
-        const float2 L = ld(c - 2);     // u[x-2], u[x-1]
-        const float2 R = ld(c + 2);     // u[x+2], u[x+3]
+        const float2 wp2 = AHEAD ? nwp2 : ld(c + 2 * P);
+        const float2 L = AHEAD ? nL : ld(c - 2);     // u[x-2], u[x-1]
+        const float2 R = AHEAD ? nR : ld(c + 2);     // u[x+2], u[x+3]
+        const float2 ab_ahead = nab;
+        if (AHEAD && r + 1 < ROWS2) {
+            nwp2 = ld(c + 3 * P);
+            nL = ld(c + P - 2);
+            nR = ld(c + P + 2);
+            nab = ld(abp + (r + 1) * P);
+        }
         // x, first neighbours: (u[x-1] - u[x]) + (u[x+1] - u[x]) per column
         const float d01 = w0.y - w0.x;
         const float2 dxA = make_float2((L.y - w0.x) + d01, (R.x - w0.y) - d01);
@@ -258,7 +270,7 @@ __device__ __forceinline__ void fwd_rows_pair(const float *__restrict__ cp, floa
         lap = fma(CX2, dxB, lap);
         lap = fma(CZ1, dzA, lap);
         lap = fma(CZ2, dzB, lap);
-        const float2 ab = ld(abp + r * P);
+        const float2 ab = AHEAD ? ab_ahead : ld(abp + r * P);
         vi[r] = fma(ka[r], lap, mul(ab, vi[r]));
         const float2 un = add(w0, vi[r]);
         st(np + r * P, un);
@@ -276,7 +288,7 @@ __device__ __forceinline__ void fwd_rows_pair(const float *__restrict__ cp, floa
 // One (model, shot) unit bs of a plan: the whole forward time loop of the
 // column-pair kernel (k_fwd_pair runs one unit a CTA, k_fwd_pair_queue draws
 // units of several plans from a counter)
-template <int P, int PR, int NZM, int TOPBC, bool STORE>
+template <int P, int PR, int NZM, int TOPBC, bool STORE, bool AHEAD>
 __device__ __forceinline__ void fwd_pair_unit(const PropArgs &a, const PropArgs &c, const int bs)
 {
     extern __shared__ __align__(16) float sm[];
@@ -381,8 +393,8 @@ __device__ __forceinline__ void fwd_pair_unit(const PropArgs &a, const PropArgs 
             if (active) {
                 const float *cp = cur + (z0 + 2) * P + x + 2;
                 float *np = nxt + (z0 + 2) * P + x + 2;
-                fwd_rows_pair<P, PR, TOPBC, STORE>(cp, np, ABt + z0 * P + x, sw, top_strip, ka,
-                                                   vi, c);
+                fwd_rows_pair<P, PR, TOPBC, STORE, AHEAD>(cp, np, ABt + z0 * P + x, sw, top_strip,
+                                                          ka, vi, c);
                 if (src_k >= 0) {
                     // point source: + kappa A s at the source cell (increment and field)
                     float kas = 0.f;
@@ -422,7 +434,7 @@ template <int P, int PR, int NZM, int TOPBC, bool STORE>
 __global__ void __launch_bounds__(kMaxThreadsAdj, 1)
 k_fwd_pair(const __grid_constant__ PropArgs a)
 {
-    fwd_pair_unit<P, PR, NZM, TOPBC, STORE>(a, a, blockIdx.x);
+    fwd_pair_unit<P, PR, NZM, TOPBC, STORE, true>(a, a, blockIdx.x);
 }
 
 // Persistent: every CTA draws units (plan p, unit bs) from the counter until
@@ -444,7 +456,7 @@ k_fwd_pair_queue(const __grid_constant__ QueueArgs q)
         if (u >= q.total) return;
         int p = 0;
         while (p + 1 < q.n && u >= q.start[p + 1]) ++p;
-        fwd_pair_unit<P, PR, NZM, TOPBC, STORE>(q.a[p], q.a[0], u - q.start[p]);
+        fwd_pair_unit<P, PR, NZM, TOPBC, STORE, false>(q.a[p], q.a[0], u - q.start[p]);
         __syncthreads();   // shared memory is reset by the next unit
     }
 }

@@ -2,7 +2,7 @@
 
   * 64 curved/faulted 70 x 70 models, 5 shots, 1000 steps, observed data with
     10 dB SNR Gaussian noise (sigma^2 = mean(d^2) / 10 per instance);
-  * 8 models of 256 x 256, 16 shots, 2000 steps (tiled kernels);
+  * 8 models of 256 x 256, 16 shots, 2000 steps (cluster kernels);
   * 2 models of 512 x 1024 (depth x width), 32 shots, 4000 steps, with
     checkpoints every 32 steps (the whole wavefield record would need 624 GB).
 

@@ -90,7 +90,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (!(w2->eps_density >= 0.0) || !std::isfinite(w2->eps_density))
         return fail(FWI_ERR_INVALID_ARG, "eps_density must be >= 0");
     if (w2->squared != 0 && w2->squared != 1) return fail(FWI_ERR_INVALID_ARG, "squared must be 0 or 1");
-    if (p.shape < FWI_SHAPE_DEFAULT || p.shape > FWI_SHAPE_TILED_ROWS4)
+    if (p.shape < FWI_SHAPE_DEFAULT || p.shape > FWI_SHAPE_CLUSTER_PAIRS)
         return fail(FWI_ERR_INVALID_ARG, "shape %d is not an FWI_SHAPE_* value", p.shape);
     if (p.kernels < FWI_KERNELS_AUTO || p.kernels > FWI_KERNELS_CPML)
         return fail(FWI_ERR_INVALID_ARG, "kernels must be 0 (auto), 1, 2, 3 or 4");
@@ -256,55 +256,58 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (pl->tiled && (fam == FWI_KERNELS_AUTO || fam == FWI_KERNELS_CLUSTER) && order == 4 &&
         p.checkpoint_every == 0 && pl->NX + 4 <= fwi::kCluPitch) {
         // rows per thread strip RS (a compile-time bucket), strips per column,
-        // rows per CTA RC = nstrip RS and CTAs per cluster C = ceil(NZ / RC)
-        const int P = fwi::kCluPitch;
+        // rows per CTA RC = nstrip RS and CTAs per cluster C = ceil(NZ / RC).
+        // Column pairs (even padded width) first, then single columns of 13 or
+        // 19 rows, as far as the requested shape allows.
         const int rc0 = (pl->NZ + fwi::kClusterCTAs - 1) / fwi::kClusterCTAs;
-        static const int rs_buckets[] = {13, 19};
-        int RS = 0, nstrip = 0, threads = 0;
-        for (int rs : rs_buckets) {
-            if ((p.shape == FWI_SHAPE_CLUSTER_RS13 && rs != 13) ||
-                (p.shape == FWI_SHAPE_CLUSTER_RS19 && rs != 19))
-                continue;
-            const int ns_ = (rc0 + rs - 1) / rs;
-            const int th = (pl->NX * ns_ + 31) / 32 * 32;
-            if (th <= fwi::clu_max_threads(rs)) {
-                RS = rs;
-                nstrip = ns_;
-                threads = th;
-                break;
-            }
-        }
-        const int RC = nstrip * RS;
-        const int C = RC > 0 ? (pl->NZ + RC - 1) / RC : 0;
-        // static shared memory of the kernels: four mbarriers, a flag, one sum
+        // static shared memory of the kernels: four mbarriers, a flag, one sum, a TMEM slot
         const size_t limit = 227 * 1024 - 64;
-        int chunk[2] = {0, 0};
-        if (C >= 2) {
-            for (int adj = 0; adj < 2; ++adj) {
-                const size_t fixed = fwi::cluster_smem(RC, P, adj != 0, 0, p.nr);
-                const size_t per = ((size_t)p.nr + 1) * 4;
-                size_t c = fixed + per > limit ? 0 : (limit - fixed) / per;
-                chunk[adj] = c > 32 ? 32 : (int)c;
-            }
-        }
-        bool ok = C >= 2 && chunk[0] >= 1 && chunk[1] >= 1;
-        // the adjoint injects each receiver from the thread owning its cell:
-        // at most one receiver per column of a strip
-        for (int i = 0; ok && i < p.nr; ++i)
-            for (int k = 0; k < i; ++k)
-                if (pl->rec_px[i] == pl->rec_px[k] && pl->rec_pz[i] / RS == pl->rec_pz[k] / RS) {
-                    ok = false;
-                    break;
+        struct Try { bool pair; int rs; };
+        const Try tries[] = {{true, fwi::kCluPairRows}, {false, 13}, {false, 19}};
+        for (const Try &t : tries) {
+            if (pl->cluster) break;
+            if ((p.shape == FWI_SHAPE_CLUSTER_PAIRS && !t.pair) ||
+                (p.shape == FWI_SHAPE_CLUSTER_RS13 && (t.pair || t.rs != 13)) ||
+                (p.shape == FWI_SHAPE_CLUSTER_RS19 && (t.pair || t.rs != 19)))
+                continue;
+            if (t.pair && (pl->NX % 2 != 0 || pl->NX + 4 > fwi::kCluPairPitch)) continue;
+            const int P = t.pair ? fwi::kCluPairPitch : fwi::kCluPitch;
+            const int RS = t.rs;
+            const int nstrip = (rc0 + RS - 1) / RS;
+            const int threads = ((t.pair ? pl->NX / 2 : pl->NX) * nstrip + 31) / 32 * 32;
+            if (threads > (t.pair ? fwi::kCluPairThreads : fwi::clu_max_threads(RS))) continue;
+            const int RC = nstrip * RS;
+            const int C = (pl->NZ + RC - 1) / RC;
+            int chunk[2] = {0, 0};
+            if (C >= 2) {
+                for (int adj = 0; adj < 2; ++adj) {
+                    const size_t fixed = fwi::cluster_smem(RC, P, adj != 0, 0, p.nr, t.pair);
+                    const size_t per = ((size_t)p.nr + 1) * 4;
+                    size_t c = fixed + per > limit ? 0 : (limit - fixed) / per;
+                    chunk[adj] = c > 32 ? 32 : (int)c;
                 }
-        if (ok) {
-            pl->cluster = true;
-            pl->clu = fwi::ClusterArgs{P, C, RC, RS, nstrip, pl->NXp, 0, nullptr, nullptr, 0, 0ull};
-            pl->clu_threads = threads;
-            pl->clu_chunk_fwd = chunk[0];
-            pl->clu_chunk_adj = chunk[1];
-            // record: C RC rows per plane at the pitch P - 1
-            pl->nzs = C * RC;
-            pl->rec_pitch = P - 1;
+            }
+            bool ok = C >= 2 && C <= fwi::kClusterCTAs && chunk[0] >= 1 && chunk[1] >= 1;
+            // the adjoint injects each receiver from the thread owning its cell:
+            // at most one receiver per column of a strip
+            for (int i = 0; ok && i < p.nr; ++i)
+                for (int k = 0; k < i; ++k)
+                    if (pl->rec_px[i] == pl->rec_px[k] &&
+                        pl->rec_pz[i] / RS == pl->rec_pz[k] / RS) {
+                        ok = false;
+                        break;
+                    }
+            if (ok) {
+                pl->cluster = true;
+                pl->clu = fwi::ClusterArgs{P, C, RC, RS, nstrip, pl->NXp, 0, nullptr, nullptr,
+                                           0, 0ull, t.pair ? 1 : 0};
+                pl->clu_threads = threads;
+                pl->clu_chunk_fwd = chunk[0];
+                pl->clu_chunk_adj = chunk[1];
+                // record: C RC rows per plane at the pitch kCluPitch - 1
+                pl->nzs = C * RC;
+                pl->rec_pitch = fwi::kCluPitch - 1;
+            }
         }
     }
     // the shape must be one of the family the plan runs on
@@ -319,7 +322,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
                  (sh == FWI_SHAPE_RESIDENT_PAIRS && pl->fwd_pair);
         } else if (pl->cluster) {
             family = "cluster";
-            ok = ok || sh == FWI_SHAPE_CLUSTER_RS13 || sh == FWI_SHAPE_CLUSTER_RS19;
+            ok = ok || sh == FWI_SHAPE_CLUSTER_RS13 || sh == FWI_SHAPE_CLUSTER_RS19 ||
+                 sh == FWI_SHAPE_CLUSTER_PAIRS;
         } else if (pl->tiled) {
             family = "tiled";
             ok = ok || sh == FWI_SHAPE_TILED_ROWS8 || sh == FWI_SHAPE_TILED_ROWS4;

@@ -4,8 +4,8 @@
 // problem (one CTA per grid, a cluster of CTAs, global-memory tiles, and
 // for the CPML absorber its own kernels) and every thread shape of the
 // family (fwi_problem.shape: column pairs or single columns for the resident
-// kernels, 13- or 19-row strips for the cluster kernels, 8 or 4 rows a
-// thread for the tiled kernels) it
+// kernels, column pairs or 13- or 19-row single-column strips for the cluster
+// kernels, 8 or 4 rows a thread for the tiled kernels) it
 // creates plans on two shortened time axes (T and 2T steps), times one
 // gradient pass (forward with the record, adjoint) on each after an untimed
 // one, in caller-provided scratch, and predicts the pass at the problem's nt
@@ -25,10 +25,12 @@ constexpr size_t kAlign = 256;
 constexpr int kFamilies[4] = {FWI_KERNELS_RESIDENT, FWI_KERNELS_TILED, FWI_KERNELS_CLUSTER,
                                FWI_KERNELS_CPML};
 // the shapes tried per family (in kFamilies order), default first
-constexpr int kShapes[4][2] = {{FWI_SHAPE_RESIDENT_PAIRS, FWI_SHAPE_RESIDENT_COLUMNS},
-                               {FWI_SHAPE_TILED_ROWS8, FWI_SHAPE_TILED_ROWS4},
-                               {FWI_SHAPE_CLUSTER_RS13, FWI_SHAPE_CLUSTER_RS19},
-                               {FWI_SHAPE_DEFAULT, -1}};
+constexpr int kMaxShapes = 3;
+constexpr int kShapes[4][kMaxShapes] = {
+    {FWI_SHAPE_RESIDENT_PAIRS, FWI_SHAPE_RESIDENT_COLUMNS, -1},
+    {FWI_SHAPE_TILED_ROWS8, FWI_SHAPE_TILED_ROWS4, -1},
+    {FWI_SHAPE_CLUSTER_PAIRS, FWI_SHAPE_CLUSTER_RS13, FWI_SHAPE_CLUSTER_RS19},
+    {FWI_SHAPE_DEFAULT, -1, -1}};
 
 size_t up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
@@ -129,8 +131,8 @@ fwi_status fwi_autotune_kernels(const fwi_problem *prob, const fwi_w2_params *w2
         return fwi::record_error(FWI_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(ce));
     }
     const int n1 = trial_steps, n2 = long_trial(*prob, trial_steps);
-    for (int cand = 0; cand < 8 && s == FWI_OK; ++cand) {
-        const int k = cand / 2, sh = kShapes[k][cand % 2];
+    for (int cand = 0; cand < 4 * kMaxShapes && s == FWI_OK; ++cand) {
+        const int k = cand / kMaxShapes, sh = kShapes[k][cand % kMaxShapes];
         if (sh < 0) continue;
         float tl[2] = {-1.f, -1.f};   // best time of one pass at n1 and n2 steps
         bool ran = false;

@@ -47,6 +47,11 @@ constexpr int kCluPitch = 341;
 // SM): 21 warps put 6 on some scheduler, whose 16K registers then give 80 a
 // thread, as 24 warps do
 __host__ __device__ constexpr int clu_max_threads(int RS) { return RS > 13 ? 672 : 768; }
+// column-pair cluster kernels: shared-memory row pitch (even: 8-byte rows),
+// rows a thread, threads at most; the record keeps the pitch kCluPitch - 1
+constexpr int kCluPairPitch = 342;
+constexpr int kCluPairRows = 10;
+constexpr int kCluPairThreads = 672;
 
 struct ClusterArgs {
     int P;          // shared-memory row pitch
@@ -60,6 +65,7 @@ struct ClusterArgs {
     float *acc_src; // adjoint: source-cell sums [bs]
     int withhold;   // 1: send no halo rows (the bounded-wait self-check)
     unsigned long long wait_ns;   // bound of one halo wait
+    int pair;       // 1: column-pair kernels (RS = kCluPairRows rows of two columns a thread)
 };
 
 struct Plan {
@@ -222,7 +228,7 @@ bool fwd_pair_ok(int NX, int NZ, int NZM);
 cudaError_t launch_fast(const Plan &pl, bool adj, const PropArgs &a, cudaStream_t st);
 // Cluster propagators (whole time loop, store-all plans): shared memory of
 // one CTA, and the launch
-size_t cluster_smem(int RC, int P, bool adj, int chunk, int nr);
+size_t cluster_smem(int RC, int P, bool adj, int chunk, int nr, bool pair = false);
 cudaError_t launch_cluster(const Plan &pl, bool adj, const PropArgs &a, unsigned char *ws,
                            cudaStream_t st, bool wait_check = false);
 cudaError_t launch_tile_fold(const Plan &pl, const PropArgs &a, unsigned char *ws,

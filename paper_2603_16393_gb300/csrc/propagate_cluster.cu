@@ -43,8 +43,11 @@
 
 #include <cstdint>
 
+#include "f32x2.cuh"
 #include "fwi_device.cuh"
 #include "fwi_internal.cuh"
+#include "stencil_pair.cuh"
+#include "tmem.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -461,6 +464,333 @@ k_clu_adj(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArg
     cl.sync();   // no CTA leaves while a neighbour may still write into it
 }
 
+// ------------------------------------------------------------------ column pairs
+// The same cluster scheme with the column-pair threads of the resident
+// kernels: a thread owns columns (x, x+1) x RW rows of its CTA's rows, moves
+// them as 8-byte accesses and updates both with packed f32x2 operations
+// (stencil_pair.cuh; per cell the operations and their order are those of
+// k_clu_fwd / k_clu_adj, so the results are bitwise theirs with the reflecting
+// top).  Halo rows go out as 8-byte st.async stores (the same bytes per level
+// on each mbarrier).  The adjoint keeps its imaging sums and (kappa A, 2A)
+// in tensor memory instead of shared memory and registers, reads the record
+// through a ring of KR rows per thread and prefetches its CTA's part of each
+// record plane into L2 two steps ahead.
+constexpr int kCluKR = 6;
+constexpr int kCluSumCols = 24;                               // 2 x 10 sums, padded to 4
+constexpr int kCluWarpCols = kCluSumCols + 4 * kCluPairRows;  // + (kappa A, 2A) a row
+constexpr int kCluTmemCols = 512;
+constexpr size_t kCluSoloSmem = 116 * 1024;   // > half of an SM's 228 KB
+static_assert(kCluWarpCols * ((kCluPairThreads / 32 + 3) / 4) <= kCluTmemCols,
+              "the lane quarters' columns must fit the allocation");
+
+// two floats into another CTA's shared memory, 8 bytes counted on its mbarrier
+__device__ __forceinline__ void put_remote2(unsigned raddr, float2 v, unsigned rmbar)
+{
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];" ::"r"(
+            raddr),
+        "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(rmbar)
+        : "memory");
+}
+
+// send_edges for a column pair (np: the thread's first row, 8-byte aligned)
+template <int P, int RW>
+__device__ __forceinline__ void send_edges_pair(const float *np, int RC, int crank, bool up,
+                                                bool dn, uint64_t *mb)
+{
+    if (up) {
+        const unsigned rm = at_rank(s_u32(mb), crank - 1);
+        const unsigned ra = at_rank(s_u32(np + RC * P), crank - 1);
+        put_remote2(ra, f2::ld(np), rm);
+        put_remote2(ra + 4 * P, f2::ld(np + P), rm);
+    }
+    if (dn) {
+        const unsigned rm = at_rank(s_u32(mb), crank + 1);
+        const unsigned ra = at_rank(s_u32(np + (RW - 2 - RC) * P), crank + 1);
+        put_remote2(ra, f2::ld(np + (RW - 2) * P), rm);
+        put_remote2(ra + 4 * P, f2::ld(np + (RW - 1) * P), rm);
+    }
+}
+
+template <int P, int RW, int TOPBC, bool STORE>
+__global__ void __launch_bounds__(kCluPairThreads, 1)
+k_clu_fwd_pair(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArgs e)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = e.C, crank = (int)cl.block_rank();
+    const int bs = blockIdx.x / C, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int NX = a.NX, NZ = a.NZ, RC = e.RC;
+    const int FS = (RC + 4) * P;
+    constexpr int PRC = kCluPitch - 1;
+    extern __shared__ __align__(16) float sm[];
+    __shared__ uint64_t mb[kHaloBars];
+    __shared__ int failed;
+    float *U0 = sm, *U1 = U0 + FS, *ABt = U1 + FS, *ST = ABt + RC * P;
+    float *RSw = ST + e.chunk * a.nr;
+    const int g0 = crank * RC;
+    for (int i = tid; i < 2 * FS; i += nth) sm[i] = 0.f;
+    for (int i = tid; i < RC * P; i += nth) {
+        const int lr = i / P, px = i - (i / P) * P, gz = g0 + lr;
+        float m = 0.f;
+        if (gz < NZ && px < NX) {
+            const double ee = e_cell(px, gz, a);
+            m = (float)((1.0 - ee) / (1.0 + ee));
+        }
+        ABt[i] = m;
+    }
+    const float *vb = a.v + (size_t)b * a.nz * a.nx;
+    const int NXP = NX / 2;
+    const int xp = tid % NXP, strip = tid / NXP;
+    const bool active = strip < e.nstrip;
+    const int x = 2 * xp, l0 = strip * RW;
+    float2 ka[RW], vi[RW];
+    int bad = 0;
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int gz = g0 + l0 + r;
+        float k[2] = {0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (active && gz < NZ) {
+                const float vv = vb[min(gz, a.nz - 1) * a.nx + min(max(x + c - a.nb, 0), a.nx - 1)];
+                if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
+                k[c] = kappaA_cell(vv, x + c, gz, a);
+            }
+        }
+        ka[r] = make_float2(k[0], k[1]);
+        vi[r] = make_float2(0.f, 0.f);
+    }
+    if (bad) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
+    const bool has_up = crank > 0, has_dn = crank + 1 < C;
+    const bool send_up = active && strip == 0 && has_up;
+    const bool send_dn = active && strip == e.nstrip - 1 && has_dn;
+    const bool top_strip = active && strip == 0 && crank == 0;
+    const unsigned halo_bytes = (unsigned)((has_up ? 1 : 0) + (has_dn ? 1 : 0)) * 8u * NX;
+    if (tid == 0) {
+        halo_init(mb, halo_bytes, a.nt);
+        failed = 0;
+    }
+    // source owner: row and column inside this thread's RW x 2 block
+    const int sz = a.src_pz[s], sx = a.src_px[s];
+    const int src_k = (active && (sx >> 1) == xp && sz >= g0 + l0 && sz < g0 + l0 + RW)
+                          ? 2 * (sz - g0 - l0) + (sx & 1) : -1;
+    float kas = 0.f;
+#pragma unroll
+    for (int k = 0; k < RW; ++k) {
+        if (2 * k == src_k) kas = ka[k].x;
+        if (2 * k + 1 == src_k) kas = ka[k].y;
+    }
+    const size_t plane = (size_t)C * RC * PRC;
+    float *sw = STORE ? a.snap + (size_t)bs * a.rec_planes * plane + (size_t)(g0 + l0) * PRC + x
+                      : nullptr;
+    cl.sync();   // every CTA's fields are zero and its mbarriers set up
+
+    for (int j0 = 0; j0 < a.nt; j0 += e.chunk) {
+        const int nch = min(e.chunk, a.nt - j0);
+        for (int q = tid; q < nch; q += nth) RSw[q] = ricker_scaled(j0 + q, a);
+        __syncthreads();
+        for (int jj = 0; jj < nch; ++jj) {
+            const int j = j0 + jj;
+            const float *cur = (j & 1) ? U1 : U0;
+            float *nxt = (j & 1) ? U0 : U1;
+            // after a halo wait has run out (the flag only goes 0 -> 1) no phase
+            // is armed again (see k_clu_fwd)
+            if (tid == 0 && j + 3 <= a.nt && !*(volatile int *)&failed)
+                halo_arm(&mb[(j + 3) & 3], halo_bytes);
+            if (active) {
+                const float *cp = cur + (l0 + 2) * P + x + 2;
+                float *np = nxt + (l0 + 2) * P + x + 2;
+                fwd_rows_pair<P, PRC, RW, TOPBC, STORE, true>(cp, np, ABt + l0 * P + x, sw,
+                                                               top_strip, ka, vi, a);
+                if (src_k >= 0) {
+                    // point source: + kappa A s at the source cell (increment and field)
+                    const float d = kas * RSw[jj];
+#pragma unroll
+                    for (int k = 0; k < RW; ++k) {
+                        if (2 * k == src_k) vi[k].x += d;
+                        if (2 * k + 1 == src_k) vi[k].y += d;
+                    }
+                    const int lz = sz - g0;
+                    nxt[(lz + 2) * P + sx + 2] += d;
+                    if (TOPBC == 1 && crank == 0 && (lz == 1 || lz == 2))
+                        nxt[(2 - lz) * P + sx + 2] += d;
+                }
+                // a CTA whose wait ran out sends no more halo rows
+                if (!e.withhold && !*(volatile int *)&failed)
+                    send_edges_pair<P, RW>(np, RC, crank, send_up, send_dn, &mb[(j + 1) & 3]);
+            }
+            if (STORE) sw += plane;
+            __syncthreads();
+            for (int i = tid; i < a.nr; i += nth) {
+                const int rz = a.rec_pz[i] - g0;
+                if (rz >= 0 && rz < RC) ST[jj * a.nr + i] = nxt[(rz + 2) * P + a.rec_px[i] + 2];
+            }
+            halo_wait(&mb[(j + 1) & 3], halo_parity(j + 1), &failed, a.status, e.wait_ns);
+        }
+        __syncthreads();
+        float *db = a.d_syn + (size_t)bs * a.nr * a.nt;
+        for (int q = tid; q < nch * a.nr; q += nth) {
+            const int i = q / nch, jj = q - (q / nch) * nch;
+            const int rz = a.rec_pz[i] - g0;
+            if (rz >= 0 && rz < RC) db[(size_t)i * a.nt + j0 + jj] = ST[jj * a.nr + i];
+        }
+        __syncthreads();
+    }
+    cl.sync();   // no CTA leaves while a neighbour may still write into it
+}
+
+template <int P, int RW, int TOPBC>
+__global__ void __launch_bounds__(kCluPairThreads, 1)
+k_clu_adj_pair(const __grid_constant__ PropArgs a, const __grid_constant__ ClusterArgs e)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = e.C, crank = (int)cl.block_rank();
+    const int bs = blockIdx.x / C, b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int NX = a.NX, NZ = a.NZ, RC = e.RC;
+    const int FS = (RC + 4) * P;
+    constexpr int PRC = kCluPitch - 1;
+    extern __shared__ __align__(16) float sm[];
+    __shared__ uint64_t mb[kHaloBars];
+    __shared__ int failed;
+    __shared__ float acc_src;
+    __shared__ uint32_t tmem_slot;
+    float *U0 = sm, *U1 = U0 + FS, *K = U1 + FS, *IC = K + RC * P;
+    float *ST = IC + a.nr, *RSw = ST + e.chunk * a.nr;
+    const int g0 = crank * RC;
+    const uint32_t tmem = tmem_alloc(&tmem_slot, kCluTmemCols);
+    for (int i = tid; i < 2 * FS; i += nth) sm[i] = 0.f;
+    const float *vb = a.v + (size_t)b * a.nz * a.nx;
+    for (int i = tid; i < a.nr; i += nth) {
+        const int rz = a.rec_pz[i], rx = a.rec_px[i];
+        const float vv = vb[min(rz, a.nz - 1) * a.nx + min(max(rx - a.nb, 0), a.nx - 1)];
+        const double vdt = (double)vv * a.dtd;
+        IC[i] = (float)(vdt * vdt / (1.0 - e_cell(rx, rz, a)));   // kappa / B
+    }
+    int bad = 0;
+    for (int i = tid; i < RC * P; i += nth) {
+        const int lr = i / P, px = i - (i / P) * P, gz = g0 + lr;
+        float k = 0.f;
+        if (gz < NZ && px < NX) {
+            const float vv = vb[min(gz, a.nz - 1) * a.nx + min(max(px - a.nb, 0), a.nx - 1)];
+            if (!(vv > 0.f && vv <= a.vmax)) bad = 1;
+            k = kappaA_cell(vv, px, gz, a);
+        }
+        K[i] = k;
+    }
+    if (bad) set_status(a.status, FWI_ERR_UNSTABLE_CFL);
+    __syncthreads();   // the kappa A table is complete before it goes to tensor memory
+    // inactive threads (past the last strip) run the row code on strip 0,
+    // columns 0 and 1, with every write gated (TMEM accesses are warp-collective)
+    const int NXP = NX / 2;
+    const int strip = tid / NXP;
+    const bool active = strip < e.nstrip;
+    const int x = active ? 2 * (tid % NXP) : 0;
+    const int l0 = active ? strip * RW : 0;
+    const bool has_up = crank > 0, has_dn = crank + 1 < C;
+    const bool send_up = active && strip == 0 && has_up;
+    const bool send_dn = active && strip == e.nstrip - 1 && has_dn;
+    const bool top_strip = active && strip == 0 && crank == 0;
+    const unsigned halo_bytes = (unsigned)((has_up ? 1 : 0) + (has_dn ? 1 : 0)) * 8u * NX;
+    if (tid == 0) {
+        halo_init(mb, halo_bytes, a.nt);
+        failed = 0;
+        acc_src = 0.f;
+    }
+    // receivers owned by this thread (one per column of a strip at most)
+    int inj0 = -1, inj1 = -1;
+    for (int i = 0; i < a.nr; ++i) {
+        const int rz = a.rec_pz[i] - g0, rx = a.rec_px[i];
+        if (active && rz >= l0 && rz < l0 + RW) {
+            if (rx == x) inj0 = i;
+            if (rx == x + 1) inj1 = i;
+        }
+    }
+    const int inj0_off = inj0 >= 0 ? (a.rec_pz[inj0] - g0 + 2) * P + x + 2 : 0;
+    const int inj1_off = inj1 >= 0 ? (a.rec_pz[inj1] - g0 + 2) * P + x + 3 : 0;
+    const int sz = a.src_pz[s], sx = a.src_px[s];
+    const bool src_here = sz >= g0 && sz < g0 + RC;
+    const int warp = tid >> 5;
+    const uint32_t tacc = tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
+                          (uint32_t)(kCluWarpCols * (warp >> 2));
+    const uint32_t tkd = tacc + kCluSumCols;
+    // imaging sums (zero) and (kappa A, 2A) of the thread's cells into its TMEM lane
+    const float zbf = (float)(g0 + l0 - (a.nz - 1));
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        tmem_st2(tacc + 2 * r, make_float2(0.f, 0.f));
+        const float ez = ez_of(zbf + (float)r, a);
+        const float2 h = f2::add(f2::splat(1.f),
+                                 f2::add(make_float2(ex_of(x, a), ex_of(x + 1, a)), f2::splat(ez)));
+        tmem_st4(tkd + 4 * r, f2::ld(K + (l0 + r) * P + x),
+                 make_float2(__fdividef(2.f, h.x), __fdividef(2.f, h.y)));
+    }
+    tmem_wait_st();
+    const size_t plane = (size_t)C * RC * PRC;
+    // this CTA's rows of a record plane (for the L2 prefetch)
+    const size_t cta_off = (size_t)g0 * PRC, cta_bytes = (size_t)RC * PRC * 4;
+    const float *plane_last = a.snap + ((size_t)bs * a.rec_planes + (a.nt - 1)) * plane;
+    const float *sr = plane_last + (size_t)(g0 + l0) * PRC + x;
+    float2 rq[kCluKR];
+#pragma unroll
+    for (int i = 0; i < kCluKR; ++i) rq[i] = f2::ld(sr + i * PRC);
+    if (a.nt > 1) prefetch_plane_l2(plane_last - plane + cta_off, cta_bytes, tid);
+    cl.sync();   // every CTA's fields are zero and its mbarriers set up
+
+    for (int j0 = 0; j0 < a.nt; j0 += e.chunk) {
+        const int nch = min(e.chunk, a.nt - j0);
+        const float *ab = a.adj + (size_t)bs * a.nr * a.nt;
+        for (int q = tid; q < nch * a.nr; q += nth) {
+            const int i = q / nch, jj = q - (q / nch) * nch;
+            ST[jj * a.nr + i] = IC[i] * ab[(size_t)i * a.nt + (a.nt - 1 - (j0 + jj))];
+        }
+        for (int q = tid; q < nch; q += nth) RSw[q] = ricker_scaled(a.nt - 1 - (j0 + q), a);
+        __syncthreads();
+        for (int jj = 0; jj < nch; ++jj) {
+            const int j = j0 + jj;
+            const float *cur = (j & 1) ? U1 : U0;
+            float *nxt = (j & 1) ? U0 : U1;
+            if (tid == 0 && j + 3 <= a.nt && !*(volatile int *)&failed)
+                halo_arm(&mb[(j + 3) & 3], halo_bytes);
+            if (inj0 >= 0) nxt[inj0_off] -= ST[jj * a.nr + inj0];   // (kappa/B) q
+            if (inj1 >= 0) nxt[inj1_off] -= ST[jj * a.nr + inj1];
+            if (j + 2 < a.nt) prefetch_plane_l2(plane_last - (size_t)(j + 2) * plane + cta_off,
+                                                cta_bytes, tid);
+            const float *sr_next = (j + 1 < a.nt) ? sr - plane : sr;
+            float *np = nxt + (l0 + 2) * P + x + 2;
+            adj_rows_pair<P, PRC, RW, kCluKR, TOPBC>(cur + (l0 + 2) * P + x + 2, np, sr, sr_next,
+                                                     top_strip, active, tacc, tkd, rq, a);
+            tmem_wait_st();
+            sr = sr_next;
+            // a CTA whose wait ran out sends no more halo rows
+            if (active && !e.withhold && !*(volatile int *)&failed)
+                send_edges_pair<P, RW>(np, RC, crank, send_up, send_dn, &mb[(j + 1) & 3]);
+            __syncthreads();
+            if (tid == nth - 1 && src_here)
+                acc_src = fmaf(nxt[(sz - g0 + 2) * P + sx + 2], RSw[jj], acc_src);
+            halo_wait(&mb[(j + 1) & 3], halo_parity(j + 1), &failed, a.status, e.wait_ns);
+        }
+        __syncthreads();
+    }
+    // imaging sums of this CTA's rows and the source-cell sum to the fold
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        uint32_t s0, s1;
+        tmem_ld2(tacc + 2 * r, s0, s1);
+        tmem_wait_ld();
+        const int gz = g0 + l0 + r;
+        if (active && gz < NZ) {
+            float *dst = e.acc + ((size_t)bs * NZ + gz) * e.NXp + x;
+            dst[0] = __uint_as_float(s0);
+            dst[1] = __uint_as_float(s1);
+        }
+    }
+    if (tid == 0 && src_here) e.acc_src[bs] = acc_src;
+    tmem_free(tmem, kCluTmemCols);
+    cl.sync();   // no CTA leaves while a neighbour may still write into it
+}
+
 template <typename Kern>
 cudaError_t launch_clu(Kern kern, const PropArgs &a, const ClusterArgs &e, int nbs, int threads,
                        size_t smem, cudaStream_t st)
@@ -485,12 +815,13 @@ cudaError_t launch_clu(Kern kern, const PropArgs &a, const ClusterArgs &e, int n
 
 }  // namespace
 
-size_t cluster_smem(int RC, int P, bool adj, int chunk, int nr)
+size_t cluster_smem(int RC, int P, bool adj, int chunk, int nr, bool pair)
 {
-    // two levels with halo rows + one per-cell table (+ the imaging sums and
-    // kappa/B per receiver for the adjoint) + staging of receiver samples and
-    // the wavelet
-    return ((size_t)2 * (RC + 4) * P + (size_t)RC * P + (adj ? (size_t)RC * (P - 1) + nr : 0) +
+    // two levels with halo rows + one per-cell table (+ the imaging sums,
+    // which the column-pair adjoint keeps in tensor memory, and kappa/B per
+    // receiver for the adjoint) + staging of receiver samples and the wavelet
+    const size_t sums = adj && !pair ? (size_t)RC * (P - 1) : 0;
+    return ((size_t)2 * (RC + 4) * P + (size_t)RC * P + sums + (adj ? (size_t)nr : 0) +
             (size_t)chunk * (nr + 1)) *
            sizeof(float);
 }
@@ -506,7 +837,7 @@ cudaError_t launch_cluster(const Plan &pl, bool adj, const PropArgs &a, unsigned
     e.acc = (float *)(ws + pl.ws_t_acc);
     e.acc_src = (float *)(ws + pl.ws_t_accsrc);
     e.chunk = adj ? pl.clu_chunk_adj : pl.clu_chunk_fwd;
-    const size_t smem = cluster_smem(e.RC, e.P, adj, e.chunk, pl.p.nr);
+    const size_t smem = cluster_smem(e.RC, e.P, adj, e.chunk, pl.p.nr, e.pair != 0);
     const int threads = pl.clu_threads;
     const int tb = pl.p.top_bc;
     const bool store = a.snap != nullptr;
@@ -520,6 +851,22 @@ cudaError_t launch_cluster(const Plan &pl, bool adj, const PropArgs &a, unsigned
                       : launch_clu(k_clu_fwd<PP, RSV, 0, true>, a, e, nbs, threads, smem, st);  \
         return tb ? launch_clu(k_clu_fwd<PP, RSV, 1, false>, a, e, nbs, threads, smem, st)      \
                   : launch_clu(k_clu_fwd<PP, RSV, 0, false>, a, e, nbs, threads, smem, st);     \
+    }
+    if (e.pair) {
+        if (e.P != kCluPairPitch || e.RS != kCluPairRows) return cudaErrorInvalidValue;
+        constexpr int PP = kCluPairPitch, RW = kCluPairRows;
+        // the adjoint takes all of its SM's tensor memory: it asks for more
+        // than half the SM's shared memory, so no second CTA (whose allocation
+        // would wait for this one, or for a CTA of its own cluster) shares the SM
+        const size_t smem_adj = smem > kCluSoloSmem ? smem : kCluSoloSmem;
+        if (adj)
+            return tb ? launch_clu(k_clu_adj_pair<PP, RW, 1>, a, e, nbs, threads, smem_adj, st)
+                      : launch_clu(k_clu_adj_pair<PP, RW, 0>, a, e, nbs, threads, smem_adj, st);
+        if (store)
+            return tb ? launch_clu(k_clu_fwd_pair<PP, RW, 1, true>, a, e, nbs, threads, smem, st)
+                      : launch_clu(k_clu_fwd_pair<PP, RW, 0, true>, a, e, nbs, threads, smem, st);
+        return tb ? launch_clu(k_clu_fwd_pair<PP, RW, 1, false>, a, e, nbs, threads, smem, st)
+                  : launch_clu(k_clu_fwd_pair<PP, RW, 0, false>, a, e, nbs, threads, smem, st);
     }
     FWI_CLU(kCluPitch, 13)
     FWI_CLU(kCluPitch, 19)

@@ -31,6 +31,8 @@
 #include "f32x2.cuh"
 #include "fwi_device.cuh"
 #include "fwi_internal.cuh"
+#include "stencil_pair.cuh"
+#include "tmem.cuh"
 
 namespace fwi {
 
@@ -230,61 +232,6 @@ __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_fwd_fast(const __grid_con
 // bitwise those of the scalar code).  Needs an even padded width.
 constexpr int ROWS2 = kFastRows / 2;
 
-template <int P, int PR, int TOPBC, bool STORE, bool AHEAD>
-__device__ __forceinline__ void fwd_rows_pair(const float *__restrict__ cp, float *__restrict__ np,
-                                              const float *__restrict__ abp,
-                                              float *__restrict__ sw, bool top_strip,
-                                              const float2 (&ka)[ROWS2], float2 (&vi)[ROWS2],
-                                              const PropArgs &a)
-{
-    using namespace f2;
-    const float2 CX1 = splat(a.cx1), CX2 = splat(a.cx2), CZ1 = splat(a.cz1), CZ2 = splat(a.cz2);
-    float2 wm2 = ld(cp - 2 * P), wm1 = ld(cp - P), w0 = ld(cp), wp1 = ld(cp + P);
-    // AHEAD: the shared-memory operands of row r + 1 are loaded while row r
-    // is updated (a row's arithmetic is a chain of dependent packed
-    // operations); the queue kernel, whose plan-indexed arguments hold more
-    // registers, loads each row's operands in its own iteration
-    float2 nwp2 = {}, nL = {}, nR = {}, nab = {};
-    if (AHEAD) nwp2 = ld(cp + 2 * P), nL = ld(cp - 2), nR = ld(cp + 2), nab = ld(abp);
-#pragma unroll
-    for (int r = 0; r < ROWS2; ++r) {
-        const float *c = cp + r * P;
-        const float2 wp2 = AHEAD ? nwp2 : ld(c + 2 * P);
-        const float2 L = AHEAD ? nL : ld(c - 2);     // u[x-2], u[x-1]
-        const float2 R = AHEAD ? nR : ld(c + 2);     // u[x+2], u[x+3]
-        const float2 ab_ahead = nab;
-        if (AHEAD && r + 1 < ROWS2) {
-            nwp2 = ld(c + 3 * P);
-            nL = ld(c + P - 2);
-            nR = ld(c + P + 2);
-            nab = ld(abp + (r + 1) * P);
-        }
-        // x, first neighbours: (u[x-1] - u[x]) + (u[x+1] - u[x]) per column
-        const float d01 = w0.y - w0.x;
-        const float2 dxA = make_float2((L.y - w0.x) + d01, (R.x - w0.y) - d01);
-        // x, second neighbours; z
-        const float2 dxB = add(sub(L, w0), sub(R, w0));
-        const float2 dzA = add(sub(wm1, w0), sub(wp1, w0));
-        const float2 dzB = add(sub(wm2, w0), sub(wp2, w0));
-        float2 lap = mul(CX1, dxA);
-        lap = fma(CX2, dxB, lap);
-        lap = fma(CZ1, dzA, lap);
-        lap = fma(CZ2, dzB, lap);
-        const float2 ab = AHEAD ? ab_ahead : ld(abp + r * P);
-        vi[r] = fma(ka[r], lap, mul(ab, vi[r]));
-        const float2 un = add(w0, vi[r]);
-        st(np + r * P, un);
-        if (TOPBC == 1 && (r == 1 || r == 2)) {
-            if (top_strip) st(np - r * P, un);   // mirrored ghost rows -1, -2
-        }
-        if (STORE) st(sw + r * PR, lap);
-        wm2 = wm1;
-        wm1 = w0;
-        w0 = wp1;
-        wp1 = wp2;
-    }
-}
-
 // One (model, shot) unit bs of a plan: the whole forward time loop of the
 // column-pair kernel (k_fwd_pair runs one unit a CTA, k_fwd_pair_queue draws
 // units of several plans from a counter)
@@ -393,8 +340,8 @@ __device__ __forceinline__ void fwd_pair_unit(const PropArgs &a, const PropArgs 
             if (active) {
                 const float *cp = cur + (z0 + 2) * P + x + 2;
                 float *np = nxt + (z0 + 2) * P + x + 2;
-                fwd_rows_pair<P, PR, TOPBC, STORE, AHEAD>(cp, np, ABt + z0 * P + x, sw, top_strip,
-                                                          ka, vi, c);
+                fwd_rows_pair<P, PR, ROWS2, TOPBC, STORE, AHEAD>(cp, np, ABt + z0 * P + x, sw,
+                                                                 top_strip, ka, vi, c);
                 if (src_k >= 0) {
                     // point source: + kappa A s at the source cell (increment and field)
                     float kas = 0.f;
@@ -726,99 +673,6 @@ constexpr int kAdjSumCols = 24;     // a warp's imaging sums: 2 x 11 rows, padde
 constexpr int kAdjWarpCols = kAdjSumCols + 4 * ROWS2;   // + (kappa A, 2A) of two cells a row
 constexpr int kAdjTmemCols = 512;   // 6 warps per lane quarter x 68 columns, rounded up
 
-// L2 prefetch of a record plane (16-byte aligned, size a multiple of 16) in
-// 4 KB pieces, one piece per thread of the first warps
-__device__ __forceinline__ void prefetch_plane_l2(const float *p, size_t bytes, int tid)
-{
-    const size_t off = (size_t)tid * 4096;
-    if (off < bytes) {
-        const unsigned n = (unsigned)min((size_t)4096, bytes - off);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((const char *)p + off),
-                     "r"(n)
-                     : "memory");
-    }
-}
-
-// two fp32 columns of this thread's TMEM lane (warp-collective; the values
-// are valid after tmem_wait_ld)
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t &a, uint32_t &b)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
-                 : "=r"(a), "=r"(b)
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t &a, uint32_t &b, uint32_t &c,
-                                         uint32_t &d)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, float2 u, float2 v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
-                 "r"(__float_as_uint(u.x)), "r"(__float_as_uint(u.y)), "r"(__float_as_uint(v.x)),
-                 "r"(__float_as_uint(v.y))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_st2(uint32_t taddr, float2 v)
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr),
-                 "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-template <int P, int PR, int TOPBC>
-__device__ __forceinline__ void adj_rows_pair(const float *__restrict__ cp,
-                                              float *__restrict__ np,
-                                              const float *__restrict__ sr,
-                                              const float *__restrict__ sr_next,
-                                              bool top_strip, bool active, uint32_t tacc,
-                                              uint32_t tkd, float2 (&rq)[KR], const PropArgs &a)
-{
-    using namespace f2;
-    const float2 &C0 = a.w2[0], &CX1 = a.w2[1], &CX2 = a.w2[2], &CZ1 = a.w2[3], &CZ2 = a.w2[4];
-    float2 wm2 = ld(cp - 2 * P), wm1 = ld(cp - P), w0 = ld(cp), wp1 = ld(cp + P);
-#pragma unroll
-    for (int r = 0; r < ROWS2; ++r) {
-        const float *c = cp + r * P;
-        const float2 wp2 = ld(c + 2 * P);
-        const float2 L = ld(c - 2);     // u[x-2], u[x-1]
-        const float2 R = ld(c + 2);     // u[x+2], u[x+3]
-        float2 lap = mul(C0, w0);
-        lap = fma(CX1, make_float2(L.y + w0.y, w0.x + R.x), lap);
-        lap = fma(CX2, add(L, R), lap);
-        lap = fma(CZ1, add(wm1, wp1), lap);
-        lap = fma(CZ2, add(wm2, wp2), lap);
-        if (TOPBC == 1 && (r == 1 || r == 2)) {
-            // transpose of the mirrored top: reflected weights back onto rows 1, 2
-            if (top_strip) lap = (r == 1) ? add(lap, fma(CZ2, w0, mul(CZ1, wm1)))
-                                          : fma(CZ2, wm2, lap);
-        }
-        uint32_t s0, s1, k0, k1, d0, d1;
-        tmem_ld2(tacc + 2 * r, s0, s1);
-        tmem_ld4(tkd + 4 * r, k0, k1, d0, d1);
-        const float2 fo = ld(np + r * P);
-        tmem_wait_ld();
-        const float2 kA = make_float2(__uint_as_float(k0), __uint_as_float(k1));
-        const float2 A2 = make_float2(__uint_as_float(d0), __uint_as_float(d1));   // 2A
-        const float2 nAB = fma(A2, splat(-1.f), splat(1.f));            // -A B = 1 - 2A
-        const float2 fn = fma(kA, lap, fma(A2, w0, mul(nAB, fo)));
-        if (active) st(np + r * P, fn);
-        tmem_st2(tacc + 2 * r,
-                 fma(fn, rq[0], make_float2(__uint_as_float(s0), __uint_as_float(s1))));
-#pragma unroll
-        for (int i = 0; i + 1 < KR; ++i) rq[i] = rq[i + 1];
-        rq[KR - 1] = (r + KR < ROWS2) ? ld(sr + (r + KR) * PR) : ld(sr_next + (r + KR - ROWS2) * PR);
-        wm2 = wm1;
-        wm1 = w0;
-        w0 = wp1;
-        wp1 = wp2;
-    }
-}
-
 // One (model, shot) unit bs of a plan: the whole adjoint time loop of the
 // column-pair kernel with its epilogue; `tmem` is the CTA's tensor-memory
 // allocation of kAdjTmemCols columns (k_adj_pair allocates it for its one
@@ -954,7 +808,7 @@ __device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const PropArgs 
             if (j + 2 < a.j_end)
                 prefetch_plane_l2(plane_jb - (size_t)(j - jb + 2) * plane, plane * 4, tid);
             const float *sr_next = (j + 1 < a.j_end) ? sr - plane : sr;
-            adj_rows_pair<P, PR, TOPBC>(cur + (z0 + 2) * P + x + 2, nxt + (z0 + 2) * P + x + 2,
+            adj_rows_pair<P, PR, ROWS2, KR, TOPBC>(cur + (z0 + 2) * P + x + 2, nxt + (z0 + 2) * P + x + 2,
                                         sr, sr_next, top_strip, active, tacc, tkd, rq, c);
             tmem_wait_st();
             sr = sr_next;
@@ -1043,40 +897,13 @@ __device__ __forceinline__ void adj_pair_unit(const PropArgs &a, const PropArgs 
 
 // the CTA's tensor memory for the pair adjoint (one warp allocates; every
 // thread sees the base address after the barrier)
-__device__ __forceinline__ uint32_t adj_tmem_alloc(uint32_t *slot)
-{
-    if (threadIdx.x < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         (uint32_t)__cvta_generic_to_shared(slot)),
-                     "r"(kAdjTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return *slot;
-}
-
-__device__ __forceinline__ void adj_tmem_free(uint32_t tmem)
-{
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kAdjTmemCols)
-                     : "memory");
-    }
-}
-
 template <int P, int PR, int NZM, int TOPBC>
 __global__ void __launch_bounds__(kMaxThreadsAdj, 1) k_adj_pair(const __grid_constant__ PropArgs a)
 {
     __shared__ uint32_t tmem_slot;
-    const uint32_t tmem = adj_tmem_alloc(&tmem_slot);
+    const uint32_t tmem = tmem_alloc(&tmem_slot, kAdjTmemCols);
     adj_pair_unit<P, PR, NZM, TOPBC>(a, a, blockIdx.x, tmem);
-    adj_tmem_free(tmem);
+    tmem_free(tmem, kAdjTmemCols);
 }
 
 // Persistent: units drawn from the counter as in k_fwd_pair_queue, one
@@ -1087,7 +914,7 @@ k_adj_pair_queue(const __grid_constant__ QueueArgs q)
 {
     __shared__ uint32_t tmem_slot;
     __shared__ int unit;
-    const uint32_t tmem = adj_tmem_alloc(&tmem_slot);
+    const uint32_t tmem = tmem_alloc(&tmem_slot, kAdjTmemCols);
     for (;;) {
         if (threadIdx.x == 0) unit = atomicAdd(q.counter, 1);
         __syncthreads();
@@ -1099,7 +926,7 @@ k_adj_pair_queue(const __grid_constant__ QueueArgs q)
         adj_pair_unit<P, PR, NZM, TOPBC>(q.a[p], q.a[0], u - q.start[p], tmem);
         __syncthreads();
     }
-    adj_tmem_free(tmem);
+    tmem_free(tmem, kAdjTmemCols);
 }
 
 template <typename K>

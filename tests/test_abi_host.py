@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(api):
     lib = ctypes.CDLL(LIB)
     for n in declared_functions():
         assert hasattr(lib, n), n
-    assert api.fwi_version() == 10900
+    assert api.fwi_version() == 11000
 
 
 def _prob(api, **kw):
@@ -71,10 +71,15 @@ def test_plan_of_a_grid_beyond_shared_memory_uses_the_tiled_fields(api):
     NZ, NX, NXp = 296, 336, 336
     assert snap == B * ns * nt * NZ * NXp * 4
     assert ws >= 6 * B * ns * NZ * NXp * 4 + 2 * B * NZ * NXp * 4
-    # the automatic choice for this grid: a cluster of 8 CTAs of 38 rows (two
-    # 19-row thread strips; the last CTA holds 30 grid rows); record rows at
-    # the cluster kernels' pitch 340
+    # the automatic choice for this grid: column pairs, a cluster of 8 CTAs of
+    # 40 rows (four 10-row strips of 168 column pairs; the last CTA holds 16
+    # grid rows); record rows at the cluster kernels' pitch 340
     h = api.fwi_plan_create(prob, api.W2Params())
+    assert api.fwi_plan_kernels(h) == api.KERNELS_CLUSTER
+    assert api.fwi_plan_sizes(h)[2] == B * ns * nt * (8 * 40) * 340 * 4
+    # single columns: 8 CTAs of 38 rows (two 19-row strips)
+    h = api.fwi_plan_create(dataclasses.replace(prob, shape=api.SHAPE_CLUSTER_RS19),
+                            api.W2Params())
     assert api.fwi_plan_kernels(h) == api.KERNELS_CLUSTER
     assert api.fwi_plan_sizes(h)[2] == B * ns * nt * (8 * 38) * 340 * 4
     # odd padded width: rows padded to a multiple of 4 floats
@@ -189,12 +194,16 @@ def test_kernel_family_selection(api):
         h = K.fwi_plan_create(_prob(api, kernels=fam), K.W2Params())
         assert K.fwi_plan_kernels(h) == fam
     # a cluster plan's record: ceil(110 / 8) = 14 rows a CTA round up to two
-    # 13-row strips, so 5 CTAs of 26 rows: 130 rows at the pitch 340
+    # 10-row strips of column pairs, so 6 CTAs of 20 rows: 120 rows at the
+    # pitch 340; with 13-row single-column strips 5 CTAs of 26 rows
     h = K.fwi_plan_create(_prob(api, kernels=K.KERNELS_CLUSTER), K.W2Params())
+    assert K.fwi_plan_sizes(h)[2] == 3 * 5 * 1000 * 120 * 340 * 4
+    h = K.fwi_plan_create(_prob(api, kernels=K.KERNELS_CLUSTER, shape=K.SHAPE_CLUSTER_RS13),
+                          K.W2Params())
     assert K.fwi_plan_sizes(h)[2] == 3 * 5 * 1000 * 130 * 340 * 4
-    # a grid of 13 rows or fewer would need a cluster of one CTA
+    # a grid of 10 rows or fewer would need a cluster of one CTA
     with pytest.raises(K.FwiError) as e:
-        K.fwi_plan_create(_prob(api, nz=10, nb=3, src_iz=(0,), src_ix=(0,),
+        K.fwi_plan_create(_prob(api, nz=7, nb=3, src_iz=(0,), src_ix=(0,),
                                 kernels=K.KERNELS_CLUSTER), K.W2Params())
     assert e.value.code == 3
     # checkpointed or 8th-order plans of a cluster-sized grid run tiled

@@ -1395,7 +1395,7 @@ def main():
     ap.add_argument("--reverse-steps", type=int, default=500, help="--posterior: reverse steps")
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="--posterior: reverse steps timed on the plain path")
-    ap.add_argument("--surrogate-models", type=int, default=16384,
+    ap.add_argument("--surrogate-models", type=int, default=20480,
                     help="--posterior: FD pairs the surrogate trains on")
     ap.add_argument("--surrogate-steps", type=int, default=6000,
                     help="--posterior: Adam steps of the surrogate's training")

@@ -27,7 +27,10 @@ Readings (the paper leaves these open):
   Eq. vp_transition the marginal at step i is N(sqrt(abar_i) mu,
   abar_i tau2 + 1 - abar_i), whose score is
       s_i(x) = -(x - sqrt(abar_i) mu) / (abar_i tau2 + 1 - abar_i),
-  with the diagonal Jacobian -1 / (abar_i tau2 + 1 - abar_i).
+  with the diagonal Jacobian -1 / (abar_i tau2 + 1 - abar_i).  A second
+  stand-in, LowRankPrior, correlates the cells along k principal directions
+  (smooth samples, as a trained prior gives); its score follows from the
+  same transition with a covariance of known eigenbasis.
 """
 from __future__ import annotations
 
@@ -82,6 +85,42 @@ def gaussian_score_vjp(g, abar: float, tau2):
     """(d s_i / d x)^T g for the Gaussian prior (a diagonal Jacobian)."""
     g, tau2 = np.asarray(g, dtype=np.float64), np.asarray(tau2, dtype=np.float64)
     return -g / (abar * tau2 + 1.0 - abar)
+
+
+class LowRankPrior:
+    """x_0 ~ N(mu, Sigma), Sigma = U diag(lam) U^T + s2 I, U [k][n] with
+    orthonormal rows: a Gaussian prior with k correlated directions (the
+    principal components of a set of models) over an isotropic floor.  By
+    Eq. vp_transition the step-i marginal is N(sqrt(abar) mu, C),
+    C = abar Sigma + (1 - abar) I, whose eigenvalues are
+    c_j = abar (lam_j + s2) + 1 - abar along row j of U and
+    c_perp = abar s2 + 1 - abar across them, so that
+        C^-1 = U^T diag(1 / c_j) U + (I - U^T U) / c_perp.
+    Score s_i(x) = -C^-1 (x - sqrt(abar) mu); its Jacobian -C^-1 is symmetric."""
+
+    def __init__(self, mu, U, lam, s2: float):
+        self.mu = np.asarray(mu, np.float64).ravel()
+        self.U = np.asarray(U, np.float64).reshape(-1, self.mu.size)
+        self.lam = np.asarray(lam, np.float64).ravel()
+        self.s2 = float(s2)
+
+    def _cinv(self, r, abar: float):
+        """C^-1 r for r [B][n] (rows of U orthonormal)."""
+        c = abar * (self.lam + self.s2) + 1.0 - abar
+        cp = abar * self.s2 + 1.0 - abar
+        p = r @ self.U.T                                     # [B][k]
+        return (r - p @ self.U) / cp + (p / c) @ self.U
+
+    def score(self, x, abar: float):
+        x = np.asarray(x, np.float64)
+        B = x.shape[0]
+        r = x.reshape(B, -1) - np.sqrt(abar) * self.mu
+        return -self._cinv(r, abar).reshape(x.shape)
+
+    def score_vjp(self, g, abar: float):
+        g = np.asarray(g, np.float64)
+        B = g.shape[0]
+        return -self._cinv(g.reshape(B, -1), abar).reshape(g.shape)
 
 
 def clean_estimate(v_i, s, abar: float):
@@ -145,19 +184,20 @@ def l2_potential(prob: O.Problem, d_obs, sigma: float):
 
 
 def reverse_step(sched: Schedule, i: int, v_i, z, potential, mu, tau2, gp: O.GuideParams,
-                 dps_zeta: float | None = None):
+                 dps_zeta: float | None = None, prior: LowRankPrior | None = None):
     """One reverse step i -> i-1 of Algorithm 2 (or, with ``dps_zeta``, of
     Algorithm 1: P_i = zeta I) for a batch v_i [B][nz][nx] in the normalised
-    space, the Gaussian-prior score and a potential (``w2_potential`` or
-    ``l2_potential``).  Returns (v_{i-1}, a dict of the intermediates)."""
+    space, the Gaussian-prior score (``prior``: a LowRankPrior instead of
+    mu, tau2) and a potential (``w2_potential`` or ``l2_potential``).
+    Returns (v_{i-1}, a dict of the intermediates)."""
     abar = sched.abar[i]
-    s = gaussian_score(v_i, abar, mu, tau2)
+    s = gaussian_score(v_i, abar, mu, tau2) if prior is None else prior.score(v_i, abar)
     x0 = clean_estimate(v_i, s, abar)
     vp = proposal(v_i, x0, z, sched, i)
     v_phys, mask = to_physical(x0)
     J, g_phys = potential(v_phys)
     g0, _ = guidance_gradients(g_phys, mask, abar)
-    u = gaussian_score_vjp(g0, abar, tau2)
+    u = gaussian_score_vjp(g0, abar, tau2) if prior is None else prior.score_vjp(g0, abar)
     g, h = guidance_gradients(g_phys, mask, abar, u)
     if dps_zeta is not None:
         v_next = vp - dps_zeta * h

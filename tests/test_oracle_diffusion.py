@@ -181,3 +181,42 @@ def test_dps_step_is_algorithm_2_with_a_scalar_preconditioner():
     b, inter = D.reverse_step(SCHED, i, v_i, z, pot, mu, tau2, O.GuideParams(), dps_zeta=zeta)
     np.testing.assert_allclose(a, b, rtol=0, atol=1e-15 * np.abs(b).max())
     assert np.abs(inter["h"]).max() > 0
+
+
+def _lowrank(n=36, k=5, seed=3, s2=0.05):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    return D.LowRankPrior(rng.standard_normal(n) * 0.3, Q.T, rng.uniform(0.2, 3.0, k), s2), rng
+
+
+@pytest.mark.parametrize("abar", [1e-4, 0.03, 0.5, 0.999])
+def test_lowrank_score_against_the_dense_covariance(abar):
+    # brute force: the step-i marginal's covariance abar Sigma + (1 - abar) I
+    # formed as a dense matrix, its score by a linear solve
+    pr, rng = _lowrank()
+    n = pr.mu.size
+    Sig = pr.U.T @ np.diag(pr.lam) @ pr.U + pr.s2 * np.eye(n)
+    C = abar * Sig + (1.0 - abar) * np.eye(n)
+    x = rng.standard_normal((3, n))
+    ref = -np.linalg.solve(C, (x - np.sqrt(abar) * pr.mu).T).T
+    np.testing.assert_allclose(pr.score(x, abar), ref, rtol=1e-10, atol=1e-12)
+    # Tweedie: the clean estimate is the Gaussian conditional mean
+    # E[x0 | x] = mu + Cov(x0, x) Var(x)^-1 (x - E x), Cov(x0, x) = sqrt(abar) Sigma
+    post = pr.mu + (np.sqrt(abar) * Sig @ np.linalg.solve(C, (x - np.sqrt(abar) * pr.mu).T)).T
+    np.testing.assert_allclose(D.clean_estimate(x, pr.score(x, abar), abar), post,
+                               rtol=1e-8, atol=1e-8)
+
+
+def test_lowrank_score_vjp_and_the_diagonal_special_case():
+    pr, rng = _lowrank(seed=5)
+    n, abar = pr.mu.size, 0.2
+    x, g = rng.standard_normal((1, n)), rng.standard_normal((1, n))
+    # (ds/dx)^T g against central differences of <s(x), g>
+    h = 1e-6
+    fd = np.array([(np.sum(pr.score(x + h * e, abar) * g) - np.sum(pr.score(x - h * e, abar) * g))
+                   / (2 * h) for e in np.eye(n)[:, None, :]])
+    np.testing.assert_allclose(pr.score_vjp(g, abar)[0], fd, rtol=1e-6, atol=1e-9)
+    # no correlated directions: the diagonal prior with tau2 = s2
+    flat = D.LowRankPrior(pr.mu, np.zeros((0, n)), np.zeros(0), 0.3)
+    np.testing.assert_allclose(flat.score(x, abar),
+                               D.gaussian_score(x, abar, pr.mu, np.full(n, 0.3)), rtol=1e-14)

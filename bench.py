@@ -944,8 +944,12 @@ def run_posterior(args, rank, world, local_rank):
                             for o in range(n_obs)])
     d_obs = torch.tensor(d_clean + noise, dtype=torch.float32, device=dev)
     ctx = plan.w2_prepare(d_obs)
-    prior = S.GaussianPrior.from_models(I.model_batch("curved_faulted", range(90_000, 90_064),
-                                                      nz, nx), device=dev)
+    if args.prior == "lowrank":
+        prior = S.LowRankPrior.from_models(I.model_batch("curved_faulted", range(90_000, 90_512),
+                                                         nz, nx), k=32, device=dev)
+    else:
+        prior = S.GaussianPrior.from_models(I.model_batch("curved_faulted", range(90_000, 90_064),
+                                                          nz, nx), device=dev)
     # the 1000-step linear schedule's total noise spread over N steps
     betas = S.linear_betas(N, 1e-4 * 1000 / N, 0.02 * 1000 / N)
     # (rho0, gamma, c): the TV damping exp(-TV / c) is off (c = 1e9) because the
@@ -1096,8 +1100,10 @@ def run_posterior(args, rank, world, local_rank):
         "value": arms[best]["samples_per_s"], "unit": "posterior samples/s", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": arms[best]["chain_s"] * 1e3 / N,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded curved/faulted true models, Gaussian noise at 10 dB; Gaussian "
-                "prior fitted to 64 seeded models)",
+        "data": "synthetic (seeded curved/faulted true models, Gaussian noise at 10 dB; "
+                + ("low-rank Gaussian prior, 32 principal directions of 512 seeded models)"
+                   if args.prior == "lowrank" else
+                   "diagonal Gaussian prior fitted to 64 seeded models)"),
         "config": {"workload": f"{n_obs} observations x {P} posterior samples = {B} models per "
                                f"GPU, {N} reverse steps, W2 guidance (5 shots, 70 receivers, "
                                "1000 steps, 40-cell layer)",
@@ -1390,6 +1396,8 @@ def main():
                          "graph-replayed chains with all-FD and with gated surrogate guidance "
                          "against one eager plan per sample")
     ap.add_argument("--observations", type=int, default=4, help="--posterior: observations")
+    ap.add_argument("--prior", choices=["diag", "lowrank"], default="diag",
+                    help="--posterior: the Gaussian prior (diagonal, or 32 principal directions)")
     ap.add_argument("--samples", type=int, default=32,
                     help="--posterior: posterior samples per observation")
     ap.add_argument("--reverse-steps", type=int, default=500, help="--posterior: reverse steps")

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 11000  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 11100  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -774,6 +774,26 @@ FWI_API fwi_status fwi_ddpm_guidance_at(int batch, int ncell, const float *table
                                         const float *vjp, const float *tau2, float *g, float *h,
                                         void *stream);
 FWI_API fwi_status fwi_ddpm_step_down(int *step, void *stream);
+
+/* Score of a low-rank Gaussian prior x_0 ~ N(mu, U^T diag(lam) U + s2 I) at
+ * step i = *step of a table (fwi_ddpm_table): the step-i marginal is
+ * N(sqrt(abar_i) mu, C), C = abar_i Sigma + (1 - abar_i) I (Eq. vp_transition),
+ * and with the rows of U orthonormal
+ *   out = -C^-1 (x - sqrt(abar_i) mu)     (mu given: the score s_i(x))
+ *   out = -C^-1 x                        (mu NULL: (ds_i/dx)^T x, the score's
+ *                                          vector-Jacobian product applied to x)
+ * through the eigenvalues c_j = abar (lam_j + s2) + 1 - abar along the rows of
+ * U and c_perp = abar s2 + 1 - abar across them.  A stand-in for a trained
+ * score (the paper's is a U-Net, Sec. 6) whose samples are smooth.
+ *   U [k][ncell], lam [k], mu [ncell], x and out [batch][ncell] (fp32, device;
+ *   out may not alias x); work: batch x k floats of device scratch; k = 0 is
+ *   the isotropic prior N(mu, s2 I).  Outside 1..n_steps nothing is written.
+ * Sums in a fixed order: a second call gives the same bits.
+ * Errors: FWI_ERR_INVALID_ARG (s2 > 0, sizes, NULL pointers), FWI_ERR_CUDA. */
+FWI_API fwi_status fwi_lowrank_score_at(int batch, int ncell, int k, const float *U,
+                                        const float *lam, double s2, const float *x,
+                                        const float *mu, const float *table, const int *step,
+                                        int n_steps, float *work, float *out, void *stream);
 
 /* ---------------------------------------------------------------- learned forward surrogate
  * Data-side steps of a convolutional encoder-decoder that maps a velocity model

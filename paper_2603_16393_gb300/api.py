@@ -220,6 +220,9 @@ _lib.fwi_sur_weights_prep.restype = _S
 _lib.fwi_sur_weights_prep.argtypes = [_i, _i] + [_vp] * 4
 _lib.fwi_sur_wgrad_centre.restype = _S
 _lib.fwi_sur_wgrad_centre.argtypes = [_i, _i] + [_vp] * 3
+_lib.fwi_lowrank_score_at.restype = _S
+_lib.fwi_lowrank_score_at.argtypes = [_i, _i, _i, _vp, _vp, ctypes.c_double] + [_vp] * 4 + \
+    [_i] + [_vp] * 3
 _lib.fwi_rel_error.restype = _S
 _lib.fwi_rel_error.argtypes = [_i, ctypes.c_longlong] + [_vp] * 4
 _lib.fwi_channel_sum.restype = _S
@@ -570,6 +573,25 @@ def fwi_ddpm_guidance_at(batch, ncell, table, step, n_steps, v0hat, g_phys, vjp,
     _check(_lib.fwi_ddpm_guidance_at(batch, ncell, _ptr(table), _ptr(step), n_steps, _ptr(v0hat),
                                      _ptr(g_phys), _ptr(vjp), _ptr(tau2), _ptr(g), _ptr(h),
                                      _stream(stream)))
+
+
+def fwi_lowrank_score_at(batch, ncell, U, lam, s2, x, mu, table, step, n_steps, work, out,
+                         stream=None):
+    """Score of the low-rank Gaussian prior N(mu, U^T diag(lam) U + s2 I) at
+    step *step: out = -C^-1 (x - sqrt(abar) mu), or with mu None -C^-1 x (the
+    score's vector-Jacobian product applied to x).  U [k][ncell] (orthonormal
+    rows), lam [k], x and out [batch][ncell], work [batch][k]; fp32 device."""
+    k = 0 if U is None else U.shape[0]
+    if step.dtype != torch.int32 or step.numel() != 1 or not step.is_cuda:
+        raise ValueError("step must be one int32 on the device")
+    if k:
+        _f32(U, (k, ncell), "U")
+        _f32(lam, (k,), "lam")
+        if work is None or work.numel() < batch * k:
+            raise ValueError("work must hold batch x k floats")
+    _check(_lib.fwi_lowrank_score_at(batch, ncell, k, _ptr(U), _ptr(lam), float(s2), _ptr(x),
+                                     _ptr(mu), _ptr(table), _ptr(step), n_steps, _ptr(work),
+                                     _ptr(out), _stream(stream)))
 
 
 def fwi_ddpm_step_down(step, stream=None):

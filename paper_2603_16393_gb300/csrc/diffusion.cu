@@ -142,6 +142,69 @@ unsigned grid_for(size_t n)
 
 __global__ void k_step_down(int *step) { *step -= 1; }
 
+// Low-rank Gaussian prior, step i = *step (nothing is written outside 1..N):
+// with r = x - sqrt(abar) mu (x alone when mu is NULL), the projections
+// p_j = U_j . r scaled by 1/c_j - 1/c_perp,
+//   c_j = abar (lam_j + s2) + 1 - abar,  c_perp = abar s2 + 1 - abar.
+// One CTA per (model, direction); per-thread strided sums, then a fixed
+// tree: the same bits on every call.
+__global__ void __launch_bounds__(kThreads)
+    k_lr_project(int ncell, int k, const float *__restrict__ U, const float *__restrict__ lam,
+                 float s2, const float *__restrict__ x, const float *__restrict__ mu,
+                 const float *__restrict__ table, const int *__restrict__ step, int n_steps,
+                 float *__restrict__ q)
+{
+    __shared__ float red[kThreads];
+    const int i = *step;
+    if (i < 1 || i > n_steps) return;
+    const float *rec = table + (size_t)i * FWI_DDPM_RECORD_FLOATS;
+    const float abar = rec[0], one_m_abar = rec[1], sqrt_abar = rec[2];
+    const int b = blockIdx.x, j = blockIdx.y;
+    const float *xb = x + (size_t)b * ncell, *Uj = U + (size_t)j * ncell;
+    float acc = 0.f;
+    for (int e = threadIdx.x; e < ncell; e += kThreads) {
+        const float r = mu ? fmaf(-sqrt_abar, mu[e], xb[e]) : xb[e];
+        acc = fmaf(Uj[e], r, acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float cj = fmaf(abar, lam[j] + s2, one_m_abar);
+        const float cp = fmaf(abar, s2, one_m_abar);
+        q[(size_t)b * k + j] = red[0] * (__fdiv_rn(1.f, cj) - __fdiv_rn(1.f, cp));
+    }
+}
+
+// out = -(r / c_perp + sum_j q_j U_j): the score of the step-i marginal at x
+// (mu given), or -C^-1 x, its vector-Jacobian product applied to x (mu NULL)
+__global__ void __launch_bounds__(kThreads)
+    k_lr_apply(int batch, int ncell, int k, const float *__restrict__ U, float s2,
+               const float *__restrict__ x, const float *__restrict__ mu,
+               const float *__restrict__ q, const float *__restrict__ table,
+               const int *__restrict__ step, int n_steps, float *__restrict__ out)
+{
+    const int i = *step;
+    if (i < 1 || i > n_steps) return;
+    const float *rec = table + (size_t)i * FWI_DDPM_RECORD_FLOATS;
+    const float abar = rec[0], one_m_abar = rec[1], sqrt_abar = rec[2];
+    const float cp = fmaf(abar, s2, one_m_abar);
+    const size_t n = (size_t)batch * ncell;
+    for (size_t e = (size_t)blockIdx.x * kThreads + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * kThreads) {
+        const int c = (int)(e % ncell);
+        const size_t b = e / ncell;
+        const float r = mu ? fmaf(-sqrt_abar, mu[c], x[e]) : x[e];
+        float acc = 0.f;
+        const float *qb = q + b * k;
+        for (int j = 0; j < k; ++j) acc = fmaf(qb[j], U[(size_t)j * ncell + c], acc);
+        out[e] = -(__fdiv_rn(r, cp) + acc);
+    }
+}
+
 bool finite(double x) { return std::isfinite(x); }
 
 static_assert(sizeof(StepF) == FWI_DDPM_RECORD_FLOATS * sizeof(float) - sizeof(float),
@@ -349,6 +412,32 @@ fwi_status fwi_ddpm_step_down(int *step, void *stream)
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return fwi::record_error(FWI_ERR_CUDA, "fwi_ddpm_step_down launch: %s",
+                                 cudaGetErrorString(e));
+    return FWI_OK;
+}
+
+fwi_status fwi_lowrank_score_at(int batch, int ncell, int k, const float *U, const float *lam,
+                                double s2, const float *x, const float *mu, const float *table,
+                                const int *step, int n_steps, float *work, float *out,
+                                void *stream)
+{
+    if (batch < 1 || ncell < 1 || k < 0 || k > 65535 || n_steps < 1 || !(s2 > 0.0) ||
+        !std::isfinite(s2))
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "batch, ncell, n_steps >= 1, 0 <= k <= 65535 and s2 > 0 needed");
+    if (!x || !table || !step || !out || (k > 0 && (!U || !lam || !work)))
+        return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                 "x, table, step, out (and U, lam, work when k > 0) must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (k > 0)
+        k_lr_project<<<dim3((unsigned)batch, (unsigned)k), kThreads, 0, st>>>(
+            ncell, k, U, lam, (float)s2, x, mu, table, step, n_steps, work);
+    const size_t n = (size_t)batch * (size_t)ncell;
+    k_lr_apply<<<grid_for(n), kThreads, 0, st>>>(batch, ncell, k, U, (float)s2, x, mu, work,
+                                                 table, step, n_steps, out);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fwi::record_error(FWI_ERR_CUDA, "fwi_lowrank_score_at launch: %s",
                                  cudaGetErrorString(e));
     return FWI_OK;
 }

@@ -64,6 +64,42 @@ class GaussianPrior:
                    torch.tensor(tau2, dtype=torch.float32, device=dev))
 
 
+@dataclasses.dataclass
+class LowRankPrior:
+    """x_0 ~ N(mu, U^T diag(lam) U + s2 I) in the normalised space: the mean and
+    the k leading principal directions of a set of models over an isotropic
+    floor s2 (fwi_lowrank_score_at gives the score of its step-i marginal).
+    Its samples are smooth where the diagonal prior's are rough cell by cell.
+    ``mu`` [nz][nx], ``U`` [k][nz nx] (orthonormal rows), ``lam`` [k]: float32
+    device tensors."""
+    mu: torch.Tensor
+    U: torch.Tensor
+    lam: torch.Tensor
+    s2: float
+
+    @classmethod
+    def from_models(cls, models, k: int = 32, space: api.DiffusionSpace = api.DiffusionSpace(),
+                    floor: float = 1e-3, device=None) -> "LowRankPrior":
+        """Principal components of velocity models [M][nz][nx] (m/s, host or
+        device) in the normalised space: lam_j = S_j^2 / (M - 1) of the k
+        largest singular values S_j of the centred models, s2 = the rest of the
+        per-cell variance spread over the other directions, at least
+        ``floor`` (fit on the host: set-up, not a step of the chain)."""
+        m = np.asarray(models.cpu() if torch.is_tensor(models) else models, dtype=np.float64)
+        M = m.shape[0]
+        x = ((m - space.shift) / space.unit).reshape(M, -1)
+        mu = x.mean(axis=0)
+        _, S, Vt = np.linalg.svd(x - mu, full_matrices=False)
+        k = min(k, Vt.shape[0])
+        lam = S[:k] ** 2 / (M - 1)
+        rest = float(np.sum(S[k:] ** 2) / (M - 1)) / max(x.shape[1] - k, 1)
+        dev = device or torch.device("cuda")
+        f32 = dict(dtype=torch.float32, device=dev)
+        return cls(torch.tensor(mu.reshape(m.shape[1:]), **f32),
+                   torch.tensor(np.ascontiguousarray(Vt[:k]), **f32),
+                   torch.tensor(lam, **f32), max(rest, floor))
+
+
 class LowFidelity:
     """The low-fidelity guidance surrogate (the multi-fidelity route to cheaper
     physics guidance, Sec. 7): the W2 potential of the problem coarsened by
@@ -221,7 +257,9 @@ class Sampler:
 
 
 class GraphChain:
-    """Algorithm 2 with the Gaussian prior, one CUDA graph per kind of reverse
+    """Algorithm 2 with a Gaussian prior (diagonal, GaussianPrior, or low-rank,
+    LowRankPrior: its score and the score's vector-Jacobian product from
+    fwi_lowrank_score_at), one CUDA graph per kind of reverse
     step.  The step index lives in device memory (the step's last launch
     decrements it), the coefficients in a device table (api.ddpm_table) and the
     draws of every step in ``zs`` [N + 1][B][nz][nx] (row i for step i), so the
@@ -239,7 +277,8 @@ class GraphChain:
     ``check_every`` steps and "sur" between checks until a check's largest
     error exceeds ``threshold``, then "fd" for the rest (FD as fallback)."""
 
-    def __init__(self, plan: api.Plan, betas: Sequence[float], ctx, prior: GaussianPrior,
+    def __init__(self, plan: api.Plan, betas: Sequence[float], ctx,
+                 prior: GaussianPrior | LowRankPrior,
                  guide: api.GuideParams, zs: torch.Tensor,
                  space: api.DiffusionSpace = api.DiffusionSpace(),
                  sigma_mode: int = api.SIGMA_POSTERIOR, surrogate=None,
@@ -256,6 +295,10 @@ class GraphChain:
         self.step = torch.full((1,), self.N, dtype=torch.int32, device=dev)
         new = lambda: torch.empty((B, nz, nx), dtype=torch.float32, device=dev)  # noqa: E731
         self.v, self.v0hat, self.v_prime, self.v_phys, self.g, self.h = (new() for _ in range(6))
+        self.lowrank = isinstance(prior, LowRankPrior)
+        if self.lowrank:
+            self.score, self.u = new(), new()
+            self.work = torch.empty(max(1, B * prior.U.shape[0]), dtype=torch.float32, device=dev)
         self.surrogate = surrogate
         self.i_switch = self.N - int(round(surrogate_fraction * self.N)) if surrogate else self.N
         self.threshold, self.check_every = float(threshold), int(check_every)
@@ -265,10 +308,17 @@ class GraphChain:
         self.counts = {"fd": 0, "sur": 0, "check": 0}
 
     def _launches(self, kind: str, stream):
-        B, n, N = self.B, self.ncell, self.N
-        api.fwi_ddpm_proposal_at(B, n, self.table, self.step, N, self.v, None, self.prior.mu,
-                                 self.prior.tau2, self.zs, B * n, self.v0hat, self.v_prime,
-                                 self.v_phys, stream)
+        B, n, N, P = self.B, self.ncell, self.N, self.prior
+        if self.lowrank:
+            api.fwi_lowrank_score_at(B, n, P.U, P.lam, P.s2, self.v, P.mu, self.table, self.step,
+                                     N, self.work, self.score, stream)
+            api.fwi_ddpm_proposal_at(B, n, self.table, self.step, N, self.v, self.score, None,
+                                     None, self.zs, B * n, self.v0hat, self.v_prime, self.v_phys,
+                                     stream)
+        else:
+            api.fwi_ddpm_proposal_at(B, n, self.table, self.step, N, self.v, None, P.mu, P.tau2,
+                                     self.zs, B * n, self.v0hat, self.v_prime, self.v_phys,
+                                     stream)
         if kind == "sur":
             _, g_phys = self.surrogate.gradient(self.v_phys, stream=stream)
         else:
@@ -276,8 +326,17 @@ class GraphChain:
             if kind == "check":
                 _, g_sur = self.surrogate.gradient(self.v_phys, stream=stream)
                 api.fwi_rel_error(g_sur, g_phys, self.err, stream)
-        api.fwi_ddpm_guidance_at(B, n, self.table, self.step, N, self.v0hat, g_phys, None,
-                                 self.prior.tau2, self.g, self.h, stream)
+        if self.lowrank:
+            # g first, then the score's vector-Jacobian product of g, then h
+            api.fwi_ddpm_guidance_at(B, n, self.table, self.step, N, self.v0hat, g_phys, None,
+                                     None, self.g, self.h, stream)
+            api.fwi_lowrank_score_at(B, n, P.U, P.lam, P.s2, self.g, None, self.table,
+                                     self.step, N, self.work, self.u, stream)
+            api.fwi_ddpm_guidance_at(B, n, self.table, self.step, N, self.v0hat, g_phys, self.u,
+                                     None, self.g, self.h, stream)
+        else:
+            api.fwi_ddpm_guidance_at(B, n, self.table, self.step, N, self.v0hat, g_phys, None,
+                                     P.tau2, self.g, self.h, stream)
         api.guided_step(self.v_prime, self.v0hat, self.g, self.h, self.gparams, v_out=self.v,
                         stream=stream)
         api.fwi_ddpm_step_down(self.step, stream)

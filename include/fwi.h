@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 11100  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 11200  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -127,14 +127,16 @@ enum {
     FWI_SHAPE_RESIDENT_COLUMNS = 2,  /* resident: one column x 22 rows a thread        */
     FWI_SHAPE_CLUSTER_RS13 = 3,      /* cluster: one column x 13-row thread strips     */
     FWI_SHAPE_CLUSTER_RS19 = 4,      /* cluster: one column x 19-row thread strips     */
-    FWI_SHAPE_TILED_ROWS8 = 5,       /* tiled: 8 rows a thread, 256 threads a 32 x 64 tile
-                                        (default)                                       */
+    FWI_SHAPE_TILED_ROWS8 = 5,       /* tiled: 8 rows a thread, 256 threads a 32 x 64 tile */
     FWI_SHAPE_TILED_ROWS4 = 6,       /* tiled: 4 rows a thread, 512 threads a tile      */
-    FWI_SHAPE_CLUSTER_PAIRS = 7      /* cluster: two columns x 10 rows a thread, packed
+    FWI_SHAPE_CLUSTER_PAIRS = 7,     /* cluster: two columns x 10 rows a thread, packed
                                         f32x2 arithmetic, the adjoint's per-cell arrays
                                         in tensor memory (default where the padded width
                                         is even and the strips fit 672 threads; else 13-,
                                         then 19-row single-column strips)               */
+    FWI_SHAPE_TILED_QUADS = 8        /* tiled: four columns x 2 rows a thread, 256 threads
+                                        a tile, 16-byte (float4) loads and stores
+                                        (default; the same bits as the row shapes)     */
 };
 
 /* Absorbing layers (fwi_problem.absorber). */

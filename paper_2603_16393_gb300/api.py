@@ -36,7 +36,8 @@ FWI_ERR_OOM = 6
 KERNELS_AUTO, KERNELS_RESIDENT, KERNELS_TILED, KERNELS_CLUSTER, KERNELS_CPML = 0, 1, 2, 3, 4
 ABSORBER_SPONGE, ABSORBER_CPML = 0, 1
 (SHAPE_DEFAULT, SHAPE_RESIDENT_PAIRS, SHAPE_RESIDENT_COLUMNS, SHAPE_CLUSTER_RS13,
- SHAPE_CLUSTER_RS19, SHAPE_TILED_ROWS8, SHAPE_TILED_ROWS4, SHAPE_CLUSTER_PAIRS) = range(8)
+ SHAPE_CLUSTER_RS19, SHAPE_TILED_ROWS8, SHAPE_TILED_ROWS4, SHAPE_CLUSTER_PAIRS,
+ SHAPE_TILED_QUADS) = range(9)
 SIGMA_POSTERIOR, SIGMA_BETA = 0, 1
 FWI_MAX_SHOTS = 256
 FWI_MAX_RECEIVERS = 1024

@@ -90,7 +90,7 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     if (!(w2->eps_density >= 0.0) || !std::isfinite(w2->eps_density))
         return fail(FWI_ERR_INVALID_ARG, "eps_density must be >= 0");
     if (w2->squared != 0 && w2->squared != 1) return fail(FWI_ERR_INVALID_ARG, "squared must be 0 or 1");
-    if (p.shape < FWI_SHAPE_DEFAULT || p.shape > FWI_SHAPE_CLUSTER_PAIRS)
+    if (p.shape < FWI_SHAPE_DEFAULT || p.shape > FWI_SHAPE_TILED_QUADS)
         return fail(FWI_ERR_INVALID_ARG, "shape %d is not an FWI_SHAPE_* value", p.shape);
     if (p.kernels < FWI_KERNELS_AUTO || p.kernels > FWI_KERNELS_CPML)
         return fail(FWI_ERR_INVALID_ARG, "kernels must be 0 (auto), 1, 2, 3 or 4");
@@ -118,6 +118,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
     pl->adj_pair = false;
     pl->tiled = false;
     pl->tile_rows = p.shape == FWI_SHAPE_TILED_ROWS4 ? 4 : 8;
+    // tiled: float4 column quads unless a scalar row shape is asked for
+    pl->tile_quads = p.shape != FWI_SHAPE_TILED_ROWS8 && p.shape != FWI_SHAPE_TILED_ROWS4;
     pl->p = p;
     pl->p.space_order = order;
     pl->w2 = *w2;
@@ -326,7 +328,8 @@ fwi_status fwi_plan_create(const fwi_problem *prob, const fwi_w2_params *w2, fwi
                  sh == FWI_SHAPE_CLUSTER_PAIRS;
         } else if (pl->tiled) {
             family = "tiled";
-            ok = ok || sh == FWI_SHAPE_TILED_ROWS8 || sh == FWI_SHAPE_TILED_ROWS4;
+            ok = ok || sh == FWI_SHAPE_TILED_ROWS8 || sh == FWI_SHAPE_TILED_ROWS4 ||
+                 sh == FWI_SHAPE_TILED_QUADS;
         }
         if (!ok) {
             delete pl;

@@ -5,7 +5,7 @@
 // for the CPML absorber its own kernels) and every thread shape of the
 // family (fwi_problem.shape: column pairs or single columns for the resident
 // kernels, column pairs or 13- or 19-row single-column strips for the cluster
-// kernels, 8 or 4 rows a thread for the tiled kernels) it
+// kernels, 8 or 4 rows a thread or float4 column quads for the tiled kernels) it
 // creates plans on two shortened time axes (T and 2T steps), times one
 // gradient pass (forward with the record, adjoint) on each after an untimed
 // one, in caller-provided scratch, and predicts the pass at the problem's nt
@@ -28,7 +28,7 @@ constexpr int kFamilies[4] = {FWI_KERNELS_RESIDENT, FWI_KERNELS_TILED, FWI_KERNE
 constexpr int kMaxShapes = 3;
 constexpr int kShapes[4][kMaxShapes] = {
     {FWI_SHAPE_RESIDENT_PAIRS, FWI_SHAPE_RESIDENT_COLUMNS, -1},
-    {FWI_SHAPE_TILED_ROWS8, FWI_SHAPE_TILED_ROWS4, -1},
+    {FWI_SHAPE_TILED_QUADS, FWI_SHAPE_TILED_ROWS8, FWI_SHAPE_TILED_ROWS4},
     {FWI_SHAPE_CLUSTER_PAIRS, FWI_SHAPE_CLUSTER_RS13, FWI_SHAPE_CLUSTER_RS19},
     {FWI_SHAPE_DEFAULT, -1, -1}};
 

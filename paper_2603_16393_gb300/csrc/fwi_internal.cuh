@@ -88,7 +88,8 @@ struct Plan {
     int rec_pitch;             // row pitch of a record plane
     bool fwd_pair;             // forward on column pairs (even padded width)
     bool adj_pair;             // adjoint on column pairs (same condition)
-    int tile_rows;             // tiled: rows a thread (8 or 4)
+    int tile_rows;             // tiled, scalar threads: rows a thread (8 or 4)
+    bool tile_quads;           // tiled: four columns x 2 rows a thread, 16-byte accesses (default)
     int fast_P, fast_PR, fast_NZM;  // their shared-memory pitch, record pitch, row capacity
     int nzs;                   // rows of one wavefield-record plane (>= NZ)
     // byte offsets inside the caller buffers

@@ -11,8 +11,11 @@
 // The fields of every (model, shot) live in global memory, [bs][NZ][NXp]
 // with NXp = NX rounded up to a multiple of 4 (16-byte rows; the pad columns
 // stay zero).  One launch advances all (model, shot) pairs by one time step.
-// A CTA owns a 32 x 64 tile: thread (tx, g) owns column x0 + tx and rows
-// z0 + 8g .. z0 + 8g + 7 and keeps a z window in registers.  The current
+// A CTA owns a 32 x 64 tile.  By default a thread owns four adjacent columns
+// and two rows and moves them with 16-byte (float4) loads and stores (the
+// column quads below); the scalar shapes give thread (tx, g) column x0 + tx
+// and rows z0 + 8g .. z0 + 8g + 7 (or 4 rows).  Either keeps a z window in
+// registers, with the same operations per cell, so the same bits.  The current
 // level's halo tile (36 x 72 cells; it starts at x0 - 4 so that the copy
 // starts on a 16-byte boundary) is moved into shared memory by one
 // cp.async.bulk.tensor load completing on an mbarrier; the tensor's
@@ -257,6 +260,262 @@ __global__ void __launch_bounds__(tile_threads<TRW>()) k_tile_fwd(const __grid_c
             ub[i] = un;
             vb[i] = vn;
             if (STORE) rb[i] = lap;
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) w[k] = w[k + 1];
+    }
+}
+
+// ------------------------------------------------------------------ column quads
+// The same steps with a thread owning four adjacent columns x .. x+3 (x a
+// multiple of 4) and QR rows: 16-byte loads of the per-cell operands and
+// 16-byte stores of the new level, the increment and the record, the
+// stencil's centre row as one 16-byte shared-memory load and its x arms as
+// 8- (4th order) or 16-byte (8th order) loads.  Per cell the operations and
+// their order are those of k_tile_fwd / k_tile_adj, so the results are the
+// same bits.  A quad that reaches the pad columns (x + 3 >= NX, < NXp) writes
+// them too: their tables are zero, so u and its increment stay zero there,
+// and no step reads their record or imaging sums.
+constexpr int QR = 2;                                   // rows a quad thread owns
+constexpr int kQuadThreads = (TX / 4) * (TZ / QR);      // 256
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float &q4(float4 &v, int q) { return (&v.x)[q]; }
+__device__ __forceinline__ float q4c(const float4 &v, int q) { return (&v.x)[q]; }
+
+// the row of u around the quad: u[x - R .. x + 3 + R] (centre at e[R .. R + 3])
+template <int R>
+__device__ __forceinline__ void row_arms(const float *c, float (&e)[4 + 2 * R])
+{
+    const float4 m = ld4(c);
+    if (R == 2) {
+        const float2 l = *reinterpret_cast<const float2 *>(c - 2);
+        const float2 r = *reinterpret_cast<const float2 *>(c + 4);
+        e[0] = l.x; e[1] = l.y; e[6] = r.x; e[7] = r.y;
+    } else {
+        const float4 l = ld4(c - 4), r = ld4(c + 4);
+        e[0] = l.x; e[1] = l.y; e[2] = l.z; e[3] = l.w;
+        e[8] = r.x; e[9] = r.y; e[10] = r.z; e[11] = r.w;
+    }
+    e[R] = m.x; e[R + 1] = m.y; e[R + 2] = m.z; e[R + 3] = m.w;
+}
+
+template <int R, int TOPBC, bool STORE>
+__global__ void __launch_bounds__(kQuadThreads) k_tile_fwd4(const __grid_constant__ CUtensorMap tm,
+                                                            const __grid_constant__ TileArgs a)
+{
+    constexpr int HZ = halo_rows<R>();
+    __shared__ __align__(128) float tile[HZ * HX];
+    __shared__ __align__(8) uint64_t mbar;
+    const int tid = threadIdx.x, tq = tid % (TX / 4), g = tid / (TX / 4);
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, bs = blockIdx.z;
+    const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    if (tid == 0) mbar_init(&mbar);
+    __syncthreads();
+    if (tid == 0 && !a.withhold) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
+
+    const int x = x0 + 4 * tq, zr = z0 + g * QR;
+    const bool quadok = x < a.NXp;
+    const size_t plane = (size_t)a.NZ * a.NXp;
+    const float *kab = a.ka + (size_t)b * plane, *abb = a.ab + (size_t)b * plane;
+    float *vb = a.vinc + (size_t)bs * plane;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 ka[QR], ab[QR], vi[QR];
+#pragma unroll
+    for (int r = 0; r < QR; ++r) {
+        const int z = zr + r;
+        const bool ok = quadok && z < a.NZ;
+        const size_t i = (size_t)z * a.NXp + x;
+        ka[r] = ok ? ld4(kab + i) : zero4;
+        ab[r] = ok ? ld4(abb + i) : zero4;
+        vi[r] = ok ? ld4(vb + i) : zero4;
+    }
+    if (!tile_wait(&mbar, a.status, a.wait_polls)) return;
+    if (TOPBC == 1 && z0 == 0) {
+        for (int c = tid; c < HX; c += kQuadThreads) {
+#pragma unroll
+            for (int k = 1; k <= R; ++k) tile[(R - k) * HX + c] = tile[(R + k) * HX + c];
+        }
+        __syncthreads();
+    }
+    if (a.d_syn && a.j > 0 && z0 <= a.rzmax && z0 + TZ > a.rzmin) {
+        for (int r = tid; r < a.nr; r += kQuadThreads) {
+            const int pz = a.rec[r] >> 16, px = a.rec[r] & 0xffff;
+            if (pz >= z0 && pz < z0 + TZ && px >= x0 && px < x0 + TX)
+                a.d_syn[((size_t)bs * a.nr + r) * a.nt + a.j - 1] =
+                    tile[(pz - z0 + R) * HX + px - x0 + 4];
+        }
+    }
+    if (a.ckpt && a.j % a.ckpt_every == 0) {
+        const size_t cells = (size_t)a.NZ * a.NX;
+        float *st = a.ckpt + ((size_t)(a.j / a.ckpt_every) * gridDim.z + bs) * 2 * cells;
+#pragma unroll
+        for (int r = 0; r < QR; ++r) {
+            const int z = zr + r;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (x + q < a.NX && z < a.NZ) {
+                    st[(size_t)z * a.NX + x + q] = tile[(z - z0 + R) * HX + 4 * tq + q + 4];
+                    st[cells + (size_t)z * a.NX + x + q] = q4c(vi[r], q);
+                }
+            }
+        }
+    }
+
+    const int sp = a.src[s], sz = sp >> 16, sx = sp & 0xffff;
+    float *ub = a.unext + (size_t)bs * plane;
+    float *rb = STORE ? a.rec_out + ((size_t)bs * a.rec_planes + (a.j - a.rec_base)) * plane
+                      : nullptr;
+    const float *cp = tile + (g * QR + R) * HX + 4 * tq + 4;
+    float4 w[2 * R + 1];     // z window: w[R + k] = row z + k, four columns
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) w[k] = ld4(cp + (k - R) * HX);
+#pragma unroll
+    for (int r = 0; r < QR; ++r) {
+        const float *c = cp + r * HX;
+        w[2 * R] = ld4(c + R * HX);
+        float e[4 + 2 * R];
+        row_arms<R>(c, e);
+        float4 lap4, vn4, un4;
+        const int z = zr + r;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float w0 = e[R + q];
+            float lap = a.cxm[0] * ((e[R + q - 1] - w0) + (e[R + q + 1] - w0));
+#pragma unroll
+            for (int m = 2; m <= R; ++m)
+                lap = fmaf(a.cxm[m - 1], (e[R + q - m] - w0) + (e[R + q + m] - w0), lap);
+#pragma unroll
+            for (int m = 1; m <= R; ++m)
+                lap = fmaf(a.czm[m - 1], (q4c(w[R - m], q) - w0) + (q4c(w[R + m], q) - w0), lap);
+            float vn = fmaf(q4c(ka[r], q), lap, q4c(ab[r], q) * q4c(vi[r], q));
+            float un = w0 + vn;
+            if (z == sz && x + q == sx) {
+                // point source: + kappa A s at the source cell (increment and field)
+                const float d = q4c(ka[r], q) * dev::ricker_scaled(a.j, a);
+                vn += d;
+                un += d;
+            }
+            q4(lap4, q) = lap;
+            q4(vn4, q) = vn;
+            q4(un4, q) = un;
+        }
+        if (quadok && z < a.NZ) {
+            const size_t i = (size_t)z * a.NXp + x;
+            st4(ub + i, un4);
+            st4(vb + i, vn4);
+            if (STORE) st4(rb + i, lap4);
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * R; ++k) w[k] = w[k + 1];
+    }
+}
+
+template <int R, int TOPBC>
+__global__ void __launch_bounds__(kQuadThreads) k_tile_adj4(const __grid_constant__ CUtensorMap tm,
+                                                            const __grid_constant__ TileArgs a)
+{
+    constexpr int HZ = halo_rows<R>();
+    __shared__ __align__(128) float tile[HZ * HX];
+    __shared__ __align__(16) float inj[TZ * TX];
+    __shared__ __align__(8) uint64_t mbar;
+    const int tid = threadIdx.x, tq = tid % (TX / 4), g = tid / (TX / 4);
+    const int x0 = blockIdx.x * TX, z0 = blockIdx.y * TZ, bs = blockIdx.z;
+    const int b = bs / a.ns, s = bs - (bs / a.ns) * a.ns;
+    if (tid == 0) mbar_init(&mbar);
+    __syncthreads();
+    if (tid == 0 && !a.withhold) tile_load(tile, &mbar, &tm, x0 - 4, z0 - R, bs, HZ * HX * sizeof(float));
+
+    const int x = x0 + 4 * tq, zr = z0 + g * QR;
+    const bool quadok = x < a.NXp;
+    const size_t plane = (size_t)a.NZ * a.NXp;
+    const float *kab = a.ka + (size_t)b * plane, *abb = a.ab + (size_t)b * plane;
+    float *wb = a.vinc + (size_t)bs * plane, *accb = a.acc + (size_t)bs * plane;
+    float *pn = a.unext + (size_t)bs * plane;
+    const float *rb =
+        a.rec_in + ((size_t)bs * a.rec_planes + (a.nt - 1 - a.j - a.rec_base)) * plane;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 ka[QR], ab[QR], wi[QR], ac[QR], sv[QR];
+#pragma unroll
+    for (int r = 0; r < QR; ++r) {
+        const int z = zr + r;
+        const bool ok = quadok && z < a.NZ;
+        const size_t i = (size_t)z * a.NXp + x;
+        ka[r] = ok ? ld4(kab + i) : zero4;
+        ab[r] = ok ? ld4(abb + i) : zero4;
+        wi[r] = ok ? ld4(wb + i) : zero4;
+        ac[r] = ok ? ld4(accb + i) : zero4;
+        sv[r] = ok ? ld4(rb + i) : zero4;
+    }
+    const bool has_rec = z0 <= a.rzmax && z0 + TZ > a.rzmin;
+    if (has_rec) {
+#pragma unroll
+        for (int r = 0; r < QR; ++r) st4(inj + (g * QR + r) * TX + 4 * tq, zero4);
+    }
+    if (!tile_wait(&mbar, a.status, a.wait_polls)) return;
+    if (has_rec) {
+        for (int r = tid; r < a.nr; r += kQuadThreads) {
+            const int pz = a.rec[r] >> 16, px = a.rec[r] & 0xffff;
+            if (pz >= z0 && pz < z0 + TZ && px >= x0 && px < x0 + TX)
+                inj[(pz - z0) * TX + px - x0] =
+                    a.adj[((size_t)bs * a.nr + r) * a.nt + (a.nt - 1 - a.j)];
+        }
+        __syncthreads();
+    }
+
+    const int sp = a.src[s], sz = sp >> 16, sx = sp & 0xffff;
+    const float *cp = tile + (g * QR + R) * HX + 4 * tq + 4;
+    float4 w[2 * R + 1];
+#pragma unroll
+    for (int k = 0; k < 2 * R; ++k) w[k] = ld4(cp + (k - R) * HX);
+#pragma unroll
+    for (int r = 0; r < QR; ++r) {
+        const float *c = cp + r * HX;
+        w[2 * R] = ld4(c + R * HX);
+        float e[4 + 2 * R];
+        row_arms<R>(c, e);
+        const int z = zr + r;
+        const float4 in4 = has_rec ? ld4(inj + (g * QR + r) * TX + 4 * tq) : zero4;
+        float4 pn4, wn4, ac4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float w0 = e[R + q];
+            float lap = a.cxm[0] * ((e[R + q - 1] - w0) + (e[R + q + 1] - w0));
+#pragma unroll
+            for (int m = 2; m <= R; ++m)
+                lap = fmaf(a.cxm[m - 1], (e[R + q - m] - w0) + (e[R + q + m] - w0), lap);
+#pragma unroll
+            for (int m = 1; m <= R; ++m)
+                lap = fmaf(a.czm[m - 1], (q4c(w[R - m], q) - w0) + (q4c(w[R + m], q) - w0), lap);
+            if (TOPBC == 1 && z0 == 0) {
+                // transpose of the mirrored top: rows 0..R-z reflect onto row z
+                // (grid rows 1..R may lie in this thread's rows or the next ones')
+#pragma unroll
+                for (int zz = 1; zz <= R; ++zz) {
+                    if (z == zz) {
+                        float extra = 0.f;
+#pragma unroll
+                        for (int r0 = 0; r0 <= R - zz; ++r0)
+                            extra = fmaf(a.czm[r0 + zz - 1], q4c(w[R + r0 - zz], q), extra);
+                        lap += extra;
+                    }
+                }
+            }
+            float wn = fmaf(q4c(ka[r], q), lap, q4c(ab[r], q) * q4c(wi[r], q));
+            if (has_rec) wn = fmaf(q4c(ka[r], q), q4c(in4, q), wn);
+            const float pnv = w0 + wn;
+            q4(pn4, q) = pnv;
+            q4(wn4, q) = wn;
+            q4(ac4, q) = fmaf(pnv, q4c(sv[r], q), q4c(ac[r], q));
+            if (quadok && z < a.NZ && z == sz && x + q == sx)
+                a.acc_src[bs] = fmaf(pnv, dev::ricker_scaled(a.nt - 1 - a.j, a), a.acc_src[bs]);
+        }
+        if (quadok && z < a.NZ) {
+            const size_t i = (size_t)z * a.NXp + x;
+            st4(pn + i, pn4);
+            st4(wb + i, wn4);
+            st4(accb + i, ac4);
         }
 #pragma unroll
         for (int k = 0; k < 2 * R; ++k) w[k] = w[k + 1];
@@ -581,7 +840,17 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
         if (store) tb ? FWI_TFWD(2, 1, true, TR) : FWI_TFWD(2, 0, true, TR);                   \
         else tb ? FWI_TFWD(2, 1, false, TR) : FWI_TFWD(2, 0, false, TR);                       \
     }
-            if (pl.tile_rows == 4) {
+            if (pl.tile_quads) {
+#define FWI_TFWD4(RR, TB, ST) k_tile_fwd4<RR, TB, ST><<<grid, kQuadThreads, 0, st>>>(maps[j & 1], s)
+                if (R == 4) {
+                    if (store) tb ? FWI_TFWD4(4, 1, true) : FWI_TFWD4(4, 0, true);
+                    else tb ? FWI_TFWD4(4, 1, false) : FWI_TFWD4(4, 0, false);
+                } else {
+                    if (store) tb ? FWI_TFWD4(2, 1, true) : FWI_TFWD4(2, 0, true);
+                    else tb ? FWI_TFWD4(2, 1, false) : FWI_TFWD4(2, 0, false);
+                }
+#undef FWI_TFWD4
+            } else if (pl.tile_rows == 4) {
                 FWI_TFWD_R(4)
             } else {
                 FWI_TFWD_R(8)
@@ -621,13 +890,18 @@ cudaError_t launch_tiled(const Plan &pl, bool adj, const PropArgs &a, unsigned c
         s.j = j;
         s.unext = t.p[(j + 1) & 1];
 #define FWI_TADJ(RR, TB, TR) k_tile_adj<RR, TB, TR><<<grid, tile_threads<TR>(), 0, st>>>(maps[j & 1], s)
-        if (pl.tile_rows == 4) {
+#define FWI_TADJ4(RR, TB) k_tile_adj4<RR, TB><<<grid, kQuadThreads, 0, st>>>(maps[j & 1], s)
+        if (pl.tile_quads) {
+            if (R == 4) tb ? FWI_TADJ4(4, 1) : FWI_TADJ4(4, 0);
+            else tb ? FWI_TADJ4(2, 1) : FWI_TADJ4(2, 0);
+        } else if (pl.tile_rows == 4) {
             if (R == 4) tb ? FWI_TADJ(4, 1, 4) : FWI_TADJ(4, 0, 4);
             else tb ? FWI_TADJ(2, 1, 4) : FWI_TADJ(2, 0, 4);
         } else {
             if (R == 4) tb ? FWI_TADJ(4, 1, 8) : FWI_TADJ(4, 0, 8);
             else tb ? FWI_TADJ(2, 1, 8) : FWI_TADJ(2, 0, 8);
         }
+#undef FWI_TADJ4
 #undef FWI_TADJ
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

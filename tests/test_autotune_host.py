@@ -22,7 +22,8 @@ def _up(n):
 
 
 SHAPES = {api.KERNELS_RESIDENT: (api.SHAPE_RESIDENT_PAIRS, api.SHAPE_RESIDENT_COLUMNS),
-          api.KERNELS_TILED: (api.SHAPE_TILED_ROWS8, api.SHAPE_TILED_ROWS4),
+          api.KERNELS_TILED: (api.SHAPE_TILED_ROWS8, api.SHAPE_TILED_ROWS4,
+                              api.SHAPE_TILED_QUADS),
           api.KERNELS_CLUSTER: (api.SHAPE_CLUSTER_PAIRS, api.SHAPE_CLUSTER_RS13,
                             api.SHAPE_CLUSTER_RS19),
           api.KERNELS_CPML: (api.SHAPE_DEFAULT,)}
@@ -96,7 +97,7 @@ def test_shapes_belong_to_their_family():
                                     api.W2Params())
             assert e.value.code == 3 and "shape" in str(e.value)
     with pytest.raises(api.FwiError) as e:
-        api.fwi_plan_create(dataclasses.replace(prob, shape=8), api.W2Params())
+        api.fwi_plan_create(dataclasses.replace(prob, shape=9), api.W2Params())
     assert e.value.code == 1
     # an odd padded width has no column pairs
     odd = _prob(nx=69, src_ix=(0, 17, 34, 51, 68), rec_ix=tuple(range(69)), rec_iz=(0,) * 69)

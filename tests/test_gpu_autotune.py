@@ -37,7 +37,8 @@ def test_autotune_times_every_family_and_picks_the_fastest(api, nz, nx, nb, n_fa
     scratch = torch.empty(n, dtype=torch.uint8, device=DEV)
     fams = [api.KERNELS_RESIDENT, api.KERNELS_TILED, api.KERNELS_CLUSTER, api.KERNELS_CPML]
     family_shapes = {api.KERNELS_RESIDENT: (api.SHAPE_RESIDENT_PAIRS, api.SHAPE_RESIDENT_COLUMNS),
-                     api.KERNELS_TILED: (api.SHAPE_TILED_ROWS8, api.SHAPE_TILED_ROWS4),
+                     api.KERNELS_TILED: (api.SHAPE_TILED_ROWS8, api.SHAPE_TILED_ROWS4,
+                                         api.SHAPE_TILED_QUADS),
                      api.KERNELS_CLUSTER: (api.SHAPE_CLUSTER_PAIRS, api.SHAPE_CLUSTER_RS13,
                                            api.SHAPE_CLUSTER_RS19)}
     for _ in range(2):                      # twice in a row on the same scratch

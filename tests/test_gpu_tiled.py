@@ -41,19 +41,25 @@ def H(t):
     return t.double().cpu().numpy()
 
 
-FAMILIES = ("tiled", "cluster", "cluster_columns")
+FAMILIES = ("tiled", "tiled_quads", "cluster", "cluster_columns")
 
 
 def _fam(api, name):
-    return {"tiled": api.KERNELS_TILED, "cluster": api.KERNELS_CLUSTER,
-            "cluster_columns": api.KERNELS_CLUSTER}[name]
+    return {"tiled": api.KERNELS_TILED, "tiled_quads": api.KERNELS_TILED,
+            "cluster": api.KERNELS_CLUSTER, "cluster_columns": api.KERNELS_CLUSTER}[name]
 
 
 def _forced(api, gp, fam):
     """gp on the family `fam`: "cluster" takes the default shape (column pairs
     where the padded width is even), "cluster_columns" the single-column
-    strips (13 rows where they fit, else 19)."""
+    strips (13 rows where they fit, else 19), "tiled" the scalar 8-row threads
+    and "tiled_quads" the float4 column quads (the default) of the tiled
+    kernels."""
     gp = dataclasses.replace(gp, kernels=_fam(api, fam))
+    if fam == "tiled_quads":
+        return dataclasses.replace(gp, shape=api.SHAPE_TILED_QUADS)
+    if fam == "tiled":
+        return dataclasses.replace(gp, shape=api.SHAPE_TILED_ROWS8)
     if fam != "cluster_columns":
         return gp
     try:
@@ -219,9 +225,34 @@ def test_cluster_gradient_agrees_with_the_tiled_gradient(api, top_bc):
     # transposed correction leaves its two products to the compiler's
     # contraction in the single-column adjoint, a rounding difference at rows
     # 1 and 2 every step (1.7e-5 measured after 400 steps): the gradient bar
+    # the tiled kernels' column quads: the same operations per cell, the same bits
+    for k in range(3):
+        assert np.array_equal(res["tiled_quads"][k], res["tiled"][k])
     assert np.array_equal(res["cluster"][0], res["cluster_columns"][0])
     if top_bc == 0:
         assert np.array_equal(res["cluster"][1], res["cluster_columns"][1])
         assert np.array_equal(res["cluster"][2], res["cluster_columns"][2])
     else:
         assert rel_l2(res["cluster"][2], res["cluster_columns"][2]) <= TOL_GRAD
+
+
+@pytest.mark.parametrize("top_bc", [0, 1])
+@pytest.mark.parametrize("order", [4, 8])
+def test_tiled_quads_are_bitwise_the_scalar_tiled_kernels(api, order, top_bc):
+    # data, J and dJ/dv of the float4 column quads against the 8-row scalar
+    # threads, with checkpoints (K = 13) so that resume and recompute run too
+    nz, nx, nb, nt, ns = 45, 77, 9, 200, 2       # 54 x 95 cells: ragged tiles, pad columns
+    gp, _ = problems(nz, nx, nb, nt, ns, batch=2, f_peak=25.0, top_bc=top_bc)
+    gp = dataclasses.replace(gp, kernels=api.KERNELS_TILED, space_order=order, checkpoint_every=13)
+    vt = T(models("curved_faulted", [5, 6], nz, nx))
+    v0 = T(initial(2, nz, nx))
+    out = []
+    for sh in (api.SHAPE_TILED_ROWS8, api.SHAPE_TILED_QUADS):
+        with api.Plan(dataclasses.replace(gp, shape=sh), api.W2Params(n_xi=300)) as plan:
+            d_obs, _ = plan.forward(vt, store=False)
+            J, g, _ = plan.gradient(v0, plan.w2_prepare(d_obs.clone()))
+            torch.cuda.synchronize()
+            plan.check()
+            out.append((H(d_obs), H(J), H(g)))
+    for k in range(3):
+        assert np.array_equal(out[0][k], out[1][k]), k

@@ -776,7 +776,7 @@ def run_sampler(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (wavefield record 10 GB per step)",
                    "score": ({"conv": "3-layer 128-channel convolutional noise-prediction "
                                       "network on the tensor cores (seeded weights)",
-                              "unet": "4-level U-Net noise-prediction network (widths 64-256) "
+                              "unet": "4-level U-Net noise-prediction network (widths 32-256) "
                                       "on the tensor cores (seeded weights)"}[args.score]
                              if net else "Gaussian prior fitted to 64 seeded models"),
                    "score_network_ms_per_step": net_ms,
@@ -1270,19 +1270,26 @@ def run_dsm_train(args, rank, world, local_rank):
     if unet:
         if rank != 0:
             return
-        flops = 0.0
-        for _, k, ci, co in net.layers:
-            hh, ww = net.sizes[k]
-            flops += 2.0 * n * hh * ww * 9 * ci * co
+        def conv_flops(layers):
+            f = 0.0
+            for _, k, ci, co in layers:
+                hh, ww = net.sizes[k]
+                f += 2.0 * n * hh * ww * 9 * ci * co
+            return f
+        # executed: the layers as the kernels run them (a 32-channel level in
+        # 64-channel blocks); logical: the network's own widths
+        flops, flops_logical = conv_flops(net.layers), conv_flops(net.logical_layers)
         print(json.dumps({
-            "metric": f"DSM training images/s ({n} x 70x70, 4-level U-Net {net.widths})",
+            "metric": f"DSM training images/s ({n} x 70x70, 4-level U-Net {net.logical_widths})",
             "value": world * n * 1e3 / ms, "unit": "images/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 activations, fp32 parameters, gradients and Adam",
             "data": "synthetic (seeded normal models, one seeded t per step)",
-            "config": {"workload": f"{n} x 70x70, U-Net widths {net.widths}, 15 conv layers, "
-                                   "Adam", "conv_tflop_per_step": 3 * flops / 1e12},
+            "config": {"workload": f"{n} x 70x70, U-Net widths {net.logical_widths} (kernel "
+                                   f"blocks {net.widths}), 15 conv layers, Adam",
+                       "conv_tflop_per_step": 3 * flops / 1e12,
+                       "conv_tflop_per_step_logical": 3 * flops_logical / 1e12},
             "loss": {"after_warmup": loss0, "last": loss1},
             "conv_tflops_per_s": 3 * flops / (ms * 1e-3) / 1e12,
             "clocks": clk}), flush=True)

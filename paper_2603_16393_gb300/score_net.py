@@ -284,20 +284,46 @@ class DSMTrainer:
 # + SiLU; a last linear convolution whose channel 0 is eps.  The step enters
 # every layer's bias as b + E phi(i).
 
-UNET_WIDTHS = (64, 128, 256, 256)
+UNET_WIDTHS = (32, 64, 128, 256)
 
 
 def unet_layers(widths=UNET_WIDTHS):
     """[(name, level, cin, cout)] of the U-Net's convolutions, in parameter order."""
     c = tuple(widths)
-    if len(c) != 4 or any(w % 64 for w in c):
-        raise ValueError("four level widths, each a multiple of 64")
+    if len(c) != 4 or any(w < 32 or w % 32 for w in c):
+        raise ValueError("four level widths, each a multiple of 32")
     out = []
     for k in range(4):
         out += [(f"enc{k}a", k, c[0] if k == 0 else c[k - 1], c[k]), (f"enc{k}b", k, c[k], c[k])]
     for k in (2, 1, 0):
         out += [(f"dec{k}u", k, c[k + 1], c[k]), (f"dec{k}c", k, c[k], c[k])]
     out.append(("out", 0, c[0], c[0]))
+    return out
+
+
+def unet_block_widths(widths=UNET_WIDTHS):
+    """The widths the tensor-core convolution computes with: each rounded up to
+    its 64-channel blocks.  A level of 32 channels runs as 64 whose last 32
+    channels hold zeros -- weights, biases and step embeddings into and out of
+    them are zero, so their activations are SiLU(0) = 0 and every gradient
+    reaching their parameters is exactly zero: the network computed is the
+    32-channel one."""
+    return tuple(-(-int(w) // 64) * 64 for w in widths)
+
+
+def unet_embed(weights, widths, block_widths):
+    """Logical weights [(W, b, E)] of ``widths`` placed into the leading
+    channels of zero arrays of ``block_widths``."""
+    out = []
+    for (W, b, E), (_, _, ci, co), (_, _, cb, ob) in zip(weights, unet_layers(widths),
+                                                          unet_layers(block_widths)):
+        Wp = np.zeros((ob, 3, 3, cb), np.float32)
+        bp = np.zeros(ob, np.float32)
+        Ep = np.zeros((ob, TIME_DIM), np.float32)
+        Wp[:co, :, :, :ci] = W
+        bp[:co] = b
+        Ep[:co] = E
+        out.append((Wp, bp, Ep))
     return out
 
 
@@ -326,14 +352,17 @@ class UNetScore:
                  widths=UNET_WIDTHS, seed: int = 0, device=None):
         B, nz, nx = model_shape
         self.shape = (B, nz, nx)
-        self.widths = tuple(widths)
-        self.layers = unet_layers(widths)
+        self.logical_widths = tuple(widths)
+        self.logical_layers = unet_layers(widths)
+        self.widths = unet_block_widths(widths)      # what the kernels compute with
+        self.layers = unet_layers(self.widths)
         self.idx = {name: l for l, (name, _, _, _) in enumerate(self.layers)}
         self.L = len(self.layers)
         self.dev = torch.device(device) if device is not None else torch.device("cuda")
         weights = weights if weights is not None else unet_seeded_weights(widths, seed)
         if len(weights) != self.L:
             raise ValueError(f"the U-Net has {self.L} layers")
+        weights = unet_embed(weights, widths, self.widths)
         self.abar = [None] + [api.fwi_ddpm_coefficients(list(betas), i).abar
                               for i in range(1, len(betas) + 1)]
         self.sizes = [(nz, nx)]
@@ -378,6 +407,12 @@ class UNetScore:
         self.dX = act(0, c[0], torch.float32)
         self.s = torch.empty(self.shape, dtype=torch.float32, device=self.dev)
         self.u = torch.empty(self.shape, dtype=torch.float32, device=self.dev)
+
+    def logical(self, views):
+        """The network's own parameters (or their gradients) out of per-layer
+        (W, b, E) views of the block widths: the leading channels."""
+        return [(W[:co, :, :, :ci], b[:co], E[:co])
+                for (W, b, E), (_, _, ci, co) in zip(views, self.logical_layers)]
 
     # the interface DSMTrainer uses
     def layer_views(self, flat: torch.Tensor):

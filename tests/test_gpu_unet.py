@@ -104,10 +104,17 @@ def test_unet_eps_vjp_and_dsm_gradients_match_oracle(mods):
     l_ref, g_ref = U.dsm_gradients(w, widths, x, z, D.Schedule(betas).abar[t], t)
     assert abs(float(loss.item()) - l_ref) <= 5 * BF16_ULP * l_ref
     names = [n for n, _, _, _ in SN.unet_layers(widths)]
-    for name, got, refl in zip(names, tr.grads, g_ref):
+    for name, got, refl in zip(names, net.logical(tr.grads), g_ref):
         for k, what in enumerate(("W", "b", "E")):
             err = rel_l2(H(got[k]), refl[k])
             assert err <= 16 * BF16_ULP, (name, what, err)
+    # a 32-channel level runs in a 64-channel block: the parameters of its
+    # zero channels get exactly zero gradients, so training keeps them zero
+    nz_pad = 0
+    for (W, b, E), (_, _, ci, co) in zip(tr.grads, SN.unet_layers(widths)):
+        nz_pad += int(torch.count_nonzero(W[co:])) + int(torch.count_nonzero(W[:, :, :, ci:]))
+        nz_pad += int(torch.count_nonzero(b[co:])) + int(torch.count_nonzero(E[co:]))
+    assert nz_pad == 0
 
 
 def test_algorithm2_with_the_unet_score(mods):

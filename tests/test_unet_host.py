@@ -1,6 +1,8 @@
 """Host logic of the U-Net score network (no GPU): the layer table chains
 channels through pooling, upsampling and the additive skips, agrees with the
-oracle's independent table, and rejects widths the convolution cannot take."""
+oracle's independent table, rejects widths the convolution cannot take, and
+embeds 32-channel levels in zero-filled 64-channel blocks."""
+import numpy as np
 import pytest
 
 from oracle import unet as U
@@ -39,7 +41,21 @@ def test_seeded_weights_shapes(SN):
         assert W.shape == (co, 3, 3, ci) and b.shape == (co,) and E.shape == (co, SN.TIME_DIM)
 
 
-@pytest.mark.parametrize("widths", [(32, 64, 128, 256), (64, 128, 256), (64, 100, 256, 256)])
+@pytest.mark.parametrize("widths", [(48, 64, 128, 256), (64, 128, 256), (64, 100, 256, 256),
+                                    (0, 64, 128, 256)])
 def test_widths_the_convolution_cannot_take(SN, widths):
     with pytest.raises(ValueError):
         SN.unet_layers(widths)
+
+
+def test_block_widths_embed_the_network_in_zero_channels(SN):
+    widths = (32, 64, 96, 256)
+    assert SN.unet_block_widths(widths) == (64, 64, 128, 256)
+    w = SN.unet_seeded_weights(widths, seed=1)
+    e = SN.unet_embed(w, widths, SN.unet_block_widths(widths))
+    for (W, b, E), (Wp, bp, Ep), (_, _, ci, co) in zip(w, e, SN.unet_layers(widths)):
+        np.testing.assert_array_equal(Wp[:co, :, :, :ci], W)
+        np.testing.assert_array_equal(bp[:co], b)
+        np.testing.assert_array_equal(Ep[:co], E)
+        assert not Wp[co:].any() and not Wp[:, :, :, ci:].any()
+        assert not bp[co:].any() and not Ep[co:].any()

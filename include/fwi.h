@@ -209,6 +209,9 @@ FWI_API void fwi_plan_destroy(fwi_plan *plan);
  *              record (nt time levels of the padded grid per model and shot)
  *              when checkpoint_every = 0, else ceil(nt/K) checkpoints of the
  *              propagator state (two padded grids per model and shot each).
+ * The workspace and snapshot buffers must start on a 16-byte boundary (the
+ * record planes and checkpoints are moved in 16-byte units); every entry
+ * point that takes them returns FWI_ERR_INVALID_ARG otherwise.
  * Any output pointer may be NULL. */
 FWI_API fwi_status fwi_plan_sizes(const fwi_plan *plan, size_t *workspace_bytes,
                           size_t *obs_ctx_bytes, size_t *snapshot_bytes);

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -37,6 +38,10 @@ fwi_status cuda_fail(cudaError_t e, const char *where)
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 const Plan *as_plan(const fwi_plan *p) { return reinterpret_cast<const Plan *>(p); }
+
+// the record planes and checkpoint slots are moved in 16-byte units (vector
+// stores and loads, bulk L2 prefetches), the workspace holds them too
+bool misaligned16(const void *p) { return p && (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
 
 
 }  // namespace
@@ -481,6 +486,8 @@ fwi_status fwi_forward(const fwi_plan *plan, const float *v, float *d_syn, float
 {
     if (!plan || !v || !d_syn || !workspace)
         return fail(FWI_ERR_INVALID_ARG, "plan, v, d_syn and workspace must not be NULL");
+    if (misaligned16(snapshots) || misaligned16(workspace))
+        return fail(FWI_ERR_INVALID_ARG, "snapshots and workspace must be 16-byte aligned");
     const Plan &pl = *as_plan(plan);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(workspace, 0, sizeof(int), st);
@@ -502,6 +509,8 @@ fwi_status fwi_forward_wait_check(const fwi_plan *plan, const float *v, float *d
 {
     if (!plan || !v || !d_syn || !workspace)
         return fail(FWI_ERR_INVALID_ARG, "plan, v, d_syn and workspace must not be NULL");
+    if (misaligned16(snapshots) || misaligned16(workspace))
+        return fail(FWI_ERR_INVALID_ARG, "snapshots and workspace must be 16-byte aligned");
     const Plan &pl = *as_plan(plan);
     if (!pl.cluster && !(pl.tiled && !pl.cpml))
         return fail(FWI_ERR_UNSUPPORTED,
@@ -546,6 +555,8 @@ fwi_status fwi_adjoint_grad(const fwi_plan *plan, const float *v, const float *a
     if (!plan || !v || !adj_src || !snapshots || !grad || !workspace)
         return fail(FWI_ERR_INVALID_ARG,
                     "plan, v, adj_src, snapshots, grad and workspace must not be NULL");
+    if (misaligned16(snapshots) || misaligned16(workspace))
+        return fail(FWI_ERR_INVALID_ARG, "snapshots and workspace must be 16-byte aligned");
     const Plan &pl = *as_plan(plan);
     unsigned char *ws = (unsigned char *)workspace;
     float *gshot = (float *)(ws + pl.ws_gshot);

@@ -350,13 +350,24 @@ __global__ void __launch_bounds__(kQuadThreads) k_tile_fwd4(const __grid_constan
     if (a.ckpt && a.j % a.ckpt_every == 0) {
         const size_t cells = (size_t)a.NZ * a.NX;
         float *st = a.ckpt + ((size_t)(a.j / a.ckpt_every) * gridDim.z + bs) * 2 * cells;
+        // a quad wholly inside the grid goes out as two 16-byte stores when
+        // the rows of the slot start on 16-byte boundaries (NX a multiple of
+        // 4); otherwise cell by cell
+        const bool whole = (a.NX & 3) == 0 && x + 3 < a.NX;
 #pragma unroll
         for (int r = 0; r < QR; ++r) {
             const int z = zr + r;
+            if (z >= a.NZ) continue;
+            const float *t = tile + (z - z0 + R) * HX + 4 * tq + 4;
+            if (whole) {
+                st4(st + (size_t)z * a.NX + x, ld4(t));
+                st4(st + cells + (size_t)z * a.NX + x, vi[r]);
+                continue;
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (x + q < a.NX && z < a.NZ) {
-                    st[(size_t)z * a.NX + x + q] = tile[(z - z0 + R) * HX + 4 * tq + q + 4];
+                if (x + q < a.NX) {
+                    st[(size_t)z * a.NX + x + q] = t[q];
                     st[cells + (size_t)z * a.NX + x + q] = q4c(vi[r], q);
                 }
             }

@@ -7,12 +7,16 @@
 // one plan while another's units wait.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "fwi_internal.cuh"
 
 namespace {
 
+// lists: nl per-plan pointer lists, none may hold NULL; bit l of align16 set:
+// list l's pointers must be 16-byte aligned (record planes, workspace)
 fwi_status check_plans(const fwi_plan *const *plans, int n, const void *const *lists[], int nl,
-                       int *counter, const char *what)
+                       unsigned align16, int *counter, const char *what)
 {
     if (!plans || n < 1 || n > fwi::kQueuePlans)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "%s: need 1 <= n <= %d plans", what,
@@ -20,10 +24,15 @@ fwi_status check_plans(const fwi_plan *const *plans, int n, const void *const *l
     if (!counter) return fwi::record_error(FWI_ERR_INVALID_ARG, "%s: counter is NULL", what);
     for (int i = 0; i < n; ++i) {
         if (!plans[i]) return fwi::record_error(FWI_ERR_INVALID_ARG, "%s: plan %d is NULL", what, i);
-        for (int l = 0; l < nl; ++l)
+        for (int l = 0; l < nl; ++l) {
             if (!lists[l] || !lists[l][i])
                 return fwi::record_error(FWI_ERR_INVALID_ARG, "%s: a pointer of plan %d is NULL",
                                          what, i);
+            if (((align16 >> l) & 1u) && (reinterpret_cast<uintptr_t>(lists[l][i]) & 15u) != 0)
+                return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                         "%s: a pointer of plan %d is not 16-byte aligned", what,
+                                         i);
+        }
         const fwi::Plan &pl = *reinterpret_cast<const fwi::Plan *>(plans[i]);
         if (!fwi::queue_ok(pl))
             return fwi::record_error(FWI_ERR_UNSUPPORTED,
@@ -58,7 +67,7 @@ fwi_status fwi_queue_forward(const fwi_plan *const *plans, int n, const float *c
 {
     const void *const *lists[] = {(const void *const *)v, (const void *const *)d_syn,
                                   (const void *const *)snapshots, (const void *const *)workspace};
-    fwi_status s = check_plans(plans, n, lists, 4, counter, "fwi_queue_forward");
+    fwi_status s = check_plans(plans, n, lists, 4, 0xcu, counter, "fwi_queue_forward");
     if (s != FWI_OK) return s;
     const fwi::Plan *pls[fwi::kQueuePlans];
     fwi::PropArgs a[fwi::kQueuePlans];
@@ -87,7 +96,7 @@ fwi_status fwi_queue_adjoint(const fwi_plan *const *plans, int n, const float *c
     const void *const *lists[] = {(const void *const *)v, (const void *const *)adj_src,
                                   (const void *const *)snapshots, (const void *const *)grad,
                                   (const void *const *)workspace};
-    fwi_status s = check_plans(plans, n, lists, 5, counter, "fwi_queue_adjoint");
+    fwi_status s = check_plans(plans, n, lists, 5, 0x14u, counter, "fwi_queue_adjoint");
     if (s != FWI_OK) return s;
     const fwi::Plan *pls[fwi::kQueuePlans];
     fwi::PropArgs a[fwi::kQueuePlans];

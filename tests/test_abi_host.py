@@ -346,3 +346,33 @@ def test_queue_rejects_plans_outside_the_column_pair_kernels(api):
     plans = (vp * 5)(*([ok.raw] * 5))
     assert api._lib.fwi_queue_forward(plans, 5, dummy, dummy, dummy, dummy, cnt, None) == \
         api.FWI_ERR_INVALID_ARG
+
+
+def test_entry_points_reject_misaligned_record_and_workspace_without_a_gpu(api):
+    # the record planes and checkpoints move in 16-byte units: a snapshot or
+    # workspace pointer off a 16-byte boundary is refused before any CUDA call
+    h = api.fwi_plan_create(_prob(api), api.W2Params())
+    lib, p, vp = api._lib, h.raw, ctypes.c_void_p
+    ok, off = vp(4096), vp(4096 + 8)
+    calls = [
+        lambda: lib.fwi_forward(p, ok, ok, off, ok, None),
+        lambda: lib.fwi_forward(p, ok, ok, ok, off, None),
+        lambda: lib.fwi_adjoint_grad(p, ok, ok, off, ok, ok, None),
+        lambda: lib.fwi_adjoint_grad(p, ok, ok, ok, ok, off, None),
+        lambda: lib.fwi_forward_wait_check(p, ok, ok, off, ok, None),
+    ]
+    for i, call in enumerate(calls):
+        assert call() == api.FWI_ERR_INVALID_ARG, i
+        assert "16-byte" in api.fwi_last_error()
+    one = (vp * 1)(ok)
+    bad = (vp * 1)(off)
+    cnt = vp(256)
+    plans = (vp * 1)(p)
+    # fwi_queue_forward(plans, n, v, d_syn, snapshots, workspace, counter, stream);
+    # every call here is refused before a launch
+    assert lib.fwi_queue_forward(plans, 1, one, one, bad, one, cnt, None) == api.FWI_ERR_INVALID_ARG
+    assert lib.fwi_queue_forward(plans, 1, one, one, one, bad, cnt, None) == api.FWI_ERR_INVALID_ARG
+    # fwi_queue_adjoint(plans, n, v, adj_src, snapshots, grad, workspace, counter, stream)
+    assert lib.fwi_queue_adjoint(plans, 1, one, one, bad, one, one, cnt, None) == \
+        api.FWI_ERR_INVALID_ARG
+    assert "16-byte" in api.fwi_last_error()

@@ -41,6 +41,22 @@ constexpr int NT_W2 = 256;          // threads per trace CTA
 constexpr int NW_W2 = NT_W2 / 32;
 constexpr unsigned FULL = 0xffffffffu;
 
+// Shared-memory arrays of a trace are padded: element k of an 8-byte (df)
+// array sits at pd(k), one gap every 16 elements, and of a 4-byte array at
+// pw(k), one gap every 32.  A thread that owns a contiguous block of 4
+// elements then meets the other threads of its half-warp (or warp) in
+// distinct banks at every step of the block.
+__device__ __forceinline__ int pd(int k) { return k + (k >> 4); }
+__device__ __forceinline__ int pw(int k) { return k + (k >> 5); }
+__host__ __device__ constexpr size_t pd_len(int n) { return (size_t)n + (n >> 4) + 1; }
+__host__ __device__ constexpr size_t pw_len(int n) { return (size_t)n + (n >> 5) + 1; }
+// df elements of the misfit kernel's SA region, which also holds the nt
+// floats of y while the CDF is built
+__host__ __device__ constexpr size_t sa_len(int nt, int nxi)
+{
+    return pd_len(nxi) > (size_t)(nt + 1) / 2 ? pd_len(nxi) : (size_t)(nt + 1) / 2;
+}
+
 // ---------------------------------------------------------------- double-float
 // A value hi + lo with |lo| <= ulp(hi)/2 (Knuth two-sum / Dekker two-product,
 // error-free transformations in float32).
@@ -166,7 +182,8 @@ __device__ df block_sum_df(df v, df *red)
 }
 
 // In-place inclusive double-float scan (OP 0: sum, 1: max) of arr[0..n) in
-// shared memory, blocked arrangement; REV scans from the end (suffix scan).
+// shared memory (padded, pd), blocked arrangement; REV scans from the end
+// (suffix scan).
 template <int OP, bool REV>
 __device__ void block_scan_df(df *arr, int n, df *red)
 {
@@ -176,8 +193,8 @@ __device__ void block_scan_df(df *arr, int n, df *red)
     df run = dident<OP>();
     for (int i = lo; i < hi; ++i) {
         const int k = REV ? n - 1 - i : i;
-        run = dcomb<OP>(run, arr[k]);
-        arr[k] = run;
+        run = dcomb<OP>(run, arr[pd(k)]);
+        arr[pd(k)] = run;
     }
     df incl = run;
 #pragma unroll
@@ -204,19 +221,19 @@ __device__ void block_scan_df(df *arr, int n, df *red)
     if (tid > 0) {
         for (int i = lo; i < hi; ++i) {
             const int k = REV ? n - 1 - i : i;
-            arr[k] = dcomb<OP>(off, arr[k]);
+            arr[pd(k)] = dcomb<OP>(off, arr[pd(k)]);
         }
     }
     __syncthreads();
 }
 
-// first k in [0, n) with a[k] >= x (a non-decreasing); n if none
+// first k in [0, n) with a[k] >= x (a non-decreasing, padded); n if none
 __device__ __forceinline__ int lower_bound_df(const df *a, int n, df x)
 {
     int lo = 0, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (df_lt(a[mid], x)) lo = mid + 1;
+        if (df_lt(a[pd(mid)], x)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -226,7 +243,7 @@ __device__ __forceinline__ int lower_bound_i(const int *a, int n, int x)
     int lo = 0, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1;
+        if (a[pw(mid)] < x) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -241,11 +258,11 @@ constexpr int kWalk = 8;
 __device__ __forceinline__ int lower_bound_df_from(const df *a, int n, df x, int k)
 {
     for (int s = 0; s < kWalk && k < n; ++s, ++k)
-        if (!df_lt(a[k], x)) return k;
+        if (!df_lt(a[pd(k)], x)) return k;
     int lo = k, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (df_lt(a[mid], x)) lo = mid + 1;
+        if (df_lt(a[pd(mid)], x)) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -253,11 +270,11 @@ __device__ __forceinline__ int lower_bound_df_from(const df *a, int n, df x, int
 __device__ __forceinline__ int lower_bound_i_from(const int *a, int n, int x, int k)
 {
     for (int s = 0; s < kWalk && k < n; ++s, ++k)
-        if (a[k] >= x) return k;
+        if (a[pw(k)] >= x) return k;
     int lo = k, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (a[mid] < x) lo = mid + 1;
+        if (a[pw(mid)] < x) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -309,16 +326,16 @@ __device__ df build_cdf(const float *y, df *G, df *Gm, int nt, int nxi, float ep
                         float *sgn)
 {
     for (int i = threadIdx.x; i < nt; i += NT_W2)
-        G[i] = i == 0 ? df{0.f, 0.f} : two_sum(y[i - 1], y[i]);
+        G[pd(i)] = i == 0 ? df{0.f, 0.f} : two_sum(y[i - 1], y[i]);
     __syncthreads();
     block_scan_df<0, false>(G, nt, red);
-    df gtot = df_add(G[nt - 1], df_from(eps2dt));
+    df gtot = df_add(G[pd(nt - 1)], df_from(eps2dt));
     const bool neg = gtot.hi < 0.f;
     __syncthreads();                  // every thread has read G[nt - 1]
     for (int i = threadIdx.x; i < nt; i += NT_W2) {
-        const df g = neg ? df_neg(G[i]) : G[i];
-        G[i] = g;
-        Gm[i] = g;
+        const df g = neg ? df_neg(G[pd(i)]) : G[pd(i)];
+        G[pd(i)] = g;
+        Gm[pd(i)] = g;
     }
     __syncthreads();
     block_scan_df<1, false>(Gm, nt, red);
@@ -349,7 +366,7 @@ __device__ __forceinline__ void quantile(const df *G, const df *Gm, int nt, df u
     if (k == 0) { *base = 0; *frac = 0.f; return; }
     if (k == nt) { *base = nt - 1; *frac = 0.f; return; }
     *base = k - 1;
-    *frac = __fdiv_rn(df_f(df_sub(t, G[k - 1])), df_f(df_sub(G[k], G[k - 1])));
+    *frac = __fdiv_rn(df_f(df_sub(t, G[pd(k - 1)])), df_f(df_sub(G[pd(k)], G[pd(k - 1)])));
 }
 
 // ------------------------------------------------------------------ kernels
@@ -379,8 +396,8 @@ __global__ void __launch_bounds__(NT_W2) k_obs_trace(const float *__restrict__ d
     __shared__ float redf[NW_W2 + 2];
     const int tr_g = blockIdx.x;                 // b * ntr + tr
     const int b = tr_g / a.ntr;
-    df *G = smd, *Gm = G + a.nt;
-    float *y = (float *)(Gm + a.nt);
+    df *G = smd, *Gm = G + pd_len(a.nt);
+    float *y = (float *)(Gm + pd_len(a.nt));
     const float *d = d_obs + (size_t)tr_g * a.nt;
     float *om = a.c.omega + (size_t)tr_g * a.nt;
     const float M = a.c.M[b];
@@ -443,10 +460,12 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
     const int tr_g = blockIdx.x;
     const int b = tr_g / a.ntr;
     const int nt = a.nt, nxi = a.nxi;
-    df *G = smd, *Gm = G + nt, *SA = Gm + nt, *SB = SA + nxi;
-    float *y = (float *)(SB + nxi);
-    float *dq = y + nt;
-    int *ks = (int *)(dq + nxi);
+    // y is read only while the CDF is built, before SA is written: it shares
+    // SA's space
+    df *G = smd, *Gm = G + pd_len(nt), *SA = Gm + pd_len(nt), *SB = SA + sa_len(nt, nxi);
+    float *y = (float *)SA;
+    float *dq = (float *)(SB + pd_len(nxi));
+    int *ks = (int *)(dq + pw_len(nxi));
     const float *d = d_syn + (size_t)tr_g * nt;
     const float *om = a.c.omega + (size_t)tr_g * nt;
     const float cs = a.c.cshift[tr_g];
@@ -467,8 +486,8 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
         kprev = k;
         // (base - base_obs) is exact; the fractions are in [0, 1]
         const float diff = ((float)(base - Qb[j]) + (frac - Qf[j])) * a.dt;
-        dq[j] = diff;
-        ks[j] = k;
+        dq[pw(j)] = diff;
+        ks[pw(j)] = k;
         const float wj = (j == 0 || j == nxi - 1) ? 0.5f : 1.f;
         part += wj * diff * diff;
     }
@@ -486,21 +505,21 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
     const float scale = a.squared ? 2.f * dxi / a.c.S2[b] : dxi / (W2 * a.c.S[b]);
     df cpart = {0.f, 0.f};
     for (int j = threadIdx.x; j < nxi; j += NT_W2) {
-        const int k = ks[j];
+        const int k = ks[pw(j)];
         df aj = {0.f, 0.f}, bj = {0.f, 0.f};
         if (k > 0 && k < nt) {
             const df t = df_mul_f(unit, (float)j);
             const float wj = (j == 0 || j == nxi - 1) ? 0.5f : 1.f;
-            const float qbar = scale * wj * dq[j];            // dJ/dQ_j
-            const float D = df_f(df_sub(G[k], G[k - 1]));
+            const float qbar = scale * wj * dq[pw(j)];        // dJ/dQ_j
+            const float D = df_f(df_sub(G[pd(k)], G[pd(k - 1)]));
             const float r = qbar * a.dt / (D * D);
-            aj = df_from(r * df_f(df_sub(t, G[k])));          // -> dJ/dG_{k-1}
-            bj = df_from(-r * df_f(df_sub(t, G[k - 1])));     // -> dJ/dG_k
+            aj = df_from(r * df_f(df_sub(t, G[pd(k)])));      // -> dJ/dG_{k-1}
+            bj = df_from(-r * df_f(df_sub(t, G[pd(k - 1)]))); // -> dJ/dG_k
             // through t_j = xi_j Gtot -> dJ/dG_{nt-1}
             cpart = df_add(cpart, df_from(qbar * a.dt * ((float)j * dxi) / D));
         }
-        SA[j] = aj;
-        SB[j] = bj;
+        SA[pd(j)] = aj;
+        SB[pd(j)] = bj;
     }
     const df C = block_sum_df(cpart, red);
     block_scan_df<0, true>(SA, nxi, red);
@@ -514,16 +533,16 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
         for (int k = k0; k < k1; ++k) {
             const int jk1 = lower_bound_i_from(ks, nxi, k + 1, jk);
             df h = C;
-            if (jk1 < nxi) h = df_add(h, SA[jk1]);
-            if (jk < nxi) h = df_add(h, SB[jk]);
-            Gm[k] = h;
+            if (jk1 < nxi) h = df_add(h, SA[pd(jk1)]);
+            if (jk < nxi) h = df_add(h, SB[pd(jk)]);
+            Gm[pd(k)] = h;
             jk = jk1;
         }
     }
     __syncthreads();
     for (int m = threadIdx.x; m < nt; m += NT_W2) {
-        df yb = m + 1 < nt ? Gm[m + 1] : df{0.f, 0.f};
-        if (m >= 1) yb = df_add(yb, Gm[m]);
+        df yb = m + 1 < nt ? Gm[pd(m + 1)] : df{0.f, 0.f};
+        if (m >= 1) yb = df_add(yb, Gm[pd(m)]);
         ad[m] = om[m] * (sgn * df_f(yb));
     }
 }
@@ -543,14 +562,14 @@ W2Args make_w2(const Plan &pl, unsigned char *ctx)
     return a;
 }
 
-size_t obs_trace_smem(int nt) { return 2 * (size_t)nt * sizeof(df) + (size_t)nt * 4; }
+size_t obs_trace_smem(int nt) { return 2 * pd_len(nt) * sizeof(df) + (size_t)nt * 4; }
 
 }  // namespace
 
 size_t w2_trace_smem(int nt, int nxi)
 {
-    return 2 * (size_t)nt * sizeof(df) + 2 * (size_t)nxi * sizeof(df) + (size_t)nt * 4 +
-           (size_t)nxi * 8;
+    // G, Gm; SA (with y), SB; dq, ks
+    return (2 * pd_len(nt) + sa_len(nt, nxi) + pd_len(nxi)) * sizeof(df) + 2 * pw_len(nxi) * 4;
 }
 
 cudaError_t launch_w2_prepare(const Plan &pl, const float *d_obs, unsigned char *ctx,

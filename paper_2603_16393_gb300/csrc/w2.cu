@@ -50,11 +50,19 @@ __device__ __forceinline__ int pd(int k) { return k + (k >> 4); }
 __device__ __forceinline__ int pw(int k) { return k + (k >> 5); }
 __host__ __device__ constexpr size_t pd_len(int n) { return (size_t)n + (n >> 4) + 1; }
 __host__ __device__ constexpr size_t pw_len(int n) { return (size_t)n + (n >> 5) + 1; }
-// df elements of the misfit kernel's SA region, which also holds the nt
-// floats of y while the CDF is built
-__host__ __device__ constexpr size_t sa_len(int nt, int nxi)
+// Regions of the misfit kernel, each reused once its first array is dead:
+//   R1: G (CDF build .. SA/SB terms), then H (suffix sums per sample)
+//   R2: Gm (CDF build .. quantiles), then SA (terms and their suffix sums)
+//   R3: y (CDF build), then SB
+// plus dq and ks (quantiles .. reverse pass).
+__host__ __device__ constexpr size_t max_len(size_t a, size_t b) { return a > b ? a : b; }
+__host__ __device__ constexpr size_t r2_len(int nt, int nxi)
 {
-    return pd_len(nxi) > (size_t)(nt + 1) / 2 ? pd_len(nxi) : (size_t)(nt + 1) / 2;
+    return max_len(pd_len(nt), pd_len(nxi));
+}
+__host__ __device__ constexpr size_t r3_len(int nt, int nxi)
+{
+    return max_len(pd_len(nxi), (size_t)(nt + 1) / 2);
 }
 
 // ---------------------------------------------------------------- double-float
@@ -450,9 +458,11 @@ __global__ void __launch_bounds__(NT_W2) k_sum_traces(const float *__restrict__ 
     if (threadIdx.x == 0) out[blockIdx.x] = div ? s / div[blockIdx.x] : s;
 }
 
-__global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict__ d_syn, W2Args a,
-                                                        float *__restrict__ w2_dst,
-                                                        float *__restrict__ adj)
+// six traces a SM: 40 registers a thread (x 256 threads x 6 = 61 440) and
+// 33.8 KB of shared arrays a trace at 1000 samples and nodes
+__global__ void __launch_bounds__(NT_W2, 6)
+    k_misfit_trace(const float *__restrict__ d_syn, W2Args a, float *__restrict__ w2_dst,
+                   float *__restrict__ adj)
 {
     extern __shared__ df smd[];
     __shared__ df red[NW_W2 + 2];
@@ -460,11 +470,10 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
     const int tr_g = blockIdx.x;
     const int b = tr_g / a.ntr;
     const int nt = a.nt, nxi = a.nxi;
-    // y is read only while the CDF is built, before SA is written: it shares
-    // SA's space
-    df *G = smd, *Gm = G + pd_len(nt), *SA = Gm + pd_len(nt), *SB = SA + sa_len(nt, nxi);
-    float *y = (float *)SA;
-    float *dq = (float *)(SB + pd_len(nxi));
+    df *G = smd, *Gm = G + pd_len(nt), *SB = Gm + r2_len(nt, nxi);
+    df *SA = Gm, *H = G;
+    float *y = (float *)SB;
+    float *dq = (float *)(SB + r3_len(nt, nxi));
     int *ks = (int *)(dq + pw_len(nxi));
     const float *d = d_syn + (size_t)tr_g * nt;
     const float *om = a.c.omega + (size_t)tr_g * nt;
@@ -524,7 +533,7 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
     const df C = block_sum_df(cpart, red);
     block_scan_df<0, true>(SA, nxi, red);
     block_scan_df<0, true>(SB, nxi, red);
-    // H_k into Gm (no longer needed), k = 0..nt-1 (H_nt = 0); j(k) = first
+    // H_k into G's region (no longer needed), k = 0..nt-1 (H_nt = 0); j(k) = first
     // node whose bracket is >= k grows with k: a block of k per thread
     int k0, k1;
     thread_block(nt, &k0, &k1);
@@ -535,14 +544,14 @@ __global__ void __launch_bounds__(NT_W2) k_misfit_trace(const float *__restrict_
             df h = C;
             if (jk1 < nxi) h = df_add(h, SA[pd(jk1)]);
             if (jk < nxi) h = df_add(h, SB[pd(jk)]);
-            Gm[pd(k)] = h;
+            H[pd(k)] = h;
             jk = jk1;
         }
     }
     __syncthreads();
     for (int m = threadIdx.x; m < nt; m += NT_W2) {
-        df yb = m + 1 < nt ? Gm[pd(m + 1)] : df{0.f, 0.f};
-        if (m >= 1) yb = df_add(yb, Gm[pd(m)]);
+        df yb = m + 1 < nt ? H[pd(m + 1)] : df{0.f, 0.f};
+        if (m >= 1) yb = df_add(yb, H[pd(m)]);
         ad[m] = om[m] * (sgn * df_f(yb));
     }
 }
@@ -568,8 +577,8 @@ size_t obs_trace_smem(int nt) { return 2 * pd_len(nt) * sizeof(df) + (size_t)nt 
 
 size_t w2_trace_smem(int nt, int nxi)
 {
-    // G, Gm; SA (with y), SB; dq, ks
-    return (2 * pd_len(nt) + sa_len(nt, nxi) + pd_len(nxi)) * sizeof(df) + 2 * pw_len(nxi) * 4;
+    // G then H; Gm then SA; y then SB; dq, ks
+    return (pd_len(nt) + r2_len(nt, nxi) + r3_len(nt, nxi)) * sizeof(df) + 2 * pw_len(nxi) * 4;
 }
 
 cudaError_t launch_w2_prepare(const Plan &pl, const float *d_obs, unsigned char *ctx,

@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 11200  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 11300  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -681,6 +681,18 @@ FWI_API fwi_status fwi_coarse_problem(const fwi_problem *fine, fwi_problem *coar
 FWI_API fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *x,
                                     const void *wt, const float *bias, int act, void *y,
                                     int y_bf16, int *status, void *stream);
+
+/* The same convolution writing a layer's two bf16 outputs at once: the
+ * pre-activation p = bf16(bias + sum ...) and its SiLU a = bf16(q / (1 + e^-q))
+ * with q = p widened to float -- bit for bit what fwi_conv3x3_bf16 (act 0,
+ * bf16 output) followed by fwi_silu_bf16 give, without the second pass over
+ * p.  The paper gives no architecture for its networks (Sec. 6); this is the
+ * layer of the score networks above (a 3x3 convolution and SiLU).
+ *   p, a [n][h][w][cout] bf16 device, 16-byte aligned, neither aliasing x
+ * Other arguments and errors as fwi_conv3x3_bf16. */
+FWI_API fwi_status fwi_conv3x3_bf16_silu(int n, int h, int w, int cin, int cout, const void *x,
+                                         const void *wt, const float *bias, void *p, void *a,
+                                         int *status, void *stream);
 
 /* ---------------------------------------------------------------- reverse diffusion
  * The elementwise steps of one reverse step i -> i-1 of Algorithm 1 (DPS) and

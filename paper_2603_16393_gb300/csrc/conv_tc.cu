@@ -52,6 +52,7 @@
 #include <mutex>
 
 #include "fwi_internal.cuh"
+#include "silu.cuh"
 
 namespace {
 
@@ -72,12 +73,13 @@ struct ConvArgs {
     unsigned long long wait_ns;    // bound of one mbarrier wait
     int withhold;                  // 1: never load the weight blocks (the wait self-check)
     int n, h, w, cin, cout;
-    int act;       // 0: none, 1: SiLU
+    int act;       // 0: none, 1: SiLU, 2: y = bf16(pre-activation), y2 = bf16(SiLU(y))
     int y_bf16;    // output type: 0 fp32, 1 bf16
     int tiles_x, tiles_y, tiles;   // pixel tiles per image row / column, tiles in all
     const float *bias;
     void *y;
     int *status;
+    void *y2;      // act 2: the activation (bf16, y's layout)
 };
 
 __device__ __forceinline__ unsigned su32(const void *p)
@@ -423,6 +425,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                            pix * a.cout + co);
                     dst[0] = *reinterpret_cast<uint4 *>(&h2[0]);
                     dst[1] = *reinterpret_cast<uint4 *>(&h2[4]);
+                    if (a.act == 2) {
+                        // SiLU of the rounded pre-activation, as k_silu forms it
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float2 f = __bfloat1622float2(h2[i]);
+                            h2[i] = __floats2bfloat162_rn(silu_of(f.x), silu_of(f.y));
+                        }
+                        uint4 *dst2 = reinterpret_cast<uint4 *>(
+                            static_cast<__nv_bfloat16 *>(a.y2) + pix * a.cout + co);
+                        dst2[0] = *reinterpret_cast<uint4 *>(&h2[0]);
+                        dst2[1] = *reinterpret_cast<uint4 *>(&h2[4]);
+                    }
                 } else {
                     float4 *dst =
                         reinterpret_cast<float4 *>(static_cast<float *>(a.y) + pix * a.cout + co);
@@ -467,6 +481,11 @@ constexpr int kPM = 128;                                    // output channels p
 constexpr int kPWBytes = kPM * kBK * 2;                     // 16 KB weight block
 constexpr int kPWStages = 8;
 constexpr uint32_t kPTmemCols = 512;                        // two 192-column accumulators
+// bf16 epilogue staging: per epilogue warp 16 pixels x 32 channels (1 KB), so
+// that a step leaves as 16-byte stores of 8 channels instead of one 2-byte
+// store per channel and pixel
+constexpr int kPStageBytes = 16 * 32 * 2;
+constexpr int kPEpiBytes = kEpiWarps * kPStageBytes;
 
 __host__ __device__ constexpr uint32_t idesc_bf16_mn(int m, int n)
 {
@@ -487,6 +506,26 @@ __device__ __forceinline__ Tile tile_of_pn(int t, const ConvArgs &a)
     r.y0 = ty * kPH;
     r.n0 = cbk * kPM;
     return r;
+}
+
+// One 16-pixel step of a pixels-as-N epilogue warp: the staging block holds
+// bf16 rows [16 pixels][32 channels, from channel c]; lane l stores chunks
+// l and l + 32 (pixel chunk / 4, eight channels (chunk % 4) 8 ..) as 16-byte
+// stores, pixels outside the image skipped.
+__device__ __forceinline__ void pn_store_rows(const __nv_bfloat16 *stg, __nv_bfloat16 *y,
+                                              const ConvArgs &a, const Tile &tl, int c0, int c,
+                                              int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int k = lane + 32 * i, j = k >> 2, part = k & 3;
+        const int m = c0 + j;
+        const int px = tl.x0 + (m % kPW), py = tl.y0 + m / kPW;
+        if (px >= a.w || py >= a.h) continue;
+        const size_t pix = ((size_t)tl.img * a.h + py) * a.w + px;
+        *reinterpret_cast<uint4 *>(y + pix * a.cout + c + part * 8) =
+            *reinterpret_cast<const uint4 *>(stg + j * 32 + part * 8);
+    }
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -607,6 +646,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // epilogue warps 2..17: lane quarter q = 32 output channels, and a
         // quarter of the 192 pixel columns
+        __nv_bfloat16 *stg = reinterpret_cast<__nv_bfloat16 *>(
+            sW + kPWStages * kPWBytes + (warp - 2) * kPStageBytes);
         const int q = warp & 3;
         const int part = (warp - 2) >> 2;
         const int cbeg = part * (kPN / 4), cend = cbeg + kPN / 4;
@@ -619,12 +660,40 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int co = tl.n0 + q * 32 + lane;
             // a 64-channel remainder: lanes past cout hold the zero rows of the
             // weight box and store nothing (the TMEM loads stay warp-wide)
-            const bool live = co < a.cout;
+            const bool live = co < a.cout;   // the same for all 32 lanes (cout % 64 == 0)
             const float bias = a.bias && live ? __ldg(a.bias + co) : 0.f;
 #pragma unroll 1
             for (int c0 = cbeg; c0 < cend; c0 += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256 + c0), v);
+                if (a.y_bf16) {
+                    if (!live) continue;
+                    // rows of 32 channels per pixel through the warp's staging
+                    // block, then two 16-byte stores a lane (a quarter of a
+                    // pixel's row each)
+                    __nv_bfloat16 yb[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float x = v[j] + bias;
+                        yb[j] = __float2bfloat16_rn(a.act == 1 ? silu(x) : x);
+                        stg[j * 32 + lane] = yb[j];
+                    }
+                    __syncwarp();
+                    pn_store_rows(stg, static_cast<__nv_bfloat16 *>(a.y), a, tl, c0,
+                                  tl.n0 + q * 32, lane);
+                    if (a.act == 2) {
+                        // SiLU of the rounded pre-activation, as k_silu forms it
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            stg[j * 32 + lane] = __float2bfloat16_rn(silu_of(__bfloat162float(yb[j])));
+                        __syncwarp();
+                        pn_store_rows(stg, static_cast<__nv_bfloat16 *>(a.y2), a, tl, c0,
+                                      tl.n0 + q * 32, lane);
+                    }
+                    __syncwarp();
+                    continue;
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int m = c0 + j;
@@ -632,11 +701,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!live || px >= a.w || py >= a.h) continue;
                     const size_t pix = ((size_t)tl.img * a.h + py) * a.w + px;
                     const float x = v[j] + bias;
-                    const float yv = a.act == 1 ? silu(x) : x;
-                    if (a.y_bf16)
-                        static_cast<__nv_bfloat16 *>(a.y)[pix * a.cout + co] = __float2bfloat16_rn(yv);
-                    else
-                        static_cast<float *>(a.y)[pix * a.cout + co] = yv;
+                    static_cast<float *>(a.y)[pix * a.cout + co] = a.act == 1 ? silu(x) : x;
                 }
             }
             tc_fence_before();
@@ -699,7 +764,8 @@ cudaError_t launch_conv(const CUtensorMap &tmx, const CUtensorMap &tmw, const Co
 cudaError_t launch_conv_pn(const CUtensorMap &tmx, const CUtensorMap &tmw, const ConvArgs &a,
                            cudaStream_t st)
 {
-    const size_t smem = (size_t)kAStages * kPHaloBytes + (size_t)kPWStages * kPWBytes + 1024;
+    const size_t smem =
+        (size_t)kAStages * kPHaloBytes + (size_t)kPWStages * kPWBytes + kPEpiBytes + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc_pn,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1018,7 +1084,7 @@ namespace {
 
 fwi_status conv_call(int n, int h, int w, int cin, int cout, const void *x, const void *wt,
                      const float *bias, int act, void *y, int y_bf16, int *status, void *stream,
-                     int withhold, unsigned long long wait_ns)
+                     int withhold, unsigned long long wait_ns, void *y2 = nullptr)
 {
     if (n < 1 || h < 1 || w < 1)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "n, h, w must be >= 1");
@@ -1026,7 +1092,13 @@ fwi_status conv_call(int n, int h, int w, int cin, int cout, const void *x, cons
         return fwi::record_error(FWI_ERR_INVALID_ARG,
                                  "cin and cout must be positive multiples of 64 (cin %d, cout %d)",
                                  cin, cout);
-    if (act != 0 && act != 1) return fwi::record_error(FWI_ERR_INVALID_ARG, "act must be 0 or 1");
+    if (y2) {
+        if (act != 2 || y_bf16 != 1 || ((uintptr_t)y2 & 15))
+            return fwi::record_error(FWI_ERR_INVALID_ARG,
+                                     "the activation output needs bf16 outputs, 16-byte aligned");
+    } else if (act != 0 && act != 1) {
+        return fwi::record_error(FWI_ERR_INVALID_ARG, "act must be 0 or 1");
+    }
     if (y_bf16 != 0 && y_bf16 != 1)
         return fwi::record_error(FWI_ERR_INVALID_ARG, "y_bf16 must be 0 or 1");
     if (!x || !wt || !y) return fwi::record_error(FWI_ERR_INVALID_ARG, "x, w and y must not be NULL");
@@ -1071,7 +1143,7 @@ fwi_status conv_call(int n, int h, int w, int cin, int cout, const void *x, cons
             return fwi::record_error(FWI_ERR_CUDA, "tensor map of w rejected");
     }
     ConvArgs a{wait_ns, withhold, n, h, w, cin, cout, act, y_bf16, tiles_x, tiles_y,
-               n * tiles_y * tiles_x, bias, y, status};
+               n * tiles_y * tiles_x, bias, y, status, y2};
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const cudaError_t e = pn ? launch_conv_pn(tmx, tmw, a, st) : launch_conv<256>(tmx, tmw, a, st);
     if (e != cudaSuccess)
@@ -1088,6 +1160,14 @@ fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, const void *
                             void *stream)
 {
     return conv_call(n, h, w, cin, cout, x, wt, bias, act, y, y_bf16, status, stream, 0, kWaitNs);
+}
+
+fwi_status fwi_conv3x3_bf16_silu(int n, int h, int w, int cin, int cout, const void *x,
+                                 const void *wt, const float *bias, void *p, void *a, int *status,
+                                 void *stream)
+{
+    if (!a) return fwi::record_error(FWI_ERR_INVALID_ARG, "a must not be NULL");
+    return conv_call(n, h, w, cin, cout, x, wt, bias, 2, p, 1, status, stream, 0, kWaitNs, a);
 }
 
 fwi_status fwi_conv3x3_bf16_wait_check(int n, int h, int w, int cin, int cout, const void *x,

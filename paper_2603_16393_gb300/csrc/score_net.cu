@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "fwi_internal.cuh"
+#include "silu.cuh"
 
 namespace {
 
@@ -57,14 +58,6 @@ __global__ void __launch_bounds__(kThreads)
         y[p] = scale * Y[p * C];
 }
 
-__device__ __forceinline__ float sigmoid(float p) { return 1.f / (1.f + __expf(-p)); }
-
-__device__ __forceinline__ float silu_of(float p) { return p * sigmoid(p); }
-__device__ __forceinline__ float silu_grad_of(float p)
-{
-    const float sg = sigmoid(p);
-    return sg * (1.f + p * (1.f - sg));
-}
 
 // VEC: 8 elements per thread through 16-byte accesses (n a multiple of 8,
 // 16-byte aligned arrays), else one element per thread

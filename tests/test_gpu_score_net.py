@@ -63,6 +63,32 @@ def test_elementwise_kernels(mods):
             assert np.all(err <= BF16_ULP * np.abs(ref) + 1e-30)
 
 
+@pytest.mark.parametrize("cout", [64, 128, 256])
+def test_fused_silu_epilogue_is_the_two_pass_layer(mods, cout):
+    # one launch writing p and SiLU(p) against the convolution (bf16 out)
+    # followed by fwi_silu_bf16: the same bits, on a ragged image (tiles cut
+    # at both edges), both kernel shapes (cout 256: pixels as M; 64, 128:
+    # pixels as N, a 64-channel remainder on zero weight rows)
+    A, _, _ = mods
+    n, h, w, cin = 2, 19, 23, 128
+    g = torch.Generator(device=DEV).manual_seed(cout)
+    x = torch.randn((n, h, w, cin), device=DEV, generator=g).to(torch.bfloat16)
+    wt = (0.05 * torch.randn((cout, 3, 3, cin), device=DEV, generator=g)).to(torch.bfloat16)
+    bias = torch.randn(cout, device=DEV, generator=g)
+    p1 = torch.empty((n, h, w, cout), dtype=torch.bfloat16, device=DEV)
+    a1 = torch.empty_like(p1)
+    A.fwi_conv3x3_bf16(x, wt, bias, 0, p1)
+    A.fwi_silu_bf16(p1, a1)
+    p2 = torch.full_like(p1, 7.0)
+    a2 = torch.full_like(p1, 7.0)
+    A.fwi_conv3x3_bf16_silu(x, wt, bias, p2, a2)
+    torch.cuda.synchronize()
+    assert torch.equal(p1.view(torch.int16), p2.view(torch.int16))
+    assert torch.equal(a1.view(torch.int16), a2.view(torch.int16))
+    with pytest.raises(A.FwiError):           # act 2 needs the activation output
+        A.fwi_conv3x3_bf16(x, wt, bias, 2, p1)
+
+
 @pytest.mark.parametrize("channels", [64, 128])
 def test_network_and_vjp_match_oracle(mods, channels):
     A, _, SN = mods

@@ -102,6 +102,12 @@ def test_conv_rejects_bad_arguments_without_a_gpu(api):
         lambda: lib.fwi_conv3x3_bf16(1, 4, 4, 64, 64, p, p, None, 2, p, 0, None, None),
         lambda: lib.fwi_conv3x3_bf16(1, 4, 4, 64, 64, p, p, None, 0, p, 3, None, None),
         lambda: lib.fwi_conv3x3_bf16(1, 4, 4, 64, 64, odd, p, None, 0, p, 0, None, None),
+        # the fused pre-activation + SiLU layer: no activation output, a
+        # misaligned one, no pre-activation output, an empty batch
+        lambda: lib.fwi_conv3x3_bf16_silu(1, 4, 4, 64, 64, p, p, None, p, None, None, None),
+        lambda: lib.fwi_conv3x3_bf16_silu(1, 4, 4, 64, 64, p, p, None, p, odd, None, None),
+        lambda: lib.fwi_conv3x3_bf16_silu(1, 4, 4, 64, 64, p, p, None, None, p, None, None),
+        lambda: lib.fwi_conv3x3_bf16_silu(0, 4, 4, 64, 64, p, p, None, p, p, None, None),
     ]
     for k, call in enumerate(calls):
         assert call() == 1, k

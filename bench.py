@@ -901,10 +901,10 @@ def run_posterior(args, rank, world, local_rank):
       graph_fd   all-FD guidance, every reverse step replayed from one CUDA
                  graph (sampler.GraphChain)
       graph_sur  the learned forward surrogate in the first 40% of the steps,
-                 judged by FD every 10 steps and replaced by FD for good once
+                 checked against FD every 10 steps and replaced by FD for good once
                  its gradient error exceeds 5%; trained first on FD pairs of
                  the clean estimates of those steps (training timed apart)
-      graph_sur_ungated  the same surrogate phase with the judge's verdicts
+      graph_sur_ungated  the same surrogate phase with the FD check's verdicts
                  recorded but not enforced (what the surrogate would save)
       plain      one plan per posterior sample (batch 1, five shots), eager
                  launches: timed over a few reverse steps of every sample; one
@@ -1044,7 +1044,7 @@ def run_posterior(args, rank, world, local_rank):
         chain_sur.capture(k)
     v_sur, ms_sur = timed(lambda: chain_sur.run(v_start).clone())
     q_sur = quality(v_sur)
-    # ---- arm graph_sur_ungated: the same surrogate phase with the judge's
+    # ---- arm graph_sur_ungated: the same surrogate phase with the FD check's
     # verdicts recorded but not enforced
     chain_free = S.GraphChain(plan, betas, ctx, prior, guide, zs, surrogate=guid,
                               surrogate_fraction=0.4, threshold=float("inf"), check_every=10)

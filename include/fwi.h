@@ -816,7 +816,7 @@ FWI_API fwi_status fwi_lowrank_score_at(int batch, int ncell, int k, const float
  * Data-side steps of a convolutional encoder-decoder that maps a velocity model
  * to the seismograms of the FD solver: the surrogate route to cheaper guidance
  * that Sec. 7 proposes, used in the early reverse steps of Algorithm 2 (Sec.
- * 5.2), with the FD solver as its judge and fallback.  The six convolutions run
+ * 5.2), with the FD solver as its check and fallback.  The six convolutions run
  * on fwi_conv3x3_bf16 (with fwi_silu_bf16, fwi_silu_grad_bf16, fwi_add_bf16,
  * fwi_conv3x3_wgrad_tc, fwi_channel_sum and fwi_adam_step for training).
  * Layout: model b is column (b mod m) of image (b / m), an image being nx pixels
@@ -889,7 +889,7 @@ FWI_API fwi_status fwi_sur_weights_prep(int cout, int cin, const float *W3, void
 FWI_API fwi_status fwi_sur_wgrad_centre(int cout, int cin, const float *dW, float *dW3,
                                         void *stream);
 
-/* The FD solver as judge of a surrogate's guidance gradient (Sec. 7's
+/* The FD solver as the check of a surrogate's guidance gradient (Sec. 7's
  * surrogate route, gated per noise level of Algorithm 2): per model b,
  *   err[b] = ||g_b - g_ref_b||_2 / ||g_ref_b||_2
  * over the n floats of model b (g, g_ref [nmod][n] fp32, device; err [nmod]

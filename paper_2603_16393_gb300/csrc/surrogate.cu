@@ -29,7 +29,7 @@
 //            transpose W^T[ci][ky][kx][co] = W[co][2-ky][2-kx][ci], from the
 //            three-tap float32 weights W3[co][ky][ci]
 //   k_wcentre dW3[co][ky][ci] = dW[co][ky][1][ci] (the taps the network has)
-//   k_rel_err err[b] = ||g_b - r_b|| / ||r_b|| per model (the FD judge's
+//   k_rel_err err[b] = ||g_b - r_b|| / ||r_b|| per model (the FD check's
 //            measure of the surrogate's gradient), sums in double, one CTA a
 //            model, a fixed order
 #include <cuda_bf16.h>

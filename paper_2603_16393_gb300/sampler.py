@@ -143,7 +143,7 @@ class Sampler:
     plan.w2_prepare), "l2" (Phi_l2 with ``d_obs`` and ``sigma_l2``) or None
     (no guidance: v_{i-1} = v').  Exactly one of ``prior`` and ``score_fn``.
     surrogate: a LowFidelity W2 potential, a NetworkSurrogate or a
-    surrogate.GatedSurrogate (the learned forward surrogate judged by FD) used
+    surrogate.GatedSurrogate (the learned forward surrogate checked by FD) used
     instead of the full one in the first ``surrogate_fraction`` of the reverse
     steps (i > N - round(fraction N)), the full physics after; its
     ``gradient(v_phys, stream=, step=)`` returns (J or None, dJ/dv)."""
@@ -271,7 +271,7 @@ class GraphChain:
       "sur"    a surrogate's gradient (surrogate.SurrogateGuidance)
       "check"  the full gradient drives the update, and the surrogate's
                gradient at the same model is compared with it: per-model
-               relative L2 errors into ``err`` (the FD solver as judge)
+               relative L2 errors into ``err`` (the FD solver as the check)
     ``run`` replays the chain; with a surrogate, the steps i > i_switch (the
     first ``surrogate_fraction`` of the chain) run "check" every
     ``check_every`` steps and "sur" between checks until a check's largest
@@ -377,7 +377,7 @@ class GraphChain:
             if i > self.i_switch and not rejected:
                 if since is None or since >= self.check_every:
                     self.graphs["check"].replay()
-                    err = float(self.err.max())           # the judge's verdict (a host read)
+                    err = float(self.err.max())           # the FD check's verdict (a host read)
                     rejected = err > self.threshold
                     self.records.append((i, err, not rejected))
                     self.counts["check"] += 1

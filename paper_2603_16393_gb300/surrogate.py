@@ -5,7 +5,7 @@ to cheaper guidance that Sec. 7 proposes: in the early, high-noise reverse
 steps of Algorithm 2 (Sec. 5.2) its W2 guidance gradient -- the W2 adjoint
 source of its predicted data (Eq. final_objective, fwi_w2_misfit) carried
 back through the network's vector-Jacobian product -- stands in for the FD
-gradient, and the FD solver stays both the judge of that gradient's error and
+gradient, and the FD solver stays both the check of that gradient's error and
 the fallback (GatedSurrogate).
 
 Network (every step runs in the CUDA library; bf16 activations and weights,
@@ -341,7 +341,7 @@ class SurrogateGuidance:
 
 def rel_error(g: torch.Tensor, g_ref: torch.Tensor, stream=None) -> torch.Tensor:
     """Per-model relative L2 error ||g - g_ref|| / ||g_ref|| [nmod] (fwi_rel_error:
-    the FD judge's measure)."""
+    the FD check's measure)."""
     return api.fwi_rel_error(g.contiguous(), g_ref.contiguous(), stream=stream)
 
 
@@ -353,7 +353,7 @@ class GateRecord:
 
 
 class GatedSurrogate:
-    """The surrogate with the FD solver as judge and fallback: at the first
+    """The surrogate with the FD solver as check and fallback: at the first
     step it is asked for and then every ``check_every`` steps, both gradients
     are computed and the surrogate's relative L2 error against FD (the largest
     over the batch's models) is recorded; above ``threshold`` the step uses

@@ -2,7 +2,7 @@
 reverse steps are bitwise the eager Sampler's, the batched chain is bitwise
 the plain path that runs one posterior sample per plan with eager launches
 (so the two reconstruct equally well by construction), and the FD gate of the
-surrogate phase judges, accepts and falls back on the device as it does on
+surrogate phase checks, accepts and falls back on the device as it does on
 the host."""
 import numpy as np
 import pytest
@@ -91,7 +91,7 @@ class _Offset:
 
 
 @pytest.mark.parametrize("rel,accepted", [(0.02, True), (0.2, False)])
-def test_device_gate_judges_and_falls_back(mods, rel, accepted):
+def test_device_gate_checks_and_falls_back(mods, rel, accepted):
     A, S, _ = mods
     gp, plan, _, ctx, prior, betas, zs, v0 = _setup(A, S, 2)
     guide = A.GuideParams(rho0=1.0, gamma=0.5)

@@ -2,7 +2,7 @@
 first 40% of the reverse steps, against the same chain with FD guidance in
 every step (70 x 70 models, 5 shots x 1000 FD steps, 10 dB observations, 2
 observations x 15 posterior samples, 100 reverse steps):
-  * gated at 5% (the FD solver as judge): the first check rejects the
+  * gated at 5% (the FD solver as the check): the first check rejects the
     surrogate (its W2 gradient misses FD's by far more than 5% on these
     inputs) and the chain falls back to FD for good -- bitwise the FD chain;
   * used without the gate: the chain costs at most 0.8 of the FD chain and
@@ -104,7 +104,7 @@ def test_surrogate_phase_cost_and_reconstruction(mods):
     v_free, ms_free = timed_run(free)
     plan.check()
 
-    # gated: the judge's first verdict decides the chain
+    # gated: the FD check's first verdict decides the chain
     first = gated.records[0]
     if not first[2]:
         assert gated.counts["sur"] == 0

@@ -181,7 +181,7 @@ def test_production_sizes_sampled_models(mods):
 
 
 def test_relative_error_per_model(mods):
-    # the FD judge's measure: ||g_b - r_b|| / ||r_b|| per model, FP64 sums
+    # the FD check's measure: ||g_b - r_b|| / ||r_b|| per model, FP64 sums
     A, _ = mods
     rng = np.random.default_rng(3)
     r = rng.standard_normal((5, 70, 70)).astype(np.float32) * 1e-7

@@ -3,7 +3,7 @@ FD seismograms of the clean estimates that the early reverse steps produce
 (70 x 70 models, 5 shots, 1000 steps) train the network, which then predicts
 the FD data of held-out clean estimates far better than before training (the
 gain of the trained network over an untrained one); its W2 guidance gradient
-is judged against FD per noise level, and the gate of the sampler falls back
+is checked against FD per noise level, and the gate of the sampler falls back
 to FD when that error exceeds 5%."""
 import numpy as np
 import pytest

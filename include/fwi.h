@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define FWI_VERSION 11300  /* major*10000 + minor*100 + patch */
+#define FWI_VERSION 11400  /* major*10000 + minor*100 + patch */
 
 #if defined(__GNUC__)
 #define FWI_API __attribute__((visibility("default")))
@@ -693,6 +693,19 @@ FWI_API fwi_status fwi_conv3x3_bf16(int n, int h, int w, int cin, int cout, cons
 FWI_API fwi_status fwi_conv3x3_bf16_silu(int n, int h, int w, int cin, int cout, const void *x,
                                          const void *wt, const float *bias, void *p, void *a,
                                          int *status, void *stream);
+
+/* The convolution (no bias) that carries a gradient back through a layer,
+ * followed by the SiLU derivative of the layer below in the same epilogue:
+ *   dp = bf16(g silu'(q)),  g = bf16(sum ...) widened,  q = p widened,
+ *   silu'(q) = sg (1 + q (1 - sg)),  sg = 1 / (1 + e^-q)
+ * -- bit for bit fwi_conv3x3_bf16 (act 0, bf16 output) followed by
+ * fwi_silu_grad_bf16 on that output and p.
+ *   p   [n][h][w][cout] bf16 device: the pre-activation, read only
+ *   dp  [n][h][w][cout] bf16 device, written; 16-byte aligned, aliasing neither x nor p
+ * Other arguments and errors as fwi_conv3x3_bf16. */
+FWI_API fwi_status fwi_conv3x3_bf16_silu_grad(int n, int h, int w, int cin, int cout,
+                                              const void *x, const void *wt, const void *p,
+                                              void *dp, int *status, void *stream);
 
 /* ---------------------------------------------------------------- reverse diffusion
  * The elementwise steps of one reverse step i -> i-1 of Algorithm 1 (DPS) and

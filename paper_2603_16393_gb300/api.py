@@ -145,6 +145,8 @@ _lib.fwi_conv3x3_bf16.argtypes = [ctypes.c_int] * 5 + [_vp, _vp, _vp, ctypes.c_i
                                                        ctypes.c_int, _vp, _vp]
 _lib.fwi_conv3x3_bf16_silu.restype = _S
 _lib.fwi_conv3x3_bf16_silu.argtypes = [ctypes.c_int] * 5 + [_vp] * 7
+_lib.fwi_conv3x3_bf16_silu_grad.restype = _S
+_lib.fwi_conv3x3_bf16_silu_grad.argtypes = [ctypes.c_int] * 5 + [_vp] * 6
 _lib.fwi_restrict2.restype = _S
 _lib.fwi_restrict2.argtypes = [ctypes.c_int] * 3 + [_vp] * 3
 _lib.fwi_restrict2_transpose.restype = _S
@@ -637,6 +639,24 @@ def fwi_conv3x3_bf16_silu(x, wt, bias, p, a, status=None, stream=None):
         _f32(bias, (cout,), "bias")
     _check(_lib.fwi_conv3x3_bf16_silu(n, h, w, cin, cout, _ptr(x), _ptr(wt), _ptr(bias), _ptr(p),
                                       _ptr(a), _ptr(status), _stream(stream)))
+
+
+def fwi_conv3x3_bf16_silu_grad(x, wt, p, dp, status=None, stream=None):
+    """The convolution (no bias) carrying a gradient x back through a layer,
+    times the SiLU derivative at the pre-activation p of the layer below: bit
+    for bit fwi_conv3x3_bf16 (act 0, bf16 out) followed by
+    fwi_silu_grad_bf16."""
+    n, h, w, cin = x.shape
+    cout = wt.shape[0]
+    if x.dtype != torch.bfloat16 or wt.dtype != torch.bfloat16:
+        raise TypeError("x and wt must be bfloat16")
+    if tuple(wt.shape) != (cout, 3, 3, cin):
+        raise ValueError(f"wt must have shape {(cout, 3, 3, cin)}, got {tuple(wt.shape)}")
+    for t, nm in ((p, "p"), (dp, "dp")):
+        if tuple(t.shape) != (n, h, w, cout) or t.dtype != torch.bfloat16:
+            raise ValueError(f"{nm} must be [n][h][w][cout] bfloat16")
+    _check(_lib.fwi_conv3x3_bf16_silu_grad(n, h, w, cin, cout, _ptr(x), _ptr(wt), _ptr(p),
+                                           _ptr(dp), _ptr(status), _stream(stream)))
 
 
 def fwi_conv3x3_bf16_wait_check(x, wt, y, status, stream=None):

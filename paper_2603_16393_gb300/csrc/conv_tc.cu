@@ -73,13 +73,15 @@ struct ConvArgs {
     unsigned long long wait_ns;    // bound of one mbarrier wait
     int withhold;                  // 1: never load the weight blocks (the wait self-check)
     int n, h, w, cin, cout;
-    int act;       // 0: none, 1: SiLU, 2: y = bf16(pre-activation), y2 = bf16(SiLU(y))
+    int act;       // 0: none, 1: SiLU, 2: y = bf16(pre-activation), y2 = bf16(SiLU(y)),
+                   // 3: y = bf16(bf16(conv) silu'(y2)) with y2 a bf16 input
+
     int y_bf16;    // output type: 0 fp32, 1 bf16
     int tiles_x, tiles_y, tiles;   // pixel tiles per image row / column, tiles in all
     const float *bias;
     void *y;
     int *status;
-    void *y2;      // act 2: the activation (bf16, y's layout)
+    void *y2;      // act 2: the activation out; act 3: the pre-activation in (bf16, y's layout)
 };
 
 __device__ __forceinline__ unsigned su32(const void *p)
@@ -421,6 +423,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
                         h2[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                    if (a.act == 3) {
+                        // times SiLU' of the pre-activation, as k_silu_grad forms it
+                        const uint4 *src = reinterpret_cast<const uint4 *>(
+                            static_cast<const __nv_bfloat16 *>(a.y2) + pix * a.cout + co);
+                        uint4 pp[2] = {src[0], src[1]};
+                        const __nv_bfloat162 *p2 = reinterpret_cast<const __nv_bfloat162 *>(pp);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float2 g = __bfloat1622float2(h2[i]), pf = __bfloat1622float2(p2[i]);
+                            h2[i] = __floats2bfloat162_rn(g.x * silu_grad_of(pf.x),
+                                                          g.y * silu_grad_of(pf.y));
+                        }
+                    }
                     uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(a.y) +
                                                            pix * a.cout + co);
                     dst[0] = *reinterpret_cast<uint4 *>(&h2[0]);
@@ -525,6 +540,25 @@ __device__ __forceinline__ void pn_store_rows(const __nv_bfloat16 *stg, __nv_bfl
         const size_t pix = ((size_t)tl.img * a.h + py) * a.w + px;
         *reinterpret_cast<uint4 *>(y + pix * a.cout + c + part * 8) =
             *reinterpret_cast<const uint4 *>(stg + j * 32 + part * 8);
+    }
+}
+
+// The reverse of pn_store_rows: rows [16 pixels][32 channels, from channel c]
+// of a bf16 NHWC tensor into the staging block (pixels outside the image
+// left as they are: their outputs are not stored).
+__device__ __forceinline__ void pn_load_rows(__nv_bfloat16 *stg, const __nv_bfloat16 *src,
+                                             const ConvArgs &a, const Tile &tl, int c0, int c,
+                                             int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int k = lane + 32 * i, j = k >> 2, part = k & 3;
+        const int m = c0 + j;
+        const int px = tl.x0 + (m % kPW), py = tl.y0 + m / kPW;
+        if (px >= a.w || py >= a.h) continue;
+        const size_t pix = ((size_t)tl.img * a.h + py) * a.w + px;
+        *reinterpret_cast<uint4 *>(stg + j * 32 + part * 8) =
+            *reinterpret_cast<const uint4 *>(src + pix * a.cout + c + part * 8);
     }
 }
 
@@ -672,11 +706,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // block, then two 16-byte stores a lane (a quarter of a
                     // pixel's row each)
                     __nv_bfloat16 yb[16];
+                    if (a.act == 3) {
+                        // the pre-activation's rows through the staging block,
+                        // then times SiLU' as k_silu_grad forms it
+                        pn_load_rows(stg, static_cast<const __nv_bfloat16 *>(a.y2), a, tl, c0,
+                                     tl.n0 + q * 32, lane);
+                        __syncwarp();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float x = v[j] + bias;
-                        yb[j] = __float2bfloat16_rn(a.act == 1 ? silu(x) : x);
-                        stg[j * 32 + lane] = yb[j];
+                        for (int j = 0; j < 16; ++j) yb[j] = stg[j * 32 + lane];
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float g = __bfloat162float(__float2bfloat16_rn(v[j] + bias));
+                            stg[j * 32 + lane] =
+                                __float2bfloat16_rn(g * silu_grad_of(__bfloat162float(yb[j])));
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float x = v[j] + bias;
+                            yb[j] = __float2bfloat16_rn(a.act == 1 ? silu(x) : x);
+                            stg[j * 32 + lane] = yb[j];
+                        }
                     }
                     __syncwarp();
                     pn_store_rows(stg, static_cast<__nv_bfloat16 *>(a.y), a, tl, c0,
@@ -1093,9 +1144,9 @@ fwi_status conv_call(int n, int h, int w, int cin, int cout, const void *x, cons
                                  "cin and cout must be positive multiples of 64 (cin %d, cout %d)",
                                  cin, cout);
     if (y2) {
-        if (act != 2 || y_bf16 != 1 || ((uintptr_t)y2 & 15))
+        if ((act != 2 && act != 3) || y_bf16 != 1 || ((uintptr_t)y2 & 15))
             return fwi::record_error(FWI_ERR_INVALID_ARG,
-                                     "the activation output needs bf16 outputs, 16-byte aligned");
+                                     "the second tensor needs bf16 outputs, 16-byte aligned");
     } else if (act != 0 && act != 1) {
         return fwi::record_error(FWI_ERR_INVALID_ARG, "act must be 0 or 1");
     }
@@ -1168,6 +1219,15 @@ fwi_status fwi_conv3x3_bf16_silu(int n, int h, int w, int cin, int cout, const v
 {
     if (!a) return fwi::record_error(FWI_ERR_INVALID_ARG, "a must not be NULL");
     return conv_call(n, h, w, cin, cout, x, wt, bias, 2, p, 1, status, stream, 0, kWaitNs, a);
+}
+
+fwi_status fwi_conv3x3_bf16_silu_grad(int n, int h, int w, int cin, int cout, const void *x,
+                                      const void *wt, const void *p, void *dp, int *status,
+                                      void *stream)
+{
+    if (!p) return fwi::record_error(FWI_ERR_INVALID_ARG, "p must not be NULL");
+    return conv_call(n, h, w, cin, cout, x, wt, nullptr, 3, dp, 1, status, stream, 0, kWaitNs,
+                     const_cast<void *>(p));
 }
 
 fwi_status fwi_conv3x3_bf16_wait_check(int n, int h, int w, int cin, int cout, const void *x,

@@ -11,9 +11,11 @@ Every step runs in the library: fwi_pack_channel0, fwi_conv3x3_bf16_silu
 SiLU written by one epilogue; the U-Net runs fwi_conv3x3_bf16 and
 fwi_silu_bf16), fwi_conv3x3_bf16 for the last layer, and for the product the
 same convolution with the transposed weights W^T[ci][ky][kx][co] =
-W[co][2-ky][2-kx][ci] (the adjoint of a zero-padded convolution), then
-fwi_silu_grad_bf16 and fwi_unpack_channel0.  The weights are the caller's,
-seeded, or trained here by denoising score matching (DSMTrainer, Eq.
+W[co][2-ky][2-kx][ci] (the adjoint of a zero-padded convolution) times SiLU'
+in its epilogue (fwi_conv3x3_bf16_silu_grad; the U-Net runs
+fwi_silu_grad_bf16 on its summed gradients), then fwi_unpack_channel0.  The
+weights are the caller's, seeded, or trained here by denoising score
+matching (DSMTrainer, Eq.
 L2_rewrite): the network keeps FP32 master parameters in one flat buffer
 and refreshes its bf16 weights, their transposes and the per-step bias
 tables from them with fwi_conv3x3_weights_prep and fwi_time_bias.
@@ -146,8 +148,7 @@ class ConvScore:
         for l in range(self.L - 1, -1, -1):
             if l > 0:
                 nxt = self.dH[1 - k]
-                api.fwi_conv3x3_bf16(d, self.WT[l], None, 0, nxt, stream=stream)
-                api.fwi_silu_grad_bf16(nxt, self.P[l - 1], nxt, stream)
+                api.fwi_conv3x3_bf16_silu_grad(d, self.WT[l], self.P[l - 1], nxt, stream=stream)
                 d, k = nxt, 1 - k
             else:
                 api.fwi_conv3x3_bf16(d, self.WT[0], None, 0, self.dX, stream=stream)
@@ -181,8 +182,7 @@ class ConvScore:
             api.fwi_time_bias_grad(db, self.phi[i], dE, stream)
             if l > 0:
                 nxt = self.dH[1 - k]
-                api.fwi_conv3x3_bf16(d, self.WT[l], None, 0, nxt, stream=stream)
-                api.fwi_silu_grad_bf16(nxt, self.P[l - 1], nxt, stream)
+                api.fwi_conv3x3_bf16_silu_grad(d, self.WT[l], self.P[l - 1], nxt, stream=stream)
                 d, k = nxt, 1 - k
 
     def __call__(self, v_i: torch.Tensor, i: int):

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol(api):
     lib = ctypes.CDLL(LIB)
     for n in declared_functions():
         assert hasattr(lib, n), n
-    assert api.fwi_version() == 11300
+    assert api.fwi_version() == 11400
 
 
 def _prob(api, **kw):

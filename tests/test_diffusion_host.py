@@ -108,6 +108,9 @@ def test_conv_rejects_bad_arguments_without_a_gpu(api):
         lambda: lib.fwi_conv3x3_bf16_silu(1, 4, 4, 64, 64, p, p, None, p, odd, None, None),
         lambda: lib.fwi_conv3x3_bf16_silu(1, 4, 4, 64, 64, p, p, None, None, p, None, None),
         lambda: lib.fwi_conv3x3_bf16_silu(0, 4, 4, 64, 64, p, p, None, p, p, None, None),
+        # the gradient convolution times SiLU': no pre-activation, a misaligned one
+        lambda: lib.fwi_conv3x3_bf16_silu_grad(1, 4, 4, 64, 64, p, p, None, p, None, None),
+        lambda: lib.fwi_conv3x3_bf16_silu_grad(1, 4, 4, 64, 64, p, p, odd, p, None, None),
     ]
     for k, call in enumerate(calls):
         assert call() == 1, k

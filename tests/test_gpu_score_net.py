@@ -89,6 +89,26 @@ def test_fused_silu_epilogue_is_the_two_pass_layer(mods, cout):
         A.fwi_conv3x3_bf16(x, wt, bias, 2, p1)
 
 
+@pytest.mark.parametrize("cout", [64, 128, 256])
+def test_fused_silu_grad_epilogue_is_the_two_pass_product(mods, cout):
+    # the gradient convolution times SiLU' of the layer below in one launch
+    # against the convolution (bf16 out) followed by fwi_silu_grad_bf16
+    A, _, _ = mods
+    n, h, w, cin = 2, 19, 23, 128
+    g = torch.Generator(device=DEV).manual_seed(100 + cout)
+    x = torch.randn((n, h, w, cin), device=DEV, generator=g).to(torch.bfloat16)
+    wt = (0.05 * torch.randn((cout, 3, 3, cin), device=DEV, generator=g)).to(torch.bfloat16)
+    p = (3 * torch.randn((n, h, w, cout), device=DEV, generator=g)).to(torch.bfloat16)
+    d1 = torch.empty((n, h, w, cout), dtype=torch.bfloat16, device=DEV)
+    A.fwi_conv3x3_bf16(x, wt, None, 0, d1)
+    A.fwi_silu_grad_bf16(d1, p, d1)
+    d2 = torch.full_like(d1, 7.0)
+    A.fwi_conv3x3_bf16_silu_grad(x, wt, p, d2)
+    torch.cuda.synchronize()
+    assert torch.equal(d1.view(torch.int16), d2.view(torch.int16))
+    assert float(d2.float().abs().max()) > 0
+
+
 @pytest.mark.parametrize("channels", [64, 128])
 def test_network_and_vjp_match_oracle(mods, channels):
     A, _, SN = mods
